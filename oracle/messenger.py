@@ -1,0 +1,255 @@
+"""Algorithm 1 (messenger-field Wiener sampler) and its G -> 0 Wiener-filter variant, in FP64.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``). The steps follow §2.2 in the paper's order, with
+A = I (§3.2) and the messenger covariance T = lambda * tau * I, where tau = min observed noise variance
+(Alg. 1 definitions) and N_bar = N - tau * I is kept fixed (the lambda-cooling reading below).
+
+Per sweep (Alg. 1):
+  1. pixel space, every pixel i:  t_i = mu_t + sqrt(var_t) * G,
+       mu_t  = (T d_i + N_bar_i s_i) / (T + N_bar_i),  var_t = T N_bar_i / (T + N_bar_i)   (observed)
+       mu_t  = s_i,                                      var_t = T                         (missing pixel,
+       the exact N_bar -> infinity limit of the same formulas; §1.1 treats missing data as infinite noise)
+  2. t_hat = U t                                           (unitary 2D DFT)
+  3. Fourier space, every mode k:  s_hat_k = mu_s + sqrt(var_s) * zeta_k,
+       mu_s = P_k / (P_k + T) * t_hat_k,   var_s = P_k T / (P_k + T)
+     (the variance line of Alg. 1 is labelled sigma^t_hat but is the s_hat variance used in the update;
+     zeta is the unitary DFT of real white noise so that s stays real)
+  4. s = U^dagger s_hat  (real part; the imaginary part is round-off)
+
+G -> 0 (§2.2, after Alg. 1) turns the sweep into a fixed-point iteration whose limit at lambda = 1 is the
+Wiener filter of Eq. 2-3. At messenger level lambda its limit is the Wiener filter with noise
+N + (lambda - 1) tau I (the joint density with T = lambda tau and fixed N_bar has marginal noise
+N_bar + T); the cooling schedule only changes how fast lambda = 1 is reached, not the answer.
+
+Noise layout (identical on the GPU; see ``oracle.philox``):
+  * t-draw: stream 0, counter group j = (y*W + x) // 4, variate slot (y*W + x) % 4;
+  * s-draw: stream 1, group g = kx*(H/2) + (ky mod H/2) for the half-spectrum mode (ky, kx),
+    kx in [0, W/2]; modes ky < H/2 use variates (z0, z1), modes ky >= H/2 use (z2, z3) as (Re, Im).
+    zeta = (Re + i Im)/sqrt(2) except: self-conjugate modes (kx in {0, W/2}, ky in {0, H/2}) take
+    zeta = Re (real, unit variance); modes with kx in {0, W/2} and ky > H/2 take conj(zeta) of the mode
+    at H - ky (their own draws are consumed but unused); kx > W/2 is the Hermitian image of W - kx.
+  * counter step for sweep i of a call is ``start_step + i``; chain id is the third counter word.
+"""
+from __future__ import annotations
+
+import math
+from functools import lru_cache
+
+import numpy as np
+
+from . import dft
+from .philox import STREAM_S, STREAM_T, normals4
+
+
+# ----------------------------------------------------------------------------------------------
+# problem set-up (Alg. 1 definitions of T and N_bar)
+# ----------------------------------------------------------------------------------------------
+def default_tau(Ndiag: np.ndarray, mask: np.ndarray, Pk: np.ndarray) -> float:
+    """tau = min over observed pixels of the noise variance (Alg. 1: T = min(N) I for A = I).
+
+    With no observed pixel the data carry no information and any tau > 0 gives a valid sampler;
+    this code base then takes tau = max_k P_k (1 if P = 0), which makes each sweep close to an exact
+    prior draw.
+    """
+    obs = mask == 0
+    if np.any(obs):
+        return float(np.min(Ndiag[obs].astype(np.float64)))
+    pmax = float(np.max(Pk))
+    return pmax if pmax > 0 else 1.0
+
+
+def _fields(d, Ndiag, mask, Pk):
+    d = np.asarray(d, dtype=np.float64)
+    N = np.asarray(Ndiag, dtype=np.float64)
+    m = np.asarray(mask) != 0
+    H, W = d.shape
+    Pfull = dft.half_to_full(np.asarray(Pk, dtype=np.float64), W)
+    return d, N, m, Pfull
+
+
+def pixel_update(s, d, N, miss, tau, lam, xi=None):
+    """Alg. 1 step 1 with T = lam*tau and N_bar = N - tau; ``xi`` = G(0,1) per pixel or None (G -> 0)."""
+    T = lam * tau
+    Nbar = np.where(miss, 0.0, N - tau)
+    denom = np.where(miss, 1.0, T + Nbar)
+    mu = np.where(miss, s, (T * d + Nbar * s) / denom)
+    if xi is None:
+        return mu
+    var = np.where(miss, T, T * Nbar / denom)
+    return mu + np.sqrt(var) * xi
+
+
+def fourier_update(t, Pfull, tau, lam, zeta=None):
+    """Alg. 1 steps 2-4: t_hat = U t, s_hat = mu_s + sqrt(var_s) zeta, s = U^dagger s_hat."""
+    T = lam * tau
+    th = dft.dft2(t)
+    sh = Pfull / (Pfull + T) * th
+    if zeta is not None:
+        sh = sh + np.sqrt(Pfull * T / (Pfull + T)) * zeta
+    s = dft.idft2(sh)
+    assert np.max(np.abs(s.imag)) <= 1e-9 * max(1.0, float(np.max(np.abs(s.real)))), "lost Hermitian symmetry"
+    return s.real
+
+
+# ----------------------------------------------------------------------------------------------
+# Gaussian variates in the counter layout shared with the GPU
+# ----------------------------------------------------------------------------------------------
+def draw_xi(seed: int, chain: int, step: int, H: int, W: int) -> np.ndarray:
+    """Pixel-space G(0,1) field [H][W] for one sweep (stream 0)."""
+    groups = np.arange(H * W // 4)
+    z = normals4(groups, step, chain, STREAM_T, seed)
+    return z.reshape(H, W)
+
+
+@lru_cache(maxsize=None)
+def _zeta_layout(H: int, W: int):
+    """Index maps of the s-draw layout for the half-spectrum [H][W//2+1] (see module docstring).
+
+    Returns (group, slot, kind) arrays of shape [H][W//2+1]: the counter group and variate pair that
+    feed each mode, and kind = 0 generic, 1 self-conjugate (real), 2 conjugate image of mode H - ky.
+    """
+    Hh, Wh = H // 2, W // 2
+    ky = np.arange(H)[:, None] * np.ones((1, Wh + 1), dtype=np.int64)
+    kx = np.ones((H, 1), dtype=np.int64) * np.arange(Wh + 1)[None, :]
+    group = kx * Hh + (ky % Hh)
+    slot = (ky >= Hh).astype(np.int64)
+    edge = (kx == 0) | (kx == Wh)
+    kind = np.zeros((H, Wh + 1), dtype=np.int64)
+    kind[edge & ((ky == 0) | (ky == Hh))] = 1
+    kind[edge & (ky > Hh)] = 2
+    for a in (group, slot, kind):
+        a.setflags(write=False)
+    return group, slot, kind
+
+
+def draw_zeta(seed: int, chain: int, step: int, H: int, W: int) -> np.ndarray:
+    """Hermitian complex white noise on the full spectrum [H][W] for one sweep (stream 1)."""
+    Hh, Wh = H // 2, W // 2
+    group, slot, kind = _zeta_layout(H, W)
+    z = normals4(np.arange((Wh + 1) * Hh), step, chain, STREAM_S, seed)    # [(Wh+1)*Hh, 4]
+    re = z[group, 2 * slot]
+    im = z[group, 2 * slot + 1]
+    half = (re + 1j * im) / math.sqrt(2.0)
+    half = np.where(kind == 1, re + 0j, half)
+    mirror = half[(H - np.arange(H)) % H, :]                # row H - ky of the same column
+    half = np.where(kind == 2, np.conj(mirror), half)
+    full = np.empty((H, W), dtype=np.complex128)
+    full[:, : Wh + 1] = half
+    kxs = np.arange(Wh + 1, W)
+    full[:, kxs] = np.conj(half[(H - np.arange(H))[:, None] % H, (W - kxs)[None, :]])
+    return full
+
+
+# ----------------------------------------------------------------------------------------------
+# Algorithm 1: the sampler
+# ----------------------------------------------------------------------------------------------
+def sample(d, Ndiag, mask, Pk, n_samples: int, seed: int, *, chain: int = 0, tau: float | None = None,
+           start_step: int = 0, burn_in: int = 0, thin: int = 1, init_s=None) -> np.ndarray:
+    """Draw ``n_samples`` posterior samples from one chain -> float64 [n_samples][H][W].
+
+    The chain starts at ``init_s`` (zero if None) and performs burn_in + n_samples*thin sweeps; sample m
+    is the state after sweep burn_in + (m+1)*thin. Sweep i uses counter step ``start_step + i``.
+    """
+    d, N, miss, Pfull = _fields(d, Ndiag, mask, Pk)
+    H, W = d.shape
+    if tau is None:
+        tau = default_tau(N, miss, Pk)
+    s = np.zeros((H, W)) if init_s is None else np.asarray(init_s, dtype=np.float64).copy()
+    out = np.empty((n_samples, H, W))
+    n_sweeps = burn_in + n_samples * thin
+    m = 0
+    for i in range(n_sweeps):
+        step = start_step + i
+        t = pixel_update(s, d, N, miss, tau, 1.0, draw_xi(seed, chain, step, H, W))
+        s = fourier_update(t, Pfull, tau, 1.0, draw_zeta(seed, chain, step, H, W))
+        done = i + 1
+        if done > burn_in and (done - burn_in) % thin == 0:
+            out[m] = s
+            m += 1
+    return out
+
+
+# ----------------------------------------------------------------------------------------------
+# G -> 0: Wiener filter with lambda-cooling
+# ----------------------------------------------------------------------------------------------
+def apply_S(v, Pfull):
+    """S v = U^dagger diag(P) U v (Eq. 7: S is diagonal in Fourier space)."""
+    return dft.idft2(Pfull * dft.dft2(v)).real
+
+
+def residual(s, d, Ndiag, mask, Pk, tau: float | None = None, lam: float = 1.0) -> float:
+    """Relative residual of the Wiener-filter equation at messenger level lambda.
+
+    The Wiener filter s_W = S (S + N)^-1 d (Eq. 2-3, A = I) solves (I + S N^-1) s = S N^-1 d, with
+    N^-1 = 0 on missing pixels. Returns ||s + S N^-1 (s - d)|| / ||S N^-1 d|| for noise
+    N + (lambda - 1) tau I (lambda = 1: the Wiener filter itself).
+    """
+    d, N, miss, Pfull = _fields(d, Ndiag, mask, Pk)
+    if tau is None:
+        tau = default_tau(N, miss, Pk)
+    Ninv = np.where(miss, 0.0, 1.0 / np.where(miss, 1.0, N + (lam - 1.0) * tau))
+    s = np.asarray(s, dtype=np.float64)
+    b = apply_S(Ninv * d, Pfull)
+    r = s + apply_S(Ninv * (s - d), Pfull)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(r) / nb) if nb > 0 else float(np.linalg.norm(r))
+
+
+class CoolingSchedule:
+    """lambda-cooling for the G -> 0 iteration (reading of §2.2; the schedule itself is not in the paper).
+
+    lambda_0 = max(1, max_k P_k / tau); after every ``check`` sweeps at level lambda the level residual
+    rho_lambda is measured; the level ends when rho_lambda < ``level_tol`` or after ``level_max`` sweeps,
+    and lambda <- max(1, eta * lambda). At lambda = 1 the iteration stops when rho < tol, or at max_iter.
+    """
+
+    def __init__(self, eta: float = 0.5, level_tol: float = 1e-2, level_max: int = 64, check: int = 1):
+        self.eta = eta
+        self.level_tol = level_tol
+        self.level_max = level_max
+        self.check = check
+
+    def lambda0(self, Pk, tau: float) -> float:
+        return max(1.0, float(np.max(Pk)) / tau)
+
+
+def wf_solve(d, Ndiag, mask, Pk, tau: float | None = None, tol: float = 1e-6, max_iter: int = 100000,
+             schedule: CoolingSchedule | None = None, init_s=None, return_history: bool = False):
+    """Wiener filter by the G -> 0 messenger iteration with lambda-cooling.
+
+    Returns (s, iters, rho) with rho the final lambda = 1 relative residual (see :func:`residual`).
+    """
+    d, N, miss, Pfull = _fields(d, Ndiag, mask, Pk)
+    H, W = d.shape
+    if tau is None:
+        tau = default_tau(N, miss, Pk)
+    sch = schedule or CoolingSchedule()
+    lam = sch.lambda0(Pk, tau)
+    s = np.zeros((H, W)) if init_s is None else np.asarray(init_s, dtype=np.float64).copy()
+    it = 0
+    level_it = 0
+    hist = []
+    rho = residual(s, d, N, miss, Pk, tau, 1.0)
+    while it < max_iter:
+        t = pixel_update(s, d, N, miss, tau, lam)
+        s = fourier_update(t, Pfull, tau, lam)
+        it += 1
+        level_it += 1
+        if level_it % sch.check:
+            continue
+        if lam > 1.0:
+            rl = residual(s, d, N, miss, Pk, tau, lam)
+            hist.append((it, lam, rl))
+            if rl < sch.level_tol or level_it >= sch.level_max:
+                lam = max(1.0, sch.eta * lam)
+                level_it = 0
+        else:
+            rho = residual(s, d, N, miss, Pk, tau, 1.0)
+            hist.append((it, lam, rho))
+            if rho < tol:
+                break
+    if lam > 1.0 or it == 0:
+        rho = residual(s, d, N, miss, Pk, tau, 1.0)
+    if return_history:
+        return s, it, rho, hist
+    return s, it, rho
