@@ -23,11 +23,15 @@ N_bar + T); the cooling schedule only changes how fast lambda = 1 is reached, no
 
 Noise layout (identical on the GPU; see ``oracle.philox``):
   * t-draw: stream 0, counter group j = (y*W + x) // 4, variate slot (y*W + x) % 4;
-  * s-draw: stream 1, group g = kx*(H/2) + (ky mod H/2) for the half-spectrum mode (ky, kx),
-    kx in [0, W/2]; modes ky < H/2 use variates (z0, z1), modes ky >= H/2 use (z2, z3) as (Re, Im).
-    zeta = (Re + i Im)/sqrt(2) except: self-conjugate modes (kx in {0, W/2}, ky in {0, H/2}) take
-    zeta = Re (real, unit variance); modes with kx in {0, W/2} and ky > H/2 take conj(zeta) of the mode
-    at H - ky (their own draws are consumed but unused); kx > W/2 is the Hermitian image of W - kx.
+  * s-draw: stream 1. One counter group feeds a mode and its mirror (ky, H - ky) of one column.
+    Interior columns kx in (0, W/2): group g = kx*(H/2) + j for j in [0, H/2); group j = 0 feeds the
+    modes ky = 0 (z0, z1) and ky = H/2 (z2, z3); group j > 0 feeds ky = j (z0, z1) and ky = H - j
+    (z2, z3); zeta = (Re + i Im)/sqrt(2).
+    Edge columns kx in {0, W/2} (Hermitian within the column): group g = j for j in (0, H/2) feeds
+    zeta = (z0 + i z1)/sqrt(2) at (j, 0) and (z2 + i z3)/sqrt(2) at (j, W/2); the modes H - j take the
+    complex conjugates; group 0 feeds the four self-conjugate modes with real, unit-variance zeta:
+    z0 -> (0, 0), z1 -> (H/2, 0), z2 -> (0, W/2), z3 -> (H/2, W/2).
+    kx > W/2 is the Hermitian image of (H - ky, W - kx).
   * counter step for sweep i of a call is ``start_step + i``; chain id is the third counter word.
 """
 from __future__ import annotations
@@ -103,32 +107,47 @@ def draw_xi(seed: int, chain: int, step: int, H: int, W: int) -> np.ndarray:
 
 @lru_cache(maxsize=None)
 def _zeta_layout(H: int, W: int):
-    """Index maps of the s-draw layout for the half-spectrum [H][W//2+1] (see module docstring).
+    """Index maps of the s-draw layout on the half-spectrum [H][W//2+1] (see module docstring).
 
-    Returns (group, slot, kind) arrays of shape [H][W//2+1]: the counter group and variate pair that
-    feed each mode, and kind = 0 generic, 1 self-conjugate (real), 2 conjugate image of mode H - ky.
+    Returns (group, re_slot, im_slot, kind) arrays of shape [H][W//2+1]: the counter group and the
+    variate slots for Re and Im of each mode, and kind = 0 complex, 1 self-conjugate (real, Re slot
+    only), 2 conjugate image of the mode at H - ky in the same column.
     """
     Hh, Wh = H // 2, W // 2
-    ky = np.arange(H)[:, None] * np.ones((1, Wh + 1), dtype=np.int64)
-    kx = np.ones((H, 1), dtype=np.int64) * np.arange(Wh + 1)[None, :]
-    group = kx * Hh + (ky % Hh)
-    slot = (ky >= Hh).astype(np.int64)
-    edge = (kx == 0) | (kx == Wh)
+    group = np.zeros((H, Wh + 1), dtype=np.int64)
+    re_slot = np.zeros((H, Wh + 1), dtype=np.int64)
+    im_slot = np.zeros((H, Wh + 1), dtype=np.int64)
     kind = np.zeros((H, Wh + 1), dtype=np.int64)
-    kind[edge & ((ky == 0) | (ky == Hh))] = 1
-    kind[edge & (ky > Hh)] = 2
-    for a in (group, slot, kind):
+    for kx in range(Wh + 1):
+        for ky in range(H):
+            if 0 < kx < Wh:                       # interior column: group pairs ky with H - ky
+                j = ky if ky < Hh else (0 if ky == Hh else H - ky)
+                first = ky < Hh
+                group[ky, kx] = kx * Hh + j
+                re_slot[ky, kx], im_slot[ky, kx] = (0, 1) if first else (2, 3)
+            else:                                 # edge column, Hermitian in ky
+                e = 0 if kx == 0 else 1
+                if ky == 0 or ky == Hh:
+                    group[ky, kx] = 0
+                    re_slot[ky, kx] = 2 * e + (0 if ky == 0 else 1)
+                    kind[ky, kx] = 1
+                elif ky < Hh:
+                    group[ky, kx] = ky
+                    re_slot[ky, kx], im_slot[ky, kx] = 2 * e, 2 * e + 1
+                else:
+                    kind[ky, kx] = 2
+    for a in (group, re_slot, im_slot, kind):
         a.setflags(write=False)
-    return group, slot, kind
+    return group, re_slot, im_slot, kind
 
 
 def draw_zeta(seed: int, chain: int, step: int, H: int, W: int) -> np.ndarray:
     """Hermitian complex white noise on the full spectrum [H][W] for one sweep (stream 1)."""
     Hh, Wh = H // 2, W // 2
-    group, slot, kind = _zeta_layout(H, W)
-    z = normals4(np.arange((Wh + 1) * Hh), step, chain, STREAM_S, seed)    # [(Wh+1)*Hh, 4]
-    re = z[group, 2 * slot]
-    im = z[group, 2 * slot + 1]
+    group, re_slot, im_slot, kind = _zeta_layout(H, W)
+    z = normals4(np.arange(Wh * Hh), step, chain, STREAM_S, seed)          # [(W/2)*(H/2), 4]
+    re = z[group, re_slot]
+    im = z[group, im_slot]
     half = (re + 1j * im) / math.sqrt(2.0)
     half = np.where(kind == 1, re + 0j, half)
     mirror = half[(H - np.arange(H)) % H, :]                # row H - ky of the same column
