@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark: 128x128 Wiener-posterior samples/s on one GB300 (messenger-field Gibbs sampler, Alg. 1).
+
+Workload (one "step"): the paper-shaped 128x128 problem (P ~ k^-2 with k0 = 1/32, noise variance
+U[0.01, 1], 10% of the pixels missing in two rectangles plus scattered pixels), 1024 independent chains
+x 100 posterior samples (thin 1, s0 = 0) in one call of the C ABI ``wf_sample_ex``. Inputs are seeded
+synthetic data of that shape (``paper_1810_02821_gb300.synth.config_paper128``).
+
+Printed JSON line (rank 0):
+  value      samples/s with inputs resident in HBM (events around each step; L2 flushed between steps)
+  e2e        same metric through the same C call with host buffers: pinned H2D of the inputs and a D2H
+             of every sample inside the timed region
+  roofline   the fused sampler kernel k_sample<128,1>: FFT flops (5 n log2 n per sweep) per launch over
+             its event-timed duration, against the FP32 peak derived from the SM count and max clock
+  cpu_baseline  the FP64 oracle on the host cores, on a bounded sample of the same workload
+  batched_vs_plain  the 1024-chain launch against one chain per launch
+
+``--impl reference`` times the oracle itself (the reference arm for this build) and prints the same line.
+Multi-GPU (torchrun): every rank runs the same workload on different chains (replicas, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H = W = 128
+N_CHAINS = 1024
+N_SAMPLES = 100
+METRIC = "128x128 Wiener-posterior samples/s (1 GB300)"
+UNIT = "samples/s"
+FLOPS_PER_SWEEP = 5.0 * H * W * math.log2(H * W)   # two real 2D FFTs at 2.5 n log2 n each
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # FMA = 2 flops
+WORKLOAD = "paper-shaped 128x128 image, 1024 independent chains x 100 posterior samples per step"
+PROFILE = os.path.join(ROOT, "profiles", "k_sample_128_paper128.txt")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="wf", choices=["wf", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the plain and single-chain measurements")
+    ap.add_argument("--chains", type=int, default=N_CHAINS, help="profiling only: chains per step")
+    ap.add_argument("--samples", type=int, default=N_SAMPLES, help="profiling only: samples per chain")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1810_02821_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of k_sample<128,1> from the committed ncu summary, if the kernel sources
+    are unchanged since it was taken (its 'csrc_hash' line); else None."""
+    if not os.path.exists(PROFILE):
+        return None
+    vals = {}
+    for line in open(PROFILE):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("csrc_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_workload"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(target_s: float = 12.0):
+    """The FP64 oracle (as it stands) on the host cores, on a bounded sample of the same workload."""
+    import numpy as np
+    from oracle import messenger as M
+    from paper_1810_02821_gb300 import synth
+    p = synth.config_paper128(0)
+    M.sample(p.d, p.Ndiag, p.mask, p.Pk, 1, seed=1)            # warm caches
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < target_s:
+        M.sample(p.d, p.Ndiag, p.mask, p.Pk, 10, seed=1, chain=n)
+        n += 10
+    dt = time.perf_counter() - t0
+    threads = os.cpu_count()
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            threads = max(i.get("num_threads", 1) for i in info)
+    except Exception:
+        pass
+    return {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n} sweeps (= samples) of one 128x128 chain of the same problem, {dt:.1f} s; "
+                      f"host has {os.cpu_count()} cores"}
+
+
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import messenger as M
+    from paper_1810_02821_gb300 import synth
+    p = synth.config_paper128(0)
+    per_step = 8   # samples per step: a bounded slice of the 1024 x 100 workload
+    for i in range(a.warmup):
+        M.sample(p.d, p.Ndiag, p.mask, p.Pk, per_step, seed=1, chain=i)
+    t0 = time.perf_counter()
+    for i in range(a.steps):
+        M.sample(p.d, p.Ndiag, p.mask, p.Pk, per_step, seed=1, chain=1000 + i)
+    dt = time.perf_counter() - t0
+    v = per_step * a.steps / dt
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + f" (reference arm: {per_step} samples of one chain per step)",
+                       "image": "128x128"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} sweeps of one 128x128 chain per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    global N_CHAINS, N_SAMPLES
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    N_CHAINS, N_SAMPLES = a.chains, a.samples
+    import torch
+    from paper_1810_02821_gb300 import build, synth, wf
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    wf.load_library()
+    wf.wf_set_kernel_timing(True)
+    dev = torch.device("cuda", local)
+    p = synth.config_paper128(0)
+    host = [torch.from_numpy(x) for x in (p.d, p.Ndiag, p.mask, p.Pk)]
+    d, Nd, mk, Pk = [x.to(dev) for x in host]
+    out = torch.empty((N_CHAINS, N_SAMPLES, H, W), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    chain0 = rank * N_CHAINS
+
+    def step(seed, o=out):
+        return wf.wf_sample_ex(d, Nd, mk, Pk, seed=seed, n_samples=N_SAMPLES, n_chains=N_CHAINS,
+                               chain_offset=chain0, out=o)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for i in range(a.warmup):
+        step(1 + i)
+    barrier()
+    stream = torch.cuda.current_stream()
+    step_ms, kern_ms = [], []
+    with ClockSampler(local) as clk:
+        barrier()
+        for i in range(a.steps):
+            flush.fill_(float(i))                         # evict L2 between timed steps (not timed)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(100 + i)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            kern_ms.append(wf.wf_last_kernel_ms())
+        barrier()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units = N_CHAINS * N_SAMPLES * a.steps * world
+    value = units / (total_ms / 1e3)
+
+    # end to end through the same call: pinned host inputs -> device -> samples -> pinned host
+    e2e = None
+    if not a.no_e2e:
+        hin = [x.pin_memory() for x in host]
+        hout = torch.empty(out.shape, dtype=torch.float32, pin_memory=True)
+        h2d = sum(x.numel() * x.element_size() for x in hin)
+        d2h = hout.numel() * hout.element_size()
+        e2e_steps = max(1, min(a.steps, 5))
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(e2e_steps):
+            dd, nn, mm, pp = [x.to(dev, non_blocking=True) for x in hin]
+            wf.wf_sample_ex(dd, nn, mm, pp, seed=500 + i, n_samples=N_SAMPLES, n_chains=N_CHAINS,
+                            chain_offset=chain0, out=out)
+            hout.copy_(out, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        ems = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ems], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": N_CHAINS * N_SAMPLES * e2e_steps * world / (ems / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps}
+        del hout
+
+    plain = single = None
+    if a.no_extras:
+        n_plain = 0
+    # batched (one launch for all chains) against plain (one chain per launch)
+    n_plain = 0 if a.no_extras else 16
+    if n_plain:
+        o1 = torch.empty((1, N_SAMPLES, H, W), dtype=torch.float32, device=dev)
+        wf.wf_sample_ex(d, Nd, mk, Pk, seed=9, n_samples=N_SAMPLES, n_chains=1, out=o1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for c in range(n_plain):
+            wf.wf_sample_ex(d, Nd, mk, Pk, seed=9, n_samples=N_SAMPLES, n_chains=1, chain_offset=chain0 + c,
+                            out=o1)
+        e1.record(stream)
+        e1.synchronize()
+        plain = n_plain * N_SAMPLES / (e0.elapsed_time(e1) / 1e3)
+
+        # one long chain (every 10th of 10^4 sweeps kept): sweeps/s of a single chain
+        ol = torch.empty((1, 1000, H, W), dtype=torch.float32, device=dev)
+        e0.record(stream)
+        wf.wf_sample_ex(d, Nd, mk, Pk, seed=3, n_samples=1000, n_chains=1, thin=10, out=ol)
+        e1.record(stream)
+        e1.synchronize()
+        single = 1e4 / (e0.elapsed_time(e1) / 1e3)
+
+    if rank != 0:
+        return
+    kms = statistics.mean(kern_ms)
+    flops = FLOPS_PER_SWEEP * N_CHAINS * N_SAMPLES
+    achieved = flops / (kms / 1e3) / 1e12
+    traffic = profiled_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "image": "128x128", "chains": N_CHAINS, "samples_per_chain": N_SAMPLES,
+                   "thin": 1, "l2": "flushed between timed steps (256 MiB write outside the step events)",
+                   "parallelism": f"replicas x{world}"},
+        "gibbs_steps_per_s": value,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                     "kernel": "wf::k_sample<128,1>", "kernel_ms": kms,
+                     "flops_per_launch": flops,
+                     "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x 2070 MHz (derived, not measured)"},
+        "batched_vs_plain": ({"batched": value, "plain_one_chain_per_launch": plain, "speedup": value / plain,
+                              "plain_chains_timed": n_plain} if plain else None),
+        "single_chain_sweeps_per_s": single,
+        "clocks": clk.summary(),
+        "gpu_launches": 3 * a.steps,
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if not a.no_cpu_baseline and world >= 1:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,141 @@
+/*
+ * wf.h — C ABI of the GB300 messenger-field Wiener filter and Wiener-posterior sampler.
+ *
+ * Problem (Jeffrey, Heavens & Fortio, "Fast Sampling from Wiener Posteriors for Image Data with
+ * Dataflow Engines", §1.1 Eq. 1-3 and §2.1 Eq. 4): data d = s + n on an H x W image (A = I), signal
+ * covariance S diagonal in Fourier space with power spectrum P(k) (§2.1, Eq. 7), noise covariance N
+ * diagonal in pixel space, missing pixels = infinite noise (§1.1). The library computes
+ *   - wf_solve:  the Wiener filter s_W = S (S + N)^-1 d (Eq. 2-3) by the G -> 0 messenger iteration
+ *                with lambda-cooling (§2.2, text after Alg. 1);
+ *   - wf_sample: draws from the Wiener posterior (Eq. 4) by the messenger-field Gibbs sampler (Alg. 1).
+ *
+ * Conventions (all calls):
+ *   - d, Ndiag: float32 [H][W], row-major. Ndiag > 0 is the noise variance; both are ignored where
+ *     mask != 0.
+ *   - mask: uint8 [H][W], nonzero = missing pixel.
+ *   - Pk: float32 [H][W/2+1], the half spectrum (ky in FFT order 0..H-1, kx = 0..W/2): P_k is the
+ *     variance of the unitary 2D DFT coefficient of s at mode k, i.e. <|(U s)_k|^2> with
+ *     U = F / sqrt(H W) and F the transform of Eq. 6 (see "normalisation" in the design notes).
+ *     P_k >= 0; P_k must be symmetric under k -> -k for the edge columns kx = 0 and kx = W/2.
+ *   - tau: messenger variance T = tau I (Alg. 1 definitions). tau <= 0 selects the paper's choice,
+ *     the minimum observed Ndiag (max_k P_k if every pixel is missing). A tau above the minimum observed
+ *     Ndiag is rejected with WF_ERR_TAU.
+ *   - Supported sizes: H == W in {16, 32, 64, 128} (wf_supported_size).
+ *   - Pointers named d, Ndiag, mask, Pk, out*, init_s are DEVICE pointers owned by the caller; pointers
+ *     to iters_out / resid_out / opts are HOST pointers (may be NULL where stated).
+ *   - Calls are ordered on `stream` and return after the stream has reached their end (they
+ *     synchronise on it to read the device status). The library allocates its scratch with
+ *     cudaMallocAsync on `stream` and frees it before returning.
+ *   - Errors never abort: the return value says what went wrong; outputs are then unspecified.
+ *     WF_ERR_CUDA keeps the CUDA error code for wf_last_cuda_error().
+ */
+#ifndef WF_H_
+#define WF_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* wf_stream_t; /* binary-compatible with cudaStream_t; NULL = legacy default */
+
+typedef enum {
+  WF_OK = 0,
+  WF_ERR_ARG = 1,            /* bad pointer / count / option, or Ndiag <= 0 / P < 0 on the inputs */
+  WF_ERR_TAU = 2,            /* tau > min observed Ndiag */
+  WF_ERR_SHAPE = 3,          /* unsupported H, W */
+  WF_ERR_CUDA = 4,           /* a CUDA runtime call failed: see wf_last_cuda_error() */
+  WF_ERR_NOT_CONVERGED = 5,  /* wf_solve reached max_iter; the last iterate is written */
+  WF_ERR_NONFINITE = 6,      /* NaN/Inf in an observed input, in P, or in the residual */
+  WF_ERR_TIMEOUT = 7         /* reserved: a bounded device-side wait gave up */
+} wf_status;
+
+/* Options of the Wiener-filter solve (wf_solve_ex). Fill with wf_solve_opts_default first. */
+typedef struct {
+  double tau;        /* <= 0: minimum observed Ndiag (Alg. 1 definition of T) */
+  double tol;        /* stop when the lambda = 1 relative residual ||s + S N^-1 (s - d)|| / ||S N^-1 d|| < tol */
+  double eta;        /* cooling factor in (0, 1): lambda_{j+1} = max(1, eta lambda_j), lambda_0 = max(1, max P / tau) */
+  double level_tol;  /* a level lambda > 1 ends when its own relative residual < level_tol ... */
+  int32_t level_max; /* ... or after level_max sweeps at that level */
+  int32_t check;     /* residual measured every `check` sweeps (>= 1) */
+  int32_t max_iter;  /* total sweep budget; WF_ERR_NOT_CONVERGED when exhausted */
+  int32_t reserved;
+  const float* init_s; /* device [H][W] starting iterate, or NULL for zero */
+} wf_solve_opts;
+
+/* Options of the sampler (wf_sample_ex). Fill with wf_sample_opts_default first. */
+typedef struct {
+  double tau;            /* <= 0: minimum observed Ndiag */
+  int64_t n_samples;     /* samples kept per chain (>= 0) */
+  int32_t n_chains;      /* independent chains (>= 1), all for the same data */
+  uint32_t chain_offset; /* chain c uses Philox chain word chain_offset + c */
+  uint32_t start_step;   /* Philox step word of the first sweep (resume a chain exactly) */
+  int32_t burn_in;       /* sweeps discarded before the first kept sample (>= 0) */
+  int32_t thin;          /* sweeps between kept samples (>= 1) */
+  int32_t init_per_chain;/* 1: init_s is [n_chains][H][W]; 0: one [H][W] state shared by all chains */
+  const float* init_s;   /* device starting state(s), or NULL for zero */
+} wf_sample_opts;
+
+void wf_solve_opts_default(wf_solve_opts* o);
+void wf_sample_opts_default(wf_sample_opts* o);
+
+/*
+ * Wiener filter (Eq. 2-3) by the G -> 0 messenger iteration with lambda-cooling (§2.2).
+ * out_s: device float32 [H][W]. iters_out (host, may be NULL): sweeps performed. resid_out (host, may
+ * be NULL): last measured lambda = 1 relative residual (-1 if never measured).
+ * Uses the defaults of wf_solve_opts_default with the given tau and tol.
+ */
+wf_status wf_solve(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int32_t H,
+                   int32_t W, double tau, double tol, float* out_s, int32_t* iters_out, double* resid_out,
+                   wf_stream_t stream);
+
+/* As wf_solve with every option explicit (opts may be NULL: defaults). */
+wf_status wf_solve_ex(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int32_t H,
+                      int32_t W, const wf_solve_opts* opts, float* out_s, int32_t* iters_out, double* resid_out,
+                      wf_stream_t stream);
+
+/*
+ * Wiener-posterior samples (Eq. 4) by Algorithm 1: one chain from s_0 = 0, no burn-in, thin 1, chain
+ * word 0, first step word 0. out: device float32 [n_samples][H][W]; sample m is the state after sweep
+ * m + 1. G(0,1) variates come from Philox4x32-10 keyed by `seed` (see the noise layout in the design
+ * notes), so the draws are reproducible and identical to the reference implementation's.
+ */
+wf_status wf_sample(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int32_t H,
+                    int32_t W, int64_t n_samples, uint64_t seed, float* out, wf_stream_t stream);
+
+/*
+ * Several chains, burn-in, thinning, resume. out: device float32 [n_chains][n_samples][H][W]; sample m of
+ * chain c is the state after sweep burn_in + (m + 1) * thin of that chain; sweep i uses Philox step word
+ * start_step + i and chain word chain_offset + c. Resuming from sample m with start_step advanced by
+ * the sweeps done reproduces the uninterrupted chain exactly.
+ */
+wf_status wf_sample_ex(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int32_t H,
+                       int32_t W, uint64_t seed, const wf_sample_opts* opts, float* out, wf_stream_t stream);
+
+/* 1 if (H, W) is supported by wf_solve / wf_sample, else 0. */
+int32_t wf_supported_size(int32_t H, int32_t W);
+
+/* Static description of a status code (never NULL). */
+const char* wf_status_string(wf_status s);
+
+/* The cudaError_t of the last WF_ERR_CUDA returned on this thread (0 if none). */
+int32_t wf_last_cuda_error(void);
+
+/*
+ * Kernel timing for benchmarks. With timing enabled (per host thread), each wf_solve* / wf_sample* call
+ * records CUDA events on its stream around its main kernel (the fused Gibbs / Wiener-filter kernel,
+ * not the set-up kernels); wf_last_kernel_ms returns that duration in milliseconds for the last call on
+ * this thread, or -1 if timing was off or the call failed before the kernel.
+ */
+void wf_set_kernel_timing(int32_t enable);
+double wf_last_kernel_ms(void);
+
+/* ABI version of this header: (major << 16) | minor. */
+int32_t wf_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WF_H_ */

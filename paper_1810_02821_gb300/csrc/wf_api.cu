@@ -1,0 +1,319 @@
+// C ABI of the messenger-field Wiener filter / sampler: argument checks, device set-up kernels, scratch,
+// launches of the fused kernels in wf_gibbs.cuh, and the status read-back.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include <cuda_runtime.h>
+
+#include "../../include/wf.h"
+#include "wf_launch.h"
+
+namespace {
+
+thread_local int g_last_cuda_error = 0;
+thread_local int g_timing = 0;
+thread_local double g_kernel_ms = -1.0;
+
+// CUDA events around the main kernel of a call (only when timing is enabled on this thread)
+struct KernelTimer : wf::LaunchTimer {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaStream_t st;
+  explicit KernelTimer(cudaStream_t s) : st(s) {
+    g_kernel_ms = -1.0;
+    if (!g_timing) return;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) e0 = e1 = nullptr;
+  }
+  void start() override { if (e0) cudaEventRecord(e0, st); }
+  void stop() override { if (e1) cudaEventRecord(e1, st); }
+  // after the stream has been synchronised
+  void collect() {
+    float ms = -1.0f;
+    if (e0 && e1 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) g_kernel_ms = ms;
+  }
+  ~KernelTimer() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+};
+
+using wf::kMaxLevels;
+
+wf_status cuda_fail(cudaError_t e) {
+  g_last_cuda_error = int(e);
+  return WF_ERR_CUDA;
+}
+
+#define WF_CUDA(call)                           \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+// ---------------------------------------------------------------------------------------------
+// set-up kernels
+// ---------------------------------------------------------------------------------------------
+// One block: tau = min observed Ndiag (or the caller's), max_k P_k, input checks, lambda_0, levels.
+__global__ void k_prep(const float* __restrict__ d, const float* __restrict__ Ndiag, const uint8_t* __restrict__ mask,
+                       const float* __restrict__ Pk, int H, int W, double tau_user, double eta, wf::Scalars* sc) {
+  __shared__ float s_min[32], s_max[32];
+  __shared__ int s_obs[32], s_bad[32], s_neg[32];
+  float vmin = INFINITY, vmax = 0.0f;
+  int nobs = 0, bad = 0, neg = 0;
+  const int n = H * W, nm = H * (W / 2 + 1);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    if (mask[i] == 0) {
+      const float nv = Ndiag[i], dv = d[i];
+      ++nobs;
+      if (!isfinite(nv) || !isfinite(dv)) bad = 1;
+      else if (!(nv > 0.0f)) neg = 1;
+      else vmin = fminf(vmin, nv);
+    }
+  }
+  for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+    const float p = Pk[i];
+    if (!isfinite(p)) bad = 1;
+    else if (p < 0.0f) neg = 1;
+    else vmax = fmaxf(vmax, p);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+    vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    nobs += __shfl_xor_sync(0xffffffffu, nobs, o);
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    neg |= __shfl_xor_sync(0xffffffffu, neg, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = int(blockDim.x >> 5);
+  if (l == 0) { s_min[w] = vmin; s_max[w] = vmax; s_obs[w] = nobs; s_bad[w] = bad; s_neg[w] = neg; }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  int total_obs = 0;
+  for (int i = 0; i < nw; ++i) {
+    vmin = fminf(vmin, s_min[i]);
+    vmax = fmaxf(vmax, s_max[i]);
+    total_obs += s_obs[i];
+    bad |= s_bad[i];
+    neg |= s_neg[i];
+  }
+  wf::Scalars r = wf::make_scalars(vmin, total_obs, vmax, bad, neg, tau_user, eta);
+  *sc = r;
+}
+
+// Per-pixel tables ([W][H], x-major so that row threads read consecutive addresses) and the
+// per-mode sample table, in FP64 then rounded once.
+__global__ void k_tables(const float* __restrict__ d, const float* __restrict__ Ndiag, const uint8_t* __restrict__ mask,
+                         const float* __restrict__ Pk, int H, int W, const wf::Scalars* __restrict__ sc,
+                         float2* __restrict__ aq, float2* __restrict__ dn, float2* __restrict__ fg) {
+  if (sc->status != 0) return;
+  const double tau = sc->tau;
+  const int n = H * W, nm = H * (W / 2 + 1);
+  const double inv_n = 1.0 / double(n);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + nm; i += gridDim.x * blockDim.x) {
+    if (i < n) {
+      const int y = i / W, x = i % W;
+      float2 a2, d2;
+      wf::table_pixel(d[i], Ndiag[i], mask[i] == 0, tau, &a2, &d2);
+      if (aq) aq[x * H + y] = a2;
+      if (dn) dn[x * H + y] = d2;
+    } else if (fg) {
+      const int j = i - n;
+      fg[j] = wf::table_mode(Pk[j], tau, inv_n);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// launch helpers per size
+// ---------------------------------------------------------------------------------------------
+bool size_ok(int H, int W) { return H == W && (H == 16 || H == 32 || H == 64 || H == 128); }
+
+// scratch carved from one stream-ordered allocation
+struct Scratch {
+  void* base = nullptr;
+  cudaStream_t st = nullptr;
+  ~Scratch() {
+    if (base) cudaFreeAsync(base, st);
+  }
+};
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+extern "C" {
+
+void wf_solve_opts_default(wf_solve_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tau = 0.0;
+  o->tol = 1e-6;
+  o->eta = 0.5;
+  o->level_tol = 1e-2;
+  o->level_max = 64;
+  o->check = 4;
+  o->max_iter = 20000;
+  o->init_s = nullptr;
+}
+
+void wf_sample_opts_default(wf_sample_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tau = 0.0;
+  o->n_samples = 0;
+  o->n_chains = 1;
+  o->chain_offset = 0;
+  o->start_step = 0;
+  o->burn_in = 0;
+  o->thin = 1;
+  o->init_per_chain = 0;
+  o->init_s = nullptr;
+}
+
+int32_t wf_supported_size(int32_t H, int32_t W) { return size_ok(H, W) ? 1 : 0; }
+
+int32_t wf_abi_version(void) { return (1 << 16) | 0; }
+
+int32_t wf_last_cuda_error(void) { return g_last_cuda_error; }
+
+void wf_set_kernel_timing(int32_t enable) { g_timing = enable ? 1 : 0; }
+
+double wf_last_kernel_ms(void) { return g_kernel_ms; }
+
+const char* wf_status_string(wf_status s) {
+  switch (s) {
+    case WF_OK: return "ok";
+    case WF_ERR_ARG: return "invalid argument";
+    case WF_ERR_TAU: return "tau exceeds the minimum observed noise variance";
+    case WF_ERR_SHAPE: return "unsupported image shape";
+    case WF_ERR_CUDA: return "CUDA runtime error";
+    case WF_ERR_NOT_CONVERGED: return "not converged within max_iter";
+    case WF_ERR_NONFINITE: return "non-finite input or residual";
+    case WF_ERR_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+wf_status wf_solve_ex(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int32_t H, int32_t W,
+                      const wf_solve_opts* opts, float* out_s, int32_t* iters_out, double* resid_out,
+                      wf_stream_t stream) {
+  wf_solve_opts o;
+  wf_solve_opts_default(&o);
+  if (opts) o = *opts;
+  if (!d || !Ndiag || !mask || !Pk || !out_s) return WF_ERR_ARG;
+  if (!size_ok(H, W)) return WF_ERR_SHAPE;
+  if (!(o.tol >= 0.0) || !(o.eta > 0.0 && o.eta < 1.0) || !(o.level_tol >= 0.0) || o.level_max < 1 || o.check < 1 ||
+      o.max_iter < 1)
+    return WF_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t n = size_t(H) * W, nm = size_t(H) * (W / 2 + 1);
+  const size_t off_sc = 0, off_st = align256(sizeof(wf::Scalars)),
+               off_bn = off_st + align256(sizeof(wf::SolveStatus)),
+               off_dn = off_bn + align256(kMaxLevels * sizeof(double)), off_prev = off_dn + align256(n * sizeof(float2)),
+               total = off_prev + align256(size_t(H) * (W / 2) * sizeof(float2));
+  (void)nm;
+  Scratch scr;
+  scr.st = st;
+  WF_CUDA(cudaMallocAsync(&scr.base, total, st));
+  char* b = static_cast<char*>(scr.base);
+  auto* sc = reinterpret_cast<wf::Scalars*>(b + off_sc);
+  auto* sst = reinterpret_cast<wf::SolveStatus*>(b + off_st);
+  auto* bn = reinterpret_cast<double*>(b + off_bn);
+  auto* dn = reinterpret_cast<float2*>(b + off_dn);
+  auto* prev = reinterpret_cast<float2*>(b + off_prev);
+  WF_CUDA(cudaMemsetAsync(sst, 0, sizeof(wf::SolveStatus), st));
+  k_prep<<<1, 1024, 0, st>>>(d, Ndiag, mask, Pk, H, W, o.tau, o.eta, sc);
+  WF_CUDA(cudaGetLastError());
+  k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc, nullptr, dn, nullptr);
+  WF_CUDA(cudaGetLastError());
+  wf::SolveArgs a{};
+  a.dn = dn; a.Pk = Pk; a.sc = sc; a.bnorm2 = bn; a.init_s = o.init_s; a.prev = prev; a.out = out_s; a.st = sst;
+  a.tol = o.tol; a.eta = o.eta; a.level_tol = o.level_tol; a.max_iter = o.max_iter; a.level_max = o.level_max;
+  a.check = o.check;
+  wf::BnormArgs bb{dn, Pk, sc, bn, o.eta};
+  KernelTimer timer(st);
+  cudaError_t e = cudaSuccess;
+  switch (H) {
+    case 16: e = wf::launch_solve<16>(a, bb, st, &timer); break;
+    case 32: e = wf::launch_solve<32>(a, bb, st, &timer); break;
+    case 64: e = wf::launch_solve<64>(a, bb, st, &timer); break;
+    case 128: e = wf::launch_solve<128>(a, bb, st, &timer); break;
+  }
+  if (e != cudaSuccess) return cuda_fail(e);
+  wf::Scalars hsc;
+  wf::SolveStatus hst;
+  WF_CUDA(cudaMemcpyAsync(&hsc, sc, sizeof(hsc), cudaMemcpyDeviceToHost, st));
+  WF_CUDA(cudaMemcpyAsync(&hst, sst, sizeof(hst), cudaMemcpyDeviceToHost, st));
+  WF_CUDA(cudaStreamSynchronize(st));
+  timer.collect();
+  if (hsc.status != WF_OK) return wf_status(hsc.status);
+  if (iters_out) *iters_out = hst.iters;
+  if (resid_out) *resid_out = hst.resid;
+  return wf_status(hst.status);
+}
+
+wf_status wf_solve(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int32_t H, int32_t W,
+                   double tau, double tol, float* out_s, int32_t* iters_out, double* resid_out, wf_stream_t stream) {
+  wf_solve_opts o;
+  wf_solve_opts_default(&o);
+  o.tau = tau;
+  o.tol = tol;
+  return wf_solve_ex(d, Ndiag, mask, Pk, H, W, &o, out_s, iters_out, resid_out, stream);
+}
+
+wf_status wf_sample_ex(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int32_t H, int32_t W,
+                       uint64_t seed, const wf_sample_opts* opts, float* out, wf_stream_t stream) {
+  if (!opts) return WF_ERR_ARG;
+  const wf_sample_opts o = *opts;
+  if (!d || !Ndiag || !mask || !Pk) return WF_ERR_ARG;
+  if (!size_ok(H, W)) return WF_ERR_SHAPE;
+  if (o.n_samples < 0 || o.n_chains < 1 || o.burn_in < 0 || o.thin < 1) return WF_ERR_ARG;
+  if (o.n_samples == 0) return WF_OK;
+  if (!out) return WF_ERR_ARG;
+  const long long sweeps = (long long)o.burn_in + o.n_samples * (long long)o.thin;
+  if (sweeps > 0x7fffffffLL || o.n_samples > 0x7fffffffLL) return WF_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t n = size_t(H) * W, nm = size_t(H) * (W / 2 + 1);
+  const size_t off_sc = 0, off_aq = align256(sizeof(wf::Scalars)), off_fg = off_aq + align256(n * sizeof(float2)),
+               total = off_fg + align256(nm * sizeof(float2));
+  Scratch scr;
+  scr.st = st;
+  WF_CUDA(cudaMallocAsync(&scr.base, total, st));
+  char* b = static_cast<char*>(scr.base);
+  auto* sc = reinterpret_cast<wf::Scalars*>(b + off_sc);
+  auto* aq = reinterpret_cast<float2*>(b + off_aq);
+  auto* fg = reinterpret_cast<float2*>(b + off_fg);
+  k_prep<<<1, 1024, 0, st>>>(d, Ndiag, mask, Pk, H, W, o.tau, 0.5, sc);
+  WF_CUDA(cudaGetLastError());
+  k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc, aq, nullptr, fg);
+  WF_CUDA(cudaGetLastError());
+  wf::SampleArgs a{};
+  a.aq = aq; a.fg = fg; a.sc = sc; a.init_s = o.init_s;
+  a.init_stride = (o.init_s && o.init_per_chain) ? (long long)n : 0;
+  a.out = out; a.n_samples = o.n_samples; a.n_chains = o.n_chains; a.n_sweeps = int(sweeps);
+  a.burn_in = o.burn_in; a.thin = o.thin; a.chain0 = o.chain_offset; a.step0 = o.start_step;
+  a.key0 = uint32_t(seed & 0xffffffffu); a.key1 = uint32_t(seed >> 32);
+  KernelTimer timer(st);
+  cudaError_t e = cudaSuccess;
+  switch (H) {
+    case 16: e = wf::launch_sample<16>(a, st, &timer); break;
+    case 32: e = wf::launch_sample<32>(a, st, &timer); break;
+    case 64: e = wf::launch_sample<64>(a, st, &timer); break;
+    case 128: e = wf::launch_sample<128>(a, st, &timer); break;
+  }
+  if (e != cudaSuccess) return cuda_fail(e);
+  wf::Scalars hsc;
+  WF_CUDA(cudaMemcpyAsync(&hsc, sc, sizeof(hsc), cudaMemcpyDeviceToHost, st));
+  WF_CUDA(cudaStreamSynchronize(st));
+  timer.collect();
+  return wf_status(hsc.status);
+}
+
+wf_status wf_sample(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int32_t H, int32_t W,
+                    int64_t n_samples, uint64_t seed, float* out, wf_stream_t stream) {
+  wf_sample_opts o;
+  wf_sample_opts_default(&o);
+  o.n_samples = n_samples;
+  return wf_sample_ex(d, Ndiag, mask, Pk, H, W, seed, &o, out, stream);
+}
+
+}  // extern "C"

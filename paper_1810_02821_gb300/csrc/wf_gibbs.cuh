@@ -1,0 +1,689 @@
+// Fused messenger-field Gibbs step (Alg. 1 of the paper, A = I) with the field resident in shared memory.
+//
+// One field (one chain of one image, N x N pixels, N in {16, 32, 64, 128}) is owned by N threads and
+// one shared-memory buffer holding the packed half-spectrum [H][W/2] (float2, row stride W/2 + 1):
+//   element (y, 0) packs the real kx = 0 and kx = W/2 values as (re, im); (y, kx) is kx otherwise.
+//
+// A sweep is two passes, each ending in a CTA barrier:
+//   column pass (thread = column c, role r = parity of ky):
+//       radix-2 split on load -> in-register FFT of length H/2 -> Fourier-space draw
+//       s_hat = f t_hat + g zeta for every mode it holds (Alg. 1 s-update, Philox stream 1)
+//       -> inverse FFT -> radix-2 twiddle -> store
+//   row pass (thread = row y):
+//       radix-2 combine on load -> C2R row transform -> s (real row in registers) -> [write sample]
+//       -> pixel draw t = w s + (1 - w) d + sqrt(tau w) xi (Alg. 1 t-update, Philox stream 0)
+//       -> R2C row transform -> store
+// Scale factors of the unnormalised transforms are folded into the Fourier-space coefficients:
+// f' = f / n and g' = g / sqrt(2 n) (per real component of an interior mode).
+#pragma once
+
+#include <cmath>
+#include <cstdint>
+#include <limits>
+
+#include "wf_math.cuh"
+
+namespace wf {
+
+template <int I>
+using ic = std::integral_constant<int, I>;
+template <class F, int... I>
+WF_HD void sfor_impl(F&& f, std::integer_sequence<int, I...>) {
+  (f(ic<I>{}), ...);
+}
+// compile-time loop: f(ic<0>), ..., f(ic<N-1>)
+template <int N, class F>
+WF_HD void sfor(F&& f) {
+  sfor_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+#if defined(__CUDA_ARCH__)
+#define WF_LDG(p) __ldg(p)
+#else
+#define WF_LDG(p) (*(p))
+#endif
+WF_HD float wf_rcp(float x) {
+#if defined(__CUDA_ARCH__)
+  return __frcp_rn(x);
+#else
+  return 1.0f / x;
+#endif
+}
+WF_HD float wf_inf() {
+#if defined(__CUDA_ARCH__)
+  return __int_as_float(0x7f800000);
+#else
+  return std::numeric_limits<float>::infinity();
+#endif
+}
+
+template <int N_>
+struct Geo {
+  static constexpr int N = N_, H = N_, W = N_;
+  static constexpr int LR = N / 2;  // complex length of a row transform
+  static constexpr int LC = N / 2;  // half length of a column (radix-2 split)
+  static constexpr int SP = LR + 1;  // float2 stride of a spectrum row in shared memory
+  static constexpr int STG = W + 1;  // float stride of a staged real row
+  static constexpr int SPEC_BYTES = H * SP * 8;
+  static constexpr int STG_BYTES = H * STG * 4;
+  static constexpr int FIELD_BYTES = ((SPEC_BYTES > STG_BYTES ? SPEC_BYTES : STG_BYTES) + 15) / 16 * 16;
+  static constexpr int WH = W / 2 + 1;  // columns of the [H][W/2+1] mode tables
+};
+
+// Per-call scalars computed on the device by the set-up kernel.
+struct Scalars {
+  double tau;      // messenger variance T = tau I (Alg. 1: min observed noise variance)
+  double lam0;     // first lambda-cooling level
+  double pmax;     // max_k P_k
+  float sqrt_tau;
+  int n_levels;    // number of cooling levels including lambda = 1
+  int status;      // wf_status of the set-up; kernels do nothing unless 0
+  int pad;
+};
+
+// Result of one Wiener-filter solve.
+struct SolveStatus {
+  double resid;
+  int iters;
+  int status;
+};
+
+// ---------------------------------------------------------------------------------------------
+// set-up arithmetic (FP64, once per call)
+// ---------------------------------------------------------------------------------------------
+constexpr int kMaxLevels = 64;
+
+// tau, lambda_0 and the number of cooling levels from the reductions over the inputs.
+// lambda_j = max(1, lambda_0 eta^j); the last level (index n_levels - 1) is lambda = 1.
+WF_HD Scalars make_scalars(float min_obs, int n_obs, float pmax, int bad, int neg, double tau_user, double eta) {
+  Scalars r{};
+  r.status = 0;
+  if (bad) r.status = 6;       // WF_ERR_NONFINITE
+  else if (neg) r.status = 1;  // WF_ERR_ARG
+  double tau;
+  if (tau_user > 0.0) {
+    tau = tau_user;
+    if (n_obs > 0 && tau_user > double(min_obs) && r.status == 0) r.status = 2;  // WF_ERR_TAU
+  } else {
+    tau = n_obs > 0 ? double(min_obs) : (pmax > 0.0f ? double(pmax) : 1.0);
+  }
+  r.tau = tau;
+  r.sqrt_tau = float(sqrt(tau));
+  r.pmax = double(pmax);
+  r.lam0 = fmax(1.0, double(pmax) / tau);
+  int levels = 1;
+  double lam = r.lam0;
+  while (lam > 1.0 && levels < kMaxLevels) {
+    lam = fmax(1.0, lam * eta);
+    ++levels;
+  }
+  r.n_levels = levels;
+  return r;
+}
+
+// lambda of cooling level lev
+WF_HD double level_lambda(const Scalars& sc, int lev, double eta) {
+  return lev >= sc.n_levels - 1 ? 1.0 : fmax(1.0, sc.lam0 * pow(eta, double(lev)));
+}
+
+// per-pixel tables of pixel i = y*W + x, stored at x*H + y:
+//   aq = ((1 - w) d, sqrt(w)) with w = N_bar/(tau + N_bar)  (sampler, lambda = 1; w = 1, a = 0 if missing)
+//   dn = (d, 1/N_bar)                                        (Wiener filter; (0, 0) if missing)
+WF_HD void table_pixel(float dv_in, float nv, bool obs, double tau, float2* aq, float2* dn) {
+  double a = 0.0, wgt = 1.0, dv = 0.0, inb = 0.0;
+  if (obs) {
+    dv = double(dv_in);
+    const double nbar = double(nv) - tau;  // >= 0 since tau <= min observed Ndiag
+    wgt = nbar / (tau + nbar);
+    a = tau / (tau + nbar) * dv;
+    inb = nbar > 0.0 ? 1.0 / nbar : double(wf_inf());
+  }
+  *aq = make_float2(float(a), float(sqrt(wgt)));
+  *dn = make_float2(float(dv), float(inb));
+}
+
+// per-mode sampler table: (f / n, g / sqrt(2 n)), f = P/(P + tau), g^2 = P tau/(P + tau) (Alg. 1)
+WF_HD float2 table_mode(float Pv, double tau, double inv_n) {
+  const double P = double(Pv);
+  const double f = P > 0.0 ? P / (P + tau) : 0.0;
+  const double g2 = P > 0.0 ? P * tau / (P + tau) : 0.0;
+  return make_float2(float(f * inv_n), float(sqrt(g2 * 0.5 * inv_n)));
+}
+
+// ---------------------------------------------------------------------------------------------
+// shared-memory passes (lt = thread index within the field, in [0, N))
+// ---------------------------------------------------------------------------------------------
+template <int N>
+WF_HD void row_load_spec(const float2* S, int lt, float2 (&c)[N / 2]) {
+  using G = Geo<N>;
+  const int col = lt % G::LC, r = lt / G::LC;
+  const float2* e = S + col * G::SP;
+  const float2* o = S + (col + G::LC) * G::SP;
+  if (r == 0) {
+#pragma unroll
+    for (int k = 0; k < G::LR; ++k) c[k] = cadd(e[k], o[k]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < G::LR; ++k) c[k] = csub(e[k], o[k]);
+  }
+}
+
+template <int N>
+WF_HD void row_store_spec(float2* S, int y, const float2 (&c)[N / 2]) {
+  using G = Geo<N>;
+#pragma unroll
+  for (int k = 0; k < G::LR; ++k) S[y * G::SP + k] = c[k];
+}
+
+// packed half-spectrum row (after the inverse column transform) -> c[m] = (s[2m], s[2m+1])
+template <int N>
+WF_HD void row_inverse(float2 (&c)[N / 2]) {
+  c2r_pre_all<N / 2>(c, std::make_integer_sequence<int, N / 2>{});
+  fft<N / 2, true>(c);
+}
+// c[m] = (t[2m], t[2m+1]) -> packed half-spectrum row
+template <int N>
+WF_HD void row_forward(float2 (&c)[N / 2]) {
+  fft<N / 2, false>(c);
+  r2c_post_all<N / 2>(c, std::make_integer_sequence<int, N / 2>{});
+}
+
+// column load with the radix-2 decimation-in-frequency split; x[k'] -> Y[2k' + r] after fft
+template <int N>
+WF_HD void col_load(const float2* S, int lt, float2 (&x)[N / 2]) {
+  using G = Geo<N>;
+  const int col = lt % G::LC, r = lt / G::LC;
+  if (r == 0) {
+#pragma unroll
+    for (int n = 0; n < G::LC; ++n) x[n] = cadd(S[n * G::SP + col], S[(n + G::LC) * G::SP + col]);
+  } else {
+    sfor<G::LC>([&](auto I) {
+      constexpr int n = decltype(I)::value;
+      x[n] = twiddle<n, G::H, false>(csub(S[n * G::SP + col], S[(n + G::LC) * G::SP + col]));
+    });
+  }
+}
+
+// inverse column transform of the modes held by this thread, then store e[n] (r = 0, rows [0, LC))
+// or o[n] = exp(+2 pi i n / H) * IFFT(odd)[n] (r = 1, rows [LC, H)).
+template <int N>
+WF_HD void col_inverse_store(float2* S, int lt, float2 (&x)[N / 2]) {
+  using G = Geo<N>;
+  const int col = lt % G::LC, r = lt / G::LC;
+  fft<G::LC, true>(x);
+  if (r == 0) {
+#pragma unroll
+    for (int n = 0; n < G::LC; ++n) S[n * G::SP + col] = x[n];
+  } else {
+    sfor<G::LC>([&](auto I) {
+      constexpr int n = decltype(I)::value;
+      S[(n + G::LC) * G::SP + col] = twiddle<n, G::H, true>(x[n]);
+    });
+  }
+}
+
+// mode pairs held by a column thread: register kp and its mirror register, with their ky values.
+// role 0 holds even ky: (kp, LC/2) for kp = 0 (ky 0 and H/2), (kp, LC - kp) otherwise (ky, H - ky).
+// role 1 holds odd ky: (kp, LC - 1 - kp) (ky = 2kp + 1 and H - ky).
+// f(kp, kq, ky1, ky2, ic<IS_ZERO_GROUP>) is called with compile-time register indices.
+template <int N, class F>
+WF_HD void for_mode_pairs(int r, F&& f) {
+  using G = Geo<N>;
+  if (r == 0) {
+    sfor<G::LC / 2>([&](auto I) {
+      constexpr int kp = decltype(I)::value;
+      constexpr int kq = kp == 0 ? G::LC / 2 : G::LC - kp;
+      f(ic<kp>{}, ic<kq>{}, 2 * kp, kp == 0 ? G::H / 2 : G::H - 2 * kp, ic<kp == 0>{});
+    });
+  } else {
+    sfor<G::LC / 2>([&](auto I) {
+      constexpr int kp = decltype(I)::value;
+      constexpr int kq = G::LC - 1 - kp;
+      f(ic<kp>{}, ic<kq>{}, 2 * kp + 1, G::H - 2 * kp - 1, ic<0>{});
+    });
+  }
+}
+
+// Staging of one real field (row y held as c[m] = (s[2m], s[2m+1])) and a coalesced copy to global.
+template <int N>
+WF_HD void stage_row(float* stg, int y, const float2 (&c)[N / 2]) {
+  using G = Geo<N>;
+#pragma unroll
+  for (int m = 0; m < G::LR; ++m) {
+    stg[y * G::STG + 2 * m] = c[m].x;
+    stg[y * G::STG + 2 * m + 1] = c[m].y;
+  }
+}
+template <int N>
+WF_HD void copy_out(const float* stg, int lt, float* __restrict__ out) {
+  using G = Geo<N>;
+#pragma unroll 4
+  for (int e = lt; e < G::H * G::W; e += N) {
+    const int y = e / G::W, x = e % G::W;
+    out[e] = stg[y * G::STG + x];
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// pixel-space updates (Alg. 1 t-update), row y, c[m] = (s[2m], s[2m+1]) -> (t[2m], t[2m+1])
+// ---------------------------------------------------------------------------------------------
+// sample mode: table aq[x*H + y] = (a, q) with a = (1 - w) d, q = sqrt(w), w = N_bar/(tau + N_bar)
+// (w = 1, a = 0 on missing pixels): t = a + q (q s + sqrt(tau) xi).
+template <int N>
+WF_HD void t_draw(float2 (&c)[N / 2], int y, const float2* __restrict__ aq, float sqrt_tau,
+                                       uint32_t step, uint32_t chain, uint32_t k0, uint32_t k1) {
+  using G = Geo<N>;
+#pragma unroll
+  for (int q = 0; q < G::W / 4; ++q) {
+    float z[4];
+    normals4(uint32_t(y * (G::W / 4) + q), step, chain, 0u, k0, k1, z);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int x = 4 * q + e;
+      const float2 co = WF_LDG(aq + x * G::H + y);
+      float& v = (e & 1) ? c[2 * q + e / 2].y : c[2 * q + e / 2].x;
+      v = fmaf(co.y, fmaf(co.y, v, sqrt_tau * z[e]), co.x);
+    }
+  }
+}
+
+// Wiener-filter mode at level lambda: table dn[x*H + y] = (d, 1/N_bar) (0 on missing pixels),
+// w = N_bar / (lambda tau + N_bar) = 1 / (1 + lambda tau / N_bar), t = d + w (s - d).
+template <int N>
+WF_HD void t_update_wf(float2 (&c)[N / 2], int y, const float2* __restrict__ dn, float lt_) {
+  using G = Geo<N>;
+#pragma unroll
+  for (int x = 0; x < G::W; ++x) {
+    const float2 co = WF_LDG(dn + x * G::H + y);
+    const float w = wf_rcp(fmaf(lt_, co.y, 1.0f));
+    float& v = (x & 1) ? c[x / 2].y : c[x / 2].x;
+    v = fmaf(w, v - co.x, co.x);
+  }
+}
+
+// right-hand side of the level-lambda Wiener equation, N_lambda^-1 d = d / (N_bar + lambda tau)
+template <int N>
+WF_HD void rhs_row(float2 (&c)[N / 2], int y, const float2* __restrict__ dn, float lt_) {
+  using G = Geo<N>;
+#pragma unroll
+  for (int x = 0; x < G::W; ++x) {
+    const float2 co = WF_LDG(dn + x * G::H + y);
+    const float nbar = co.y > 0.0f ? wf_rcp(co.y) : wf_inf();
+    const float v = co.x / (nbar + lt_);
+    if (x & 1) c[x / 2].y = v; else c[x / 2].x = v;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Fourier-space updates (Alg. 1 s-update) on the modes held by a column thread
+// ---------------------------------------------------------------------------------------------
+// sample mode, table fg[ky*WH + kx] = (f / n, g / sqrt(2 n)), f = P/(P + tau), g^2 = P tau/(P + tau)
+template <int N>
+WF_HD void s_draw(float2 (&x)[N / 2], int lt, const float2* __restrict__ fg, uint32_t step,
+                                       uint32_t chain, uint32_t k0, uint32_t k1) {
+  using G = Geo<N>;
+  constexpr int WH = G::WH;
+  const int col = lt % G::LC, r = lt / G::LC;
+  for_mode_pairs<N>(r, [&](auto KP, auto KQ, int ky1, int ky2, auto ZG) {
+    constexpr int kp = decltype(KP)::value, kq = decltype(KQ)::value;
+    constexpr bool zero_group = decltype(ZG)::value != 0;
+    float z[4];
+    normals4(uint32_t(col * (G::H / 2) + ky1), step, chain, 1u, k0, k1, z);
+    if (col != 0) {
+      const float2 m1 = WF_LDG(fg + ky1 * WH + col), m2 = WF_LDG(fg + ky2 * WH + col);
+      x[kp] = make_float2(fmaf(m1.x, x[kp].x, m1.y * z[0]), fmaf(m1.x, x[kp].y, m1.y * z[1]));
+      x[kq] = make_float2(fmaf(m2.x, x[kq].x, m2.y * z[2]), fmaf(m2.x, x[kq].y, m2.y * z[3]));
+    } else {
+      // edge columns kx = 0 (A) and kx = W/2 (B) packed as Y = A + i B, both Hermitian in ky
+      const float2 a1 = WF_LDG(fg + ky1 * WH), b1 = WF_LDG(fg + ky1 * WH + G::W / 2);
+      if constexpr (zero_group) {
+        const float2 a2 = WF_LDG(fg + ky2 * WH), b2 = WF_LDG(fg + ky2 * WH + G::W / 2);
+        constexpr float R2 = 1.41421356237309505f;  // self-conjugate modes: real, variance g^2
+        x[kp] = make_float2(fmaf(a1.x, x[kp].x, R2 * a1.y * z[0]), fmaf(b1.x, x[kp].y, R2 * b1.y * z[2]));
+        x[kq] = make_float2(fmaf(a2.x, x[kq].x, R2 * a2.y * z[1]), fmaf(b2.x, x[kq].y, R2 * b2.y * z[3]));
+      } else {
+        const float2 y1 = x[kp], y2c = cconj(x[kq]);
+        const float2 A = cscale(cadd(y1, y2c), 0.5f);
+        const float2 B = cmul_mi(cscale(csub(y1, y2c), 0.5f));
+        const float2 Ap = make_float2(fmaf(a1.x, A.x, a1.y * z[0]), fmaf(a1.x, A.y, a1.y * z[1]));
+        const float2 Bp = make_float2(fmaf(b1.x, B.x, b1.y * z[2]), fmaf(b1.x, B.y, b1.y * z[3]));
+        x[kp] = cadd(Ap, cmul_i(Bp));
+        x[kq] = cadd(cconj(Ap), cmul_i(cconj(Bp)));
+      }
+    }
+  });
+}
+
+// Wiener-filter mode at level lambda: s_hat = f t_hat with f = P/(P + lambda tau) (scaled by 1/n).
+// With STORE the result is written to prev[ky*LR + col]; with CMP the residual of the previous iterate,
+// |r_k| = |s_hat_new - s_hat_old| / (1 - f), is accumulated over the full spectrum (returned, scaled 1/n).
+template <int N, bool CMP, bool STORE>
+WF_HD double s_update_wf(float2 (&x)[N / 2], int lt, const float* __restrict__ Pk, float lt_,
+                                              float2* __restrict__ prev) {
+  using G = Geo<N>;
+  constexpr int WH = G::WH;
+  constexpr float INV_N = 1.0f / float(G::H * G::W);
+  const int col = lt % G::LC, r = lt / G::LC;
+  double acc = 0.0;
+  // |d|^2 / (1 - f_true)^2 with 1/(1 - f_true) = (P + lambda tau) / (lambda tau)
+  auto wres = [&](float P, float dre, float dim) -> double {
+    const double g = (double(P) + double(lt_)) / double(lt_);
+    return (double(dre) * dre + double(dim) * dim) * g * g;
+  };
+  for_mode_pairs<N>(r, [&](auto KP, auto KQ, int ky1, int ky2, auto ZG) {
+    constexpr int kp = decltype(KP)::value, kq = decltype(KQ)::value;
+    constexpr bool zero_group = decltype(ZG)::value != 0;
+    if (col != 0) {
+      const float P1 = WF_LDG(Pk + ky1 * WH + col), P2 = WF_LDG(Pk + ky2 * WH + col);
+      const float f1 = P1 / (P1 + lt_) * INV_N, f2 = P2 / (P2 + lt_) * INV_N;
+      const float2 n1 = cscale(x[kp], f1), n2 = cscale(x[kq], f2);
+      if constexpr (CMP) {
+        const float2 o1 = prev[ky1 * G::LR + col], o2 = prev[ky2 * G::LR + col];
+        acc += 2.0 * (wres(P1, n1.x - o1.x, n1.y - o1.y) + wres(P2, n2.x - o2.x, n2.y - o2.y));
+      }
+      x[kp] = n1;
+      x[kq] = n2;
+    } else {
+      const float Pa1 = WF_LDG(Pk + ky1 * WH), Pb1 = WF_LDG(Pk + ky1 * WH + G::W / 2);
+      const float Pa2 = WF_LDG(Pk + ky2 * WH), Pb2 = WF_LDG(Pk + ky2 * WH + G::W / 2);
+      const float fa1 = Pa1 / (Pa1 + lt_) * INV_N, fb1 = Pb1 / (Pb1 + lt_) * INV_N;
+      const float fa2 = Pa2 / (Pa2 + lt_) * INV_N, fb2 = Pb2 / (Pb2 + lt_) * INV_N;
+      if constexpr (zero_group) {
+        const float2 n1 = make_float2(fa1 * x[kp].x, fb1 * x[kp].y);
+        const float2 n2 = make_float2(fa2 * x[kq].x, fb2 * x[kq].y);
+        if constexpr (CMP) {
+          const float2 o1 = prev[ky1 * G::LR], o2 = prev[ky2 * G::LR];
+          acc += wres(Pa1, n1.x - o1.x, 0.f) + wres(Pb1, n1.y - o1.y, 0.f) + wres(Pa2, n2.x - o2.x, 0.f) +
+                 wres(Pb2, n2.y - o2.y, 0.f);
+        }
+        x[kp] = n1;
+        x[kq] = n2;
+      } else {
+        const float2 y1 = x[kp], y2c = cconj(x[kq]);
+        const float2 A = cscale(cscale(cadd(y1, y2c), 0.5f), fa1);
+        const float2 B = cscale(cmul_mi(cscale(csub(y1, y2c), 0.5f)), fb1);
+        const float2 n1 = cadd(A, cmul_i(B));
+        const float2 n2 = cadd(cconj(A), cmul_i(cconj(B)));
+        if constexpr (CMP) {
+          const float2 o1 = prev[ky1 * G::LR], o2c = cconj(prev[ky2 * G::LR]);
+          const float2 oA = cscale(cadd(o1, o2c), 0.5f);
+          const float2 oB = cmul_mi(cscale(csub(o1, o2c), 0.5f));
+          // modes ky1 and H - ky1 of each edge column have equal magnitude: weight 2
+          acc += 2.0 * (wres(Pa1, A.x - oA.x, A.y - oA.y) + wres(Pb1, B.x - oB.x, B.y - oB.y));
+        }
+        x[kp] = n1;
+        x[kq] = n2;
+      }
+    }
+    if constexpr (STORE) {
+      prev[ky1 * G::LR + col] = x[kp];
+      prev[ky2 * G::LR + col] = x[kq];
+    }
+  });
+  return acc;
+}
+
+// sum over the full spectrum of P^2 |V|^2 for the forward transform V held by this thread
+// (edge columns separated into kx = 0 and kx = W/2)
+template <int N>
+WF_HD double p2_power(const float2 (&x)[N / 2], int lt, const float* __restrict__ Pk) {
+  using G = Geo<N>;
+  constexpr int WH = G::WH;
+  const int col = lt % G::LC, r = lt / G::LC;
+  double acc = 0.0;
+  auto p2 = [](float P, float re, float im) -> double {
+    return double(P) * double(P) * (double(re) * re + double(im) * im);
+  };
+  for_mode_pairs<N>(r, [&](auto KP, auto KQ, int ky1, int ky2, auto ZG) {
+    constexpr int kp = decltype(KP)::value, kq = decltype(KQ)::value;
+    constexpr bool zero_group = decltype(ZG)::value != 0;
+    if (col != 0) {
+      acc += 2.0 * (p2(WF_LDG(Pk + ky1 * WH + col), x[kp].x, x[kp].y) + p2(WF_LDG(Pk + ky2 * WH + col), x[kq].x, x[kq].y));
+    } else if constexpr (zero_group) {
+      acc += p2(WF_LDG(Pk + ky1 * WH), x[kp].x, 0.f) + p2(WF_LDG(Pk + ky1 * WH + G::W / 2), x[kp].y, 0.f) +
+             p2(WF_LDG(Pk + ky2 * WH), x[kq].x, 0.f) + p2(WF_LDG(Pk + ky2 * WH + G::W / 2), x[kq].y, 0.f);
+    } else {
+      const float2 y1 = x[kp], y2c = cconj(x[kq]);
+      const float2 A = cscale(cadd(y1, y2c), 0.5f);
+      const float2 B = cmul_mi(cscale(csub(y1, y2c), 0.5f));
+      acc += 2.0 * (p2(WF_LDG(Pk + ky1 * WH), A.x, A.y) + p2(WF_LDG(Pk + ky1 * WH + G::W / 2), B.x, B.y));
+    }
+  });
+  return acc;
+}
+
+// block-wide double sum; every thread gets the result. red must hold >= 33 doubles.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < nw; ++i) s += red[i];
+    red[32] = s;
+  }
+  __syncthreads();
+  const double s = red[32];
+  __syncthreads();
+  return s;
+}
+
+// ---------------------------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------------------------
+struct SampleArgs {
+  const float2* aq;      // [W][H] pixel table (a, q)
+  const float2* fg;      // [H][W/2+1] mode table (f/n, g/sqrt(2n))
+  const Scalars* sc;
+  const float* init_s;   // nullptr -> zeros; else [n_chains or 1][H][W]
+  long long init_stride; // elements between chains' initial states (0: shared)
+  float* out;            // [n_chains][n_samples][H][W]
+  long long n_samples;
+  int n_chains;
+  int n_sweeps;
+  int burn_in;
+  int thin;
+  uint32_t chain0;
+  uint32_t step0;
+  uint32_t key0, key1;
+};
+
+// CTAs per SM the sample kernel is compiled for (register budget 65536 / (threads * CTAs)):
+// 128^2 fields are limited to three per SM by shared memory (66.5 KB each).
+template <int N>
+constexpr int sample_min_ctas() { return N >= 128 ? 3 : (N == 64 ? 4 : 8); }
+
+template <int N, int FPC>
+__global__ void __launch_bounds__(N * FPC, sample_min_ctas<N>()) k_sample(SampleArgs a) {
+  using G = Geo<N>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int fld = threadIdx.x / N, lt = threadIdx.x % N;
+  const int ci = blockIdx.x * FPC + fld;
+  const bool active = ci < a.n_chains;
+  float2* S = reinterpret_cast<float2*>(smem_raw + fld * G::FIELD_BYTES);
+  float* stg = reinterpret_cast<float*>(S);
+  if (a.sc->status != 0) return;  // uniform over the grid
+  const float sqrt_tau = a.sc->sqrt_tau;
+  const uint32_t chain = a.chain0 + uint32_t(ci);
+  float2 c[G::LR];
+
+  // state s_0 -> first pixel draw -> forward row transform
+  if (a.init_s != nullptr && active) {
+    const float2* src = reinterpret_cast<const float2*>(a.init_s + ci * a.init_stride + lt * G::W);
+#pragma unroll
+    for (int m = 0; m < G::LR; ++m) c[m] = WF_LDG(src + m);
+  } else {
+#pragma unroll
+    for (int m = 0; m < G::LR; ++m) c[m] = make_float2(0.f, 0.f);
+  }
+  t_draw<N>(c, lt, a.aq, sqrt_tau, a.step0, chain, a.key0, a.key1);
+  row_forward<N>(c);
+  row_store_spec<N>(S, lt, c);
+  __syncthreads();
+
+  for (int i = 0; i < a.n_sweeps; ++i) {
+    const uint32_t step = a.step0 + uint32_t(i);
+    // column pass: Fourier-space draw
+    col_load<N>(S, lt, c);
+    __syncthreads();
+    fft<G::LC, false>(c);
+    s_draw<N>(c, lt, a.fg, step, chain, a.key0, a.key1);
+    col_inverse_store<N>(S, lt, c);
+    __syncthreads();
+    // row pass: back to pixel space, emit, next pixel draw
+    row_load_spec<N>(S, lt, c);
+    __syncthreads();
+    row_inverse<N>(c);
+    const int done = i + 1;
+    if (done > a.burn_in && (done - a.burn_in) % a.thin == 0) {
+      const long long m = (done - a.burn_in) / a.thin - 1;
+      stage_row<N>(stg, lt, c);
+      __syncthreads();
+      if (active) copy_out<N>(stg, lt, a.out + (ci * a.n_samples + m) * (long long)(G::H * G::W));
+      __syncthreads();
+    }
+    if (done < a.n_sweeps) {
+      t_draw<N>(c, lt, a.aq, sqrt_tau, step + 1u, chain, a.key0, a.key1);
+      row_forward<N>(c);
+      row_store_spec<N>(S, lt, c);
+      __syncthreads();
+    }
+  }
+}
+
+struct SolveArgs {
+  const float2* dn;      // [W][H] pixel table (d, 1/N_bar)
+  const float* Pk;       // [H][W/2+1]
+  const Scalars* sc;
+  const double* bnorm2;  // [n_levels] ||S N_lambda^-1 d||^2 per level
+  const float* init_s;   // nullptr -> zeros
+  float2* prev;          // [H][W/2] scratch: previous s_hat at check sweeps
+  float* out;            // [H][W]
+  SolveStatus* st;
+  double tol;
+  double eta;
+  double level_tol;
+  int max_iter;
+  int level_max;
+  int check;
+};
+
+template <int N>
+__global__ void __launch_bounds__(N) k_solve(SolveArgs a) {
+  using G = Geo<N>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* S = reinterpret_cast<float2*>(smem_raw);
+  float* stg = reinterpret_cast<float*>(S);
+  double* red = reinterpret_cast<double*>(smem_raw + G::FIELD_BYTES);
+  const int lt = threadIdx.x;
+  const Scalars sc = *a.sc;
+  if (sc.status != 0) return;
+  const double tau = sc.tau;
+  int lev = 0;
+  double lam = sc.lam0;
+  float ltau = float(lam * tau);
+  const int last_level = sc.n_levels - 1;
+  float2 c[G::LR];
+
+  if (a.init_s != nullptr) {
+    const float2* src = reinterpret_cast<const float2*>(a.init_s + lt * G::W);
+#pragma unroll
+    for (int m = 0; m < G::LR; ++m) c[m] = WF_LDG(src + m);
+  } else {
+#pragma unroll
+    for (int m = 0; m < G::LR; ++m) c[m] = make_float2(0.f, 0.f);
+  }
+  t_update_wf<N>(c, lt, a.dn, ltau);
+  row_forward<N>(c);
+  row_store_spec<N>(S, lt, c);
+  __syncthreads();
+
+  int it = 0, k = 0;  // sweeps in total / at the current level
+  int status = 1;     // 1 = running
+  double rho = -1.0;
+  while (true) {
+    ++k;
+    ++it;
+    const bool cmp = (k % a.check == 0) && k >= 2;
+    const bool store = ((k + 1) % a.check == 0);
+    col_load<N>(S, lt, c);
+    __syncthreads();
+    fft<G::LC, false>(c);
+    double acc;
+    if (cmp && store) acc = s_update_wf<N, true, true>(c, lt, a.Pk, ltau, a.prev);
+    else if (cmp) acc = s_update_wf<N, true, false>(c, lt, a.Pk, ltau, a.prev);
+    else if (store) acc = s_update_wf<N, false, true>(c, lt, a.Pk, ltau, a.prev);
+    else acc = s_update_wf<N, false, false>(c, lt, a.Pk, ltau, a.prev);
+    if (cmp) {
+      const double tot = block_sum(acc, red) * double(G::H * G::W);
+      const double bn = a.bnorm2[lev];
+      const double r2 = bn > 0.0 ? tot / bn : tot;
+      rho = sqrt(r2);
+      if (!(r2 == r2) || r2 > 1e300) {
+        status = 6;  // non-finite residual
+      } else if (lev < last_level) {
+        if (rho < a.level_tol || k >= a.level_max) {
+          ++lev;
+          lam = level_lambda(sc, lev, a.eta);
+          ltau = float(lam * tau);
+          k = 0;
+        }
+      } else if (rho < a.tol) {
+        status = 0;
+      }
+    }
+    if (status == 1 && it >= a.max_iter) status = 5;  // not converged
+    col_inverse_store<N>(S, lt, c);
+    __syncthreads();
+    row_load_spec<N>(S, lt, c);
+    __syncthreads();
+    row_inverse<N>(c);
+    if (status != 1) break;
+    t_update_wf<N>(c, lt, a.dn, ltau);
+    row_forward<N>(c);
+    row_store_spec<N>(S, lt, c);
+    __syncthreads();
+  }
+  stage_row<N>(stg, lt, c);
+  __syncthreads();
+  copy_out<N>(stg, lt, a.out);
+  if (lt == 0) {
+    a.st->status = status;
+    a.st->iters = it;
+    a.st->resid = rho;
+  }
+}
+
+// ||S N_lambda^-1 d||^2 for every cooling level (one CTA per level)
+struct BnormArgs {
+  const float2* dn;
+  const float* Pk;
+  const Scalars* sc;
+  double* bnorm2;
+  double eta;
+};
+
+template <int N>
+__global__ void __launch_bounds__(N) k_bnorm(BnormArgs a) {
+  using G = Geo<N>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* S = reinterpret_cast<float2*>(smem_raw);
+  double* red = reinterpret_cast<double*>(smem_raw + G::FIELD_BYTES);
+  const int lev = blockIdx.x, lt = threadIdx.x;
+  const Scalars sc = *a.sc;
+  if (sc.status != 0 || lev >= sc.n_levels) return;
+  const double lam = level_lambda(sc, lev, a.eta);
+  float2 c[G::LR];
+  rhs_row<N>(c, lt, a.dn, float(lam * sc.tau));
+  row_forward<N>(c);
+  row_store_spec<N>(S, lt, c);
+  __syncthreads();
+  col_load<N>(S, lt, c);
+  fft<G::LC, false>(c);
+  const double tot = block_sum(p2_power<N>(c, lt, a.Pk), red);
+  if (lt == 0) a.bnorm2[lev] = tot / double(G::H * G::W);
+}
+
+}  // namespace wf

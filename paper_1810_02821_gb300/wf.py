@@ -1,0 +1,209 @@
+"""Python binding of the C ABI in ``include/wf.h`` (argument marshalling only).
+
+Every function takes CUDA tensors from PyTorch (which owns device memory and streams), checks dtype,
+device and shape, and passes raw pointers to ``libwfgpu.so``. All arithmetic runs in the CUDA kernels;
+there is no CPU fallback: if the library cannot be loaded every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libwfgpu.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "wf.h")
+
+WF_OK = 0
+STATUS_NAMES = {0: "WF_OK", 1: "WF_ERR_ARG", 2: "WF_ERR_TAU", 3: "WF_ERR_SHAPE", 4: "WF_ERR_CUDA",
+                5: "WF_ERR_NOT_CONVERGED", 6: "WF_ERR_NONFINITE", 7: "WF_ERR_TIMEOUT"}
+
+
+class WFError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)} ({detail})")
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("tol", ctypes.c_double), ("eta", ctypes.c_double),
+                ("level_tol", ctypes.c_double), ("level_max", ctypes.c_int32), ("check", ctypes.c_int32),
+                ("max_iter", ctypes.c_int32), ("reserved", ctypes.c_int32), ("init_s", ctypes.c_void_p)]
+
+
+class SampleOpts(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("n_samples", ctypes.c_int64), ("n_chains", ctypes.c_int32),
+                ("chain_offset", ctypes.c_uint32), ("start_step", ctypes.c_uint32), ("burn_in", ctypes.c_int32),
+                ("thin", ctypes.c_int32), ("init_per_chain", ctypes.c_int32), ("init_s", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load ``libwfgpu.so`` (built by ``paper_1810_02821_gb300.build``) and declare its signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libwfgpu.so not found at {path}: run `python -m paper_1810_02821_gb300.build` "
+                           "(the CUDA library is required; there is no CPU fallback)")
+    L = ctypes.CDLL(path)
+    P, I32, I64, U32, U64, D = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                ctypes.c_uint64, ctypes.c_double)
+    L.wf_solve.argtypes = [P, P, P, P, I32, I32, D, D, P, ctypes.POINTER(I32), ctypes.POINTER(D), P]
+    L.wf_solve_ex.argtypes = [P, P, P, P, I32, I32, ctypes.POINTER(SolveOpts), P, ctypes.POINTER(I32),
+                              ctypes.POINTER(D), P]
+    L.wf_sample.argtypes = [P, P, P, P, I32, I32, I64, U64, P, P]
+    L.wf_sample_ex.argtypes = [P, P, P, P, I32, I32, U64, ctypes.POINTER(SampleOpts), P, P]
+    for name in ("wf_solve", "wf_solve_ex", "wf_sample", "wf_sample_ex"):
+        getattr(L, name).restype = ctypes.c_int
+    L.wf_solve_opts_default.argtypes = [ctypes.POINTER(SolveOpts)]
+    L.wf_solve_opts_default.restype = None
+    L.wf_sample_opts_default.argtypes = [ctypes.POINTER(SampleOpts)]
+    L.wf_sample_opts_default.restype = None
+    L.wf_supported_size.argtypes = [I32, I32]
+    L.wf_supported_size.restype = I32
+    L.wf_status_string.argtypes = [ctypes.c_int]
+    L.wf_status_string.restype = ctypes.c_char_p
+    L.wf_last_cuda_error.argtypes = []
+    L.wf_last_cuda_error.restype = I32
+    L.wf_abi_version.argtypes = []
+    L.wf_abi_version.restype = I32
+    L.wf_set_kernel_timing.argtypes = [I32]
+    L.wf_set_kernel_timing.restype = None
+    L.wf_last_kernel_ms.argtypes = []
+    L.wf_last_kernel_ms.restype = D
+    _lib = L
+    return L
+
+
+def header_functions(path: str = HEADER) -> list[str]:
+    """Names of the functions declared in ``include/wf.h``."""
+    txt = open(path).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(wf_[a-z0-9_]+)\s*\(", txt)))
+
+
+def _check(status: int, where: str, ok=(WF_OK,)):
+    if status not in ok:
+        L = load_library()
+        detail = L.wf_status_string(status).decode()
+        if status == 4:
+            detail += f", cudaError {L.wf_last_cuda_error()}"
+        raise WFError(status, where, detail)
+
+
+def _stream_ptr(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _inputs(d, Ndiag, mask, Pk):
+    import torch
+    H, W = d.shape
+    return (H, W, _dev(d, torch.float32, (H, W), "d"), _dev(Ndiag, torch.float32, (H, W), "Ndiag"),
+            _dev(mask, torch.uint8, (H, W), "mask"), _dev(Pk, torch.float32, (H, W // 2 + 1), "Pk"))
+
+
+@dataclass
+class SolveResult:
+    s: object      # torch tensor [H][W]
+    iters: int
+    resid: float
+    status: int
+
+
+def wf_solve(d, Ndiag, mask, Pk, tau: float = 0.0, tol: float = 1e-6, out=None, stream=None,
+             allow_not_converged: bool = False) -> SolveResult:
+    """Wiener filter s_W = S (S + N)^-1 d by the cooled messenger iteration (C call ``wf_solve``)."""
+    return wf_solve_ex(d, Ndiag, mask, Pk, tau=tau, tol=tol, out=out, stream=stream,
+                       allow_not_converged=allow_not_converged)
+
+
+def wf_solve_ex(d, Ndiag, mask, Pk, *, tau: float = 0.0, tol: float = 1e-6, eta: float = 0.5,
+                level_tol: float = 1e-2, level_max: int = 64, check: int = 4, max_iter: int = 20000,
+                init_s=None, out=None, stream=None, allow_not_converged: bool = False) -> SolveResult:
+    """All options of the cooled Wiener-filter solve (C call ``wf_solve_ex``)."""
+    import torch
+    L = load_library()
+    H, W, pd, pn, pm, pp = _inputs(d, Ndiag, mask, Pk)
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.float32, device=d.device)
+    po = _dev(out, torch.float32, (H, W), "out")
+    o = SolveOpts()
+    L.wf_solve_opts_default(ctypes.byref(o))
+    o.tau, o.tol, o.eta, o.level_tol = float(tau), float(tol), float(eta), float(level_tol)
+    o.level_max, o.check, o.max_iter = int(level_max), int(check), int(max_iter)
+    o.init_s = _dev(init_s, torch.float32, (H, W), "init_s").value if init_s is not None else None
+    it = ctypes.c_int32(0)
+    rs = ctypes.c_double(0.0)
+    st = L.wf_solve_ex(pd, pn, pm, pp, H, W, ctypes.byref(o), po, ctypes.byref(it), ctypes.byref(rs),
+                       _stream_ptr(stream))
+    _check(st, "wf_solve_ex", ok=(WF_OK, 5) if allow_not_converged else (WF_OK,))
+    return SolveResult(out, it.value, rs.value, st)
+
+
+def wf_sample(d, Ndiag, mask, Pk, n_samples: int, seed: int, out=None, stream=None):
+    """``n_samples`` posterior draws of one chain from s0 = 0 (C call ``wf_sample``) -> [n][H][W]."""
+    import torch
+    L = load_library()
+    H, W, pd, pn, pm, pp = _inputs(d, Ndiag, mask, Pk)
+    if out is None:
+        out = torch.empty((n_samples, H, W), dtype=torch.float32, device=d.device)
+    po = _dev(out, torch.float32, (n_samples, H, W), "out")
+    st = L.wf_sample(pd, pn, pm, pp, H, W, int(n_samples), int(seed) & 0xFFFFFFFFFFFFFFFF, po, _stream_ptr(stream))
+    _check(st, "wf_sample")
+    return out
+
+
+def wf_sample_ex(d, Ndiag, mask, Pk, seed: int, n_samples: int, *, n_chains: int = 1, chain_offset: int = 0,
+                 start_step: int = 0, burn_in: int = 0, thin: int = 1, tau: float = 0.0, init_s=None,
+                 out=None, stream=None):
+    """Several chains with burn-in, thinning and resume (C call ``wf_sample_ex``) -> [chains][n][H][W]."""
+    import torch
+    L = load_library()
+    H, W, pd, pn, pm, pp = _inputs(d, Ndiag, mask, Pk)
+    if out is None:
+        out = torch.empty((n_chains, n_samples, H, W), dtype=torch.float32, device=d.device)
+    po = _dev(out, torch.float32, (n_chains, n_samples, H, W), "out")
+    o = SampleOpts()
+    L.wf_sample_opts_default(ctypes.byref(o))
+    o.tau, o.n_samples, o.n_chains = float(tau), int(n_samples), int(n_chains)
+    o.chain_offset, o.start_step, o.burn_in, o.thin = int(chain_offset), int(start_step), int(burn_in), int(thin)
+    if init_s is not None:
+        per_chain = init_s.dim() == 3
+        shape = (n_chains, H, W) if per_chain else (H, W)
+        o.init_s = _dev(init_s, torch.float32, shape, "init_s").value
+        o.init_per_chain = 1 if per_chain else 0
+    st = L.wf_sample_ex(pd, pn, pm, pp, H, W, int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(o), po,
+                        _stream_ptr(stream))
+    _check(st, "wf_sample_ex")
+    return out
+
+
+def wf_set_kernel_timing(enable: bool) -> None:
+    load_library().wf_set_kernel_timing(1 if enable else 0)
+
+
+def wf_last_kernel_ms() -> float:
+    return float(load_library().wf_last_kernel_ms())
+
+
+def wf_supported_size(H: int, W: int) -> bool:
+    return bool(load_library().wf_supported_size(H, W))
