@@ -131,6 +131,26 @@ int32_t wf_last_cuda_error(void);
 void wf_set_kernel_timing(int32_t enable);
 double wf_last_kernel_ms(void);
 
+/*
+ * wf_sample_ex without any device allocation. The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate GPU memory at call time, for instance code running while a CUDA graph is
+ * being captured, real-time loops that forbid the allocator's latency and synchronisation, or hosts
+ * whose memory budget is fixed in advance. Arguments, results and statuses are those of wf_sample_ex;
+ * the caller passes every input and the output buffer as before.
+ *   - Scratch (the per-call coefficient tables) lives in one statically sized device array compiled into
+ *     the library, 262,144 bytes, which every GPU that loads the library keeps until the process exits.
+ *     Images needing more (H * W > 128 * 128; all sizes wf_supported_size accepts fit) are rejected with
+ *     WF_ERR_SHAPE before anything is launched.
+ *   - The first call on each device looks up that array's device address (cudaGetSymbolAddress) with the
+ *     device current; make that first call before any stream capture. Later calls reuse the address.
+ *   - No cudaMalloc, cudaFree or allocating library routine is called.
+ *   - All calls on a device share the one array and leave the last call's tables in it; every call
+ *     rewrites what it reads before reading it, so nothing needs clearing, but calls that overlap on the
+ *     GPU (other streams or host threads on the same device) race on it: serialise them.
+ */
+wf_status wf_sample_noalloc(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int32_t H,
+                            int32_t W, uint64_t seed, const wf_sample_opts* opts, float* out, wf_stream_t stream);
+
 /* ABI version of this header: (major << 16) | minor. */
 int32_t wf_abi_version(void);
 

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -314,6 +315,91 @@ wf_status wf_sample(const float* d, const float* Ndiag, const uint8_t* mask, con
   wf_sample_opts_default(&o);
   o.n_samples = n_samples;
   return wf_sample_ex(d, Ndiag, mask, Pk, H, W, seed, &o, out, stream);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// wf_sample_noalloc: the sampler with its scratch in a static device array instead of cudaMallocAsync,
+// for callers that cannot allocate device memory when they call (graph capture, real-time loops, fixed
+// memory budgets).
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocBytes = 262144;  // tables of a 128 x 128 image: 256 + 131072 + 66560 bytes
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once per device. In host code
+// the array's name is only a host-side stand-in, so the kernels must be given this address.
+cudaError_t noalloc_scratch(void** ptr) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (g_noalloc_addr[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = p;
+  }
+  *ptr = g_noalloc_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+wf_status wf_sample_noalloc(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int32_t H,
+                            int32_t W, uint64_t seed, const wf_sample_opts* opts, float* out, wf_stream_t stream) {
+  if (!opts) return WF_ERR_ARG;
+  const wf_sample_opts o = *opts;
+  if (!d || !Ndiag || !mask || !Pk) return WF_ERR_ARG;
+  if (!size_ok(H, W)) return WF_ERR_SHAPE;
+  const size_t n = size_t(H) * W, nm = size_t(H) * (W / 2 + 1);
+  const size_t off_aq = align256(sizeof(wf::Scalars)), off_fg = off_aq + align256(n * sizeof(float2)),
+               total = off_fg + align256(nm * sizeof(float2));
+  if (total > kNoAllocBytes) return WF_ERR_SHAPE;  // image too large for the static scratch array
+  if (o.n_samples < 0 || o.n_chains < 1 || o.burn_in < 0 || o.thin < 1) return WF_ERR_ARG;
+  if (o.n_samples == 0) return WF_OK;
+  if (!out) return WF_ERR_ARG;
+  const long long sweeps = (long long)o.burn_in + o.n_samples * (long long)o.thin;
+  if (sweeps > 0x7fffffffLL || o.n_samples > 0x7fffffffLL) return WF_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  void* base = nullptr;
+  WF_CUDA(noalloc_scratch(&base));
+  char* b = static_cast<char*>(base);
+  auto* sc = reinterpret_cast<wf::Scalars*>(b);
+  auto* aq = reinterpret_cast<float2*>(b + off_aq);
+  auto* fg = reinterpret_cast<float2*>(b + off_fg);
+  // k_prep rewrites every field of sc and k_tables every table entry before the sampler reads them
+  k_prep<<<1, 1024, 0, st>>>(d, Ndiag, mask, Pk, H, W, o.tau, 0.5, sc);
+  WF_CUDA(cudaGetLastError());
+  k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc, aq, nullptr, fg);
+  WF_CUDA(cudaGetLastError());
+  wf::SampleArgs a{};
+  a.aq = aq; a.fg = fg; a.sc = sc; a.init_s = o.init_s;
+  a.init_stride = (o.init_s && o.init_per_chain) ? (long long)n : 0;
+  a.out = out; a.n_samples = o.n_samples; a.n_chains = o.n_chains; a.n_sweeps = int(sweeps);
+  a.burn_in = o.burn_in; a.thin = o.thin; a.chain0 = o.chain_offset; a.step0 = o.start_step;
+  a.key0 = uint32_t(seed & 0xffffffffu); a.key1 = uint32_t(seed >> 32);
+  cudaError_t e = cudaSuccess;
+  switch (H) {
+    case 16: e = wf::launch_sample<16>(a, st, nullptr); break;
+    case 32: e = wf::launch_sample<32>(a, st, nullptr); break;
+    case 64: e = wf::launch_sample<64>(a, st, nullptr); break;
+    case 128: e = wf::launch_sample<128>(a, st, nullptr); break;
+  }
+  if (e != cudaSuccess) return cuda_fail(e);
+  wf::Scalars hsc;
+  WF_CUDA(cudaMemcpyAsync(&hsc, sc, sizeof(hsc), cudaMemcpyDeviceToHost, st));
+  WF_CUDA(cudaStreamSynchronize(st));
+  return wf_status(hsc.status);
 }
 
 }  // extern "C"
