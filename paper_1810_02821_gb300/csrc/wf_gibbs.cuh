@@ -42,6 +42,7 @@ WF_HD void sfor(F&& f) {
 #else
 #define WF_LDG(p) (*(p))
 #endif
+
 WF_HD float wf_rcp(float x) {
 #if defined(__CUDA_ARCH__)
   return __frcp_rn(x);
@@ -204,6 +205,29 @@ WF_HD void col_load(const float2* S, int lt, float2 (&x)[N / 2]) {
   }
 }
 
+// after the inverse column transform: store e[n] (r = 0, rows [0, LC)) or exp(+2 pi i n / H) * o[n]
+// (r = 1, rows [LC, H)); x holds the transform already.
+template <int N>
+WF_HD void col_store_inv(float2* S, int lt, const float2 (&x)[N / 2]) {
+  using G = Geo<N>;
+  const int col = lt % G::LC, r = lt / G::LC;
+  if (r == 0) {
+#pragma unroll
+    for (int n = 0; n < G::LC; ++n) S[n * G::SP + col] = x[n];
+  } else {
+    sfor<G::LC>([&](auto I) {
+      constexpr int n = decltype(I)::value;
+      S[(n + G::LC) * G::SP + col] = twiddle<n, G::H, true>(x[n]);
+    });
+  }
+}
+
+template <int L>
+WF_HD void conj_all(float2 (&x)[L]) {
+#pragma unroll
+  for (int k = 0; k < L; ++k) x[k].y = -x[k].y;
+}
+
 // inverse column transform of the modes held by this thread, then store e[n] (r = 0, rows [0, LC))
 // or o[n] = exp(+2 pi i n / H) * IFFT(odd)[n] (r = 1, rows [LC, H)).
 template <int N>
@@ -267,26 +291,6 @@ WF_HD void copy_out(const float* stg, int lt, float* __restrict__ out) {
 // ---------------------------------------------------------------------------------------------
 // pixel-space updates (Alg. 1 t-update), row y, c[m] = (s[2m], s[2m+1]) -> (t[2m], t[2m+1])
 // ---------------------------------------------------------------------------------------------
-// sample mode: table aq[x*H + y] = (a, q) with a = (1 - w) d, q = sqrt(w), w = N_bar/(tau + N_bar)
-// (w = 1, a = 0 on missing pixels): t = a + q (q s + sqrt(tau) xi).
-template <int N>
-WF_HD void t_draw(float2 (&c)[N / 2], int y, const float2* __restrict__ aq, float sqrt_tau,
-                                       uint32_t step, uint32_t chain, uint32_t k0, uint32_t k1) {
-  using G = Geo<N>;
-#pragma unroll
-  for (int q = 0; q < G::W / 4; ++q) {
-    float z[4];
-    normals4(uint32_t(y * (G::W / 4) + q), step, chain, 0u, k0, k1, z);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int x = 4 * q + e;
-      const float2 co = WF_LDG(aq + x * G::H + y);
-      float& v = (e & 1) ? c[2 * q + e / 2].y : c[2 * q + e / 2].x;
-      v = fmaf(co.y, fmaf(co.y, v, sqrt_tau * z[e]), co.x);
-    }
-  }
-}
-
 // Wiener-filter mode at level lambda: table dn[x*H + y] = (d, 1/N_bar) (0 on missing pixels),
 // w = N_bar / (lambda tau + N_bar) = 1 / (1 + lambda tau / N_bar), t = d + w (s - d).
 template <int N>
@@ -317,43 +321,6 @@ WF_HD void rhs_row(float2 (&c)[N / 2], int y, const float2* __restrict__ dn, flo
 // ---------------------------------------------------------------------------------------------
 // Fourier-space updates (Alg. 1 s-update) on the modes held by a column thread
 // ---------------------------------------------------------------------------------------------
-// sample mode, table fg[ky*WH + kx] = (f / n, g / sqrt(2 n)), f = P/(P + tau), g^2 = P tau/(P + tau)
-template <int N>
-WF_HD void s_draw(float2 (&x)[N / 2], int lt, const float2* __restrict__ fg, uint32_t step,
-                                       uint32_t chain, uint32_t k0, uint32_t k1) {
-  using G = Geo<N>;
-  constexpr int WH = G::WH;
-  const int col = lt % G::LC, r = lt / G::LC;
-  for_mode_pairs<N>(r, [&](auto KP, auto KQ, int ky1, int ky2, auto ZG) {
-    constexpr int kp = decltype(KP)::value, kq = decltype(KQ)::value;
-    constexpr bool zero_group = decltype(ZG)::value != 0;
-    float z[4];
-    normals4(uint32_t(col * (G::H / 2) + ky1), step, chain, 1u, k0, k1, z);
-    if (col != 0) {
-      const float2 m1 = WF_LDG(fg + ky1 * WH + col), m2 = WF_LDG(fg + ky2 * WH + col);
-      x[kp] = make_float2(fmaf(m1.x, x[kp].x, m1.y * z[0]), fmaf(m1.x, x[kp].y, m1.y * z[1]));
-      x[kq] = make_float2(fmaf(m2.x, x[kq].x, m2.y * z[2]), fmaf(m2.x, x[kq].y, m2.y * z[3]));
-    } else {
-      // edge columns kx = 0 (A) and kx = W/2 (B) packed as Y = A + i B, both Hermitian in ky
-      const float2 a1 = WF_LDG(fg + ky1 * WH), b1 = WF_LDG(fg + ky1 * WH + G::W / 2);
-      if constexpr (zero_group) {
-        const float2 a2 = WF_LDG(fg + ky2 * WH), b2 = WF_LDG(fg + ky2 * WH + G::W / 2);
-        constexpr float R2 = 1.41421356237309505f;  // self-conjugate modes: real, variance g^2
-        x[kp] = make_float2(fmaf(a1.x, x[kp].x, R2 * a1.y * z[0]), fmaf(b1.x, x[kp].y, R2 * b1.y * z[2]));
-        x[kq] = make_float2(fmaf(a2.x, x[kq].x, R2 * a2.y * z[1]), fmaf(b2.x, x[kq].y, R2 * b2.y * z[3]));
-      } else {
-        const float2 y1 = x[kp], y2c = cconj(x[kq]);
-        const float2 A = cscale(cadd(y1, y2c), 0.5f);
-        const float2 B = cmul_mi(cscale(csub(y1, y2c), 0.5f));
-        const float2 Ap = make_float2(fmaf(a1.x, A.x, a1.y * z[0]), fmaf(a1.x, A.y, a1.y * z[1]));
-        const float2 Bp = make_float2(fmaf(b1.x, B.x, b1.y * z[2]), fmaf(b1.x, B.y, b1.y * z[3]));
-        x[kp] = cadd(Ap, cmul_i(Bp));
-        x[kq] = cadd(cconj(Ap), cmul_i(cconj(Bp)));
-      }
-    }
-  });
-}
-
 // Wiener-filter mode at level lambda: s_hat = f t_hat with f = P/(P + lambda tau) (scaled by 1/n).
 // With STORE the result is written to prev[ky*LR + col]; with CMP the residual of the previous iterate,
 // |r_k| = |s_hat_new - s_hat_old| / (1 - f), is accumulated over the full spectrum (returned, scaled 1/n).
@@ -492,9 +459,108 @@ struct SampleArgs {
 
 // CTAs per SM the sample kernel is compiled for (register budget 65536 / (threads * CTAs)):
 // 128^2 fields are limited to three per SM by shared memory (66.5 KB each).
+#ifndef WF_SAMPLE_MIN_CTAS_128
+#define WF_SAMPLE_MIN_CTAS_128 3
+#endif
 template <int N>
-constexpr int sample_min_ctas() { return N >= 128 ? 3 : (N == 64 ? 4 : 8); }
+constexpr int sample_min_ctas() { return N >= 128 ? WF_SAMPLE_MIN_CTAS_128 : (N == 64 ? 4 : 8); }
 
+// ---------------------------------------------------------------------------------------------
+// pointwise draws as rolled loops over shared memory: the thread parks the data it holds in its own
+// slots of the (dead) field buffer, updates it in place with the Philox draws generated inline, and
+// reloads it. The field registers are dead meanwhile, which keeps register pressure off these loops.
+// ---------------------------------------------------------------------------------------------
+// t-draw of row y, staged as stg[y*STG + x] (the same layout as stage_row):
+// t = a + q (q s + sqrt(tau) xi), table aq[x*H + y] = ((1 - w) d, sqrt(w)); Philox stream 0,
+// group y*W/4 + q feeds pixels 4q .. 4q+3.
+template <int N>
+WF_HD void t_draw_staged(float* stg, int y, const float2* __restrict__ aq, float sqrt_tau, uint32_t step,
+                         uint32_t chain, uint32_t k0, uint32_t k1) {
+  using G = Geo<N>;
+  float* row = stg + y * G::STG;
+#pragma unroll 2
+  for (int q = 0; q < G::W / 4; ++q) {
+    float z[4];
+    normals4(uint32_t(y * (G::W / 4) + q), step, chain, 0u, k0, k1, z);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int x = 4 * q + e;
+      const float2 co = WF_LDG(aq + x * G::H + y);
+      row[x] = fmaf(co.y, fmaf(co.y, row[x], sqrt_tau * z[e]), co.x);
+    }
+  }
+}
+
+template <int N>
+WF_HD void load_staged_row(const float* stg, int y, float2 (&c)[N / 2]) {
+  using G = Geo<N>;
+#pragma unroll
+  for (int m = 0; m < G::LR; ++m) c[m] = make_float2(stg[y * G::STG + 2 * m], stg[y * G::STG + 2 * m + 1]);
+}
+
+// the modes of a column thread parked at cs[k * N + lt] (float2), k = register index
+template <int N>
+WF_HD void park_modes(float2* cs, int lt, const float2 (&x)[N / 2]) {
+#pragma unroll
+  for (int k = 0; k < N / 2; ++k) cs[k * N + lt] = x[k];
+}
+template <int N>
+WF_HD void unpark_modes(const float2* cs, int lt, float2 (&x)[N / 2]) {
+#pragma unroll
+  for (int k = 0; k < N / 2; ++k) x[k] = cs[k * N + lt];
+}
+
+// s-draw on parked modes: s_hat = f t_hat + g zeta, table fg[ky*WH + kx] = (f / n, g / sqrt(2 n)).
+// Mode pair kp of role r: registers kp and kq with ky1 = 2kp + r and its mirror ky2 (for_mode_pairs);
+// Philox stream 1, group col*H/2 + ky1. The packed edge column (col 0: kx = 0 as A and kx = W/2 as B in
+// Y = A + i B, both Hermitian in ky) separates A and B before the update.
+template <int N>
+WF_HD void s_draw_parked(float2* cs, int lt, const float2* __restrict__ fg, uint32_t step, uint32_t chain,
+                         uint32_t k0, uint32_t k1) {
+  using G = Geo<N>;
+  constexpr int WH = G::WH, LC = G::LC, H = G::H;
+  const int col = lt % LC, r = lt / LC;
+#pragma unroll 2
+  for (int kp = 0; kp < LC / 2; ++kp) {
+    const int kq = r == 0 ? (kp == 0 ? LC / 2 : LC - kp) : LC - 1 - kp;
+    const int ky1 = 2 * kp + r;
+    const int ky2 = r == 0 ? (kp == 0 ? H / 2 : H - 2 * kp) : H - 2 * kp - 1;
+    float z[4];
+    normals4(uint32_t(col * (H / 2) + ky1), step, chain, 1u, k0, k1, z);
+    float2 y1 = cs[kp * N + lt], y2 = cs[kq * N + lt];
+    if (col != 0) {
+      const float2 m1 = WF_LDG(fg + ky1 * WH + col), m2 = WF_LDG(fg + ky2 * WH + col);
+      y1 = make_float2(fmaf(m1.x, y1.x, m1.y * z[0]), fmaf(m1.x, y1.y, m1.y * z[1]));
+      y2 = make_float2(fmaf(m2.x, y2.x, m2.y * z[2]), fmaf(m2.x, y2.y, m2.y * z[3]));
+    } else {
+      const float2 a1 = WF_LDG(fg + ky1 * WH), b1 = WF_LDG(fg + ky1 * WH + G::W / 2);
+      if (ky1 == 0) {
+        // group 0: the four self-conjugate modes, real with variance g^2
+        const float2 a2 = WF_LDG(fg + ky2 * WH), b2 = WF_LDG(fg + ky2 * WH + G::W / 2);
+        constexpr float R2 = 1.41421356237309505f;
+        y1 = make_float2(fmaf(a1.x, y1.x, R2 * a1.y * z[0]), fmaf(b1.x, y1.y, R2 * b1.y * z[2]));
+        y2 = make_float2(fmaf(a2.x, y2.x, R2 * a2.y * z[1]), fmaf(b2.x, y2.y, R2 * b2.y * z[3]));
+      } else {
+        const float2 y2c = cconj(y2);
+        const float2 A = cscale(cadd(y1, y2c), 0.5f);
+        const float2 B = cmul_mi(cscale(csub(y1, y2c), 0.5f));
+        const float2 Ap = make_float2(fmaf(a1.x, A.x, a1.y * z[0]), fmaf(a1.x, A.y, a1.y * z[1]));
+        const float2 Bp = make_float2(fmaf(b1.x, B.x, b1.y * z[2]), fmaf(b1.x, B.y, b1.y * z[3]));
+        y1 = cadd(Ap, cmul_i(Bp));
+        y2 = cadd(cconj(Ap), cmul_i(cconj(Bp)));
+      }
+    }
+    cs[kp * N + lt] = y1;
+    cs[kq * N + lt] = y2;
+  }
+}
+
+// One sweep = four transforms, all run by the single forward-FFT block at the top of the loop (an
+// inverse transform is conj(FFT(conj(x)))), so the kernel holds one copy of the transform code:
+//   ROW_FWD: t (pixel space, after the t-draw) -> R2C rows -> store; load columns
+//   COL_FWD: column FFT -> s-draw on the parked modes -> conj
+//   COL_INV: conj -> store; load rows -> C2R pre-pass -> conj
+//   ROW_INV: conj -> s (pixel space) -> [write sample] -> t-draw on the staged row for the next sweep
 template <int N, int FPC>
 __global__ void __launch_bounds__(N * FPC, sample_min_ctas<N>()) k_sample(SampleArgs a) {
   using G = Geo<N>;
@@ -503,13 +569,13 @@ __global__ void __launch_bounds__(N * FPC, sample_min_ctas<N>()) k_sample(Sample
   const int ci = blockIdx.x * FPC + fld;
   const bool active = ci < a.n_chains;
   float2* S = reinterpret_cast<float2*>(smem_raw + fld * G::FIELD_BYTES);
-  float* stg = reinterpret_cast<float*>(S);
+  float* stg = reinterpret_cast<float*>(S);  // staged rows (between the row load and the next store)
+  float2* cs = S;                            // parked column modes (between the column load and store)
   if (a.sc->status != 0) return;  // uniform over the grid
   const float sqrt_tau = a.sc->sqrt_tau;
   const uint32_t chain = a.chain0 + uint32_t(ci);
   float2 c[G::LR];
 
-  // state s_0 -> first pixel draw -> forward row transform
   if (a.init_s != nullptr && active) {
     const float2* src = reinterpret_cast<const float2*>(a.init_s + ci * a.init_stride + lt * G::W);
 #pragma unroll
@@ -518,37 +584,53 @@ __global__ void __launch_bounds__(N * FPC, sample_min_ctas<N>()) k_sample(Sample
 #pragma unroll
     for (int m = 0; m < G::LR; ++m) c[m] = make_float2(0.f, 0.f);
   }
-  t_draw<N>(c, lt, a.aq, sqrt_tau, a.step0, chain, a.key0, a.key1);
-  row_forward<N>(c);
-  row_store_spec<N>(S, lt, c);
-  __syncthreads();
+  stage_row<N>(stg, lt, c);
+  t_draw_staged<N>(stg, lt, a.aq, sqrt_tau, a.step0, chain, a.key0, a.key1);
+  load_staged_row<N>(stg, lt, c);
 
-  for (int i = 0; i < a.n_sweeps; ++i) {
-    const uint32_t step = a.step0 + uint32_t(i);
-    // column pass: Fourier-space draw
-    col_load<N>(S, lt, c);
-    __syncthreads();
-    fft<G::LC, false>(c);
-    s_draw<N>(c, lt, a.fg, step, chain, a.key0, a.key1);
-    col_inverse_store<N>(S, lt, c);
-    __syncthreads();
-    // row pass: back to pixel space, emit, next pixel draw
-    row_load_spec<N>(S, lt, c);
-    __syncthreads();
-    row_inverse<N>(c);
-    const int done = i + 1;
-    if (done > a.burn_in && (done - a.burn_in) % a.thin == 0) {
-      const long long m = (done - a.burn_in) / a.thin - 1;
-      stage_row<N>(stg, lt, c);
-      __syncthreads();
-      if (active) copy_out<N>(stg, lt, a.out + (ci * a.n_samples + m) * (long long)(G::H * G::W));
-      __syncthreads();
-    }
-    if (done < a.n_sweeps) {
-      t_draw<N>(c, lt, a.aq, sqrt_tau, step + 1u, chain, a.key0, a.key1);
-      row_forward<N>(c);
+  enum { ROW_FWD, COL_FWD, COL_INV, ROW_INV };
+  int phase = ROW_FWD;
+  int done = 0;  // sweeps completed
+  while (true) {
+    fft<G::LR, false>(c);
+    if (phase == ROW_FWD) {
+      r2c_post_all<G::LR>(c, std::make_integer_sequence<int, G::LR>{});
+      __syncthreads();  // every staged row consumed
       row_store_spec<N>(S, lt, c);
       __syncthreads();
+      col_load<N>(S, lt, c);
+      __syncthreads();  // buffer free for the parked modes
+      phase = COL_FWD;
+    } else if (phase == COL_FWD) {
+      park_modes<N>(cs, lt, c);
+      s_draw_parked<N>(cs, lt, a.fg, a.step0 + uint32_t(done), chain, a.key0, a.key1);
+      unpark_modes<N>(cs, lt, c);
+      conj_all<G::LC>(c);
+      phase = COL_INV;
+    } else if (phase == COL_INV) {
+      conj_all<G::LC>(c);
+      __syncthreads();  // every parked mode reloaded
+      col_store_inv<N>(S, lt, c);
+      __syncthreads();
+      row_load_spec<N>(S, lt, c);
+      __syncthreads();
+      c2r_pre_all<G::LR>(c, std::make_integer_sequence<int, G::LR>{});
+      conj_all<G::LR>(c);
+      phase = ROW_INV;
+    } else {
+      conj_all<G::LR>(c);  // c[m] = (s[2m], s[2m+1]) after sweep done + 1
+      ++done;
+      stage_row<N>(stg, lt, c);
+      if (done > a.burn_in && (done - a.burn_in) % a.thin == 0) {
+        const long long m = (done - a.burn_in) / a.thin - 1;
+        __syncthreads();
+        if (active) copy_out<N>(stg, lt, a.out + (ci * a.n_samples + m) * (long long)(G::H * G::W));
+        __syncthreads();
+      }
+      if (done == a.n_sweeps) break;
+      t_draw_staged<N>(stg, lt, a.aq, sqrt_tau, a.step0 + uint32_t(done), chain, a.key0, a.key1);
+      load_staged_row<N>(stg, lt, c);
+      phase = ROW_FWD;
     }
   }
 }

@@ -148,10 +148,75 @@ WF_HD void stages(float2 (&x)[L]) {
 
 // X[k] = sum_m x[m] exp(-+2 pi i m k / L)
 template <int L, bool INV>
-WF_HD void fft(float2 (&x)[L]) {
+WF_HD void fft_radix2(float2 (&x)[L]) {
   static_assert((L & (L - 1)) == 0 && L >= 2, "power-of-two length");
   bitrev_all<L>(x, std::make_integer_sequence<int, L>{});
   stages<L, 1, INV>(x);
+}
+
+// Two consecutive radix-2 decimation-in-time stages (halves HALF and 2*HALF) fused into one radix-4
+// butterfly on x[b+j], x[b+j+H], x[b+j+2H], x[b+j+3H] with w = exp(-+2 pi i j / 4H):
+//   y0 = (a0 + w^2 a1) + (w a2 + w^3 a3)     y2 = (a0 + w^2 a1) - (w a2 + w^3 a3)
+//   y1 = (a0 - w^2 a1) -+ i (w a2 - w^3 a3)  y3 = (a0 - w^2 a1) +- i (w a2 - w^3 a3)
+// (three twiddle products instead of four).
+// s = a + w x and d = a - w x for the compile-time twiddle w = exp(-+2 pi i K / N). For a general w the
+// product is fused into s (four FMAs) and d = 2a - s (two FMAs) instead of a product and two sums.
+template <long K, long N, bool INV>
+WF_HD void tw_addsub(float2 a, float2 x, float2& s, float2& d) {
+  constexpr long k = ((K % N) + N) % N;
+  if constexpr (k == 0 || 4 * k == N || 2 * k == N || 4 * k == 3 * N) {
+    const float2 t = twiddle<K, N, INV>(x);  // 1, -+i, -1, +-i: no multiplications
+    s = cadd(a, t);
+    d = csub(a, t);
+  } else {
+    constexpr float wr = Tw<k, N, INV>::re, wi = Tw<k, N, INV>::im;
+    s = make_float2(fmaf(wr, x.x, fmaf(-wi, x.y, a.x)), fmaf(wr, x.y, fmaf(wi, x.x, a.y)));
+    d = make_float2(fmaf(2.0f, a.x, -s.x), fmaf(2.0f, a.y, -s.y));
+  }
+}
+
+// Two consecutive radix-2 decimation-in-time stages (halves HALF and 2*HALF) fused into one radix-4
+// butterfly on x[b+j], x[b+j+H], x[b+j+2H], x[b+j+3H] with w = exp(-+2 pi i j / 4H):
+//   y0 = (a0 + w^2 a1) + (w a2 + w^3 a3)     y2 = (a0 + w^2 a1) - (w a2 + w^3 a3)
+//   y1 = (a0 - w^2 a1) -+ i (w a2 - w^3 a3)  y3 = (a0 - w^2 a1) +- i (w a2 - w^3 a3)
+// (three twiddle products instead of four, two of them fused into the sums).
+template <int L, int HALF, bool INV, int B>
+WF_HD void butterfly4(float2 (&x)[L]) {
+  constexpr int j = B % HALF;
+  constexpr int i0 = (B / HALF) * 4 * HALF + j;
+  float2 s01, d01, s23, d23;
+  tw_addsub<2 * j, 4 * HALF, INV>(x[i0], x[i0 + HALF], s01, d01);
+  tw_addsub<3 * j, 4 * HALF, INV>(twiddle<j, 4 * HALF, INV>(x[i0 + 2 * HALF]), x[i0 + 3 * HALF], s23, d23);
+  const float2 rot = INV ? cmul_i(d23) : cmul_mi(d23);
+  x[i0] = cadd(s01, s23);
+  x[i0 + 2 * HALF] = csub(s01, s23);
+  x[i0 + HALF] = cadd(d01, rot);
+  x[i0 + 3 * HALF] = csub(d01, rot);
+}
+template <int L, int HALF, bool INV, int... B>
+WF_HD void stage4(float2 (&x)[L], std::integer_sequence<int, B...>) {
+  (butterfly4<L, HALF, INV, B>(x), ...);
+}
+template <int L, int HALF, bool INV>
+WF_HD void stages4(float2 (&x)[L]) {
+  if constexpr (4 * HALF <= L) {
+    stage4<L, HALF, INV>(x, std::make_integer_sequence<int, L / 4>{});
+    stages4<L, 4 * HALF, INV>(x);
+  }
+}
+
+// X[k] = sum_m x[m] exp(-+2 pi i m k / L): bit reversal, one radix-2 stage if log2 L is odd, then
+// radix-4 stages.
+template <int L, bool INV>
+WF_HD void fft(float2 (&x)[L]) {
+  static_assert((L & (L - 1)) == 0 && L >= 2, "power-of-two length");
+  bitrev_all<L>(x, std::make_integer_sequence<int, L>{});
+  if constexpr (ilog2(L) % 2 == 1) {
+    stage<L, 1, INV>(x, std::make_integer_sequence<int, L / 2>{});
+    stages4<L, 2, INV>(x);
+  } else {
+    stages4<L, 1, INV>(x);
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -237,19 +302,25 @@ WF_HD u4 philox4x32_10(u4 c, uint32_t k0, uint32_t k1) {
 // 32-bit word -> odd multiple of 2^-24 in (0, 1), exact in float
 WF_HD float to_uniform(uint32_t x) { return float(2u * (x >> 9) + 1u) * 5.9604644775390625e-08f; }
 
-// (z0, z1) = sqrt(-2 ln u0) (cos 2 pi u1, sin 2 pi u1)
+// (z0, z1) = sqrt(-2 ln u0) (cos 2 pi u1, sin 2 pi u1), u = (2 floor(x / 2^9) + 1) 2^-24.
+// Device: -2 ln u0 = -2 ln(2) log2(u0) from the hardware log2, clamped at the smallest normal float
+// (log2 of the largest u, 1 - 2^-24, may round to zero), its square root as x * rsqrt(x); the angle
+// 2 pi (u1 - 1/2) in (-pi, pi), for which cos(2 pi u) = -cos(2 pi (u - 1/2)) and likewise for sin.
 WF_HD void box_muller(uint32_t a, uint32_t b, float& z0, float& z1) {
-  float u0 = to_uniform(a), u1 = to_uniform(b);
 #if defined(__CUDA_ARCH__)
-  float r = sqrtf(-2.0f * __logf(u0));
+  const float ka = float(a >> 9), kb = float(b >> 9);
+  const float u0 = fmaf(ka, 1.1920928955078125e-07f, 5.9604644775390625e-08f);        // (2k + 1) 2^-24
+  const float ang = fmaf(kb, 7.490140565847157e-07f, -3.1415922790827646f);            // 2 pi (u1 - 1/2)
+  const float e = fmaxf(-1.3862943611198906f * __log2f(u0), 1.17549435e-38f);          // -2 ln u0
+  const float r = e * rsqrtf(e);
   float sn, cs;
-  // 2 pi u1 folded to (-pi, pi): cos(2 pi u) = -cos(2 pi (u - 1/2)), same for sin
-  __sincosf(6.28318530717958647692f * (u1 - 0.5f), &sn, &cs);
+  __sincosf(ang, &sn, &cs);
   z0 = -r * cs;
   z1 = -r * sn;
 #else
-  float r = sqrtf(-2.0f * logf(u0));
-  float a2 = 6.28318530717958647692f * (u1 - 0.5f);
+  const float u0 = to_uniform(a), u1 = to_uniform(b);
+  const float r = sqrtf(-2.0f * logf(u0));
+  const float a2 = 6.28318530717958647692f * (u1 - 0.5f);
   z0 = -r * cosf(a2);
   z1 = -r * sinf(a2);
 #endif
