@@ -20,7 +20,11 @@
  *   - tau: messenger variance T = tau I (Alg. 1 definitions). tau <= 0 selects the paper's choice,
  *     the minimum observed Ndiag (max_k P_k if every pixel is missing). A tau above the minimum observed
  *     Ndiag is rejected with WF_ERR_TAU.
- *   - Supported sizes: H == W in {16, 32, 64, 128} (wf_supported_size).
+ *   - Supported sizes: H == W in {16, 32, 64, 128, 256, 512, 1024} (wf_supported_size). Up to 128 x 128
+ *     a chain's field stays in one SM's shared memory for the whole call; larger images keep the field in
+ *     global memory and run as one cooperative launch (all CTAs co-resident) whose phases are separated by
+ *     a bounded grid barrier (WF_ERR_TIMEOUT if a barrier wait gives up). For those sizes wf_solve_ex
+ *     starts from zero (opts->init_s must be NULL).
  *   - Pointers named d, Ndiag, mask, Pk, out*, init_s are DEVICE pointers owned by the caller; pointers
  *     to iters_out / resid_out / opts are HOST pointers (may be NULL where stated).
  *   - Calls are ordered on `stream` and return after the stream has reached their end (they

@@ -126,7 +126,40 @@ __global__ void k_tables(const float* __restrict__ d, const float* __restrict__ 
 // ---------------------------------------------------------------------------------------------
 // launch helpers per size
 // ---------------------------------------------------------------------------------------------
-bool size_ok(int H, int W) { return H == W && (H == 16 || H == 32 || H == 64 || H == 128); }
+bool size_ok(int H, int W) {
+  return H == W && (H == 16 || H == 32 || H == 64 || H == 128 || H == 256 || H == 512 || H == 1024);
+}
+bool size_on_chip(int H) { return H <= 128; }
+
+// Twiddle tables of the large-image path, in FP64 then rounded once:
+// tw_row[j] = exp(-2 pi i j / (W/2)), tw_col[j] = exp(-2 pi i j / H), tw_real[k] = exp(-2 pi i k / W).
+__global__ void k_twiddles(int H, int W, float2* tw_row, float2* tw_col, float2* tw_real) {
+  const int LR = W / 2;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < LR + H + LR; i += gridDim.x * blockDim.x) {
+    double sn, cs;
+    if (i < LR) {
+      sincospi(-2.0 * double(i) / double(LR), &sn, &cs);
+      tw_row[i] = make_float2(float(cs), float(sn));
+    } else if (i < LR + H) {
+      const int j = i - LR;
+      sincospi(-2.0 * double(j) / double(H), &sn, &cs);
+      tw_col[j] = make_float2(float(cs), float(sn));
+    } else {
+      const int k = i - LR - H;
+      sincospi(-2.0 * double(k) / double(W), &sn, &cs);
+      tw_real[k] = make_float2(float(cs), float(sn));
+    }
+  }
+}
+
+cudaError_t launch_global_any(int H, const wf::GlobalArgs& a, cudaStream_t st, wf::LaunchTimer* t) {
+  switch (H) {
+    case 256: return wf::launch_global<256>(a, st, t);
+    case 512: return wf::launch_global<512>(a, st, t);
+    case 1024: return wf::launch_global<1024>(a, st, t);
+  }
+  return cudaErrorInvalidValue;
+}
 
 // scratch carved from one stream-ordered allocation
 struct Scratch {
@@ -138,6 +171,157 @@ struct Scratch {
 };
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// bump allocator over one cudaMallocAsync block
+struct Carve {
+  size_t off = 0;
+  template <class T>
+  size_t take(size_t count) {
+    const size_t o = off;
+    off += align256(count * sizeof(T));
+    return o;
+  }
+};
+
+// Sampler for H >= 256: fields = chains, state in global memory, one cooperative launch.
+wf_status sample_global(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int H, int W,
+                        uint64_t seed, const wf_sample_opts& o, long long sweeps, float* out, cudaStream_t st,
+                        wf::LaunchTimer* timer) {
+  const size_t n = size_t(H) * W, nm = size_t(H) * (W / 2 + 1), nz = size_t(H) * (W / 2);
+  Carve cv;
+  const size_t o_sc = cv.take<wf::Scalars>(1), o_bar = cv.take<wf::GridBar>(1), o_aq = cv.take<float2>(n),
+               o_fg = cv.take<float2>(nm), o_tr = cv.take<float2>(W / 2), o_tc = cv.take<float2>(H),
+               o_tw = cv.take<float2>(W / 2), o_z = cv.take<float2>(nz * size_t(o.n_chains));
+  Scratch scr;
+  scr.st = st;
+  WF_CUDA(cudaMallocAsync(&scr.base, cv.off, st));
+  char* b = static_cast<char*>(scr.base);
+  auto* sc = reinterpret_cast<wf::Scalars*>(b + o_sc);
+  auto* bar = reinterpret_cast<wf::GridBar*>(b + o_bar);
+  WF_CUDA(cudaMemsetAsync(bar, 0, sizeof(wf::GridBar), st));
+  k_prep<<<1, 1024, 0, st>>>(d, Ndiag, mask, Pk, H, W, o.tau, 0.5, sc);
+  WF_CUDA(cudaGetLastError());
+  k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc,
+                                                       reinterpret_cast<float2*>(b + o_aq), nullptr,
+                                                       reinterpret_cast<float2*>(b + o_fg));
+  WF_CUDA(cudaGetLastError());
+  k_twiddles<<<8, 256, 0, st>>>(H, W, reinterpret_cast<float2*>(b + o_tr), reinterpret_cast<float2*>(b + o_tc),
+                                reinterpret_cast<float2*>(b + o_tw));
+  WF_CUDA(cudaGetLastError());
+  wf::GlobalArgs a{};
+  a.Z = reinterpret_cast<float2*>(b + o_z);
+  a.tw_row = reinterpret_cast<float2*>(b + o_tr);
+  a.tw_col = reinterpret_cast<float2*>(b + o_tc);
+  a.tw_real = reinterpret_cast<float2*>(b + o_tw);
+  a.aq = reinterpret_cast<float2*>(b + o_aq);
+  a.fg = reinterpret_cast<float2*>(b + o_fg);
+  a.Pk = Pk;
+  a.sc = sc;
+  a.bar = bar;
+  a.init_s = o.init_s;
+  a.init_stride = (o.init_s && o.init_per_chain) ? (long long)n : 0;
+  a.out = out;
+  a.n_samples = o.n_samples;
+  a.n_fields = o.n_chains;
+  a.n_sweeps = int(sweeps);
+  a.burn_in = o.burn_in;
+  a.thin = o.thin;
+  a.chain0 = o.chain_offset;
+  a.step0 = o.start_step;
+  a.key0 = uint32_t(seed & 0xffffffffu);
+  a.key1 = uint32_t(seed >> 32);
+  a.mode = 0;
+  cudaError_t e = launch_global_any(H, a, st, timer);
+  if (e != cudaSuccess) return cuda_fail(e);
+  wf::Scalars hsc;
+  wf::GridBar hb;
+  WF_CUDA(cudaMemcpyAsync(&hsc, sc, sizeof(hsc), cudaMemcpyDeviceToHost, st));
+  WF_CUDA(cudaMemcpyAsync(&hb, bar, sizeof(hb), cudaMemcpyDeviceToHost, st));
+  WF_CUDA(cudaStreamSynchronize(st));
+  if (hsc.status != WF_OK) return wf_status(hsc.status);
+  return hb.err ? wf_status(hb.err) : WF_OK;
+}
+
+// Wiener filter for H >= 256: level norms (fields = levels), then the cooled iteration, field in
+// global memory.
+wf_status solve_global(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int H, int W,
+                       const wf_solve_opts& o, float* out_s, int32_t* iters_out, double* resid_out, cudaStream_t st,
+                       wf::LaunchTimer* timer) {
+  const size_t n = size_t(H) * W, nz = size_t(H) * (W / 2);
+  // scalars first: the number of cooling levels sizes the level-norm pass
+  Scratch s1;
+  s1.st = st;
+  WF_CUDA(cudaMallocAsync(&s1.base, sizeof(wf::Scalars), st));
+  auto* sc1 = static_cast<wf::Scalars*>(s1.base);
+  k_prep<<<1, 1024, 0, st>>>(d, Ndiag, mask, Pk, H, W, o.tau, o.eta, sc1);
+  WF_CUDA(cudaGetLastError());
+  wf::Scalars hsc;
+  WF_CUDA(cudaMemcpyAsync(&hsc, sc1, sizeof(hsc), cudaMemcpyDeviceToHost, st));
+  WF_CUDA(cudaStreamSynchronize(st));
+  if (hsc.status != WF_OK) return wf_status(hsc.status);
+  const int levels = hsc.n_levels;
+  Carve cv;
+  const size_t o_sc = cv.take<wf::Scalars>(1), o_bar = cv.take<wf::GridBar>(2), o_dn = cv.take<float2>(n),
+               o_tr = cv.take<float2>(W / 2), o_tc = cv.take<float2>(H), o_tw = cv.take<float2>(W / 2),
+               o_bn = cv.take<double>(wf::kMaxLevels), o_acc = cv.take<double>(2), o_st = cv.take<wf::SolveStatus>(1),
+               o_prev = cv.take<float2>(nz), o_z = cv.take<float2>(nz * size_t(levels > 1 ? levels : 1));
+  Scratch scr;
+  scr.st = st;
+  WF_CUDA(cudaMallocAsync(&scr.base, cv.off, st));
+  char* b = static_cast<char*>(scr.base);
+  auto* sc = reinterpret_cast<wf::Scalars*>(b + o_sc);
+  auto* bar = reinterpret_cast<wf::GridBar*>(b + o_bar);
+  WF_CUDA(cudaMemcpyAsync(sc, &hsc, sizeof(hsc), cudaMemcpyHostToDevice, st));
+  WF_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(wf::GridBar), st));
+  WF_CUDA(cudaMemsetAsync(b + o_bn, 0, wf::kMaxLevels * sizeof(double), st));
+  WF_CUDA(cudaMemsetAsync(b + o_acc, 0, 2 * sizeof(double), st));
+  WF_CUDA(cudaMemsetAsync(b + o_st, 0, sizeof(wf::SolveStatus), st));
+  k_tables<<<int((n + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc, nullptr,
+                                                 reinterpret_cast<float2*>(b + o_dn), nullptr);
+  WF_CUDA(cudaGetLastError());
+  k_twiddles<<<8, 256, 0, st>>>(H, W, reinterpret_cast<float2*>(b + o_tr), reinterpret_cast<float2*>(b + o_tc),
+                                reinterpret_cast<float2*>(b + o_tw));
+  WF_CUDA(cudaGetLastError());
+  wf::GlobalArgs a{};
+  a.Z = reinterpret_cast<float2*>(b + o_z);
+  a.tw_row = reinterpret_cast<float2*>(b + o_tr);
+  a.tw_col = reinterpret_cast<float2*>(b + o_tc);
+  a.tw_real = reinterpret_cast<float2*>(b + o_tw);
+  a.dn = reinterpret_cast<float2*>(b + o_dn);
+  a.Pk = Pk;
+  a.sc = sc;
+  a.bar = bar;
+  a.eta = o.eta;
+  a.mode = 2;
+  a.n_fields = levels;
+  a.bnorm_out = reinterpret_cast<double*>(b + o_bn);
+  cudaError_t e = launch_global_any(H, a, st, nullptr);
+  if (e != cudaSuccess) return cuda_fail(e);
+  a.mode = 1;
+  a.n_fields = 1;
+  a.bar = bar + 1;
+  a.bnorm2 = reinterpret_cast<double*>(b + o_bn);
+  a.acc = reinterpret_cast<double*>(b + o_acc);
+  a.prev = reinterpret_cast<float2*>(b + o_prev);
+  a.st = reinterpret_cast<wf::SolveStatus*>(b + o_st);
+  a.out = out_s;
+  a.tol = o.tol;
+  a.level_tol = o.level_tol;
+  a.max_iter = o.max_iter;
+  a.level_max = o.level_max;
+  a.check = o.check;
+  e = launch_global_any(H, a, st, timer);
+  if (e != cudaSuccess) return cuda_fail(e);
+  wf::SolveStatus hst;
+  wf::GridBar hb[2];
+  WF_CUDA(cudaMemcpyAsync(&hst, a.st, sizeof(hst), cudaMemcpyDeviceToHost, st));
+  WF_CUDA(cudaMemcpyAsync(hb, bar, sizeof(hb), cudaMemcpyDeviceToHost, st));
+  WF_CUDA(cudaStreamSynchronize(st));
+  if (hb[0].err || hb[1].err) return wf_status(hb[0].err ? hb[0].err : hb[1].err);
+  if (iters_out) *iters_out = hst.iters;
+  if (resid_out) *resid_out = hst.resid;
+  return wf_status(hst.status);
+}
 
 }  // namespace
 
@@ -206,6 +390,13 @@ wf_status wf_solve_ex(const float* d, const float* Ndiag, const uint8_t* mask, c
       o.max_iter < 1)
     return WF_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (!size_on_chip(H)) {
+    if (o.init_s) return WF_ERR_ARG;  // the large-image solve starts from zero
+    KernelTimer gt(st);
+    const wf_status r = solve_global(d, Ndiag, mask, Pk, H, W, o, out_s, iters_out, resid_out, st, &gt);
+    gt.collect();
+    return r;
+  }
   const size_t n = size_t(H) * W, nm = size_t(H) * (W / 2 + 1);
   const size_t off_sc = 0, off_st = align256(sizeof(wf::Scalars)),
                off_bn = off_st + align256(sizeof(wf::SolveStatus)),
@@ -273,6 +464,12 @@ wf_status wf_sample_ex(const float* d, const float* Ndiag, const uint8_t* mask, 
   const long long sweeps = (long long)o.burn_in + o.n_samples * (long long)o.thin;
   if (sweeps > 0x7fffffffLL || o.n_samples > 0x7fffffffLL) return WF_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (!size_on_chip(H)) {
+    KernelTimer gt(st);
+    const wf_status r = sample_global(d, Ndiag, mask, Pk, H, W, seed, o, sweeps, out, st, &gt);
+    gt.collect();
+    return r;
+  }
   const size_t n = size_t(H) * W, nm = size_t(H) * (W / 2 + 1);
   const size_t off_sc = 0, off_aq = align256(sizeof(wf::Scalars)), off_fg = off_aq + align256(n * sizeof(float2)),
                total = off_fg + align256(nm * sizeof(float2));

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "wf_gibbs.cuh"
+#include "wf_global.cuh"
 
 namespace wf {
 
@@ -22,6 +23,10 @@ cudaError_t launch_sample(const SampleArgs& a, cudaStream_t st, LaunchTimer* t);
 
 template <int N>
 cudaError_t launch_solve(const SolveArgs& a, const BnormArgs& b, cudaStream_t st, LaunchTimer* t);
+
+// large images (N >= 256): one cooperative launch of k_global<N> (all CTAs co-resident)
+template <int N>
+cudaError_t launch_global(const GlobalArgs& a, cudaStream_t st, LaunchTimer* t);
 
 // definitions, included by the per-size translation units only
 #if defined(WF_LAUNCH_DEFINE)
@@ -55,9 +60,34 @@ cudaError_t launch_solve(const SolveArgs& a, const BnormArgs& b, cudaStream_t st
   return cudaGetLastError();
 }
 
+
 #define WF_INSTANTIATE(N)                                                              \
   template cudaError_t launch_sample<N>(const SampleArgs&, cudaStream_t, LaunchTimer*); \
   template cudaError_t launch_solve<N>(const SolveArgs&, const BnormArgs&, cudaStream_t, LaunchTimer*);
+#endif
+
+#if defined(WF_LAUNCH_DEFINE_GLOBAL)
+template <int N>
+cudaError_t launch_global(const GlobalArgs& a, cudaStream_t st, LaunchTimer* t) {
+  using G = GGeo<N>;
+  cudaError_t e = cudaFuncSetAttribute(k_global<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_global<N>, 128, G::SMEM)) != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const long long items = (long long)(G::ROW_ITEMS > G::COL_ITEMS ? G::ROW_ITEMS : G::COL_ITEMS) * a.n_fields;
+  const int grid = int(items < (long long)per_sm * sms ? items : (long long)per_sm * sms);
+  GlobalArgs arg = a;
+  void* args[] = {&arg};
+  if (t) t->start();
+  e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_global<N>), dim3(grid), dim3(128), args, G::SMEM, st);
+  if (t) t->stop();
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+#define WF_INSTANTIATE_GLOBAL(N) template cudaError_t launch_global<N>(const GlobalArgs&, cudaStream_t, LaunchTimer*);
 #endif
 
 }  // namespace wf

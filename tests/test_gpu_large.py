@@ -1,0 +1,75 @@
+"""GPU parity of the large-image path (N = 256, 512, 1024: field in global memory, cooperative kernel)."""
+import numpy as np
+import pytest
+
+from gpu_common import need_gpu, rel, to_dev, torch
+from oracle import messenger as M
+from paper_1810_02821_gb300 import build, synth, wf
+
+pytestmark = pytest.mark.gpu
+
+SAMPLE_TOL = 1e-4
+WF_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    need_gpu()
+    build.build()
+    wf.load_library()
+
+
+@pytest.mark.parametrize("H", [256, 512])
+def test_sample_large_draw_for_draw(H):
+    p = synth.make_problem(H, seed=H, mask_frac=0.1, block=(10, 60, 20, 90), slope=-2.0, k0=1.0 / 32,
+                           sigma2=(0.05, 0.5))
+    n_samples = 3 if H == 256 else 2
+    got = wf.wf_sample_ex(*to_dev(p), seed=13, n_samples=n_samples, n_chains=3, chain_offset=7, burn_in=1)
+    got = got.cpu().numpy()
+    for c in ([0, 2] if H == 256 else [1]):
+        ref = M.sample(p.d, p.Ndiag, p.mask, p.Pk, n_samples, seed=13, chain=7 + c, burn_in=1)
+        for m in range(n_samples):
+            assert rel(got[c, m], ref[m]) < SAMPLE_TOL, (H, c, m, rel(got[c, m], ref[m]))
+
+
+def test_sample_1024_one_sweep():
+    p = synth.make_problem(1024, seed=4, mask_frac=0.05, slope=-1.5, sigma2=(0.001, 0.1))
+    got = wf.wf_sample_ex(*to_dev(p), seed=3, n_samples=1, n_chains=1).cpu().numpy()
+    ref = M.sample(p.d, p.Ndiag, p.mask, p.Pk, 1, seed=3)
+    assert rel(got[0, 0], ref[0]) < SAMPLE_TOL
+
+
+def _easy(H):
+    # small signal-to-noise range so that the iteration converges in tens of sweeps
+    return synth.make_problem(H, seed=H + 3, mask_frac=0.05, slope=-1.0, k0=1.0 / 4, sigma2=(0.5, 1.0))
+
+
+@pytest.mark.parametrize("H", [256, 512])
+def test_wiener_filter_large(H):
+    p = _easy(H)
+    r = wf.wf_solve(*to_dev(p), tol=1e-7)
+    assert r.status == 0
+    ref, it, rho = M.wf_solve(p.d, p.Ndiag, p.mask, p.Pk, tol=1e-10)
+    assert rho < 1e-10
+    assert rel(r.s.cpu().numpy(), ref) < WF_TOL
+
+
+def _residual_fft(s, p):
+    """||s + S N^-1 (s - d)|| / ||S N^-1 d|| with numpy.fft (unitary; N^-1 = 0 on missing pixels)."""
+    obs = p.mask == 0
+    Ninv = np.where(obs, 1.0 / p.Ndiag.astype(np.float64), 0.0)
+    P = p.Pk.astype(np.float64)
+    H, W = p.d.shape
+    S = lambda v: np.fft.irfft2(P * np.fft.rfft2(v, norm="ortho"), s=(H, W), norm="ortho")
+    d = p.d.astype(np.float64)
+    b = S(Ninv * d)
+    r = s + S(Ninv * (s - d))
+    return np.linalg.norm(r) / np.linalg.norm(b)
+
+
+def test_wiener_filter_1024_converges():
+    p = synth.make_problem(1024, seed=9, mask_frac=0.1, slope=-1.5, sigma2=(0.01, 0.1))
+    r = wf.wf_solve_ex(*to_dev(p), tol=1e-6, max_iter=20000)
+    assert r.status == 0
+    s = r.s.double().cpu().numpy()
+    assert _residual_fft(s, p) < 2e-5
