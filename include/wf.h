@@ -117,6 +117,50 @@ wf_status wf_sample(const float* d, const float* Ndiag, const uint8_t* mask, con
 wf_status wf_sample_ex(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int32_t H,
                        int32_t W, uint64_t seed, const wf_sample_opts* opts, float* out, wf_stream_t stream);
 
+/*
+ * Batched form: many independent images of possibly different sizes, each with its own data, noise map,
+ * mask, power spectrum and outputs. For every item the library computes the Wiener filter (as wf_solve_ex
+ * with the options below, from zero) and then n_samples posterior samples of one chain started at the
+ * Wiener filter (Alg. 1 from s_0 = s_W, no burn-in, thin 1, Philox key `seed`, chain word `chain`, step
+ * words 0 .. n_samples-1). Chains are independent (§4.2 of the paper runs independent chains in parallel).
+ *   - Images up to 128 x 128 run through one persistent launch per size: every CTA keeps one image's field
+ *     in shared memory and takes images from an atomic work counter until none is left. Larger images run
+ *     their cooperative pipelines on a pool of `large_streams` streams. All of it is ordered after the
+ *     work already on `stream` and the call returns when everything has finished.
+ *   - items: HOST array; the pointers inside are DEVICE pointers owned by the caller; out_wf may be NULL
+ *     (then the filter is not written), out_samples may be NULL when n_samples == 0.
+ *   - On return items[i].status / iters / resid hold each image's wf_status, solve sweeps and last
+ *     measured residual. The return value is WF_OK if every item succeeded, else the status of the first
+ *     failing item (argument and CUDA errors abort the call before any work).
+ */
+typedef struct {
+  const float* d;
+  const float* Ndiag;
+  const uint8_t* mask;
+  const float* Pk;
+  int32_t H, W;
+  float* out_wf;       /* device [H][W] or NULL */
+  float* out_samples;  /* device [n_samples][H][W] or NULL */
+  uint64_t seed;
+  uint32_t chain;
+  int32_t status;      /* out */
+  int32_t iters;       /* out */
+  int32_t reserved;
+  double resid;        /* out */
+} wf_batch_item;
+
+typedef struct {
+  double tau;          /* <= 0: each image's minimum observed Ndiag */
+  double tol, eta, level_tol;
+  int32_t level_max, check, max_iter;
+  int32_t n_samples;   /* samples per image (>= 0) */
+  int32_t large_streams; /* concurrent pipelines for images above 128 x 128 (>= 1) */
+  int32_t reserved;
+} wf_batch_opts;
+
+void wf_batch_opts_default(wf_batch_opts* o);
+wf_status wf_batch_run(wf_batch_item* items, int32_t n_items, const wf_batch_opts* opts, wf_stream_t stream);
+
 /* 1 if (H, W) is supported by wf_solve / wf_sample, else 0. */
 int32_t wf_supported_size(int32_t H, int32_t W);
 

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -512,6 +513,310 @@ wf_status wf_sample(const float* d, const float* Ndiag, const uint8_t* mask, con
   wf_sample_opts_default(&o);
   o.n_samples = n_samples;
   return wf_sample_ex(d, Ndiag, mask, Pk, H, W, seed, &o, out, stream);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// batched form
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+cudaError_t launch_batch_any(int H, const wf::BatchArgs& b, cudaStream_t st) {
+  switch (H) {
+    case 16: return wf::launch_batch<16>(b, nullptr, st);
+    case 32: return wf::launch_batch<32>(b, nullptr, st);
+    case 64: return wf::launch_batch<64>(b, nullptr, st);
+    case 128: return wf::launch_batch<128>(b, nullptr, st);
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t batch_grid_any(int H, int n, int* g) {
+  switch (H) {
+    case 16: return wf::batch_grid<16>(n, g);
+    case 32: return wf::batch_grid<32>(n, g);
+    case 64: return wf::batch_grid<64>(n, g);
+    case 128: return wf::batch_grid<128>(n, g);
+  }
+  return cudaErrorInvalidValue;
+}
+long long batch_slot_any(int H) {
+  switch (H) {
+    case 16: return wf::batch_slot_bytes<16>();
+    case 32: return wf::batch_slot_bytes<32>();
+    case 64: return wf::batch_slot_bytes<64>();
+    case 128: return wf::batch_slot_bytes<128>();
+  }
+  return 0;
+}
+
+// One large image (H >= 256) of a batch on stream st: tables, level norms, cooled solve, samples from
+// s_W, status into res. Scratch `b` (carved by the caller) is reused by the images of the same stream.
+struct LargeScratch {
+  char* base = nullptr;
+  size_t o_sc, o_bar, o_aq, o_dn, o_fg, o_tr, o_tc, o_tw, o_bn, o_acc, o_st, o_prev, o_sw, o_z, total;
+};
+LargeScratch large_layout(int H) {
+  const size_t n = size_t(H) * H, nm = size_t(H) * (H / 2 + 1), nz = size_t(H) * (H / 2);
+  Carve cv;
+  LargeScratch L;
+  L.o_sc = cv.take<wf::Scalars>(1);
+  L.o_bar = cv.take<wf::GridBar>(3);
+  L.o_aq = cv.take<float2>(n);
+  L.o_dn = cv.take<float2>(n);
+  L.o_fg = cv.take<float2>(nm);
+  L.o_tr = cv.take<float2>(H / 2);
+  L.o_tc = cv.take<float2>(H);
+  L.o_tw = cv.take<float2>(H / 2);
+  L.o_bn = cv.take<double>(wf::kMaxLevels);
+  L.o_acc = cv.take<double>(2);
+  L.o_st = cv.take<wf::SolveStatus>(1);
+  L.o_prev = cv.take<float2>(nz);
+  L.o_sw = cv.take<float>(n);
+  L.o_z = cv.take<float2>(nz * size_t(wf::kMaxLevels));
+  L.total = cv.off;
+  return L;
+}
+
+wf_status run_large_item(const wf::BatchItem& it, int W, const wf_batch_opts& o, const LargeScratch& L,
+                         wf::BatchResult* res, cudaStream_t st) {
+  const int H = it.H;
+  const size_t n = size_t(H) * W, nm = size_t(H) * (W / 2 + 1);
+  char* b = L.base;
+  auto* sc = reinterpret_cast<wf::Scalars*>(b + L.o_sc);
+  auto* bar = reinterpret_cast<wf::GridBar*>(b + L.o_bar);
+  WF_CUDA(cudaMemsetAsync(bar, 0, 3 * sizeof(wf::GridBar), st));
+  WF_CUDA(cudaMemsetAsync(b + L.o_bn, 0, wf::kMaxLevels * sizeof(double), st));
+  WF_CUDA(cudaMemsetAsync(b + L.o_acc, 0, 2 * sizeof(double), st));
+  WF_CUDA(cudaMemsetAsync(b + L.o_st, 0, sizeof(wf::SolveStatus), st));
+  k_prep<<<1, 1024, 0, st>>>(it.d, it.Ndiag, it.mask, it.Pk, H, W, o.tau, o.eta, sc);
+  WF_CUDA(cudaGetLastError());
+  k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(it.d, it.Ndiag, it.mask, it.Pk, H, W, sc,
+                                                       reinterpret_cast<float2*>(b + L.o_aq),
+                                                       reinterpret_cast<float2*>(b + L.o_dn),
+                                                       reinterpret_cast<float2*>(b + L.o_fg));
+  WF_CUDA(cudaGetLastError());
+  k_twiddles<<<8, 256, 0, st>>>(H, W, reinterpret_cast<float2*>(b + L.o_tr), reinterpret_cast<float2*>(b + L.o_tc),
+                                reinterpret_cast<float2*>(b + L.o_tw));
+  WF_CUDA(cudaGetLastError());
+  float* sw = it.out_wf ? it.out_wf : reinterpret_cast<float*>(b + L.o_sw);
+  wf::GlobalArgs a{};
+  a.Z = reinterpret_cast<float2*>(b + L.o_z);
+  a.tw_row = reinterpret_cast<float2*>(b + L.o_tr);
+  a.tw_col = reinterpret_cast<float2*>(b + L.o_tc);
+  a.tw_real = reinterpret_cast<float2*>(b + L.o_tw);
+  a.aq = reinterpret_cast<float2*>(b + L.o_aq);
+  a.fg = reinterpret_cast<float2*>(b + L.o_fg);
+  a.dn = reinterpret_cast<float2*>(b + L.o_dn);
+  a.Pk = it.Pk;
+  a.sc = sc;
+  a.eta = o.eta;
+  // level norms (fields = levels; fields past the schedule are skipped on the device)
+  a.mode = 2;
+  a.bar = bar;
+  a.n_fields = wf::kMaxLevels;
+  a.bnorm_out = reinterpret_cast<double*>(b + L.o_bn);
+  cudaError_t e = launch_global_any(H, a, st, nullptr);
+  if (e != cudaSuccess) return cuda_fail(e);
+  // cooled solve
+  a.mode = 1;
+  a.bar = bar + 1;
+  a.n_fields = 1;
+  a.bnorm2 = reinterpret_cast<double*>(b + L.o_bn);
+  a.acc = reinterpret_cast<double*>(b + L.o_acc);
+  a.prev = reinterpret_cast<float2*>(b + L.o_prev);
+  a.st = reinterpret_cast<wf::SolveStatus*>(b + L.o_st);
+  a.out = sw;
+  a.tol = o.tol;
+  a.level_tol = o.level_tol;
+  a.max_iter = o.max_iter;
+  a.level_max = o.level_max;
+  a.check = o.check;
+  if ((e = launch_global_any(H, a, st, nullptr)) != cudaSuccess) return cuda_fail(e);
+  WF_CUDA(cudaMemcpyAsync(res, a.st, sizeof(wf::SolveStatus), cudaMemcpyDeviceToDevice, st));
+  // samples from s_W
+  if (o.n_samples > 0 && it.out_samples) {
+    a.mode = 0;
+    a.bar = bar + 2;
+    a.init_s = sw;
+    a.init_stride = 0;
+    a.out = it.out_samples;
+    a.n_samples = o.n_samples;
+    a.n_fields = 1;
+    a.n_sweeps = o.n_samples;
+    a.burn_in = 0;
+    a.thin = 1;
+    a.chain0 = it.chain;
+    a.step0 = 0;
+    a.key0 = uint32_t(it.seed & 0xffffffffu);
+    a.key1 = uint32_t(it.seed >> 32);
+    if ((e = launch_global_any(H, a, st, nullptr)) != cudaSuccess) return cuda_fail(e);
+  }
+  return WF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void wf_batch_opts_default(wf_batch_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tau = 0.0;
+  o->tol = 1e-5;
+  o->eta = 0.5;
+  o->level_tol = 1e-2;
+  o->level_max = 64;
+  o->check = 4;
+  o->max_iter = 20000;
+  o->n_samples = 0;
+  o->large_streams = 8;
+}
+
+wf_status wf_batch_run(wf_batch_item* items, int32_t n_items, const wf_batch_opts* opts, wf_stream_t stream) {
+  wf_batch_opts o;
+  wf_batch_opts_default(&o);
+  if (opts) o = *opts;
+  if (n_items < 0 || (n_items > 0 && !items)) return WF_ERR_ARG;
+  if (!(o.tol >= 0.0) || !(o.eta > 0.0 && o.eta < 1.0) || o.level_max < 1 || o.check < 1 || o.max_iter < 1 ||
+      o.n_samples < 0 || o.large_streams < 1)
+    return WF_ERR_ARG;
+  if (n_items == 0) return WF_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int sizes[7] = {16, 32, 64, 128, 256, 512, 1024};
+  std::vector<std::vector<int>> cls(7);
+  std::vector<wf::BatchItem> dev_items(n_items);
+  for (int i = 0; i < n_items; ++i) {
+    const wf_batch_item& it = items[i];
+    if (!it.d || !it.Ndiag || !it.mask || !it.Pk) return WF_ERR_ARG;
+    if (!size_ok(it.H, it.W)) return WF_ERR_SHAPE;
+    if (o.n_samples > 0 && !it.out_samples) return WF_ERR_ARG;
+    int c = 0;
+    while (sizes[c] != it.H) ++c;
+    cls[c].push_back(i);
+    dev_items[i] = wf::BatchItem{it.d, it.Ndiag, it.mask, it.Pk, it.out_wf, it.out_samples, it.seed, it.chain, it.H};
+  }
+  // one allocation: items, order, results, queues, per-class CTA slots, per-stream large scratch
+  Carve cv;
+  const size_t o_items = cv.take<wf::BatchItem>(n_items), o_order = cv.take<int>(n_items),
+               o_res = cv.take<wf::BatchResult>(n_items), o_q = cv.take<int>(8);
+  size_t o_slot[4] = {0, 0, 0, 0};
+  int grid[4] = {0, 0, 0, 0};
+  for (int c = 0; c < 4; ++c) {
+    if (cls[c].empty()) continue;
+    cudaError_t e = batch_grid_any(sizes[c], int(cls[c].size()), &grid[c]);
+    if (e != cudaSuccess) return cuda_fail(e);
+    o_slot[c] = cv.take<char>(size_t(grid[c]) * size_t(batch_slot_any(sizes[c])));
+  }
+  int max_large = 0, n_large = 0;
+  for (int c = 4; c < 7; ++c)
+    if (!cls[c].empty()) {
+      max_large = sizes[c];
+      n_large += int(cls[c].size());
+    }
+  const int nls = n_large ? (o.large_streams < n_large ? o.large_streams : n_large) : 0;
+  LargeScratch lay{};
+  size_t o_large = 0;
+  if (nls) {
+    lay = large_layout(max_large);
+    o_large = cv.take<char>(lay.total * size_t(nls));
+  }
+  std::vector<int> order;
+  for (int c = 0; c < 7; ++c) order.insert(order.end(), cls[c].begin(), cls[c].end());
+  Scratch scr;
+  scr.st = st;
+  WF_CUDA(cudaMallocAsync(&scr.base, cv.off, st));
+  char* b = static_cast<char*>(scr.base);
+  auto* d_items = reinterpret_cast<wf::BatchItem*>(b + o_items);
+  auto* d_order = reinterpret_cast<int*>(b + o_order);
+  auto* d_res = reinterpret_cast<wf::BatchResult*>(b + o_res);
+  auto* d_q = reinterpret_cast<int*>(b + o_q);
+  WF_CUDA(cudaMemcpyAsync(d_items, dev_items.data(), n_items * sizeof(wf::BatchItem), cudaMemcpyHostToDevice, st));
+  WF_CUDA(cudaMemcpyAsync(d_order, order.data(), n_items * sizeof(int), cudaMemcpyHostToDevice, st));
+  WF_CUDA(cudaMemsetAsync(d_q, 0, 8 * sizeof(int), st));
+  WF_CUDA(cudaMemsetAsync(d_res, 0, n_items * sizeof(wf::BatchResult), st));
+
+  // fork: one stream per small size class, a pool for the large images
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> evs;
+  auto cleanup = [&]() {
+    for (auto e : evs) cudaEventDestroy(e);
+    for (auto s2 : side) cudaStreamDestroy(s2);
+  };
+  cudaEvent_t ready;
+  if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  evs.push_back(ready);
+  if (cudaEventRecord(ready, st) != cudaSuccess) { cleanup(); return cuda_fail(cudaGetLastError()); }
+  auto new_stream = [&](cudaStream_t* out) -> cudaError_t {
+    cudaError_t e = cudaStreamCreateWithFlags(out, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    side.push_back(*out);
+    return cudaStreamWaitEvent(*out, ready, 0);
+  };
+  wf_status fail = WF_OK;
+  int offset = 0;
+  for (int c = 0; c < 4 && fail == WF_OK; ++c) {
+    if (cls[c].empty()) continue;
+    cudaStream_t s2;
+    cudaError_t e = new_stream(&s2);
+    if (e != cudaSuccess) { fail = cuda_fail(e); break; }
+    wf::BatchArgs ba{};
+    ba.items = d_items;
+    ba.order = d_order + offset;
+    ba.n = int(cls[c].size());
+    ba.res = d_res;
+    ba.queue = d_q + c;
+    ba.scratch = b + o_slot[c];
+    ba.slot_bytes = batch_slot_any(sizes[c]);
+    ba.tau = o.tau;
+    ba.tol = o.tol;
+    ba.eta = o.eta;
+    ba.level_tol = o.level_tol;
+    ba.max_iter = o.max_iter;
+    ba.level_max = o.level_max;
+    ba.check = o.check;
+    ba.n_samples = o.n_samples;
+    if ((e = launch_batch_any(sizes[c], ba, s2)) != cudaSuccess) fail = cuda_fail(e);
+    offset += int(cls[c].size());
+  }
+  if (fail == WF_OK && nls) {
+    std::vector<cudaStream_t> pool(nls);
+    for (int k = 0; k < nls && fail == WF_OK; ++k) {
+      cudaError_t e = new_stream(&pool[k]);
+      if (e != cudaSuccess) fail = cuda_fail(e);
+    }
+    int j = 0;
+    for (int c = 4; c < 7 && fail == WF_OK; ++c)
+      for (int idx : cls[c]) {
+        LargeScratch L = lay;
+        L.base = b + o_large + size_t(j % nls) * lay.total;
+        const wf_status r = run_large_item(dev_items[idx], sizes[c], o, L, d_res + idx, pool[j % nls]);
+        if (r != WF_OK) { fail = r; break; }
+        ++j;
+      }
+  }
+  // join
+  for (auto s2 : side) {
+    cudaEvent_t done;
+    if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) continue;
+    evs.push_back(done);
+    cudaEventRecord(done, s2);
+    cudaStreamWaitEvent(st, done, 0);
+  }
+  std::vector<wf::BatchResult> hres(n_items);
+  cudaError_t e = cudaMemcpyAsync(hres.data(), d_res, n_items * sizeof(wf::BatchResult), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cleanup();
+  if (fail != WF_OK) return fail;
+  if (e != cudaSuccess) return cuda_fail(e);
+  wf_status first = WF_OK;
+  for (int i = 0; i < n_items; ++i) {
+    items[i].status = hres[i].status;
+    items[i].iters = hres[i].iters;
+    items[i].resid = hres[i].resid;
+    if (first == WF_OK && hres[i].status != WF_OK) first = wf_status(hres[i].status);
+  }
+  return first;
 }
 
 }  // extern "C"

@@ -419,11 +419,19 @@ WF_HD double p2_power(const float2 (&x)[N / 2], int lt, const float* __restrict_
   return acc;
 }
 
-// block-wide double sum; every thread gets the result. red must hold >= 33 doubles.
+// block-wide double sum; every thread gets the result. red must hold >= 33 doubles. Blocks of fewer than
+// 32 threads (power of two) reduce within their partial warp only.
 __device__ __forceinline__ double block_sum(double v, double* red) {
+  const int nt = blockDim.x;
+  if (nt < 32) {
+    const unsigned int mask = (1u << nt) - 1u;
+    for (int o = nt / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+    __syncthreads();
+    return v;
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (nt + 31) >> 5;
   if (lane == 0) red[warp] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -555,37 +563,26 @@ WF_HD void s_draw_parked(float2* cs, int lt, const float2* __restrict__ fg, uint
   }
 }
 
+// Sampler sweeps of one field (Alg. 1). On entry c holds the state s_0 as pixel rows, c[m] =
+// (s[2m], s[2m+1]) of row lt; S is the field's shared-memory buffer. Sweep i uses Philox step word
+// step0 + i; sample m (the state after sweep burn_in + (m+1) thin) goes to out + m*H*W when active.
+//
 // One sweep = four transforms, all run by the single forward-FFT block at the top of the loop (an
 // inverse transform is conj(FFT(conj(x)))), so the kernel holds one copy of the transform code:
 //   ROW_FWD: t (pixel space, after the t-draw) -> R2C rows -> store; load columns
 //   COL_FWD: column FFT -> s-draw on the parked modes -> conj
 //   COL_INV: conj -> store; load rows -> C2R pre-pass -> conj
 //   ROW_INV: conj -> s (pixel space) -> [write sample] -> t-draw on the staged row for the next sweep
-template <int N, int FPC>
-__global__ void __launch_bounds__(N * FPC, sample_min_ctas<N>()) k_sample(SampleArgs a) {
+template <int N>
+__device__ __forceinline__ void sample_sweeps(float2* S, int lt, float2 (&c)[N / 2], const float2* __restrict__ aq,
+                                              const float2* __restrict__ fg, float sqrt_tau, uint32_t step0,
+                                              uint32_t chain, uint32_t k0, uint32_t k1, int n_sweeps, int burn_in,
+                                              int thin, float* out, bool active) {
   using G = Geo<N>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int fld = threadIdx.x / N, lt = threadIdx.x % N;
-  const int ci = blockIdx.x * FPC + fld;
-  const bool active = ci < a.n_chains;
-  float2* S = reinterpret_cast<float2*>(smem_raw + fld * G::FIELD_BYTES);
   float* stg = reinterpret_cast<float*>(S);  // staged rows (between the row load and the next store)
   float2* cs = S;                            // parked column modes (between the column load and store)
-  if (a.sc->status != 0) return;  // uniform over the grid
-  const float sqrt_tau = a.sc->sqrt_tau;
-  const uint32_t chain = a.chain0 + uint32_t(ci);
-  float2 c[G::LR];
-
-  if (a.init_s != nullptr && active) {
-    const float2* src = reinterpret_cast<const float2*>(a.init_s + ci * a.init_stride + lt * G::W);
-#pragma unroll
-    for (int m = 0; m < G::LR; ++m) c[m] = WF_LDG(src + m);
-  } else {
-#pragma unroll
-    for (int m = 0; m < G::LR; ++m) c[m] = make_float2(0.f, 0.f);
-  }
   stage_row<N>(stg, lt, c);
-  t_draw_staged<N>(stg, lt, a.aq, sqrt_tau, a.step0, chain, a.key0, a.key1);
+  t_draw_staged<N>(stg, lt, aq, sqrt_tau, step0, chain, k0, k1);
   load_staged_row<N>(stg, lt, c);
 
   enum { ROW_FWD, COL_FWD, COL_INV, ROW_INV };
@@ -603,7 +600,7 @@ __global__ void __launch_bounds__(N * FPC, sample_min_ctas<N>()) k_sample(Sample
       phase = COL_FWD;
     } else if (phase == COL_FWD) {
       park_modes<N>(cs, lt, c);
-      s_draw_parked<N>(cs, lt, a.fg, a.step0 + uint32_t(done), chain, a.key0, a.key1);
+      s_draw_parked<N>(cs, lt, fg, step0 + uint32_t(done), chain, k0, k1);
       unpark_modes<N>(cs, lt, c);
       conj_all<G::LC>(c);
       phase = COL_INV;
@@ -621,18 +618,41 @@ __global__ void __launch_bounds__(N * FPC, sample_min_ctas<N>()) k_sample(Sample
       conj_all<G::LR>(c);  // c[m] = (s[2m], s[2m+1]) after sweep done + 1
       ++done;
       stage_row<N>(stg, lt, c);
-      if (done > a.burn_in && (done - a.burn_in) % a.thin == 0) {
-        const long long m = (done - a.burn_in) / a.thin - 1;
+      if (done > burn_in && (done - burn_in) % thin == 0) {
+        const long long m = (done - burn_in) / thin - 1;
         __syncthreads();
-        if (active) copy_out<N>(stg, lt, a.out + (ci * a.n_samples + m) * (long long)(G::H * G::W));
+        if (active) copy_out<N>(stg, lt, out + m * (long long)(G::H * G::W));
         __syncthreads();
       }
-      if (done == a.n_sweeps) break;
-      t_draw_staged<N>(stg, lt, a.aq, sqrt_tau, a.step0 + uint32_t(done), chain, a.key0, a.key1);
+      if (done == n_sweeps) break;
+      t_draw_staged<N>(stg, lt, aq, sqrt_tau, step0 + uint32_t(done), chain, k0, k1);
       load_staged_row<N>(stg, lt, c);
       phase = ROW_FWD;
     }
   }
+  __syncthreads();  // the buffer is reused by the caller
+}
+
+template <int N, int FPC>
+__global__ void __launch_bounds__(N * FPC, sample_min_ctas<N>()) k_sample(SampleArgs a) {
+  using G = Geo<N>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int fld = threadIdx.x / N, lt = threadIdx.x % N;
+  const int ci = blockIdx.x * FPC + fld;
+  const bool active = ci < a.n_chains;
+  float2* S = reinterpret_cast<float2*>(smem_raw + fld * G::FIELD_BYTES);
+  if (a.sc->status != 0) return;  // uniform over the grid
+  float2 c[G::LR];
+  if (a.init_s != nullptr && active) {
+    const float2* src = reinterpret_cast<const float2*>(a.init_s + ci * a.init_stride + lt * G::W);
+#pragma unroll
+    for (int m = 0; m < G::LR; ++m) c[m] = WF_LDG(src + m);
+  } else {
+#pragma unroll
+    for (int m = 0; m < G::LR; ++m) c[m] = make_float2(0.f, 0.f);
+  }
+  sample_sweeps<N>(S, lt, c, a.aq, a.fg, a.sc->sqrt_tau, a.step0, a.chain0 + uint32_t(ci), a.key0, a.key1,
+                   a.n_sweeps, a.burn_in, a.thin, a.out + ci * a.n_samples * (long long)(G::H * G::W), active);
 }
 
 struct SolveArgs {
@@ -652,6 +672,76 @@ struct SolveArgs {
   int check;
 };
 
+// The G -> 0 iteration with lambda-cooling for one field (one CTA of N threads). On entry c holds the
+// starting iterate as pixel rows; on exit the last iterate. Returns the wf_status (0 converged,
+// 5 not converged, 6 non-finite); it and rho receive the sweeps done and the last measured residual.
+template <int N>
+__device__ __forceinline__ int solve_sweeps(float2* S, double* red, int lt, float2 (&c)[N / 2],
+                                            const float2* __restrict__ dn, const float* __restrict__ Pk,
+                                            const Scalars& sc, const double* bnorm2, float2* prev, double tol,
+                                            double eta, double level_tol, int max_iter, int level_max, int check,
+                                            int& it, double& rho) {
+  using G = Geo<N>;
+  const double tau = sc.tau;
+  int lev = 0;
+  double lam = sc.lam0;
+  float ltau = float(lam * tau);
+  const int last_level = sc.n_levels - 1;
+  t_update_wf<N>(c, lt, dn, ltau);
+  row_forward<N>(c);
+  row_store_spec<N>(S, lt, c);
+  __syncthreads();
+
+  it = 0;
+  int k = 0;       // sweeps at the current level
+  int status = 1;  // 1 = running
+  rho = -1.0;
+  while (true) {
+    ++k;
+    ++it;
+    const bool cmp = (k % check == 0) && k >= 2;
+    const bool store = ((k + 1) % check == 0);
+    col_load<N>(S, lt, c);
+    __syncthreads();
+    fft<G::LC, false>(c);
+    double acc;
+    if (cmp && store) acc = s_update_wf<N, true, true>(c, lt, Pk, ltau, prev);
+    else if (cmp) acc = s_update_wf<N, true, false>(c, lt, Pk, ltau, prev);
+    else if (store) acc = s_update_wf<N, false, true>(c, lt, Pk, ltau, prev);
+    else acc = s_update_wf<N, false, false>(c, lt, Pk, ltau, prev);
+    if (cmp) {
+      const double tot = block_sum(acc, red) * double(G::H * G::W);
+      const double bn = bnorm2[lev];
+      const double r2 = bn > 0.0 ? tot / bn : tot;
+      rho = sqrt(r2);
+      if (!(r2 == r2) || r2 > 1e300) {
+        status = 6;  // non-finite residual
+      } else if (lev < last_level) {
+        if (rho < level_tol || k >= level_max) {
+          ++lev;
+          lam = level_lambda(sc, lev, eta);
+          ltau = float(lam * tau);
+          k = 0;
+        }
+      } else if (rho < tol) {
+        status = 0;
+      }
+    }
+    if (status == 1 && it >= max_iter) status = 5;  // not converged
+    col_inverse_store<N>(S, lt, c);
+    __syncthreads();
+    row_load_spec<N>(S, lt, c);
+    __syncthreads();
+    row_inverse<N>(c);
+    if (status != 1) break;
+    t_update_wf<N>(c, lt, dn, ltau);
+    row_forward<N>(c);
+    row_store_spec<N>(S, lt, c);
+    __syncthreads();
+  }
+  return status;
+}
+
 template <int N>
 __global__ void __launch_bounds__(N) k_solve(SolveArgs a) {
   using G = Geo<N>;
@@ -662,13 +752,7 @@ __global__ void __launch_bounds__(N) k_solve(SolveArgs a) {
   const int lt = threadIdx.x;
   const Scalars sc = *a.sc;
   if (sc.status != 0) return;
-  const double tau = sc.tau;
-  int lev = 0;
-  double lam = sc.lam0;
-  float ltau = float(lam * tau);
-  const int last_level = sc.n_levels - 1;
   float2 c[G::LR];
-
   if (a.init_s != nullptr) {
     const float2* src = reinterpret_cast<const float2*>(a.init_s + lt * G::W);
 #pragma unroll
@@ -677,57 +761,10 @@ __global__ void __launch_bounds__(N) k_solve(SolveArgs a) {
 #pragma unroll
     for (int m = 0; m < G::LR; ++m) c[m] = make_float2(0.f, 0.f);
   }
-  t_update_wf<N>(c, lt, a.dn, ltau);
-  row_forward<N>(c);
-  row_store_spec<N>(S, lt, c);
-  __syncthreads();
-
-  int it = 0, k = 0;  // sweeps in total / at the current level
-  int status = 1;     // 1 = running
+  int it = 0;
   double rho = -1.0;
-  while (true) {
-    ++k;
-    ++it;
-    const bool cmp = (k % a.check == 0) && k >= 2;
-    const bool store = ((k + 1) % a.check == 0);
-    col_load<N>(S, lt, c);
-    __syncthreads();
-    fft<G::LC, false>(c);
-    double acc;
-    if (cmp && store) acc = s_update_wf<N, true, true>(c, lt, a.Pk, ltau, a.prev);
-    else if (cmp) acc = s_update_wf<N, true, false>(c, lt, a.Pk, ltau, a.prev);
-    else if (store) acc = s_update_wf<N, false, true>(c, lt, a.Pk, ltau, a.prev);
-    else acc = s_update_wf<N, false, false>(c, lt, a.Pk, ltau, a.prev);
-    if (cmp) {
-      const double tot = block_sum(acc, red) * double(G::H * G::W);
-      const double bn = a.bnorm2[lev];
-      const double r2 = bn > 0.0 ? tot / bn : tot;
-      rho = sqrt(r2);
-      if (!(r2 == r2) || r2 > 1e300) {
-        status = 6;  // non-finite residual
-      } else if (lev < last_level) {
-        if (rho < a.level_tol || k >= a.level_max) {
-          ++lev;
-          lam = level_lambda(sc, lev, a.eta);
-          ltau = float(lam * tau);
-          k = 0;
-        }
-      } else if (rho < a.tol) {
-        status = 0;
-      }
-    }
-    if (status == 1 && it >= a.max_iter) status = 5;  // not converged
-    col_inverse_store<N>(S, lt, c);
-    __syncthreads();
-    row_load_spec<N>(S, lt, c);
-    __syncthreads();
-    row_inverse<N>(c);
-    if (status != 1) break;
-    t_update_wf<N>(c, lt, a.dn, ltau);
-    row_forward<N>(c);
-    row_store_spec<N>(S, lt, c);
-    __syncthreads();
-  }
+  const int status = solve_sweeps<N>(S, red, lt, c, a.dn, a.Pk, sc, a.bnorm2, a.prev, a.tol, a.eta, a.level_tol,
+                                     a.max_iter, a.level_max, a.check, it, rho);
   stage_row<N>(stg, lt, c);
   __syncthreads();
   copy_out<N>(stg, lt, a.out);
@@ -736,6 +773,22 @@ __global__ void __launch_bounds__(N) k_solve(SolveArgs a) {
     a.st->iters = it;
     a.st->resid = rho;
   }
+}
+
+// ||S N_lambda^-1 d||^2 of one cooling level (all N threads of the CTA; every thread gets the sum)
+template <int N>
+__device__ __forceinline__ double level_norm(float2* S, double* red, int lt, const float2* __restrict__ dn,
+                                             const float* __restrict__ Pk, float ltau) {
+  using G = Geo<N>;
+  float2 c[G::LR];
+  rhs_row<N>(c, lt, dn, ltau);
+  row_forward<N>(c);
+  row_store_spec<N>(S, lt, c);
+  __syncthreads();
+  col_load<N>(S, lt, c);
+  fft<G::LC, false>(c);
+  const double tot = block_sum(p2_power<N>(c, lt, Pk), red);
+  return tot / double(G::H * G::W);
 }
 
 // ||S N_lambda^-1 d||^2 for every cooling level (one CTA per level)
@@ -756,16 +809,8 @@ __global__ void __launch_bounds__(N) k_bnorm(BnormArgs a) {
   const int lev = blockIdx.x, lt = threadIdx.x;
   const Scalars sc = *a.sc;
   if (sc.status != 0 || lev >= sc.n_levels) return;
-  const double lam = level_lambda(sc, lev, a.eta);
-  float2 c[G::LR];
-  rhs_row<N>(c, lt, a.dn, float(lam * sc.tau));
-  row_forward<N>(c);
-  row_store_spec<N>(S, lt, c);
-  __syncthreads();
-  col_load<N>(S, lt, c);
-  fft<G::LC, false>(c);
-  const double tot = block_sum(p2_power<N>(c, lt, a.Pk), red);
-  if (lt == 0) a.bnorm2[lev] = tot / double(G::H * G::W);
+  const double v = level_norm<N>(S, red, lt, a.dn, a.Pk, float(level_lambda(sc, lev, a.eta) * sc.tau));
+  if (lt == 0) a.bnorm2[lev] = v;
 }
 
 }  // namespace wf

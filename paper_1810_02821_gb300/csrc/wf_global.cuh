@@ -427,13 +427,19 @@ __global__ void __launch_bounds__(128, 3) k_global(GlobalArgs a) {
   float2* buf = reinterpret_cast<float2*>(smem_raw);
   __shared__ double red[4];
   const Scalars sc = *a.sc;
-  if (sc.status != 0) return;
+  if (sc.status != 0) {
+    if (a.mode == 1 && blockIdx.x == 0 && threadIdx.x == 0) a.st->status = sc.status;
+    return;
+  }
   const unsigned int nb = gridDim.x;
   const int row_items = G::ROW_ITEMS * a.n_fields, col_items = G::COL_ITEMS * a.n_fields;
 
   auto rows = [&](int done, bool first, bool emit_only, float ltau) {
-    for (int it = blockIdx.x; it < row_items; it += nb)
-      row_item<N>(a, buf, it / G::ROW_ITEMS, (it % G::ROW_ITEMS) * G::RB, done, first, emit_only, ltau, sc);
+    for (int it = blockIdx.x; it < row_items; it += nb) {
+      const int f = it / G::ROW_ITEMS;
+      if (a.mode == 2 && f >= sc.n_levels) continue;  // level fields past the schedule
+      row_item<N>(a, buf, f, (it % G::ROW_ITEMS) * G::RB, done, first, emit_only, ltau, sc);
+    }
   };
   auto cols = [&](int done, float ltau, bool cmp, bool store) -> double {
     double acc = 0.0;
@@ -457,6 +463,7 @@ __global__ void __launch_bounds__(128, 3) k_global(GlobalArgs a) {
     if (!grid_barrier(a.bar, nb)) return;
     for (int it = blockIdx.x; it < col_items; it += nb) {
       const int f = it / G::COL_ITEMS;
+      if (f >= sc.n_levels) continue;
       const double s = block_sum_128(col_item<N>(a, buf, f, (it % G::COL_ITEMS) * G::CB, 0, 0.f, false, false), red);
       if (threadIdx.x == 0) atomicAdd(a.bnorm_out + f, s / double(G::H * G::W));
     }

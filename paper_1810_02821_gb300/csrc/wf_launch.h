@@ -5,6 +5,7 @@
 
 #include "wf_gibbs.cuh"
 #include "wf_global.cuh"
+#include "wf_batch.cuh"
 
 namespace wf {
 
@@ -23,6 +24,12 @@ cudaError_t launch_sample(const SampleArgs& a, cudaStream_t st, LaunchTimer* t);
 
 template <int N>
 cudaError_t launch_solve(const SolveArgs& a, const BnormArgs& b, cudaStream_t st, LaunchTimer* t);
+
+// batched persistent form for N <= 128: grid = min(items, resident CTAs), per-CTA scratch slots
+template <int N>
+cudaError_t launch_batch(const BatchArgs& b, int* grid_out, cudaStream_t st);
+template <int N>
+cudaError_t batch_grid(int n_items, int* grid_out);
 
 // large images (N >= 256): one cooperative launch of k_global<N> (all CTAs co-resident)
 template <int N>
@@ -61,9 +68,35 @@ cudaError_t launch_solve(const SolveArgs& a, const BnormArgs& b, cudaStream_t st
 }
 
 
+template <int N>
+cudaError_t batch_grid(int n_items, int* grid_out) {
+  const int smem = batch_smem_bytes<N>();
+  cudaError_t e = cudaFuncSetAttribute(k_batch<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<N>, N, smem)) != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  *grid_out = n_items < per_sm * sms ? n_items : per_sm * sms;
+  return cudaSuccess;
+}
+
+template <int N>
+cudaError_t launch_batch(const BatchArgs& b, int* grid_out, cudaStream_t st) {
+  int grid = 0;
+  cudaError_t e = batch_grid<N>(b.n, &grid);
+  if (e != cudaSuccess) return e;
+  if (grid_out) *grid_out = grid;
+  if (grid > 0) k_batch<N><<<grid, N, batch_smem_bytes<N>(), st>>>(b);
+  return cudaGetLastError();
+}
+
 #define WF_INSTANTIATE(N)                                                              \
   template cudaError_t launch_sample<N>(const SampleArgs&, cudaStream_t, LaunchTimer*); \
-  template cudaError_t launch_solve<N>(const SolveArgs&, const BnormArgs&, cudaStream_t, LaunchTimer*);
+  template cudaError_t launch_solve<N>(const SolveArgs&, const BnormArgs&, cudaStream_t, LaunchTimer*); \
+  template cudaError_t launch_batch<N>(const BatchArgs&, int*, cudaStream_t);                     \
+  template cudaError_t batch_grid<N>(int, int*);
 #endif
 
 #if defined(WF_LAUNCH_DEFINE_GLOBAL)

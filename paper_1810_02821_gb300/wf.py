@@ -38,6 +38,21 @@ class SampleOpts(ctypes.Structure):
                 ("thin", ctypes.c_int32), ("init_per_chain", ctypes.c_int32), ("init_s", ctypes.c_void_p)]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_void_p), ("Ndiag", ctypes.c_void_p), ("mask", ctypes.c_void_p), ("Pk", ctypes.c_void_p),
+                ("H", ctypes.c_int32), ("W", ctypes.c_int32), ("out_wf", ctypes.c_void_p),
+                ("out_samples", ctypes.c_void_p), ("seed", ctypes.c_uint64), ("chain", ctypes.c_uint32),
+                ("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("resid", ctypes.c_double)]
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("tol", ctypes.c_double), ("eta", ctypes.c_double),
+                ("level_tol", ctypes.c_double), ("level_max", ctypes.c_int32), ("check", ctypes.c_int32),
+                ("max_iter", ctypes.c_int32), ("n_samples", ctypes.c_int32), ("large_streams", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 _lib = None
 
 
@@ -71,6 +86,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.wf_last_cuda_error.restype = I32
     L.wf_abi_version.argtypes = []
     L.wf_abi_version.restype = I32
+    L.wf_batch_opts_default.argtypes = [ctypes.POINTER(BatchOpts)]
+    L.wf_batch_opts_default.restype = None
+    L.wf_batch_run.argtypes = [ctypes.POINTER(BatchItem), I32, ctypes.POINTER(BatchOpts), P]
+    L.wf_batch_run.restype = ctypes.c_int
     L.wf_set_kernel_timing.argtypes = [I32]
     L.wf_set_kernel_timing.restype = None
     L.wf_last_kernel_ms.argtypes = []
@@ -195,6 +214,57 @@ def wf_sample_ex(d, Ndiag, mask, Pk, seed: int, n_samples: int, *, n_chains: int
                         _stream_ptr(stream))
     _check(st, "wf_sample_ex")
     return out
+
+
+@dataclass
+class BatchImage:
+    """One image of a batch: CUDA tensors d, Ndiag [H][W] f32, mask [H][W] u8, Pk [H][W/2+1] f32."""
+    d: object
+    Ndiag: object
+    mask: object
+    Pk: object
+    seed: int = 0
+    chain: int = 0
+    out_wf: object = None       # [H][W] f32, allocated if None
+    out_samples: object = None  # [n_samples][H][W] f32, allocated if None and n_samples > 0
+    status: int = -1
+    iters: int = 0
+    resid: float = -1.0
+
+
+def wf_batch_run(images, *, n_samples: int = 0, tau: float = 0.0, tol: float = 1e-5, eta: float = 0.5,
+                 level_tol: float = 1e-2, level_max: int = 64, check: int = 4, max_iter: int = 20000,
+                 large_streams: int = 8, stream=None, allow_not_converged: bool = False):
+    """Wiener filter + ``n_samples`` posterior samples for every image (C call ``wf_batch_run``).
+
+    Fills ``out_wf``, ``out_samples``, ``status``, ``iters`` and ``resid`` of each ``BatchImage``.
+    """
+    import torch
+    L = load_library()
+    arr = (BatchItem * len(images))()
+    for i, im in enumerate(images):
+        H, W, pd, pn, pm, pp = _inputs(im.d, im.Ndiag, im.mask, im.Pk)
+        if im.out_wf is None:
+            im.out_wf = torch.empty((H, W), dtype=torch.float32, device=im.d.device)
+        if n_samples > 0 and im.out_samples is None:
+            im.out_samples = torch.empty((n_samples, H, W), dtype=torch.float32, device=im.d.device)
+        arr[i].d, arr[i].Ndiag, arr[i].mask, arr[i].Pk = pd.value, pn.value, pm.value, pp.value
+        arr[i].H, arr[i].W = H, W
+        arr[i].out_wf = _dev(im.out_wf, torch.float32, (H, W), "out_wf").value
+        arr[i].out_samples = (_dev(im.out_samples, torch.float32, (n_samples, H, W), "out_samples").value
+                              if n_samples > 0 else None)
+        arr[i].seed = int(im.seed) & 0xFFFFFFFFFFFFFFFF
+        arr[i].chain = int(im.chain)
+    o = BatchOpts()
+    L.wf_batch_opts_default(ctypes.byref(o))
+    o.tau, o.tol, o.eta, o.level_tol = float(tau), float(tol), float(eta), float(level_tol)
+    o.level_max, o.check, o.max_iter, o.n_samples = int(level_max), int(check), int(max_iter), int(n_samples)
+    o.large_streams = int(large_streams)
+    st = L.wf_batch_run(arr, len(images), ctypes.byref(o), _stream_ptr(stream))
+    for i, im in enumerate(images):
+        im.status, im.iters, im.resid = arr[i].status, arr[i].iters, arr[i].resid
+    _check(st, "wf_batch_run", ok=(WF_OK, 5) if allow_not_converged else (WF_OK,))
+    return images
 
 
 def wf_set_kernel_timing(enable: bool) -> None:
