@@ -10,10 +10,12 @@ It is deliberately plain and slow:
 * ``dft``      — unitary 2D DFT as products with explicit DFT matrices (Eq. 6, normalised, §2.1);
 * ``philox``   — Philox4x32-10 from its published definition (Salmon et al., SC'11) + Box–Muller;
 * ``messenger``— Algorithm 1 (sampler) and its G -> 0 variant with lambda-cooling (§2.2);
-* ``dense``    — the Wiener filter of Eq. 2-3 and the posterior covariance of Eq. 4 by dense solves.
+* ``dense``    — the Wiener filter of Eq. 2-3 and the posterior covariance of Eq. 4 by dense solves;
+* ``likelihood``— the Gaussian evidence of the data for a power-law P(k) and scaled noise, and its exact
+  gradient with respect to (amplitude, slope, noise scale), by dense algebra.
 
 Every function is pinned by ``tests/test_oracle_*.py`` against something other than itself
 (explicit DFT sums, numpy.fft, dense linear algebra, closed forms, curand's Philox, Monte-Carlo
 moments). No function is "parity unpinned".
 """
-from . import dft, philox, messenger, dense  # noqa: F401
+from . import dft, philox, messenger, dense, likelihood  # noqa: F401
