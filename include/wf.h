@@ -161,6 +161,38 @@ typedef struct {
 void wf_batch_opts_default(wf_batch_opts* o);
 wf_status wf_batch_run(wf_batch_item* items, int32_t n_items, const wf_batch_opts* opts, wf_stream_t stream);
 
+/*
+ * Weighted spectral power: out[f * nw + j] = sum_k w_j(k) |(U v_f)_k|^2 over the full spectrum, with
+ * v_f = a_f + sgn * b_f (b may be NULL), U the unitary 2D DFT, f < n_fields, j < nw <= 4.
+ * a, b: device float32 [n_fields][H][W]; w: device float32 [nw][H][W/2+1] (half-spectrum layout of Pk,
+ * symmetric under k -> -k); out: HOST double [n_fields * nw]. (Building block of the gradient below;
+ * S = U^dagger diag(P) U makes v^T S v the case w = P, §2.1 Eq. 7.)
+ */
+wf_status wf_spectral_power(const float* a, const float* b, float sgn, int32_t n_fields, const float* w, int32_t nw,
+                            int32_t H, int32_t W, double* out, wf_stream_t stream);
+
+/*
+ * Gaussian log-likelihood of the data (§2.1: Gaussian likelihood and Gaussian-random-field prior,
+ * A = I) for a power-law spectrum P(k) = amp (k/k0)^slope (P = 0 at k = 0, k in cycles/pixel as for Pk)
+ * and noise N = alpha * sigma2, and its gradient with respect to (amp, slope, alpha):
+ *   lnL = -1/2 d^T C^-1 d - 1/2 ln det C + const,  C = S + N over the observed pixels.
+ * out_quad (HOST, may be NULL): Q = -1/2 d^T C^-1 d, exact up to the solve tolerance.
+ * out_grad_quad (HOST double[3], may be NULL): dQ/dtheta = 1/2 x^T (dC/dtheta) x, x = C^-1 d, from one
+ *   Wiener solve (x = N^-1 (d - s_W) on observed pixels) and weighted spectral powers of x.
+ * out_grad (HOST double[3], may be NULL): d lnL / dtheta = dQ/dtheta - 1/2 tr(C^-1 dC/dtheta), the traces
+ *   estimated with n_probes Rademacher probes z (Philox stream 5 keyed by seed; counter = (pixel/4,
+ *   probe, 0, 5), sign from the top bit), each needing one more solve: C^-1 z = N^-1 (z - s_W(z)),
+ *   run to max(tol, 1e-5) (far below the Monte-Carlo error of the estimate).
+ * out_grad_var (HOST double[3], may be NULL): variance of the trace part of out_grad (sample variance
+ *   over probes / n_probes).
+ * out_wf (device [H][W], may be NULL): the Wiener filter of d.
+ * d, sigma2: device float32 [H][W]; mask: device uint8 [H][W]; params = {amp, slope, k0, alpha}.
+ */
+wf_status wf_loglike_grad(const float* d, const float* sigma2, const uint8_t* mask, int32_t H, int32_t W,
+                          const double* params, int32_t n_probes, uint64_t seed, double tol, double* out_quad,
+                          double* out_grad_quad, double* out_grad, double* out_grad_var, float* out_wf,
+                          wf_stream_t stream);
+
 /* 1 if (H, W) is supported by wf_solve / wf_sample, else 0. */
 int32_t wf_supported_size(int32_t H, int32_t W);
 

@@ -822,6 +822,251 @@ wf_status wf_batch_run(wf_batch_item* items, int32_t n_items, const wf_batch_opt
 }  // extern "C"
 
 // ---------------------------------------------------------------------------------------------
+// differentiation form: spectral powers and the log-likelihood gradient
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+// P = amp (k/k0)^slope, dP/damp = P/amp, dP/dslope = P ln(k/k0) on the half spectrum (FP64, rounded once),
+// k = sqrt((ky/H)^2 + (kx/W)^2) with ky folded to [-1/2, 1/2); and N = alpha * sigma2 per pixel.
+__global__ void k_psd(int H, int W, double amp, double slope, double k0, double alpha, const float* __restrict__ sigma2,
+                      float* P, float* dPa, float* dPn, float* Nd) {
+  const int WH = W / 2 + 1, nm = H * WH, n = H * W;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nm + n; i += gridDim.x * blockDim.x) {
+    if (i < nm) {
+      const int ky = i / WH, kx = i % WH;
+      const double fy = double(ky < H / 2 ? ky : ky - H) / H, fx = double(kx) / W;
+      const double k = sqrt(fy * fy + fx * fx);
+      double p = 0.0, dn = 0.0;
+      if (k > 0.0) {
+        p = amp * pow(k / k0, slope);
+        dn = p * log(k / k0);
+      }
+      P[i] = float(p);
+      dPa[i] = float(p / amp);
+      dPn[i] = float(dn);
+    } else {
+      const int j = i - nm;
+      Nd[j] = float(alpha * double(sigma2[j]));
+    }
+  }
+}
+
+// x = (v - s) / N on observed pixels (0 on missing) and the FP64 sums
+//   sums[0] += v x,  sums[1] += sigma2 x v,  sums[2] += sigma2 x^2   (observed pixels)
+__global__ void k_xres(int n, const float* __restrict__ v, const float* __restrict__ s, const float* __restrict__ Nd,
+                       const float* __restrict__ sigma2, const uint8_t* __restrict__ mask, float* x, double* sums) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    float xi = 0.0f;
+    if (mask[i] == 0) {
+      xi = (v[i] - s[i]) / Nd[i];
+      const double xd = xi, vd = v[i], s2 = sigma2[i];
+      a0 += vd * xd;
+      a1 += s2 * xd * vd;
+      a2 += s2 * xd * xd;
+    }
+    x[i] = xi;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(sums + 0, a0);
+    atomicAdd(sums + 1, a1);
+    atomicAdd(sums + 2, a2);
+  }
+}
+
+// Rademacher probe z (+-1 on observed pixels, 0 on missing): Philox stream 5, counter (i/4, probe, 0, 5),
+// word i mod 4, sign from its top bit.
+__global__ void k_rademacher(int n, uint32_t probe, uint32_t k0, uint32_t k1, const uint8_t* __restrict__ mask,
+                             float* z) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n / 4; g += gridDim.x * blockDim.x) {
+    const wf::u4 r = wf::philox4x32_10(wf::u4{uint32_t(g), probe, 0u, 5u}, k0, k1);
+    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int i = 4 * g + e;
+      z[i] = mask[i] ? 0.0f : ((w[e] >> 31) ? -1.0f : 1.0f);
+    }
+  }
+}
+
+// weighted spectral power into device memory dout[n_fields * nw]
+cudaError_t spectral_power_dev(const float* a, const float* b, float sgn, int n_fields, const float* w, int nw, int H,
+                               int W, double* dout, cudaStream_t st) {
+  if (size_on_chip(H)) {
+    wf::WpowerArgs p{a, b, sgn, n_fields, w, nw, dout};
+    switch (H) {
+      case 16: return wf::launch_wpower<16>(p, st);
+      case 32: return wf::launch_wpower<32>(p, st);
+      case 64: return wf::launch_wpower<64>(p, st);
+      case 128: return wf::launch_wpower<128>(p, st);
+    }
+    return cudaErrorInvalidValue;
+  }
+  // large images: mode 3 of the cooperative kernel (tables and twiddles in a scratch block)
+  const size_t nz = size_t(H) * (W / 2);
+  Carve cv;
+  const size_t o_sc = cv.take<wf::Scalars>(1), o_bar = cv.take<wf::GridBar>(1), o_tr = cv.take<float2>(W / 2),
+               o_tc = cv.take<float2>(H), o_tw = cv.take<float2>(W / 2), o_z = cv.take<float2>(nz * size_t(n_fields));
+  void* base = nullptr;
+  cudaError_t e = cudaMallocAsync(&base, cv.off, st);
+  if (e != cudaSuccess) return e;
+  char* bb = static_cast<char*>(base);
+  wf::Scalars sc{};
+  sc.status = 0;
+  sc.n_levels = 1;
+  sc.tau = 1.0;
+  e = cudaMemcpyAsync(bb + o_sc, &sc, sizeof(sc), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bb + o_bar, 0, sizeof(wf::GridBar), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dout, 0, sizeof(double) * size_t(n_fields) * nw, st);
+  if (e == cudaSuccess) {
+    k_twiddles<<<8, 256, 0, st>>>(H, W, reinterpret_cast<float2*>(bb + o_tr), reinterpret_cast<float2*>(bb + o_tc),
+                                  reinterpret_cast<float2*>(bb + o_tw));
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    wf::GlobalArgs g{};
+    g.Z = reinterpret_cast<float2*>(bb + o_z);
+    g.tw_row = reinterpret_cast<float2*>(bb + o_tr);
+    g.tw_col = reinterpret_cast<float2*>(bb + o_tc);
+    g.tw_real = reinterpret_cast<float2*>(bb + o_tw);
+    g.sc = reinterpret_cast<wf::Scalars*>(bb + o_sc);
+    g.bar = reinterpret_cast<wf::GridBar*>(bb + o_bar);
+    g.mode = 3;
+    g.n_fields = n_fields;
+    g.va = a;
+    g.vb = b;
+    g.vsign = sgn;
+    g.wts = w;
+    g.nw = nw;
+    g.wout = dout;
+    e = launch_global_any(H, g, st, nullptr);
+  }
+  const cudaError_t e2 = cudaFreeAsync(base, st);
+  return e != cudaSuccess ? e : e2;
+}
+
+}  // namespace
+
+extern "C" {
+
+wf_status wf_spectral_power(const float* a, const float* b, float sgn, int32_t n_fields, const float* w, int32_t nw,
+                            int32_t H, int32_t W, double* out, wf_stream_t stream) {
+  if (!a || !w || !out || n_fields < 0 || nw < 1 || nw > 4) return WF_ERR_ARG;
+  if (!size_ok(H, W)) return WF_ERR_SHAPE;
+  if (n_fields == 0) return WF_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Scratch scr;
+  scr.st = st;
+  WF_CUDA(cudaMallocAsync(&scr.base, sizeof(double) * size_t(n_fields) * nw, st));
+  auto* dout = static_cast<double*>(scr.base);
+  cudaError_t e = spectral_power_dev(a, b, sgn, n_fields, w, nw, H, W, dout, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  WF_CUDA(cudaMemcpyAsync(out, dout, sizeof(double) * size_t(n_fields) * nw, cudaMemcpyDeviceToHost, st));
+  WF_CUDA(cudaStreamSynchronize(st));
+  return WF_OK;
+}
+
+wf_status wf_loglike_grad(const float* d, const float* sigma2, const uint8_t* mask, int32_t H, int32_t W,
+                          const double* params, int32_t n_probes, uint64_t seed, double tol, double* out_quad,
+                          double* out_grad_quad, double* out_grad, double* out_grad_var, float* out_wf,
+                          wf_stream_t stream) {
+  if (!d || !sigma2 || !mask || !params) return WF_ERR_ARG;
+  if (!size_ok(H, W)) return WF_ERR_SHAPE;
+  const double amp = params[0], slope = params[1], k0 = params[2], alpha = params[3];
+  if (!(amp > 0.0) || !(k0 > 0.0) || !(alpha > 0.0) || !std::isfinite(slope) || n_probes < 0 || !(tol > 0.0))
+    return WF_ERR_ARG;
+  if (out_grad && n_probes < 1) return WF_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t n = size_t(H) * W, nm = size_t(H) * (W / 2 + 1);
+  Carve cv;
+  const size_t o_P = cv.take<float>(3 * nm), o_N = cv.take<float>(n), o_s = cv.take<float>(n), o_x = cv.take<float>(n),
+               o_z = cv.take<float>(n), o_w = cv.take<float>(n), o_sum = cv.take<double>(4),
+               o_pow = cv.take<double>(8);
+  Scratch scr;
+  scr.st = st;
+  WF_CUDA(cudaMallocAsync(&scr.base, cv.off, st));
+  char* b = static_cast<char*>(scr.base);
+  float* P = reinterpret_cast<float*>(b + o_P);
+  float* dPa = P + nm;
+  float* dPn = P + 2 * nm;
+  float* Nd = reinterpret_cast<float*>(b + o_N);
+  float* sW = out_wf ? out_wf : reinterpret_cast<float*>(b + o_s);
+  float* x = reinterpret_cast<float*>(b + o_x);
+  float* z = reinterpret_cast<float*>(b + o_z);
+  float* wv = reinterpret_cast<float*>(b + o_w);
+  double* sums = reinterpret_cast<double*>(b + o_sum);
+  double* pw = reinterpret_cast<double*>(b + o_pow);
+  const int nblk = int((nm + n + 255) / 256);
+  k_psd<<<nblk < 1024 ? nblk : 1024, 256, 0, st>>>(H, W, amp, slope, k0, alpha, sigma2, P, dPa, dPn, Nd);
+  WF_CUDA(cudaGetLastError());
+  wf_solve_opts so;
+  wf_solve_opts_default(&so);
+  so.tol = tol;
+  int32_t it = 0;
+  double rs = 0.0;
+  wf_status r = wf_solve_ex(d, Nd, mask, P, H, W, &so, sW, &it, &rs, stream);
+  if (r != WF_OK) return r;
+  // x = C^-1 d on observed pixels; Q = -1/2 d.x, dQ/dalpha = 1/2 sigma2 x.x
+  WF_CUDA(cudaMemsetAsync(sums, 0, 4 * sizeof(double), st));
+  const int xb = int((n + 255) / 256) < 1024 ? int((n + 255) / 256) : 1024;
+  k_xres<<<xb, 256, 0, st>>>(int(n), d, sW, Nd, sigma2, mask, x, sums);
+  WF_CUDA(cudaGetLastError());
+  // dQ/d(amp, slope) = 1/2 sum_k dP |U x|^2
+  cudaError_t e = spectral_power_dev(x, nullptr, 0.f, 1, dPa, 2, H, W, pw, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  double hs[4], hp[2];
+  WF_CUDA(cudaMemcpyAsync(hs, sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  WF_CUDA(cudaMemcpyAsync(hp, pw, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  WF_CUDA(cudaStreamSynchronize(st));
+  const double gq[3] = {0.5 * hp[0], 0.5 * hp[1], 0.5 * hs[2]};
+  if (out_quad) *out_quad = -0.5 * hs[0];
+  if (out_grad_quad)
+    for (int i = 0; i < 3; ++i) out_grad_quad[i] = gq[i];
+  if (!out_grad && !out_grad_var) return WF_OK;
+  // trace terms: t = z^T C^-1 dC z per probe, C^-1 z = N^-1 (z - s_W(z))
+  // the probe solves only need an error far below the Monte-Carlo error of the trace estimate
+  wf_solve_opts sp = so;
+  sp.tol = tol > 1e-5 ? tol : 1e-5;
+  double tsum[3] = {0, 0, 0}, tsq[3] = {0, 0, 0};
+  for (int j = 0; j < n_probes; ++j) {
+    k_rademacher<<<int((n / 4 + 255) / 256), 256, 0, st>>>(int(n), uint32_t(j), uint32_t(seed & 0xffffffffu),
+                                                          uint32_t(seed >> 32), mask, z);
+    WF_CUDA(cudaGetLastError());
+    r = wf_solve_ex(z, Nd, mask, P, H, W, &sp, wv, &it, &rs, stream);  // wv = s_W(z)
+    if (r != WF_OK) return r;
+    WF_CUDA(cudaMemsetAsync(sums, 0, 4 * sizeof(double), st));
+    k_xres<<<xb, 256, 0, st>>>(int(n), z, wv, Nd, sigma2, mask, x, sums);  // x = C^-1 z
+    WF_CUDA(cudaGetLastError());
+    // w^T dS z = (|U(w+z)|^2_dP - |U(w-z)|^2_dP) / 4
+    if ((e = spectral_power_dev(x, z, 1.f, 1, dPa, 2, H, W, pw, st)) != cudaSuccess) return cuda_fail(e);
+    if ((e = spectral_power_dev(x, z, -1.f, 1, dPa, 2, H, W, pw + 2, st)) != cudaSuccess) return cuda_fail(e);
+    double hq[4];
+    WF_CUDA(cudaMemcpyAsync(hs, sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    WF_CUDA(cudaMemcpyAsync(hq, pw, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    WF_CUDA(cudaStreamSynchronize(st));
+    const double t[3] = {0.25 * (hq[0] - hq[2]), 0.25 * (hq[1] - hq[3]), hs[1]};
+    for (int i = 0; i < 3; ++i) {
+      tsum[i] += t[i];
+      tsq[i] += t[i] * t[i];
+    }
+  }
+  for (int i = 0; i < 3; ++i) {
+    const double mean = tsum[i] / n_probes;
+    const double var = n_probes > 1 ? (tsq[i] - n_probes * mean * mean) / (n_probes - 1) : 0.0;
+    if (out_grad) out_grad[i] = gq[i] - 0.5 * mean;
+    if (out_grad_var) out_grad_var[i] = 0.25 * var / n_probes;
+  }
+  return WF_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
 // wf_sample_noalloc: the sampler with its scratch in a static device array instead of cudaMallocAsync,
 // for callers that cannot allocate device memory when they call (graph capture, real-time loops, fixed
 // memory budgets).

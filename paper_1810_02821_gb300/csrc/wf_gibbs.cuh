@@ -419,6 +419,37 @@ WF_HD double p2_power(const float2 (&x)[N / 2], int lt, const float* __restrict_
   return acc;
 }
 
+// sum over the full spectrum of w_j(k) |V_k|^2, j < nw <= 4, for the forward transform V held by this
+// thread; tables w_j = w + j*H*(W/2+1) on the half spectrum; edge columns separated into kx = 0 and W/2
+template <int N>
+WF_HD void wpower_acc(const float2 (&x)[N / 2], int lt, const float* __restrict__ w, int nw, double (&acc)[4]) {
+  using G = Geo<N>;
+  constexpr int WH = G::WH, TS = G::H * G::WH;
+  const int col = lt % G::LC, r = lt / G::LC;
+  auto sq = [](float a, float b) -> double { return double(a) * a + double(b) * b; };
+  for_mode_pairs<N>(r, [&](auto KP, auto KQ, int ky1, int ky2, auto ZG) {
+    constexpr int kp = decltype(KP)::value, kq = decltype(KQ)::value;
+    constexpr bool zero_group = decltype(ZG)::value != 0;
+    for (int j = 0; j < nw; ++j) {
+      const float* wt = w + j * TS;
+      double v;
+      if (col != 0) {
+        v = 2.0 * (WF_LDG(wt + ky1 * WH + col) * sq(x[kp].x, x[kp].y) +
+                   WF_LDG(wt + ky2 * WH + col) * sq(x[kq].x, x[kq].y));
+      } else if (zero_group) {
+        v = WF_LDG(wt + ky1 * WH) * sq(x[kp].x, 0.f) + WF_LDG(wt + ky1 * WH + G::W / 2) * sq(x[kp].y, 0.f) +
+            WF_LDG(wt + ky2 * WH) * sq(x[kq].x, 0.f) + WF_LDG(wt + ky2 * WH + G::W / 2) * sq(x[kq].y, 0.f);
+      } else {
+        const float2 y1 = x[kp], y2c = cconj(x[kq]);
+        const float2 A = cscale(cadd(y1, y2c), 0.5f);
+        const float2 B = cmul_mi(cscale(csub(y1, y2c), 0.5f));
+        v = 2.0 * (WF_LDG(wt + ky1 * WH) * sq(A.x, A.y) + WF_LDG(wt + ky1 * WH + G::W / 2) * sq(B.x, B.y));
+      }
+      acc[j] += v;
+    }
+  });
+}
+
 // block-wide double sum; every thread gets the result. red must hold >= 33 doubles. Blocks of fewer than
 // 32 threads (power of two) reduce within their partial warp only.
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -811,6 +842,49 @@ __global__ void __launch_bounds__(N) k_bnorm(BnormArgs a) {
   if (sc.status != 0 || lev >= sc.n_levels) return;
   const double v = level_norm<N>(S, red, lt, a.dn, a.Pk, float(level_lambda(sc, lev, a.eta) * sc.tau));
   if (lt == 0) a.bnorm2[lev] = v;
+}
+
+// Weighted spectral power of real fields v_f = a_f + sgn * b_f (b may be null): out[f*nw + j] =
+// sum_k w_j(k) |(U v_f)_k|^2 with U the unitary 2D DFT (one CTA per field).
+struct WpowerArgs {
+  const float* a;
+  const float* b;
+  float sgn;
+  int n_fields;
+  const float* w;
+  int nw;
+  double* out;
+};
+
+template <int N>
+__global__ void __launch_bounds__(N) k_wpower(WpowerArgs p) {
+  using G = Geo<N>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* S = reinterpret_cast<float2*>(smem_raw);
+  double* red = reinterpret_cast<double*>(smem_raw + G::FIELD_BYTES);
+  const int f = blockIdx.x, lt = threadIdx.x;
+  const long long base = (long long)f * G::H * G::W + (long long)lt * G::W;
+  float2 c[G::LR];
+#pragma unroll
+  for (int m = 0; m < G::LR; ++m) {
+    float2 v = reinterpret_cast<const float2*>(p.a + base)[m];
+    if (p.b) {
+      const float2 u = reinterpret_cast<const float2*>(p.b + base)[m];
+      v = make_float2(fmaf(p.sgn, u.x, v.x), fmaf(p.sgn, u.y, v.y));
+    }
+    c[m] = v;
+  }
+  row_forward<N>(c);
+  row_store_spec<N>(S, lt, c);
+  __syncthreads();
+  col_load<N>(S, lt, c);
+  fft<G::LC, false>(c);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  wpower_acc<N>(c, lt, p.w, p.nw, acc);
+  for (int j = 0; j < p.nw; ++j) {
+    const double tot = block_sum(acc[j], red);
+    if (lt == 0) p.out[f * p.nw + j] = tot / double(G::H * G::W);
+  }
 }
 
 }  // namespace wf

@@ -148,8 +148,15 @@ struct GlobalArgs {
   SolveStatus* st;
   double tol, eta, level_tol;
   int max_iter, level_max, check;
-  int mode;                // 0 sampler, 1 Wiener filter, 2 level norms (fields = levels)
+  int mode;                // 0 sampler, 1 Wiener filter, 2 level norms (fields = levels), 3 weighted power
   double* bnorm_out;       // mode 2: [n_fields]
+  // mode 3: fields v_f = va_f + vsign * vb_f, tables wts[nw][H][W/2+1], sums into wout[f*nw + j]
+  const float* va;
+  const float* vb;
+  float vsign;
+  const float* wts;
+  int nw;
+  double* wout;
 };
 
 // R2C post-processing / C2R pre-processing of one padded row vector (pairs k <-> LR - k), all threads of
@@ -201,6 +208,14 @@ __device__ void row_item(const GlobalArgs& a, float2* buf, int f, int y0, int do
       float2 v = make_float2(0.f, 0.f);
       if (a.mode == 0 && a.init_s != nullptr)
         v = reinterpret_cast<const float2*>(a.init_s + f * a.init_stride + (long long)(y0 + j) * G::W)[m];
+      if (a.mode == 3) {
+        const long long o = (long long)f * G::H * G::W + (long long)(y0 + j) * G::W;
+        v = reinterpret_cast<const float2*>(a.va + o)[m];
+        if (a.vb) {
+          const float2 u = reinterpret_cast<const float2*>(a.vb + o)[m];
+          v = make_float2(fmaf(a.vsign, u.x, v.x), fmaf(a.vsign, u.y, v.y));
+        }
+      }
       buf[j * G::VROW + padi(m)] = v;
     }
     __syncthreads();
@@ -236,10 +251,11 @@ __device__ void row_item(const GlobalArgs& a, float2* buf, int f, int y0, int do
     __syncthreads();
     return;
   }
-  // pixel-space update on 4-pixel groups (Philox group (y W + x)/4 in the sampler)
+  // pixel-space update on 4-pixel groups (Philox group (y W + x)/4 in the sampler); mode 3 transforms
+  // the field as loaded
   const uint32_t step = a.step0 + uint32_t(done);
   const uint32_t chain = a.chain0 + uint32_t(f);
-  for (int task = threadIdx.x; task < G::RB * (G::W / 4); task += nthr) {
+  for (int task = threadIdx.x; task < (a.mode == 3 ? 0 : G::RB * (G::W / 4)); task += nthr) {
     const int j = task / (G::W / 4), q = task % (G::W / 4);
     const int y = y0 + j;
     float2* v = buf + j * G::VROW;
@@ -410,6 +426,45 @@ __device__ double col_item(const GlobalArgs& a, float2* buf, int f, int c0, int 
   return acc;
 }
 
+// mode 3: weighted power sums of CB columns of field f into acc[j], j < nw
+template <int N>
+__device__ void col_wpower(const GlobalArgs& a, float2* buf, int f, int c0, double (&acc)[4]) {
+  using G = GGeo<N>;
+  constexpr int L = G::LR, H = G::H, WH = G::WH, TS = G::H * G::WH;
+  const float2* Zf = a.Z + (long long)f * H * L;
+  for (int e = threadIdx.x; e < G::CB * H; e += 128) {
+    const int j = e % G::CB, y = e / G::CB;
+    buf[j * G::VCOL + padi(y)] = __ldcg(Zf + (long long)y * L + c0 + j);
+  }
+  __syncthreads();
+  fft_smem<G::RC, G::CB, G::VCOL, false>(buf, a.tw_col);
+  auto sq = [](float p, float q) -> double { return double(p) * p + double(q) * q; };
+  for (int task = threadIdx.x; task < G::CB * (H / 2); task += 128) {
+    const int jc = task / (H / 2), j = task % (H / 2);
+    const int col = c0 + jc;
+    const int ky1 = j, ky2 = j == 0 ? H / 2 : H - j;
+    const float2* v = buf + jc * G::VCOL;
+    const float2 y1 = v[padi(ky1)], y2 = v[padi(ky2)];
+    for (int t = 0; t < a.nw; ++t) {
+      const float* wt = a.wts + t * TS;
+      double s;
+      if (col != 0) {
+        s = 2.0 * (__ldg(wt + ky1 * WH + col) * sq(y1.x, y1.y) + __ldg(wt + ky2 * WH + col) * sq(y2.x, y2.y));
+      } else if (j == 0) {
+        s = __ldg(wt + ky1 * WH) * sq(y1.x, 0.f) + __ldg(wt + ky1 * WH + G::W / 2) * sq(y1.y, 0.f) +
+            __ldg(wt + ky2 * WH) * sq(y2.x, 0.f) + __ldg(wt + ky2 * WH + G::W / 2) * sq(y2.y, 0.f);
+      } else {
+        const float2 y2c = cconj(y2);
+        const float2 A = cscale(cadd(y1, y2c), 0.5f);
+        const float2 B = cmul_mi(cscale(csub(y1, y2c), 0.5f));
+        s = 2.0 * (__ldg(wt + ky1 * WH) * sq(A.x, A.y) + __ldg(wt + ky1 * WH + G::W / 2) * sq(B.x, B.y));
+      }
+      acc[t] += s;
+    }
+  }
+  __syncthreads();
+}
+
 __device__ __forceinline__ double block_sum_128(double v, double* red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -455,6 +510,20 @@ __global__ void __launch_bounds__(128, 3) k_global(GlobalArgs a) {
       cols(i, 0.f, false, false);
       if (!grid_barrier(a.bar, nb)) return;
       rows(i + 1, false, i + 1 == a.n_sweeps, 0.f);
+    }
+    return;
+  }
+  if (a.mode == 3) {  // weighted power of given fields
+    rows(0, true, false, 0.f);
+    if (!grid_barrier(a.bar, nb)) return;
+    for (int it = blockIdx.x; it < col_items; it += nb) {
+      const int f = it / G::COL_ITEMS;
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      col_wpower<N>(a, buf, f, (it % G::COL_ITEMS) * G::CB, acc);
+      for (int t = 0; t < a.nw; ++t) {
+        const double s = block_sum_128(acc[t], red);
+        if (threadIdx.x == 0) atomicAdd(a.wout + f * a.nw + t, s / double(G::H * G::W));
+      }
     }
     return;
   }

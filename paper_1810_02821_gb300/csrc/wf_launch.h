@@ -28,6 +28,10 @@ cudaError_t launch_solve(const SolveArgs& a, const BnormArgs& b, cudaStream_t st
 // batched persistent form for N <= 128: grid = min(items, resident CTAs), per-CTA scratch slots
 template <int N>
 cudaError_t launch_batch(const BatchArgs& b, int* grid_out, cudaStream_t st);
+
+// weighted spectral power of real fields (N <= 128, one CTA per field)
+template <int N>
+cudaError_t launch_wpower(const WpowerArgs& p, cudaStream_t st);
 template <int N>
 cudaError_t batch_grid(int n_items, int* grid_out);
 
@@ -92,11 +96,21 @@ cudaError_t launch_batch(const BatchArgs& b, int* grid_out, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int N>
+cudaError_t launch_wpower(const WpowerArgs& p, cudaStream_t st) {
+  const int smem = Geo<N>::FIELD_BYTES + 33 * 8;
+  cudaError_t e = cudaFuncSetAttribute(k_wpower<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  if (p.n_fields > 0) k_wpower<N><<<p.n_fields, N, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
 #define WF_INSTANTIATE(N)                                                              \
   template cudaError_t launch_sample<N>(const SampleArgs&, cudaStream_t, LaunchTimer*); \
   template cudaError_t launch_solve<N>(const SolveArgs&, const BnormArgs&, cudaStream_t, LaunchTimer*); \
   template cudaError_t launch_batch<N>(const BatchArgs&, int*, cudaStream_t);                     \
-  template cudaError_t batch_grid<N>(int, int*);
+  template cudaError_t batch_grid<N>(int, int*);                                                   \
+  template cudaError_t launch_wpower<N>(const WpowerArgs&, cudaStream_t);
 #endif
 
 #if defined(WF_LAUNCH_DEFINE_GLOBAL)

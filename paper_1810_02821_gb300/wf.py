@@ -90,6 +90,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.wf_batch_opts_default.restype = None
     L.wf_batch_run.argtypes = [ctypes.POINTER(BatchItem), I32, ctypes.POINTER(BatchOpts), P]
     L.wf_batch_run.restype = ctypes.c_int
+    L.wf_spectral_power.argtypes = [P, P, ctypes.c_float, I32, P, I32, I32, I32, ctypes.POINTER(D), P]
+    L.wf_spectral_power.restype = ctypes.c_int
+    L.wf_loglike_grad.argtypes = [P, P, P, I32, I32, ctypes.POINTER(D), I32, U64, D, ctypes.POINTER(D),
+                                  ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D), P, P]
+    L.wf_loglike_grad.restype = ctypes.c_int
     L.wf_set_kernel_timing.argtypes = [I32]
     L.wf_set_kernel_timing.restype = None
     L.wf_last_kernel_ms.argtypes = []
@@ -265,6 +270,97 @@ def wf_batch_run(images, *, n_samples: int = 0, tau: float = 0.0, tol: float = 1
         im.status, im.iters, im.resid = arr[i].status, arr[i].iters, arr[i].resid
     _check(st, "wf_batch_run", ok=(WF_OK, 5) if allow_not_converged else (WF_OK,))
     return images
+
+
+def wf_spectral_power(a, w, b=None, sgn: float = 1.0, stream=None):
+    """sum_k w_j(k) |(U v_f)_k|^2 with v = a + sgn*b (C call ``wf_spectral_power``) -> numpy [F][nw].
+
+    a, b: CUDA float32 [F][H][W] (or [H][W]); w: CUDA float32 [nw][H][W/2+1] (or [H][W/2+1]).
+    """
+    import numpy as np
+    import torch
+    L = load_library()
+    a3 = a if a.dim() == 3 else a.unsqueeze(0)
+    w3 = w if w.dim() == 3 else w.unsqueeze(0)
+    F, H, W = a3.shape
+    nw = w3.shape[0]
+    pa = _dev(a3, torch.float32, (F, H, W), "a")
+    pb = _dev(b if b.dim() == 3 else b.unsqueeze(0), torch.float32, (F, H, W), "b") if b is not None else None
+    pw = _dev(w3, torch.float32, (nw, H, W // 2 + 1), "w")
+    out = (ctypes.c_double * (F * nw))()
+    st = L.wf_spectral_power(pa, pb, float(sgn), F, pw, nw, H, W, out, _stream_ptr(stream))
+    _check(st, "wf_spectral_power")
+    return np.array(out[:]).reshape(F, nw)
+
+
+@dataclass
+class LogLikGrad:
+    quad: float          # Q = -1/2 d^T C^-1 d
+    grad_quad: object    # numpy [3]: dQ/d(amp, slope, alpha)
+    grad: object         # numpy [3]: d lnL/d(amp, slope, alpha) (stochastic trace) or None
+    grad_var: object     # numpy [3]: variance of the trace estimate or None
+    wf: object           # torch [H][W]: Wiener filter of d
+
+
+def wf_loglike_grad(d, sigma2, mask, amp: float, slope: float, k0: float, alpha: float, *, n_probes: int = 16,
+                    seed: int = 0, tol: float = 1e-7, with_trace: bool = True, stream=None) -> LogLikGrad:
+    """Log-likelihood quadratic term and gradients w.r.t. (amp, slope, alpha) (C call ``wf_loglike_grad``)."""
+    import numpy as np
+    import torch
+    L = load_library()
+    H, W = d.shape
+    pd = _dev(d, torch.float32, (H, W), "d")
+    ps = _dev(sigma2, torch.float32, (H, W), "sigma2")
+    pm = _dev(mask, torch.uint8, (H, W), "mask")
+    prm = (ctypes.c_double * 4)(float(amp), float(slope), float(k0), float(alpha))
+    q = ctypes.c_double(0.0)
+    gq, g, gv = (ctypes.c_double * 3)(), (ctypes.c_double * 3)(), (ctypes.c_double * 3)()
+    out = torch.empty((H, W), dtype=torch.float32, device=d.device)
+    st = L.wf_loglike_grad(pd, ps, pm, H, W, prm, int(n_probes), int(seed) & 0xFFFFFFFFFFFFFFFF, float(tol),
+                           ctypes.byref(q), gq, g if with_trace else None, gv if with_trace else None,
+                           ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream))
+    _check(st, "wf_loglike_grad")
+    return LogLikGrad(q.value, np.array(gq[:]), np.array(g[:]) if with_trace else None,
+                      np.array(gv[:]) if with_trace else None, out)
+
+
+def _make_loglik_function():
+    import torch
+
+    class WienerLogLik(torch.autograd.Function):
+        """theta = (amp, slope, alpha) -> Q = -1/2 d^T C^-1 d (the data term of lnL).
+
+        The backward pass returns the gradient of the full log-likelihood, including the log-determinant
+        term through its stochastic trace (Hutchinson probes), so gradient-based inference sees d lnL /
+        d theta; the forward value omits the constant and the log-determinant. The forward call computes
+        and keeps (checkpoints) the Wiener solution and the gradient, so backward runs no new solve.
+        """
+
+        @staticmethod
+        def forward(ctx, theta, d, sigma2, mask, k0, n_probes, seed, tol):
+            t = theta.detach().double().cpu().numpy()
+            r = wf_loglike_grad(d, sigma2, mask, t[0], t[1], k0, t[2], n_probes=n_probes, seed=seed, tol=tol)
+            ctx.save_for_backward(torch.as_tensor(r.grad, dtype=theta.dtype, device=theta.device))
+            ctx.wf = r.wf
+            return torch.as_tensor(r.quad, dtype=theta.dtype, device=theta.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            (grad,) = ctx.saved_tensors
+            return g * grad, None, None, None, None, None, None, None
+
+    return WienerLogLik
+
+
+_WienerLogLik = None
+
+
+def wiener_loglik(theta, d, sigma2, mask, k0: float, n_probes: int = 16, seed: int = 0, tol: float = 1e-7):
+    """Differentiable data term of the Gaussian log-likelihood (see WienerLogLik)."""
+    global _WienerLogLik
+    if _WienerLogLik is None:
+        _WienerLogLik = _make_loglik_function()
+    return _WienerLogLik.apply(theta, d, sigma2, mask, k0, n_probes, seed, tol)
 
 
 def wf_set_kernel_timing(enable: bool) -> None:
