@@ -64,7 +64,7 @@ struct Geo {
   static constexpr int LR = N / 2;  // complex length of a row transform
   static constexpr int LC = N / 2;  // half length of a column (radix-2 split)
   static constexpr int SP = LR + 1;  // float2 stride of a spectrum row in shared memory
-  static constexpr int STG = W + 1;  // float stride of a staged real row
+  static constexpr int STG = W + 2;  // float stride of a staged real row (= the spectrum row's span)
   static constexpr int SPEC_BYTES = H * SP * 8;
   static constexpr int STG_BYTES = H * STG * 4;
   static constexpr int FIELD_BYTES = ((SPEC_BYTES > STG_BYTES ? SPEC_BYTES : STG_BYTES) + 15) / 16 * 16;
@@ -222,6 +222,15 @@ WF_HD void col_store_inv(float2* S, int lt, const float2 (&x)[N / 2]) {
   }
 }
 
+// order shared-memory accesses between the edge thread and its helpers (threads of columns 0 .. LC/2-1
+// of the same role): they always share a warp
+template <int N>
+WF_HD void sync_field() {
+#if defined(__CUDA_ARCH__)
+  __syncwarp();
+#endif
+}
+
 template <int L>
 WF_HD void conj_all(float2 (&x)[L]) {
 #pragma unroll
@@ -269,22 +278,24 @@ WF_HD void for_mode_pairs(int r, F&& f) {
 }
 
 // Staging of one real field (row y held as c[m] = (s[2m], s[2m+1])) and a coalesced copy to global.
+// A staged row occupies exactly the floats of spectrum row y, so a thread's staged row and its
+// spectrum row are the same memory.
 template <int N>
 WF_HD void stage_row(float* stg, int y, const float2 (&c)[N / 2]) {
   using G = Geo<N>;
+  float2* r = reinterpret_cast<float2*>(stg) + y * G::SP;
 #pragma unroll
-  for (int m = 0; m < G::LR; ++m) {
-    stg[y * G::STG + 2 * m] = c[m].x;
-    stg[y * G::STG + 2 * m + 1] = c[m].y;
-  }
+  for (int m = 0; m < G::LR; ++m) r[m] = c[m];
 }
 template <int N>
 WF_HD void copy_out(const float* stg, int lt, float* __restrict__ out) {
   using G = Geo<N>;
+  const float2* s2 = reinterpret_cast<const float2*>(stg);
+  float2* o2 = reinterpret_cast<float2*>(out);
 #pragma unroll 4
-  for (int e = lt; e < G::H * G::W; e += N) {
-    const int y = e / G::W, x = e % G::W;
-    out[e] = stg[y * G::STG + x];
+  for (int e = lt; e < G::H * G::LR; e += N) {
+    const int y = e / G::LR, m = e % G::LR;
+    o2[e] = s2[y * G::SP + m];
   }
 }
 
@@ -498,6 +509,11 @@ struct SampleArgs {
 
 // CTAs per SM the sample kernel is compiled for (register budget 65536 / (threads * CTAs)):
 // 128^2 fields are limited to three per SM by shared memory (66.5 KB each).
+// Philox calls in flight in the rolled pointwise-draw loops (the field registers are dead there)
+#ifndef WF_RNG_UNROLL
+#define WF_RNG_UNROLL 4
+#endif
+constexpr int kRngUnroll = WF_RNG_UNROLL;
 #ifndef WF_SAMPLE_MIN_CTAS_128
 #define WF_SAMPLE_MIN_CTAS_128 3
 #endif
@@ -516,88 +532,121 @@ template <int N>
 WF_HD void t_draw_staged(float* stg, int y, const float2* __restrict__ aq, float sqrt_tau, uint32_t step,
                          uint32_t chain, uint32_t k0, uint32_t k1) {
   using G = Geo<N>;
-  float* row = stg + y * G::STG;
-#pragma unroll 2
+  float2* row = reinterpret_cast<float2*>(stg) + y * G::SP;  // (s[2m], s[2m+1]) pairs
+#pragma unroll (kRngUnroll)
   for (int q = 0; q < G::W / 4; ++q) {
     float z[4];
     normals4(uint32_t(y * (G::W / 4) + q), step, chain, 0u, k0, k1, z);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int x = 4 * q + e;
-      const float2 co = WF_LDG(aq + x * G::H + y);
-      row[x] = fmaf(co.y, fmaf(co.y, row[x], sqrt_tau * z[e]), co.x);
-    }
+    float2 p0 = row[2 * q], p1 = row[2 * q + 1];
+    const float2 c0 = WF_LDG(aq + (4 * q) * G::H + y), c1 = WF_LDG(aq + (4 * q + 1) * G::H + y);
+    const float2 c2 = WF_LDG(aq + (4 * q + 2) * G::H + y), c3 = WF_LDG(aq + (4 * q + 3) * G::H + y);
+    p0.x = fmaf(c0.y, fmaf(c0.y, p0.x, sqrt_tau * z[0]), c0.x);
+    p0.y = fmaf(c1.y, fmaf(c1.y, p0.y, sqrt_tau * z[1]), c1.x);
+    p1.x = fmaf(c2.y, fmaf(c2.y, p1.x, sqrt_tau * z[2]), c2.x);
+    p1.y = fmaf(c3.y, fmaf(c3.y, p1.y, sqrt_tau * z[3]), c3.x);
+    row[2 * q] = p0;
+    row[2 * q + 1] = p1;
   }
 }
 
 template <int N>
 WF_HD void load_staged_row(const float* stg, int y, float2 (&c)[N / 2]) {
   using G = Geo<N>;
+  const float2* r = reinterpret_cast<const float2*>(stg) + y * G::SP;
 #pragma unroll
-  for (int m = 0; m < G::LR; ++m) c[m] = make_float2(stg[y * G::STG + 2 * m], stg[y * G::STG + 2 * m + 1]);
+  for (int m = 0; m < G::LR; ++m) c[m] = r[m];
 }
 
-// the modes of a column thread parked at cs[k * N + lt] (float2), k = register index
+// The modes of column thread (col, r) are parked in the slots it stores to after the inverse column
+// transform: register k at cs[(k + r*LC) * SP + col] (rows r*LC .. r*LC+LC-1 of its column).
+template <int N>
+WF_HD int park_index(int lt, int k) {
+  using G = Geo<N>;
+  return (k + (lt / G::LC) * G::LC) * G::SP + lt % G::LC;
+}
 template <int N>
 WF_HD void park_modes(float2* cs, int lt, const float2 (&x)[N / 2]) {
 #pragma unroll
-  for (int k = 0; k < N / 2; ++k) cs[k * N + lt] = x[k];
+  for (int k = 0; k < N / 2; ++k) cs[park_index<N>(lt, k)] = x[k];
 }
 template <int N>
 WF_HD void unpark_modes(const float2* cs, int lt, float2 (&x)[N / 2]) {
 #pragma unroll
-  for (int k = 0; k < N / 2; ++k) x[k] = cs[k * N + lt];
+  for (int k = 0; k < N / 2; ++k) x[k] = cs[park_index<N>(lt, k)];
 }
 
 // s-draw on parked modes: s_hat = f t_hat + g zeta, table fg[ky*WH + kx] = (f / n, g / sqrt(2 n)).
 // Mode pair kp of role r: registers kp and kq with ky1 = 2kp + r and its mirror ky2 (for_mode_pairs);
-// Philox stream 1, group col*H/2 + ky1. The packed edge column (col 0: kx = 0 as A and kx = W/2 as B in
-// Y = A + i B, both Hermitian in ky) separates A and B before the update.
+// Philox stream 1, group col*H/2 + ky1.
 template <int N>
-WF_HD void s_draw_parked(float2* cs, int lt, const float2* __restrict__ fg, uint32_t step, uint32_t chain,
-                         uint32_t k0, uint32_t k1) {
+WF_HD void mode_pair(int r, int kp, int& kq, int& ky1, int& ky2) {
+  using G = Geo<N>;
+  kq = r == 0 ? (kp == 0 ? G::LC / 2 : G::LC - kp) : G::LC - 1 - kp;
+  ky1 = 2 * kp + r;
+  ky2 = r == 0 ? (kp == 0 ? G::H / 2 : G::H - 2 * kp) : G::H - 2 * kp - 1;
+}
+
+// interior columns (col > 0): every thread but the edge thread updates its own parked modes
+template <int N>
+WF_HD void s_draw_interior(float2* cs, int lt, const float2* __restrict__ fg, uint32_t step, uint32_t chain,
+                           uint32_t k0, uint32_t k1) {
   using G = Geo<N>;
   constexpr int WH = G::WH, LC = G::LC, H = G::H;
   const int col = lt % LC, r = lt / LC;
-#pragma unroll 2
+  if (col == 0) return;
+#pragma unroll (kRngUnroll)
   for (int kp = 0; kp < LC / 2; ++kp) {
-    const int kq = r == 0 ? (kp == 0 ? LC / 2 : LC - kp) : LC - 1 - kp;
-    const int ky1 = 2 * kp + r;
-    const int ky2 = r == 0 ? (kp == 0 ? H / 2 : H - 2 * kp) : H - 2 * kp - 1;
+    int kq, ky1, ky2;
+    mode_pair<N>(r, kp, kq, ky1, ky2);
     float z[4];
     normals4(uint32_t(col * (H / 2) + ky1), step, chain, 1u, k0, k1, z);
-    float2 y1 = cs[kp * N + lt], y2 = cs[kq * N + lt];
-    if (col != 0) {
-      const float2 m1 = WF_LDG(fg + ky1 * WH + col), m2 = WF_LDG(fg + ky2 * WH + col);
-      y1 = make_float2(fmaf(m1.x, y1.x, m1.y * z[0]), fmaf(m1.x, y1.y, m1.y * z[1]));
-      y2 = make_float2(fmaf(m2.x, y2.x, m2.y * z[2]), fmaf(m2.x, y2.y, m2.y * z[3]));
-    } else {
-      const float2 a1 = WF_LDG(fg + ky1 * WH), b1 = WF_LDG(fg + ky1 * WH + G::W / 2);
-      if (ky1 == 0) {
-        // group 0: the four self-conjugate modes, real with variance g^2
-        const float2 a2 = WF_LDG(fg + ky2 * WH), b2 = WF_LDG(fg + ky2 * WH + G::W / 2);
-        constexpr float R2 = 1.41421356237309505f;
-        y1 = make_float2(fmaf(a1.x, y1.x, R2 * a1.y * z[0]), fmaf(b1.x, y1.y, R2 * b1.y * z[2]));
-        y2 = make_float2(fmaf(a2.x, y2.x, R2 * a2.y * z[1]), fmaf(b2.x, y2.y, R2 * b2.y * z[3]));
-      } else {
-        const float2 y2c = cconj(y2);
-        const float2 A = cscale(cadd(y1, y2c), 0.5f);
-        const float2 B = cmul_mi(cscale(csub(y1, y2c), 0.5f));
-        const float2 Ap = make_float2(fmaf(a1.x, A.x, a1.y * z[0]), fmaf(a1.x, A.y, a1.y * z[1]));
-        const float2 Bp = make_float2(fmaf(b1.x, B.x, b1.y * z[2]), fmaf(b1.x, B.y, b1.y * z[3]));
-        y1 = cadd(Ap, cmul_i(Bp));
-        y2 = cadd(cconj(Ap), cmul_i(cconj(Bp)));
-      }
-    }
-    cs[kp * N + lt] = y1;
-    cs[kq * N + lt] = y2;
+    const int i1 = park_index<N>(lt, kp), i2 = park_index<N>(lt, kq);
+    float2 y1 = cs[i1], y2 = cs[i2];
+    const float2 m1 = WF_LDG(fg + ky1 * WH + col), m2 = WF_LDG(fg + ky2 * WH + col);
+    y1 = make_float2(fmaf(m1.x, y1.x, m1.y * z[0]), fmaf(m1.x, y1.y, m1.y * z[1]));
+    y2 = make_float2(fmaf(m2.x, y2.x, m2.y * z[2]), fmaf(m2.x, y2.y, m2.y * z[3]));
+    cs[i1] = y1;
+    cs[i2] = y2;
   }
 }
 
-// Sampler sweeps of one field (Alg. 1). On entry c holds the state s_0 as pixel rows, c[m] =
-// (s[2m], s[2m+1]) of row lt; S is the field's shared-memory buffer. Sweep i uses Philox step word
-// step0 + i; sample m (the state after sweep burn_in + (m+1) thin) goes to out + m*H*W when active.
-//
+// the packed edge column (col 0: kx = 0 as A and kx = W/2 as B in Y = A + i B, both Hermitian in ky):
+// its LC/2 mode pairs of role r are shared out to the threads of columns 0 .. LC/2-1 of that role
+// (one pair each), which read and write the edge thread's parked slots. Group ky1 (col 0) feeds the pair.
+template <int N>
+WF_HD void s_draw_edge(float2* cs, int lt, const float2* __restrict__ fg, uint32_t step, uint32_t chain,
+                       uint32_t k0, uint32_t k1) {
+  using G = Geo<N>;
+  constexpr int WH = G::WH, LC = G::LC;
+  const int kp = lt % LC, r = lt / LC;
+  if (kp >= LC / 2) return;
+  const int edge = r * LC;  // thread index of the edge thread of this role
+  int kq, ky1, ky2;
+  mode_pair<N>(r, kp, kq, ky1, ky2);
+  float z[4];
+  normals4(uint32_t(ky1), step, chain, 1u, k0, k1, z);
+  const int i1 = park_index<N>(edge, kp), i2 = park_index<N>(edge, kq);
+  float2 y1 = cs[i1], y2 = cs[i2];
+  const float2 a1 = WF_LDG(fg + ky1 * WH), b1 = WF_LDG(fg + ky1 * WH + G::W / 2);
+  if (ky1 == 0) {
+    // group 0: the four self-conjugate modes, real with variance g^2
+    const float2 a2 = WF_LDG(fg + ky2 * WH), b2 = WF_LDG(fg + ky2 * WH + G::W / 2);
+    constexpr float R2 = 1.41421356237309505f;
+    y1 = make_float2(fmaf(a1.x, y1.x, R2 * a1.y * z[0]), fmaf(b1.x, y1.y, R2 * b1.y * z[2]));
+    y2 = make_float2(fmaf(a2.x, y2.x, R2 * a2.y * z[1]), fmaf(b2.x, y2.y, R2 * b2.y * z[3]));
+  } else {
+    const float2 y2c = cconj(y2);
+    const float2 A = cscale(cadd(y1, y2c), 0.5f);
+    const float2 B = cmul_mi(cscale(csub(y1, y2c), 0.5f));
+    const float2 Ap = make_float2(fmaf(a1.x, A.x, a1.y * z[0]), fmaf(a1.x, A.y, a1.y * z[1]));
+    const float2 Bp = make_float2(fmaf(b1.x, B.x, b1.y * z[2]), fmaf(b1.x, B.y, b1.y * z[3]));
+    y1 = cadd(Ap, cmul_i(Bp));
+    y2 = cadd(cconj(Ap), cmul_i(cconj(Bp)));
+  }
+  cs[i1] = y1;
+  cs[i2] = y2;
+}
+
 // One sweep = four transforms, all run by the single forward-FFT block at the top of the loop (an
 // inverse transform is conj(FFT(conj(x)))), so the kernel holds one copy of the transform code:
 //   ROW_FWD: t (pixel space, after the t-draw) -> R2C rows -> store; load columns
@@ -623,22 +672,23 @@ __device__ __forceinline__ void sample_sweeps(float2* S, int lt, float2 (&c)[N /
     fft<G::LR, false>(c);
     if (phase == ROW_FWD) {
       r2c_post_all<G::LR>(c, std::make_integer_sequence<int, G::LR>{});
-      __syncthreads();  // every staged row consumed
-      row_store_spec<N>(S, lt, c);
+      row_store_spec<N>(S, lt, c);  // over this thread's own staged row
       __syncthreads();
       col_load<N>(S, lt, c);
       __syncthreads();  // buffer free for the parked modes
       phase = COL_FWD;
     } else if (phase == COL_FWD) {
       park_modes<N>(cs, lt, c);
-      s_draw_parked<N>(cs, lt, fg, step0 + uint32_t(done), chain, k0, k1);
+      s_draw_interior<N>(cs, lt, fg, step0 + uint32_t(done), chain, k0, k1);
+      sync_field<N>();  // the edge thread's parked modes are visible to its helpers
+      s_draw_edge<N>(cs, lt, fg, step0 + uint32_t(done), chain, k0, k1);
+      sync_field<N>();
       unpark_modes<N>(cs, lt, c);
       conj_all<G::LC>(c);
       phase = COL_INV;
     } else if (phase == COL_INV) {
       conj_all<G::LC>(c);
-      __syncthreads();  // every parked mode reloaded
-      col_store_inv<N>(S, lt, c);
+      col_store_inv<N>(S, lt, c);  // over this thread's own parked slots
       __syncthreads();
       row_load_spec<N>(S, lt, c);
       __syncthreads();
