@@ -65,6 +65,27 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def replica_chain_offset(rank: int, chains: int) -> int:
+    """Replicas only: rank r runs chains [r*chains, (r+1)*chains) (Philox chain words), no collective."""
+    return rank * chains
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The largest of the ranks' values (timed-region length): every rank gets it (all-reduce MAX)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_throughput(units_per_rank: int, world: int, max_ms: float) -> float:
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    return units_per_rank * world / (max_ms / 1e3)
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     for f in sorted(glob.glob(os.path.join(ROOT, "paper_1810_02821_gb300", "csrc", "*"))):
@@ -220,7 +241,7 @@ def main():
     d, Nd, mk, Pk = [x.to(dev) for x in host]
     out = torch.empty((N_CHAINS, N_SAMPLES, H, W), dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
-    chain0 = rank * N_CHAINS
+    chain0 = replica_chain_offset(rank, N_CHAINS)
 
     def step(seed, o=out):
         return wf.wf_sample_ex(d, Nd, mk, Pk, seed=seed, n_samples=N_SAMPLES, n_chains=N_CHAINS,
@@ -248,13 +269,8 @@ def main():
             step_ms.append(e0.elapsed_time(e1))
             kern_ms.append(wf.wf_last_kernel_ms())
         barrier()
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    units = N_CHAINS * N_SAMPLES * a.steps * world
-    value = units / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
+    value = aggregate_throughput(N_CHAINS * N_SAMPLES * a.steps, world, total_ms)
 
     # end to end through the same call: pinned host inputs -> device -> samples -> pinned host
     e2e = None
@@ -274,12 +290,8 @@ def main():
             hout.copy_(out, non_blocking=True)
         e1.record(stream)
         e1.synchronize()
-        ems = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ems], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": N_CHAINS * N_SAMPLES * e2e_steps * world / (ems / 1e3), "unit": UNIT,
+        ems = max_over_ranks(e0.elapsed_time(e1), world, dev)
+        e2e = {"value": aggregate_throughput(N_CHAINS * N_SAMPLES * e2e_steps, world, ems), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps}
         del hout
 
