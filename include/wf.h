@@ -15,7 +15,7 @@
  *   - mask: uint8 [H][W], nonzero = missing pixel.
  *   - Pk: float32 [H][W/2+1], the half spectrum (ky in FFT order 0..H-1, kx = 0..W/2): P_k is the
  *     variance of the unitary 2D DFT coefficient of s at mode k, i.e. <|(U s)_k|^2> with
- *     U = F / sqrt(H W) and F the transform of Eq. 6 (see "normalisation" in the design notes).
+ *     U = F / sqrt(H W) and F the transform of Eq. 6 (the paper's unnormalised F has variance H W P_k).
  *     P_k >= 0; P_k must be symmetric under k -> -k for the edge columns kx = 0 and kx = W/2.
  *   - tau: messenger variance T = tau I (Alg. 1 definitions). tau <= 0 selects the paper's choice,
  *     the minimum observed Ndiag (max_k P_k if every pixel is missing). A tau above the minimum observed
@@ -63,9 +63,13 @@ typedef struct {
   double level_tol;  /* a level lambda > 1 ends when its own relative residual < level_tol ... */
   int32_t level_max; /* ... or after level_max sweeps at that level */
   int32_t check;     /* residual measured every `check` sweeps (>= 1) */
-  int32_t max_iter;  /* total sweep budget; WF_ERR_NOT_CONVERGED when exhausted */
-  int32_t reserved;
-  const float* init_s; /* device [H][W] starting iterate, or NULL for zero */
+  int32_t max_iter;  /* sweep budget of each messenger solve; WF_ERR_NOT_CONVERGED when exhausted */
+  int32_t refine;    /* 0: plain FP32 iteration (its residual estimate floors near 1e-6); k > 0: up to k
+                        mixed-precision refinement steps: the residual r = N^-1 (d - s) - S^-1 s and the
+                        stopping test are evaluated in FP64 on the GPU and each step adds the FP32 messenger
+                        solution e of (S^-1 + N^-1) e = r; resid_out is then the FP64 residual */
+  const float* init_s; /* device [H][W] starting iterate, or NULL for zero (sizes <= 128 only) */
+  double refine_tol; /* relative residual target of each correction solve */
 } wf_solve_opts;
 
 /* Options of the sampler (wf_sample_ex). Fill with wf_sample_opts_default first. */
@@ -102,8 +106,14 @@ wf_status wf_solve_ex(const float* d, const float* Ndiag, const uint8_t* mask, c
 /*
  * Wiener-posterior samples (Eq. 4) by Algorithm 1: one chain from s_0 = 0, no burn-in, thin 1, chain
  * word 0, first step word 0. out: device float32 [n_samples][H][W]; sample m is the state after sweep
- * m + 1. G(0,1) variates come from Philox4x32-10 keyed by `seed` (see the noise layout in the design
- * notes), so the draws are reproducible and identical to the reference implementation's.
+ * m + 1. G(0,1) variates come from Philox4x32-10 with key (seed low word, seed high word) and counter
+ * (group, step, chain, stream). The messenger draw xi uses stream 0, group (y W + x) / 4 and variate
+ * (y W + x) % 4. The signal draw zeta uses stream 1: for 0 < kx < W/2, group kx H/2 + j holds mode
+ * (j, kx) in variates 0, 1 (Re, Im) and mode (H - j, kx) in variates 2, 3 (j = 0: modes 0 and H/2); in
+ * the columns kx = 0 and kx = W/2, group j (0 < j < H/2) holds mode (j, 0) in variates 0, 1 and mode
+ * (j, W/2) in variates 2, 3, their conjugates fill the rows H - j, and group 0 holds the four real modes
+ * (0, 0), (H/2, 0), (0, W/2), (H/2, W/2). Complex modes are (Re + i Im) / sqrt(2). Draws are therefore
+ * reproducible, and an FP64 implementation of the same layout reproduces them draw for draw.
  */
 wf_status wf_sample(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int32_t H,
                     int32_t W, int64_t n_samples, uint64_t seed, float* out, wf_stream_t stream);

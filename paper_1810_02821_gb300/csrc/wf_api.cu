@@ -10,6 +10,7 @@
 
 #include "../../include/wf.h"
 #include "wf_launch.h"
+#include "wf_refine.h"
 
 namespace {
 
@@ -247,7 +248,7 @@ wf_status sample_global(const float* d, const float* Ndiag, const uint8_t* mask,
 // global memory.
 wf_status solve_global(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int H, int W,
                        const wf_solve_opts& o, float* out_s, int32_t* iters_out, double* resid_out, cudaStream_t st,
-                       wf::LaunchTimer* timer) {
+                       wf::LaunchTimer* timer, const float2* rhs_tab = nullptr, const double* rhs_norms = nullptr) {
   const size_t n = size_t(H) * W, nz = size_t(H) * (W / 2);
   // scalars first: the number of cooling levels sizes the level-norm pass
   Scratch s1;
@@ -265,7 +266,8 @@ wf_status solve_global(const float* d, const float* Ndiag, const uint8_t* mask, 
   const size_t o_sc = cv.take<wf::Scalars>(1), o_bar = cv.take<wf::GridBar>(2), o_dn = cv.take<float2>(n),
                o_tr = cv.take<float2>(W / 2), o_tc = cv.take<float2>(H), o_tw = cv.take<float2>(W / 2),
                o_bn = cv.take<double>(wf::kMaxLevels), o_acc = cv.take<double>(2), o_st = cv.take<wf::SolveStatus>(1),
-               o_prev = cv.take<float2>(nz), o_z = cv.take<float2>(nz * size_t(levels > 1 ? levels : 1));
+               o_prev = cv.take<float2>(nz),
+               o_z = cv.take<float2>(nz * size_t(levels > 1 && !rhs_tab ? levels : 1));
   Scratch scr;
   scr.st = st;
   WF_CUDA(cudaMallocAsync(&scr.base, cv.off, st));
@@ -277,9 +279,11 @@ wf_status solve_global(const float* d, const float* Ndiag, const uint8_t* mask, 
   WF_CUDA(cudaMemsetAsync(b + o_bn, 0, wf::kMaxLevels * sizeof(double), st));
   WF_CUDA(cudaMemsetAsync(b + o_acc, 0, 2 * sizeof(double), st));
   WF_CUDA(cudaMemsetAsync(b + o_st, 0, sizeof(wf::SolveStatus), st));
-  k_tables<<<int((n + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc, nullptr,
-                                                 reinterpret_cast<float2*>(b + o_dn), nullptr);
-  WF_CUDA(cudaGetLastError());
+  if (!rhs_tab) {
+    k_tables<<<int((n + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc, nullptr,
+                                                   reinterpret_cast<float2*>(b + o_dn), nullptr);
+    WF_CUDA(cudaGetLastError());
+  }
   k_twiddles<<<8, 256, 0, st>>>(H, W, reinterpret_cast<float2*>(b + o_tr), reinterpret_cast<float2*>(b + o_tc),
                                 reinterpret_cast<float2*>(b + o_tw));
   WF_CUDA(cudaGetLastError());
@@ -288,20 +292,24 @@ wf_status solve_global(const float* d, const float* Ndiag, const uint8_t* mask, 
   a.tw_row = reinterpret_cast<float2*>(b + o_tr);
   a.tw_col = reinterpret_cast<float2*>(b + o_tc);
   a.tw_real = reinterpret_cast<float2*>(b + o_tw);
-  a.dn = reinterpret_cast<float2*>(b + o_dn);
+  a.dn = rhs_tab ? rhs_tab : reinterpret_cast<float2*>(b + o_dn);
   a.Pk = Pk;
   a.sc = sc;
   a.bar = bar;
   a.eta = o.eta;
-  a.mode = 2;
-  a.n_fields = levels;
-  a.bnorm_out = reinterpret_cast<double*>(b + o_bn);
-  cudaError_t e = launch_global_any(H, a, st, nullptr);
-  if (e != cudaSuccess) return cuda_fail(e);
+  cudaError_t e = cudaSuccess;
+  if (!rhs_tab) {  // level norms (rhs mode: supplied)
+    a.mode = 2;
+    a.n_fields = levels;
+    a.bnorm_out = reinterpret_cast<double*>(b + o_bn);
+    e = launch_global_any(H, a, st, nullptr);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
   a.mode = 1;
+  a.rhs_mode = rhs_tab ? 1 : 0;
   a.n_fields = 1;
   a.bar = bar + 1;
-  a.bnorm2 = reinterpret_cast<double*>(b + o_bn);
+  a.bnorm2 = rhs_tab ? rhs_norms : reinterpret_cast<double*>(b + o_bn);
   a.acc = reinterpret_cast<double*>(b + o_acc);
   a.prev = reinterpret_cast<float2*>(b + o_prev);
   a.st = reinterpret_cast<wf::SolveStatus*>(b + o_st);
@@ -338,7 +346,9 @@ void wf_solve_opts_default(wf_solve_opts* o) {
   o->level_max = 64;
   o->check = 4;
   o->max_iter = 20000;
+  o->refine = 0;
   o->init_s = nullptr;
+  o->refine_tol = 1e-3;
 }
 
 void wf_sample_opts_default(wf_sample_opts* o) {
@@ -379,34 +389,27 @@ const char* wf_status_string(wf_status s) {
   return "unknown status";
 }
 
-wf_status wf_solve_ex(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int32_t H, int32_t W,
-                      const wf_solve_opts* opts, float* out_s, int32_t* iters_out, double* resid_out,
-                      wf_stream_t stream) {
-  wf_solve_opts o;
-  wf_solve_opts_default(&o);
-  if (opts) o = *opts;
-  if (!d || !Ndiag || !mask || !Pk || !out_s) return WF_ERR_ARG;
-  if (!size_ok(H, W)) return WF_ERR_SHAPE;
-  if (!(o.tol >= 0.0) || !(o.eta > 0.0 && o.eta < 1.0) || !(o.level_tol >= 0.0) || o.level_max < 1 || o.check < 1 ||
-      o.max_iter < 1)
-    return WF_ERR_ARG;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+}  // extern "C"
+
+namespace {
+
+// One cooled messenger solve (data mode, or rhs mode when rhs_tab is given: solves (S^-1 + N^-1) s = r
+// with the table's r and the supplied per-level norms).
+wf_status solve_pass(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int32_t H, int32_t W,
+                     const wf_solve_opts& o, float* out_s, int32_t* iters_out, double* resid_out, cudaStream_t st,
+                     wf::LaunchTimer* timer, const float2* rhs_tab = nullptr, const double* rhs_norms = nullptr) {
   if (!size_on_chip(H)) {
     if (o.init_s) return WF_ERR_ARG;  // the large-image solve starts from zero
-    KernelTimer gt(st);
-    const wf_status r = solve_global(d, Ndiag, mask, Pk, H, W, o, out_s, iters_out, resid_out, st, &gt);
-    gt.collect();
-    return r;
+    return solve_global(d, Ndiag, mask, Pk, H, W, o, out_s, iters_out, resid_out, st, timer, rhs_tab, rhs_norms);
   }
   const size_t n = size_t(H) * W, nm = size_t(H) * (W / 2 + 1);
-  const size_t off_sc = 0, off_st = align256(sizeof(wf::Scalars)),
-               off_bn = off_st + align256(sizeof(wf::SolveStatus)),
-               off_dn = off_bn + align256(kMaxLevels * sizeof(double)), off_prev = off_dn + align256(n * sizeof(float2)),
-               total = off_prev + align256(size_t(H) * (W / 2) * sizeof(float2));
-  (void)nm;
+  Carve cv;
+  const size_t off_sc = cv.take<wf::Scalars>(1), off_st = cv.take<wf::SolveStatus>(1),
+               off_bn = cv.take<double>(kMaxLevels), off_dn = cv.take<float2>(n),
+               off_prev = cv.take<float2>(size_t(H) * (W / 2));
   Scratch scr;
   scr.st = st;
-  WF_CUDA(cudaMallocAsync(&scr.base, total, st));
+  WF_CUDA(cudaMallocAsync(&scr.base, cv.off, st));
   char* b = static_cast<char*>(scr.base);
   auto* sc = reinterpret_cast<wf::Scalars*>(b + off_sc);
   auto* sst = reinterpret_cast<wf::SolveStatus*>(b + off_st);
@@ -416,20 +419,33 @@ wf_status wf_solve_ex(const float* d, const float* Ndiag, const uint8_t* mask, c
   WF_CUDA(cudaMemsetAsync(sst, 0, sizeof(wf::SolveStatus), st));
   k_prep<<<1, 1024, 0, st>>>(d, Ndiag, mask, Pk, H, W, o.tau, o.eta, sc);
   WF_CUDA(cudaGetLastError());
-  k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc, nullptr, dn, nullptr);
-  WF_CUDA(cudaGetLastError());
+  if (!rhs_tab) {
+    k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc, nullptr, dn, nullptr);
+    WF_CUDA(cudaGetLastError());
+  }
   wf::SolveArgs a{};
-  a.dn = dn; a.Pk = Pk; a.sc = sc; a.bnorm2 = bn; a.init_s = o.init_s; a.prev = prev; a.out = out_s; a.st = sst;
-  a.tol = o.tol; a.eta = o.eta; a.level_tol = o.level_tol; a.max_iter = o.max_iter; a.level_max = o.level_max;
+  a.dn = rhs_tab ? rhs_tab : dn;
+  a.Pk = Pk;
+  a.sc = sc;
+  a.bnorm2 = rhs_tab ? rhs_norms : bn;
+  a.init_s = o.init_s;
+  a.prev = prev;
+  a.out = out_s;
+  a.st = sst;
+  a.tol = o.tol;
+  a.eta = o.eta;
+  a.level_tol = o.level_tol;
+  a.max_iter = o.max_iter;
+  a.level_max = o.level_max;
   a.check = o.check;
+  a.rhs_mode = rhs_tab ? 1 : 0;
   wf::BnormArgs bb{dn, Pk, sc, bn, o.eta};
-  KernelTimer timer(st);
   cudaError_t e = cudaSuccess;
   switch (H) {
-    case 16: e = wf::launch_solve<16>(a, bb, st, &timer); break;
-    case 32: e = wf::launch_solve<32>(a, bb, st, &timer); break;
-    case 64: e = wf::launch_solve<64>(a, bb, st, &timer); break;
-    case 128: e = wf::launch_solve<128>(a, bb, st, &timer); break;
+    case 16: e = wf::launch_solve<16>(a, bb, st, timer); break;
+    case 32: e = wf::launch_solve<32>(a, bb, st, timer); break;
+    case 64: e = wf::launch_solve<64>(a, bb, st, timer); break;
+    case 128: e = wf::launch_solve<128>(a, bb, st, timer); break;
   }
   if (e != cudaSuccess) return cuda_fail(e);
   wf::Scalars hsc;
@@ -437,11 +453,103 @@ wf_status wf_solve_ex(const float* d, const float* Ndiag, const uint8_t* mask, c
   WF_CUDA(cudaMemcpyAsync(&hsc, sc, sizeof(hsc), cudaMemcpyDeviceToHost, st));
   WF_CUDA(cudaMemcpyAsync(&hst, sst, sizeof(hst), cudaMemcpyDeviceToHost, st));
   WF_CUDA(cudaStreamSynchronize(st));
-  timer.collect();
   if (hsc.status != WF_OK) return wf_status(hsc.status);
   if (iters_out) *iters_out = hst.iters;
   if (resid_out) *resid_out = hst.resid;
   return wf_status(hst.status);
+}
+
+// Mixed-precision iterative refinement: FP32 messenger solves, FP64 residuals (wf_refine.cu).
+wf_status solve_refined(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int32_t H, int32_t W,
+                        const wf_solve_opts& o, float* out_s, int32_t* iters_out, double* resid_out, cudaStream_t st,
+                        wf::LaunchTimer* timer) {
+  wf_solve_opts first = o;
+  first.tol = o.tol > 1e-5 ? o.tol : 1e-5;  // the FP32 iteration alone stops above its floor
+  int32_t it = 0, total = 0;
+  double rs = 0.0;
+  wf_status r = solve_pass(d, Ndiag, mask, Pk, H, W, first, out_s, &it, &rs, st, timer);
+  total += it;
+  if (r != WF_OK && r != WF_ERR_NOT_CONVERGED) return r;
+  const size_t n = size_t(H) * W, nm = size_t(H) * (W / 2 + 1);
+  Carve cv;
+  const size_t o_sc = cv.take<wf::Scalars>(1), o_dn = cv.take<float2>(n), o_rt = cv.take<float2>(n),
+               o_e = cv.take<float>(n), o_nr = cv.take<double>(4), o_ln = cv.take<double>(kMaxLevels),
+               o_fft = cv.take<char>(wf::refine_scratch_bytes(H, W));
+  Scratch scr;
+  scr.st = st;
+  WF_CUDA(cudaMallocAsync(&scr.base, cv.off, st));
+  char* b = static_cast<char*>(scr.base);
+  auto* sc = reinterpret_cast<wf::Scalars*>(b + o_sc);
+  k_prep<<<1, 1024, 0, st>>>(d, Ndiag, mask, Pk, H, W, o.tau, o.eta, sc);
+  WF_CUDA(cudaGetLastError());
+  k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc, nullptr,
+                                                       reinterpret_cast<float2*>(b + o_dn), nullptr);
+  WF_CUDA(cudaGetLastError());
+  double* norms = reinterpret_cast<double*>(b + o_nr);
+  wf::RefineArgs ra{};
+  ra.H = H;
+  ra.W = W;
+  ra.d = d;
+  ra.Nd = Ndiag;
+  ra.mask = mask;
+  ra.Pk = Pk;
+  ra.s = out_s;
+  ra.dn = reinterpret_cast<float2*>(b + o_dn);
+  ra.rtab = reinterpret_cast<float2*>(b + o_rt);
+  ra.rnorm = norms;
+  ra.bnorm = norms + 1;
+  ra.level_norms = reinterpret_cast<double*>(b + o_ln);
+  ra.n_levels = kMaxLevels;
+  ra.scratch = b + o_fft;
+  cudaError_t e = wf::refine_bnorm(ra, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  wf_solve_opts corr = o;
+  corr.tol = o.refine_tol;
+  corr.init_s = nullptr;
+  float* ev = reinterpret_cast<float*>(b + o_e);
+  double rho = -1.0;
+  wf_status status = WF_ERR_NOT_CONVERGED;
+  for (int k = 0; k <= o.refine; ++k) {
+    if ((e = wf::refine_residual(ra, st)) != cudaSuccess) return cuda_fail(e);
+    double h[2];
+    WF_CUDA(cudaMemcpyAsync(h, norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    WF_CUDA(cudaStreamSynchronize(st));
+    rho = h[1] > 0.0 ? sqrt(h[0] / h[1]) : sqrt(h[0]);
+    if (!(rho == rho)) { status = WF_ERR_NONFINITE; break; }
+    if (rho < o.tol) { status = WF_OK; break; }
+    if (k == o.refine) break;
+    r = solve_pass(d, Ndiag, mask, Pk, H, W, corr, ev, &it, &rs, st, nullptr, ra.rtab, ra.level_norms);
+    total += it;
+    if (r != WF_OK && r != WF_ERR_NOT_CONVERGED) return r;
+    if ((e = wf::refine_update(int(n), out_s, ev, st)) != cudaSuccess) return cuda_fail(e);
+  }
+  WF_CUDA(cudaStreamSynchronize(st));
+  if (iters_out) *iters_out = total;
+  if (resid_out) *resid_out = rho;
+  return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+wf_status wf_solve_ex(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int32_t H, int32_t W,
+                      const wf_solve_opts* opts, float* out_s, int32_t* iters_out, double* resid_out,
+                      wf_stream_t stream) {
+  wf_solve_opts o;
+  wf_solve_opts_default(&o);
+  if (opts) o = *opts;
+  if (!d || !Ndiag || !mask || !Pk || !out_s) return WF_ERR_ARG;
+  if (!size_ok(H, W)) return WF_ERR_SHAPE;
+  if (!(o.tol >= 0.0) || !(o.eta > 0.0 && o.eta < 1.0) || !(o.level_tol >= 0.0) || o.level_max < 1 || o.check < 1 ||
+      o.max_iter < 1 || o.refine < 0 || (o.refine > 0 && !(o.refine_tol > 0.0)))
+    return WF_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  KernelTimer timer(st);
+  const wf_status r = o.refine > 0 ? solve_refined(d, Ndiag, mask, Pk, H, W, o, out_s, iters_out, resid_out, st, &timer)
+                                   : solve_pass(d, Ndiag, mask, Pk, H, W, o, out_s, iters_out, resid_out, st, &timer);
+  timer.collect();
+  return r;
 }
 
 wf_status wf_solve(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int32_t H, int32_t W,

@@ -304,15 +304,18 @@ WF_HD void copy_out(const float* stg, int lt, float* __restrict__ out) {
 // ---------------------------------------------------------------------------------------------
 // Wiener-filter mode at level lambda: table dn[x*H + y] = (d, 1/N_bar) (0 on missing pixels),
 // w = N_bar / (lambda tau + N_bar) = 1 / (1 + lambda tau / N_bar), t = d + w (s - d).
+// rhs mode (refinement corrections): dn holds (r, 1/N_bar) and t = lambda tau r + w s, whose fixed point
+// solves (S^-1 + N_lambda^-1) s = r for any pixel-space r (r need not vanish on missing pixels).
 template <int N>
-WF_HD void t_update_wf(float2 (&c)[N / 2], int y, const float2* __restrict__ dn, float lt_) {
+WF_HD void t_update_wf(float2 (&c)[N / 2], int y, const float2* __restrict__ dn, float lt_, bool rhs = false) {
   using G = Geo<N>;
+  const float g = rhs ? 0.0f : 1.0f, h = rhs ? lt_ : 1.0f;
 #pragma unroll
   for (int x = 0; x < G::W; ++x) {
     const float2 co = WF_LDG(dn + x * G::H + y);
     const float w = wf_rcp(fmaf(lt_, co.y, 1.0f));
     float& v = (x & 1) ? c[x / 2].y : c[x / 2].x;
-    v = fmaf(w, v - co.x, co.x);
+    v = fmaf(w, fmaf(-g, co.x, v), h * co.x);
   }
 }
 
@@ -737,10 +740,10 @@ __global__ void __launch_bounds__(N * FPC, sample_min_ctas<N>()) k_sample(Sample
 }
 
 struct SolveArgs {
-  const float2* dn;      // [W][H] pixel table (d, 1/N_bar)
+  const float2* dn;      // [W][H] pixel table (d, 1/N_bar), or (r, 1/N_bar) in rhs mode
   const float* Pk;       // [H][W/2+1]
   const Scalars* sc;
-  const double* bnorm2;  // [n_levels] ||S N_lambda^-1 d||^2 per level
+  const double* bnorm2;  // [n_levels] ||S N_lambda^-1 d||^2 per level (rhs mode: ||S r||^2)
   const float* init_s;   // nullptr -> zeros
   float2* prev;          // [H][W/2] scratch: previous s_hat at check sweeps
   float* out;            // [H][W]
@@ -751,6 +754,7 @@ struct SolveArgs {
   int max_iter;
   int level_max;
   int check;
+  int rhs_mode;          // 1: solve (S^-1 + N^-1) s = r with the table's r (refinement correction)
 };
 
 // The G -> 0 iteration with lambda-cooling for one field (one CTA of N threads). On entry c holds the
@@ -761,14 +765,14 @@ __device__ __forceinline__ int solve_sweeps(float2* S, double* red, int lt, floa
                                             const float2* __restrict__ dn, const float* __restrict__ Pk,
                                             const Scalars& sc, const double* bnorm2, float2* prev, double tol,
                                             double eta, double level_tol, int max_iter, int level_max, int check,
-                                            int& it, double& rho) {
+                                            int& it, double& rho, bool rhs = false) {
   using G = Geo<N>;
   const double tau = sc.tau;
   int lev = 0;
   double lam = sc.lam0;
   float ltau = float(lam * tau);
   const int last_level = sc.n_levels - 1;
-  t_update_wf<N>(c, lt, dn, ltau);
+  t_update_wf<N>(c, lt, dn, ltau, rhs);
   row_forward<N>(c);
   row_store_spec<N>(S, lt, c);
   __syncthreads();
@@ -815,7 +819,7 @@ __device__ __forceinline__ int solve_sweeps(float2* S, double* red, int lt, floa
     __syncthreads();
     row_inverse<N>(c);
     if (status != 1) break;
-    t_update_wf<N>(c, lt, dn, ltau);
+    t_update_wf<N>(c, lt, dn, ltau, rhs);
     row_forward<N>(c);
     row_store_spec<N>(S, lt, c);
     __syncthreads();
@@ -845,7 +849,7 @@ __global__ void __launch_bounds__(N) k_solve(SolveArgs a) {
   int it = 0;
   double rho = -1.0;
   const int status = solve_sweeps<N>(S, red, lt, c, a.dn, a.Pk, sc, a.bnorm2, a.prev, a.tol, a.eta, a.level_tol,
-                                     a.max_iter, a.level_max, a.check, it, rho);
+                                     a.max_iter, a.level_max, a.check, it, rho, a.rhs_mode != 0);
   stage_row<N>(stg, lt, c);
   __syncthreads();
   copy_out<N>(stg, lt, a.out);

@@ -148,6 +148,7 @@ struct GlobalArgs {
   SolveStatus* st;
   double tol, eta, level_tol;
   int max_iter, level_max, check;
+  int rhs_mode;            // mode 1: dn holds (r, 1/N_bar), t = lambda tau r + w s (refinement correction)
   int mode;                // 0 sampler, 1 Wiener filter, 2 level norms (fields = levels), 3 weighted power
   double* bnorm_out;       // mode 2: [n_fields]
   // mode 3: fields v_f = va_f + vsign * vb_f, tables wts[nw][H][W/2+1], sums into wout[f*nw + j]
@@ -270,11 +271,12 @@ __device__ void row_item(const GlobalArgs& a, float2* buf, int f, int y0, int do
         s4[e] = fmaf(co.y, fmaf(co.y, s4[e], sc.sqrt_tau * z[e]), co.x);
       }
     } else if (a.mode == 1) {
+      const float g = a.rhs_mode ? 0.0f : 1.0f, h = a.rhs_mode ? ltau : 1.0f;
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const float2 co = __ldg(a.dn + (4 * q + e) * G::H + y);
         const float w = wf_rcp(fmaf(ltau, co.y, 1.0f));
-        s4[e] = fmaf(w, s4[e] - co.x, co.x);
+        s4[e] = fmaf(w, fmaf(-g, co.x, s4[e]), h * co.x);
       }
     } else {
       // level norms: right-hand side N_lambda^-1 d of level f

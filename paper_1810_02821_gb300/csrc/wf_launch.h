@@ -62,9 +62,11 @@ cudaError_t launch_solve(const SolveArgs& a, const BnormArgs& b, cudaStream_t st
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_solve<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  k_bnorm<N><<<kMaxLevels, N, smem, st>>>(b);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (!a.rhs_mode) {  // rhs mode: the level norms are supplied
+    k_bnorm<N><<<kMaxLevels, N, smem, st>>>(b);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   if (t) t->start();
   k_solve<N><<<1, N, smem, st>>>(a);
   if (t) t->stop();

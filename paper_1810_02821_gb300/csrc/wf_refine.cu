@@ -1,0 +1,198 @@
+// FP64 pieces of the mixed-precision iterative refinement of the Wiener filter:
+//   * a batched radix-2 Stockham FFT in FP64 over rows or columns of a [H][W] complex array in global
+//     memory (self-sorting, one kernel per stage; Govindaraju et al., "High performance discrete Fourier
+//     transforms on graphics processors", SC'08);
+//   * the refinement residual r = N^-1 (d - s) - S^-1 s of an FP32 iterate s and its norm ||S r||, with
+//     S = U^dagger diag(P) U applied through the FP64 transforms (S^-1 only on modes with P > 0).
+// The Wiener-filter equation (S^-1 + N^-1) s = N^-1 d (Eq. 2-3 with A = I, N^-1 = 0 on missing pixels)
+// gives (I + S N^-1) s - S N^-1 d = -S r, so ||S r|| / ||S N^-1 d|| is the relative residual used
+// everywhere else in the library, here evaluated in FP64.
+#include <cuda_runtime.h>
+
+#include "wf_refine.h"
+
+namespace wf {
+
+namespace {
+
+__device__ __forceinline__ double2 dadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 dsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 dmul(double2 a, double2 w) {
+  return make_double2(fma(a.x, w.x, -a.y * w.y), fma(a.x, w.y, a.y * w.x));
+}
+
+// One radix-2 Stockham stage (sub-transform size Ns -> 2 Ns) of `batch` sequences of length n; element i
+// of sequence b at [b * bstride + i * estride]. sign = -1 forward, +1 inverse (unnormalised).
+__global__ void k_stockham2(const double2* __restrict__ in, double2* __restrict__ out, int n, int Ns, int batch,
+                            long long bstride, long long estride, double sign) {
+  const long long half = n / 2;
+  const long long total = half * batch;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long b, j;
+    if (estride == 1) {  // rows: consecutive threads walk along a sequence
+      b = t / half;
+      j = t % half;
+    } else {  // columns: consecutive threads walk across sequences (coalesced)
+      j = t / batch;
+      b = t % batch;
+    }
+    const double2* x = in + b * bstride;
+    double2* y = out + b * bstride;
+    const double2 v0 = x[j * estride];
+    double2 v1 = x[(j + half) * estride];
+    const long long k = j % Ns;
+    double sn, cs;
+    sincospi(sign * double(k) / double(Ns), &sn, &cs);  // exp(sign * i pi k / Ns)
+    v1 = dmul(v1, make_double2(cs, sn));
+    const long long d = (j / Ns) * Ns * 2 + k;
+    y[d * estride] = dadd(v0, v1);
+    y[(d + Ns) * estride] = dsub(v0, v1);
+  }
+}
+
+int ilog2i(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+// s -> (s, 0) complex; rpix = N^-1 (d - s) on observed pixels (0 on missing)
+__global__ void k_ir_start(int n, const float* __restrict__ d, const float* __restrict__ Nd,
+                           const uint8_t* __restrict__ mask, const float* __restrict__ s, double2* xs, double* rpix) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    xs[i] = make_double2(double(s[i]), 0.0);
+    rpix[i] = mask[i] ? 0.0 : (double(d[i]) - double(s[i])) / double(Nd[i]);
+  }
+}
+
+// P on the full spectrum from the half table (P depends on |k|: (ky, kx) for kx > W/2 is (-ky, W - kx))
+__device__ __forceinline__ double p_full(const float* __restrict__ Pk, int H, int W, int ky, int kx) {
+  const int WH = W / 2 + 1;
+  return kx <= W / 2 ? double(Pk[ky * WH + kx]) : double(Pk[((H - ky) % H) * WH + (W - kx)]);
+}
+
+// X <- X / (n P) on modes with P > 0, 0 elsewhere (forward then inverse unnormalised transforms give n)
+__global__ void k_ir_divp(int H, int W, const float* __restrict__ Pk, double2* X) {
+  const int n = H * W;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double p = p_full(Pk, H, W, i / W, i % W);
+    X[i] = p > 0.0 ? make_double2(X[i].x / (double(n) * p), X[i].y / (double(n) * p)) : make_double2(0.0, 0.0);
+  }
+}
+
+// r = rpix - Re(q); xr = (r, 0); rtab[x*H + y] = (float(r), 1/N_bar) for the correction solve
+__global__ void k_ir_finish(int H, int W, const double* __restrict__ rpix, const double2* __restrict__ q,
+                            const float2* __restrict__ dn, double2* xr, float2* rtab) {
+  const int n = H * W;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double r = rpix[i] - q[i].x;
+    xr[i] = make_double2(r, 0.0);
+    const int y = i / W, x = i % W;
+    rtab[x * H + y] = make_float2(float(r), dn[x * H + y].y);
+  }
+}
+
+// v -> (v, 0) with v = N^-1 d on observed pixels
+__global__ void k_ir_rhs(int n, const float* __restrict__ d, const float* __restrict__ Nd,
+                         const uint8_t* __restrict__ mask, double2* x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    x[i] = make_double2(mask[i] ? 0.0 : double(d[i]) / double(Nd[i]), 0.0);
+}
+
+// out += sum_k P_k^2 |X_k|^2 / n (full spectrum, unnormalised X)
+__global__ void k_ir_pnorm(int H, int W, const float* __restrict__ Pk, const double2* __restrict__ X, double* out) {
+  const int n = H * W;
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double p = p_full(Pk, H, W, i / W, i % W);
+    acc += p * p * (X[i].x * X[i].x + X[i].y * X[i].y);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, acc / double(n));
+}
+
+__global__ void k_fill(double* a, int n, const double* v) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] = *v;
+}
+
+__global__ void k_add_f32(int n, float* s, const float* __restrict__ e) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s[i] += e[i];
+}
+
+int grid_for(long long n) {
+  const long long g = (n + 255) / 256;
+  return int(g < 2048 ? (g < 1 ? 1 : g) : 2048);
+}
+
+}  // namespace
+
+cudaError_t fft2_f64(double2* a, double2* b, int H, int W, int sign, cudaStream_t st, double2** result) {
+  double2* in = a;
+  double2* out = b;
+  const double sg = sign < 0 ? -1.0 : 1.0;
+  for (int s = 0; s < ilog2i(W); ++s) {  // rows
+    k_stockham2<<<grid_for((long long)H * W / 2), 256, 0, st>>>(in, out, W, 1 << s, H, W, 1, sg);
+    double2* t = in;
+    in = out;
+    out = t;
+  }
+  for (int s = 0; s < ilog2i(H); ++s) {  // columns
+    k_stockham2<<<grid_for((long long)H * W / 2), 256, 0, st>>>(in, out, H, 1 << s, W, 1, W, sg);
+    double2* t = in;
+    in = out;
+    out = t;
+  }
+  *result = in;
+  return cudaGetLastError();
+}
+
+size_t refine_scratch_bytes(int H, int W) {
+  const size_t n = size_t(H) * W;
+  return 2 * n * sizeof(double2) + n * sizeof(double) + 4 * sizeof(double) + 64;
+}
+
+cudaError_t refine_bnorm(const RefineArgs& a, cudaStream_t st) {
+  const int n = a.H * a.W;
+  double2* xa = reinterpret_cast<double2*>(a.scratch);
+  double2* xb = xa + n;
+  cudaError_t e = cudaMemsetAsync(a.bnorm, 0, sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  k_ir_rhs<<<grid_for(n), 256, 0, st>>>(n, a.d, a.Nd, a.mask, xa);
+  double2* X = nullptr;
+  if ((e = fft2_f64(xa, xb, a.H, a.W, -1, st, &X)) != cudaSuccess) return e;
+  k_ir_pnorm<<<grid_for(n), 256, 0, st>>>(a.H, a.W, a.Pk, X, a.bnorm);
+  return cudaGetLastError();
+}
+
+cudaError_t refine_residual(const RefineArgs& a, cudaStream_t st) {
+  const int n = a.H * a.W;
+  double2* xa = reinterpret_cast<double2*>(a.scratch);
+  double2* xb = xa + n;
+  double* rpix = reinterpret_cast<double*>(xb + n);
+  cudaError_t e = cudaMemsetAsync(a.rnorm, 0, sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  k_ir_start<<<grid_for(n), 256, 0, st>>>(n, a.d, a.Nd, a.mask, a.s, xa, rpix);
+  double2* X = nullptr;
+  if ((e = fft2_f64(xa, xb, a.H, a.W, -1, st, &X)) != cudaSuccess) return e;
+  k_ir_divp<<<grid_for(n), 256, 0, st>>>(a.H, a.W, a.Pk, X);
+  double2* other = X == xa ? xb : xa;
+  double2* q = nullptr;
+  if ((e = fft2_f64(X, other, a.H, a.W, +1, st, &q)) != cudaSuccess) return e;  // q = S^-1 s
+  double2* xr = q == xa ? xb : xa;
+  k_ir_finish<<<grid_for(n), 256, 0, st>>>(a.H, a.W, rpix, q, a.dn, xr, a.rtab);
+  double2* other2 = xr == xa ? xb : xa;
+  double2* R = nullptr;
+  if ((e = fft2_f64(xr, other2, a.H, a.W, -1, st, &R)) != cudaSuccess) return e;
+  k_ir_pnorm<<<grid_for(n), 256, 0, st>>>(a.H, a.W, a.Pk, R, a.rnorm);
+  // every cooling level of the correction solve measures its residual against ||S r||
+  k_fill<<<1, 64, 0, st>>>(a.level_norms, a.n_levels, a.rnorm);
+  return cudaGetLastError();
+}
+
+cudaError_t refine_update(int n, float* s, const float* e, cudaStream_t st) {
+  k_add_f32<<<grid_for(n), 256, 0, st>>>(n, s, e);
+  return cudaGetLastError();
+}
+
+}  // namespace wf

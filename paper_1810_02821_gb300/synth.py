@@ -134,6 +134,54 @@ def config_paper128(seed: int = 0) -> WFProblem:
     return _finish(signal, Ndiag, mask, Pk, rng, dict(kind="paper128", H=H, W=W, seed=seed))
 
 
+def circular_holes(H: int, W: int, n_holes: int, r_range: tuple[float, float], area_frac: float,
+                   rng: np.random.Generator) -> np.ndarray:
+    """Mask of ``n_holes`` discs (periodic wrap) with radii in ``r_range`` covering ``area_frac`` of the image.
+
+    Centres are uniform; radii are r_lo + (r_hi - r_lo) u^a with u uniform, and the exponent a is set by
+    bisection so that the union of the discs covers ``area_frac`` of the pixels (to within a pixel or so
+    of the reachable fractions).
+    """
+    cy = rng.uniform(0, H, n_holes)
+    cx = rng.uniform(0, W, n_holes)
+    u = rng.uniform(0.0, 1.0, n_holes)
+    r_lo, r_hi = r_range
+
+    def paint(a):
+        mask = np.zeros((H, W), np.uint8)
+        for y0, x0, r in zip(cy, cx, r_lo + (r_hi - r_lo) * u ** a):
+            R = int(np.ceil(r)) + 1
+            ys = np.arange(int(np.floor(y0)) - R, int(np.floor(y0)) + R + 1)
+            xs = np.arange(int(np.floor(x0)) - R, int(np.floor(x0)) + R + 1)
+            inside = (ys[:, None] + 0.5 - y0) ** 2 + (xs[None, :] + 0.5 - x0) ** 2 <= r * r
+            yy, xx = np.nonzero(inside)
+            mask[ys[yy] % H, xs[xx] % W] = 1
+        return mask
+
+    lo, hi = np.log(1e-3), np.log(1e3)           # a small: radii near r_hi (largest cover)
+    for _ in range(40):
+        mid = 0.5 * (lo + hi)
+        if paint(np.exp(mid)).mean() > area_frac:
+            lo = mid
+        else:
+            hi = mid
+    return paint(np.exp(0.5 * (lo + hi)))
+
+
+def config_precision(H: int = 1024, seed: int = 0, n_holes: int = 200, r_range: tuple[float, float] = (4.0, 30.0),
+                     area_frac: float = 0.25) -> WFProblem:
+    """Precision case: P = (k/k0)^-1.5 with k0 = 1/32, sigma^2 ~ U[0.001, 0.1] (noise dynamic range 100), and
+    a mask of ``n_holes`` circular holes with radii in ``r_range`` covering ``area_frac`` of the area
+    (defaults: the 1024x1024 map with 200 holes of radius 4-30 px over 25%)."""
+    W = H
+    rng = np.random.default_rng(seed)
+    Pk = power_law_pk(H, W, 1.0, -1.5, 1.0 / 32)
+    signal = gaussian_random_field(Pk, H, W, rng)
+    Ndiag = rng.uniform(0.001, 0.1, size=(H, W))
+    mask = circular_holes(H, W, n_holes, r_range, area_frac, rng)
+    return _finish(signal, Ndiag, mask, Pk, rng, dict(kind="precision", H=H, W=W, seed=seed))
+
+
 def flat_problem(H: int, W: int | None = None, *, seed: int = 0, P: float = 1.0, sigma2: float = 0.3,
                  all_masked: bool = False) -> WFProblem:
     """Special cases with closed-form answers: flat P (except P0 = 0), homogeneous noise, and either no

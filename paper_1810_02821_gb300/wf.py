@@ -29,7 +29,8 @@ class WFError(RuntimeError):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("tol", ctypes.c_double), ("eta", ctypes.c_double),
                 ("level_tol", ctypes.c_double), ("level_max", ctypes.c_int32), ("check", ctypes.c_int32),
-                ("max_iter", ctypes.c_int32), ("reserved", ctypes.c_int32), ("init_s", ctypes.c_void_p)]
+                ("max_iter", ctypes.c_int32), ("refine", ctypes.c_int32), ("init_s", ctypes.c_void_p),
+                ("refine_tol", ctypes.c_double)]
 
 
 class SampleOpts(ctypes.Structure):
@@ -162,8 +163,15 @@ def wf_solve(d, Ndiag, mask, Pk, tau: float = 0.0, tol: float = 1e-6, out=None, 
 
 def wf_solve_ex(d, Ndiag, mask, Pk, *, tau: float = 0.0, tol: float = 1e-6, eta: float = 0.5,
                 level_tol: float = 1e-2, level_max: int = 64, check: int = 4, max_iter: int = 20000,
-                init_s=None, out=None, stream=None, allow_not_converged: bool = False) -> SolveResult:
-    """All options of the cooled Wiener-filter solve (C call ``wf_solve_ex``)."""
+                refine: int = 0, refine_tol: float = 1e-3, init_s=None, out=None, stream=None,
+                allow_not_converged: bool = False) -> SolveResult:
+    """All options of the cooled Wiener-filter solve (C call ``wf_solve_ex``).
+
+    ``refine`` > 0 turns on mixed-precision iterative refinement: after the FP32 messenger solve, up to
+    ``refine`` corrections, each an FP32 messenger solve of (S^-1 + N^-1) e = r (to relative residual
+    ``refine_tol``) for the residual r = N^-1 (d - s) - S^-1 s evaluated in FP64. The returned residual is
+    then the FP64 relative residual ||S r|| / ||S N^-1 d||, and ``iters`` counts the sweeps of all solves.
+    """
     import torch
     L = load_library()
     H, W, pd, pn, pm, pp = _inputs(d, Ndiag, mask, Pk)
@@ -174,6 +182,7 @@ def wf_solve_ex(d, Ndiag, mask, Pk, *, tau: float = 0.0, tol: float = 1e-6, eta:
     L.wf_solve_opts_default(ctypes.byref(o))
     o.tau, o.tol, o.eta, o.level_tol = float(tau), float(tol), float(eta), float(level_tol)
     o.level_max, o.check, o.max_iter = int(level_max), int(check), int(max_iter)
+    o.refine, o.refine_tol = int(refine), float(refine_tol)
     o.init_s = _dev(init_s, torch.float32, (H, W), "init_s").value if init_s is not None else None
     it = ctypes.c_int32(0)
     rs = ctypes.c_double(0.0)

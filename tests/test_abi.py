@@ -61,3 +61,44 @@ def test_product_path_has_no_oracle_import():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_refine_options_validated_without_gpu(lib):
+    o = wf.SolveOpts()
+    lib.wf_solve_opts_default(ctypes.byref(o))
+    assert o.refine == 0 and o.refine_tol == 1e-3 and not o.init_s
+    p = ctypes.c_void_p(16)
+    it, rs = ctypes.c_int32(0), ctypes.c_double(0.0)
+    for field, value in (("refine", -1), ("refine_tol", 0.0)):
+        bad = wf.SolveOpts()
+        lib.wf_solve_opts_default(ctypes.byref(bad))
+        bad.refine = 2
+        setattr(bad, field, value)
+        assert lib.wf_solve_ex(p, p, p, p, 32, 32, ctypes.byref(bad), p, ctypes.byref(it), ctypes.byref(rs), None) == 1
+
+
+def test_option_structs_match_the_header(tmp_path):
+    """sizeof/offsetof of the option structs as a C compiler lays them out from include/wf.h."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"wf_solve_opts": wf.SolveOpts, "wf_sample_opts": wf.SampleOpts,
+               "wf_batch_item": wf.BatchItem, "wf_batch_opts": wf.BatchOpts}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "wf.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", build.INCLUDE, str(src), "-o", str(exe)], check=True)
+    got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                          text=True).stdout.split("\n") if l)
+    for cname, py in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert int(got[f"{cname}.{fname}"]) == getattr(py, fname).offset, (cname, fname)
