@@ -10,6 +10,12 @@ N = alpha * sigma2 for a known base map sigma2. Then
 
 with dC/dA = dS_oo/dA (dP/dA = P/A), dC/dn = dS_oo/dn (dP/dn = P ln(k/k0)), dC/dalpha = sigma2_oo.
 The quadratic part Q = -1/2 d_o^T C^-1 d_o has gradient 1/2 x^T (dC/dtheta) x.
+
+The Wiener map itself, s_W(theta) = S[:, o] C^-1 d_o (Eq. 2-3), has the derivative
+
+    d s_W / d theta = dS[:, o] x - S[:, o] C^-1 (dC/dtheta) x,
+
+so a cotangent g (all pixels) pulls back to g^T dS[:, o] x - y^T (dC/dtheta) x with y = C^-1 S[o, :] g.
 """
 from __future__ import annotations
 
@@ -72,3 +78,33 @@ def loglike_grad_dense(d, sigma2, mask, A: float, n: float, k0: float, alpha: fl
     gq = np.array([0.5 * x @ dC @ x for dC in dCs])
     tr = np.array([np.sum(Ci * dC) for dC in dCs])      # tr(C^-1 dC), both symmetric
     return gq - 0.5 * tr, gq
+
+
+def wiener_param_dense(d, sigma2, mask, A: float, n: float, k0: float, alpha: float) -> np.ndarray:
+    """Wiener filter (Eq. 2-3) for P = A (k/k0)^n and N = alpha * sigma2, by the dense solve -> [H][W]."""
+    H, W = np.asarray(d).shape
+    P, _, _ = psd_tables(H, W, A, n, k0)
+    S = _dense_S(P, H, W)
+    o = np.flatnonzero(np.asarray(mask).ravel() == 0)
+    C = S[np.ix_(o, o)] + np.diag(alpha * np.asarray(sigma2, dtype=np.float64).ravel()[o])
+    x = np.linalg.solve(C, np.asarray(d, dtype=np.float64).ravel()[o])
+    return (S[:, o] @ x).reshape(H, W)
+
+
+def wiener_vjp_dense(d, sigma2, mask, A: float, n: float, k0: float, alpha: float, g) -> np.ndarray:
+    """g^T d s_W / d(A, n, alpha) for the Wiener map of :func:`wiener_param_dense` (dense algebra)."""
+    H, W = np.asarray(d).shape
+    P, dA, dn = psd_tables(H, W, A, n, k0)
+    S = _dense_S(P, H, W)
+    o = np.flatnonzero(np.asarray(mask).ravel() == 0)
+    s2 = np.asarray(sigma2, dtype=np.float64).ravel()[o]
+    C = S[np.ix_(o, o)] + np.diag(alpha * s2)
+    x = np.linalg.solve(C, np.asarray(d, dtype=np.float64).ravel()[o])
+    gv = np.asarray(g, dtype=np.float64).ravel()
+    dSs = [_dense_S(dA, H, W), _dense_S(dn, H, W), np.zeros_like(S)]
+    dCs = [dSs[0][np.ix_(o, o)], dSs[1][np.ix_(o, o)], np.diag(s2)]
+    out = []
+    for dS, dC in zip(dSs, dCs):
+        ds = dS[:, o] @ x - S[:, o] @ np.linalg.solve(C, dC @ x)
+        out.append(gv @ ds)
+    return np.array(out)

@@ -52,3 +52,27 @@ def test_gradient_matches_finite_differences():
         Lm, Qm = LL.loglike_dense(d, s2, mask, tm[0], tm[1], k0, tm[2])
         assert abs(g[i] - (Lp - Lm) / (2 * h)) < 1e-6 * max(1.0, abs(g[i]))
         assert abs(gq[i] - (Qp - Qm) / (2 * h)) < 1e-6 * max(1.0, abs(gq[i]))
+
+
+def test_wiener_param_dense_is_the_dense_wiener_filter():
+    from oracle import dense
+    d, s2, mask = _problem(seed=5)
+    P, _, _ = LL.psd_tables(8, 8, 1.3, -1.7, 1.0 / 8)
+    np.testing.assert_allclose(LL.wiener_param_dense(d, s2, mask, 1.3, -1.7, 1.0 / 8, 0.9),
+                               dense.wiener_dense(d, 0.9 * s2, mask, P), rtol=1e-10, atol=1e-12)
+
+
+def test_wiener_vjp_matches_finite_differences_of_the_dense_filter():
+    d, s2, mask = _problem(seed=7)
+    g = np.random.default_rng(1).standard_normal(d.shape)
+    th = np.array([1.3, -1.7, 0.9])
+    k0 = 1.0 / 8
+    v = LL.wiener_vjp_dense(d, s2, mask, th[0], th[1], k0, th[2], g)
+    for i in range(3):
+        h = 1e-5 * max(1.0, abs(th[i]))
+        tp, tm = th.copy(), th.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = g.ravel() @ (LL.wiener_param_dense(d, s2, mask, tp[0], tp[1], k0, tp[2]) -
+                          LL.wiener_param_dense(d, s2, mask, tm[0], tm[1], k0, tm[2])).ravel() / (2 * h)
+        assert abs(v[i] - fd) < 1e-6 * max(1.0, abs(fd)), (i, v[i], fd)
