@@ -203,6 +203,27 @@ wf_status wf_loglike_grad(const float* d, const float* sigma2, const uint8_t* ma
                           double* out_grad_quad, double* out_grad, double* out_grad_var, float* out_wf,
                           wf_stream_t stream);
 
+/*
+ * The Wiener map (Eq. 2-3, A = I) as a function of the parameters of wf_loglike_grad (P = amp (k/k0)^slope,
+ * N = alpha * sigma2): s_W(theta) = S[:, o] C^-1 d_o with C = S_oo + N_oo over the observed pixels o, and
+ * its vector-Jacobian product for a cotangent g:
+ *   out_vjp[i] = g^T d s_W / d theta_i = g^T dS[:, o] x - y^T (dC/dtheta_i) x,  theta = (amp, slope, alpha),
+ *   x = C^-1 d_o = N^-1 (d - s_W) on o,  y = C^-1 (S g)_o  (C is symmetric, so the adjoint of the solve
+ *   is one more Wiener solve: y = N^-1 (S g - s_W(S g)) on o, with the Wiener filter of "data" S g).
+ * The dS terms are cross spectral powers sum_k dP_k Re(conj(U a)_k (U b)_k), evaluated as in
+ * wf_spectral_power; S g is applied with FP64 transforms.
+ *   s_w_in: device [H][W], the Wiener filter of d for these parameters kept from an earlier call (the
+ *           checkpointed forward solve), or NULL: it is solved here.
+ *   g:      device [H][W] cotangent, or NULL: only the forward map is computed (out_vjp untouched).
+ *   tol:    relative-residual target of each solve; below 1e-6 the solves use FP64-residual refinement.
+ *   out_vjp: HOST double[3] (required when g is given); out_wf: device [H][W] receiving s_W, or NULL.
+ * d, sigma2: device float32 [H][W]; mask: device uint8 [H][W]; params = {amp, slope, k0, alpha}.
+ * Statuses as wf_solve_ex (WF_ERR_NOT_CONVERGED when a solve misses tol).
+ */
+wf_status wf_wiener_vjp(const float* d, const float* sigma2, const uint8_t* mask, int32_t H, int32_t W,
+                        const double* params, const float* g, const float* s_w_in, double tol, double* out_vjp,
+                        float* out_wf, wf_stream_t stream);
+
 /* 1 if (H, W) is supported by wf_solve / wf_sample, else 0. */
 int32_t wf_supported_size(int32_t H, int32_t W);
 

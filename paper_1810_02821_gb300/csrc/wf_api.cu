@@ -1002,6 +1002,18 @@ __global__ void k_rademacher(int n, uint32_t probe, uint32_t k0, uint32_t k1, co
   }
 }
 
+// v = g - y (all pixels; y is 0 on missing ones) and sum[0] += sum_o sigma2 y x
+__global__ void k_vjp_mix(int n, const float* __restrict__ g, const float* __restrict__ y, const float* __restrict__ x,
+                          const float* __restrict__ sigma2, const uint8_t* __restrict__ mask, float* v, double* sum) {
+  double a = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    v[i] = g[i] - y[i];
+    if (mask[i] == 0) a += double(sigma2[i]) * double(y[i]) * double(x[i]);
+  }
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(sum, a);
+}
+
 // weighted spectral power into device memory dout[n_fields * nw]
 cudaError_t spectral_power_dev(const float* a, const float* b, float sgn, int n_fields, const float* w, int nw, int H,
                                int W, double* dout, cudaStream_t st) {
@@ -1169,6 +1181,78 @@ wf_status wf_loglike_grad(const float* d, const float* sigma2, const uint8_t* ma
     if (out_grad) out_grad[i] = gq[i] - 0.5 * mean;
     if (out_grad_var) out_grad_var[i] = 0.25 * var / n_probes;
   }
+  return WF_OK;
+}
+
+wf_status wf_wiener_vjp(const float* d, const float* sigma2, const uint8_t* mask, int32_t H, int32_t W,
+                        const double* params, const float* g, const float* s_w_in, double tol, double* out_vjp,
+                        float* out_wf, wf_stream_t stream) {
+  if (!d || !sigma2 || !mask || !params || (g && !out_vjp)) return WF_ERR_ARG;
+  if (!size_ok(H, W)) return WF_ERR_SHAPE;
+  const double amp = params[0], slope = params[1], k0 = params[2], alpha = params[3];
+  if (!(amp > 0.0) || !(k0 > 0.0) || !(alpha > 0.0) || !std::isfinite(slope) || !(tol > 0.0)) return WF_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t n = size_t(H) * W, nm = size_t(H) * (W / 2 + 1);
+  Carve cv;
+  const size_t o_P = cv.take<float>(3 * nm), o_N = cv.take<float>(n), o_s = cv.take<float>(n), o_x = cv.take<float>(n),
+               o_b = cv.take<float>(n), o_y = cv.take<float>(n), o_w = cv.take<float>(n), o_sum = cv.take<double>(4),
+               o_pow = cv.take<double>(8), o_f64 = cv.take<double2>(2 * n);
+  Scratch scr;
+  scr.st = st;
+  WF_CUDA(cudaMallocAsync(&scr.base, cv.off, st));
+  char* b = static_cast<char*>(scr.base);
+  float* P = reinterpret_cast<float*>(b + o_P);
+  float* dPa = P + nm;
+  float* dPn = P + 2 * nm;
+  float* Nd = reinterpret_cast<float*>(b + o_N);
+  float* sW = out_wf ? out_wf : reinterpret_cast<float*>(b + o_s);
+  float* x = reinterpret_cast<float*>(b + o_x);
+  float* bv = reinterpret_cast<float*>(b + o_b);
+  float* y = reinterpret_cast<float*>(b + o_y);
+  float* wv = reinterpret_cast<float*>(b + o_w);
+  double* sums = reinterpret_cast<double*>(b + o_sum);
+  double* pw = reinterpret_cast<double*>(b + o_pow);
+  const int nblk = int((nm + n + 255) / 256);
+  k_psd<<<nblk < 1024 ? nblk : 1024, 256, 0, st>>>(H, W, amp, slope, k0, alpha, sigma2, P, dPa, dPn, Nd);
+  WF_CUDA(cudaGetLastError());
+  wf_solve_opts so;
+  wf_solve_opts_default(&so);
+  so.tol = tol;
+  if (tol < 1e-6) so.refine = 8;  // below the FP32 iteration's floor
+  int32_t it = 0;
+  double rs = 0.0;
+  wf_status r = WF_OK;
+  if (s_w_in) {
+    if (s_w_in != sW) WF_CUDA(cudaMemcpyAsync(sW, s_w_in, n * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  } else if ((r = wf_solve_ex(d, Nd, mask, P, H, W, &so, sW, &it, &rs, stream)) != WF_OK) {
+    return r;
+  }
+  if (!g) {
+    WF_CUDA(cudaStreamSynchronize(st));
+    return WF_OK;
+  }
+  const int xb = int((n + 255) / 256) < 1024 ? int((n + 255) / 256) : 1024;
+  WF_CUDA(cudaMemsetAsync(sums, 0, 4 * sizeof(double), st));
+  k_xres<<<xb, 256, 0, st>>>(int(n), d, sW, Nd, sigma2, mask, x, sums);  // x = C^-1 d (0 on missing)
+  WF_CUDA(cudaGetLastError());
+  cudaError_t e = wf::apply_S_f64(g, P, H, W, bv, b + o_f64, st);    // b = S g
+  if (e != cudaSuccess) return cuda_fail(e);
+  if ((r = wf_solve_ex(bv, Nd, mask, P, H, W, &so, wv, &it, &rs, stream)) != WF_OK) return r;  // s_W(S g)
+  k_xres<<<xb, 256, 0, st>>>(int(n), bv, wv, Nd, sigma2, mask, y, sums);  // y = C^-1 (S g)_o
+  WF_CUDA(cudaGetLastError());
+  WF_CUDA(cudaMemsetAsync(sums, 0, sizeof(double), st));
+  k_vjp_mix<<<xb, 256, 0, st>>>(int(n), g, y, x, sigma2, mask, bv, sums);  // bv = g - y
+  WF_CUDA(cudaGetLastError());
+  // (g - y)^T dS x = (|U(x + v)|^2_dP - |U(x - v)|^2_dP) / 4
+  if ((e = spectral_power_dev(x, bv, 1.f, 1, dPa, 2, H, W, pw, st)) != cudaSuccess) return cuda_fail(e);
+  if ((e = spectral_power_dev(x, bv, -1.f, 1, dPa, 2, H, W, pw + 2, st)) != cudaSuccess) return cuda_fail(e);
+  double hs, hq[4];
+  WF_CUDA(cudaMemcpyAsync(&hs, sums, sizeof(double), cudaMemcpyDeviceToHost, st));
+  WF_CUDA(cudaMemcpyAsync(hq, pw, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  WF_CUDA(cudaStreamSynchronize(st));
+  out_vjp[0] = 0.25 * (hq[0] - hq[2]);
+  out_vjp[1] = 0.25 * (hq[1] - hq[3]);
+  out_vjp[2] = -hs;
   return WF_OK;
 }
 

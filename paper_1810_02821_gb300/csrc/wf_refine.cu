@@ -190,6 +190,43 @@ cudaError_t refine_residual(const RefineArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+namespace {
+
+// X <- X P / n on the full spectrum (forward then inverse unnormalised transforms give n)
+__global__ void k_ir_mulp(int H, int W, const float* __restrict__ Pk, double2* X) {
+  const int n = H * W;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double p = p_full(Pk, H, W, i / W, i % W) / double(n);
+    X[i] = make_double2(X[i].x * p, X[i].y * p);
+  }
+}
+
+__global__ void k_ir_load(int n, const float* __restrict__ v, double2* x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    x[i] = make_double2(double(v[i]), 0.0);
+}
+
+__global__ void k_ir_store(int n, const double2* __restrict__ x, float* v) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = float(x[i].x);
+}
+
+}  // namespace
+
+cudaError_t apply_S_f64(const float* v, const float* Pk, int H, int W, float* out, void* scratch, cudaStream_t st) {
+  const int n = H * W;
+  double2* xa = reinterpret_cast<double2*>(scratch);
+  double2* xb = xa + n;
+  k_ir_load<<<grid_for(n), 256, 0, st>>>(n, v, xa);
+  double2* X = nullptr;
+  cudaError_t e = fft2_f64(xa, xb, H, W, -1, st, &X);
+  if (e != cudaSuccess) return e;
+  k_ir_mulp<<<grid_for(n), 256, 0, st>>>(H, W, Pk, X);
+  double2* q = nullptr;
+  if ((e = fft2_f64(X, X == xa ? xb : xa, H, W, +1, st, &q)) != cudaSuccess) return e;
+  k_ir_store<<<grid_for(n), 256, 0, st>>>(n, q, out);
+  return cudaGetLastError();
+}
+
 cudaError_t refine_update(int n, float* s, const float* e, cudaStream_t st) {
   k_add_f32<<<grid_for(n), 256, 0, st>>>(n, s, e);
   return cudaGetLastError();

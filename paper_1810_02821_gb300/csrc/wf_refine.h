@@ -32,5 +32,7 @@ size_t refine_scratch_bytes(int H, int W);
 cudaError_t refine_bnorm(const RefineArgs& a, cudaStream_t st);
 cudaError_t refine_residual(const RefineArgs& a, cudaStream_t st);
 cudaError_t refine_update(int n, float* s, const float* e, cudaStream_t st);
+// out = S v = U^dagger diag(P) U v in FP64 (rounded once to float); scratch: 2 H W double2
+cudaError_t apply_S_f64(const float* v, const float* Pk, int H, int W, float* out, void* scratch, cudaStream_t st);
 
 }  // namespace wf

@@ -96,6 +96,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.wf_loglike_grad.argtypes = [P, P, P, I32, I32, ctypes.POINTER(D), I32, U64, D, ctypes.POINTER(D),
                                   ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D), P, P]
     L.wf_loglike_grad.restype = ctypes.c_int
+    L.wf_wiener_vjp.argtypes = [P, P, P, I32, I32, ctypes.POINTER(D), P, P, D, ctypes.POINTER(D), P, P]
+    L.wf_wiener_vjp.restype = ctypes.c_int
     L.wf_set_kernel_timing.argtypes = [I32]
     L.wf_set_kernel_timing.restype = None
     L.wf_last_kernel_ms.argtypes = []
@@ -382,3 +384,65 @@ def wf_last_kernel_ms() -> float:
 
 def wf_supported_size(H: int, W: int) -> bool:
     return bool(load_library().wf_supported_size(H, W))
+
+
+def wf_wiener_vjp(d, sigma2, mask, amp: float, slope: float, k0: float, alpha: float, g=None, *, s_w=None,
+                  tol: float = 1e-7, out=None, stream=None):
+    """Wiener map s_W(amp, slope, alpha) and, for a cotangent ``g``, g^T ds_W/d(amp, slope, alpha)
+    (C call ``wf_wiener_vjp``). ``s_w``: the forward Wiener filter kept from an earlier call (skips that
+    solve). Returns (s_W tensor, vjp numpy[3] or None)."""
+    import numpy as np
+    import torch
+    L = load_library()
+    H, W = d.shape
+    pd = _dev(d, torch.float32, (H, W), "d")
+    ps = _dev(sigma2, torch.float32, (H, W), "sigma2")
+    pm = _dev(mask, torch.uint8, (H, W), "mask")
+    pg = _dev(g, torch.float32, (H, W), "g") if g is not None else None
+    pw = _dev(s_w, torch.float32, (H, W), "s_w") if s_w is not None else None
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.float32, device=d.device)
+    po = _dev(out, torch.float32, (H, W), "out")
+    prm = (ctypes.c_double * 4)(float(amp), float(slope), float(k0), float(alpha))
+    v = (ctypes.c_double * 3)()
+    st = L.wf_wiener_vjp(pd, ps, pm, H, W, prm, pg, pw, float(tol), v if g is not None else None, po,
+                         _stream_ptr(stream))
+    _check(st, "wf_wiener_vjp")
+    return out, (np.array(v[:]) if g is not None else None)
+
+
+def _make_wiener_map_function():
+    import torch
+
+    class WienerMap(torch.autograd.Function):
+        """theta = (amp, slope, alpha) -> the Wiener filter s_W [H][W] of d (Eq. 2-3) for P = amp (k/k0)^slope
+        and N = alpha * sigma2. The forward solve is kept (checkpointed) for the backward pass, which runs
+        one adjoint Wiener solve per cotangent (``wf_wiener_vjp``)."""
+
+        @staticmethod
+        def forward(ctx, theta, d, sigma2, mask, k0, tol):
+            t = theta.detach().double().cpu().numpy()
+            s, _ = wf_wiener_vjp(d, sigma2, mask, t[0], t[1], k0, t[2], tol=tol)
+            ctx.args = (d, sigma2, mask, k0, tol, t, theta.dtype, theta.device)
+            ctx.save_for_backward(s)
+            return s
+
+        @staticmethod
+        def backward(ctx, g):
+            (s,) = ctx.saved_tensors
+            d, sigma2, mask, k0, tol, t, dtype, device = ctx.args
+            _, v = wf_wiener_vjp(d, sigma2, mask, t[0], t[1], k0, t[2], g.contiguous().float(), s_w=s, tol=tol)
+            return torch.as_tensor(v, dtype=dtype, device=device), None, None, None, None, None
+
+    return WienerMap
+
+
+_WienerMap = None
+
+
+def wiener_map(theta, d, sigma2, mask, k0: float, tol: float = 1e-7):
+    """Differentiable Wiener filter as a function of theta = (amp, slope, alpha) (see WienerMap)."""
+    global _WienerMap
+    if _WienerMap is None:
+        _WienerMap = _make_wiener_map_function()
+    return _WienerMap.apply(theta, d, sigma2, mask, k0, tol)

@@ -81,3 +81,53 @@ def test_autograd_function_returns_the_gradient():
     r = wf.wf_loglike_grad(dev[0], dev[1], dev[2], 1.1, -2.0, 1.0 / 16, 1.2, n_probes=64, seed=9, tol=1e-6)
     np.testing.assert_allclose(theta.grad.numpy(), r.grad, rtol=1e-12)
     assert abs(q.item() - r.quad) < 1e-12 * abs(r.quad)
+
+
+# ---------------------------------------------------------------------------------------------------
+# Wiener-map vector-Jacobian product (one adjoint solve; C is symmetric)
+# ---------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("H", [16, 32])
+def test_wiener_vjp_matches_dense_oracle(H):
+    p = synth.make_problem(H, seed=H + 1, mask_frac=0.1, slope=-2.0, k0=1.0 / H, sigma2=(0.05, 0.3))
+    amp, slope, k0, alpha = 1.3, -1.8, 1.0 / H, 0.9
+    g = np.random.default_rng(H).standard_normal((H, H)).astype(np.float32)
+    dev = to_dev(p)
+    s, v = wf.wf_wiener_vjp(dev[0], dev[1], dev[2], amp, slope, k0, alpha, torch.from_numpy(g).cuda(), tol=3e-8)
+    s_ref = LL.wiener_param_dense(p.d, p.Ndiag, p.mask, amp, slope, k0, alpha)
+    v_ref = LL.wiener_vjp_dense(p.d, p.Ndiag, p.mask, amp, slope, k0, alpha, g)
+    assert rel(s.cpu().numpy(), s_ref) < 1e-6
+    np.testing.assert_allclose(v, v_ref, rtol=1e-4, atol=1e-6 * np.abs(v_ref).max())
+
+
+def test_wiener_vjp_matches_finite_differences_256():
+    rng = np.random.default_rng(5)
+    H = 256
+    amp, slope, alpha = float(rng.uniform(0.5, 2)), float(rng.uniform(-2.5, -1.5)), 1.0
+    k0 = 1.0 / H
+    p = synth.make_problem(H, seed=2, mask_frac=0.1, slope=slope, amp=amp, k0=k0, sigma2=(0.01, 0.2))
+    dev = to_dev(p)
+    g = torch.from_numpy(rng.standard_normal((H, H)).astype(np.float32)).cuda()
+    _, v = wf.wf_wiener_vjp(dev[0], dev[1], dev[2], amp, slope, k0, alpha, g, tol=3e-8)
+    th = np.array([amp, slope, alpha])
+    gd = g.double()
+    for i in range(3):
+        h = 1e-3 * max(1.0, abs(th[i]))
+        tp, tm = th.copy(), th.copy()
+        tp[i] += h
+        tm[i] -= h
+        sp, _ = wf.wf_wiener_vjp(dev[0], dev[1], dev[2], tp[0], tp[1], k0, tp[2], tol=3e-8)
+        sm, _ = wf.wf_wiener_vjp(dev[0], dev[1], dev[2], tm[0], tm[1], k0, tm[2], tol=3e-8)
+        fd = float((gd * (sp.double() - sm.double())).sum()) / (2 * h)
+        assert abs(v[i] - fd) < 1e-3 * abs(fd) + 1e-6, (i, v[i], fd)
+
+
+def test_wiener_map_autograd_uses_the_checkpointed_forward():
+    p = _prob16(11)
+    dev = to_dev(p)
+    g = torch.from_numpy(np.random.default_rng(2).standard_normal((16, 16)).astype(np.float32)).cuda()
+    theta = torch.tensor([0.9, -1.6, 1.1], dtype=torch.float64, requires_grad=True)
+    s = wf.wiener_map(theta, dev[0], dev[1], dev[2], 1.0 / 16, 3e-8)
+    (s.double() * g.double()).sum().backward()
+    s2, v = wf.wf_wiener_vjp(dev[0], dev[1], dev[2], 0.9, -1.6, 1.0 / 16, 1.1, g, tol=3e-8)
+    assert rel(s.detach().cpu().numpy(), s2.cpu().numpy()) < 1e-7
+    np.testing.assert_allclose(theta.grad.numpy(), v, rtol=1e-6)
