@@ -14,6 +14,9 @@ Printed JSON line (rank 0):
              its event-timed duration, against the FP32 peak derived from the SM count and max clock
   cpu_baseline  the FP64 oracle on the host cores, on a bounded sample of the same workload
   batched_vs_plain  the 1024-chain launch against one chain per launch
+  batch_mixed_sizes 4096 images of mixed sizes (40% 64^2, 40% 128^2, 15% 256^2, 5% 512^2), each a Wiener
+             solve to 1e-5 plus 64 samples, as one CUDA-graph replay with autotuned launch shapes, against
+             one image per call
 
 ``--impl reference`` times the oracle itself (the reference arm for this build) and prints the same line.
 Multi-GPU (torchrun): every rank runs the same workload on different chains (replicas, weak scaling).
@@ -55,7 +58,8 @@ def parse():
     ap.add_argument("--impl", default="wf", choices=["wf", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the plain and single-chain measurements")
+    ap.add_argument("--no-extras", action="store_true", help="skip the plain, single-chain and batch measurements")
+    ap.add_argument("--no-batch", action="store_true", help="skip the mixed-size batch measurement")
     ap.add_argument("--chains", type=int, default=N_CHAINS, help="profiling only: chains per step")
     ap.add_argument("--samples", type=int, default=N_SAMPLES, help="profiling only: samples per chain")
     return ap.parse_args()
@@ -219,6 +223,67 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def batch_mixed(dev, n_images: int = 4096, n_samples: int = 64, n_plain: int = 64):
+    """Mixed-size batch: Wiener solve to 1e-5 plus n_samples samples per image, all images in one graph
+    replay (launch shapes autotuned on a 1/8 subset), against the same work one image per call."""
+    import torch
+    from paper_1810_02821_gb300 import synth, wf
+    probs = synth.config_batch(n_images, seed=0)
+    imgs = [wf.BatchImage(*[torch.from_numpy(x).to(dev) for x in (q.d, q.Ndiag, q.mask, q.Pk)], seed=i, chain=i)
+            for i, q in enumerate(probs)]
+    sizes = [q.d.shape[0] for q in probs]
+    del probs
+    stream = torch.cuda.current_stream()
+
+    def replay_ms(g, reps=2):
+        g.launch()
+        g.results(allow_not_converged=True)                 # warm-up replay
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            g.launch(stream)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    with wf.BatchGraph(imgs, n_samples=n_samples, tol=1e-5) as g:
+        default_ms = replay_ms(g)
+    tuned, _ = wf.wf_batch_autotune(imgs[: max(1, n_images // 8)], n_samples=n_samples, reps=1, tol=1e-5)
+    with wf.BatchGraph(imgs, n_samples=n_samples, tol=1e-5, **tuned) as g:
+        ms = replay_ms(g)
+        g.results(allow_not_converged=True)
+    ok = sum(im.status == 0 for im in imgs)
+    flops = sum((im.iters + n_samples) * 5.0 * h * h * math.log2(h * h) for im, h in zip(imgs, sizes))
+    pix = sum(h * h for h in sizes)
+    # the same work one image per call: Wiener solve, then the samples from it
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(n_plain):
+        im = imgs[i]
+        r = wf.wf_solve_ex(im.d, im.Ndiag, im.mask, im.Pk, tol=1e-5, allow_not_converged=True)
+        wf.wf_sample_ex(im.d, im.Ndiag, im.mask, im.Pk, seed=i, n_samples=n_samples, chain_offset=i, init_s=r.s,
+                        out=im.out_samples.unsqueeze(0))
+    torch.cuda.synchronize()
+    plain_ms_per_image = (time.perf_counter() - t0) * 1e3 / n_plain
+    plain_pix = sum(sizes[:n_plain])
+    counts = {f"{h}x{h}": sizes.count(h) for h in sorted(set(sizes))}
+    achieved = flops / (ms / 1e3) / 1e12
+    return {
+        "workload": f"{n_images} images {counts}, Wiener solve to 1e-5 + {n_samples} samples each, one graph replay",
+        "ms": ms, "images_per_s": n_images / (ms / 1e3), "samples_per_s": n_images * n_samples / (ms / 1e3),
+        "pixel_samples_per_s": pix * n_samples / (ms / 1e3), "solves_ok": ok,
+        "mean_solve_sweeps": statistics.mean(im.iters for im in imgs),
+        "untuned_ms": default_ms, "tuned_launch_shape": tuned,
+        "plain_one_image_per_call_ms_per_image": plain_ms_per_image,
+        "speedup_vs_plain": plain_ms_per_image * n_images / ms,
+        "plain_sample_note": f"first {n_plain} images (mixed sizes) timed one call each, scaled to the batch",
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS,
+                     "flops": flops, "flops_note": "5 n log2 n per solve or sample sweep (level norms excluded)"},
+        "output_bytes": pix * n_samples * 4, "plain_pixels_timed": plain_pix,
+    }
+
+
 def main():
     global N_CHAINS, N_SAMPLES
     a = parse()
@@ -323,6 +388,14 @@ def main():
 
     if rank != 0:
         return
+    batch = None
+    if not a.no_extras and not a.no_batch:
+        try:
+            del out
+            torch.cuda.empty_cache()
+            batch = batch_mixed(dev)
+        except Exception as ex:  # reported, never fatal for the headline line
+            batch = {"error": f"{type(ex).__name__}: {ex}"}
     kms = statistics.mean(kern_ms)
     flops = FLOPS_PER_SWEEP * N_CHAINS * N_SAMPLES
     achieved = flops / (kms / 1e3) / 1e12
@@ -343,6 +416,7 @@ def main():
         "batched_vs_plain": ({"batched": value, "plain_one_chain_per_launch": plain, "speedup": value / plain,
                               "plain_chains_timed": n_plain} if plain else None),
         "single_chain_sweeps_per_s": single,
+        "batch_mixed_sizes": batch,
         "clocks": clk.summary(),
         "gpu_launches": 3 * a.steps,
     }

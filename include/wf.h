@@ -165,11 +165,48 @@ typedef struct {
   int32_t level_max, check, max_iter;
   int32_t n_samples;   /* samples per image (>= 0) */
   int32_t large_streams; /* concurrent pipelines for images above 128 x 128 (>= 1) */
+  int32_t small_grid_pct; /* launch shape: persistent CTAs of each size class up to 128 x 128, in percent of
+                             the occupancy limit (1..100; 0 = 100) */
+  int32_t large_grid_pct; /* launch shape: CTAs of each cooperative launch for larger images, in percent of
+                             the co-resident limit (1..100; 0 = 100); smaller grids let pipelines overlap */
   int32_t reserved;
 } wf_batch_opts;
 
 void wf_batch_opts_default(wf_batch_opts* o);
 wf_status wf_batch_run(wf_batch_item* items, int32_t n_items, const wf_batch_opts* opts, wf_stream_t stream);
+
+/*
+ * The batched form recorded once as a CUDA graph and replayed. wf_batch_graph_create validates the items
+ * and options exactly as wf_batch_run, allocates the batch's scratch for the graph's lifetime (device
+ * memory, freed by wf_batch_graph_destroy), uploads the item table and captures the whole batch -- the
+ * resets of the work counters and statuses, one persistent launch per size class up to 128 x 128 and the
+ * cooperative pipelines of the larger images, forked over streams and joined -- into one graph.
+ *   - wf_batch_graph_launch enqueues one replay on `stream` and returns without waiting. Every replay
+ *     recomputes every item from its inputs as they are in device memory when it runs (the pointers are
+ *     fixed at creation). Replays share the graph's scratch: launch them on one stream (or order them).
+ *   - wf_batch_graph_results waits for `stream` and copies each item's status, iters and resid of the last
+ *     finished replay into items[0 .. n_items-1] (n_items must equal the created count); its return value
+ *     is that of wf_batch_run.
+ *   - creation runs a stream capture on a private stream; the device current at creation must be current
+ *     for the other calls.
+ */
+typedef struct wf_batch_graph_s* wf_batch_graph;
+wf_status wf_batch_graph_create(const wf_batch_item* items, int32_t n_items, const wf_batch_opts* opts,
+                                wf_batch_graph* out);
+wf_status wf_batch_graph_launch(wf_batch_graph g, wf_stream_t stream);
+wf_status wf_batch_graph_results(wf_batch_graph g, wf_batch_item* items, int32_t n_items, wf_stream_t stream);
+void wf_batch_graph_destroy(wf_batch_graph g);
+
+/*
+ * Launch-shape autotuner of the batched form. Starting from *opts, it times graph replays of this batch
+ * (one warm-up and `reps` timed replays per candidate, CUDA events on `stream`) and keeps, one knob at a
+ * time, the fastest large_grid_pct in {100, 50, 25, 12}, large_streams in {2, 4, 8, 16} (when the batch has
+ * images above 128 x 128) and small_grid_pct in {100, 50, 25}; the chosen values are written back to *opts and the
+ * best replay time to *best_ms (HOST, may be NULL). The items' outputs are overwritten by the trial runs.
+ * A representative subset of a large batch tunes faster than the whole batch.
+ */
+wf_status wf_batch_autotune(const wf_batch_item* items, int32_t n_items, wf_batch_opts* opts, int32_t reps,
+                            double* best_ms, wf_stream_t stream);
 
 /*
  * Weighted spectral power: out[f * nw + j] = sum_k w_j(k) |(U v_f)_k|^2 over the full spectrum, with

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <mutex>
 #include <vector>
 
@@ -57,8 +58,9 @@ wf_status cuda_fail(cudaError_t e) {
 // set-up kernels
 // ---------------------------------------------------------------------------------------------
 // One block: tau = min observed Ndiag (or the caller's), max_k P_k, input checks, lambda_0, levels.
-__global__ void k_prep(const float* __restrict__ d, const float* __restrict__ Ndiag, const uint8_t* __restrict__ mask,
-                       const float* __restrict__ Pk, int H, int W, double tau_user, double eta, wf::Scalars* sc) {
+__device__ void prep_block(const float* __restrict__ d, const float* __restrict__ Ndiag,
+                           const uint8_t* __restrict__ mask, const float* __restrict__ Pk, int H, int W,
+                           double tau_user, double eta, wf::Scalars* sc) {
   __shared__ float s_min[32], s_max[32];
   __shared__ int s_obs[32], s_bad[32], s_neg[32];
   float vmin = INFINITY, vmax = 0.0f;
@@ -100,6 +102,11 @@ __global__ void k_prep(const float* __restrict__ d, const float* __restrict__ Nd
   }
   wf::Scalars r = wf::make_scalars(vmin, total_obs, vmax, bad, neg, tau_user, eta);
   *sc = r;
+}
+
+__global__ void k_prep(const float* __restrict__ d, const float* __restrict__ Ndiag, const uint8_t* __restrict__ mask,
+                       const float* __restrict__ Pk, int H, int W, double tau_user, double eta, wf::Scalars* sc) {
+  prep_block(d, Ndiag, mask, Pk, H, W, tau_user, eta, sc);
 }
 
 // Per-pixel tables ([W][H], x-major so that row threads read consecutive addresses) and the
@@ -639,12 +646,12 @@ cudaError_t launch_batch_any(int H, const wf::BatchArgs& b, cudaStream_t st) {
   }
   return cudaErrorInvalidValue;
 }
-cudaError_t batch_grid_any(int H, int n, int* g) {
+cudaError_t batch_grid_any(int H, int n, int pct, int* g) {
   switch (H) {
-    case 16: return wf::batch_grid<16>(n, g);
-    case 32: return wf::batch_grid<32>(n, g);
-    case 64: return wf::batch_grid<64>(n, g);
-    case 128: return wf::batch_grid<128>(n, g);
+    case 16: return wf::batch_grid<16>(n, pct, g);
+    case 32: return wf::batch_grid<32>(n, pct, g);
+    case 64: return wf::batch_grid<64>(n, pct, g);
+    case 128: return wf::batch_grid<128>(n, pct, g);
   }
   return cudaErrorInvalidValue;
 }
@@ -658,108 +665,174 @@ long long batch_slot_any(int H) {
   return 0;
 }
 
-// One large image (H >= 256) of a batch on stream st: tables, level norms, cooled solve, samples from
-// s_W, status into res. Scratch `b` (carved by the caller) is reused by the images of the same stream.
-struct LargeScratch {
-  char* base = nullptr;
-  size_t o_sc, o_bar, o_aq, o_dn, o_fg, o_tr, o_tc, o_tw, o_bn, o_acc, o_st, o_prev, o_sw, o_z, total;
+// Large images (H >= 256) of a batch: the images of a size class are split into chunks, and every chunk
+// is one cooperative launch of k_gbatch with one field per image (see wf_gbatch.cuh). Per-field buffers:
+// pixel tables aq, dn [n], mode table fg [nm], state Z and previous Wiener iterate [H][W/2].
+struct GBChunk {
+  int H = 0, stream = 0;
+  std::vector<int> items;  // batch item indices
+  size_t o_fields = 0, o_idx = 0, o_sc = 0, o_state = 0, o_acc = 0, o_bn = 0, o_active = 0, o_bar = 0, o_tr = 0,
+         o_tc = 0, o_tw = 0, o_data = 0, per_field = 0;
+  size_t f_aq = 0, f_dn = 0, f_fg = 0, f_z = 0, f_prev = 0;
 };
-LargeScratch large_layout(int H) {
+
+void layout_chunk(GBChunk& c, Carve& cv) {
+  const int H = c.H, F = int(c.items.size());
   const size_t n = size_t(H) * H, nm = size_t(H) * (H / 2 + 1), nz = size_t(H) * (H / 2);
-  Carve cv;
-  LargeScratch L;
-  L.o_sc = cv.take<wf::Scalars>(1);
-  L.o_bar = cv.take<wf::GridBar>(3);
-  L.o_aq = cv.take<float2>(n);
-  L.o_dn = cv.take<float2>(n);
-  L.o_fg = cv.take<float2>(nm);
-  L.o_tr = cv.take<float2>(H / 2);
-  L.o_tc = cv.take<float2>(H);
-  L.o_tw = cv.take<float2>(H / 2);
-  L.o_bn = cv.take<double>(wf::kMaxLevels);
-  L.o_acc = cv.take<double>(2);
-  L.o_st = cv.take<wf::SolveStatus>(1);
-  L.o_prev = cv.take<float2>(nz);
-  L.o_sw = cv.take<float>(n);
-  L.o_z = cv.take<float2>(nz * size_t(wf::kMaxLevels));
-  L.total = cv.off;
-  return L;
+  c.o_fields = cv.take<wf::GBField>(F);
+  c.o_idx = cv.take<int>(F);
+  c.o_sc = cv.take<wf::Scalars>(F);
+  c.o_state = cv.take<wf::GBState>(2 * size_t(F));
+  c.o_acc = cv.take<double>(2 * size_t(F));
+  c.o_bn = cv.take<double>(size_t(F) * wf::kMaxLevels);
+  c.o_active = cv.take<int>(1);
+  c.o_bar = cv.take<wf::GridBar>(1);
+  c.o_tr = cv.take<float2>(H / 2);
+  c.o_tc = cv.take<float2>(H);
+  c.o_tw = cv.take<float2>(H / 2);
+  Carve f;
+  c.f_aq = f.take<float2>(n);
+  c.f_dn = f.take<float2>(n);
+  c.f_fg = f.take<float2>(nm);
+  c.f_z = f.take<float2>(nz);
+  c.f_prev = f.take<float2>(nz);
+  c.per_field = f.off;
+  c.o_data = cv.take<char>(c.per_field * size_t(F));
 }
 
-wf_status run_large_item(const wf::BatchItem& it, int W, const wf_batch_opts& o, const LargeScratch& L,
-                         wf::BatchResult* res, cudaStream_t st) {
-  const int H = it.H;
-  const size_t n = size_t(H) * W, nm = size_t(H) * (W / 2 + 1);
-  char* b = L.base;
-  auto* sc = reinterpret_cast<wf::Scalars*>(b + L.o_sc);
-  auto* bar = reinterpret_cast<wf::GridBar*>(b + L.o_bar);
-  WF_CUDA(cudaMemsetAsync(bar, 0, 3 * sizeof(wf::GridBar), st));
-  WF_CUDA(cudaMemsetAsync(b + L.o_bn, 0, wf::kMaxLevels * sizeof(double), st));
-  WF_CUDA(cudaMemsetAsync(b + L.o_acc, 0, 2 * sizeof(double), st));
-  WF_CUDA(cudaMemsetAsync(b + L.o_st, 0, sizeof(wf::SolveStatus), st));
-  k_prep<<<1, 1024, 0, st>>>(it.d, it.Ndiag, it.mask, it.Pk, H, W, o.tau, o.eta, sc);
+// device descriptors of a chunk's fields (host side, from the scratch base address)
+std::vector<wf::GBField> chunk_fields(const GBChunk& c, const std::vector<wf::BatchItem>& items, char* b) {
+  std::vector<wf::GBField> v(c.items.size());
+  for (size_t f = 0; f < c.items.size(); ++f) {
+    const wf::BatchItem& it = items[c.items[f]];
+    char* base = b + c.o_data + f * c.per_field;
+    wf::GBField& g = v[f];
+    g.aq = reinterpret_cast<const float2*>(base + c.f_aq);
+    g.dn = reinterpret_cast<const float2*>(base + c.f_dn);
+    g.fg = reinterpret_cast<const float2*>(base + c.f_fg);
+    g.Pk = it.Pk;
+    g.Z = reinterpret_cast<float2*>(base + c.f_z);
+    g.prev = reinterpret_cast<float2*>(base + c.f_prev);
+    g.out_wf = it.out_wf;
+    g.out_samples = it.out_samples;
+    g.chain = it.chain;
+    g.key0 = uint32_t(it.seed & 0xffffffffu);
+    g.key1 = uint32_t(it.seed >> 32);
+    g.item = c.items[f];
+  }
+  return v;
+}
+
+// per-field set-up: one block per field (as k_prep)
+__global__ void k_prep_fields(const wf::BatchItem* __restrict__ items, const int* __restrict__ idx, int H,
+                              double tau_user, double eta, wf::Scalars* sc) {
+  const wf::BatchItem it = items[idx[blockIdx.x]];
+  prep_block(it.d, it.Ndiag, it.mask, it.Pk, H, H, tau_user, eta, sc + blockIdx.x);
+}
+
+// per-field tables (as k_tables), grid-stride over fields x (n + nm)
+__global__ void k_tables_fields(const wf::BatchItem* __restrict__ items, const int* __restrict__ idx,
+                                const wf::GBField* __restrict__ fields, const wf::Scalars* __restrict__ sc, int F,
+                                int H) {
+  const long long n = (long long)H * H, nm = (long long)H * (H / 2 + 1), per = n + nm;
+  const double inv_n = 1.0 / double(n);
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < per * F;
+       g += (long long)gridDim.x * blockDim.x) {
+    const int f = int(g / per);
+    const long long i = g % per;
+    const wf::Scalars s = sc[f];
+    if (s.status != 0) continue;
+    const wf::BatchItem it = items[idx[f]];
+    const wf::GBField fd = fields[f];
+    if (i < n) {
+      const int y = int(i / H), x = int(i % H);
+      float2 a2, d2;
+      wf::table_pixel(it.d[i], it.Ndiag[i], it.mask[i] == 0, s.tau, &a2, &d2);
+      const_cast<float2*>(fd.aq)[x * H + y] = a2;
+      const_cast<float2*>(fd.dn)[x * H + y] = d2;
+    } else {
+      const long long j = i - n;
+      const_cast<float2*>(fd.fg)[j] = wf::table_mode(it.Pk[j], s.tau, inv_n);
+    }
+  }
+}
+
+// zero the schedule state, residual sums and level norms; active = F
+__global__ void k_gb_init(wf::GBState* state, double* acc, double* bnorm, int* active, wf::GridBar* bar, int F) {
+  const long long words = 2LL * F * (sizeof(wf::GBState) / 4);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < words; i += (long long)gridDim.x * blockDim.x)
+    reinterpret_cast<int*>(state)[i] = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 2LL * F; i += (long long)gridDim.x * blockDim.x)
+    acc[i] = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)F * wf::kMaxLevels;
+       i += (long long)gridDim.x * blockDim.x)
+    bnorm[i] = 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *active = F;
+    bar->count = 0;
+    bar->gen = 0;
+    bar->err = 0;
+    bar->pad = 0;
+  }
+}
+
+cudaError_t launch_gbatch_any(int H, const wf::GBArgs& a, cudaStream_t st) {
+  switch (H) {
+    case 256: return wf::launch_gbatch<256>(a, st);
+    case 512: return wf::launch_gbatch<512>(a, st);
+    case 1024: return wf::launch_gbatch<1024>(a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// set-up and launch of one chunk on stream st (item table uploaded, descriptors in place)
+wf_status run_chunk(const GBChunk& c, const wf::BatchItem* d_items, wf::BatchResult* d_res, const wf_batch_opts& o,
+                    char* b, cudaStream_t st) {
+  const int F = int(c.items.size()), H = c.H;
+  auto* fields = reinterpret_cast<wf::GBField*>(b + c.o_fields);
+  auto* idx = reinterpret_cast<int*>(b + c.o_idx);
+  auto* sc = reinterpret_cast<wf::Scalars*>(b + c.o_sc);
+  auto* state = reinterpret_cast<wf::GBState*>(b + c.o_state);
+  auto* acc = reinterpret_cast<double*>(b + c.o_acc);
+  auto* bn = reinterpret_cast<double*>(b + c.o_bn);
+  auto* active = reinterpret_cast<int*>(b + c.o_active);
+  auto* bar = reinterpret_cast<wf::GridBar*>(b + c.o_bar);
+  const long long init_words = 2LL * F * 16;
+  k_gb_init<<<int((init_words + 255) / 256 < 1024 ? (init_words + 255) / 256 : 1024), 256, 0, st>>>(state, acc, bn,
+                                                                                                   active, bar, F);
   WF_CUDA(cudaGetLastError());
-  k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(it.d, it.Ndiag, it.mask, it.Pk, H, W, sc,
-                                                       reinterpret_cast<float2*>(b + L.o_aq),
-                                                       reinterpret_cast<float2*>(b + L.o_dn),
-                                                       reinterpret_cast<float2*>(b + L.o_fg));
+  k_prep_fields<<<F, 1024, 0, st>>>(d_items, idx, H, o.tau, o.eta, sc);
   WF_CUDA(cudaGetLastError());
-  k_twiddles<<<8, 256, 0, st>>>(H, W, reinterpret_cast<float2*>(b + L.o_tr), reinterpret_cast<float2*>(b + L.o_tc),
-                                reinterpret_cast<float2*>(b + L.o_tw));
+  const long long tab = (long long)F * (size_t(H) * H + size_t(H) * (H / 2 + 1));
+  k_tables_fields<<<int((tab + 255) / 256 < 4096 ? (tab + 255) / 256 : 4096), 256, 0, st>>>(d_items, idx, fields, sc,
+                                                                                           F, H);
   WF_CUDA(cudaGetLastError());
-  float* sw = it.out_wf ? it.out_wf : reinterpret_cast<float*>(b + L.o_sw);
-  wf::GlobalArgs a{};
-  a.Z = reinterpret_cast<float2*>(b + L.o_z);
-  a.tw_row = reinterpret_cast<float2*>(b + L.o_tr);
-  a.tw_col = reinterpret_cast<float2*>(b + L.o_tc);
-  a.tw_real = reinterpret_cast<float2*>(b + L.o_tw);
-  a.aq = reinterpret_cast<float2*>(b + L.o_aq);
-  a.fg = reinterpret_cast<float2*>(b + L.o_fg);
-  a.dn = reinterpret_cast<float2*>(b + L.o_dn);
-  a.Pk = it.Pk;
+  k_twiddles<<<8, 256, 0, st>>>(H, H, reinterpret_cast<float2*>(b + c.o_tr), reinterpret_cast<float2*>(b + c.o_tc),
+                                reinterpret_cast<float2*>(b + c.o_tw));
+  WF_CUDA(cudaGetLastError());
+  wf::GBArgs a{};
+  a.fields = fields;
   a.sc = sc;
-  a.eta = o.eta;
-  // level norms (fields = levels; fields past the schedule are skipped on the device)
-  a.mode = 2;
+  a.state = state;
+  a.acc = acc;
+  a.bnorm = bn;
+  a.res = d_res;
+  a.active = active;
   a.bar = bar;
-  a.n_fields = wf::kMaxLevels;
-  a.bnorm_out = reinterpret_cast<double*>(b + L.o_bn);
-  cudaError_t e = launch_global_any(H, a, st, nullptr);
-  if (e != cudaSuccess) return cuda_fail(e);
-  // cooled solve
-  a.mode = 1;
-  a.bar = bar + 1;
-  a.n_fields = 1;
-  a.bnorm2 = reinterpret_cast<double*>(b + L.o_bn);
-  a.acc = reinterpret_cast<double*>(b + L.o_acc);
-  a.prev = reinterpret_cast<float2*>(b + L.o_prev);
-  a.st = reinterpret_cast<wf::SolveStatus*>(b + L.o_st);
-  a.out = sw;
+  a.tw_row = reinterpret_cast<float2*>(b + c.o_tr);
+  a.tw_col = reinterpret_cast<float2*>(b + c.o_tc);
+  a.tw_real = reinterpret_cast<float2*>(b + c.o_tw);
+  a.F = F;
   a.tol = o.tol;
+  a.eta = o.eta;
   a.level_tol = o.level_tol;
   a.max_iter = o.max_iter;
   a.level_max = o.level_max;
   a.check = o.check;
-  if ((e = launch_global_any(H, a, st, nullptr)) != cudaSuccess) return cuda_fail(e);
-  WF_CUDA(cudaMemcpyAsync(res, a.st, sizeof(wf::SolveStatus), cudaMemcpyDeviceToDevice, st));
-  // samples from s_W
-  if (o.n_samples > 0 && it.out_samples) {
-    a.mode = 0;
-    a.bar = bar + 2;
-    a.init_s = sw;
-    a.init_stride = 0;
-    a.out = it.out_samples;
-    a.n_samples = o.n_samples;
-    a.n_fields = 1;
-    a.n_sweeps = o.n_samples;
-    a.burn_in = 0;
-    a.thin = 1;
-    a.chain0 = it.chain;
-    a.step0 = 0;
-    a.key0 = uint32_t(it.seed & 0xffffffffu);
-    a.key1 = uint32_t(it.seed >> 32);
-    if ((e = launch_global_any(H, a, st, nullptr)) != cudaSuccess) return cuda_fail(e);
-  }
+  a.n_samples = o.n_samples;
+  a.grid_pct = o.large_grid_pct;
+  const cudaError_t e = launch_gbatch_any(H, a, st);
+  if (e != cudaSuccess) return cuda_fail(e);
   return WF_OK;
 }
 
@@ -781,101 +854,127 @@ void wf_batch_opts_default(wf_batch_opts* o) {
   o->large_streams = 8;
 }
 
-wf_status wf_batch_run(wf_batch_item* items, int32_t n_items, const wf_batch_opts* opts, wf_stream_t stream) {
-  wf_batch_opts o;
-  wf_batch_opts_default(&o);
-  if (opts) o = *opts;
-  if (n_items < 0 || (n_items > 0 && !items)) return WF_ERR_ARG;
-  if (!(o.tol >= 0.0) || !(o.eta > 0.0 && o.eta < 1.0) || o.level_max < 1 || o.check < 1 || o.max_iter < 1 ||
-      o.n_samples < 0 || o.large_streams < 1)
-    return WF_ERR_ARG;
-  if (n_items == 0) return WF_OK;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const int sizes[7] = {16, 32, 64, 128, 256, 512, 1024};
-  std::vector<std::vector<int>> cls(7);
-  std::vector<wf::BatchItem> dev_items(n_items);
+}  // extern "C"
+
+namespace {
+
+const int kBatchSizes[7] = {16, 32, 64, 128, 256, 512, 1024};
+
+// Host-side plan of a batch: validated items grouped by size class and the layout of its one scratch block.
+struct BatchPlan {
+  int n_items = 0;
+  wf_batch_opts o{};
+  std::vector<std::vector<int>> cls;
+  std::vector<wf::BatchItem> dev_items;
+  std::vector<int> order;
+  size_t o_items = 0, o_order = 0, o_res = 0, o_q = 0, o_slot[4] = {0, 0, 0, 0}, bytes = 0;
+  int nls = 0;                  // streams of the large-image chunks
+  std::vector<GBChunk> chunks;  // large images: one cooperative launch each
+};
+
+bool batch_opts_ok(const wf_batch_opts& o) {
+  return o.tol >= 0.0 && o.eta > 0.0 && o.eta < 1.0 && o.level_max >= 1 && o.check >= 1 && o.max_iter >= 1 &&
+         o.n_samples >= 0 && o.large_streams >= 1 && o.small_grid_pct >= 0 && o.small_grid_pct <= 100 &&
+         o.large_grid_pct >= 0 && o.large_grid_pct <= 100;
+}
+
+wf_status plan_batch(const wf_batch_item* items, int n_items, const wf_batch_opts& o, BatchPlan* p) {
+  p->n_items = n_items;
+  p->o = o;
+  p->cls.assign(7, {});
+  p->dev_items.resize(n_items);
   for (int i = 0; i < n_items; ++i) {
     const wf_batch_item& it = items[i];
     if (!it.d || !it.Ndiag || !it.mask || !it.Pk) return WF_ERR_ARG;
     if (!size_ok(it.H, it.W)) return WF_ERR_SHAPE;
     if (o.n_samples > 0 && !it.out_samples) return WF_ERR_ARG;
     int c = 0;
-    while (sizes[c] != it.H) ++c;
-    cls[c].push_back(i);
-    dev_items[i] = wf::BatchItem{it.d, it.Ndiag, it.mask, it.Pk, it.out_wf, it.out_samples, it.seed, it.chain, it.H};
+    while (kBatchSizes[c] != it.H) ++c;
+    p->cls[c].push_back(i);
+    p->dev_items[i] = wf::BatchItem{it.d, it.Ndiag, it.mask, it.Pk, it.out_wf, it.out_samples, it.seed, it.chain, it.H};
   }
-  // one allocation: items, order, results, queues, per-class CTA slots, per-stream large scratch
+  // one block: items, order, results, queues, per-class CTA slots, per-stream large scratch
   Carve cv;
-  const size_t o_items = cv.take<wf::BatchItem>(n_items), o_order = cv.take<int>(n_items),
-               o_res = cv.take<wf::BatchResult>(n_items), o_q = cv.take<int>(8);
-  size_t o_slot[4] = {0, 0, 0, 0};
-  int grid[4] = {0, 0, 0, 0};
+  p->o_items = cv.take<wf::BatchItem>(n_items);
+  p->o_order = cv.take<int>(n_items);
+  p->o_res = cv.take<wf::BatchResult>(n_items);
+  p->o_q = cv.take<int>(8);
   for (int c = 0; c < 4; ++c) {
-    if (cls[c].empty()) continue;
-    cudaError_t e = batch_grid_any(sizes[c], int(cls[c].size()), &grid[c]);
+    if (p->cls[c].empty()) continue;
+    int grid = 0;
+    cudaError_t e = batch_grid_any(kBatchSizes[c], int(p->cls[c].size()), o.small_grid_pct, &grid);
     if (e != cudaSuccess) return cuda_fail(e);
-    o_slot[c] = cv.take<char>(size_t(grid[c]) * size_t(batch_slot_any(sizes[c])));
+    p->o_slot[c] = cv.take<char>(size_t(grid) * size_t(batch_slot_any(kBatchSizes[c])));
   }
-  int max_large = 0, n_large = 0;
-  for (int c = 4; c < 7; ++c)
-    if (!cls[c].empty()) {
-      max_large = sizes[c];
-      n_large += int(cls[c].size());
+  // large images: each size class split into up to large_streams chunks, chunk k on stream k
+  p->chunks.clear();
+  p->nls = 0;
+  for (int c = 4; c < 7; ++c) {
+    const int nc = int(p->cls[c].size());
+    if (!nc) continue;
+    const int parts = o.large_streams < nc ? o.large_streams : nc;
+    for (int k = 0; k < parts; ++k) {
+      GBChunk ch;
+      ch.H = kBatchSizes[c];
+      ch.stream = k;
+      for (int i = k * nc / parts; i < (k + 1) * nc / parts; ++i) ch.items.push_back(p->cls[c][i]);
+      layout_chunk(ch, cv);
+      p->chunks.push_back(std::move(ch));
     }
-  const int nls = n_large ? (o.large_streams < n_large ? o.large_streams : n_large) : 0;
-  LargeScratch lay{};
-  size_t o_large = 0;
-  if (nls) {
-    lay = large_layout(max_large);
-    o_large = cv.take<char>(lay.total * size_t(nls));
+    if (parts > p->nls) p->nls = parts;
   }
-  std::vector<int> order;
-  for (int c = 0; c < 7; ++c) order.insert(order.end(), cls[c].begin(), cls[c].end());
-  Scratch scr;
-  scr.st = st;
-  WF_CUDA(cudaMallocAsync(&scr.base, cv.off, st));
-  char* b = static_cast<char*>(scr.base);
-  auto* d_items = reinterpret_cast<wf::BatchItem*>(b + o_items);
-  auto* d_order = reinterpret_cast<int*>(b + o_order);
-  auto* d_res = reinterpret_cast<wf::BatchResult*>(b + o_res);
-  auto* d_q = reinterpret_cast<int*>(b + o_q);
-  WF_CUDA(cudaMemcpyAsync(d_items, dev_items.data(), n_items * sizeof(wf::BatchItem), cudaMemcpyHostToDevice, st));
-  WF_CUDA(cudaMemcpyAsync(d_order, order.data(), n_items * sizeof(int), cudaMemcpyHostToDevice, st));
-  WF_CUDA(cudaMemsetAsync(d_q, 0, 8 * sizeof(int), st));
-  WF_CUDA(cudaMemsetAsync(d_res, 0, n_items * sizeof(wf::BatchResult), st));
+  p->order.clear();
+  for (int c = 0; c < 7; ++c) p->order.insert(p->order.end(), p->cls[c].begin(), p->cls[c].end());
+  p->bytes = cv.off;
+  return WF_OK;
+}
 
-  // fork: one stream per small size class, a pool for the large images
+// Streams and events of one recorded batch (destroyed after the work, or after the capture, has ended).
+struct ForkJoin {
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> evs;
-  auto cleanup = [&]() {
+  ~ForkJoin() {
     for (auto e : evs) cudaEventDestroy(e);
     for (auto s2 : side) cudaStreamDestroy(s2);
-  };
+  }
+};
+
+// Enqueue the whole batch on `st` (work counters and statuses reset, per-class persistent launches and
+// the large-image pipelines forked over side streams, joined back into `st`). The item table and order
+// must already be in the scratch block `b`.
+wf_status record_batch(const BatchPlan& p, char* b, cudaStream_t st, ForkJoin& fj) {
+  const wf_batch_opts& o = p.o;
+  auto* d_items = reinterpret_cast<wf::BatchItem*>(b + p.o_items);
+  auto* d_order = reinterpret_cast<int*>(b + p.o_order);
+  auto* d_res = reinterpret_cast<wf::BatchResult*>(b + p.o_res);
+  auto* d_q = reinterpret_cast<int*>(b + p.o_q);
+  WF_CUDA(cudaMemsetAsync(d_q, 0, 8 * sizeof(int), st));
+  WF_CUDA(cudaMemsetAsync(d_res, 0, p.n_items * sizeof(wf::BatchResult), st));
   cudaEvent_t ready;
-  if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess) return cuda_fail(cudaGetLastError());
-  evs.push_back(ready);
-  if (cudaEventRecord(ready, st) != cudaSuccess) { cleanup(); return cuda_fail(cudaGetLastError()); }
+  WF_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+  fj.evs.push_back(ready);
+  WF_CUDA(cudaEventRecord(ready, st));
   auto new_stream = [&](cudaStream_t* out) -> cudaError_t {
     cudaError_t e = cudaStreamCreateWithFlags(out, cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
-    side.push_back(*out);
+    fj.side.push_back(*out);
     return cudaStreamWaitEvent(*out, ready, 0);
   };
   wf_status fail = WF_OK;
   int offset = 0;
   for (int c = 0; c < 4 && fail == WF_OK; ++c) {
-    if (cls[c].empty()) continue;
+    if (p.cls[c].empty()) continue;
     cudaStream_t s2;
     cudaError_t e = new_stream(&s2);
     if (e != cudaSuccess) { fail = cuda_fail(e); break; }
     wf::BatchArgs ba{};
     ba.items = d_items;
     ba.order = d_order + offset;
-    ba.n = int(cls[c].size());
+    ba.n = int(p.cls[c].size());
     ba.res = d_res;
     ba.queue = d_q + c;
-    ba.scratch = b + o_slot[c];
-    ba.slot_bytes = batch_slot_any(sizes[c]);
+    ba.scratch = b + p.o_slot[c];
+    ba.slot_bytes = batch_slot_any(kBatchSizes[c]);
     ba.tau = o.tau;
     ba.tol = o.tol;
     ba.eta = o.eta;
@@ -884,39 +983,52 @@ wf_status wf_batch_run(wf_batch_item* items, int32_t n_items, const wf_batch_opt
     ba.level_max = o.level_max;
     ba.check = o.check;
     ba.n_samples = o.n_samples;
-    if ((e = launch_batch_any(sizes[c], ba, s2)) != cudaSuccess) fail = cuda_fail(e);
-    offset += int(cls[c].size());
+    ba.grid_pct = o.small_grid_pct;
+    if ((e = launch_batch_any(kBatchSizes[c], ba, s2)) != cudaSuccess) fail = cuda_fail(e);
+    offset += int(p.cls[c].size());
   }
-  if (fail == WF_OK && nls) {
-    std::vector<cudaStream_t> pool(nls);
-    for (int k = 0; k < nls && fail == WF_OK; ++k) {
+  if (fail == WF_OK && p.nls) {
+    std::vector<cudaStream_t> pool(p.nls);
+    for (int k = 0; k < p.nls && fail == WF_OK; ++k) {
       cudaError_t e = new_stream(&pool[k]);
       if (e != cudaSuccess) fail = cuda_fail(e);
     }
-    int j = 0;
-    for (int c = 4; c < 7 && fail == WF_OK; ++c)
-      for (int idx : cls[c]) {
-        LargeScratch L = lay;
-        L.base = b + o_large + size_t(j % nls) * lay.total;
-        const wf_status r = run_large_item(dev_items[idx], sizes[c], o, L, d_res + idx, pool[j % nls]);
-        if (r != WF_OK) { fail = r; break; }
-        ++j;
-      }
+    for (size_t k = 0; k < p.chunks.size() && fail == WF_OK; ++k) {
+      const GBChunk& c = p.chunks[k];
+      fail = run_chunk(c, d_items, d_res, o, b, pool[c.stream]);
+    }
   }
-  // join
-  for (auto s2 : side) {
+  // join (also after a failure, so that a capture can end)
+  for (auto s2 : fj.side) {
     cudaEvent_t done;
     if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) continue;
-    evs.push_back(done);
+    fj.evs.push_back(done);
     cudaEventRecord(done, s2);
     cudaStreamWaitEvent(st, done, 0);
   }
-  std::vector<wf::BatchResult> hres(n_items);
-  cudaError_t e = cudaMemcpyAsync(hres.data(), d_res, n_items * sizeof(wf::BatchResult), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cleanup();
-  if (fail != WF_OK) return fail;
-  if (e != cudaSuccess) return cuda_fail(e);
+  return fail;
+}
+
+// Item table, order and the large-image field descriptors into the scratch block. The host copies stay
+// alive in `keep` until the stream has passed them.
+wf_status upload_batch(const BatchPlan& p, char* b, cudaStream_t st, std::vector<std::vector<char>>& keep) {
+  WF_CUDA(cudaMemcpyAsync(b + p.o_items, p.dev_items.data(), p.n_items * sizeof(wf::BatchItem), cudaMemcpyHostToDevice,
+                          st));
+  WF_CUDA(cudaMemcpyAsync(b + p.o_order, p.order.data(), p.n_items * sizeof(int), cudaMemcpyHostToDevice, st));
+  for (const GBChunk& c : p.chunks) {
+    const std::vector<wf::GBField> fv = chunk_fields(c, p.dev_items, b);
+    keep.emplace_back(reinterpret_cast<const char*>(fv.data()),
+                      reinterpret_cast<const char*>(fv.data()) + fv.size() * sizeof(wf::GBField));
+    WF_CUDA(cudaMemcpyAsync(b + c.o_fields, keep.back().data(), keep.back().size(), cudaMemcpyHostToDevice, st));
+    keep.emplace_back(reinterpret_cast<const char*>(c.items.data()),
+                      reinterpret_cast<const char*>(c.items.data()) + c.items.size() * sizeof(int));
+    WF_CUDA(cudaMemcpyAsync(b + c.o_idx, keep.back().data(), keep.back().size(), cudaMemcpyHostToDevice, st));
+  }
+  return WF_OK;
+}
+
+// device results -> items[].status/iters/resid (after the stream has been synchronised)
+wf_status batch_results(const std::vector<wf::BatchResult>& hres, wf_batch_item* items, int n_items) {
   wf_status first = WF_OK;
   for (int i = 0; i < n_items; ++i) {
     items[i].status = hres[i].status;
@@ -925,6 +1037,169 @@ wf_status wf_batch_run(wf_batch_item* items, int32_t n_items, const wf_batch_opt
     if (first == WF_OK && hres[i].status != WF_OK) first = wf_status(hres[i].status);
   }
   return first;
+}
+
+}  // namespace
+
+struct wf_batch_graph_s {
+  BatchPlan plan;
+  void* base = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ~wf_batch_graph_s() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (base) cudaFree(base);
+  }
+};
+
+extern "C" {
+
+wf_status wf_batch_run(wf_batch_item* items, int32_t n_items, const wf_batch_opts* opts, wf_stream_t stream) {
+  wf_batch_opts o;
+  wf_batch_opts_default(&o);
+  if (opts) o = *opts;
+  if (n_items < 0 || (n_items > 0 && !items)) return WF_ERR_ARG;
+  if (!batch_opts_ok(o)) return WF_ERR_ARG;
+  if (n_items == 0) return WF_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  BatchPlan p;
+  wf_status r = plan_batch(items, n_items, o, &p);
+  if (r != WF_OK) return r;
+  Scratch scr;
+  scr.st = st;
+  WF_CUDA(cudaMallocAsync(&scr.base, p.bytes, st));
+  char* b = static_cast<char*>(scr.base);
+  std::vector<std::vector<char>> keep;
+  if ((r = upload_batch(p, b, st, keep)) != WF_OK) return r;
+  wf_status fail;
+  {
+    ForkJoin fj;
+    fail = record_batch(p, b, st, fj);
+    std::vector<wf::BatchResult> hres(n_items);
+    cudaError_t e = cudaMemcpyAsync(hres.data(), b + p.o_res, n_items * sizeof(wf::BatchResult),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (fail != WF_OK) return fail;
+    if (e != cudaSuccess) return cuda_fail(e);
+    return batch_results(hres, items, n_items);
+  }
+}
+
+wf_status wf_batch_graph_create(const wf_batch_item* items, int32_t n_items, const wf_batch_opts* opts,
+                                wf_batch_graph* out) {
+  if (!out) return WF_ERR_ARG;
+  *out = nullptr;
+  wf_batch_opts o;
+  wf_batch_opts_default(&o);
+  if (opts) o = *opts;
+  if (n_items < 1 || !items || !batch_opts_ok(o)) return WF_ERR_ARG;
+  auto* g = new wf_batch_graph_s();
+  wf_status r = plan_batch(items, n_items, o, &g->plan);
+  cudaStream_t cs = nullptr;
+  auto fail = [&](wf_status s) {
+    if (cs) cudaStreamDestroy(cs);
+    delete g;
+    return s;
+  };
+  if (r != WF_OK) return fail(r);
+  cudaError_t e = cudaMalloc(&g->base, g->plan.bytes);
+  if (e != cudaSuccess) return fail(cuda_fail(e));
+  if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return fail(cuda_fail(e));
+  char* b = static_cast<char*>(g->base);
+  std::vector<std::vector<char>> keep;
+  if ((r = upload_batch(g->plan, b, cs, keep)) != WF_OK) return fail(r);
+  if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) return fail(cuda_fail(e));
+  if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed)) != cudaSuccess) return fail(cuda_fail(e));
+  {
+    ForkJoin fj;
+    r = record_batch(g->plan, b, cs, fj);
+    e = cudaStreamEndCapture(cs, &g->graph);
+  }
+  if (r != WF_OK) return fail(r);
+  if (e != cudaSuccess) return fail(cuda_fail(e));
+  if ((e = cudaGraphInstantiate(&g->exec, g->graph, 0)) != cudaSuccess) return fail(cuda_fail(e));
+  cudaStreamDestroy(cs);
+  *out = g;
+  return WF_OK;
+}
+
+wf_status wf_batch_graph_launch(wf_batch_graph g, wf_stream_t stream) {
+  if (!g || !g->exec) return WF_ERR_ARG;
+  WF_CUDA(cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(stream)));
+  return WF_OK;
+}
+
+wf_status wf_batch_graph_results(wf_batch_graph g, wf_batch_item* items, int32_t n_items, wf_stream_t stream) {
+  if (!g || !items || n_items != g->plan.n_items) return WF_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  std::vector<wf::BatchResult> hres(n_items);
+  WF_CUDA(cudaMemcpyAsync(hres.data(), static_cast<char*>(g->base) + g->plan.o_res,
+                          n_items * sizeof(wf::BatchResult), cudaMemcpyDeviceToHost, st));
+  WF_CUDA(cudaStreamSynchronize(st));
+  return batch_results(hres, items, n_items);
+}
+
+void wf_batch_graph_destroy(wf_batch_graph g) { delete g; }
+
+wf_status wf_batch_autotune(const wf_batch_item* items, int32_t n_items, wf_batch_opts* opts, int32_t reps,
+                            double* best_ms, wf_stream_t stream) {
+  if (!opts || !items || n_items < 1 || reps < 1) return WF_ERR_ARG;
+  if (!batch_opts_ok(*opts)) return WF_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  bool has_large = false;
+  for (int i = 0; i < n_items; ++i) has_large |= items[i].H > 128;
+  cudaEvent_t e0, e1;
+  WF_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(cudaGetLastError());
+  }
+  // time one candidate: capture, one warm-up replay, `reps` timed replays
+  auto time_opts = [&](const wf_batch_opts& c, double* ms) -> wf_status {
+    wf_batch_graph g = nullptr;
+    wf_status r = wf_batch_graph_create(items, n_items, &c, &g);
+    if (r != WF_OK) return r;
+    cudaError_t e = cudaGraphLaunch(g->exec, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    for (int k = 0; k < reps && e == cudaSuccess; ++k) e = cudaGraphLaunch(g->exec, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    wf_batch_graph_destroy(g);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *ms = double(t) / reps;
+    return WF_OK;
+  };
+  wf_batch_opts best = *opts;
+  double best_t = 0.0;
+  wf_status r = time_opts(best, &best_t);
+  auto try_knob = [&](int32_t wf_batch_opts::*knob, std::initializer_list<int> vals) {
+    for (int v : vals) {
+      if (r != WF_OK) return;
+      if (best.*knob == v) continue;
+      wf_batch_opts c = best;
+      c.*knob = v;
+      double t = 0.0;
+      r = time_opts(c, &t);
+      if (r == WF_OK && t < best_t) {
+        best_t = t;
+        best = c;
+      }
+    }
+  };
+  if (has_large) {
+    try_knob(&wf_batch_opts::large_grid_pct, {100, 50, 25, 12});
+    try_knob(&wf_batch_opts::large_streams, {2, 4, 8, 16});
+  }
+  try_knob(&wf_batch_opts::small_grid_pct, {100, 50, 25});
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (r != WF_OK) return r;
+  *opts = best;
+  if (best_ms) *best_ms = best_t;
+  return WF_OK;
 }
 
 }  // extern "C"

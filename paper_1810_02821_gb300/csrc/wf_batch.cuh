@@ -39,6 +39,7 @@ struct BatchArgs {
   double tol, eta, level_tol;
   int max_iter, level_max, check;
   int n_samples;
+  int grid_pct;      // host side: percent of the occupancy-limited persistent grid (0 or >= 100: all)
 };
 
 template <int N>

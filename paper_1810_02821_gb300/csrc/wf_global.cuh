@@ -158,6 +158,7 @@ struct GlobalArgs {
   const float* wts;
   int nw;
   double* wout;
+  int grid_pct;            // host side: percent of the co-resident grid to launch (0 or >= 100: all of it)
 };
 
 // R2C post-processing / C2R pre-processing of one padded row vector (pairs k <-> LR - k), all threads of
@@ -191,6 +192,54 @@ __device__ __forceinline__ void real_pass(float2* buf, int nrows, const float2* 
         v[padi(L - k)] = cadd(cconj(E), cmul_i(cconj(O)));
       }
     }
+  }
+  __syncthreads();
+}
+
+// Row-phase pixel update of rows y0 .. y0+RB-1 held in buf as (s[2m], s[2m+1]) pairs (then a CTA barrier):
+//   mode 0: sampler t-draw t = (1 - w) d + sqrt(w) (sqrt(w) s + sqrt(tau) xi) with the (a, q) table, Philox
+//           counter (pixel group (y W + x) / 4, step, chain, stream 0);
+//   mode 1: Wiener-filter t-update t = w (s - d) + d, w = 1 / (1 + lambda tau / N_bar) from the (d, 1/N_bar)
+//           table (rhs_mode: t = w s + lambda tau r with r in place of d);
+//   mode 2: the level right-hand side N_lambda^-1 d with N_lambda = N_bar + lt2 (s ignored).
+template <int N>
+__device__ __forceinline__ void pixel_update(int mode, float2* buf, int y0, const float2* __restrict__ aq,
+                                             const float2* __restrict__ dn, uint32_t step, uint32_t chain,
+                                             uint32_t key0, uint32_t key1, float sqrt_tau, float ltau, int rhs_mode,
+                                             float lt2) {
+  using G = GGeo<N>;
+  for (int task = threadIdx.x; task < G::RB * (G::W / 4); task += 128) {
+    const int j = task / (G::W / 4), q = task % (G::W / 4);
+    const int y = y0 + j;
+    float2* v = buf + j * G::VROW;
+    float2 p0 = v[padi(2 * q)], p1 = v[padi(2 * q + 1)];
+    float s4[4] = {p0.x, p0.y, p1.x, p1.y};
+    if (mode == 0) {
+      float z[4];
+      normals4(uint32_t(y * (G::W / 4) + q), step, chain, 0u, key0, key1, z);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float2 co = __ldg(aq + (4 * q + e) * G::H + y);
+        s4[e] = fmaf(co.y, fmaf(co.y, s4[e], sqrt_tau * z[e]), co.x);
+      }
+    } else if (mode == 1) {
+      const float g = rhs_mode ? 0.0f : 1.0f, h = rhs_mode ? ltau : 1.0f;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float2 co = __ldg(dn + (4 * q + e) * G::H + y);
+        const float w = wf_rcp(fmaf(ltau, co.y, 1.0f));
+        s4[e] = fmaf(w, fmaf(-g, co.x, s4[e]), h * co.x);
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float2 co = __ldg(dn + (4 * q + e) * G::H + y);
+        const float nbar = co.y > 0.0f ? wf_rcp(co.y) : wf_inf();
+        s4[e] = co.x / (nbar + lt2);
+      }
+    }
+    v[padi(2 * q)] = make_float2(s4[0], s4[1]);
+    v[padi(2 * q + 1)] = make_float2(s4[2], s4[3]);
   }
   __syncthreads();
 }
@@ -241,6 +290,7 @@ __device__ void row_item(const GlobalArgs& a, float2* buf, int f, int y0, int do
         reinterpret_cast<float2*>(o + (long long)(y0 + j) * G::W)[m] = buf[j * G::VROW + padi(m)];
       }
     }
+    __syncthreads();  // the pixel update below maps threads to other elements of buf
   }
   if (emit_only) {
     if (a.mode == 1) {  // Wiener filter: final state to out
@@ -254,45 +304,11 @@ __device__ void row_item(const GlobalArgs& a, float2* buf, int f, int y0, int do
   }
   // pixel-space update on 4-pixel groups (Philox group (y W + x)/4 in the sampler); mode 3 transforms
   // the field as loaded
-  const uint32_t step = a.step0 + uint32_t(done);
-  const uint32_t chain = a.chain0 + uint32_t(f);
-  for (int task = threadIdx.x; task < (a.mode == 3 ? 0 : G::RB * (G::W / 4)); task += nthr) {
-    const int j = task / (G::W / 4), q = task % (G::W / 4);
-    const int y = y0 + j;
-    float2* v = buf + j * G::VROW;
-    float2 p0 = v[padi(2 * q)], p1 = v[padi(2 * q + 1)];
-    float s4[4] = {p0.x, p0.y, p1.x, p1.y};
-    if (a.mode == 0) {
-      float z[4];
-      normals4(uint32_t(y * (G::W / 4) + q), step, chain, 0u, a.key0, a.key1, z);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float2 co = __ldg(a.aq + (4 * q + e) * G::H + y);
-        s4[e] = fmaf(co.y, fmaf(co.y, s4[e], sc.sqrt_tau * z[e]), co.x);
-      }
-    } else if (a.mode == 1) {
-      const float g = a.rhs_mode ? 0.0f : 1.0f, h = a.rhs_mode ? ltau : 1.0f;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float2 co = __ldg(a.dn + (4 * q + e) * G::H + y);
-        const float w = wf_rcp(fmaf(ltau, co.y, 1.0f));
-        s4[e] = fmaf(w, fmaf(-g, co.x, s4[e]), h * co.x);
-      }
-    } else {
-      // level norms: right-hand side N_lambda^-1 d of level f
-      const double lam = level_lambda(sc, f, a.eta);
-      const float lt2 = float(lam * sc.tau);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float2 co = __ldg(a.dn + (4 * q + e) * G::H + y);
-        const float nbar = co.y > 0.0f ? wf_rcp(co.y) : wf_inf();
-        s4[e] = co.x / (nbar + lt2);
-      }
-    }
-    v[padi(2 * q)] = make_float2(s4[0], s4[1]);
-    v[padi(2 * q + 1)] = make_float2(s4[2], s4[3]);
-  }
-  __syncthreads();
+  if (a.mode != 3)
+    pixel_update<N>(a.mode, buf, y0, a.aq, a.dn, a.step0 + uint32_t(done), a.chain0 + uint32_t(f), a.key0, a.key1,
+                    sc.sqrt_tau, ltau, a.rhs_mode, a.mode == 2 ? float(level_lambda(sc, f, a.eta) * sc.tau) : 0.f);
+  else
+    __syncthreads();
   fft_smem<G::RR, G::RB, G::VROW, false>(buf, a.tw_row);
   real_pass<N, true>(buf, G::RB, a.tw_real);
   for (int e = threadIdx.x; e < G::RB * L; e += nthr) {
@@ -302,25 +318,23 @@ __device__ void row_item(const GlobalArgs& a, float2* buf, int f, int y0, int do
   __syncthreads();
 }
 
-// Column phase on one work item: columns c0 .. c0+CB-1 of field f.
-// mode 0: s-draw; mode 1: s_hat = f_lambda t_hat with residual bookkeeping (returns this CTA's partial
-// sum when cmp); mode 2: P^2 |V|^2 power of the level right-hand side (no write-back).
+// Column-phase spectral update of columns c0 .. c0+CB-1 held in buf (after the forward column FFT), over
+// the mode pairs (j, H - j) of each column (j = 0 pairs ky = 0 with ky = H/2), then a CTA barrier:
+//   mode 0: sampler s-draw s_hat = f t_hat + g zeta with the (f/n, g/sqrt(2n)) table and Philox counter
+//           (column pair group col H/2 + j, step, chain, stream 1; edge column shared as in the on-chip kernel);
+//   mode 1: Wiener-filter update s_hat = P/(P + lambda tau) t_hat / n; with cmp, returns this CTA's part of
+//           sum_k |s_hat - prev|^2 ((P + lambda tau)/(lambda tau))^2 (the residual from consecutive
+//           iterates); with store, keeps s_hat in prev;
+//   mode 2: returns sum_k P^2 |t_hat|^2 of the level right-hand side (buf unchanged).
 template <int N>
-__device__ double col_item(const GlobalArgs& a, float2* buf, int f, int c0, int done, float ltau, bool cmp,
-                           bool store) {
+__device__ __forceinline__ double col_update(int mode, float2* buf, int c0, const float2* __restrict__ fg,
+                                             const float* __restrict__ Pk, float2* prev, uint32_t step,
+                                             uint32_t chain, uint32_t key0, uint32_t key1, float ltau, bool cmp,
+                                             bool store) {
   using G = GGeo<N>;
   constexpr int L = G::LR, H = G::H, WH = G::WH;
   constexpr float INV_N = 1.0f / float(G::H * G::W);
-  float2* Zf = a.Z + (long long)f * H * L;
-  for (int e = threadIdx.x; e < G::CB * H; e += 128) {
-    const int j = e % G::CB, y = e / G::CB;  // consecutive threads: consecutive columns of a row
-    buf[j * G::VCOL + padi(y)] = __ldcg(Zf + (long long)y * L + c0 + j);
-  }
-  __syncthreads();
-  fft_smem<G::RC, G::CB, G::VCOL, false>(buf, a.tw_col);
   double acc = 0.0;
-  const uint32_t step = a.step0 + uint32_t(done);
-  const uint32_t chain = a.chain0 + uint32_t(f);
   // mode pairs (j, H - j) of each column, j in [0, H/2); j = 0 pairs ky = 0 with ky = H/2
   for (int task = threadIdx.x; task < G::CB * (H / 2); task += 128) {
     const int jc = task / (H / 2), j = task % (H / 2);
@@ -328,17 +342,17 @@ __device__ double col_item(const GlobalArgs& a, float2* buf, int f, int c0, int 
     const int ky1 = j, ky2 = j == 0 ? H / 2 : H - j;
     float2* v = buf + jc * G::VCOL;
     float2 y1 = v[padi(ky1)], y2 = v[padi(ky2)];
-    if (a.mode == 0) {
+    if (mode == 0) {
       float z[4];
-      normals4(uint32_t(col * (H / 2) + j), step, chain, 1u, a.key0, a.key1, z);
+      normals4(uint32_t(col * (H / 2) + j), step, chain, 1u, key0, key1, z);
       if (col != 0) {
-        const float2 m1 = __ldg(a.fg + ky1 * WH + col), m2 = __ldg(a.fg + ky2 * WH + col);
+        const float2 m1 = __ldg(fg + ky1 * WH + col), m2 = __ldg(fg + ky2 * WH + col);
         y1 = make_float2(fmaf(m1.x, y1.x, m1.y * z[0]), fmaf(m1.x, y1.y, m1.y * z[1]));
         y2 = make_float2(fmaf(m2.x, y2.x, m2.y * z[2]), fmaf(m2.x, y2.y, m2.y * z[3]));
       } else {
-        const float2 a1 = __ldg(a.fg + ky1 * WH), b1 = __ldg(a.fg + ky1 * WH + G::W / 2);
+        const float2 a1 = __ldg(fg + ky1 * WH), b1 = __ldg(fg + ky1 * WH + G::W / 2);
         if (j == 0) {
-          const float2 a2 = __ldg(a.fg + ky2 * WH), b2 = __ldg(a.fg + ky2 * WH + G::W / 2);
+          const float2 a2 = __ldg(fg + ky2 * WH), b2 = __ldg(fg + ky2 * WH + G::W / 2);
           constexpr float R2 = 1.41421356237309505f;
           y1 = make_float2(fmaf(a1.x, y1.x, R2 * a1.y * z[0]), fmaf(b1.x, y1.y, R2 * b1.y * z[2]));
           y2 = make_float2(fmaf(a2.x, y2.x, R2 * a2.y * z[1]), fmaf(b2.x, y2.y, R2 * b2.y * z[3]));
@@ -352,29 +366,29 @@ __device__ double col_item(const GlobalArgs& a, float2* buf, int f, int c0, int 
           y2 = cadd(cconj(Ap), cmul_i(cconj(Bp)));
         }
       }
-    } else if (a.mode == 1) {
+    } else if (mode == 1) {
       auto wres = [&](float P, float dre, float dim) -> double {
         const double g = (double(P) + double(ltau)) / double(ltau);
         return (double(dre) * dre + double(dim) * dim) * g * g;
       };
       if (col != 0) {
-        const float P1 = __ldg(a.Pk + ky1 * WH + col), P2 = __ldg(a.Pk + ky2 * WH + col);
+        const float P1 = __ldg(Pk + ky1 * WH + col), P2 = __ldg(Pk + ky2 * WH + col);
         const float2 n1 = cscale(y1, P1 / (P1 + ltau) * INV_N), n2 = cscale(y2, P2 / (P2 + ltau) * INV_N);
         if (cmp) {
-          const float2 o1 = a.prev[ky1 * L + col], o2 = a.prev[ky2 * L + col];
+          const float2 o1 = prev[ky1 * L + col], o2 = prev[ky2 * L + col];
           acc += 2.0 * (wres(P1, n1.x - o1.x, n1.y - o1.y) + wres(P2, n2.x - o2.x, n2.y - o2.y));
         }
         y1 = n1;
         y2 = n2;
       } else {
-        const float Pa1 = __ldg(a.Pk + ky1 * WH), Pb1 = __ldg(a.Pk + ky1 * WH + G::W / 2);
-        const float Pa2 = __ldg(a.Pk + ky2 * WH), Pb2 = __ldg(a.Pk + ky2 * WH + G::W / 2);
+        const float Pa1 = __ldg(Pk + ky1 * WH), Pb1 = __ldg(Pk + ky1 * WH + G::W / 2);
+        const float Pa2 = __ldg(Pk + ky2 * WH), Pb2 = __ldg(Pk + ky2 * WH + G::W / 2);
         const float fa1 = Pa1 / (Pa1 + ltau) * INV_N, fb1 = Pb1 / (Pb1 + ltau) * INV_N;
         const float fa2 = Pa2 / (Pa2 + ltau) * INV_N, fb2 = Pb2 / (Pb2 + ltau) * INV_N;
         if (j == 0) {
           const float2 n1 = make_float2(fa1 * y1.x, fb1 * y1.y), n2 = make_float2(fa2 * y2.x, fb2 * y2.y);
           if (cmp) {
-            const float2 o1 = a.prev[ky1 * L], o2 = a.prev[ky2 * L];
+            const float2 o1 = prev[ky1 * L], o2 = prev[ky2 * L];
             acc += wres(Pa1, n1.x - o1.x, 0.f) + wres(Pb1, n1.y - o1.y, 0.f) + wres(Pa2, n2.x - o2.x, 0.f) +
                    wres(Pb2, n2.y - o2.y, 0.f);
           }
@@ -385,7 +399,7 @@ __device__ double col_item(const GlobalArgs& a, float2* buf, int f, int c0, int 
           const float2 A = cscale(cscale(cadd(y1, y2c), 0.5f), fa1);
           const float2 B = cscale(cmul_mi(cscale(csub(y1, y2c), 0.5f)), fb1);
           if (cmp) {
-            const float2 o1 = a.prev[ky1 * L], o2c = cconj(a.prev[ky2 * L]);
+            const float2 o1 = prev[ky1 * L], o2c = cconj(prev[ky2 * L]);
             const float2 oA = cscale(cadd(o1, o2c), 0.5f);
             const float2 oB = cmul_mi(cscale(csub(o1, o2c), 0.5f));
             acc += 2.0 * (wres(Pa1, A.x - oA.x, A.y - oA.y) + wres(Pb1, B.x - oB.x, B.y - oB.y));
@@ -395,29 +409,49 @@ __device__ double col_item(const GlobalArgs& a, float2* buf, int f, int c0, int 
         }
       }
       if (store) {
-        a.prev[ky1 * L + col] = y1;
-        a.prev[ky2 * L + col] = y2;
+        prev[ky1 * L + col] = y1;
+        prev[ky2 * L + col] = y2;
       }
     } else {
       auto p2 = [](float P, float re, float im) -> double {
         return double(P) * double(P) * (double(re) * re + double(im) * im);
       };
       if (col != 0) {
-        acc += 2.0 * (p2(__ldg(a.Pk + ky1 * WH + col), y1.x, y1.y) + p2(__ldg(a.Pk + ky2 * WH + col), y2.x, y2.y));
+        acc += 2.0 * (p2(__ldg(Pk + ky1 * WH + col), y1.x, y1.y) + p2(__ldg(Pk + ky2 * WH + col), y2.x, y2.y));
       } else if (j == 0) {
-        acc += p2(__ldg(a.Pk + ky1 * WH), y1.x, 0.f) + p2(__ldg(a.Pk + ky1 * WH + G::W / 2), y1.y, 0.f) +
-               p2(__ldg(a.Pk + ky2 * WH), y2.x, 0.f) + p2(__ldg(a.Pk + ky2 * WH + G::W / 2), y2.y, 0.f);
+        acc += p2(__ldg(Pk + ky1 * WH), y1.x, 0.f) + p2(__ldg(Pk + ky1 * WH + G::W / 2), y1.y, 0.f) +
+               p2(__ldg(Pk + ky2 * WH), y2.x, 0.f) + p2(__ldg(Pk + ky2 * WH + G::W / 2), y2.y, 0.f);
       } else {
         const float2 y2c = cconj(y2);
         const float2 A = cscale(cadd(y1, y2c), 0.5f);
         const float2 B = cmul_mi(cscale(csub(y1, y2c), 0.5f));
-        acc += 2.0 * (p2(__ldg(a.Pk + ky1 * WH), A.x, A.y) + p2(__ldg(a.Pk + ky1 * WH + G::W / 2), B.x, B.y));
+        acc += 2.0 * (p2(__ldg(Pk + ky1 * WH), A.x, A.y) + p2(__ldg(Pk + ky1 * WH + G::W / 2), B.x, B.y));
       }
     }
     v[padi(ky1)] = y1;
     v[padi(ky2)] = y2;
   }
   __syncthreads();
+  return acc;
+}
+
+// Column phase on one work item: columns c0 .. c0+CB-1 of field f.
+// mode 0: s-draw; mode 1: s_hat = f_lambda t_hat with residual bookkeeping (returns this CTA's partial
+// sum when cmp); mode 2: P^2 |V|^2 power of the level right-hand side (no write-back).
+template <int N>
+__device__ double col_item(const GlobalArgs& a, float2* buf, int f, int c0, int done, float ltau, bool cmp,
+                           bool store) {
+  using G = GGeo<N>;
+  constexpr int L = G::LR, H = G::H;
+  float2* Zf = a.Z + (long long)f * H * L;
+  for (int e = threadIdx.x; e < G::CB * H; e += 128) {
+    const int j = e % G::CB, y = e / G::CB;  // consecutive threads: consecutive columns of a row
+    buf[j * G::VCOL + padi(y)] = __ldcg(Zf + (long long)y * L + c0 + j);
+  }
+  __syncthreads();
+  fft_smem<G::RC, G::CB, G::VCOL, false>(buf, a.tw_col);
+  const double acc = col_update<N>(a.mode, buf, c0, a.fg, a.Pk, a.prev, a.step0 + uint32_t(done),
+                                   a.chain0 + uint32_t(f), a.key0, a.key1, ltau, cmp, store);
   if (a.mode == 2) return acc;
   fft_smem<G::RC, G::CB, G::VCOL, true>(buf, a.tw_col);
   for (int e = threadIdx.x; e < G::CB * H; e += 128) {

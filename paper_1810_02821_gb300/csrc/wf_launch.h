@@ -6,6 +6,7 @@
 #include "wf_gibbs.cuh"
 #include "wf_global.cuh"
 #include "wf_batch.cuh"
+#include "wf_gbatch.cuh"
 
 namespace wf {
 
@@ -33,11 +34,15 @@ cudaError_t launch_batch(const BatchArgs& b, int* grid_out, cudaStream_t st);
 template <int N>
 cudaError_t launch_wpower(const WpowerArgs& p, cudaStream_t st);
 template <int N>
-cudaError_t batch_grid(int n_items, int* grid_out);
+cudaError_t batch_grid(int n_items, int grid_pct, int* grid_out);
 
 // large images (N >= 256): one cooperative launch of k_global<N> (all CTAs co-resident)
 template <int N>
 cudaError_t launch_global(const GlobalArgs& a, cudaStream_t st, LaunchTimer* t);
+
+// batched large images (N >= 256): one cooperative launch of k_gbatch<N> over all fields of a size class
+template <int N>
+cudaError_t launch_gbatch(const GBArgs& a, cudaStream_t st);
 
 // definitions, included by the per-size translation units only
 #if defined(WF_LAUNCH_DEFINE)
@@ -75,7 +80,7 @@ cudaError_t launch_solve(const SolveArgs& a, const BnormArgs& b, cudaStream_t st
 
 
 template <int N>
-cudaError_t batch_grid(int n_items, int* grid_out) {
+cudaError_t batch_grid(int n_items, int grid_pct, int* grid_out) {
   const int smem = batch_smem_bytes<N>();
   cudaError_t e = cudaFuncSetAttribute(k_batch<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
@@ -84,14 +89,16 @@ cudaError_t batch_grid(int n_items, int* grid_out) {
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<N>, N, smem)) != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  *grid_out = n_items < per_sm * sms ? n_items : per_sm * sms;
+  int full = per_sm * sms;
+  if (grid_pct > 0 && grid_pct < 100) full = (full * grid_pct + 99) / 100;
+  *grid_out = n_items < full ? n_items : full;
   return cudaSuccess;
 }
 
 template <int N>
 cudaError_t launch_batch(const BatchArgs& b, int* grid_out, cudaStream_t st) {
   int grid = 0;
-  cudaError_t e = batch_grid<N>(b.n, &grid);
+  cudaError_t e = batch_grid<N>(b.n, b.grid_pct, &grid);
   if (e != cudaSuccess) return e;
   if (grid_out) *grid_out = grid;
   if (grid > 0) k_batch<N><<<grid, N, batch_smem_bytes<N>(), st>>>(b);
@@ -111,7 +118,7 @@ cudaError_t launch_wpower(const WpowerArgs& p, cudaStream_t st) {
   template cudaError_t launch_sample<N>(const SampleArgs&, cudaStream_t, LaunchTimer*); \
   template cudaError_t launch_solve<N>(const SolveArgs&, const BnormArgs&, cudaStream_t, LaunchTimer*); \
   template cudaError_t launch_batch<N>(const BatchArgs&, int*, cudaStream_t);                     \
-  template cudaError_t batch_grid<N>(int, int*);                                                   \
+  template cudaError_t batch_grid<N>(int, int, int*);                                                   \
   template cudaError_t launch_wpower<N>(const WpowerArgs&, cudaStream_t);
 #endif
 
@@ -127,7 +134,9 @@ cudaError_t launch_global(const GlobalArgs& a, cudaStream_t st, LaunchTimer* t) 
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_global<N>, 128, G::SMEM)) != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const long long items = (long long)(G::ROW_ITEMS > G::COL_ITEMS ? G::ROW_ITEMS : G::COL_ITEMS) * a.n_fields;
-  const int grid = int(items < (long long)per_sm * sms ? items : (long long)per_sm * sms);
+  long long full = (long long)per_sm * sms;
+  if (a.grid_pct > 0 && a.grid_pct < 100) full = (full * a.grid_pct + 99) / 100;
+  const int grid = int(items < full ? items : full);
   GlobalArgs arg = a;
   void* args[] = {&arg};
   if (t) t->start();
@@ -136,7 +145,29 @@ cudaError_t launch_global(const GlobalArgs& a, cudaStream_t st, LaunchTimer* t) 
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
-#define WF_INSTANTIATE_GLOBAL(N) template cudaError_t launch_global<N>(const GlobalArgs&, cudaStream_t, LaunchTimer*);
+template <int N>
+cudaError_t launch_gbatch(const GBArgs& a, cudaStream_t st) {
+  using G = GGeo<N>;
+  cudaError_t e = cudaFuncSetAttribute(k_gbatch<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gbatch<N>, 128, G::SMEM)) != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const long long items = (long long)(G::ROW_ITEMS > G::COL_ITEMS ? G::ROW_ITEMS : G::COL_ITEMS) * a.F;
+  long long full = (long long)per_sm * sms;
+  if (a.grid_pct > 0 && a.grid_pct < 100) full = (full * a.grid_pct + 99) / 100;
+  const int grid = int(items < full ? items : full);
+  GBArgs arg = a;
+  void* args[] = {&arg};
+  e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_gbatch<N>), dim3(grid), dim3(128), args, G::SMEM, st);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+#define WF_INSTANTIATE_GLOBAL(N)                                                               \
+  template cudaError_t launch_global<N>(const GlobalArgs&, cudaStream_t, LaunchTimer*);         \
+  template cudaError_t launch_gbatch<N>(const GBArgs&, cudaStream_t);
 #endif
 
 }  // namespace wf

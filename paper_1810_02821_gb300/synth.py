@@ -182,6 +182,49 @@ def config_precision(H: int = 1024, seed: int = 0, n_holes: int = 200, r_range: 
     return _finish(signal, Ndiag, mask, Pk, rng, dict(kind="precision", H=H, W=W, seed=seed))
 
 
+def batch_class_counts(n_images: int, fractions=((64, 0.40), (128, 0.40), (256, 0.15), (512, 0.05))) -> dict:
+    """Images per size by largest-remainder rounding of ``n_images * fraction`` (ties: the first size)."""
+    raw = [(H, n_images * f) for H, f in fractions]
+    counts = {H: int(np.floor(x)) for H, x in raw}
+    left = n_images - sum(counts.values())
+    for H, x in sorted(raw, key=lambda t: -(t[1] - np.floor(t[1])))[:left]:
+        counts[H] += 1
+    return counts
+
+
+def config_batch(n_images: int = 4096, seed: int = 0, fractions=((64, 0.40), (128, 0.40), (256, 0.15), (512, 0.05))):
+    """Mixed-size batch (default: 4096 images, 1639 x 64^2, 1638 x 128^2, 614 x 256^2, 205 x 512^2), in a
+    random order. Per image: slope ~ U[-3, -1] with k0 = 1/N; sigma^2 ~ U[a, b] with a ~ U[0.01, 0.1] and
+    b = a * U[2, 20]; masked fraction f ~ U[0, 0.2], half of it one random rectangle (periodic wrap) and
+    half scattered pixels. Returns a list of WFProblem."""
+    rng = np.random.default_rng(seed)
+    counts = batch_class_counts(n_images, fractions)
+    sizes = np.concatenate([np.full(c, H) for H, c in counts.items()])
+    sizes = sizes[rng.permutation(sizes.size)]
+    out = []
+    for H in sizes:
+        H = int(H)
+        slope = rng.uniform(-3.0, -1.0)
+        Pk = power_law_pk(H, H, 1.0, slope, 1.0 / H)
+        signal = gaussian_random_field(Pk, H, H, rng)
+        a = rng.uniform(0.01, 0.1)
+        b = a * rng.uniform(2.0, 20.0)
+        Ndiag = rng.uniform(a, b, size=(H, H))
+        mask = np.zeros((H, H), np.uint8)
+        f = rng.uniform(0.0, 0.2)
+        rect = int(round(0.5 * f * H * H))
+        if rect:
+            h = int(np.clip(round(np.sqrt(rect * rng.uniform(0.5, 2.0))), 1, H))
+            w = int(np.clip(round(rect / h), 1, H))
+            y0, x0 = rng.integers(0, H, size=2)
+            mask[np.ix_((y0 + np.arange(h)) % H, (x0 + np.arange(w)) % H)] = 1
+        n_scatter = int(round(0.5 * f * H * H))
+        if n_scatter:
+            _scatter(mask, min(n_scatter, int((mask == 0).sum())), rng)
+        out.append(_finish(signal, Ndiag, mask, Pk, rng, dict(kind="batch", H=H, W=H, slope=slope)))
+    return out
+
+
 def flat_problem(H: int, W: int | None = None, *, seed: int = 0, P: float = 1.0, sigma2: float = 0.3,
                  all_masked: bool = False) -> WFProblem:
     """Special cases with closed-form answers: flat P (except P0 = 0), homogeneous noise, and either no

@@ -51,7 +51,7 @@ class BatchOpts(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("tol", ctypes.c_double), ("eta", ctypes.c_double),
                 ("level_tol", ctypes.c_double), ("level_max", ctypes.c_int32), ("check", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("n_samples", ctypes.c_int32), ("large_streams", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("small_grid_pct", ctypes.c_int32), ("large_grid_pct", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -91,6 +91,18 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.wf_batch_opts_default.restype = None
     L.wf_batch_run.argtypes = [ctypes.POINTER(BatchItem), I32, ctypes.POINTER(BatchOpts), P]
     L.wf_batch_run.restype = ctypes.c_int
+    L.wf_batch_graph_create.argtypes = [ctypes.POINTER(BatchItem), I32, ctypes.POINTER(BatchOpts),
+                                        ctypes.POINTER(ctypes.c_void_p)]
+    L.wf_batch_graph_create.restype = ctypes.c_int
+    L.wf_batch_graph_launch.argtypes = [P, P]
+    L.wf_batch_graph_launch.restype = ctypes.c_int
+    L.wf_batch_graph_results.argtypes = [P, ctypes.POINTER(BatchItem), I32, P]
+    L.wf_batch_graph_results.restype = ctypes.c_int
+    L.wf_batch_graph_destroy.argtypes = [P]
+    L.wf_batch_graph_destroy.restype = None
+    L.wf_batch_autotune.argtypes = [ctypes.POINTER(BatchItem), I32, ctypes.POINTER(BatchOpts), I32,
+                                    ctypes.POINTER(D), P]
+    L.wf_batch_autotune.restype = ctypes.c_int
     L.wf_spectral_power.argtypes = [P, P, ctypes.c_float, I32, P, I32, I32, I32, ctypes.POINTER(D), P]
     L.wf_spectral_power.restype = ctypes.c_int
     L.wf_loglike_grad.argtypes = [P, P, P, I32, I32, ctypes.POINTER(D), I32, U64, D, ctypes.POINTER(D),
@@ -248,15 +260,8 @@ class BatchImage:
     resid: float = -1.0
 
 
-def wf_batch_run(images, *, n_samples: int = 0, tau: float = 0.0, tol: float = 1e-5, eta: float = 0.5,
-                 level_tol: float = 1e-2, level_max: int = 64, check: int = 4, max_iter: int = 20000,
-                 large_streams: int = 8, stream=None, allow_not_converged: bool = False):
-    """Wiener filter + ``n_samples`` posterior samples for every image (C call ``wf_batch_run``).
-
-    Fills ``out_wf``, ``out_samples``, ``status``, ``iters`` and ``resid`` of each ``BatchImage``.
-    """
+def _batch_items(images, n_samples: int):
     import torch
-    L = load_library()
     arr = (BatchItem * len(images))()
     for i, im in enumerate(images):
         H, W, pd, pn, pm, pp = _inputs(im.d, im.Ndiag, im.mask, im.Pk)
@@ -271,16 +276,93 @@ def wf_batch_run(images, *, n_samples: int = 0, tau: float = 0.0, tol: float = 1
                               if n_samples > 0 else None)
         arr[i].seed = int(im.seed) & 0xFFFFFFFFFFFFFFFF
         arr[i].chain = int(im.chain)
+    return arr
+
+
+def _batch_opts(n_samples=0, tau=0.0, tol=1e-5, eta=0.5, level_tol=1e-2, level_max=64, check=4, max_iter=20000,
+                large_streams=8, small_grid_pct=0, large_grid_pct=0) -> BatchOpts:
+    L = load_library()
     o = BatchOpts()
     L.wf_batch_opts_default(ctypes.byref(o))
     o.tau, o.tol, o.eta, o.level_tol = float(tau), float(tol), float(eta), float(level_tol)
     o.level_max, o.check, o.max_iter, o.n_samples = int(level_max), int(check), int(max_iter), int(n_samples)
-    o.large_streams = int(large_streams)
-    st = L.wf_batch_run(arr, len(images), ctypes.byref(o), _stream_ptr(stream))
+    o.large_streams, o.small_grid_pct, o.large_grid_pct = int(large_streams), int(small_grid_pct), int(large_grid_pct)
+    return o
+
+
+def _batch_copy_results(images, arr):
     for i, im in enumerate(images):
         im.status, im.iters, im.resid = arr[i].status, arr[i].iters, arr[i].resid
+
+
+def wf_batch_run(images, *, n_samples: int = 0, stream=None, allow_not_converged: bool = False, **opts):
+    """Wiener filter + ``n_samples`` posterior samples for every image (C call ``wf_batch_run``).
+
+    ``opts``: tau, tol, eta, level_tol, level_max, check, max_iter, large_streams, small_grid_pct,
+    large_grid_pct (as ``wf_batch_opts``). Fills ``out_wf``, ``out_samples``, ``status``, ``iters`` and
+    ``resid`` of each ``BatchImage``.
+    """
+    L = load_library()
+    arr = _batch_items(images, n_samples)
+    o = _batch_opts(n_samples=n_samples, **opts)
+    st = L.wf_batch_run(arr, len(images), ctypes.byref(o), _stream_ptr(stream))
+    _batch_copy_results(images, arr)
     _check(st, "wf_batch_run", ok=(WF_OK, 5) if allow_not_converged else (WF_OK,))
     return images
+
+
+class BatchGraph:
+    """The batch recorded once as a CUDA graph (C calls ``wf_batch_graph_*``): ``launch()`` replays it
+    asynchronously on a stream, ``results()`` waits and fills each image's status / iters / resid."""
+
+    def __init__(self, images, *, n_samples: int = 0, **opts):
+        L = load_library()
+        self.images = images
+        self._arr = _batch_items(images, n_samples)
+        o = _batch_opts(n_samples=n_samples, **opts)
+        h = ctypes.c_void_p(None)
+        _check(L.wf_batch_graph_create(self._arr, len(images), ctypes.byref(o), ctypes.byref(h)),
+               "wf_batch_graph_create")
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(load_library().wf_batch_graph_launch(self._h, _stream_ptr(stream)), "wf_batch_graph_launch")
+
+    def results(self, stream=None, allow_not_converged: bool = False):
+        st = load_library().wf_batch_graph_results(self._h, self._arr, len(self.images), _stream_ptr(stream))
+        _batch_copy_results(self.images, self._arr)
+        _check(st, "wf_batch_graph_results", ok=(WF_OK, 5) if allow_not_converged else (WF_OK,))
+        return self.images
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load_library().wf_batch_graph_destroy(self._h)
+            self._h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def wf_batch_autotune(images, *, n_samples: int = 0, reps: int = 1, stream=None, **opts):
+    """Launch-shape autotuner of the batched form (C call ``wf_batch_autotune``) -> (chosen options dict,
+    best replay ms). The images' outputs are overwritten by the trial runs."""
+    L = load_library()
+    arr = _batch_items(images, n_samples)
+    o = _batch_opts(n_samples=n_samples, **opts)
+    best = ctypes.c_double(0.0)
+    _check(L.wf_batch_autotune(arr, len(images), ctypes.byref(o), int(reps), ctypes.byref(best), _stream_ptr(stream)),
+           "wf_batch_autotune")
+    return dict(large_streams=o.large_streams, small_grid_pct=o.small_grid_pct,
+                large_grid_pct=o.large_grid_pct), best.value
 
 
 def wf_spectral_power(a, w, b=None, sgn: float = 1.0, stream=None):

@@ -102,3 +102,19 @@ def test_option_structs_match_the_header(tmp_path):
         assert int(got[cname]) == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert int(got[f"{cname}.{fname}"]) == getattr(py, fname).offset, (cname, fname)
+
+
+def test_batch_graph_argument_errors_need_no_gpu(lib):
+    h = ctypes.c_void_p(None)
+    assert lib.wf_batch_graph_create(None, 0, None, ctypes.byref(h)) == 1 and not h.value
+    items = (wf.BatchItem * 1)()
+    o = wf.BatchOpts()
+    lib.wf_batch_opts_default(ctypes.byref(o))
+    assert o.small_grid_pct == 0 and o.large_grid_pct == 0 and o.large_streams >= 1
+    o.small_grid_pct = 101
+    assert lib.wf_batch_graph_create(items, 1, ctypes.byref(o), ctypes.byref(h)) == 1
+    assert lib.wf_batch_run(items, 1, ctypes.byref(o), None) == 1
+    assert lib.wf_batch_autotune(items, 1, ctypes.byref(o), 1, None, None) == 1
+    assert lib.wf_batch_graph_launch(None, None) == 1
+    assert lib.wf_batch_graph_results(None, items, 1, None) == 1
+    lib.wf_batch_graph_destroy(None)

@@ -78,3 +78,77 @@ def test_batch_many_small_images():
     for i in (0, 123, 239):
         r = wf.wf_solve_ex(*to_dev(probs[i]), tol=1e-5)
         assert rel(imgs[i].out_wf.cpu().numpy(), r.s.cpu().numpy()) < WF_TOL
+
+
+def _outputs(imgs):
+    return [(im.out_wf.cpu().numpy().copy(), im.out_samples.cpu().numpy().copy()) for im in imgs]
+
+
+def test_batch_graph_replays_match_the_direct_run_and_follow_input_changes():
+    sizes = [64, 128, 256, 32, 512, 64, 16]
+    probs = _mixed(sizes, seed0=70)
+    n_samples = 3
+    ref_imgs = [wf.BatchImage(*to_dev(p), seed=5 + i, chain=i) for i, p in enumerate(probs)]
+    wf.wf_batch_run(ref_imgs, n_samples=n_samples, tol=1e-5)
+    ref = _outputs(ref_imgs)
+    imgs = [wf.BatchImage(*to_dev(p), seed=5 + i, chain=i) for i, p in enumerate(probs)]
+    with wf.BatchGraph(imgs, n_samples=n_samples, tol=1e-5) as g:
+        for _ in range(2):
+            g.launch()
+            g.results()
+            assert all(im.status == 0 for im in imgs)
+            for (rw, rs), (gw, gs) in zip(ref, _outputs(imgs)):
+                assert rel(gw, rw) < WF_TOL
+                for m in range(n_samples):
+                    assert rel(gs[m], rs[m]) < SAMPLE_TOL
+        # a replay reads the inputs as they are when it runs: doubling d doubles the Wiener filter
+        for im in imgs:
+            im.d.mul_(2.0)
+        g.launch()
+        g.results()
+        for (rw, _), im in zip(ref, imgs):
+            assert rel(im.out_wf.cpu().numpy(), 2.0 * rw) < WF_TOL
+
+
+def test_batch_launch_shapes_and_autotune_keep_the_results():
+    sizes = [64, 128, 256, 256, 32]
+    probs = _mixed(sizes, seed0=90)
+    ref_imgs = [wf.BatchImage(*to_dev(p), seed=i, chain=i) for i, p in enumerate(probs)]
+    wf.wf_batch_run(ref_imgs, n_samples=2, tol=1e-5)
+    ref = _outputs(ref_imgs)
+    imgs = [wf.BatchImage(*to_dev(p), seed=i, chain=i) for i, p in enumerate(probs)]
+    wf.wf_batch_run(imgs, n_samples=2, tol=1e-5, small_grid_pct=25, large_grid_pct=25, large_streams=2)
+    for (rw, rs), (gw, gs) in zip(ref, _outputs(imgs)):
+        assert rel(gw, rw) < WF_TOL and rel(gs, rs) < SAMPLE_TOL
+    chosen, ms = wf.wf_batch_autotune(imgs, n_samples=2, reps=1, tol=1e-5)
+    assert chosen["large_grid_pct"] in (0, 100, 50, 25, 12) and chosen["large_streams"] in (2, 4, 8, 16)
+    assert chosen["small_grid_pct"] in (0, 100, 50, 25) and ms > 0
+    wf.wf_batch_run(imgs, n_samples=2, tol=1e-5, **chosen)
+    for (rw, rs), (gw, gs) in zip(ref, _outputs(imgs)):
+        assert rel(gw, rw) < WF_TOL and rel(gs, rs) < SAMPLE_TOL
+
+
+def test_batch_large_images_in_shared_launches():
+    # many images above 128 x 128: every size class runs as chunks of fields of one cooperative launch
+    sizes = [256] * 10 + [512] * 3
+    probs = _mixed(sizes, seed0=200)
+    bad = synth.make_problem(256, seed=7, mask_frac=0.1)
+    o = np.argwhere(bad.mask == 0)[0]
+    bad.d[o[0], o[1]] = np.inf
+    probs.append(bad)
+    n_samples = 3
+    imgs = [wf.BatchImage(*to_dev(p), seed=300 + i, chain=i) for i, p in enumerate(probs)]
+    with pytest.raises(wf.WFError) as e:
+        wf.wf_batch_run(imgs, n_samples=n_samples, tol=1e-6, large_streams=2)
+    assert e.value.status == 6 and imgs[-1].status == 6
+    assert all(im.status == 0 for im in imgs[:-1])
+    for i in (0, 7, 10, 12):
+        dev = to_dev(probs[i])
+        r = wf.wf_solve_ex(*dev, tol=1e-6)
+        assert rel(imgs[i].out_wf.cpu().numpy(), r.s.cpu().numpy()) < WF_TOL, i
+        assert imgs[i].iters == r.iters, (i, imgs[i].iters, r.iters)
+        ref = wf.wf_sample_ex(*dev, seed=300 + i, n_samples=n_samples, chain_offset=i,
+                              init_s=imgs[i].out_wf.contiguous())
+        g, w = imgs[i].out_samples.cpu().numpy(), ref[0].cpu().numpy()
+        for m in range(n_samples):
+            assert rel(g[m], w[m]) < SAMPLE_TOL, (i, m)
