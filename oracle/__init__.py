@@ -9,8 +9,10 @@ It is deliberately plain and slow:
 
 * ``dft``      — unitary 2D DFT as products with explicit DFT matrices (Eq. 6, normalised, §2.1);
 * ``philox``   — Philox4x32-10 from its published definition (Salmon et al., SC'11) + Box–Muller;
-* ``messenger``— Algorithm 1 (sampler) and its G -> 0 variant with lambda-cooling (§2.2);
-* ``dense``    — the Wiener filter of Eq. 2-3 and the posterior covariance of Eq. 4 by dense solves;
+* ``messenger``— Algorithm 1 (sampler) and its G -> 0 variant with lambda-cooling (§2.2), A = I or a
+  diagonal pixel response A (the general t-update of the Alg. 1 definitions);
+* ``dense``    — the Wiener filter of Eq. 2-3 and the posterior covariance of Eq. 4 by dense solves (with
+  an optional diagonal response A);
 * ``likelihood``— the Gaussian evidence of the data for a power-law P(k) and scaled noise, and its exact
   gradient with respect to (amplitude, slope, noise scale), by dense algebra.
 

@@ -29,28 +29,34 @@ def signal_covariance(Pk, H: int, W: int) -> np.ndarray:
     return 0.5 * (S + S.T)
 
 
-def _observed_system(Ndiag, mask, Pk, extra_noise):
+def _observed_system(Ndiag, mask, Pk, extra_noise, A=None):
+    """S, the data pixels o, the response A_o on them and C = A_o S_oo A_o + N_oo + extra I."""
     H, W = np.asarray(Ndiag).shape
     S = signal_covariance(Pk, H, W)
-    o = np.flatnonzero(np.asarray(mask).ravel() == 0)
+    keep = np.asarray(mask).ravel() == 0
+    Av = np.ones(H * W) if A is None else np.asarray(A, dtype=np.float64).ravel()
+    o = np.flatnonzero(keep & (Av != 0))
     N = np.asarray(Ndiag, dtype=np.float64).ravel()[o] + extra_noise
-    C = S[np.ix_(o, o)] + np.diag(N)
-    return S, o, C
+    Ao = Av[o]
+    C = Ao[:, None] * S[np.ix_(o, o)] * Ao[None, :] + np.diag(N)
+    return S, o, Ao, C
 
 
-def wiener_dense(d, Ndiag, mask, Pk, extra_noise: float = 0.0) -> np.ndarray:
-    """s_W = S[:, o] (S_oo + N_oo + extra I)^-1 d_o -> float64 [H][W]."""
+def wiener_dense(d, Ndiag, mask, Pk, extra_noise: float = 0.0, A=None) -> np.ndarray:
+    """s_W = S[:, o] A_o (A_o S_oo A_o + N_oo + extra I)^-1 d_o -> float64 [H][W] (A = I by default: the
+    data model d = A s + n of Eq. 1 with a diagonal response)."""
     H, W = np.asarray(d).shape
-    S, o, C = _observed_system(Ndiag, mask, Pk, extra_noise)
+    S, o, Ao, C = _observed_system(Ndiag, mask, Pk, extra_noise, A)
     if o.size == 0:
         return np.zeros((H, W))
     x = np.linalg.solve(C, np.asarray(d, dtype=np.float64).ravel()[o])
-    return (S[:, o] @ x).reshape(H, W)
+    return (S[:, o] @ (Ao * x)).reshape(H, W)
 
 
-def posterior_cov_dense(Ndiag, mask, Pk) -> np.ndarray:
-    """Posterior covariance S - S[:, o] C^-1 S[o, :] (n x n)."""
-    S, o, C = _observed_system(Ndiag, mask, Pk, 0.0)
+def posterior_cov_dense(Ndiag, mask, Pk, A=None) -> np.ndarray:
+    """Posterior covariance S - S[:, o] A_o C^-1 A_o S[o, :] (n x n)."""
+    S, o, Ao, C = _observed_system(Ndiag, mask, Pk, 0.0, A)
     if o.size == 0:
         return S
-    return S - S[:, o] @ np.linalg.solve(C, S[o, :])
+    SA = S[:, o] * Ao[None, :]
+    return S - SA @ np.linalg.solve(C, SA.T)

@@ -48,35 +48,54 @@ from .philox import STREAM_S, STREAM_T, normals4
 # ----------------------------------------------------------------------------------------------
 # problem set-up (Alg. 1 definitions of T and N_bar)
 # ----------------------------------------------------------------------------------------------
-def default_tau(Ndiag: np.ndarray, mask: np.ndarray, Pk: np.ndarray) -> float:
-    """tau = min over observed pixels of the noise variance (Alg. 1: T = min(N) I for A = I).
+def default_tau(Ndiag: np.ndarray, mask: np.ndarray, Pk: np.ndarray, A=None) -> float:
+    """tau = min over observed pixels of N_i / A_i^2 (Alg. 1: T = min((A^-1)^dagger N A^-1) I; A = I by
+    default). Pixels with A_i = 0 carry no data and are left out like missing pixels.
 
     With no observed pixel the data carry no information and any tau > 0 gives a valid sampler;
     this code base then takes tau = max_k P_k (1 if P = 0), which makes each sweep close to an exact
     prior draw.
     """
-    obs = mask == 0
+    obs = np.asarray(mask) == 0
+    N = np.asarray(Ndiag, dtype=np.float64)
+    if A is not None:
+        A = np.asarray(A, dtype=np.float64)
+        obs = obs & (A != 0)
+        N = N / np.where(obs, A * A, 1.0)
     if np.any(obs):
-        return float(np.min(Ndiag[obs].astype(np.float64)))
+        return float(np.min(N[obs]))
     pmax = float(np.max(Pk))
     return pmax if pmax > 0 else 1.0
 
 
-def _fields(d, Ndiag, mask, Pk):
+def _fields(d, Ndiag, mask, Pk, A=None):
     d = np.asarray(d, dtype=np.float64)
     N = np.asarray(Ndiag, dtype=np.float64)
     m = np.asarray(mask) != 0
+    if A is not None:
+        m = m | (np.asarray(A) == 0)   # A_i = 0: no data at pixel i (the A_i^2 > 0 condition of Alg. 1)
     H, W = d.shape
     Pfull = dft.half_to_full(np.asarray(Pk, dtype=np.float64), W)
     return d, N, m, Pfull
 
 
-def pixel_update(s, d, N, miss, tau, lam, xi=None):
-    """Alg. 1 step 1 with T = lam*tau and N_bar = N - tau; ``xi`` = G(0,1) per pixel or None (G -> 0)."""
+def pixel_update(s, d, N, miss, tau, lam, xi=None, A=None):
+    """Alg. 1 step 1 with T = lam*tau; ``xi`` = G(0,1) per pixel or None (G -> 0).
+
+    A = I: N_bar = N - tau, mu_t = (T d + N_bar s) / (T + N_bar), var_t = T N_bar / (T + N_bar).
+    Diagonal response A (Alg. 1 definitions, pixels with A_i^2 > 0): N_bar = N - A^2 tau,
+    mu_t = T A d / (T A^2 + N_bar) + N_bar s / (T A^2 + N_bar), var_t = T N_bar / (T A^2 + N_bar).
+    """
     T = lam * tau
-    Nbar = np.where(miss, 0.0, N - tau)
-    denom = np.where(miss, 1.0, T + Nbar)
-    mu = np.where(miss, s, (T * d + Nbar * s) / denom)
+    if A is None:
+        Nbar = np.where(miss, 0.0, N - tau)
+        denom = np.where(miss, 1.0, T + Nbar)
+        mu = np.where(miss, s, (T * d + Nbar * s) / denom)
+    else:
+        A = np.asarray(A, dtype=np.float64)
+        Nbar = np.where(miss, 0.0, N - A * A * tau)
+        denom = np.where(miss, 1.0, T * A * A + Nbar)
+        mu = np.where(miss, s, T * A * d / denom + Nbar * s / denom)
     if xi is None:
         return mu
     var = np.where(miss, T, T * Nbar / denom)
@@ -163,23 +182,23 @@ def draw_zeta(seed: int, chain: int, step: int, H: int, W: int) -> np.ndarray:
 # Algorithm 1: the sampler
 # ----------------------------------------------------------------------------------------------
 def sample(d, Ndiag, mask, Pk, n_samples: int, seed: int, *, chain: int = 0, tau: float | None = None,
-           start_step: int = 0, burn_in: int = 0, thin: int = 1, init_s=None) -> np.ndarray:
+           start_step: int = 0, burn_in: int = 0, thin: int = 1, init_s=None, A=None) -> np.ndarray:
     """Draw ``n_samples`` posterior samples from one chain -> float64 [n_samples][H][W].
 
     The chain starts at ``init_s`` (zero if None) and performs burn_in + n_samples*thin sweeps; sample m
     is the state after sweep burn_in + (m+1)*thin. Sweep i uses counter step ``start_step + i``.
     """
-    d, N, miss, Pfull = _fields(d, Ndiag, mask, Pk)
+    d, N, miss, Pfull = _fields(d, Ndiag, mask, Pk, A)
     H, W = d.shape
     if tau is None:
-        tau = default_tau(N, miss, Pk)
+        tau = default_tau(N, miss, Pk, A)
     s = np.zeros((H, W)) if init_s is None else np.asarray(init_s, dtype=np.float64).copy()
     out = np.empty((n_samples, H, W))
     n_sweeps = burn_in + n_samples * thin
     m = 0
     for i in range(n_sweeps):
         step = start_step + i
-        t = pixel_update(s, d, N, miss, tau, 1.0, draw_xi(seed, chain, step, H, W))
+        t = pixel_update(s, d, N, miss, tau, 1.0, draw_xi(seed, chain, step, H, W), A)
         s = fourier_update(t, Pfull, tau, 1.0, draw_zeta(seed, chain, step, H, W))
         done = i + 1
         if done > burn_in and (done - burn_in) % thin == 0:
@@ -196,20 +215,22 @@ def apply_S(v, Pfull):
     return dft.idft2(Pfull * dft.dft2(v)).real
 
 
-def residual(s, d, Ndiag, mask, Pk, tau: float | None = None, lam: float = 1.0) -> float:
+def residual(s, d, Ndiag, mask, Pk, tau: float | None = None, lam: float = 1.0, A=None) -> float:
     """Relative residual of the Wiener-filter equation at messenger level lambda.
 
     The Wiener filter s_W = S (S + N)^-1 d (Eq. 2-3, A = I) solves (I + S N^-1) s = S N^-1 d, with
     N^-1 = 0 on missing pixels. Returns ||s + S N^-1 (s - d)|| / ||S N^-1 d|| for noise
-    N + (lambda - 1) tau I (lambda = 1: the Wiener filter itself).
+    N + (lambda - 1) tau I (lambda = 1: the Wiener filter itself). With a diagonal response A the
+    equation is (I + S A N^-1 A) s = S A N^-1 d and the level-lambda noise N + (lambda - 1) tau A^2.
     """
-    d, N, miss, Pfull = _fields(d, Ndiag, mask, Pk)
+    d, N, miss, Pfull = _fields(d, Ndiag, mask, Pk, A)
     if tau is None:
-        tau = default_tau(N, miss, Pk)
-    Ninv = np.where(miss, 0.0, 1.0 / np.where(miss, 1.0, N + (lam - 1.0) * tau))
+        tau = default_tau(N, miss, Pk, A)
+    Av = np.ones_like(d) if A is None else np.asarray(A, dtype=np.float64)
+    Ninv = np.where(miss, 0.0, 1.0 / np.where(miss, 1.0, N + (lam - 1.0) * tau * Av * Av))
     s = np.asarray(s, dtype=np.float64)
-    b = apply_S(Ninv * d, Pfull)
-    r = s + apply_S(Ninv * (s - d), Pfull)
+    b = apply_S(Av * Ninv * d, Pfull)
+    r = s + apply_S(Av * Ninv * (Av * s - d), Pfull)
     nb = np.linalg.norm(b)
     return float(np.linalg.norm(r) / nb) if nb > 0 else float(np.linalg.norm(r))
 
@@ -233,42 +254,42 @@ class CoolingSchedule:
 
 
 def wf_solve(d, Ndiag, mask, Pk, tau: float | None = None, tol: float = 1e-6, max_iter: int = 100000,
-             schedule: CoolingSchedule | None = None, init_s=None, return_history: bool = False):
+             schedule: CoolingSchedule | None = None, init_s=None, return_history: bool = False, A=None):
     """Wiener filter by the G -> 0 messenger iteration with lambda-cooling.
 
     Returns (s, iters, rho) with rho the final lambda = 1 relative residual (see :func:`residual`).
     """
-    d, N, miss, Pfull = _fields(d, Ndiag, mask, Pk)
+    d, N, miss, Pfull = _fields(d, Ndiag, mask, Pk, A)
     H, W = d.shape
     if tau is None:
-        tau = default_tau(N, miss, Pk)
+        tau = default_tau(N, miss, Pk, A)
     sch = schedule or CoolingSchedule()
     lam = sch.lambda0(Pk, tau)
     s = np.zeros((H, W)) if init_s is None else np.asarray(init_s, dtype=np.float64).copy()
     it = 0
     level_it = 0
     hist = []
-    rho = residual(s, d, N, miss, Pk, tau, 1.0)
+    rho = residual(s, d, N, miss, Pk, tau, 1.0, A)
     while it < max_iter:
-        t = pixel_update(s, d, N, miss, tau, lam)
+        t = pixel_update(s, d, N, miss, tau, lam, None, A)
         s = fourier_update(t, Pfull, tau, lam)
         it += 1
         level_it += 1
         if level_it % sch.check:
             continue
         if lam > 1.0:
-            rl = residual(s, d, N, miss, Pk, tau, lam)
+            rl = residual(s, d, N, miss, Pk, tau, lam, A)
             hist.append((it, lam, rl))
             if rl < sch.level_tol or level_it >= sch.level_max:
                 lam = max(1.0, sch.eta * lam)
                 level_it = 0
         else:
-            rho = residual(s, d, N, miss, Pk, tau, 1.0)
+            rho = residual(s, d, N, miss, Pk, tau, 1.0, A)
             hist.append((it, lam, rho))
             if rho < tol:
                 break
     if lam > 1.0 or it == 0:
-        rho = residual(s, d, N, miss, Pk, tau, 1.0)
+        rho = residual(s, d, N, miss, Pk, tau, 1.0, A)
     if return_history:
         return s, it, rho, hist
     return s, it, rho
