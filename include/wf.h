@@ -70,6 +70,10 @@ typedef struct {
                         solution e of (S^-1 + N^-1) e = r; resid_out is then the FP64 residual */
   const float* init_s; /* device [H][W] starting iterate, or NULL for zero (sizes <= 128 only) */
   double refine_tol; /* relative residual target of each correction solve */
+  const float* A;    /* device [H][W] diagonal pixel response of d = A s + n (Eq. 1), or NULL for A = I.
+                        Pixels with A = 0 carry no data. tau (default) = min over data pixels of
+                        Ndiag / A^2 (Alg. 1 definition of T). Solved as the same problem with data d / A
+                        and noise Ndiag / A^2, which the t-update of Alg. 1 with A_i^2 > 0 equals exactly */
 } wf_solve_opts;
 
 /* Options of the sampler (wf_sample_ex). Fill with wf_sample_opts_default first. */
@@ -83,6 +87,8 @@ typedef struct {
   int32_t thin;          /* sweeps between kept samples (>= 1) */
   int32_t init_per_chain;/* 1: init_s is [n_chains][H][W]; 0: one [H][W] state shared by all chains */
   const float* init_s;   /* device starting state(s), or NULL for zero */
+  const float* A;        /* device [H][W] diagonal pixel response (as wf_solve_opts::A), or NULL for A = I;
+                            not accepted by wf_sample_noalloc (WF_ERR_ARG) */
 } wf_sample_opts;
 
 void wf_solve_opts_default(wf_solve_opts* o);

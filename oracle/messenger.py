@@ -93,7 +93,8 @@ def pixel_update(s, d, N, miss, tau, lam, xi=None, A=None):
         mu = np.where(miss, s, (T * d + Nbar * s) / denom)
     else:
         A = np.asarray(A, dtype=np.float64)
-        Nbar = np.where(miss, 0.0, N - A * A * tau)
+        # N_bar >= 0 by the definition of T (min of N / A^2); the clamp only removes rounding at the minimum
+        Nbar = np.where(miss, 0.0, np.maximum(N - A * A * tau, 0.0))
         denom = np.where(miss, 1.0, T * A * A + Nbar)
         mu = np.where(miss, s, T * A * d / denom + Nbar * s / denom)
     if xi is None:

@@ -192,6 +192,53 @@ struct Carve {
   }
 };
 
+// Diagonal pixel response A of d = A s + n (Alg. 1 definitions with A_i^2 > 0): the t-update with A equals
+// the A = I update for data d / A and noise N / A^2, and A_i = 0 leaves pixel i without data. Values are
+// formed in FP64 and rounded once.
+__global__ void k_response(int n, const float* __restrict__ d, const float* __restrict__ Nd,
+                           const uint8_t* __restrict__ mask, const float* __restrict__ A, float* d2, float* N2,
+                           uint8_t* m2) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double a = A[i];
+    if (mask[i] != 0 || a == 0.0) {
+      d2[i] = 0.0f;
+      N2[i] = 1.0f;
+      m2[i] = 1;
+    } else {
+      d2[i] = float(double(d[i]) / a);
+      N2[i] = float(double(Nd[i]) / (a * a));
+      m2[i] = 0;
+    }
+  }
+}
+
+// transformed inputs of a call with a response (scratch freed with the object, stream-ordered)
+struct Response {
+  Scratch scr;
+  const float* d = nullptr;
+  const float* Nd = nullptr;
+  const uint8_t* mask = nullptr;
+};
+
+cudaError_t apply_response(const float* d, const float* Nd, const uint8_t* mask, const float* A, size_t n,
+                           cudaStream_t st, Response* r) {
+  Carve cv;
+  const size_t o_d = cv.take<float>(n), o_n = cv.take<float>(n), o_m = cv.take<uint8_t>(n);
+  r->scr.st = st;
+  cudaError_t e = cudaMallocAsync(&r->scr.base, cv.off, st);
+  if (e != cudaSuccess) return e;
+  char* b = static_cast<char*>(r->scr.base);
+  float* d2 = reinterpret_cast<float*>(b + o_d);
+  float* n2 = reinterpret_cast<float*>(b + o_n);
+  uint8_t* m2 = reinterpret_cast<uint8_t*>(b + o_m);
+  const long long blocks = (long long)(n + 255) / 256;
+  k_response<<<int(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(int(n), d, Nd, mask, A, d2, n2, m2);
+  r->d = d2;
+  r->Nd = n2;
+  r->mask = m2;
+  return cudaGetLastError();
+}
+
 // Sampler for H >= 256: fields = chains, state in global memory, one cooperative launch.
 wf_status sample_global(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int H, int W,
                         uint64_t seed, const wf_sample_opts& o, long long sweeps, float* out, cudaStream_t st,
@@ -552,6 +599,13 @@ wf_status wf_solve_ex(const float* d, const float* Ndiag, const uint8_t* mask, c
       o.max_iter < 1 || o.refine < 0 || (o.refine > 0 && !(o.refine_tol > 0.0)))
     return WF_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Response resp;
+  if (o.A) {
+    WF_CUDA(apply_response(d, Ndiag, mask, o.A, size_t(H) * W, st, &resp));
+    d = resp.d;
+    Ndiag = resp.Nd;
+    mask = resp.mask;
+  }
   KernelTimer timer(st);
   const wf_status r = o.refine > 0 ? solve_refined(d, Ndiag, mask, Pk, H, W, o, out_s, iters_out, resid_out, st, &timer)
                                    : solve_pass(d, Ndiag, mask, Pk, H, W, o, out_s, iters_out, resid_out, st, &timer);
@@ -580,6 +634,13 @@ wf_status wf_sample_ex(const float* d, const float* Ndiag, const uint8_t* mask, 
   const long long sweeps = (long long)o.burn_in + o.n_samples * (long long)o.thin;
   if (sweeps > 0x7fffffffLL || o.n_samples > 0x7fffffffLL) return WF_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Response resp;
+  if (o.A) {
+    WF_CUDA(apply_response(d, Ndiag, mask, o.A, size_t(H) * W, st, &resp));
+    d = resp.d;
+    Ndiag = resp.Nd;
+    mask = resp.mask;
+  }
   if (!size_on_chip(H)) {
     KernelTimer gt(st);
     const wf_status r = sample_global(d, Ndiag, mask, Pk, H, W, seed, o, sweeps, out, st, &gt);
@@ -1580,6 +1641,7 @@ wf_status wf_sample_noalloc(const float* d, const float* Ndiag, const uint8_t* m
                total = off_fg + align256(nm * sizeof(float2));
   if (total > kNoAllocBytes) return WF_ERR_SHAPE;  // image too large for the static scratch array
   if (o.n_samples < 0 || o.n_chains < 1 || o.burn_in < 0 || o.thin < 1) return WF_ERR_ARG;
+  if (o.A) return WF_ERR_ARG;  // the response needs transformed copies of the inputs (device memory)
   if (o.n_samples == 0) return WF_OK;
   if (!out) return WF_ERR_ARG;
   const long long sweeps = (long long)o.burn_in + o.n_samples * (long long)o.thin;

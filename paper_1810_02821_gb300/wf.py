@@ -30,13 +30,14 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("tol", ctypes.c_double), ("eta", ctypes.c_double),
                 ("level_tol", ctypes.c_double), ("level_max", ctypes.c_int32), ("check", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("refine", ctypes.c_int32), ("init_s", ctypes.c_void_p),
-                ("refine_tol", ctypes.c_double)]
+                ("refine_tol", ctypes.c_double), ("A", ctypes.c_void_p)]
 
 
 class SampleOpts(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("n_samples", ctypes.c_int64), ("n_chains", ctypes.c_int32),
                 ("chain_offset", ctypes.c_uint32), ("start_step", ctypes.c_uint32), ("burn_in", ctypes.c_int32),
-                ("thin", ctypes.c_int32), ("init_per_chain", ctypes.c_int32), ("init_s", ctypes.c_void_p)]
+                ("thin", ctypes.c_int32), ("init_per_chain", ctypes.c_int32), ("init_s", ctypes.c_void_p),
+                ("A", ctypes.c_void_p)]
 
 
 class BatchItem(ctypes.Structure):
@@ -177,7 +178,7 @@ def wf_solve(d, Ndiag, mask, Pk, tau: float = 0.0, tol: float = 1e-6, out=None, 
 
 def wf_solve_ex(d, Ndiag, mask, Pk, *, tau: float = 0.0, tol: float = 1e-6, eta: float = 0.5,
                 level_tol: float = 1e-2, level_max: int = 64, check: int = 4, max_iter: int = 20000,
-                refine: int = 0, refine_tol: float = 1e-3, init_s=None, out=None, stream=None,
+                refine: int = 0, refine_tol: float = 1e-3, init_s=None, A=None, out=None, stream=None,
                 allow_not_converged: bool = False) -> SolveResult:
     """All options of the cooled Wiener-filter solve (C call ``wf_solve_ex``).
 
@@ -185,6 +186,7 @@ def wf_solve_ex(d, Ndiag, mask, Pk, *, tau: float = 0.0, tol: float = 1e-6, eta:
     ``refine`` corrections, each an FP32 messenger solve of (S^-1 + N^-1) e = r (to relative residual
     ``refine_tol``) for the residual r = N^-1 (d - s) - S^-1 s evaluated in FP64. The returned residual is
     then the FP64 relative residual ||S r|| / ||S N^-1 d||, and ``iters`` counts the sweeps of all solves.
+    ``A``: optional CUDA float32 [H][W] diagonal pixel response of d = A s + n.
     """
     import torch
     L = load_library()
@@ -198,6 +200,7 @@ def wf_solve_ex(d, Ndiag, mask, Pk, *, tau: float = 0.0, tol: float = 1e-6, eta:
     o.level_max, o.check, o.max_iter = int(level_max), int(check), int(max_iter)
     o.refine, o.refine_tol = int(refine), float(refine_tol)
     o.init_s = _dev(init_s, torch.float32, (H, W), "init_s").value if init_s is not None else None
+    o.A = _dev(A, torch.float32, (H, W), "A").value if A is not None else None
     it = ctypes.c_int32(0)
     rs = ctypes.c_double(0.0)
     st = L.wf_solve_ex(pd, pn, pm, pp, H, W, ctypes.byref(o), po, ctypes.byref(it), ctypes.byref(rs),
@@ -221,8 +224,9 @@ def wf_sample(d, Ndiag, mask, Pk, n_samples: int, seed: int, out=None, stream=No
 
 def wf_sample_ex(d, Ndiag, mask, Pk, seed: int, n_samples: int, *, n_chains: int = 1, chain_offset: int = 0,
                  start_step: int = 0, burn_in: int = 0, thin: int = 1, tau: float = 0.0, init_s=None,
-                 out=None, stream=None):
-    """Several chains with burn-in, thinning and resume (C call ``wf_sample_ex``) -> [chains][n][H][W]."""
+                 A=None, out=None, stream=None):
+    """Several chains with burn-in, thinning and resume (C call ``wf_sample_ex``) -> [chains][n][H][W].
+    ``A``: optional CUDA float32 [H][W] diagonal pixel response of d = A s + n."""
     import torch
     L = load_library()
     H, W, pd, pn, pm, pp = _inputs(d, Ndiag, mask, Pk)
@@ -238,6 +242,7 @@ def wf_sample_ex(d, Ndiag, mask, Pk, seed: int, n_samples: int, *, n_chains: int
         shape = (n_chains, H, W) if per_chain else (H, W)
         o.init_s = _dev(init_s, torch.float32, shape, "init_s").value
         o.init_per_chain = 1 if per_chain else 0
+    o.A = _dev(A, torch.float32, (H, W), "A").value if A is not None else None
     st = L.wf_sample_ex(pd, pn, pm, pp, H, W, int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(o), po,
                         _stream_ptr(stream))
     _check(st, "wf_sample_ex")

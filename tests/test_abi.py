@@ -118,3 +118,16 @@ def test_batch_graph_argument_errors_need_no_gpu(lib):
     assert lib.wf_batch_graph_launch(None, None) == 1
     assert lib.wf_batch_graph_results(None, items, 1, None) == 1
     lib.wf_batch_graph_destroy(None)
+
+
+def test_noalloc_rejects_a_response_without_gpu(lib):
+    p = ctypes.c_void_p(16)
+    o = wf.SampleOpts()
+    lib.wf_sample_opts_default(ctypes.byref(o))
+    assert not o.A
+    o.n_samples, o.A = 1, 16
+    fn = lib.wf_sample_noalloc
+    fn.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                          ctypes.POINTER(wf.SampleOpts), ctypes.c_void_p, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    assert fn(p, p, p, p, 32, 32, 0, ctypes.byref(o), p, None) == 1
