@@ -514,9 +514,12 @@ wf_status solve_pass(const float* d, const float* Ndiag, const uint8_t* mask, co
 }
 
 // Mixed-precision iterative refinement: FP32 messenger solves, FP64 residuals (wf_refine.cu).
+// The FP32 solves use (d, Ndiag, mask); the FP64 residual uses the caller's inputs (d0, N0, m0) and
+// response A0 (null: the same inputs, A = I).
 wf_status solve_refined(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int32_t H, int32_t W,
                         const wf_solve_opts& o, float* out_s, int32_t* iters_out, double* resid_out, cudaStream_t st,
-                        wf::LaunchTimer* timer) {
+                        wf::LaunchTimer* timer, const float* d0, const float* N0, const uint8_t* m0,
+                        const float* A0) {
   wf_solve_opts first = o;
   first.tol = o.tol > 1e-5 ? o.tol : 1e-5;  // the FP32 iteration alone stops above its floor
   int32_t it = 0, total = 0;
@@ -543,9 +546,10 @@ wf_status solve_refined(const float* d, const float* Ndiag, const uint8_t* mask,
   wf::RefineArgs ra{};
   ra.H = H;
   ra.W = W;
-  ra.d = d;
-  ra.Nd = Ndiag;
-  ra.mask = mask;
+  ra.d = d0;
+  ra.Nd = N0;
+  ra.mask = m0;
+  ra.A = A0;
   ra.Pk = Pk;
   ra.s = out_s;
   ra.dn = reinterpret_cast<float2*>(b + o_dn);
@@ -599,6 +603,9 @@ wf_status wf_solve_ex(const float* d, const float* Ndiag, const uint8_t* mask, c
       o.max_iter < 1 || o.refine < 0 || (o.refine > 0 && !(o.refine_tol > 0.0)))
     return WF_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const float* d0 = d;
+  const float* N0 = Ndiag;
+  const uint8_t* m0 = mask;
   Response resp;
   if (o.A) {
     WF_CUDA(apply_response(d, Ndiag, mask, o.A, size_t(H) * W, st, &resp));
@@ -607,7 +614,8 @@ wf_status wf_solve_ex(const float* d, const float* Ndiag, const uint8_t* mask, c
     mask = resp.mask;
   }
   KernelTimer timer(st);
-  const wf_status r = o.refine > 0 ? solve_refined(d, Ndiag, mask, Pk, H, W, o, out_s, iters_out, resid_out, st, &timer)
+  const wf_status r = o.refine > 0 ? solve_refined(d, Ndiag, mask, Pk, H, W, o, out_s, iters_out, resid_out, st, &timer,
+                                                   d0, N0, m0, o.A)
                                    : solve_pass(d, Ndiag, mask, Pk, H, W, o, out_s, iters_out, resid_out, st, &timer);
   timer.collect();
   return r;

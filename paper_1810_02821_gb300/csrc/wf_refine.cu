@@ -2,11 +2,12 @@
 //   * a batched radix-2 Stockham FFT in FP64 over rows or columns of a [H][W] complex array in global
 //     memory (self-sorting, one kernel per stage; Govindaraju et al., "High performance discrete Fourier
 //     transforms on graphics processors", SC'08);
-//   * the refinement residual r = N^-1 (d - s) - S^-1 s of an FP32 iterate s and its norm ||S r||, with
-//     S = U^dagger diag(P) U applied through the FP64 transforms (S^-1 only on modes with P > 0).
-// The Wiener-filter equation (S^-1 + N^-1) s = N^-1 d (Eq. 2-3 with A = I, N^-1 = 0 on missing pixels)
-// gives (I + S N^-1) s - S N^-1 d = -S r, so ||S r|| / ||S N^-1 d|| is the relative residual used
-// everywhere else in the library, here evaluated in FP64.
+//   * the refinement residual r = A N^-1 (d - A s) - S^-1 s of an FP32 iterate s and its norm ||S r||,
+//     with S = U^dagger diag(P) U applied through the FP64 transforms (S^-1 only on modes with P > 0) and
+//     A the diagonal pixel response (A = I unless given).
+// The Wiener-filter equation (S^-1 + A N^-1 A) s = A N^-1 d (Eq. 2-3 with a diagonal response, N^-1 = 0
+// on missing pixels) gives (I + S A N^-1 A) s - S A N^-1 d = -S r, so ||S r|| / ||S A N^-1 d|| is the
+// relative residual used everywhere else in the library, here evaluated in FP64.
 #include <cuda_runtime.h>
 
 #include "wf_refine.h"
@@ -57,12 +58,14 @@ int ilog2i(int n) {
   return l;
 }
 
-// s -> (s, 0) complex; rpix = N^-1 (d - s) on observed pixels (0 on missing)
+// s -> (s, 0) complex; rpix = A N^-1 (d - A s) on observed pixels with A != 0 (A = 1 when null), else 0
 __global__ void k_ir_start(int n, const float* __restrict__ d, const float* __restrict__ Nd,
-                           const uint8_t* __restrict__ mask, const float* __restrict__ s, double2* xs, double* rpix) {
+                           const uint8_t* __restrict__ mask, const float* __restrict__ A, const float* __restrict__ s,
+                           double2* xs, double* rpix) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     xs[i] = make_double2(double(s[i]), 0.0);
-    rpix[i] = mask[i] ? 0.0 : (double(d[i]) - double(s[i])) / double(Nd[i]);
+    const double a = A ? double(A[i]) : 1.0;
+    rpix[i] = (mask[i] || a == 0.0) ? 0.0 : a * (double(d[i]) - a * double(s[i])) / double(Nd[i]);
   }
 }
 
@@ -72,13 +75,22 @@ __device__ __forceinline__ double p_full(const float* __restrict__ Pk, int H, in
   return kx <= W / 2 ? double(Pk[ky * WH + kx]) : double(Pk[((H - ky) % H) * WH + (W - kx)]);
 }
 
-// X <- X / (n P) on modes with P > 0, 0 elsewhere (forward then inverse unnormalised transforms give n)
-__global__ void k_ir_divp(int H, int W, const float* __restrict__ Pk, double2* X) {
+// X <- X / (n P) on modes with P > 0, 0 elsewhere (forward then inverse unnormalised transforms give n).
+// On the modes with P = 0 the residual s + S A N^-1 (A s - d) is s itself: out += sum |X|^2 / n there.
+__global__ void k_ir_divp(int H, int W, const float* __restrict__ Pk, double2* X, double* out) {
   const int n = H * W;
+  double acc = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const double p = p_full(Pk, H, W, i / W, i % W);
-    X[i] = p > 0.0 ? make_double2(X[i].x / (double(n) * p), X[i].y / (double(n) * p)) : make_double2(0.0, 0.0);
+    if (p > 0.0) {
+      X[i] = make_double2(X[i].x / (double(n) * p), X[i].y / (double(n) * p));
+    } else {
+      acc += (X[i].x * X[i].x + X[i].y * X[i].y) / double(n);
+      X[i] = make_double2(0.0, 0.0);
+    }
   }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(out, acc);
 }
 
 // r = rpix - Re(q); xr = (r, 0); rtab[x*H + y] = (float(r), 1/N_bar) for the correction solve
@@ -93,11 +105,13 @@ __global__ void k_ir_finish(int H, int W, const double* __restrict__ rpix, const
   }
 }
 
-// v -> (v, 0) with v = N^-1 d on observed pixels
+// v -> (v, 0) with v = A N^-1 d on observed pixels with A != 0
 __global__ void k_ir_rhs(int n, const float* __restrict__ d, const float* __restrict__ Nd,
-                         const uint8_t* __restrict__ mask, double2* x) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    x[i] = make_double2(mask[i] ? 0.0 : double(d[i]) / double(Nd[i]), 0.0);
+                         const uint8_t* __restrict__ mask, const float* __restrict__ A, double2* x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double a = A ? double(A[i]) : 1.0;
+    x[i] = make_double2((mask[i] || a == 0.0) ? 0.0 : a * double(d[i]) / double(Nd[i]), 0.0);
+  }
 }
 
 // out += sum_k P_k^2 |X_k|^2 / n (full spectrum, unnormalised X)
@@ -158,7 +172,7 @@ cudaError_t refine_bnorm(const RefineArgs& a, cudaStream_t st) {
   double2* xb = xa + n;
   cudaError_t e = cudaMemsetAsync(a.bnorm, 0, sizeof(double), st);
   if (e != cudaSuccess) return e;
-  k_ir_rhs<<<grid_for(n), 256, 0, st>>>(n, a.d, a.Nd, a.mask, xa);
+  k_ir_rhs<<<grid_for(n), 256, 0, st>>>(n, a.d, a.Nd, a.mask, a.A, xa);
   double2* X = nullptr;
   if ((e = fft2_f64(xa, xb, a.H, a.W, -1, st, &X)) != cudaSuccess) return e;
   k_ir_pnorm<<<grid_for(n), 256, 0, st>>>(a.H, a.W, a.Pk, X, a.bnorm);
@@ -172,10 +186,10 @@ cudaError_t refine_residual(const RefineArgs& a, cudaStream_t st) {
   double* rpix = reinterpret_cast<double*>(xb + n);
   cudaError_t e = cudaMemsetAsync(a.rnorm, 0, sizeof(double), st);
   if (e != cudaSuccess) return e;
-  k_ir_start<<<grid_for(n), 256, 0, st>>>(n, a.d, a.Nd, a.mask, a.s, xa, rpix);
+  k_ir_start<<<grid_for(n), 256, 0, st>>>(n, a.d, a.Nd, a.mask, a.A, a.s, xa, rpix);
   double2* X = nullptr;
   if ((e = fft2_f64(xa, xb, a.H, a.W, -1, st, &X)) != cudaSuccess) return e;
-  k_ir_divp<<<grid_for(n), 256, 0, st>>>(a.H, a.W, a.Pk, X);
+  k_ir_divp<<<grid_for(n), 256, 0, st>>>(a.H, a.W, a.Pk, X, a.rnorm);
   double2* other = X == xa ? xb : xa;
   double2* q = nullptr;
   if ((e = fft2_f64(X, other, a.H, a.W, +1, st, &q)) != cudaSuccess) return e;  // q = S^-1 s

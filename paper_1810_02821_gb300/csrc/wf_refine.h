@@ -13,6 +13,7 @@ struct RefineArgs {
   const float* d;
   const float* Nd;       // noise variance (observed pixels)
   const uint8_t* mask;
+  const float* A;        // diagonal pixel response of d = A s + n, or null for A = I
   const float* Pk;       // [H][W/2+1]
   const float* s;        // current FP32 iterate [H][W]
   const float2* dn;      // Wiener-filter pixel table [W][H] (d, 1/N_bar)

@@ -47,10 +47,10 @@ def test_wiener_filter_with_response_matches_dense(H):
     ref = dense.wiener_dense(p.d, p.Ndiag, p.mask, p.Pk, A=A)
     r = wf.wf_solve_ex(*to_dev(p), tol=1e-7, A=torch.from_numpy(A).cuda())
     assert r.status == 0 and rel(r.s.cpu().numpy(), ref) < WF_TOL
-    rr = wf.wf_solve_ex(*to_dev(p), tol=1e-8, refine=8, A=torch.from_numpy(A).cuda())
+    rr = wf.wf_solve_ex(*to_dev(p), tol=1e-7, refine=8, A=torch.from_numpy(A).cuda())
     assert rr.status == 0 and rel(rr.s.cpu().numpy(), ref) < 1e-6
     rho = M.residual(rr.s.double().cpu().numpy(), p.d, p.Ndiag, p.mask, p.Pk, A=A)
-    assert abs(rho - rr.resid) <= 1e-2 * rho + 1e-12, (rho, rr.resid)
+    assert abs(rho - rr.resid) <= 1e-3 * rho + 1e-13, (rho, rr.resid)
 
 
 def test_unit_response_is_the_identity_and_large_solve():
@@ -61,7 +61,7 @@ def test_unit_response_is_the_identity_and_large_solve():
     assert torch.equal(a, b)
     q, A = _problem(256, 5)
     q = synth.make_problem(256, seed=5, mask_frac=0.05, slope=-1.0, k0=1.0 / 4, sigma2=(0.5, 1.0))
-    r = wf.wf_solve_ex(*to_dev(q), tol=1e-7, A=torch.from_numpy(A).cuda())
+    r = wf.wf_solve_ex(*to_dev(q), tol=1e-7, refine=4, A=torch.from_numpy(A).cuda())
     ref, _, rho = M.wf_solve(q.d, q.Ndiag, q.mask, q.Pk, tol=1e-10, A=A)
     assert r.status == 0 and rho < 1e-10
     assert rel(r.s.cpu().numpy(), ref) < WF_TOL
