@@ -17,6 +17,9 @@ Printed JSON line (rank 0):
   batch_mixed_sizes 4096 images of mixed sizes (40% 64^2, 40% 128^2, 15% 256^2, 5% 512^2), each a Wiener
              solve to 1e-5 plus 64 samples, as one CUDA-graph replay with autotuned launch shapes, against
              one image per call
+  plain_32x32, precision_1024x1024, differentiation_256x256
+             the other workloads: the 32x32 plain case, the 1024x1024 solve to FP64 residual 1e-7, and
+             likelihood gradients / Wiener-map VJPs of 64 images of 256x256
 
 ``--impl reference`` times the oracle itself (the reference arm for this build) and prints the same line.
 Multi-GPU (torchrun): every rank runs the same workload on different chains (replicas, weak scaling).
@@ -284,6 +287,79 @@ def batch_mixed(dev, n_images: int = 4096, n_samples: int = 64, n_plain: int = 6
     }
 
 
+def plain_32(dev):
+    """32x32 plain-method case: Wiener solve to 1e-6, then 1000 samples of one chain from s0 = 0."""
+    import torch
+    from paper_1810_02821_gb300 import synth, wf
+    p = synth.config_plain32(0)
+    d, Nd, mk, Pk = [torch.from_numpy(x).to(dev) for x in (p.d, p.Ndiag, p.mask, p.Pk)]
+    wf.wf_solve_ex(d, Nd, mk, Pk, tol=1e-6)
+    wf.wf_sample_ex(d, Nd, mk, Pk, seed=0, n_samples=1000)
+    stream = torch.cuda.current_stream()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    r = wf.wf_solve_ex(d, Nd, mk, Pk, tol=1e-6)
+    e1.record(stream)
+    wf.wf_sample_ex(d, Nd, mk, Pk, seed=0, n_samples=1000)
+    e2.record(stream)
+    e2.synchronize()
+    return {"workload": "32x32, Wiener solve to 1e-6 then 1000 samples of one chain",
+            "solve_ms": e0.elapsed_time(e1), "solve_sweeps": r.iters,
+            "gibbs_steps_per_s_one_chain": 1000 / (e1.elapsed_time(e2) / 1e3)}
+
+
+def precision_1024(dev):
+    """1024x1024 precision case: Wiener solve to FP64 relative residual 1e-7 (iterative refinement)."""
+    import torch
+    from paper_1810_02821_gb300 import synth, wf
+    p = synth.config_precision(1024, seed=0)
+    d, Nd, mk, Pk = [torch.from_numpy(x).to(dev) for x in (p.d, p.Ndiag, p.mask, p.Pk)]
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r = wf.wf_solve_ex(d, Nd, mk, Pk, tol=1e-7, refine=8, refine_tol=1e-3, max_iter=400000)
+    e1.record(stream)
+    e1.synchronize()
+    return {"workload": "1024x1024, P ~ k^-1.5, noise variance U[0.001, 0.1], 25% in 200 circular holes; "
+                        "Wiener solve to FP64 relative residual 1e-7",
+            "time_to_solution_s": e0.elapsed_time(e1) / 1e3, "sweeps": r.iters, "fp64_resid": r.resid,
+            "status": r.status}
+
+
+def differentiation_256(dev, n_images: int = 64, n_probes: int = 8):
+    """64 images of 256x256 with P = A (k/k0)^n, N = alpha sigma2: log-likelihood gradient (quadratic term,
+    one solve; trace term, n_probes solves) and the Wiener-map VJP (one adjoint solve) per image."""
+    import numpy as np
+    import torch
+    from paper_1810_02821_gb300 import synth, wf
+    rng = np.random.default_rng(0)
+    H = 256
+    imgs = []
+    for i in range(n_images):
+        amp, slope = float(rng.uniform(0.5, 2.0)), float(rng.uniform(-2.5, -1.5))
+        q = synth.make_problem(H, seed=1000 + i, amp=amp, slope=slope, k0=1.0 / H, sigma2=(0.01, 0.2),
+                               mask_frac=0.1)
+        imgs.append((amp, slope, [torch.from_numpy(x).to(dev) for x in (q.d, q.Ndiag, q.mask)]))
+    g = torch.randn((H, H), device=dev)
+    wf.wf_loglike_grad(*imgs[0][2], imgs[0][0], imgs[0][1], 1.0 / H, 1.0, n_probes=1, tol=1e-6)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for amp, slope, (d, s2, mk) in imgs:
+        wf.wf_loglike_grad(d, s2, mk, amp, slope, 1.0 / H, 1.0, n_probes=n_probes, tol=1e-6)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for amp, slope, (d, s2, mk) in imgs:
+        s, _ = wf.wf_wiener_vjp(d, s2, mk, amp, slope, 1.0 / H, 1.0, tol=1e-6)
+        wf.wf_wiener_vjp(d, s2, mk, amp, slope, 1.0 / H, 1.0, g, s_w=s, tol=1e-6)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    return {"workload": f"{n_images} images 256x256, gradient of lnL in (A, n, alpha) with {n_probes} probes, "
+                        "and the Wiener-map VJP, one image per call",
+            "loglike_grad_images_per_s": n_images / (t1 - t0),
+            "loglike_grad_solves_per_s": n_images * (1 + n_probes) / (t1 - t0),
+            "vjp_images_per_s": n_images / (t2 - t1), "vjp_solves_per_s": 2 * n_images / (t2 - t1)}
+
+
 def main():
     global N_CHAINS, N_SAMPLES
     a = parse()
@@ -389,13 +465,20 @@ def main():
     if rank != 0:
         return
     batch = None
-    if not a.no_extras and not a.no_batch:
-        try:
-            del out
-            torch.cuda.empty_cache()
-            batch = batch_mixed(dev)
-        except Exception as ex:  # reported, never fatal for the headline line
-            batch = {"error": f"{type(ex).__name__}: {ex}"}
+    other = {}
+    if not a.no_extras:
+        del out
+        torch.cuda.empty_cache()
+        jobs = [("plain_32x32", plain_32), ("precision_1024x1024", precision_1024),
+                ("differentiation_256x256", differentiation_256)]
+        if not a.no_batch:
+            jobs.insert(0, ("batch_mixed_sizes", batch_mixed))
+        for name, fn in jobs:
+            try:
+                other[name] = fn(dev)
+            except Exception as ex:  # reported, never fatal for the headline line
+                other[name] = {"error": f"{type(ex).__name__}: {ex}"}
+        batch = other.pop("batch_mixed_sizes", None)
     kms = statistics.mean(kern_ms)
     flops = FLOPS_PER_SWEEP * N_CHAINS * N_SAMPLES
     achieved = flops / (kms / 1e3) / 1e12
@@ -417,6 +500,7 @@ def main():
                               "plain_chains_timed": n_plain} if plain else None),
         "single_chain_sweeps_per_s": single,
         "batch_mixed_sizes": batch,
+        **other,
         "clocks": clk.summary(),
         "gpu_launches": 3 * a.steps,
     }
