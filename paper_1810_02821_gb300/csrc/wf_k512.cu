@@ -1,5 +1,7 @@
 // Cooperative multi-phase kernel and launcher for 512x512 images (field in global memory).
 #define WF_LAUNCH_DEFINE_GLOBAL
+// scalar FP32 here: with the paired forms the shared-memory FFT kernels spill (measured 20-30% slower)
+#define WF_NO_F32X2 1
 #include "wf_launch.h"
 
 namespace wf {
