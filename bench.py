@@ -63,6 +63,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the plain, single-chain and batch measurements")
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed-size batch measurement")
+    ap.add_argument("--extras", default="batch,plain,precision,grad",
+                    help="extra workloads to run (comma list of batch, plain, precision, grad)")
+    ap.add_argument("--batch-images", type=int, default=4096, help="images of the mixed-size batch")
+    ap.add_argument("--batch-large-streams", type=int, default=8,
+                    help="large-image chunks per size class of the untuned batch replay")
     ap.add_argument("--chains", type=int, default=N_CHAINS, help="profiling only: chains per step")
     ap.add_argument("--samples", type=int, default=N_SAMPLES, help="profiling only: samples per chain")
     return ap.parse_args()
@@ -93,10 +98,14 @@ def aggregate_throughput(units_per_rank: int, world: int, max_ms: float) -> floa
     return units_per_rank * world / (max_ms / 1e3)
 
 
+# the sources k_sample<128,1> is compiled from (kernel, register FFT and RNG, launcher, translation unit)
+SAMPLE_KERNEL_SOURCES = ("wf_math.cuh", "wf_gibbs.cuh", "wf_launch.h", "wf_k128.cu")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1810_02821_gb300", "csrc", "*"))):
-        with open(f, "rb") as fh:
+    for name in SAMPLE_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1810_02821_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -226,7 +235,7 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
-def batch_mixed(dev, n_images: int = 4096, n_samples: int = 64, n_plain: int = 64):
+def batch_mixed(dev, n_images: int = 4096, n_samples: int = 64, n_plain: int = 64, large_streams: int = 8):
     """Mixed-size batch: Wiener solve to 1e-5 plus n_samples samples per image, all images in one graph
     replay (launch shapes autotuned on a 1/8 subset), against the same work one image per call."""
     import torch
@@ -249,7 +258,7 @@ def batch_mixed(dev, n_images: int = 4096, n_samples: int = 64, n_plain: int = 6
         e1.synchronize()
         return e0.elapsed_time(e1) / reps
 
-    with wf.BatchGraph(imgs, n_samples=n_samples, tol=1e-5) as g:
+    with wf.BatchGraph(imgs, n_samples=n_samples, tol=1e-5, large_streams=large_streams) as g:
         default_ms = replay_ms(g)
     tuned, _ = wf.wf_batch_autotune(imgs[: max(1, n_images // 8)], n_samples=n_samples, reps=1, tol=1e-5)
     with wf.BatchGraph(imgs, n_samples=n_samples, tol=1e-5, **tuned) as g:
@@ -413,28 +422,45 @@ def main():
     total_ms = max_over_ranks(sum(step_ms), world, dev)
     value = aggregate_throughput(N_CHAINS * N_SAMPLES * a.steps, world, total_ms)
 
-    # end to end through the same call: pinned host inputs -> device -> samples -> pinned host
+    # end to end through the same call: pinned host inputs -> device -> samples -> pinned host. The
+    # samples of step i go to the host on a copy stream while step i + 1 computes into the other buffer.
     e2e = None
     if not a.no_e2e:
         hin = [x.pin_memory() for x in host]
-        hout = torch.empty(out.shape, dtype=torch.float32, pin_memory=True)
+        houts = [torch.empty(out.shape, dtype=torch.float32, pin_memory=True) for _ in range(2)]
+        outs = [out, torch.empty_like(out)]
         h2d = sum(x.numel() * x.element_size() for x in hin)
-        d2h = hout.numel() * hout.element_size()
+        d2h = houts[0].numel() * houts[0].element_size()
         e2e_steps = max(1, min(a.steps, 5))
+        copy_stream = torch.cuda.Stream(device=dev)
+        copied = [None, None]
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for i in range(e2e_steps):
+            b = i % 2
             dd, nn, mm, pp = [x.to(dev, non_blocking=True) for x in hin]
+            if copied[b] is not None:
+                stream.wait_event(copied[b])             # buffer b's previous samples have reached the host
             wf.wf_sample_ex(dd, nn, mm, pp, seed=500 + i, n_samples=N_SAMPLES, n_chains=N_CHAINS,
-                            chain_offset=chain0, out=out)
-            hout.copy_(out, non_blocking=True)
+                            chain_offset=chain0, out=outs[b])
+            ready = torch.cuda.Event()
+            ready.record(stream)
+            copy_stream.wait_event(ready)
+            with torch.cuda.stream(copy_stream):
+                houts[b].copy_(outs[b], non_blocking=True)
+                copied[b] = torch.cuda.Event()
+                copied[b].record(copy_stream)
+        for ev in copied:
+            if ev is not None:
+                stream.wait_event(ev)
         e1.record(stream)
         e1.synchronize()
         ems = max_over_ranks(e0.elapsed_time(e1), world, dev)
         e2e = {"value": aggregate_throughput(N_CHAINS * N_SAMPLES * e2e_steps, world, ems), "unit": UNIT,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps}
-        del hout
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+               "note": "D2H of step i overlaps the sampling of step i + 1 (two device and two pinned buffers)"}
+        del houts, outs
 
     plain = single = None
     if a.no_extras:
@@ -469,11 +495,13 @@ def main():
     if not a.no_extras:
         del out
         torch.cuda.empty_cache()
-        jobs = [("plain_32x32", plain_32), ("precision_1024x1024", precision_1024),
-                ("differentiation_256x256", differentiation_256)]
-        if not a.no_batch:
-            jobs.insert(0, ("batch_mixed_sizes", batch_mixed))
-        for name, fn in jobs:
+        want = set(a.extras.split(","))
+        jobs = [(k, name, fn) for k, name, fn in (
+            ("batch", "batch_mixed_sizes",
+             lambda dv: batch_mixed(dv, n_images=a.batch_images, large_streams=a.batch_large_streams)),
+            ("plain", "plain_32x32", plain_32), ("precision", "precision_1024x1024", precision_1024),
+            ("grad", "differentiation_256x256", differentiation_256)) if k in want and not (k == "batch" and a.no_batch)]
+        for _, name, fn in jobs:
             try:
                 other[name] = fn(dev)
             except Exception as ex:  # reported, never fatal for the headline line
