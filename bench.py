@@ -63,8 +63,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the plain, single-chain and batch measurements")
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed-size batch measurement")
-    ap.add_argument("--extras", default="batch,plain,precision,grad",
-                    help="extra workloads to run (comma list of batch, plain, precision, grad)")
+    ap.add_argument("--extras", default="batch,plain,precision,grad,bf16",
+                    help="extra workloads to run (comma list of batch, plain, precision, grad, bf16)")
     ap.add_argument("--batch-images", type=int, default=4096, help="images of the mixed-size batch")
     ap.add_argument("--batch-large-streams", type=int, default=8,
                     help="large-image chunks per size class of the untuned batch replay")
@@ -369,6 +369,54 @@ def differentiation_256(dev, n_images: int = 64, n_probes: int = 8):
             "vjp_images_per_s": n_images / (t2 - t1), "vjp_solves_per_s": 2 * n_images / (t2 - t1)}
 
 
+def reduced_output(dev, steps: int = 3):
+    """The headline workload with samples stored as BF16 (chain in FP32, each sample rounded once): kernel
+    throughput and end-to-end throughput with half the device-to-host bytes."""
+    import torch
+    from paper_1810_02821_gb300 import synth, wf
+    p = synth.config_paper128(0)
+    host = [torch.from_numpy(x).pin_memory() for x in (p.d, p.Ndiag, p.mask, p.Pk)]
+    d, Nd, mk, Pk = [x.to(dev) for x in host]
+    outs = [torch.empty((N_CHAINS, N_SAMPLES, H, W), dtype=torch.bfloat16, device=dev) for _ in range(2)]
+    houts = [torch.empty(outs[0].shape, dtype=torch.bfloat16, pin_memory=True) for _ in range(2)]
+    stream = torch.cuda.current_stream()
+    wf.wf_sample_ex(d, Nd, mk, Pk, seed=1, n_samples=N_SAMPLES, n_chains=N_CHAINS, out=outs[0], out_dtype="bf16")
+    ks = []
+    for i in range(steps):
+        wf.wf_sample_ex(d, Nd, mk, Pk, seed=2 + i, n_samples=N_SAMPLES, n_chains=N_CHAINS, out=outs[0],
+                        out_dtype="bf16")
+        ks.append(wf.wf_last_kernel_ms())
+    copy_stream = torch.cuda.Stream(device=dev)
+    copied = [None, None]
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        b = i % 2
+        dd, nn, mm, pp = [x.to(dev, non_blocking=True) for x in host]
+        if copied[b] is not None:
+            stream.wait_event(copied[b])
+        wf.wf_sample_ex(dd, nn, mm, pp, seed=50 + i, n_samples=N_SAMPLES, n_chains=N_CHAINS, out=outs[b],
+                        out_dtype="bf16")
+        ready = torch.cuda.Event()
+        ready.record(stream)
+        copy_stream.wait_event(ready)
+        with torch.cuda.stream(copy_stream):
+            houts[b].copy_(outs[b], non_blocking=True)
+            copied[b] = torch.cuda.Event()
+            copied[b].record(copy_stream)
+    for ev in copied:
+        if ev is not None:
+            stream.wait_event(ev)
+    e1.record(stream)
+    e1.synchronize()
+    kms = statistics.mean(ks)
+    return {"workload": "paper-shaped 128x128, 1024 chains x 100 samples, samples stored as BF16",
+            "kernel_samples_per_s": N_CHAINS * N_SAMPLES / (kms / 1e3), "kernel_ms": kms,
+            "e2e_samples_per_s": N_CHAINS * N_SAMPLES * steps / (e0.elapsed_time(e1) / 1e3),
+            "d2h_bytes_per_step": houts[0].numel() * 2}
+
+
 def main():
     global N_CHAINS, N_SAMPLES
     a = parse()
@@ -500,7 +548,8 @@ def main():
             ("batch", "batch_mixed_sizes",
              lambda dv: batch_mixed(dv, n_images=a.batch_images, large_streams=a.batch_large_streams)),
             ("plain", "plain_32x32", plain_32), ("precision", "precision_1024x1024", precision_1024),
-            ("grad", "differentiation_256x256", differentiation_256)) if k in want and not (k == "batch" and a.no_batch)]
+            ("grad", "differentiation_256x256", differentiation_256),
+            ("bf16", "bf16_sample_storage", reduced_output)) if k in want and not (k == "batch" and a.no_batch)]
         for _, name, fn in jobs:
             try:
                 other[name] = fn(dev)

@@ -89,7 +89,14 @@ typedef struct {
   const float* init_s;   /* device starting state(s), or NULL for zero */
   const float* A;        /* device [H][W] diagonal pixel response (as wf_solve_opts::A), or NULL for A = I;
                             not accepted by wf_sample_noalloc (WF_ERR_ARG) */
+  int32_t out_dtype;     /* element type of `out`: WF_OUT_F32 (default), or the FP32 state rounded once to
+                            nearest even as WF_OUT_BF16 or WF_OUT_F16 (2 bytes per value; `out` then points
+                            to such elements). The chain itself always runs in FP32. */
 } wf_sample_opts;
+
+#define WF_OUT_F32 0
+#define WF_OUT_BF16 1
+#define WF_OUT_F16 2
 
 void wf_solve_opts_default(wf_solve_opts* o);
 void wf_sample_opts_default(wf_sample_opts* o);

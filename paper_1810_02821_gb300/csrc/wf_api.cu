@@ -286,6 +286,7 @@ wf_status sample_global(const float* d, const float* Ndiag, const uint8_t* mask,
   a.step0 = o.start_step;
   a.key0 = uint32_t(seed & 0xffffffffu);
   a.key1 = uint32_t(seed >> 32);
+  a.out_dtype = o.out_dtype;
   a.mode = 0;
   cudaError_t e = launch_global_any(H, a, st, timer);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -637,6 +638,7 @@ wf_status wf_sample_ex(const float* d, const float* Ndiag, const uint8_t* mask, 
   if (!d || !Ndiag || !mask || !Pk) return WF_ERR_ARG;
   if (!size_ok(H, W)) return WF_ERR_SHAPE;
   if (o.n_samples < 0 || o.n_chains < 1 || o.burn_in < 0 || o.thin < 1) return WF_ERR_ARG;
+  if (o.out_dtype < WF_OUT_F32 || o.out_dtype > WF_OUT_F16) return WF_ERR_ARG;
   if (o.n_samples == 0) return WF_OK;
   if (!out) return WF_ERR_ARG;
   const long long sweeps = (long long)o.burn_in + o.n_samples * (long long)o.thin;
@@ -675,6 +677,7 @@ wf_status wf_sample_ex(const float* d, const float* Ndiag, const uint8_t* mask, 
   a.out = out; a.n_samples = o.n_samples; a.n_chains = o.n_chains; a.n_sweeps = int(sweeps);
   a.burn_in = o.burn_in; a.thin = o.thin; a.chain0 = o.chain_offset; a.step0 = o.start_step;
   a.key0 = uint32_t(seed & 0xffffffffu); a.key1 = uint32_t(seed >> 32);
+  a.out_dtype = o.out_dtype;
   KernelTimer timer(st);
   cudaError_t e = cudaSuccess;
   switch (H) {
@@ -1650,6 +1653,7 @@ wf_status wf_sample_noalloc(const float* d, const float* Ndiag, const uint8_t* m
   if (total > kNoAllocBytes) return WF_ERR_SHAPE;  // image too large for the static scratch array
   if (o.n_samples < 0 || o.n_chains < 1 || o.burn_in < 0 || o.thin < 1) return WF_ERR_ARG;
   if (o.A) return WF_ERR_ARG;  // the response needs transformed copies of the inputs (device memory)
+  if (o.out_dtype < WF_OUT_F32 || o.out_dtype > WF_OUT_F16) return WF_ERR_ARG;
   if (o.n_samples == 0) return WF_OK;
   if (!out) return WF_ERR_ARG;
   const long long sweeps = (long long)o.burn_in + o.n_samples * (long long)o.thin;
@@ -1672,6 +1676,7 @@ wf_status wf_sample_noalloc(const float* d, const float* Ndiag, const uint8_t* m
   a.out = out; a.n_samples = o.n_samples; a.n_chains = o.n_chains; a.n_sweeps = int(sweeps);
   a.burn_in = o.burn_in; a.thin = o.thin; a.chain0 = o.chain_offset; a.step0 = o.start_step;
   a.key0 = uint32_t(seed & 0xffffffffu); a.key1 = uint32_t(seed >> 32);
+  a.out_dtype = o.out_dtype;
   cudaError_t e = cudaSuccess;
   switch (H) {
     case 16: e = wf::launch_sample<16>(a, st, nullptr); break;

@@ -298,6 +298,23 @@ WF_HD void copy_out(const float* stg, int lt, float* __restrict__ out) {
     o2[e] = s2[y * G::SP + m];
   }
 }
+// the staged field to an output image of element type t (OutType)
+#if defined(__CUDACC__)
+template <int N>
+__device__ __forceinline__ void copy_out_t(const float* stg, int lt, void* __restrict__ out, int t) {
+  using G = Geo<N>;
+  if (t == kOutF32) {
+    copy_out<N>(stg, lt, static_cast<float*>(out));
+    return;
+  }
+  const float2* s2 = reinterpret_cast<const float2*>(stg);
+#pragma unroll 4
+  for (int e = lt; e < G::H * G::LR; e += N) {
+    const int y = e / G::LR, m = e % G::LR;
+    store_pair(out, e, s2[y * G::SP + m], t);
+  }
+}
+#endif
 
 // ---------------------------------------------------------------------------------------------
 // pixel-space updates (Alg. 1 t-update), row y, c[m] = (s[2m], s[2m+1]) -> (t[2m], t[2m+1])
@@ -508,6 +525,7 @@ struct SampleArgs {
   uint32_t chain0;
   uint32_t step0;
   uint32_t key0, key1;
+  int out_dtype;         // OutType of out
 };
 
 // CTAs per SM the sample kernel is compiled for (register budget 65536 / (threads * CTAs)):
@@ -660,7 +678,7 @@ template <int N>
 __device__ __forceinline__ void sample_sweeps(float2* S, int lt, float2 (&c)[N / 2], const float2* __restrict__ aq,
                                               const float2* __restrict__ fg, float sqrt_tau, uint32_t step0,
                                               uint32_t chain, uint32_t k0, uint32_t k1, int n_sweeps, int burn_in,
-                                              int thin, float* out, bool active) {
+                                              int thin, void* out, bool active, int out_dtype = kOutF32) {
   using G = Geo<N>;
   float* stg = reinterpret_cast<float*>(S);  // staged rows (between the row load and the next store)
   float2* cs = S;                            // parked column modes (between the column load and store)
@@ -705,7 +723,9 @@ __device__ __forceinline__ void sample_sweeps(float2* S, int lt, float2 (&c)[N /
       if (done > burn_in && (done - burn_in) % thin == 0) {
         const long long m = (done - burn_in) / thin - 1;
         __syncthreads();
-        if (active) copy_out<N>(stg, lt, out + m * (long long)(G::H * G::W));
+        if (active)
+          copy_out_t<N>(stg, lt, static_cast<char*>(out) + m * (long long)(G::H * G::W) * out_elem_bytes(out_dtype),
+                        out_dtype);
         __syncthreads();
       }
       if (done == n_sweeps) break;
@@ -736,7 +756,10 @@ __global__ void __launch_bounds__(N * FPC, sample_min_ctas<N>()) k_sample(Sample
     for (int m = 0; m < G::LR; ++m) c[m] = make_float2(0.f, 0.f);
   }
   sample_sweeps<N>(S, lt, c, a.aq, a.fg, a.sc->sqrt_tau, a.step0, a.chain0 + uint32_t(ci), a.key0, a.key1,
-                   a.n_sweeps, a.burn_in, a.thin, a.out + ci * a.n_samples * (long long)(G::H * G::W), active);
+                   a.n_sweeps, a.burn_in, a.thin,
+                   reinterpret_cast<char*>(a.out) +
+                       ci * a.n_samples * (long long)(G::H * G::W) * out_elem_bytes(a.out_dtype),
+                   active, a.out_dtype);
 }
 
 struct SolveArgs {

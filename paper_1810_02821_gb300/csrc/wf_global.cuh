@@ -159,6 +159,7 @@ struct GlobalArgs {
   int nw;
   double* wout;
   int grid_pct;            // host side: percent of the co-resident grid to launch (0 or >= 100: all of it)
+  int out_dtype;           // mode 0: OutType of the samples
 };
 
 // R2C post-processing / C2R pre-processing of one padded row vector (pairs k <-> LR - k), all threads of
@@ -284,10 +285,10 @@ __device__ void row_item(const GlobalArgs& a, float2* buf, int f, int y0, int do
     const int d1 = done;  // sweeps completed
     if (d1 > a.burn_in && (d1 - a.burn_in) % a.thin == 0 && f < a.n_fields) {
       const long long ms = (d1 - a.burn_in) / a.thin - 1;
-      float* o = a.out + ((long long)f * a.n_samples + ms) * (long long)(G::H * G::W);
+      const long long base = ((long long)f * a.n_samples + ms) * (long long)(G::H * G::W) / 2;  // pairs
       for (int e = threadIdx.x; e < G::RB * L; e += nthr) {
         const int j = e / L, m = e % L;
-        reinterpret_cast<float2*>(o + (long long)(y0 + j) * G::W)[m] = buf[j * G::VROW + padi(m)];
+        store_pair(a.out, base + (long long)(y0 + j) * (G::W / 2) + m, buf[j * G::VROW + padi(m)], a.out_dtype);
       }
     }
     __syncthreads();  // the pixel update below maps threads to other elements of buf

@@ -9,6 +9,8 @@
 #include <cstdint>
 #include <utility>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #if defined(__CUDA_ARCH__)
@@ -320,6 +322,23 @@ template <int L, int... K>
 WF_HD void c2r_pre_all(float2 (&c)[L], std::integer_sequence<int, K...>) {
   (c2r_pre_pair<L, K>(c), ...);
 }
+
+// ---------------------------------------------------------------------------------------------
+// sample output element types: FP32, or the state rounded once (to nearest even) to BF16 or FP16
+// ---------------------------------------------------------------------------------------------
+enum OutType { kOutF32 = 0, kOutBF16 = 1, kOutF16 = 2 };
+WF_HD int out_elem_bytes(int t) { return t == kOutF32 ? 4 : 2; }
+// pair e = (value 2e, value 2e+1) of an output array of type t
+#if defined(__CUDACC__)
+__device__ __forceinline__ void store_pair(void* out, long long e, float2 v, int t) {
+  if (t == kOutBF16)
+    reinterpret_cast<__nv_bfloat162*>(out)[e] = __floats2bfloat162_rn(v.x, v.y);
+  else if (t == kOutF16)
+    reinterpret_cast<__half2*>(out)[e] = __floats2half2_rn(v.x, v.y);
+  else
+    reinterpret_cast<float2*>(out)[e] = v;
+}
+#endif
 
 // ---------------------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11) and Box-Muller

@@ -37,7 +37,7 @@ class SampleOpts(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("n_samples", ctypes.c_int64), ("n_chains", ctypes.c_int32),
                 ("chain_offset", ctypes.c_uint32), ("start_step", ctypes.c_uint32), ("burn_in", ctypes.c_int32),
                 ("thin", ctypes.c_int32), ("init_per_chain", ctypes.c_int32), ("init_s", ctypes.c_void_p),
-                ("A", ctypes.c_void_p)]
+                ("A", ctypes.c_void_p), ("out_dtype", ctypes.c_int32)]
 
 
 class BatchItem(ctypes.Structure):
@@ -224,15 +224,20 @@ def wf_sample(d, Ndiag, mask, Pk, n_samples: int, seed: int, out=None, stream=No
 
 def wf_sample_ex(d, Ndiag, mask, Pk, seed: int, n_samples: int, *, n_chains: int = 1, chain_offset: int = 0,
                  start_step: int = 0, burn_in: int = 0, thin: int = 1, tau: float = 0.0, init_s=None,
-                 A=None, out=None, stream=None):
+                 A=None, out_dtype: str = "f32", out=None, stream=None):
     """Several chains with burn-in, thinning and resume (C call ``wf_sample_ex``) -> [chains][n][H][W].
-    ``A``: optional CUDA float32 [H][W] diagonal pixel response of d = A s + n."""
+    ``A``: optional CUDA float32 [H][W] diagonal pixel response of d = A s + n. ``out_dtype``: "f32", or
+    "bf16" / "f16" for samples rounded once from the FP32 chain state."""
     import torch
     L = load_library()
     H, W, pd, pn, pm, pp = _inputs(d, Ndiag, mask, Pk)
+    codes = {"f32": (0, torch.float32), "bf16": (1, torch.bfloat16), "f16": (2, torch.float16)}
+    if out_dtype not in codes:
+        raise ValueError(f"out_dtype must be one of {sorted(codes)}")
+    code, tdt = codes[out_dtype]
     if out is None:
-        out = torch.empty((n_chains, n_samples, H, W), dtype=torch.float32, device=d.device)
-    po = _dev(out, torch.float32, (n_chains, n_samples, H, W), "out")
+        out = torch.empty((n_chains, n_samples, H, W), dtype=tdt, device=d.device)
+    po = _dev(out, tdt, (n_chains, n_samples, H, W), "out")
     o = SampleOpts()
     L.wf_sample_opts_default(ctypes.byref(o))
     o.tau, o.n_samples, o.n_chains = float(tau), int(n_samples), int(n_chains)
@@ -243,6 +248,7 @@ def wf_sample_ex(d, Ndiag, mask, Pk, seed: int, n_samples: int, *, n_chains: int
         o.init_s = _dev(init_s, torch.float32, shape, "init_s").value
         o.init_per_chain = 1 if per_chain else 0
     o.A = _dev(A, torch.float32, (H, W), "A").value if A is not None else None
+    o.out_dtype = code
     st = L.wf_sample_ex(pd, pn, pm, pp, H, W, int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(o), po,
                         _stream_ptr(stream))
     _check(st, "wf_sample_ex")

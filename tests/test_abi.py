@@ -131,3 +131,12 @@ def test_noalloc_rejects_a_response_without_gpu(lib):
                                           ctypes.POINTER(wf.SampleOpts), ctypes.c_void_p, ctypes.c_void_p]
     fn.restype = ctypes.c_int
     assert fn(p, p, p, p, 32, 32, 0, ctypes.byref(o), p, None) == 1
+
+
+def test_sample_output_type_validated_without_gpu(lib):
+    p = ctypes.c_void_p(16)
+    o = wf.SampleOpts()
+    lib.wf_sample_opts_default(ctypes.byref(o))
+    assert o.out_dtype == 0
+    o.n_samples, o.out_dtype = 1, 3
+    assert lib.wf_sample_ex(p, p, p, p, 32, 32, 0, ctypes.byref(o), p, None) == 1
