@@ -388,6 +388,8 @@ def reduced_output(dev, steps: int = 3):
         ks.append(wf.wf_last_kernel_ms())
     copy_stream = torch.cuda.Stream(device=dev)
     copied = [None, None]
+    for b in range(2):  # untimed: first use of both pinned buffers
+        houts[b].copy_(outs[b])
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -482,6 +484,8 @@ def main():
         e2e_steps = max(1, min(a.steps, 5))
         copy_stream = torch.cuda.Stream(device=dev)
         copied = [None, None]
+        for b in range(2):  # untimed: first use of both pinned buffers
+            houts[b].copy_(outs[b])
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
