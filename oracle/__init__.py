@@ -14,10 +14,12 @@ It is deliberately plain and slow:
 * ``dense``    — the Wiener filter of Eq. 2-3 and the posterior covariance of Eq. 4 by dense solves (with
   an optional diagonal response A);
 * ``likelihood``— the Gaussian evidence of the data for a power-law P(k) and scaled noise, and its exact
-  gradient with respect to (amplitude, slope, noise scale), by dense algebra.
+  gradient with respect to (amplitude, slope, noise scale), by dense algebra;
+* ``hierarchical``— Alg. 1 sweeps alternated with inverse-gamma draws of binned band powers (the power
+  spectrum inference of §5).
 
 Every function is pinned by ``tests/test_oracle_*.py`` against something other than itself
 (explicit DFT sums, numpy.fft, dense linear algebra, closed forms, curand's Philox, Monte-Carlo
 moments). No function is "parity unpinned".
 """
-from . import dft, philox, messenger, dense, likelihood  # noqa: F401
+from . import dft, philox, messenger, dense, likelihood, hierarchical  # noqa: F401

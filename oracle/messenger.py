@@ -161,11 +161,11 @@ def _zeta_layout(H: int, W: int):
     return group, re_slot, im_slot, kind
 
 
-def draw_zeta(seed: int, chain: int, step: int, H: int, W: int) -> np.ndarray:
-    """Hermitian complex white noise on the full spectrum [H][W] for one sweep (stream 1)."""
+def draw_zeta(seed: int, chain: int, step: int, H: int, W: int, stream: int = STREAM_S) -> np.ndarray:
+    """Hermitian complex white noise on the full spectrum [H][W] for one sweep (stream 1 by default)."""
     Hh, Wh = H // 2, W // 2
     group, re_slot, im_slot, kind = _zeta_layout(H, W)
-    z = normals4(np.arange(Wh * Hh), step, chain, STREAM_S, seed)          # [(W/2)*(H/2), 4]
+    z = normals4(np.arange(Wh * Hh), step, chain, stream, seed)            # [(W/2)*(H/2), 4]
     re = z[group, re_slot]
     im = z[group, im_slot]
     half = (re + 1j * im) / math.sqrt(2.0)

@@ -30,6 +30,7 @@ MASK32 = 0xFFFFFFFF
 STREAM_T = 0   # pixel-space messenger draw (Alg. 1, t-update)
 STREAM_S = 1   # Fourier-space signal draw (Alg. 1, s-update)
 STREAM_PROBE = 5  # Rademacher probes for stochastic traces
+STREAM_BAND = 6   # chi-square variates of the band-power draw (hierarchical sampler)
 
 
 def philox4x32_10(ctr: np.ndarray, key: tuple[int, int]) -> np.ndarray:
