@@ -63,8 +63,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the plain, single-chain and batch measurements")
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed-size batch measurement")
-    ap.add_argument("--extras", default="batch,plain,precision,grad,bf16",
-                    help="extra workloads to run (comma list of batch, plain, precision, grad, bf16)")
+    ap.add_argument("--extras", default="batch,plain,precision,grad,bf16,band",
+                    help="extra workloads to run (comma list of batch, plain, precision, grad, bf16, band)")
     ap.add_argument("--batch-images", type=int, default=4096, help="images of the mixed-size batch")
     ap.add_argument("--batch-large-streams", type=int, default=8,
                     help="large-image chunks per size class of the untuned batch replay")
@@ -419,6 +419,32 @@ def reduced_output(dev, steps: int = 3):
             "d2h_bytes_per_step": houts[0].numel() * 2}
 
 
+def band_sampler(dev):
+    """Hierarchical Gibbs sampler on the headline workload: 1024 chains x 100 sweeps of the paper-shaped
+    128x128 problem with the power spectrum drawn in integer-radius bands every sweep."""
+    import numpy as np
+    import torch
+    from paper_1810_02821_gb300 import synth, wf
+    p = synth.config_paper128(0)
+    d, Nd, mk, Pk = [torch.from_numpy(x).to(dev) for x in (p.d, p.Ndiag, p.mask, p.Pk)]
+    ky = np.fft.fftfreq(H) * H
+    r = np.sqrt(ky[:, None] ** 2 + np.arange(W // 2 + 1)[None, :] ** 2)
+    bins = np.floor(r).astype(np.int32) - 1
+    bins[0, 0] = -1
+    nb = int(bins.max()) + 1
+    bt = torch.from_numpy(bins).to(dev)
+    P0 = torch.ones(nb, device=dev)
+    wf.wf_sample_band(d, Nd, mk, Pk, bt, P0, seed=1, n_samples=N_SAMPLES, n_chains=N_CHAINS)
+    ks = []
+    for i in range(3):
+        wf.wf_sample_band(d, Nd, mk, Pk, bt, P0, seed=2 + i, n_samples=N_SAMPLES, n_chains=N_CHAINS)
+        ks.append(wf.wf_last_kernel_ms())
+    kms = statistics.mean(ks)
+    return {"workload": f"paper-shaped 128x128, 1024 chains x 100 sweeps, {nb} radial band powers drawn each sweep",
+            "samples_per_s": N_CHAINS * N_SAMPLES / (kms / 1e3), "kernel_ms": kms,
+            "n_bins": nb}
+
+
 def main():
     global N_CHAINS, N_SAMPLES
     a = parse()
@@ -553,7 +579,8 @@ def main():
              lambda dv: batch_mixed(dv, n_images=a.batch_images, large_streams=a.batch_large_streams)),
             ("plain", "plain_32x32", plain_32), ("precision", "precision_1024x1024", precision_1024),
             ("grad", "differentiation_256x256", differentiation_256),
-            ("bf16", "bf16_sample_storage", reduced_output)) if k in want and not (k == "batch" and a.no_batch)]
+            ("bf16", "bf16_sample_storage", reduced_output),
+            ("band", "hierarchical_band_sampler", band_sampler)) if k in want and not (k == "batch" and a.no_batch)]
         for _, name, fn in jobs:
             try:
                 other[name] = fn(dev)

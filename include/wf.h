@@ -141,6 +141,23 @@ wf_status wf_sample_ex(const float* d, const float* Ndiag, const uint8_t* mask, 
                        int32_t W, uint64_t seed, const wf_sample_opts* opts, float* out, wf_stream_t stream);
 
 /*
+ * Hierarchical Gibbs sampler (the power spectrum inference of §5): Alg. 1 sweeps alternated with draws of
+ * a binned power spectrum. bins: device int32 [H][W/2+1], the bin in [0, n_bins) of each half-spectrum
+ * mode, or -1 for modes whose power stays at Pk (for instance k = 0); the map must be symmetric under
+ * k -> -k, as P is. P0: device float32 [n_bins], the initial band powers (>= 0). Each sweep runs the t-draw,
+ * the s-draw with P_k = P_b(k), then the band draw P_b | s ~ InvGamma(n_b / 2, S_b / 2) (prior 1 / P_b),
+ * with S_b the sum of |U s|^2 over the full-spectrum modes of bin b and n_b their number, drawn as
+ * P_b = S_b / X_b where X_b sums n_b squared normals from Philox stream 6 in the counter layout of the
+ * s-draw (a complex mode pair gives Re^2 + Im^2, a self-conjugate mode one square). out_P (device float32
+ * [n_chains][n_samples][n_bins], may be NULL) receives the band powers of each kept sample (drawn in the
+ * same sweep). opts and out as for wf_sample_ex (opts->A must be NULL); sizes up to 128 x 128;
+ * 0 <= n_bins <= 256. A bin outside [-1, n_bins) or a negative or non-finite P0: WF_ERR_ARG.
+ */
+wf_status wf_sample_band(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, const int32_t* bins,
+                         int32_t n_bins, const float* P0, int32_t H, int32_t W, uint64_t seed,
+                         const wf_sample_opts* opts, float* out, float* out_P, wf_stream_t stream);
+
+/*
  * Batched form: many independent images of possibly different sizes, each with its own data, noise map,
  * mask, power spectrum and outputs. For every item the library computes the Wiener filter (as wf_solve_ex
  * with the options below, from zero) and then n_samples posterior samples of one chain started at the

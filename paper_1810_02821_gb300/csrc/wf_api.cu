@@ -694,6 +694,83 @@ wf_status wf_sample_ex(const float* d, const float* Ndiag, const uint8_t* mask, 
   return wf_status(hsc.status);
 }
 
+}  // extern "C"
+
+namespace {
+// bins in [-1, n_bins) and band powers finite and >= 0, else WF_ERR_ARG in sc->status
+__global__ void k_check_band(const int32_t* __restrict__ bins, int nm, int n_bins, const float* __restrict__ P0,
+                             wf::Scalars* sc) {
+  bool bad = false;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nm + n_bins; i += gridDim.x * blockDim.x) {
+    if (i < nm) {
+      bad |= bins[i] < -1 || bins[i] >= n_bins;
+    } else {
+      const float p = P0[i - nm];
+      bad |= !(p >= 0.0f) || !isfinite(p);
+    }
+  }
+  if (bad && sc->status == 0) sc->status = WF_ERR_ARG;
+}
+}  // namespace
+
+extern "C" {
+
+wf_status wf_sample_band(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, const int32_t* bins,
+                         int32_t n_bins, const float* P0, int32_t H, int32_t W, uint64_t seed,
+                         const wf_sample_opts* opts, float* out, float* out_P, wf_stream_t stream) {
+  if (!opts) return WF_ERR_ARG;
+  const wf_sample_opts o = *opts;
+  if (!d || !Ndiag || !mask || !Pk || !bins || (n_bins > 0 && !P0)) return WF_ERR_ARG;
+  if (!size_ok(H, W)) return WF_ERR_SHAPE;
+  if (!size_on_chip(H)) return WF_ERR_SHAPE;
+  if (n_bins < 0 || n_bins > 256 || o.A) return WF_ERR_ARG;
+  if (o.n_samples < 0 || o.n_chains < 1 || o.burn_in < 0 || o.thin < 1) return WF_ERR_ARG;
+  if (o.out_dtype < WF_OUT_F32 || o.out_dtype > WF_OUT_F16) return WF_ERR_ARG;
+  if (o.n_samples == 0) return WF_OK;
+  if (!out) return WF_ERR_ARG;
+  const long long sweeps = (long long)o.burn_in + o.n_samples * (long long)o.thin;
+  if (sweeps > 0x7fffffffLL || o.n_samples > 0x7fffffffLL) return WF_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t n = size_t(H) * W, nm = size_t(H) * (W / 2 + 1);
+  Carve cv;
+  const size_t off_sc = cv.take<wf::Scalars>(1), off_aq = cv.take<float2>(n), off_fg = cv.take<float2>(nm);
+  Scratch scr;
+  scr.st = st;
+  WF_CUDA(cudaMallocAsync(&scr.base, cv.off, st));
+  char* b = static_cast<char*>(scr.base);
+  auto* sc = reinterpret_cast<wf::Scalars*>(b + off_sc);
+  auto* aq = reinterpret_cast<float2*>(b + off_aq);
+  auto* fg = reinterpret_cast<float2*>(b + off_fg);
+  k_prep<<<1, 1024, 0, st>>>(d, Ndiag, mask, Pk, H, W, o.tau, 0.5, sc);
+  WF_CUDA(cudaGetLastError());
+  k_check_band<<<int((nm + n_bins + 255) / 256), 256, 0, st>>>(bins, int(nm), n_bins, P0, sc);
+  WF_CUDA(cudaGetLastError());
+  k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc, aq, nullptr, fg);
+  WF_CUDA(cudaGetLastError());
+  wf::SampleArgs a{};
+  a.aq = aq; a.fg = fg; a.sc = sc; a.init_s = o.init_s;
+  a.init_stride = (o.init_s && o.init_per_chain) ? (long long)n : 0;
+  a.out = out; a.n_samples = o.n_samples; a.n_chains = o.n_chains; a.n_sweeps = int(sweeps);
+  a.burn_in = o.burn_in; a.thin = o.thin; a.chain0 = o.chain_offset; a.step0 = o.start_step;
+  a.key0 = uint32_t(seed & 0xffffffffu); a.key1 = uint32_t(seed >> 32);
+  a.out_dtype = o.out_dtype;
+  a.bins = bins; a.n_bins = n_bins; a.P0 = P0; a.out_P = out_P;
+  KernelTimer timer(st);
+  cudaError_t e = cudaSuccess;
+  switch (H) {
+    case 16: e = wf::launch_sample_band<16>(a, st, &timer); break;
+    case 32: e = wf::launch_sample_band<32>(a, st, &timer); break;
+    case 64: e = wf::launch_sample_band<64>(a, st, &timer); break;
+    case 128: e = wf::launch_sample_band<128>(a, st, &timer); break;
+  }
+  if (e != cudaSuccess) return cuda_fail(e);
+  wf::Scalars hsc;
+  WF_CUDA(cudaMemcpyAsync(&hsc, sc, sizeof(hsc), cudaMemcpyDeviceToHost, st));
+  WF_CUDA(cudaStreamSynchronize(st));
+  timer.collect();
+  return wf_status(hsc.status);
+}
+
 wf_status wf_sample(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int32_t H, int32_t W,
                     int64_t n_samples, uint64_t seed, float* out, wf_stream_t stream) {
   wf_sample_opts o;

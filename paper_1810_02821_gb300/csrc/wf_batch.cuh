@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(N, N >= 128 ? 3 : 4) k_batch(BatchArgs b) {
     }
     __syncthreads();
     if (b.n_samples > 0 && it.out_samples != nullptr)
-      sample_sweeps<N>(S, lt, c, aq, fg, sc.sqrt_tau, 0u, it.chain, uint32_t(it.seed & 0xffffffffu),
+      sample_sweeps<N>(S, lt, c, aq, TableCoef{fg, G::WH}, sc.sqrt_tau, 0u, it.chain, uint32_t(it.seed & 0xffffffffu),
                        uint32_t(it.seed >> 32), b.n_samples, 0, 1, it.out_samples, true);
     if (lt == 0) b.res[idx] = BatchResult{rho, iters, status};
     __syncthreads();

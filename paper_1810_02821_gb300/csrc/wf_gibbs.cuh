@@ -526,7 +526,15 @@ struct SampleArgs {
   uint32_t step0;
   uint32_t key0, key1;
   int out_dtype;         // OutType of out
+  // hierarchical sampler (k_sample_band) only
+  const int* bins;       // [H][W/2+1] bin of each mode, -1: power from the table
+  int n_bins;
+  const float* P0;       // [n_bins] initial band powers
+  float* out_P;          // [n_chains][n_samples][n_bins] or nullptr
 };
+
+// shared bytes per field of the hierarchical sampler: band powers and the two FP64 accumulators
+WF_HD int band_bytes(int n_bins) { return ((n_bins * 20 + 15) / 16) * 16; }
 
 // CTAs per SM the sample kernel is compiled for (register budget 65536 / (threads * CTAs)):
 // 128^2 fields are limited to three per SM by shared memory (66.5 KB each).
@@ -607,12 +615,50 @@ WF_HD void mode_pair(int r, int kp, int& kq, int& ky1, int& ky2) {
   ky2 = r == 0 ? (kp == 0 ? G::H / 2 : G::H - 2 * kp) : G::H - 2 * kp - 1;
 }
 
+// Mode coefficients (f/n, g/sqrt(2n)) of the s-draw. TableCoef reads the per-call table; BandCoef (the
+// hierarchical sampler) derives them from the band power P_b of the mode's bin (bins >= 0, in shared
+// memory) with the same formulas as table_mode, and accumulates the band-power statistics of the new
+// modes: S_b += |s_hat|^2 (unitary scale, full spectrum) and X_b += the squares of the stream-6 normals.
+struct TableCoef {
+  static constexpr bool kBand = false;
+  const float2* __restrict__ fg;
+  int wh;
+  WF_HD float2 coef(int ky, int kx) const { return WF_LDG(fg + ky * wh + kx); }
+  WF_HD void add(int, int, float, float) const {}
+};
+struct BandCoef {
+  static constexpr bool kBand = true;
+  const float2* __restrict__ fg;
+  int wh;
+  const int* __restrict__ bins;  // [H][W/2+1], -1: the table's coefficients
+  float* Pb;                     // shared [n_bins]
+  double* acc;                   // shared [2][n_bins]: S_b then X_b
+  int n_bins;
+  float tau, inv_n, n;
+  WF_HD float2 coef(int ky, int kx) const {
+    const int b = WF_LDG(bins + ky * wh + kx);
+    if (b < 0) return WF_LDG(fg + ky * wh + kx);
+    const float P = Pb[b];
+    if (!(P > 0.0f)) return make_float2(0.0f, 0.0f);
+    const float q = P / (P + tau);
+    return make_float2(q * inv_n, sqrtf(q * tau * 0.5f * inv_n));
+  }
+  WF_HD void add(int ky, int kx, float s2, float x2) const {
+#if defined(__CUDA_ARCH__)
+    const int b = WF_LDG(bins + ky * wh + kx);
+    if (b < 0) return;
+    atomicAdd(acc + b, double(s2) * double(n));
+    atomicAdd(acc + n_bins + b, double(x2));
+#endif
+  }
+};
+
 // interior columns (col > 0): every thread but the edge thread updates its own parked modes
-template <int N>
-WF_HD void s_draw_interior(float2* cs, int lt, const float2* __restrict__ fg, uint32_t step, uint32_t chain,
-                           uint32_t k0, uint32_t k1) {
+template <int N, class Coef>
+WF_HD void s_draw_interior(float2* cs, int lt, const Coef& cf, uint32_t step, uint32_t chain, uint32_t k0,
+                           uint32_t k1) {
   using G = Geo<N>;
-  constexpr int WH = G::WH, LC = G::LC, H = G::H;
+  constexpr int LC = G::LC, H = G::H;
   const int col = lt % LC, r = lt / LC;
   if (col == 0) return;
 #pragma unroll (kRngUnroll)
@@ -623,22 +669,28 @@ WF_HD void s_draw_interior(float2* cs, int lt, const float2* __restrict__ fg, ui
     normals4(uint32_t(col * (H / 2) + ky1), step, chain, 1u, k0, k1, z);
     const int i1 = park_index<N>(lt, kp), i2 = park_index<N>(lt, kq);
     float2 y1 = cs[i1], y2 = cs[i2];
-    const float2 m1 = WF_LDG(fg + ky1 * WH + col), m2 = WF_LDG(fg + ky2 * WH + col);
+    const float2 m1 = cf.coef(ky1, col), m2 = cf.coef(ky2, col);
     y1 = make_float2(fmaf(m1.x, y1.x, m1.y * z[0]), fmaf(m1.x, y1.y, m1.y * z[1]));
     y2 = make_float2(fmaf(m2.x, y2.x, m2.y * z[2]), fmaf(m2.x, y2.y, m2.y * z[3]));
     cs[i1] = y1;
     cs[i2] = y2;
+    if constexpr (Coef::kBand) {  // both modes have their mirror in the other half plane: weight 2
+      float zb[4];
+      normals4(uint32_t(col * (H / 2) + ky1), step, chain, 6u, k0, k1, zb);
+      cf.add(ky1, col, 2.0f * (y1.x * y1.x + y1.y * y1.y), zb[0] * zb[0] + zb[1] * zb[1]);
+      cf.add(ky2, col, 2.0f * (y2.x * y2.x + y2.y * y2.y), zb[2] * zb[2] + zb[3] * zb[3]);
+    }
   }
 }
 
 // the packed edge column (col 0: kx = 0 as A and kx = W/2 as B in Y = A + i B, both Hermitian in ky):
 // its LC/2 mode pairs of role r are shared out to the threads of columns 0 .. LC/2-1 of that role
 // (one pair each), which read and write the edge thread's parked slots. Group ky1 (col 0) feeds the pair.
-template <int N>
-WF_HD void s_draw_edge(float2* cs, int lt, const float2* __restrict__ fg, uint32_t step, uint32_t chain,
-                       uint32_t k0, uint32_t k1) {
+template <int N, class Coef>
+WF_HD void s_draw_edge(float2* cs, int lt, const Coef& cf, uint32_t step, uint32_t chain, uint32_t k0,
+                       uint32_t k1) {
   using G = Geo<N>;
-  constexpr int WH = G::WH, LC = G::LC;
+  constexpr int LC = G::LC;
   const int kp = lt % LC, r = lt / LC;
   if (kp >= LC / 2) return;
   const int edge = r * LC;  // thread index of the edge thread of this role
@@ -648,13 +700,21 @@ WF_HD void s_draw_edge(float2* cs, int lt, const float2* __restrict__ fg, uint32
   normals4(uint32_t(ky1), step, chain, 1u, k0, k1, z);
   const int i1 = park_index<N>(edge, kp), i2 = park_index<N>(edge, kq);
   float2 y1 = cs[i1], y2 = cs[i2];
-  const float2 a1 = WF_LDG(fg + ky1 * WH), b1 = WF_LDG(fg + ky1 * WH + G::W / 2);
+  const float2 a1 = cf.coef(ky1, 0), b1 = cf.coef(ky1, G::W / 2);
+  float zb[4] = {0.f, 0.f, 0.f, 0.f};
+  if constexpr (Coef::kBand) normals4(uint32_t(ky1), step, chain, 6u, k0, k1, zb);
   if (ky1 == 0) {
     // group 0: the four self-conjugate modes, real with variance g^2
-    const float2 a2 = WF_LDG(fg + ky2 * WH), b2 = WF_LDG(fg + ky2 * WH + G::W / 2);
+    const float2 a2 = cf.coef(ky2, 0), b2 = cf.coef(ky2, G::W / 2);
     constexpr float R2 = 1.41421356237309505f;
     y1 = make_float2(fmaf(a1.x, y1.x, R2 * a1.y * z[0]), fmaf(b1.x, y1.y, R2 * b1.y * z[2]));
     y2 = make_float2(fmaf(a2.x, y2.x, R2 * a2.y * z[1]), fmaf(b2.x, y2.y, R2 * b2.y * z[3]));
+    if constexpr (Coef::kBand) {  // one real degree of freedom each
+      cf.add(ky1, 0, y1.x * y1.x, zb[0] * zb[0]);
+      cf.add(ky1, G::W / 2, y1.y * y1.y, zb[2] * zb[2]);
+      cf.add(ky2, 0, y2.x * y2.x, zb[1] * zb[1]);
+      cf.add(ky2, G::W / 2, y2.y * y2.y, zb[3] * zb[3]);
+    }
   } else {
     const float2 y2c = cconj(y2);
     const float2 A = cscale(cadd(y1, y2c), 0.5f);
@@ -663,9 +723,24 @@ WF_HD void s_draw_edge(float2* cs, int lt, const float2* __restrict__ fg, uint32
     const float2 Bp = make_float2(fmaf(b1.x, B.x, b1.y * z[2]), fmaf(b1.x, B.y, b1.y * z[3]));
     y1 = cadd(Ap, cmul_i(Bp));
     y2 = cadd(cconj(Ap), cmul_i(cconj(Bp)));
+    if constexpr (Coef::kBand) {  // (ky1, 0) and (ky1, W/2) with their mirrors at H - ky1: weight 2
+      cf.add(ky1, 0, 2.0f * (Ap.x * Ap.x + Ap.y * Ap.y), zb[0] * zb[0] + zb[1] * zb[1]);
+      cf.add(ky1, G::W / 2, 2.0f * (Bp.x * Bp.x + Bp.y * Bp.y), zb[2] * zb[2] + zb[3] * zb[3]);
+    }
   }
   cs[i1] = y1;
   cs[i2] = y2;
+}
+
+// band-power draw after the s-draw (all accumulations done): P_b = S_b / X_b, accumulators reset
+template <int N>
+WF_HD void band_update(const BandCoef& bc, int lt) {
+  for (int b = lt; b < bc.n_bins; b += N) {
+    const double S = bc.acc[b], X = bc.acc[bc.n_bins + b];
+    bc.Pb[b] = X > 0.0 ? float(S / X) : 0.0f;
+    bc.acc[b] = 0.0;
+    bc.acc[bc.n_bins + b] = 0.0;
+  }
 }
 
 // One sweep = four transforms, all run by the single forward-FFT block at the top of the loop (an
@@ -674,11 +749,12 @@ WF_HD void s_draw_edge(float2* cs, int lt, const float2* __restrict__ fg, uint32
 //   COL_FWD: column FFT -> s-draw on the parked modes -> conj
 //   COL_INV: conj -> store; load rows -> C2R pre-pass -> conj
 //   ROW_INV: conj -> s (pixel space) -> [write sample] -> t-draw on the staged row for the next sweep
-template <int N>
+template <int N, class Coef>
 __device__ __forceinline__ void sample_sweeps(float2* S, int lt, float2 (&c)[N / 2], const float2* __restrict__ aq,
-                                              const float2* __restrict__ fg, float sqrt_tau, uint32_t step0,
+                                              const Coef& cf, float sqrt_tau, uint32_t step0,
                                               uint32_t chain, uint32_t k0, uint32_t k1, int n_sweeps, int burn_in,
-                                              int thin, void* out, bool active, int out_dtype = kOutF32) {
+                                              int thin, void* out, bool active, int out_dtype = kOutF32,
+                                              float* out_P = nullptr) {
   using G = Geo<N>;
   float* stg = reinterpret_cast<float*>(S);  // staged rows (between the row load and the next store)
   float2* cs = S;                            // parked column modes (between the column load and store)
@@ -700,10 +776,14 @@ __device__ __forceinline__ void sample_sweeps(float2* S, int lt, float2 (&c)[N /
       phase = COL_FWD;
     } else if (phase == COL_FWD) {
       park_modes<N>(cs, lt, c);
-      s_draw_interior<N>(cs, lt, fg, step0 + uint32_t(done), chain, k0, k1);
+      s_draw_interior<N>(cs, lt, cf, step0 + uint32_t(done), chain, k0, k1);
       sync_field<N>();  // the edge thread's parked modes are visible to its helpers
-      s_draw_edge<N>(cs, lt, fg, step0 + uint32_t(done), chain, k0, k1);
+      s_draw_edge<N>(cs, lt, cf, step0 + uint32_t(done), chain, k0, k1);
       sync_field<N>();
+      if constexpr (Coef::kBand) {  // P | s: every mode's statistics are in before the band draw
+        __syncthreads();
+        band_update<N>(cf, lt);
+      }
       unpark_modes<N>(cs, lt, c);
       conj_all<G::LC>(c);
       phase = COL_INV;
@@ -726,6 +806,10 @@ __device__ __forceinline__ void sample_sweeps(float2* S, int lt, float2 (&c)[N /
         if (active)
           copy_out_t<N>(stg, lt, static_cast<char*>(out) + m * (long long)(G::H * G::W) * out_elem_bytes(out_dtype),
                         out_dtype);
+        if constexpr (Coef::kBand) {
+          if (active && out_P)
+            for (int b = lt; b < cf.n_bins; b += N) out_P[m * cf.n_bins + b] = cf.Pb[b];
+        }
         __syncthreads();
       }
       if (done == n_sweeps) break;
@@ -755,11 +839,51 @@ __global__ void __launch_bounds__(N * FPC, sample_min_ctas<N>()) k_sample(Sample
 #pragma unroll
     for (int m = 0; m < G::LR; ++m) c[m] = make_float2(0.f, 0.f);
   }
-  sample_sweeps<N>(S, lt, c, a.aq, a.fg, a.sc->sqrt_tau, a.step0, a.chain0 + uint32_t(ci), a.key0, a.key1,
+  sample_sweeps<N>(S, lt, c, a.aq, TableCoef{a.fg, G::WH}, a.sc->sqrt_tau, a.step0, a.chain0 + uint32_t(ci),
+                   a.key0, a.key1,
                    a.n_sweeps, a.burn_in, a.thin,
                    reinterpret_cast<char*>(a.out) +
                        ci * a.n_samples * (long long)(G::H * G::W) * out_elem_bytes(a.out_dtype),
                    active, a.out_dtype);
+}
+
+// The hierarchical sampler: k_sample's sweeps with the s-draw coefficients taken from band powers held in
+// shared memory and a band-power draw (P | s) after every s-draw. Field fld's band region follows the FPC
+// field buffers: accumulators [2][n_bins] doubles, then the band powers [n_bins] floats.
+template <int N, int FPC>
+__global__ void __launch_bounds__(N * FPC, sample_min_ctas<N>()) k_sample_band(SampleArgs a) {
+  using G = Geo<N>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int fld = threadIdx.x / N, lt = threadIdx.x % N;
+  const int ci = blockIdx.x * FPC + fld;
+  const bool active = ci < a.n_chains;
+  float2* S = reinterpret_cast<float2*>(smem_raw + fld * G::FIELD_BYTES);
+  unsigned char* band = smem_raw + FPC * G::FIELD_BYTES + fld * band_bytes(a.n_bins);
+  double* acc = reinterpret_cast<double*>(band);
+  float* Pb = reinterpret_cast<float*>(band + 16 * a.n_bins);
+  if (a.sc->status != 0) return;  // uniform over the grid
+  for (int b = lt; b < a.n_bins; b += N) {
+    acc[b] = 0.0;
+    acc[a.n_bins + b] = 0.0;
+    Pb[b] = a.P0[b];
+  }
+  __syncthreads();
+  float2 c[G::LR];
+  if (a.init_s != nullptr && active) {
+    const float2* src = reinterpret_cast<const float2*>(a.init_s + ci * a.init_stride + lt * G::W);
+#pragma unroll
+    for (int m = 0; m < G::LR; ++m) c[m] = WF_LDG(src + m);
+  } else {
+#pragma unroll
+    for (int m = 0; m < G::LR; ++m) c[m] = make_float2(0.f, 0.f);
+  }
+  const float tau = float(a.sc->tau);
+  const BandCoef cf{a.fg, G::WH, a.bins, Pb, acc, a.n_bins, tau, 1.0f / float(G::H * G::W), float(G::H * G::W)};
+  sample_sweeps<N>(S, lt, c, a.aq, cf, a.sc->sqrt_tau, a.step0, a.chain0 + uint32_t(ci), a.key0, a.key1,
+                   a.n_sweeps, a.burn_in, a.thin,
+                   reinterpret_cast<char*>(a.out) +
+                       ci * a.n_samples * (long long)(G::H * G::W) * out_elem_bytes(a.out_dtype),
+                   active, a.out_dtype, a.out_P ? a.out_P + ci * a.n_samples * (long long)a.n_bins : nullptr);
 }
 
 struct SolveArgs {

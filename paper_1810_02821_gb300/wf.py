@@ -74,6 +74,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                               ctypes.POINTER(D), P]
     L.wf_sample.argtypes = [P, P, P, P, I32, I32, I64, U64, P, P]
     L.wf_sample_ex.argtypes = [P, P, P, P, I32, I32, U64, ctypes.POINTER(SampleOpts), P, P]
+    L.wf_sample_band.argtypes = [P, P, P, P, P, I32, P, I32, I32, U64, ctypes.POINTER(SampleOpts), P, P, P]
+    L.wf_sample_band.restype = ctypes.c_int
     for name in ("wf_solve", "wf_solve_ex", "wf_sample", "wf_sample_ex"):
         getattr(L, name).restype = ctypes.c_int
     L.wf_solve_opts_default.argtypes = [ctypes.POINTER(SolveOpts)]
@@ -253,6 +255,38 @@ def wf_sample_ex(d, Ndiag, mask, Pk, seed: int, n_samples: int, *, n_chains: int
                         _stream_ptr(stream))
     _check(st, "wf_sample_ex")
     return out
+
+
+def wf_sample_band(d, Ndiag, mask, Pk, bins, P0, seed: int, n_samples: int, *, n_chains: int = 1,
+                   chain_offset: int = 0, start_step: int = 0, burn_in: int = 0, thin: int = 1, tau: float = 0.0,
+                   init_s=None, out_dtype: str = "f32", keep_P: bool = True, stream=None):
+    """Hierarchical Gibbs sampler (C call ``wf_sample_band``): samples [chains][n][H][W] and band powers
+    [chains][n][n_bins] (None unless ``keep_P``). ``bins``: CUDA int32 [H][W/2+1] (-1: power from Pk);
+    ``P0``: CUDA float32 [n_bins] initial band powers."""
+    import torch
+    L = load_library()
+    H, W, pd, pn, pm, pp = _inputs(d, Ndiag, mask, Pk)
+    n_bins = int(P0.numel())
+    pb = _dev(bins, torch.int32, (H, W // 2 + 1), "bins")
+    p0 = _dev(P0, torch.float32, (n_bins,), "P0")
+    codes = {"f32": (0, torch.float32), "bf16": (1, torch.bfloat16), "f16": (2, torch.float16)}
+    code, tdt = codes[out_dtype]
+    out = torch.empty((n_chains, n_samples, H, W), dtype=tdt, device=d.device)
+    outP = torch.empty((n_chains, n_samples, n_bins), dtype=torch.float32, device=d.device) if keep_P else None
+    o = SampleOpts()
+    L.wf_sample_opts_default(ctypes.byref(o))
+    o.tau, o.n_samples, o.n_chains = float(tau), int(n_samples), int(n_chains)
+    o.chain_offset, o.start_step, o.burn_in, o.thin = int(chain_offset), int(start_step), int(burn_in), int(thin)
+    if init_s is not None:
+        per_chain = init_s.dim() == 3
+        o.init_s = _dev(init_s, torch.float32, (n_chains, H, W) if per_chain else (H, W), "init_s").value
+        o.init_per_chain = 1 if per_chain else 0
+    o.out_dtype = code
+    st = L.wf_sample_band(pd, pn, pm, pp, pb, n_bins, p0, H, W, int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(o),
+                          ctypes.c_void_p(out.data_ptr()),
+                          ctypes.c_void_p(outP.data_ptr()) if outP is not None else None, _stream_ptr(stream))
+    _check(st, "wf_sample_band")
+    return out, outP
 
 
 @dataclass
