@@ -16,10 +16,12 @@ It is deliberately plain and slow:
 * ``likelihood``— the Gaussian evidence of the data for a power-law P(k) and scaled noise, and its exact
   gradient with respect to (amplitude, slope, noise scale), by dense algebra;
 * ``hierarchical``— Alg. 1 sweeps alternated with inverse-gamma draws of binned band powers (the power
-  spectrum inference of §5).
+  spectrum inference of §5);
+* ``spin2``    — shear data of a convergence field (the Kaiser-Squires operator of §5's mass mapping) in
+  the messenger sampler, its Wiener filter and posterior by dense algebra.
 
 Every function is pinned by ``tests/test_oracle_*.py`` against something other than itself
 (explicit DFT sums, numpy.fft, dense linear algebra, closed forms, curand's Philox, Monte-Carlo
 moments). No function is "parity unpinned".
 """
-from . import dft, philox, messenger, dense, likelihood, hierarchical  # noqa: F401
+from . import dft, philox, messenger, dense, likelihood, hierarchical, spin2  # noqa: F401

@@ -118,10 +118,10 @@ def fourier_update(t, Pfull, tau, lam, zeta=None):
 # ----------------------------------------------------------------------------------------------
 # Gaussian variates in the counter layout shared with the GPU
 # ----------------------------------------------------------------------------------------------
-def draw_xi(seed: int, chain: int, step: int, H: int, W: int) -> np.ndarray:
-    """Pixel-space G(0,1) field [H][W] for one sweep (stream 0)."""
+def draw_xi(seed: int, chain: int, step: int, H: int, W: int, stream: int = STREAM_T) -> np.ndarray:
+    """Pixel-space G(0,1) field [H][W] for one sweep (stream 0 by default)."""
     groups = np.arange(H * W // 4)
-    z = normals4(groups, step, chain, STREAM_T, seed)
+    z = normals4(groups, step, chain, stream, seed)
     return z.reshape(H, W)
 
 

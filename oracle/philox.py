@@ -31,6 +31,8 @@ STREAM_T = 0   # pixel-space messenger draw (Alg. 1, t-update)
 STREAM_S = 1   # Fourier-space signal draw (Alg. 1, s-update)
 STREAM_PROBE = 5  # Rademacher probes for stochastic traces
 STREAM_BAND = 6   # chi-square variates of the band-power draw (hierarchical sampler)
+STREAM_T2 = 8     # spin-2: messenger draw of the second shear component
+STREAM_SB = 9     # spin-2: Fourier-space draw of the B mode
 
 
 def philox4x32_10(ctr: np.ndarray, key: tuple[int, int]) -> np.ndarray:
