@@ -63,8 +63,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the plain, single-chain and batch measurements")
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed-size batch measurement")
-    ap.add_argument("--extras", default="batch,plain,precision,grad,bf16,band",
-                    help="extra workloads to run (comma list of batch, plain, precision, grad, bf16, band)")
+    ap.add_argument("--extras", default="batch,plain,precision,grad,bf16,band,spin2",
+                    help="extra workloads (comma list of batch, plain, precision, grad, bf16, band, spin2)")
     ap.add_argument("--batch-images", type=int, default=4096, help="images of the mixed-size batch")
     ap.add_argument("--batch-large-streams", type=int, default=8,
                     help="large-image chunks per size class of the untuned batch replay")
@@ -445,6 +445,31 @@ def band_sampler(dev):
             "n_bins": nb}
 
 
+def spin2_sampler(dev, n_chains: int = 512):
+    """Spin-2 (shear) sampler: the paper-shaped 128x128 problem as one shear component and a second
+    component of the same noise model, E spectrum as the headline's, B = 0.2 E; 512 chains x 100 sweeps."""
+    import numpy as np
+    import torch
+    from paper_1810_02821_gb300 import synth, wf
+    p = synth.config_paper128(0)
+    rng = np.random.default_rng(1)
+    d2 = np.where(p.mask == 1, 0.0, rng.standard_normal(p.d.shape)).astype(np.float32)
+    N2 = rng.uniform(0.01, 1.0, p.d.shape).astype(np.float32)
+    args = [torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+            for x in (p.d, d2, p.Ndiag, N2, p.mask, p.Pk, (0.2 * p.Pk).astype(np.float32))]
+    wf.wf_sample_spin2(*args, seed=1, n_samples=N_SAMPLES, n_chains=n_chains)
+    ks = []
+    for i in range(3):
+        wf.wf_sample_spin2(*args, seed=2 + i, n_samples=N_SAMPLES, n_chains=n_chains)
+        ks.append(wf.wf_last_kernel_ms())
+    kms = statistics.mean(ks)
+    return {"workload": f"128x128 shear pair, {n_chains} chains x 100 sweeps (4 real 2D FFTs per sweep)",
+            "samples_per_s": n_chains * N_SAMPLES / (kms / 1e3), "kernel_ms": kms,
+            "roofline": {"bound": "alu", "achieved": 2 * FLOPS_PER_SWEEP * n_chains * N_SAMPLES / (kms / 1e3) / 1e12,
+                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": 2 * FLOPS_PER_SWEEP * n_chains * N_SAMPLES / (kms / 1e3) / 1e12 / FP32_PEAK_TFLOPS}}
+
+
 def main():
     global N_CHAINS, N_SAMPLES
     a = parse()
@@ -580,7 +605,8 @@ def main():
             ("plain", "plain_32x32", plain_32), ("precision", "precision_1024x1024", precision_1024),
             ("grad", "differentiation_256x256", differentiation_256),
             ("bf16", "bf16_sample_storage", reduced_output),
-            ("band", "hierarchical_band_sampler", band_sampler)) if k in want and not (k == "batch" and a.no_batch)]
+            ("band", "hierarchical_band_sampler", band_sampler),
+            ("spin2", "spin2_shear_sampler", spin2_sampler)) if k in want and not (k == "batch" and a.no_batch)]
         for _, name, fn in jobs:
             try:
                 other[name] = fn(dev)

@@ -158,6 +158,31 @@ wf_status wf_sample_band(const float* d, const float* Ndiag, const uint8_t* mask
                          const wf_sample_opts* opts, float* out, float* out_P, wf_stream_t stream);
 
 /*
+ * Spin-2 (shear) sampler for a convergence signal (the mass mapping of §5): data are the two real shear
+ * components d1, d2 (noise variances N1, N2, one mask); the signal is kappa = kappa_E + i kappa_B with E and
+ * B power spectra PE, PB ([H][W/2+1] as Pk), seen through the Kaiser-Squires operator: in Fourier space
+ * gamma1_hat = c kappa_E_hat - s kappa_B_hat, gamma2_hat = s kappa_E_hat + c kappa_B_hat with
+ * (c, s) = (cos 2 phi, sin 2 phi), phi the angle of k = (kx, ky), and (c, s) = (1, 0) at k = 0 and on the
+ * Nyquist row and column. Each sweep is Alg. 1 for the pair: a t-draw per component (xi from Philox
+ * streams 0 and 8), then per mode the rotation into E and B, the scalar s-draw of each with its spectrum
+ * (zeta_E stream 1, zeta_B stream 9, the counter layout of wf_sample), and the rotation back. tau = the
+ * minimum observed noise variance of both components unless opts->tau > 0. out: device
+ * [n_chains][n_samples][2][H][W] shear samples (element type opts->out_dtype); opts->init_s, when given,
+ * is [2][H][W] (or [n_chains][2][H][W] with init_per_chain). Sizes up to 128 x 128; opts->A must be NULL.
+ */
+wf_status wf_sample_spin2(const float* d1, const float* d2, const float* N1, const float* N2, const uint8_t* mask,
+                          const float* PE, const float* PB, int32_t H, int32_t W, uint64_t seed,
+                          const wf_sample_opts* opts, float* out, wf_stream_t stream);
+
+/*
+ * Convergence from shear fields: kappa_E_hat = c gamma1_hat + s gamma2_hat, kappa_B_hat = -s gamma1_hat +
+ * c gamma2_hat (the inverse of the rotation above), with FP64 transforms. gamma: device [n][2][H][W];
+ * kappa: device [n][2][H][W] (E then B). Any supported size.
+ */
+wf_status wf_shear_to_convergence(const float* gamma, int64_t n, int32_t H, int32_t W, float* kappa,
+                                  wf_stream_t stream);
+
+/*
  * Batched form: many independent images of possibly different sizes, each with its own data, noise map,
  * mask, power spectrum and outputs. For every item the library computes the Wiener filter (as wf_solve_ex
  * with the options below, from zero) and then n_samples posterior samples of one chain started at the

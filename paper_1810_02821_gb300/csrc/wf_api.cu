@@ -771,6 +771,100 @@ wf_status wf_sample_band(const float* d, const float* Ndiag, const uint8_t* mask
   return wf_status(hsc.status);
 }
 
+}  // extern "C"
+
+namespace {
+// the spin-2 messenger variance: the smaller of the two components' minima (statuses combined)
+__global__ void k_min_tau(wf::Scalars* a, const wf::Scalars* b, double tau_user) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (a->status == 0 && b->status != 0) a->status = b->status;
+  if (a->status != 0) return;
+  const double t = tau_user > 0.0 ? tau_user : fmin(a->tau, b->tau);
+  a->tau = t;
+  a->sqrt_tau = float(sqrt(t));
+}
+}  // namespace
+
+extern "C" {
+
+wf_status wf_sample_spin2(const float* d1, const float* d2, const float* N1, const float* N2, const uint8_t* mask,
+                          const float* PE, const float* PB, int32_t H, int32_t W, uint64_t seed,
+                          const wf_sample_opts* opts, float* out, wf_stream_t stream) {
+  if (!opts) return WF_ERR_ARG;
+  const wf_sample_opts o = *opts;
+  if (!d1 || !d2 || !N1 || !N2 || !mask || !PE || !PB) return WF_ERR_ARG;
+  if (!size_ok(H, W)) return WF_ERR_SHAPE;
+  if (!size_on_chip(H)) return WF_ERR_SHAPE;
+  if (o.A || o.n_samples < 0 || o.n_chains < 1 || o.burn_in < 0 || o.thin < 1) return WF_ERR_ARG;
+  if (o.out_dtype < WF_OUT_F32 || o.out_dtype > WF_OUT_F16) return WF_ERR_ARG;
+  if (o.n_samples == 0) return WF_OK;
+  if (!out) return WF_ERR_ARG;
+  const long long sweeps = (long long)o.burn_in + o.n_samples * (long long)o.thin;
+  if (sweeps > 0x7fffffffLL || o.n_samples > 0x7fffffffLL) return WF_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t n = size_t(H) * W, nm = size_t(H) * (W / 2 + 1);
+  Carve cv;
+  const size_t o_sc = cv.take<wf::Scalars>(2), o_aq = cv.take<float2>(2 * n), o_fe = cv.take<float2>(nm),
+               o_fb = cv.take<float2>(nm);
+  Scratch scr;
+  scr.st = st;
+  WF_CUDA(cudaMallocAsync(&scr.base, cv.off, st));
+  char* b = static_cast<char*>(scr.base);
+  auto* sc = reinterpret_cast<wf::Scalars*>(b + o_sc);
+  auto* aq = reinterpret_cast<float2*>(b + o_aq);
+  auto* fgE = reinterpret_cast<float2*>(b + o_fe);
+  auto* fgB = reinterpret_cast<float2*>(b + o_fb);
+  // each component's set-up checks the caller's tau against its own noise (or finds its own minimum);
+  // the pair then uses the caller's tau or the smaller minimum
+  k_prep<<<1, 1024, 0, st>>>(d1, N1, mask, PE, H, W, o.tau, 0.5, sc);
+  k_prep<<<1, 1024, 0, st>>>(d2, N2, mask, PB, H, W, o.tau, 0.5, sc + 1);
+  k_min_tau<<<1, 32, 0, st>>>(sc, sc + 1, o.tau);
+  WF_CUDA(cudaGetLastError());
+  k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d1, N1, mask, PE, H, W, sc, aq, nullptr, fgE);
+  k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d2, N2, mask, PB, H, W, sc, aq + n, nullptr, fgB);
+  WF_CUDA(cudaGetLastError());
+  wf::Spin2Args a{};
+  a.aq2 = aq; a.fgE = fgE; a.fgB = fgB; a.sc = sc; a.init_s = o.init_s;
+  a.init_stride = (o.init_s && o.init_per_chain) ? 2 * (long long)n : 0;
+  a.out = out; a.n_samples = o.n_samples; a.n_chains = o.n_chains; a.n_sweeps = int(sweeps);
+  a.burn_in = o.burn_in; a.thin = o.thin; a.chain0 = o.chain_offset; a.step0 = o.start_step;
+  a.key0 = uint32_t(seed & 0xffffffffu); a.key1 = uint32_t(seed >> 32);
+  a.out_dtype = o.out_dtype;
+  KernelTimer timer(st);
+  cudaError_t e = cudaSuccess;
+  switch (H) {
+    case 16: e = wf::launch_sample_spin2<16>(a, st, &timer); break;
+    case 32: e = wf::launch_sample_spin2<32>(a, st, &timer); break;
+    case 64: e = wf::launch_sample_spin2<64>(a, st, &timer); break;
+    case 128: e = wf::launch_sample_spin2<128>(a, st, &timer); break;
+  }
+  if (e != cudaSuccess) return cuda_fail(e);
+  wf::Scalars hsc;
+  WF_CUDA(cudaMemcpyAsync(&hsc, sc, sizeof(hsc), cudaMemcpyDeviceToHost, st));
+  WF_CUDA(cudaStreamSynchronize(st));
+  timer.collect();
+  return wf_status(hsc.status);
+}
+
+wf_status wf_shear_to_convergence(const float* gamma, int64_t n_fields, int32_t H, int32_t W, float* kappa,
+                                  wf_stream_t stream) {
+  if (!gamma || !kappa || n_fields < 0) return WF_ERR_ARG;
+  if (!size_ok(H, W)) return WF_ERR_SHAPE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t n = size_t(H) * W;
+  Scratch scr;
+  scr.st = st;
+  WF_CUDA(cudaMallocAsync(&scr.base, 4 * n * sizeof(double2), st));
+  for (int64_t i = 0; i < n_fields; ++i) {
+    const float* g = gamma + i * 2 * n;
+    float* k = kappa + i * 2 * n;
+    cudaError_t e = wf::shear_to_convergence_f64(g, g + n, H, W, k, k + n, scr.base, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  WF_CUDA(cudaStreamSynchronize(st));
+  return WF_OK;
+}
+
 wf_status wf_sample(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int32_t H, int32_t W,
                     int64_t n_samples, uint64_t seed, float* out, wf_stream_t stream) {
   wf_sample_opts o;

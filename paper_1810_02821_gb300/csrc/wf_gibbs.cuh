@@ -20,6 +20,7 @@
 #include <cmath>
 #include <cstdint>
 #include <limits>
+#include <type_traits>
 
 #include "wf_math.cuh"
 
@@ -559,13 +560,13 @@ constexpr int sample_min_ctas() { return N >= 128 ? WF_SAMPLE_MIN_CTAS_128 : (N 
 // group y*W/4 + q feeds pixels 4q .. 4q+3.
 template <int N>
 WF_HD void t_draw_staged(float* stg, int y, const float2* __restrict__ aq, float sqrt_tau, uint32_t step,
-                         uint32_t chain, uint32_t k0, uint32_t k1) {
+                         uint32_t chain, uint32_t k0, uint32_t k1, uint32_t stream = 0u) {
   using G = Geo<N>;
   float2* row = reinterpret_cast<float2*>(stg) + y * G::SP;  // (s[2m], s[2m+1]) pairs
 #pragma unroll (kRngUnroll)
   for (int q = 0; q < G::W / 4; ++q) {
     float z[4];
-    normals4(uint32_t(y * (G::W / 4) + q), step, chain, 0u, k0, k1, z);
+    normals4(uint32_t(y * (G::W / 4) + q), step, chain, stream, k0, k1, z);
     float2 p0 = row[2 * q], p1 = row[2 * q + 1];
     const float2 c0 = WF_LDG(aq + (4 * q) * G::H + y), c1 = WF_LDG(aq + (4 * q + 1) * G::H + y);
     const float2 c2 = WF_LDG(aq + (4 * q + 2) * G::H + y), c3 = WF_LDG(aq + (4 * q + 3) * G::H + y);
@@ -732,6 +733,130 @@ WF_HD void s_draw_edge(float2* cs, int lt, const Coef& cf, uint32_t step, uint32
   cs[i2] = y2;
 }
 
+// Spin-2 (shear) sampler: the two shear components are two fields of one CTA (component = field index
+// mod 2) and the s-draw couples them per mode: rotate (t1_hat, t2_hat) by the Kaiser-Squires angle into
+// E and B, draw each with its own spectrum (tables fgE, fgB; E draws from stream 1, B from stream 9 in the
+// counter layout of the scalar s-draw), rotate back. (c, s) = (cos 2 phi, sin 2 phi) of k = (kx, ky), with
+// (1, 0) at k = 0 and on the Nyquist row and column.
+struct Spin2Coef {
+  static constexpr bool kBand = false;
+  const float2* __restrict__ fgE;
+  const float2* __restrict__ fgB;
+  int wh;
+  float2* cs0;  // parked modes of component 1 and 2 (shared)
+  float2* cs1;
+  int comp;
+  WF_HD float2 coef(int, int) const { return make_float2(0.f, 0.f); }
+  WF_HD void add(int, int, float, float) const {}
+};
+
+template <int N>
+WF_HD void ks_rot(int ky, int kx, float& c, float& s) {
+  using G = Geo<N>;
+  const int y = ky < G::H / 2 ? ky : ky - G::H;  // folded row frequency
+  if ((kx == 0 && y == 0) || ky == G::H / 2 || kx == G::W / 2) {
+    c = 1.0f;
+    s = 0.0f;
+    return;
+  }
+  const float k1 = float(kx), k2 = float(y), r = 1.0f / (k1 * k1 + k2 * k2);
+  c = (k1 * k1 - k2 * k2) * r;
+  s = 2.0f * k1 * k2 * r;
+}
+
+// one complex mode: (a, b) = (t1_hat, t2_hat) -> new (gamma1_hat, gamma2_hat); mE, mB = (f/n, g/sqrt(2n))
+WF_HD void spin2_mode(float2& a, float2& b, float c, float s, float2 mE, float2 mB, float zE0, float zE1, float zB0,
+                      float zB1) {
+  const float2 e = make_float2(fmaf(c, a.x, s * b.x), fmaf(c, a.y, s * b.y));
+  const float2 q = make_float2(fmaf(c, b.x, -s * a.x), fmaf(c, b.y, -s * a.y));
+  const float2 e2 = make_float2(fmaf(mE.x, e.x, mE.y * zE0), fmaf(mE.x, e.y, mE.y * zE1));
+  const float2 q2 = make_float2(fmaf(mB.x, q.x, mB.y * zB0), fmaf(mB.x, q.y, mB.y * zB1));
+  a = make_float2(fmaf(c, e2.x, -s * q2.x), fmaf(c, e2.y, -s * q2.y));
+  b = make_float2(fmaf(s, e2.x, c * q2.x), fmaf(s, e2.y, c * q2.y));
+}
+
+// interior columns: the pairs of column thread (col, r) are shared out to the two components' threads
+template <int N>
+WF_HD void spin2_interior(const Spin2Coef& cf, int lt, uint32_t step, uint32_t chain, uint32_t k0, uint32_t k1) {
+  using G = Geo<N>;
+  constexpr int LC = G::LC, H = G::H;
+  const int col = lt % LC, r = lt / LC;
+  if (col == 0) return;
+  const int kp0 = cf.comp == 0 ? 0 : LC / 4, kp1 = cf.comp == 0 ? LC / 4 : LC / 2;
+#pragma unroll 2
+  for (int kp = kp0; kp < kp1; ++kp) {
+    int kq, ky1, ky2;
+    mode_pair<N>(r, kp, kq, ky1, ky2);
+    float zE[4], zB[4];
+    normals4(uint32_t(col * (H / 2) + ky1), step, chain, 1u, k0, k1, zE);
+    normals4(uint32_t(col * (H / 2) + ky1), step, chain, 9u, k0, k1, zB);
+    const int i1 = park_index<N>(lt, kp), i2 = park_index<N>(lt, kq);
+    float2 a1 = cf.cs0[i1], b1 = cf.cs1[i1], a2 = cf.cs0[i2], b2 = cf.cs1[i2];
+    float c, s;
+    ks_rot<N>(ky1, col, c, s);
+    spin2_mode(a1, b1, c, s, WF_LDG(cf.fgE + ky1 * cf.wh + col), WF_LDG(cf.fgB + ky1 * cf.wh + col), zE[0], zE[1],
+               zB[0], zB[1]);
+    ks_rot<N>(ky2, col, c, s);
+    spin2_mode(a2, b2, c, s, WF_LDG(cf.fgE + ky2 * cf.wh + col), WF_LDG(cf.fgB + ky2 * cf.wh + col), zE[2], zE[3],
+               zB[2], zB[3]);
+    cf.cs0[i1] = a1;
+    cf.cs1[i1] = b1;
+    cf.cs0[i2] = a2;
+    cf.cs1[i2] = b2;
+  }
+}
+
+// the packed edge column (kx = 0 as A and kx = W/2 as B in Y = A + i B) of both components, by the first
+// component's threads of columns 0 .. LC/2-1 (one mode pair each)
+template <int N>
+WF_HD void spin2_edge(const Spin2Coef& cf, int lt, uint32_t step, uint32_t chain, uint32_t k0, uint32_t k1) {
+  using G = Geo<N>;
+  constexpr int LC = G::LC, WH2 = G::W / 2;
+  const int kp = lt % LC, r = lt / LC;
+  if (cf.comp != 0 || kp >= LC / 2) return;
+  const int edge = r * LC;
+  int kq, ky1, ky2;
+  mode_pair<N>(r, kp, kq, ky1, ky2);
+  float zE[4], zB[4];
+  normals4(uint32_t(ky1), step, chain, 1u, k0, k1, zE);
+  normals4(uint32_t(ky1), step, chain, 9u, k0, k1, zB);
+  const int i1 = park_index<N>(edge, kp), i2 = park_index<N>(edge, kq);
+  float2 y1a = cf.cs0[i1], y2a = cf.cs0[i2], y1b = cf.cs1[i1], y2b = cf.cs1[i2];
+  const int wh = cf.wh;
+  if (ky1 == 0) {
+    // four real modes, each on k = 0 or a Nyquist line: no rotation, real draws with variance g^2
+    constexpr float R2 = 1.41421356237309505f;
+    auto upd = [&](float& a, float& b, int ky, int kx, float ze, float zb) {
+      const float2 mE = WF_LDG(cf.fgE + ky * wh + kx), mB = WF_LDG(cf.fgB + ky * wh + kx);
+      a = fmaf(mE.x, a, R2 * mE.y * ze);
+      b = fmaf(mB.x, b, R2 * mB.y * zb);
+    };
+    upd(y1a.x, y1b.x, ky1, 0, zE[0], zB[0]);
+    upd(y1a.y, y1b.y, ky1, WH2, zE[2], zB[2]);
+    upd(y2a.x, y2b.x, ky2, 0, zE[1], zB[1]);
+    upd(y2a.y, y2b.y, ky2, WH2, zE[3], zB[3]);
+  } else {
+    // unpack both components: A = value at (ky1, 0), B = value at (ky1, W/2)
+    const float2 Aa = cscale(cadd(y1a, cconj(y2a)), 0.5f), Ba = cmul_mi(cscale(csub(y1a, cconj(y2a)), 0.5f));
+    const float2 Ab = cscale(cadd(y1b, cconj(y2b)), 0.5f), Bb = cmul_mi(cscale(csub(y1b, cconj(y2b)), 0.5f));
+    float2 A1 = Aa, A2 = Ab, B1 = Ba, B2 = Bb;
+    float c, s;
+    ks_rot<N>(ky1, 0, c, s);
+    spin2_mode(A1, A2, c, s, WF_LDG(cf.fgE + ky1 * wh), WF_LDG(cf.fgB + ky1 * wh), zE[0], zE[1], zB[0], zB[1]);
+    ks_rot<N>(ky1, WH2, c, s);
+    spin2_mode(B1, B2, c, s, WF_LDG(cf.fgE + ky1 * wh + WH2), WF_LDG(cf.fgB + ky1 * wh + WH2), zE[2], zE[3], zB[2],
+               zB[3]);
+    y1a = cadd(A1, cmul_i(B1));
+    y2a = cadd(cconj(A1), cmul_i(cconj(B1)));
+    y1b = cadd(A2, cmul_i(B2));
+    y2b = cadd(cconj(A2), cmul_i(cconj(B2)));
+  }
+  cf.cs0[i1] = y1a;
+  cf.cs0[i2] = y2a;
+  cf.cs1[i1] = y1b;
+  cf.cs1[i2] = y2b;
+}
+
 // band-power draw after the s-draw (all accumulations done): P_b = S_b / X_b, accumulators reset
 template <int N>
 WF_HD void band_update(const BandCoef& bc, int lt) {
@@ -754,12 +879,13 @@ __device__ __forceinline__ void sample_sweeps(float2* S, int lt, float2 (&c)[N /
                                               const Coef& cf, float sqrt_tau, uint32_t step0,
                                               uint32_t chain, uint32_t k0, uint32_t k1, int n_sweeps, int burn_in,
                                               int thin, void* out, bool active, int out_dtype = kOutF32,
-                                              float* out_P = nullptr) {
+                                              float* out_P = nullptr, uint32_t t_stream = 0u,
+                                              long long out_stride = (long long)N * N) {
   using G = Geo<N>;
   float* stg = reinterpret_cast<float*>(S);  // staged rows (between the row load and the next store)
   float2* cs = S;                            // parked column modes (between the column load and store)
   stage_row<N>(stg, lt, c);
-  t_draw_staged<N>(stg, lt, aq, sqrt_tau, step0, chain, k0, k1);
+  t_draw_staged<N>(stg, lt, aq, sqrt_tau, step0, chain, k0, k1, t_stream);
   load_staged_row<N>(stg, lt, c);
 
   enum { ROW_FWD, COL_FWD, COL_INV, ROW_INV };
@@ -776,10 +902,17 @@ __device__ __forceinline__ void sample_sweeps(float2* S, int lt, float2 (&c)[N /
       phase = COL_FWD;
     } else if (phase == COL_FWD) {
       park_modes<N>(cs, lt, c);
-      s_draw_interior<N>(cs, lt, cf, step0 + uint32_t(done), chain, k0, k1);
-      sync_field<N>();  // the edge thread's parked modes are visible to its helpers
-      s_draw_edge<N>(cs, lt, cf, step0 + uint32_t(done), chain, k0, k1);
-      sync_field<N>();
+      if constexpr (std::is_same<Coef, Spin2Coef>::value) {  // both components parked, then coupled
+        __syncthreads();
+        spin2_interior<N>(cf, lt, step0 + uint32_t(done), chain, k0, k1);
+        spin2_edge<N>(cf, lt, step0 + uint32_t(done), chain, k0, k1);
+        __syncthreads();
+      } else {
+        s_draw_interior<N>(cs, lt, cf, step0 + uint32_t(done), chain, k0, k1);
+        sync_field<N>();  // the edge thread's parked modes are visible to its helpers
+        s_draw_edge<N>(cs, lt, cf, step0 + uint32_t(done), chain, k0, k1);
+        sync_field<N>();
+      }
       if constexpr (Coef::kBand) {  // P | s: every mode's statistics are in before the band draw
         __syncthreads();
         band_update<N>(cf, lt);
@@ -804,8 +937,7 @@ __device__ __forceinline__ void sample_sweeps(float2* S, int lt, float2 (&c)[N /
         const long long m = (done - burn_in) / thin - 1;
         __syncthreads();
         if (active)
-          copy_out_t<N>(stg, lt, static_cast<char*>(out) + m * (long long)(G::H * G::W) * out_elem_bytes(out_dtype),
-                        out_dtype);
+          copy_out_t<N>(stg, lt, static_cast<char*>(out) + m * out_stride * out_elem_bytes(out_dtype), out_dtype);
         if constexpr (Coef::kBand) {
           if (active && out_P)
             for (int b = lt; b < cf.n_bins; b += N) out_P[m * cf.n_bins + b] = cf.Pb[b];
@@ -813,7 +945,7 @@ __device__ __forceinline__ void sample_sweeps(float2* S, int lt, float2 (&c)[N /
         __syncthreads();
       }
       if (done == n_sweeps) break;
-      t_draw_staged<N>(stg, lt, aq, sqrt_tau, step0 + uint32_t(done), chain, k0, k1);
+      t_draw_staged<N>(stg, lt, aq, sqrt_tau, step0 + uint32_t(done), chain, k0, k1, t_stream);
       load_staged_row<N>(stg, lt, c);
       phase = ROW_FWD;
     }
@@ -884,6 +1016,58 @@ __global__ void __launch_bounds__(N * FPC, sample_min_ctas<N>()) k_sample_band(S
                    reinterpret_cast<char*>(a.out) +
                        ci * a.n_samples * (long long)(G::H * G::W) * out_elem_bytes(a.out_dtype),
                    active, a.out_dtype, a.out_P ? a.out_P + ci * a.n_samples * (long long)a.n_bins : nullptr);
+}
+
+// Spin-2 sampler: CTA = FPC images x 2 shear components, component fields interleaved (field 2 i + comp);
+// tables aq2 [2][W][H] (per component), fgE and fgB [H][W/2+1]; out [n_chains][n_samples][2][H][W];
+// init_s [2][H][W] per image when given (init_stride elements between chains).
+struct Spin2Args {
+  const float2* aq2;
+  const float2* fgE;
+  const float2* fgB;
+  const Scalars* sc;
+  const float* init_s;
+  long long init_stride;
+  float* out;
+  long long n_samples;
+  int n_chains;
+  int n_sweeps;
+  int burn_in;
+  int thin;
+  uint32_t chain0;
+  uint32_t step0;
+  uint32_t key0, key1;
+  int out_dtype;
+};
+
+template <int N, int FPC>
+__global__ void __launch_bounds__(2 * N * FPC, 1) k_sample_spin2(Spin2Args a) {
+  using G = Geo<N>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int fld = threadIdx.x / N, lt = threadIdx.x % N;
+  const int img = fld / 2, comp = fld % 2;
+  const int ci = blockIdx.x * FPC + img;
+  const bool active = ci < a.n_chains;
+  float2* S = reinterpret_cast<float2*>(smem_raw + fld * G::FIELD_BYTES);
+  float2* S0 = reinterpret_cast<float2*>(smem_raw + (2 * img) * G::FIELD_BYTES);
+  float2* S1 = reinterpret_cast<float2*>(smem_raw + (2 * img + 1) * G::FIELD_BYTES);
+  if (a.sc->status != 0) return;  // uniform over the grid
+  float2 c[G::LR];
+  if (a.init_s != nullptr && active) {
+    const float2* src =
+        reinterpret_cast<const float2*>(a.init_s + ci * a.init_stride + comp * (long long)(G::H * G::W) + lt * G::W);
+#pragma unroll
+    for (int m = 0; m < G::LR; ++m) c[m] = WF_LDG(src + m);
+  } else {
+#pragma unroll
+    for (int m = 0; m < G::LR; ++m) c[m] = make_float2(0.f, 0.f);
+  }
+  const Spin2Coef cf{a.fgE, a.fgB, G::WH, S0, S1, comp};
+  const long long n = (long long)(G::H * G::W);
+  sample_sweeps<N>(S, lt, c, a.aq2 + comp * n, cf, a.sc->sqrt_tau, a.step0, a.chain0 + uint32_t(ci), a.key0, a.key1,
+                   a.n_sweeps, a.burn_in, a.thin,
+                   reinterpret_cast<char*>(a.out) + (ci * a.n_samples * 2 + comp) * n * out_elem_bytes(a.out_dtype),
+                   active, a.out_dtype, nullptr, comp == 0 ? 0u : 8u, 2 * n);
 }
 
 struct SolveArgs {

@@ -27,6 +27,9 @@ template <int N>
 cudaError_t launch_sample_band(const SampleArgs& a, cudaStream_t st, LaunchTimer* t);
 
 template <int N>
+cudaError_t launch_sample_spin2(const Spin2Args& a, cudaStream_t st, LaunchTimer* t);
+
+template <int N>
 cudaError_t launch_solve(const SolveArgs& a, const BnormArgs& b, cudaStream_t st, LaunchTimer* t);
 
 // batched persistent form for N <= 128: grid = min(items, resident CTAs), per-CTA scratch slots
@@ -73,6 +76,20 @@ cudaError_t launch_sample_band(const SampleArgs& a, cudaStream_t st, LaunchTimer
   const int blocks = (a.n_chains + FPC - 1) / FPC;
   if (t) t->start();
   kern<<<blocks, N * FPC, smem, st>>>(a);
+  if (t) t->stop();
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_sample_spin2(const Spin2Args& a, cudaStream_t st, LaunchTimer* t) {
+  constexpr int FPC = fields_per_cta<N>();  // images per CTA; two component fields each
+  const int smem = 2 * FPC * Geo<N>::FIELD_BYTES;
+  auto kern = k_sample_spin2<N, FPC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const int blocks = (a.n_chains + FPC - 1) / FPC;
+  if (t) t->start();
+  kern<<<blocks, 2 * N * FPC, smem, st>>>(a);
   if (t) t->stop();
   return cudaGetLastError();
 }
@@ -134,6 +151,7 @@ cudaError_t launch_wpower(const WpowerArgs& p, cudaStream_t st) {
 #define WF_INSTANTIATE(N)                                                              \
   template cudaError_t launch_sample<N>(const SampleArgs&, cudaStream_t, LaunchTimer*); \
   template cudaError_t launch_sample_band<N>(const SampleArgs&, cudaStream_t, LaunchTimer*); \
+  template cudaError_t launch_sample_spin2<N>(const Spin2Args&, cudaStream_t, LaunchTimer*); \
   template cudaError_t launch_solve<N>(const SolveArgs&, const BnormArgs&, cudaStream_t, LaunchTimer*); \
   template cudaError_t launch_batch<N>(const BatchArgs&, int*, cudaStream_t);                     \
   template cudaError_t batch_grid<N>(int, int, int*);                                                   \

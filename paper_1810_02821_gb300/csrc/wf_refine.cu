@@ -241,6 +241,57 @@ cudaError_t apply_S_f64(const float* v, const float* Pk, int H, int W, float* ou
   return cudaGetLastError();
 }
 
+namespace {
+
+// rotation (c, s) of the Kaiser-Squires operator at full-spectrum mode (ky, kx), as in the samplers
+__device__ __forceinline__ void ks_rot_d(int H, int W, int ky, int kx, double& c, double& s) {
+  const int y = ky < H / 2 ? ky : ky - H, x = kx < W / 2 ? kx : kx - W;
+  if ((x == 0 && y == 0) || ky == H / 2 || kx == W / 2) {
+    c = 1.0;
+    s = 0.0;
+    return;
+  }
+  const double k1 = x, k2 = y, r = 1.0 / (k1 * k1 + k2 * k2);
+  c = (k1 * k1 - k2 * k2) * r;
+  s = 2.0 * k1 * k2 * r;
+}
+
+// (A, B) <- (c A + s B, -s A + c B) / n on the full spectra
+__global__ void k_ks_inverse(int H, int W, double2* A, double2* B) {
+  const int n = H * W;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double c, s;
+    ks_rot_d(H, W, i / W, i % W, c, s);
+    const double2 a = A[i], b = B[i];
+    A[i] = make_double2((c * a.x + s * b.x) / n, (c * a.y + s * b.y) / n);
+    B[i] = make_double2((-s * a.x + c * b.x) / n, (-s * a.y + c * b.y) / n);
+  }
+}
+
+}  // namespace
+
+cudaError_t shear_to_convergence_f64(const float* g1, const float* g2, int H, int W, float* kE, float* kB, void* scratch,
+                                     cudaStream_t st) {
+  const int n = H * W;
+  double2* a0 = reinterpret_cast<double2*>(scratch);
+  double2* a1 = a0 + n;
+  double2* b0 = a1 + n;
+  double2* b1 = b0 + n;
+  k_ir_load<<<grid_for(n), 256, 0, st>>>(n, g1, a0);
+  k_ir_load<<<grid_for(n), 256, 0, st>>>(n, g2, b0);
+  double2 *A = nullptr, *B = nullptr;
+  cudaError_t e = fft2_f64(a0, a1, H, W, -1, st, &A);
+  if (e == cudaSuccess) e = fft2_f64(b0, b1, H, W, -1, st, &B);
+  if (e != cudaSuccess) return e;
+  k_ks_inverse<<<grid_for(n), 256, 0, st>>>(H, W, A, B);
+  double2 *ka = nullptr, *kb = nullptr;
+  if ((e = fft2_f64(A, A == a0 ? a1 : a0, H, W, +1, st, &ka)) != cudaSuccess) return e;
+  if ((e = fft2_f64(B, B == b0 ? b1 : b0, H, W, +1, st, &kb)) != cudaSuccess) return e;
+  k_ir_store<<<grid_for(n), 256, 0, st>>>(n, ka, kE);
+  k_ir_store<<<grid_for(n), 256, 0, st>>>(n, kb, kB);
+  return cudaGetLastError();
+}
+
 cudaError_t refine_update(int n, float* s, const float* e, cudaStream_t st) {
   k_add_f32<<<grid_for(n), 256, 0, st>>>(n, s, e);
   return cudaGetLastError();

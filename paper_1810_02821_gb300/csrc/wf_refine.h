@@ -33,6 +33,9 @@ size_t refine_scratch_bytes(int H, int W);
 cudaError_t refine_bnorm(const RefineArgs& a, cudaStream_t st);
 cudaError_t refine_residual(const RefineArgs& a, cudaStream_t st);
 cudaError_t refine_update(int n, float* s, const float* e, cudaStream_t st);
+// (kappa_E, kappa_B) of a shear pair by the inverse Kaiser-Squires rotation; scratch: 4 H W double2
+cudaError_t shear_to_convergence_f64(const float* g1, const float* g2, int H, int W, float* kE, float* kB, void* scratch,
+                                     cudaStream_t st);
 // out = S v = U^dagger diag(P) U v in FP64 (rounded once to float); scratch: 2 H W double2
 cudaError_t apply_S_f64(const float* v, const float* Pk, int H, int W, float* out, void* scratch, cudaStream_t st);
 

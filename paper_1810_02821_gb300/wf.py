@@ -76,6 +76,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.wf_sample_ex.argtypes = [P, P, P, P, I32, I32, U64, ctypes.POINTER(SampleOpts), P, P]
     L.wf_sample_band.argtypes = [P, P, P, P, P, I32, P, I32, I32, U64, ctypes.POINTER(SampleOpts), P, P, P]
     L.wf_sample_band.restype = ctypes.c_int
+    L.wf_sample_spin2.argtypes = [P, P, P, P, P, P, P, I32, I32, U64, ctypes.POINTER(SampleOpts), P, P]
+    L.wf_sample_spin2.restype = ctypes.c_int
+    L.wf_shear_to_convergence.argtypes = [P, I64, I32, I32, P, P]
+    L.wf_shear_to_convergence.restype = ctypes.c_int
     for name in ("wf_solve", "wf_solve_ex", "wf_sample", "wf_sample_ex"):
         getattr(L, name).restype = ctypes.c_int
     L.wf_solve_opts_default.argtypes = [ctypes.POINTER(SolveOpts)]
@@ -287,6 +291,48 @@ def wf_sample_band(d, Ndiag, mask, Pk, bins, P0, seed: int, n_samples: int, *, n
                           ctypes.c_void_p(outP.data_ptr()) if outP is not None else None, _stream_ptr(stream))
     _check(st, "wf_sample_band")
     return out, outP
+
+
+def wf_sample_spin2(d1, d2, N1, N2, mask, PE, PB, seed: int, n_samples: int, *, n_chains: int = 1,
+                    chain_offset: int = 0, start_step: int = 0, burn_in: int = 0, thin: int = 1, tau: float = 0.0,
+                    init=None, out_dtype: str = "f32", stream=None):
+    """Spin-2 (shear) sampler (C call ``wf_sample_spin2``) -> shear samples [chains][n][2][H][W]."""
+    import torch
+    L = load_library()
+    H, W, pd1, pn1, pm, pe = _inputs(d1, N1, mask, PE)
+    pd2 = _dev(d2, torch.float32, (H, W), "d2")
+    pn2 = _dev(N2, torch.float32, (H, W), "N2")
+    pb = _dev(PB, torch.float32, (H, W // 2 + 1), "PB")
+    codes = {"f32": (0, torch.float32), "bf16": (1, torch.bfloat16), "f16": (2, torch.float16)}
+    code, tdt = codes[out_dtype]
+    out = torch.empty((n_chains, n_samples, 2, H, W), dtype=tdt, device=d1.device)
+    o = SampleOpts()
+    L.wf_sample_opts_default(ctypes.byref(o))
+    o.tau, o.n_samples, o.n_chains = float(tau), int(n_samples), int(n_chains)
+    o.chain_offset, o.start_step, o.burn_in, o.thin = int(chain_offset), int(start_step), int(burn_in), int(thin)
+    if init is not None:
+        per_chain = init.dim() == 4
+        o.init_s = _dev(init, torch.float32, (n_chains, 2, H, W) if per_chain else (2, H, W), "init").value
+        o.init_per_chain = 1 if per_chain else 0
+    o.out_dtype = code
+    st = L.wf_sample_spin2(pd1, pd2, pn1, pn2, pm, pe, pb, H, W, int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(o),
+                           ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream))
+    _check(st, "wf_sample_spin2")
+    return out
+
+
+def wf_shear_to_convergence(gamma, stream=None):
+    """(kappa_E, kappa_B) of shear fields [..., 2, H, W] (C call ``wf_shear_to_convergence``)."""
+    import torch
+    L = load_library()
+    H, W = gamma.shape[-2:]
+    g = gamma.reshape(-1, 2, H, W)
+    _dev(g, torch.float32, tuple(g.shape), "gamma")
+    out = torch.empty_like(g)
+    st = L.wf_shear_to_convergence(ctypes.c_void_p(g.data_ptr()), int(g.shape[0]), H, W,
+                                   ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream))
+    _check(st, "wf_shear_to_convergence")
+    return out.reshape(gamma.shape)
 
 
 @dataclass
