@@ -51,6 +51,14 @@ WF_HD float wf_rcp(float x) {
   return 1.0f / x;
 #endif
 }
+// 1 / sqrt(x) for x > 0 (hardware approximation on the device)
+WF_HD float wf_rsqrt(float x) {
+#if defined(__CUDA_ARCH__)
+  return rsqrtf(x);
+#else
+  return 1.0f / std::sqrt(x);
+#endif
+}
 WF_HD float wf_inf() {
 #if defined(__CUDA_ARCH__)
   return __int_as_float(0x7f800000);
@@ -534,8 +542,8 @@ struct SampleArgs {
   float* out_P;          // [n_chains][n_samples][n_bins] or nullptr
 };
 
-// shared bytes per field of the hierarchical sampler: band powers and the two FP64 accumulators
-WF_HD int band_bytes(int n_bins) { return ((n_bins * 20 + 15) / 16) * 16; }
+// shared bytes per field of the hierarchical sampler: the two accumulators and the band powers
+WF_HD int band_bytes(int n_bins) { return ((n_bins * 12 + 15) / 16) * 16; }
 
 // CTAs per SM the sample kernel is compiled for (register budget 65536 / (threads * CTAs)):
 // 128^2 fields are limited to three per SM by shared memory (66.5 KB each).
@@ -618,8 +626,9 @@ WF_HD void mode_pair(int r, int kp, int& kq, int& ky1, int& ky2) {
 
 // Mode coefficients (f/n, g/sqrt(2n)) of the s-draw. TableCoef reads the per-call table; BandCoef (the
 // hierarchical sampler) derives them from the band power P_b of the mode's bin (bins >= 0, in shared
-// memory) with the same formulas as table_mode, and accumulates the band-power statistics of the new
-// modes: S_b += |s_hat|^2 (unitary scale, full spectrum) and X_b += the squares of the stream-6 normals.
+// memory) with the formulas of table_mode in FP32, and accumulates the band-power statistics of the new
+// modes: S_b += |s_hat|^2 (unitary scale, full spectrum) and X_b += the squares of the stream-6 normals,
+// in FP32 shared-memory sums (their order of addition varies, so band powers repeat to FP32 rounding).
 struct TableCoef {
   static constexpr bool kBand = false;
   const float2* __restrict__ fg;
@@ -633,7 +642,7 @@ struct BandCoef {
   int wh;
   const int* __restrict__ bins;  // [H][W/2+1], -1: the table's coefficients
   float* Pb;                     // shared [n_bins]
-  double* acc;                   // shared [2][n_bins]: S_b then X_b
+  float* acc;                    // shared [2][n_bins]: S_b then X_b
   int n_bins;
   float tau, inv_n, n;
   WF_HD float2 coef(int ky, int kx) const {
@@ -641,17 +650,19 @@ struct BandCoef {
     if (b < 0) return WF_LDG(fg + ky * wh + kx);
     const float P = Pb[b];
     if (!(P > 0.0f)) return make_float2(0.0f, 0.0f);
-    const float q = P / (P + tau);
-    return make_float2(q * inv_n, sqrtf(q * tau * 0.5f * inv_n));
+    const float q = P * wf_rcp(P + tau);
+    const float g2 = q * tau * 0.5f * inv_n;
+    return make_float2(q * inv_n, g2 * wf_rsqrt(g2));
   }
-  WF_HD void add(int ky, int kx, float s2, float x2) const {
+  WF_HD int bin(int ky, int kx) const { return WF_LDG(bins + ky * wh + kx); }
+  WF_HD void flush(int b, float s2, float x2) const {
 #if defined(__CUDA_ARCH__)
-    const int b = WF_LDG(bins + ky * wh + kx);
     if (b < 0) return;
-    atomicAdd(acc + b, double(s2) * double(n));
-    atomicAdd(acc + n_bins + b, double(x2));
+    atomicAdd(acc + b, s2 * n);
+    atomicAdd(acc + n_bins + b, x2);
 #endif
   }
+  WF_HD void add(int ky, int kx, float s2, float x2) const { flush(bin(ky, kx), s2, x2); }
 };
 
 // interior columns (col > 0): every thread but the edge thread updates its own parked modes
@@ -662,6 +673,23 @@ WF_HD void s_draw_interior(float2* cs, int lt, const Coef& cf, uint32_t step, ui
   constexpr int LC = G::LC, H = G::H;
   const int col = lt % LC, r = lt / LC;
   if (col == 0) return;
+  // band statistics: consecutive modes of a column thread mostly share a bin, so they are summed in
+  // registers and added to the shared FP64 sums once per run of equal bins
+  int run_b = -1;
+  float run_s = 0.0f, run_x = 0.0f;
+  auto band_add = [&](int ky, float s2, float x2) {
+    if constexpr (Coef::kBand) {
+      const int b = cf.bin(ky, col);
+      if (b != run_b) {
+        cf.flush(run_b, run_s, run_x);
+        run_b = b;
+        run_s = 0.0f;
+        run_x = 0.0f;
+      }
+      run_s += s2;
+      run_x += x2;
+    }
+  };
 #pragma unroll (kRngUnroll)
   for (int kp = 0; kp < LC / 2; ++kp) {
     int kq, ky1, ky2;
@@ -678,10 +706,11 @@ WF_HD void s_draw_interior(float2* cs, int lt, const Coef& cf, uint32_t step, ui
     if constexpr (Coef::kBand) {  // both modes have their mirror in the other half plane: weight 2
       float zb[4];
       normals4(uint32_t(col * (H / 2) + ky1), step, chain, 6u, k0, k1, zb);
-      cf.add(ky1, col, 2.0f * (y1.x * y1.x + y1.y * y1.y), zb[0] * zb[0] + zb[1] * zb[1]);
-      cf.add(ky2, col, 2.0f * (y2.x * y2.x + y2.y * y2.y), zb[2] * zb[2] + zb[3] * zb[3]);
+      band_add(ky1, 2.0f * (y1.x * y1.x + y1.y * y1.y), zb[0] * zb[0] + zb[1] * zb[1]);
+      band_add(ky2, 2.0f * (y2.x * y2.x + y2.y * y2.y), zb[2] * zb[2] + zb[3] * zb[3]);
     }
   }
+  if constexpr (Coef::kBand) cf.flush(run_b, run_s, run_x);
 }
 
 // the packed edge column (col 0: kx = 0 as A and kx = W/2 as B in Y = A + i B, both Hermitian in ky):
@@ -861,10 +890,10 @@ WF_HD void spin2_edge(const Spin2Coef& cf, int lt, uint32_t step, uint32_t chain
 template <int N>
 WF_HD void band_update(const BandCoef& bc, int lt) {
   for (int b = lt; b < bc.n_bins; b += N) {
-    const double S = bc.acc[b], X = bc.acc[bc.n_bins + b];
-    bc.Pb[b] = X > 0.0 ? float(S / X) : 0.0f;
-    bc.acc[b] = 0.0;
-    bc.acc[bc.n_bins + b] = 0.0;
+    const float S = bc.acc[b], X = bc.acc[bc.n_bins + b];
+    bc.Pb[b] = X > 0.0f ? S / X : 0.0f;
+    bc.acc[b] = 0.0f;
+    bc.acc[bc.n_bins + b] = 0.0f;
   }
 }
 
@@ -991,12 +1020,12 @@ __global__ void __launch_bounds__(N * FPC, sample_min_ctas<N>()) k_sample_band(S
   const bool active = ci < a.n_chains;
   float2* S = reinterpret_cast<float2*>(smem_raw + fld * G::FIELD_BYTES);
   unsigned char* band = smem_raw + FPC * G::FIELD_BYTES + fld * band_bytes(a.n_bins);
-  double* acc = reinterpret_cast<double*>(band);
-  float* Pb = reinterpret_cast<float*>(band + 16 * a.n_bins);
+  float* acc = reinterpret_cast<float*>(band);
+  float* Pb = acc + 2 * a.n_bins;
   if (a.sc->status != 0) return;  // uniform over the grid
   for (int b = lt; b < a.n_bins; b += N) {
-    acc[b] = 0.0;
-    acc[a.n_bins + b] = 0.0;
+    acc[b] = 0.0f;
+    acc[a.n_bins + b] = 0.0f;
     Pb[b] = a.P0[b];
   }
   __syncthreads();
