@@ -296,6 +296,32 @@ wf_status wf_loglike_grad(const float* d, const float* sigma2, const uint8_t* ma
                           wf_stream_t stream);
 
 /*
+ * wf_loglike_grad for many images at once: the forward Wiener solves of all images run as one batch
+ * (wf_batch_run), then the probe solves of all images as a second batch. Each item's results equal those
+ * of wf_loglike_grad with the item's own seed (same probes), up to the solve tolerance. Items are HOST
+ * structs; d, sigma2, mask are device pointers ([H][W]); params = {amp, slope, k0, alpha}; the outputs
+ * quad, grad_quad, grad (n_probes > 0) and grad_var are written into the items, with each item's status.
+ * Returns WF_OK, or the first failing item's status (argument and CUDA errors before any work).
+ */
+typedef struct {
+  const float* d;
+  const float* sigma2;
+  const uint8_t* mask;
+  int32_t H, W;
+  double params[4];
+  uint64_t seed;
+  double quad;          /* out */
+  double grad_quad[3];  /* out */
+  double grad[3];       /* out (n_probes > 0) */
+  double grad_var[3];   /* out (n_probes > 0) */
+  int32_t status;       /* out */
+  int32_t reserved;
+} wf_lik_item;
+
+wf_status wf_loglike_grad_batch(wf_lik_item* items, int32_t n_items, int32_t n_probes, double tol,
+                                wf_stream_t stream);
+
+/*
  * The Wiener map (Eq. 2-3, A = I) as a function of the parameters of wf_loglike_grad (P = amp (k/k0)^slope,
  * N = alpha * sigma2): s_W(theta) = S[:, o] C^-1 d_o with C = S_oo + N_oo over the observed pixels o, and
  * its vector-Jacobian product for a cotangent g:

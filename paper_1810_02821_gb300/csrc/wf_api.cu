@@ -1702,6 +1702,146 @@ wf_status wf_loglike_grad(const float* d, const float* sigma2, const uint8_t* ma
   return WF_OK;
 }
 
+wf_status wf_loglike_grad_batch(wf_lik_item* items, int32_t n_items, int32_t n_probes, double tol,
+                                wf_stream_t stream) {
+  if (n_items < 0 || (n_items > 0 && !items) || n_probes < 0 || !(tol > 0.0)) return WF_ERR_ARG;
+  for (int i = 0; i < n_items; ++i) {
+    const wf_lik_item& it = items[i];
+    if (!it.d || !it.sigma2 || !it.mask) return WF_ERR_ARG;
+    if (!size_ok(it.H, it.W)) return WF_ERR_SHAPE;
+    if (!(it.params[0] > 0.0) || !(it.params[2] > 0.0) || !(it.params[3] > 0.0) || !std::isfinite(it.params[1]))
+      return WF_ERR_ARG;
+  }
+  if (n_items == 0) return WF_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // per item: P, dP/damp, dP/dslope [3 nm], N [n], s_W [n], x [n], sums [4], powers [2];
+  // per item and probe: z [n], s_W(z) [n], sums [4], powers [4]
+  Carve cv;
+  std::vector<size_t> o_P(n_items), o_N(n_items), o_s(n_items), o_x(n_items), o_z(n_items), o_w(n_items);
+  for (int i = 0; i < n_items; ++i) {
+    const size_t n = size_t(items[i].H) * items[i].W, nm = size_t(items[i].H) * (items[i].W / 2 + 1);
+    o_P[i] = cv.take<float>(3 * nm);
+    o_N[i] = cv.take<float>(n);
+    o_s[i] = cv.take<float>(n);
+    o_x[i] = cv.take<float>(n);
+    o_z[i] = cv.take<float>(n * size_t(n_probes));
+    o_w[i] = cv.take<float>(n * size_t(n_probes));
+  }
+  const size_t o_sum = cv.take<double>(4 * size_t(n_items) * (1 + n_probes)),
+               o_pow = cv.take<double>(4 * size_t(n_items) * (1 + n_probes));
+  Scratch scr;
+  scr.st = st;
+  WF_CUDA(cudaMallocAsync(&scr.base, cv.off, st));
+  char* b = static_cast<char*>(scr.base);
+  double* sums = reinterpret_cast<double*>(b + o_sum);
+  double* pws = reinterpret_cast<double*>(b + o_pow);
+  WF_CUDA(cudaMemsetAsync(sums, 0, 4 * sizeof(double) * size_t(n_items) * (1 + n_probes), st));
+  auto F = [&](size_t off) { return reinterpret_cast<float*>(b + off); };
+  std::vector<wf_batch_item> fwd(n_items);
+  for (int i = 0; i < n_items; ++i) {
+    const wf_lik_item& it = items[i];
+    const size_t n = size_t(it.H) * it.W, nm = size_t(it.H) * (it.W / 2 + 1);
+    float* P = F(o_P[i]);
+    const int nblk = int((nm + n + 255) / 256);
+    k_psd<<<nblk < 1024 ? nblk : 1024, 256, 0, st>>>(it.H, it.W, it.params[0], it.params[1], it.params[2],
+                                                     it.params[3], it.sigma2, P, P + nm, P + 2 * nm, F(o_N[i]));
+    WF_CUDA(cudaGetLastError());
+    wf_batch_item& bi = fwd[i];
+    std::memset(&bi, 0, sizeof(bi));
+    bi.d = it.d; bi.Ndiag = F(o_N[i]); bi.mask = it.mask; bi.Pk = P; bi.H = it.H; bi.W = it.W;
+    bi.out_wf = F(o_s[i]);
+  }
+  wf_batch_opts bo;
+  wf_batch_opts_default(&bo);
+  bo.tol = tol;
+  bo.n_samples = 0;
+  wf_status r = wf_batch_run(fwd.data(), n_items, &bo, stream);
+  if (r != WF_OK && r != WF_ERR_NOT_CONVERGED) {
+    for (int i = 0; i < n_items; ++i) items[i].status = fwd[i].status;
+    return r;
+  }
+  // x = C^-1 d; Q and dQ/dalpha from the sums, dQ/d(amp, slope) from weighted powers of x
+  for (int i = 0; i < n_items; ++i) {
+    const wf_lik_item& it = items[i];
+    const size_t n = size_t(it.H) * it.W, nm = size_t(it.H) * (it.W / 2 + 1);
+    const int xb = int((n + 255) / 256) < 1024 ? int((n + 255) / 256) : 1024;
+    k_xres<<<xb, 256, 0, st>>>(int(n), it.d, F(o_s[i]), F(o_N[i]), it.sigma2, it.mask, F(o_x[i]), sums + 4 * i);
+    WF_CUDA(cudaGetLastError());
+    cudaError_t e = spectral_power_dev(F(o_x[i]), nullptr, 0.f, 1, F(o_P[i]) + nm, 2, it.H, it.W, pws + 4 * i, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  // probes: all images x probes as one batch of solves, C^-1 z = N^-1 (z - s_W(z))
+  if (n_probes > 0) {
+    std::vector<wf_batch_item> pr(size_t(n_items) * n_probes);
+    for (int i = 0; i < n_items; ++i) {
+      const wf_lik_item& it = items[i];
+      const size_t n = size_t(it.H) * it.W;
+      for (int j = 0; j < n_probes; ++j) {
+        float* z = F(o_z[i]) + size_t(j) * n;
+        k_rademacher<<<int((n / 4 + 255) / 256), 256, 0, st>>>(int(n), uint32_t(j), uint32_t(it.seed & 0xffffffffu),
+                                                              uint32_t(it.seed >> 32), it.mask, z);
+        WF_CUDA(cudaGetLastError());
+        wf_batch_item& bi = pr[size_t(i) * n_probes + j];
+        std::memset(&bi, 0, sizeof(bi));
+        bi.d = z; bi.Ndiag = F(o_N[i]); bi.mask = it.mask; bi.Pk = F(o_P[i]); bi.H = it.H; bi.W = it.W;
+        bi.out_wf = F(o_w[i]) + size_t(j) * n;
+      }
+    }
+    wf_batch_opts bp = bo;
+    bp.tol = tol > 1e-5 ? tol : 1e-5;
+    r = wf_batch_run(pr.data(), int32_t(pr.size()), &bp, stream);
+    if (r != WF_OK && r != WF_ERR_NOT_CONVERGED) return r;
+    for (int i = 0; i < n_items; ++i) {
+      const wf_lik_item& it = items[i];
+      const size_t n = size_t(it.H) * it.W, nm = size_t(it.H) * (it.W / 2 + 1);
+      const int xb = int((n + 255) / 256) < 1024 ? int((n + 255) / 256) : 1024;
+      for (int j = 0; j < n_probes; ++j) {
+        const size_t q = size_t(n_items) + size_t(i) * n_probes + j;
+        float* z = F(o_z[i]) + size_t(j) * n;
+        float* wv = F(o_w[i]) + size_t(j) * n;
+        k_xres<<<xb, 256, 0, st>>>(int(n), z, wv, F(o_N[i]), it.sigma2, it.mask, F(o_x[i]), sums + 4 * q);
+        WF_CUDA(cudaGetLastError());
+        cudaError_t e = spectral_power_dev(F(o_x[i]), z, 1.f, 1, F(o_P[i]) + nm, 2, it.H, it.W, pws + 4 * q, st);
+        if (e == cudaSuccess)
+          e = spectral_power_dev(F(o_x[i]), z, -1.f, 1, F(o_P[i]) + nm, 2, it.H, it.W, pws + 4 * q + 2, st);
+        if (e != cudaSuccess) return cuda_fail(e);
+      }
+    }
+  }
+  const size_t nq = size_t(n_items) * (1 + n_probes);
+  std::vector<double> hs(4 * nq), hp(4 * nq);
+  WF_CUDA(cudaMemcpyAsync(hs.data(), sums, 4 * nq * sizeof(double), cudaMemcpyDeviceToHost, st));
+  WF_CUDA(cudaMemcpyAsync(hp.data(), pws, 4 * nq * sizeof(double), cudaMemcpyDeviceToHost, st));
+  WF_CUDA(cudaStreamSynchronize(st));
+  wf_status first = WF_OK;
+  for (int i = 0; i < n_items; ++i) {
+    wf_lik_item& it = items[i];
+    it.status = fwd[i].status;
+    const double gq[3] = {0.5 * hp[4 * i], 0.5 * hp[4 * i + 1], 0.5 * hs[4 * i + 2]};
+    it.quad = -0.5 * hs[4 * i];
+    for (int k = 0; k < 3; ++k) it.grad_quad[k] = gq[k];
+    if (n_probes > 0) {
+      double tsum[3] = {0, 0, 0}, tsq[3] = {0, 0, 0};
+      for (int j = 0; j < n_probes; ++j) {
+        const size_t q = size_t(n_items) + size_t(i) * n_probes + j;
+        const double t[3] = {0.25 * (hp[4 * q] - hp[4 * q + 2]), 0.25 * (hp[4 * q + 1] - hp[4 * q + 3]), hs[4 * q + 1]};
+        for (int k = 0; k < 3; ++k) {
+          tsum[k] += t[k];
+          tsq[k] += t[k] * t[k];
+        }
+      }
+      for (int k = 0; k < 3; ++k) {
+        const double mean = tsum[k] / n_probes;
+        const double var = n_probes > 1 ? (tsq[k] - n_probes * mean * mean) / (n_probes - 1) : 0.0;
+        it.grad[k] = gq[k] - 0.5 * mean;
+        it.grad_var[k] = 0.25 * var / n_probes;
+      }
+    }
+    if (first == WF_OK && it.status != WF_OK) first = wf_status(it.status);
+  }
+  return first;
+}
+
 wf_status wf_wiener_vjp(const float* d, const float* sigma2, const uint8_t* mask, int32_t H, int32_t W,
                         const double* params, const float* g, const float* s_w_in, double tol, double* out_vjp,
                         float* out_wf, wf_stream_t stream) {

@@ -48,6 +48,14 @@ class BatchItem(ctypes.Structure):
                 ("resid", ctypes.c_double)]
 
 
+class LikItem(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_void_p), ("sigma2", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+                ("H", ctypes.c_int32), ("W", ctypes.c_int32), ("params", ctypes.c_double * 4),
+                ("seed", ctypes.c_uint64), ("quad", ctypes.c_double), ("grad_quad", ctypes.c_double * 3),
+                ("grad", ctypes.c_double * 3), ("grad_var", ctypes.c_double * 3), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 class BatchOpts(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("tol", ctypes.c_double), ("eta", ctypes.c_double),
                 ("level_tol", ctypes.c_double), ("level_max", ctypes.c_int32), ("check", ctypes.c_int32),
@@ -115,6 +123,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.wf_loglike_grad.argtypes = [P, P, P, I32, I32, ctypes.POINTER(D), I32, U64, D, ctypes.POINTER(D),
                                   ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D), P, P]
     L.wf_loglike_grad.restype = ctypes.c_int
+    L.wf_loglike_grad_batch.argtypes = [ctypes.POINTER(LikItem), I32, I32, D, P]
+    L.wf_loglike_grad_batch.restype = ctypes.c_int
     L.wf_wiener_vjp.argtypes = [P, P, P, I32, I32, ctypes.POINTER(D), P, P, D, ctypes.POINTER(D), P, P]
     L.wf_wiener_vjp.restype = ctypes.c_int
     L.wf_set_kernel_timing.argtypes = [I32]
@@ -506,6 +516,29 @@ def wf_loglike_grad(d, sigma2, mask, amp: float, slope: float, k0: float, alpha:
     _check(st, "wf_loglike_grad")
     return LogLikGrad(q.value, np.array(gq[:]), np.array(g[:]) if with_trace else None,
                       np.array(gv[:]) if with_trace else None, out)
+
+
+def wf_loglike_grad_batch(images, *, n_probes: int = 16, tol: float = 1e-7, stream=None):
+    """Log-likelihood data terms and gradients of many images (C call ``wf_loglike_grad_batch``).
+
+    ``images``: sequence of (d, sigma2, mask, amp, slope, k0, alpha, seed) with CUDA tensors; returns a
+    list of LogLikGrad (``wf`` is None)."""
+    import numpy as np
+    import torch
+    L = load_library()
+    arr = (LikItem * len(images))()
+    for i, (d, s2, m, amp, slope, k0, alpha, seed) in enumerate(images):
+        H, W = d.shape
+        arr[i].d = _dev(d, torch.float32, (H, W), "d").value
+        arr[i].sigma2 = _dev(s2, torch.float32, (H, W), "sigma2").value
+        arr[i].mask = _dev(m, torch.uint8, (H, W), "mask").value
+        arr[i].H, arr[i].W = H, W
+        arr[i].params[:] = [float(amp), float(slope), float(k0), float(alpha)]
+        arr[i].seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    st = L.wf_loglike_grad_batch(arr, len(images), int(n_probes), float(tol), _stream_ptr(stream))
+    _check(st, "wf_loglike_grad_batch", ok=(WF_OK, 5))
+    return [LogLikGrad(a.quad, np.array(a.grad_quad[:]), np.array(a.grad[:]) if n_probes else None,
+                       np.array(a.grad_var[:]) if n_probes else None, None) for a in arr]
 
 
 def _make_loglik_function():

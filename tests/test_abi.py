@@ -85,7 +85,7 @@ def test_option_structs_match_the_header(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     structs = {"wf_solve_opts": wf.SolveOpts, "wf_sample_opts": wf.SampleOpts,
-               "wf_batch_item": wf.BatchItem, "wf_batch_opts": wf.BatchOpts}
+               "wf_batch_item": wf.BatchItem, "wf_batch_opts": wf.BatchOpts, "wf_lik_item": wf.LikItem}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "wf.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')

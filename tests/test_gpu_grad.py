@@ -131,3 +131,22 @@ def test_wiener_map_autograd_uses_the_checkpointed_forward():
     s2, v = wf.wf_wiener_vjp(dev[0], dev[1], dev[2], 0.9, -1.6, 1.0 / 16, 1.1, g, tol=3e-8)
     assert rel(s.detach().cpu().numpy(), s2.cpu().numpy()) < 1e-7
     np.testing.assert_allclose(theta.grad.numpy(), v, rtol=1e-6)
+
+
+def test_batched_loglike_gradient_equals_single_calls():
+    rng = np.random.default_rng(9)
+    imgs, probs = [], []
+    for i, H in enumerate([16, 64, 256, 256, 128]):
+        amp, slope = float(rng.uniform(0.5, 2)), float(rng.uniform(-2.5, -1.5))
+        p = synth.make_problem(H, seed=40 + i, mask_frac=0.1, slope=slope, amp=amp, k0=1.0 / H, sigma2=(0.01, 0.2))
+        dev = to_dev(p)
+        imgs.append((dev[0], dev[1], dev[2], amp, slope, 1.0 / H, 1.0, 7 + i))
+        probs.append(p)
+    got = wf.wf_loglike_grad_batch(imgs, n_probes=4, tol=1e-6)
+    for (d, s2, m, amp, slope, k0, alpha, seed), g in zip(imgs, got):
+        r = wf.wf_loglike_grad(d, s2, m, amp, slope, k0, alpha, n_probes=4, seed=seed, tol=1e-6)
+        assert abs(g.quad - r.quad) < 1e-4 * abs(r.quad)
+        np.testing.assert_allclose(g.grad_quad, r.grad_quad, rtol=1e-3)
+        sd = np.sqrt(r.grad_var) + 1e-12
+        # same probes, solves to the same tolerance: the stochastic gradients agree far inside their error
+        assert np.all(np.abs(g.grad - r.grad) < 0.05 * sd + 1e-3 * np.abs(r.grad)), (g.grad, r.grad, sd)
