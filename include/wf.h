@@ -342,6 +342,16 @@ wf_status wf_wiener_vjp(const float* d, const float* sigma2, const uint8_t* mask
                         const double* params, const float* g, const float* s_w_in, double tol, double* out_vjp,
                         float* out_wf, wf_stream_t stream);
 
+/*
+ * Self-test of the bounded device-side wait used by the large-image kernels (the grid barrier between
+ * their phases). It runs one cooperative launch of n_blocks CTAs (1 .. 1024) whose barrier waits for one
+ * arrival more than the grid has, so every wait reaches its poll limit (about a second) and gives up. The
+ * expected result is WF_ERR_TIMEOUT with the context intact (later calls work); WF_OK would mean the wait
+ * did not give up. elapsed_ms (HOST, may be NULL): the launch's duration. The paper has no counterpart:
+ * this exercises the failure path of the library's waits without faulting the GPU.
+ */
+wf_status wf_selftest_wait_timeout(int32_t n_blocks, double* elapsed_ms);
+
 /* 1 if (H, W) is supported by wf_solve / wf_sample, else 0. */
 int32_t wf_supported_size(int32_t H, int32_t W);
 

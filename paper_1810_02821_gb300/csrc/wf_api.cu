@@ -865,6 +865,53 @@ wf_status wf_shear_to_convergence(const float* gamma, int64_t n_fields, int32_t 
   return WF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// a grid barrier that expects one arrival more than the grid: every CTA's wait runs out
+__global__ void k_wait_timeout(wf::GridBar* bar) {
+  wf::grid_barrier(bar, gridDim.x + 1);
+}
+}  // namespace
+
+extern "C" {
+
+wf_status wf_selftest_wait_timeout(int32_t n_blocks, double* elapsed_ms) {
+  if (n_blocks < 1 || n_blocks > 1024) return WF_ERR_ARG;
+  int dev = 0, sms = 0, per_sm = 0;
+  WF_CUDA(cudaGetDevice(&dev));
+  WF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  WF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wait_timeout, 32, 0));
+  if ((long long)per_sm * sms < n_blocks) return WF_ERR_ARG;  // the grid must be co-resident
+  cudaStream_t st;
+  WF_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  wf::GridBar* bar = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  wf::GridBar hb{};
+  float ms = 0.f;
+  cudaError_t e = cudaMallocAsync(&bar, sizeof(wf::GridBar), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bar, 0, sizeof(wf::GridBar), st);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+  if (e == cudaSuccess) {
+    void* args[] = {&bar};
+    e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_wait_timeout), dim3(n_blocks), dim3(32), args, 0, st);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, bar, sizeof(hb), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (bar) cudaFreeAsync(bar, st);
+  cudaStreamSynchronize(st);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamDestroy(st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (elapsed_ms) *elapsed_ms = ms;
+  return hb.err ? wf_status(hb.err) : WF_OK;
+}
+
 wf_status wf_sample(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int32_t H, int32_t W,
                     int64_t n_samples, uint64_t seed, float* out, wf_stream_t stream) {
   wf_sample_opts o;

@@ -125,6 +125,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.wf_loglike_grad.restype = ctypes.c_int
     L.wf_loglike_grad_batch.argtypes = [ctypes.POINTER(LikItem), I32, I32, D, P]
     L.wf_loglike_grad_batch.restype = ctypes.c_int
+    L.wf_selftest_wait_timeout.argtypes = [I32, ctypes.POINTER(D)]
+    L.wf_selftest_wait_timeout.restype = ctypes.c_int
     L.wf_wiener_vjp.argtypes = [P, P, P, I32, I32, ctypes.POINTER(D), P, P, D, ctypes.POINTER(D), P, P]
     L.wf_wiener_vjp.restype = ctypes.c_int
     L.wf_set_kernel_timing.argtypes = [I32]
@@ -652,3 +654,12 @@ def wiener_map(theta, d, sigma2, mask, k0: float, tol: float = 1e-7):
     if _WienerMap is None:
         _WienerMap = _make_wiener_map_function()
     return _WienerMap.apply(theta, d, sigma2, mask, k0, tol)
+
+
+def wf_selftest_wait_timeout(n_blocks: int = 64):
+    """Run the bounded-wait self-test (C call ``wf_selftest_wait_timeout``) -> (status, elapsed ms); the
+    expected status is 7 (WF_ERR_TIMEOUT)."""
+    L = load_library()
+    ms = ctypes.c_double(0.0)
+    st = L.wf_selftest_wait_timeout(int(n_blocks), ctypes.byref(ms))
+    return st, ms.value

@@ -140,3 +140,7 @@ def test_sample_output_type_validated_without_gpu(lib):
     assert o.out_dtype == 0
     o.n_samples, o.out_dtype = 1, 3
     assert lib.wf_sample_ex(p, p, p, p, 32, 32, 0, ctypes.byref(o), p, None) == 1
+
+
+def test_selftest_argument_check_without_gpu(lib):
+    assert lib.wf_selftest_wait_timeout(0, None) == 1
