@@ -175,6 +175,19 @@ wf_status wf_sample_spin2(const float* d1, const float* d2, const float* N1, con
                           const wf_sample_opts* opts, float* out, wf_stream_t stream);
 
 /*
+ * Wiener filter of the shear pair (the mass-mapping filter of §5): the G -> 0 form of wf_sample_spin2's
+ * sweep with lambda-cooling. Per level lambda (lambda_0 = max(1, max(PE, PB) / tau), then
+ * max(1, eta lambda)): opts->level_max sweeps with T = lambda tau (N_bar = N - tau fixed), no draws; at
+ * lambda = 1 the FP64 relative residual ||g + S N^-1 (g - d)|| / ||S N^-1 d|| (S the shear covariance of
+ * the E/B spectra) is evaluated every opts->check sweeps until it is below opts->tol or opts->max_iter
+ * sweeps have run (WF_ERR_NOT_CONVERGED). out: device [2][H][W]; iters_out, resid_out: HOST, may be NULL.
+ * Sizes up to 128 x 128; opts may be NULL (defaults); opts->refine, init_s and A are not used.
+ */
+wf_status wf_solve_spin2(const float* d1, const float* d2, const float* N1, const float* N2, const uint8_t* mask,
+                         const float* PE, const float* PB, int32_t H, int32_t W, const wf_solve_opts* opts, float* out,
+                         int32_t* iters_out, double* resid_out, wf_stream_t stream);
+
+/*
  * Convergence from shear fields: kappa_E_hat = c gamma1_hat + s gamma2_hat, kappa_B_hat = -s gamma1_hat +
  * c gamma2_hat (the inverse of the rotation above), with FP64 transforms. gamma: device [n][2][H][W];
  * kappa: device [n][2][H][W] (E then B). Any supported size.

@@ -846,6 +846,137 @@ wf_status wf_sample_spin2(const float* d1, const float* d2, const float* N1, con
   return wf_status(hsc.status);
 }
 
+}  // extern "C"
+
+namespace {
+// Wiener-filter tables of one shear component at level lambda for the spin-2 sweep: aq = ((1 - w) d, sqrt w)
+// with w = N_bar / (N_bar + lambda tau), N_bar = N - tau (missing pixels: w = 1); fg = (f / n, 0) with
+// f = P / (P + lambda tau) (no draws)
+__global__ void k_s2_level_tables(const float* __restrict__ d, const float* __restrict__ Nd,
+                                  const uint8_t* __restrict__ mask, const float* __restrict__ Pk, int H, int W,
+                                  const wf::Scalars* __restrict__ sc, double lam, float2* aq, float2* fg) {
+  const int n = H * W, nm = H * (W / 2 + 1);
+  const double tau = sc->tau, lt = lam * tau;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + nm; i += gridDim.x * blockDim.x) {
+    if (i < n) {
+      const int y = i / W, x = i % W;
+      double a = 0.0, w = 1.0;
+      if (mask[i] == 0) {
+        const double nb = double(Nd[i]) - tau;
+        w = nb / (nb + lt);
+        a = (1.0 - w) * double(d[i]);
+      }
+      aq[x * H + y] = make_float2(float(a), float(sqrt(w)));
+    } else {
+      const int j = i - n;
+      const double P = double(Pk[j]);
+      fg[j] = make_float2(P > 0.0 ? float(P / (P + lt) / double(n)) : 0.0f, 0.0f);
+    }
+  }
+}
+__global__ void k_s2_quiet(const wf::Scalars* a, wf::Scalars* b) {  // the draws' scale set to zero
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    *b = *a;
+    b->sqrt_tau = 0.0f;
+  }
+}
+}  // namespace
+
+extern "C" {
+
+wf_status wf_solve_spin2(const float* d1, const float* d2, const float* N1, const float* N2, const uint8_t* mask,
+                         const float* PE, const float* PB, int32_t H, int32_t W, const wf_solve_opts* opts, float* out,
+                         int32_t* iters_out, double* resid_out, wf_stream_t stream) {
+  wf_solve_opts o;
+  wf_solve_opts_default(&o);
+  if (opts) o = *opts;
+  if (!d1 || !d2 || !N1 || !N2 || !mask || !PE || !PB || !out) return WF_ERR_ARG;
+  if (!size_ok(H, W)) return WF_ERR_SHAPE;
+  if (!size_on_chip(H)) return WF_ERR_SHAPE;
+  if (!(o.tol > 0.0) || !(o.eta > 0.0 && o.eta < 1.0) || o.level_max < 1 || o.check < 1 || o.max_iter < 1)
+    return WF_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t n = size_t(H) * W, nm = size_t(H) * (W / 2 + 1);
+  Carve cv;
+  const size_t o_sc = cv.take<wf::Scalars>(3), o_aq = cv.take<float2>(2 * n), o_fe = cv.take<float2>(nm),
+               o_fb = cv.take<float2>(nm), o_r = cv.take<double>(2), o_x = cv.take<double2>(8 * n);
+  Scratch scr;
+  scr.st = st;
+  WF_CUDA(cudaMallocAsync(&scr.base, cv.off, st));
+  char* b = static_cast<char*>(scr.base);
+  auto* sc = reinterpret_cast<wf::Scalars*>(b + o_sc);
+  auto* aq = reinterpret_cast<float2*>(b + o_aq);
+  auto* fgE = reinterpret_cast<float2*>(b + o_fe);
+  auto* fgB = reinterpret_cast<float2*>(b + o_fb);
+  auto* rn = reinterpret_cast<double*>(b + o_r);
+  k_prep<<<1, 1024, 0, st>>>(d1, N1, mask, PE, H, W, o.tau, o.eta, sc);
+  k_prep<<<1, 1024, 0, st>>>(d2, N2, mask, PB, H, W, o.tau, o.eta, sc + 1);
+  k_min_tau<<<1, 32, 0, st>>>(sc, sc + 1, o.tau);
+  k_s2_quiet<<<1, 32, 0, st>>>(sc, sc + 2);
+  WF_CUDA(cudaGetLastError());
+  wf::Scalars hs[2];
+  WF_CUDA(cudaMemcpyAsync(hs, sc, 2 * sizeof(wf::Scalars), cudaMemcpyDeviceToHost, st));
+  WF_CUDA(cudaMemsetAsync(out, 0, 2 * n * sizeof(float), st));
+  WF_CUDA(cudaMemsetAsync(rn, 0, 2 * sizeof(double), st));
+  WF_CUDA(cudaStreamSynchronize(st));
+  if (hs[0].status != WF_OK) return wf_status(hs[0].status);
+  const double tau = hs[0].tau, pmax = hs[0].pmax > hs[1].pmax ? hs[0].pmax : hs[1].pmax;
+  const double lam0 = pmax / tau > 1.0 ? pmax / tau : 1.0;
+  cudaError_t e = wf::spin2_residual_f64(out, d1, d2, N1, N2, mask, PE, PB, H, W, true, rn, b + o_x, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  double hb[2];
+  WF_CUDA(cudaMemcpyAsync(hb, rn, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  WF_CUDA(cudaStreamSynchronize(st));
+  const double bnorm = hb[1];
+  wf::Spin2Args a{};
+  a.aq2 = aq; a.fgE = fgE; a.fgB = fgB; a.sc = sc + 2; a.init_s = out; a.init_stride = 0;
+  a.out = out; a.n_samples = 1; a.n_chains = 1; a.burn_in = 0; a.thin = 1; a.out_dtype = 0;
+  auto run = [&](double lam, int sweeps) -> wf_status {
+    k_s2_level_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d1, N1, mask, PE, H, W, sc, lam, aq, fgE);
+    k_s2_level_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d2, N2, mask, PB, H, W, sc, lam, aq + n, fgB);
+    WF_CUDA(cudaGetLastError());
+    a.n_sweeps = sweeps;
+    a.thin = sweeps;  // the state after the last sweep is the only sample
+    cudaError_t e2 = cudaSuccess;
+    switch (H) {
+      case 16: e2 = wf::launch_sample_spin2<16>(a, st, nullptr); break;
+      case 32: e2 = wf::launch_sample_spin2<32>(a, st, nullptr); break;
+      case 64: e2 = wf::launch_sample_spin2<64>(a, st, nullptr); break;
+      case 128: e2 = wf::launch_sample_spin2<128>(a, st, nullptr); break;
+    }
+    if (e2 != cudaSuccess) return cuda_fail(e2);
+    return WF_OK;
+  };
+  int iters = 0;
+  wf_status r = WF_OK;
+  for (int lev = 0; lev < wf::kMaxLevels; ++lev) {  // cooling levels above lambda = 1
+    double lam = lam0;
+    for (int j = 0; j < lev; ++j) lam = lam * o.eta > 1.0 ? lam * o.eta : 1.0;
+    if (lam <= 1.0) break;
+    if ((r = run(lam, o.level_max)) != WF_OK) return r;
+    iters += o.level_max;
+  }
+  double rho = -1.0;
+  wf_status status = WF_ERR_NOT_CONVERGED;
+  while (iters < o.max_iter) {
+    const int k = o.check < o.max_iter - iters ? o.check : o.max_iter - iters;
+    if ((r = run(1.0, k)) != WF_OK) return r;
+    iters += k;
+    WF_CUDA(cudaMemsetAsync(rn, 0, sizeof(double), st));
+    e = wf::spin2_residual_f64(out, d1, d2, N1, N2, mask, PE, PB, H, W, false, rn, b + o_x, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    double h;
+    WF_CUDA(cudaMemcpyAsync(&h, rn, sizeof(double), cudaMemcpyDeviceToHost, st));
+    WF_CUDA(cudaStreamSynchronize(st));
+    rho = bnorm > 0.0 ? sqrt(h / bnorm) : sqrt(h);
+    if (!(rho == rho)) { status = WF_ERR_NONFINITE; break; }
+    if (rho < o.tol) { status = WF_OK; break; }
+  }
+  if (iters_out) *iters_out = iters;
+  if (resid_out) *resid_out = rho;
+  return status;
+}
+
 wf_status wf_shear_to_convergence(const float* gamma, int64_t n_fields, int32_t H, int32_t W, float* kappa,
                                   wf_stream_t stream) {
   if (!gamma || !kappa || n_fields < 0) return WF_ERR_ARG;

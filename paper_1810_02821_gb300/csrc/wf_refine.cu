@@ -292,6 +292,65 @@ cudaError_t shear_to_convergence_f64(const float* g1, const float* g2, int H, in
   return cudaGetLastError();
 }
 
+namespace {
+
+// G_c = (g_c, 0); V_c = (g_c - d_c) / N_c on observed pixels (b: V_c = d_c / N_c, G = 0)
+__global__ void k_s2_load(int n, const float* __restrict__ g, const float* __restrict__ d1,
+                          const float* __restrict__ d2, const float* __restrict__ N1, const float* __restrict__ N2,
+                          const uint8_t* __restrict__ mask, int rhs, double2* G1, double2* G2, double2* V1,
+                          double2* V2) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double a = rhs ? 0.0 : double(g[i]), b = rhs ? 0.0 : double(g[n + i]);
+    G1[i] = make_double2(a, 0.0);
+    G2[i] = make_double2(b, 0.0);
+    const bool obs = mask[i] == 0;
+    V1[i] = make_double2(obs ? (rhs ? double(d1[i]) : a - double(d1[i])) / double(N1[i]) : 0.0, 0.0);
+    V2[i] = make_double2(obs ? (rhs ? double(d2[i]) : b - double(d2[i])) / double(N2[i]) : 0.0, 0.0);
+  }
+}
+
+// out += sum_k |G_k + S V_k|^2 / n with S V = rotate(P_E e, P_B b), (e, b) = rotate^T V
+__global__ void k_s2_norm(int H, int W, const float* __restrict__ PE, const float* __restrict__ PB,
+                          const double2* __restrict__ G1, const double2* __restrict__ G2,
+                          const double2* __restrict__ V1, const double2* __restrict__ V2, double* out) {
+  const int n = H * W;
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int ky = i / W, kx = i % W;
+    double c, s;
+    ks_rot_d(H, W, ky, kx, c, s);
+    const double pe = p_full(PE, H, W, ky, kx), pb = p_full(PB, H, W, ky, kx);
+    const double2 v1 = V1[i], v2 = V2[i];
+    const double2 e = make_double2(pe * (c * v1.x + s * v2.x), pe * (c * v1.y + s * v2.y));
+    const double2 b = make_double2(pb * (-s * v1.x + c * v2.x), pb * (-s * v1.y + c * v2.y));
+    const double2 r1 = make_double2(G1[i].x + c * e.x - s * b.x, G1[i].y + c * e.y - s * b.y);
+    const double2 r2 = make_double2(G2[i].x + s * e.x + c * b.x, G2[i].y + s * e.y + c * b.y);
+    acc += (r1.x * r1.x + r1.y * r1.y + r2.x * r2.x + r2.y * r2.y) / double(n);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
+}  // namespace
+
+cudaError_t spin2_residual_f64(const float* g, const float* d1, const float* d2, const float* N1, const float* N2,
+                               const uint8_t* mask, const float* PE, const float* PB, int H, int W, bool with_b,
+                               double* out, void* scratch, cudaStream_t st) {
+  const int n = H * W;
+  double2* x = reinterpret_cast<double2*>(scratch);  // 4 arrays and their ping-pong partners
+  cudaError_t e = cudaSuccess;
+  for (int pass = 0; pass < (with_b ? 2 : 1) && e == cudaSuccess; ++pass) {
+    const int rhs = pass;  // pass 0: the residual of g; pass 1: the right-hand side S N^-1 d
+    k_s2_load<<<grid_for(n), 256, 0, st>>>(n, g, d1, d2, N1, N2, mask, rhs, x, x + 2 * n, x + 4 * n, x + 6 * n);
+    double2* F[4];
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = fft2_f64(x + 2 * k * n, x + (2 * k + 1) * n, H, W, -1, st, &F[k]);
+    if (e != cudaSuccess) break;
+    k_s2_norm<<<grid_for(n), 256, 0, st>>>(H, W, PE, PB, F[0], F[1], F[2], F[3], out + pass);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
 cudaError_t refine_update(int n, float* s, const float* e, cudaStream_t st) {
   k_add_f32<<<grid_for(n), 256, 0, st>>>(n, s, e);
   return cudaGetLastError();

@@ -36,6 +36,11 @@ cudaError_t refine_update(int n, float* s, const float* e, cudaStream_t st);
 // (kappa_E, kappa_B) of a shear pair by the inverse Kaiser-Squires rotation; scratch: 4 H W double2
 cudaError_t shear_to_convergence_f64(const float* g1, const float* g2, int H, int W, float* kE, float* kB, void* scratch,
                                      cudaStream_t st);
+// spin-2 Wiener-filter residual in FP64: out[0] += ||g + S N^-1 (g - d)||^2 (g = (g1, g2), the shear
+// covariance S of the E/B spectra), out[1] += ||S N^-1 d||^2 (when with_b); scratch: 8 H W double2
+cudaError_t spin2_residual_f64(const float* g, const float* d1, const float* d2, const float* N1, const float* N2,
+                               const uint8_t* mask, const float* PE, const float* PB, int H, int W, bool with_b,
+                               double* out, void* scratch, cudaStream_t st);
 // out = S v = U^dagger diag(P) U v in FP64 (rounded once to float); scratch: 2 H W double2
 cudaError_t apply_S_f64(const float* v, const float* Pk, int H, int W, float* out, void* scratch, cudaStream_t st);
 

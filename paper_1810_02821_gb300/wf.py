@@ -86,6 +86,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.wf_sample_band.restype = ctypes.c_int
     L.wf_sample_spin2.argtypes = [P, P, P, P, P, P, P, I32, I32, U64, ctypes.POINTER(SampleOpts), P, P]
     L.wf_sample_spin2.restype = ctypes.c_int
+    L.wf_solve_spin2.argtypes = [P, P, P, P, P, P, P, I32, I32, ctypes.POINTER(SolveOpts), P,
+                                 ctypes.POINTER(I32), ctypes.POINTER(D), P]
+    L.wf_solve_spin2.restype = ctypes.c_int
     L.wf_shear_to_convergence.argtypes = [P, I64, I32, I32, P, P]
     L.wf_shear_to_convergence.restype = ctypes.c_int
     for name in ("wf_solve", "wf_solve_ex", "wf_sample", "wf_sample_ex"):
@@ -331,6 +334,29 @@ def wf_sample_spin2(d1, d2, N1, N2, mask, PE, PB, seed: int, n_samples: int, *, 
                            ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream))
     _check(st, "wf_sample_spin2")
     return out
+
+
+def wf_solve_spin2(d1, d2, N1, N2, mask, PE, PB, *, tol: float = 1e-5, tau: float = 0.0, eta: float = 0.5,
+                   level_sweeps: int = 64, check: int = 16, max_iter: int = 50000, allow_not_converged: bool = False,
+                   stream=None) -> SolveResult:
+    """Wiener filter of a shear pair (C call ``wf_solve_spin2``) -> SolveResult with s = [2][H][W]."""
+    import torch
+    L = load_library()
+    H, W, pd1, pn1, pm, pe = _inputs(d1, N1, mask, PE)
+    pd2 = _dev(d2, torch.float32, (H, W), "d2")
+    pn2 = _dev(N2, torch.float32, (H, W), "N2")
+    pb = _dev(PB, torch.float32, (H, W // 2 + 1), "PB")
+    out = torch.empty((2, H, W), dtype=torch.float32, device=d1.device)
+    o = SolveOpts()
+    L.wf_solve_opts_default(ctypes.byref(o))
+    o.tau, o.tol, o.eta = float(tau), float(tol), float(eta)
+    o.level_max, o.check, o.max_iter = int(level_sweeps), int(check), int(max_iter)
+    it = ctypes.c_int32(0)
+    rs = ctypes.c_double(0.0)
+    st = L.wf_solve_spin2(pd1, pd2, pn1, pn2, pm, pe, pb, H, W, ctypes.byref(o), ctypes.c_void_p(out.data_ptr()),
+                          ctypes.byref(it), ctypes.byref(rs), _stream_ptr(stream))
+    _check(st, "wf_solve_spin2", ok=(WF_OK, 5) if allow_not_converged else (WF_OK,))
+    return SolveResult(out, it.value, rs.value, st)
 
 
 def wf_shear_to_convergence(gamma, stream=None):

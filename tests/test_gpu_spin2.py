@@ -53,3 +53,14 @@ def test_shear_to_convergence_matches_oracle():
         for i in range(3):
             kE, kB = S2.convergence_from_shear(g[i, 0], g[i, 1])
             assert rel(k[i, 0], kE) < 1e-6 and rel(k[i, 1], kB) < 1e-6
+
+
+@pytest.mark.parametrize("H", [16, 32])
+def test_spin2_wiener_filter_matches_dense(H):
+    p, d2, N2, PB = _pair(H, H + 7)
+    ref = S2.wiener_dense(p.d, d2, p.Ndiag, N2, p.mask, p.Pk, PB)
+    r = wf.wf_solve_spin2(*_dev(p.d, d2, p.Ndiag, N2, p.mask, p.Pk, PB), tol=5e-6)
+    got = r.s.cpu().numpy()
+    print(f"spin-2 WF {H}: resid {r.resid:.2e} sweeps {r.iters} err {rel(got[0], ref[0]):.2e} {rel(got[1], ref[1]):.2e}")
+    assert r.status == 0 and r.resid < 5e-6
+    assert rel(got[0], ref[0]) < 2e-5 and rel(got[1], ref[1]) < 2e-5
