@@ -268,7 +268,7 @@ void wf_batch_graph_destroy(wf_batch_graph g);
 /*
  * Launch-shape autotuner of the batched form. Starting from *opts, it times graph replays of this batch
  * (one warm-up and `reps` timed replays per candidate, CUDA events on `stream`) and keeps, one knob at a
- * time, the fastest large_grid_pct in {100, 50, 25, 12}, large_streams in {2, 4, 8, 16} (when the batch has
+ * time, the fastest large_grid_pct in {100, 50, 25, 12}, large_streams in {1, 2, 4, 8, 16} (when the batch has
  * images above 128 x 128) and small_grid_pct in {100, 50, 25}; the chosen values are written back to *opts and the
  * best replay time to *best_ms (HOST, may be NULL). The items' outputs are overwritten by the trial runs.
  * A representative subset of a large batch tunes faster than the whole batch.

@@ -1612,7 +1612,7 @@ wf_status wf_batch_autotune(const wf_batch_item* items, int32_t n_items, wf_batc
   };
   if (has_large) {
     try_knob(&wf_batch_opts::large_grid_pct, {100, 50, 25, 12});
-    try_knob(&wf_batch_opts::large_streams, {2, 4, 8, 16});
+    try_knob(&wf_batch_opts::large_streams, {1, 2, 4, 8, 16});
   }
   try_knob(&wf_batch_opts::small_grid_pct, {100, 50, 25});
   cudaEventDestroy(e0);

@@ -121,7 +121,7 @@ def test_batch_launch_shapes_and_autotune_keep_the_results():
     for (rw, rs), (gw, gs) in zip(ref, _outputs(imgs)):
         assert rel(gw, rw) < WF_TOL and rel(gs, rs) < SAMPLE_TOL
     chosen, ms = wf.wf_batch_autotune(imgs, n_samples=2, reps=1, tol=1e-5)
-    assert chosen["large_grid_pct"] in (0, 100, 50, 25, 12) and chosen["large_streams"] in (2, 4, 8, 16)
+    assert chosen["large_grid_pct"] in (0, 100, 50, 25, 12) and chosen["large_streams"] in (1, 2, 4, 8, 16)
     assert chosen["small_grid_pct"] in (0, 100, 50, 25) and ms > 0
     wf.wf_batch_run(imgs, n_samples=2, tol=1e-5, **chosen)
     for (rw, rs), (gw, gs) in zip(ref, _outputs(imgs)):
