@@ -152,3 +152,28 @@ def test_batch_large_images_in_shared_launches():
         g, w = imgs[i].out_samples.cpu().numpy(), ref[0].cpu().numpy()
         for m in range(n_samples):
             assert rel(g[m], w[m]) < SAMPLE_TOL, (i, m)
+
+
+def test_full_size_mixed_batch_4096_sampled():
+    """The 4096-image mixed batch (solve to 1e-5 plus 64 samples each, one graph replay as timed): a few
+    images of each size against the oracle (64^2, 128^2) or the single-image calls (256^2, 512^2)."""
+    from oracle import messenger as M
+    probs = synth.config_batch(4096, seed=0)
+    imgs = [wf.BatchImage(*to_dev(p), seed=i, chain=i) for i, p in enumerate(probs)]
+    with wf.BatchGraph(imgs, n_samples=64, tol=1e-5) as g:
+        g.launch()
+        g.results()
+    assert all(im.status == 0 for im in imgs)
+    sizes = [p.d.shape[0] for p in probs]
+    for H in (64, 128, 256, 512):
+        i = sizes.index(H)
+        p, im = probs[i], imgs[i]
+        r = wf.wf_solve_ex(*to_dev(p), tol=1e-5)   # the same cooled solve, one image per call
+        assert rel(im.out_wf.cpu().numpy(), r.s.cpu().numpy()) < WF_TOL
+        if H <= 128:
+            ref_s = M.sample(p.d, p.Ndiag, p.mask, p.Pk, 3, seed=i, chain=i, init_s=im.out_wf.cpu().numpy())
+        else:
+            ref_s = wf.wf_sample_ex(*to_dev(p), seed=i, n_samples=3, chain_offset=i,
+                                    init_s=im.out_wf.contiguous())[0].cpu().numpy()
+        for m in range(3):
+            assert rel(im.out_samples[m].cpu().numpy(), ref_s[m]) < SAMPLE_TOL, (H, m)

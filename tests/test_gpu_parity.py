@@ -83,6 +83,17 @@ def test_full_size_128_1024_chains_sampled():
         assert max(errs) < SAMPLE_TOL, (c, max(errs))
 
 
+def test_full_size_128_one_long_chain_thin_10_sampled():
+    """The long-chain configuration (one chain, 10^4 kept samples of 10^5 sweeps, thin 10): the first kept
+    samples and a later one vs the oracle (each sample needs only the sweeps before it)."""
+    p = synth.config_paper128(0)
+    got = wf.wf_sample_ex(*to_dev(p), seed=11, n_samples=10000, n_chains=1, thin=10)
+    assert got.shape == (1, 10000, 128, 128) and bool(torch.isfinite(got).all())
+    ref = M.sample(p.d, p.Ndiag, p.mask, p.Pk, 30, seed=11, thin=10)
+    g = got[0, :30].cpu().numpy()
+    assert max(rel(g[m], ref[m]) for m in range(30)) < SAMPLE_TOL
+
+
 def test_resume_is_exact_and_runs_are_deterministic():
     p = synth.make_problem(64, seed=2, mask_frac=0.1)
     dev = to_dev(p)
