@@ -51,6 +51,14 @@ WF_HD float wf_rcp(float x) {
   return 1.0f / x;
 #endif
 }
+// a / b with the fast device division (about 2 ulp); used where a few ulp do not matter
+WF_HD float wf_fdiv(float a, float b) {
+#if defined(__CUDA_ARCH__)
+  return __fdividef(a, b);
+#else
+  return a / b;
+#endif
+}
 // 1 / sqrt(x) for x > 0 (hardware approximation on the device)
 WF_HD float wf_rsqrt(float x) {
 #if defined(__CUDA_ARCH__)
@@ -372,17 +380,20 @@ WF_HD double s_update_wf(float2 (&x)[N / 2], int lt, const float* __restrict__ P
   constexpr float INV_N = 1.0f / float(G::H * G::W);
   const int col = lt % G::LC, r = lt / G::LC;
   double acc = 0.0;
-  // |d|^2 / (1 - f_true)^2 with 1/(1 - f_true) = (P + lambda tau) / (lambda tau)
+  // |d|^2 / (1 - f_true)^2 with 1/(1 - f_true) = (P + lambda tau) / (lambda tau) = 1 + P / (lambda tau):
+  // per-mode terms in FP32 (a residual estimate needs a few digits), summed in FP64
+  const float inv_lt = 1.0f / lt_;
   auto wres = [&](float P, float dre, float dim) -> double {
-    const double g = (double(P) + double(lt_)) / double(lt_);
-    return (double(dre) * dre + double(dim) * dim) * g * g;
+    const float g = fmaf(P, inv_lt, 1.0f);
+    return double(fmaf(dre, dre, dim * dim) * (g * g));
   };
+  auto fcoef = [&](float P) { return wf_fdiv(P, P + lt_) * INV_N; };
   for_mode_pairs<N>(r, [&](auto KP, auto KQ, int ky1, int ky2, auto ZG) {
     constexpr int kp = decltype(KP)::value, kq = decltype(KQ)::value;
     constexpr bool zero_group = decltype(ZG)::value != 0;
     if (col != 0) {
       const float P1 = WF_LDG(Pk + ky1 * WH + col), P2 = WF_LDG(Pk + ky2 * WH + col);
-      const float f1 = P1 / (P1 + lt_) * INV_N, f2 = P2 / (P2 + lt_) * INV_N;
+      const float f1 = fcoef(P1), f2 = fcoef(P2);
       const float2 n1 = cscale(x[kp], f1), n2 = cscale(x[kq], f2);
       if constexpr (CMP) {
         const float2 o1 = prev[ky1 * G::LR + col], o2 = prev[ky2 * G::LR + col];
@@ -393,8 +404,8 @@ WF_HD double s_update_wf(float2 (&x)[N / 2], int lt, const float* __restrict__ P
     } else {
       const float Pa1 = WF_LDG(Pk + ky1 * WH), Pb1 = WF_LDG(Pk + ky1 * WH + G::W / 2);
       const float Pa2 = WF_LDG(Pk + ky2 * WH), Pb2 = WF_LDG(Pk + ky2 * WH + G::W / 2);
-      const float fa1 = Pa1 / (Pa1 + lt_) * INV_N, fb1 = Pb1 / (Pb1 + lt_) * INV_N;
-      const float fa2 = Pa2 / (Pa2 + lt_) * INV_N, fb2 = Pb2 / (Pb2 + lt_) * INV_N;
+      const float fa1 = fcoef(Pa1), fb1 = fcoef(Pb1);
+      const float fa2 = fcoef(Pa2), fb2 = fcoef(Pb2);
       if constexpr (zero_group) {
         const float2 n1 = make_float2(fa1 * x[kp].x, fb1 * x[kp].y);
         const float2 n2 = make_float2(fa2 * x[kq].x, fb2 * x[kq].y);
@@ -438,9 +449,7 @@ WF_HD double p2_power(const float2 (&x)[N / 2], int lt, const float* __restrict_
   constexpr int WH = G::WH;
   const int col = lt % G::LC, r = lt / G::LC;
   double acc = 0.0;
-  auto p2 = [](float P, float re, float im) -> double {
-    return double(P) * double(P) * (double(re) * re + double(im) * im);
-  };
+  auto p2 = [](float P, float re, float im) -> double { return double(P * P * fmaf(re, re, im * im)); };
   for_mode_pairs<N>(r, [&](auto KP, auto KQ, int ky1, int ky2, auto ZG) {
     constexpr int kp = decltype(KP)::value, kq = decltype(KQ)::value;
     constexpr bool zero_group = decltype(ZG)::value != 0;

@@ -368,13 +368,15 @@ __device__ __forceinline__ double col_update(int mode, float2* buf, int c0, cons
         }
       }
     } else if (mode == 1) {
+      // per-mode residual terms in FP32, summed in FP64 (see s_update_wf)
+      const float inv_lt = 1.0f / ltau;
       auto wres = [&](float P, float dre, float dim) -> double {
-        const double g = (double(P) + double(ltau)) / double(ltau);
-        return (double(dre) * dre + double(dim) * dim) * g * g;
+        const float g = fmaf(P, inv_lt, 1.0f);
+        return double(fmaf(dre, dre, dim * dim) * (g * g));
       };
       if (col != 0) {
         const float P1 = __ldg(Pk + ky1 * WH + col), P2 = __ldg(Pk + ky2 * WH + col);
-        const float2 n1 = cscale(y1, P1 / (P1 + ltau) * INV_N), n2 = cscale(y2, P2 / (P2 + ltau) * INV_N);
+        const float2 n1 = cscale(y1, wf_fdiv(P1, P1 + ltau) * INV_N), n2 = cscale(y2, wf_fdiv(P2, P2 + ltau) * INV_N);
         if (cmp) {
           const float2 o1 = prev[ky1 * L + col], o2 = prev[ky2 * L + col];
           acc += 2.0 * (wres(P1, n1.x - o1.x, n1.y - o1.y) + wres(P2, n2.x - o2.x, n2.y - o2.y));
@@ -384,8 +386,8 @@ __device__ __forceinline__ double col_update(int mode, float2* buf, int c0, cons
       } else {
         const float Pa1 = __ldg(Pk + ky1 * WH), Pb1 = __ldg(Pk + ky1 * WH + G::W / 2);
         const float Pa2 = __ldg(Pk + ky2 * WH), Pb2 = __ldg(Pk + ky2 * WH + G::W / 2);
-        const float fa1 = Pa1 / (Pa1 + ltau) * INV_N, fb1 = Pb1 / (Pb1 + ltau) * INV_N;
-        const float fa2 = Pa2 / (Pa2 + ltau) * INV_N, fb2 = Pb2 / (Pb2 + ltau) * INV_N;
+        const float fa1 = wf_fdiv(Pa1, Pa1 + ltau) * INV_N, fb1 = wf_fdiv(Pb1, Pb1 + ltau) * INV_N;
+        const float fa2 = wf_fdiv(Pa2, Pa2 + ltau) * INV_N, fb2 = wf_fdiv(Pb2, Pb2 + ltau) * INV_N;
         if (j == 0) {
           const float2 n1 = make_float2(fa1 * y1.x, fb1 * y1.y), n2 = make_float2(fa2 * y2.x, fb2 * y2.y);
           if (cmp) {
@@ -414,9 +416,7 @@ __device__ __forceinline__ double col_update(int mode, float2* buf, int c0, cons
         prev[ky2 * L + col] = y2;
       }
     } else {
-      auto p2 = [](float P, float re, float im) -> double {
-        return double(P) * double(P) * (double(re) * re + double(im) * im);
-      };
+      auto p2 = [](float P, float re, float im) -> double { return double(P * P * fmaf(re, re, im * im)); };
       if (col != 0) {
         acc += 2.0 * (p2(__ldg(Pk + ky1 * WH + col), y1.x, y1.y) + p2(__ldg(Pk + ky2 * WH + col), y2.x, y2.y));
       } else if (j == 0) {
