@@ -27,6 +27,12 @@
  *     starts from zero (opts->init_s must be NULL).
  *   - Pointers named d, Ndiag, mask, Pk, out*, init_s are DEVICE pointers owned by the caller; pointers
  *     to iters_out / resid_out / opts are HOST pointers (may be NULL where stated).
+ *   - The sample outputs of wf_sample, wf_sample_ex, wf_sample_band and wf_sample_spin2 (out, out_P)
+ *     may instead be page-locked host memory mapped into the device address space at the same address
+ *     (cudaHostAlloc, or cudaHostRegister with mapping, under unified addressing); the kernel then
+ *     stores each sample straight into host memory over the CPU-GPU link, with no staging buffer or
+ *     copy. Page-locked memory without that mapping, or pageable host memory on a device that cannot
+ *     access it (cudaDevAttrPageableMemoryAccess = 0), is refused with WF_ERR_ARG.
  *   - Calls are ordered on `stream` and return after the stream has reached their end (they
  *     synchronise on it to read the device status). The library allocates its scratch with
  *     cudaMallocAsync on `stream` and frees it before returning.

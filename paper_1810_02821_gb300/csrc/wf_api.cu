@@ -140,6 +140,29 @@ bool size_ok(int H, int W) {
 }
 bool size_on_chip(int H) { return H <= 128; }
 
+// An output the kernels may store to: device or managed memory, or page-locked host memory that is
+// mapped into the device address space at the same address (cudaHostAlloc, or cudaHostRegister with
+// mapping, under unified addressing). Page-locked memory without that mapping cannot be written by a
+// kernel and is refused here instead of faulting in the kernel.
+bool out_ptr_ok(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return true;  // not known to the runtime: left to the caller
+  }
+  if (at.type == cudaMemoryTypeHost) return at.devicePointer == p;
+  if (at.type == cudaMemoryTypeUnregistered) {  // pageable host memory: only where the GPU can reach it
+    int dev = 0, pageable = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return pageable != 0;
+  }
+  return true;
+}
+
 // Twiddle tables of the large-image path, in FP64 then rounded once:
 // tw_row[j] = exp(-2 pi i j / (W/2)), tw_col[j] = exp(-2 pi i j / H), tw_real[k] = exp(-2 pi i k / W).
 __global__ void k_twiddles(int H, int W, float2* tw_row, float2* tw_col, float2* tw_real) {
@@ -640,7 +663,7 @@ wf_status wf_sample_ex(const float* d, const float* Ndiag, const uint8_t* mask, 
   if (o.n_samples < 0 || o.n_chains < 1 || o.burn_in < 0 || o.thin < 1) return WF_ERR_ARG;
   if (o.out_dtype < WF_OUT_F32 || o.out_dtype > WF_OUT_F16) return WF_ERR_ARG;
   if (o.n_samples == 0) return WF_OK;
-  if (!out) return WF_ERR_ARG;
+  if (!out || !out_ptr_ok(out)) return WF_ERR_ARG;
   const long long sweeps = (long long)o.burn_in + o.n_samples * (long long)o.thin;
   if (sweeps > 0x7fffffffLL || o.n_samples > 0x7fffffffLL) return WF_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -727,7 +750,7 @@ wf_status wf_sample_band(const float* d, const float* Ndiag, const uint8_t* mask
   if (o.n_samples < 0 || o.n_chains < 1 || o.burn_in < 0 || o.thin < 1) return WF_ERR_ARG;
   if (o.out_dtype < WF_OUT_F32 || o.out_dtype > WF_OUT_F16) return WF_ERR_ARG;
   if (o.n_samples == 0) return WF_OK;
-  if (!out) return WF_ERR_ARG;
+  if (!out || !out_ptr_ok(out) || (out_P && !out_ptr_ok(out_P))) return WF_ERR_ARG;
   const long long sweeps = (long long)o.burn_in + o.n_samples * (long long)o.thin;
   if (sweeps > 0x7fffffffLL || o.n_samples > 0x7fffffffLL) return WF_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -798,7 +821,7 @@ wf_status wf_sample_spin2(const float* d1, const float* d2, const float* N1, con
   if (o.A || o.n_samples < 0 || o.n_chains < 1 || o.burn_in < 0 || o.thin < 1) return WF_ERR_ARG;
   if (o.out_dtype < WF_OUT_F32 || o.out_dtype > WF_OUT_F16) return WF_ERR_ARG;
   if (o.n_samples == 0) return WF_OK;
-  if (!out) return WF_ERR_ARG;
+  if (!out || !out_ptr_ok(out)) return WF_ERR_ARG;
   const long long sweeps = (long long)o.burn_in + o.n_samples * (long long)o.thin;
   if (sweeps > 0x7fffffffLL || o.n_samples > 0x7fffffffLL) return WF_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

@@ -162,9 +162,9 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _dev(t, dtype, shape, name):
+def _dev(t, dtype, shape, name, host_ok=False):
     import torch
-    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+    if not isinstance(t, torch.Tensor) or not (t.is_cuda or host_ok):
         raise TypeError(f"{name} must be a CUDA tensor")
     if t.dtype != dtype:
         raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
@@ -173,6 +173,17 @@ def _dev(t, dtype, shape, name):
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _out(t, dtype, shape, name):
+    """A sample output: a CUDA tensor, or a page-locked CPU tensor (pin_memory) that the kernel writes
+    directly over the CPU-GPU link (the library refuses page-locked memory it cannot map)."""
+    import torch
+    if isinstance(t, torch.Tensor) and not t.is_cuda:
+        if not t.is_pinned():
+            raise TypeError(f"{name} must be a CUDA tensor or a pinned (page-locked) CPU tensor")
+        return _dev(t, dtype, shape, name, host_ok=True)
+    return _dev(t, dtype, shape, name)
 
 
 def _inputs(d, Ndiag, mask, Pk):
@@ -237,7 +248,7 @@ def wf_sample(d, Ndiag, mask, Pk, n_samples: int, seed: int, out=None, stream=No
     H, W, pd, pn, pm, pp = _inputs(d, Ndiag, mask, Pk)
     if out is None:
         out = torch.empty((n_samples, H, W), dtype=torch.float32, device=d.device)
-    po = _dev(out, torch.float32, (n_samples, H, W), "out")
+    po = _out(out, torch.float32, (n_samples, H, W), "out")
     st = L.wf_sample(pd, pn, pm, pp, H, W, int(n_samples), int(seed) & 0xFFFFFFFFFFFFFFFF, po, _stream_ptr(stream))
     _check(st, "wf_sample")
     return out
@@ -248,7 +259,8 @@ def wf_sample_ex(d, Ndiag, mask, Pk, seed: int, n_samples: int, *, n_chains: int
                  A=None, out_dtype: str = "f32", out=None, stream=None):
     """Several chains with burn-in, thinning and resume (C call ``wf_sample_ex``) -> [chains][n][H][W].
     ``A``: optional CUDA float32 [H][W] diagonal pixel response of d = A s + n. ``out_dtype``: "f32", or
-    "bf16" / "f16" for samples rounded once from the FP32 chain state."""
+    "bf16" / "f16" for samples rounded once from the FP32 chain state. ``out``: a CUDA tensor, or a pinned
+    CPU tensor that the kernel fills directly over the CPU-GPU link."""
     import torch
     L = load_library()
     H, W, pd, pn, pm, pp = _inputs(d, Ndiag, mask, Pk)
@@ -258,7 +270,7 @@ def wf_sample_ex(d, Ndiag, mask, Pk, seed: int, n_samples: int, *, n_chains: int
     code, tdt = codes[out_dtype]
     if out is None:
         out = torch.empty((n_chains, n_samples, H, W), dtype=tdt, device=d.device)
-    po = _dev(out, tdt, (n_chains, n_samples, H, W), "out")
+    po = _out(out, tdt, (n_chains, n_samples, H, W), "out")
     o = SampleOpts()
     L.wf_sample_opts_default(ctypes.byref(o))
     o.tau, o.n_samples, o.n_chains = float(tau), int(n_samples), int(n_chains)
