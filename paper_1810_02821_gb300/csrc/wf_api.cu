@@ -17,6 +17,7 @@ namespace {
 
 thread_local int g_last_cuda_error = 0;
 thread_local int g_timing = 0;
+thread_local int g_large_sampler = 0;  // 0: cluster sampler where it fits, 1: global-memory sampler
 thread_local double g_kernel_ms = -1.0;
 
 // CUDA events around the main kernel of a call (only when timing is enabled on this thread)
@@ -139,6 +140,26 @@ bool size_ok(int H, int W) {
   return H == W && (H == 16 || H == 32 || H == 64 || H == 128 || H == 256 || H == 512 || H == 1024);
 }
 bool size_on_chip(int H) { return H <= 128; }
+
+// whether at least one sampler cluster for H x H fits on the current device (queried once per device)
+bool cluster_fits(int H) {
+  static std::mutex mu;
+  static int known[2][64] = {};  // 0 unknown, 1 fits, 2 does not
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return false;
+  }
+  const int k = H == 256 ? 0 : 1;
+  std::lock_guard<std::mutex> lock(mu);
+  if (known[k][dev] == 0) {
+    int clusters = 0;
+    const cudaError_t e = H == 256 ? wf::csample_clusters<256>(&clusters) : wf::csample_clusters<512>(&clusters);
+    if (e != cudaSuccess) cudaGetLastError();
+    known[k][dev] = (e == cudaSuccess && clusters > 0) ? 1 : 2;
+  }
+  return known[k][dev] == 1;
+}
 
 // An output the kernels may store to: device or managed memory, or page-locked host memory that is
 // mapped into the device address space at the same address (cudaHostAlloc, or cudaHostRegister with
@@ -451,6 +472,12 @@ int32_t wf_last_cuda_error(void) { return g_last_cuda_error; }
 
 void wf_set_kernel_timing(int32_t enable) { g_timing = enable ? 1 : 0; }
 
+int32_t wf_set_large_image_sampler(int32_t mode) {
+  const int prev = g_large_sampler;
+  g_large_sampler = mode == 1 ? 1 : 0;
+  return prev;
+}
+
 double wf_last_kernel_ms(void) { return g_kernel_ms; }
 
 const char* wf_status_string(wf_status s) {
@@ -674,7 +701,9 @@ wf_status wf_sample_ex(const float* d, const float* Ndiag, const uint8_t* mask, 
     Ndiag = resp.Nd;
     mask = resp.mask;
   }
-  if (!size_on_chip(H)) {
+  // 256 and 512: one cluster per chain when the device can host the cluster, else the field in global memory
+  const bool cluster = (H == 256 || H == 512) && g_large_sampler == 0 && cluster_fits(H);
+  if (!size_on_chip(H) && !cluster) {
     KernelTimer gt(st);
     const wf_status r = sample_global(d, Ndiag, mask, Pk, H, W, seed, o, sweeps, out, st, &gt);
     gt.collect();
@@ -708,6 +737,8 @@ wf_status wf_sample_ex(const float* d, const float* Ndiag, const uint8_t* mask, 
     case 32: e = wf::launch_sample<32>(a, st, &timer); break;
     case 64: e = wf::launch_sample<64>(a, st, &timer); break;
     case 128: e = wf::launch_sample<128>(a, st, &timer); break;
+    case 256: e = wf::launch_csample<256>(a, st, &timer); break;
+    case 512: e = wf::launch_csample<512>(a, st, &timer); break;
   }
   if (e != cudaSuccess) return cuda_fail(e);
   wf::Scalars hsc;

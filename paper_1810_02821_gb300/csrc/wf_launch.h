@@ -7,6 +7,7 @@
 #include "wf_global.cuh"
 #include "wf_batch.cuh"
 #include "wf_gbatch.cuh"
+#include "wf_cluster.cuh"
 
 namespace wf {
 
@@ -49,6 +50,14 @@ cudaError_t launch_global(const GlobalArgs& a, cudaStream_t st, LaunchTimer* t);
 // batched large images (N >= 256): one cooperative launch of k_gbatch<N> over all fields of a size class
 template <int N>
 cudaError_t launch_gbatch(const GBArgs& a, cudaStream_t st);
+
+// cluster-resident sampler (N in {256, 512}): one cluster of N / 64 CTAs per chain.
+// cudaErrorNotSupported when no cluster of that shape can be resident on the device.
+template <int N>
+cudaError_t launch_csample(const SampleArgs& a, cudaStream_t st, LaunchTimer* t);
+// clusters of k_csample<N> that can be resident at once on the current device (0: none)
+template <int N>
+cudaError_t csample_clusters(int* clusters);
 
 // definitions, included by the per-size translation units only
 #if defined(WF_LAUNCH_DEFINE)
@@ -204,6 +213,49 @@ cudaError_t launch_gbatch(const GBArgs& a, cudaStream_t st) {
 #define WF_INSTANTIATE_GLOBAL(N)                                                               \
   template cudaError_t launch_global<N>(const GlobalArgs&, cudaStream_t, LaunchTimer*);         \
   template cudaError_t launch_gbatch<N>(const GBArgs&, cudaStream_t);
+#endif
+
+#if defined(WF_LAUNCH_DEFINE_CLUSTER)
+template <int N>
+cudaError_t csample_config(cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr, int n_chains, cudaStream_t st) {
+  using G = CGeo<N>;
+  const cudaError_t e = cudaFuncSetAttribute(k_csample<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+  if (e != cudaSuccess) return e;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = G::P;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  *cfg = cudaLaunchConfig_t{};
+  cfg->gridDim = dim3(unsigned(n_chains) * G::P, 1, 1);
+  cfg->blockDim = dim3(G::L, 1, 1);
+  cfg->dynamicSmemBytes = G::SMEM;
+  cfg->stream = st;
+  cfg->attrs = attr;
+  cfg->numAttrs = 1;
+  return cudaSuccess;
+}
+template <int N>
+cudaError_t csample_clusters(int* clusters) {
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  cudaError_t e = csample_config<N>(&cfg, attr, 1, nullptr);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveClusters(clusters, k_csample<N>, &cfg);
+}
+template <int N>
+cudaError_t launch_csample(const SampleArgs& a, cudaStream_t st, LaunchTimer* t) {
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  cudaError_t e = csample_config<N>(&cfg, attr, a.n_chains, st);
+  if (e != cudaSuccess) return e;
+  if (t) t->start();
+  e = cudaLaunchKernelEx(&cfg, k_csample<N>, a);
+  if (t) t->stop();
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+#define WF_INSTANTIATE_CLUSTER(N)                                                            \
+  template cudaError_t launch_csample<N>(const SampleArgs&, cudaStream_t, LaunchTimer*);     \
+  template cudaError_t csample_clusters<N>(int*);
 #endif
 
 }  // namespace wf

@@ -132,6 +132,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.wf_selftest_wait_timeout.restype = ctypes.c_int
     L.wf_wiener_vjp.argtypes = [P, P, P, I32, I32, ctypes.POINTER(D), P, P, D, ctypes.POINTER(D), P, P]
     L.wf_wiener_vjp.restype = ctypes.c_int
+    L.wf_set_large_image_sampler.argtypes = [I32]
+    L.wf_set_large_image_sampler.restype = I32
     L.wf_set_kernel_timing.argtypes = [I32]
     L.wf_set_kernel_timing.restype = None
     L.wf_last_kernel_ms.argtypes = []
@@ -622,6 +624,17 @@ def wiener_loglik(theta, d, sigma2, mask, k0: float, n_probes: int = 16, seed: i
 
 def wf_set_kernel_timing(enable: bool) -> None:
     load_library().wf_set_kernel_timing(1 if enable else 0)
+
+
+def wf_set_large_image_sampler(mode: str) -> str:
+    """Sampler for 256 x 256 and 512 x 512 images on this thread: "cluster" (the field in the shared memory
+    of one thread-block cluster per chain, where the device can host it) or "global" (fields in global
+    memory, one cooperative launch). Returns the previous mode."""
+    modes = {"cluster": 0, "global": 1}
+    if mode not in modes:
+        raise ValueError(f"mode must be one of {sorted(modes)}")
+    prev = load_library().wf_set_large_image_sampler(modes[mode])
+    return "global" if prev == 1 else "cluster"
 
 
 def wf_last_kernel_ms() -> float:

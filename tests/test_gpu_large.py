@@ -1,4 +1,6 @@
-"""GPU parity of the large-image path (N = 256, 512, 1024: field in global memory, cooperative kernel)."""
+"""GPU parity of the large-image paths: N = 256 and 512 sample with one thread-block cluster per chain
+(the field in distributed shared memory) or with the fields in global memory (one cooperative kernel, also
+the Wiener filter and N = 1024); both run the oracle's chain draw for draw."""
 import numpy as np
 import pytest
 
@@ -19,8 +21,15 @@ def _lib():
     wf.load_library()
 
 
+@pytest.fixture(params=["cluster", "global"])
+def sampler(request):
+    prev = wf.wf_set_large_image_sampler(request.param)
+    yield request.param
+    wf.wf_set_large_image_sampler(prev)
+
+
 @pytest.mark.parametrize("H", [256, 512])
-def test_sample_large_draw_for_draw(H):
+def test_sample_large_draw_for_draw(H, sampler):
     p = synth.make_problem(H, seed=H, mask_frac=0.1, block=(10, 60, 20, 90), slope=-2.0, k0=1.0 / 32,
                            sigma2=(0.05, 0.5))
     n_samples = 3 if H == 256 else 2
@@ -30,6 +39,35 @@ def test_sample_large_draw_for_draw(H):
         ref = M.sample(p.d, p.Ndiag, p.mask, p.Pk, n_samples, seed=13, chain=7 + c, burn_in=1)
         for m in range(n_samples):
             assert rel(got[c, m], ref[m]) < SAMPLE_TOL, (H, c, m, rel(got[c, m], ref[m]))
+
+
+@pytest.mark.parametrize("H", [256, 512])
+def test_cluster_and_global_samplers_agree(H):
+    """Many chains with thinning, per-chain initial states and BF16 storage: the cluster sampler and the
+    global-memory sampler draw the same chain (FP32 results agree to rounding, ragged chain count)."""
+    p = synth.make_problem(H, seed=H + 1, mask_frac=0.15, slope=-1.5, k0=1.0 / 16, sigma2=(0.02, 0.8))
+    dev = to_dev(p)
+    chains = 7 if H == 256 else 3
+    g = torch.Generator().manual_seed(H)
+    init = torch.randn((chains, H, H), generator=g).cuda() * 0.1
+    kw = dict(seed=77, n_samples=3, n_chains=chains, chain_offset=5, start_step=11, burn_in=2, thin=2, init_s=init)
+    out = {}
+    for mode in ("cluster", "global"):
+        prev = wf.wf_set_large_image_sampler(mode)
+        try:
+            out[mode] = wf.wf_sample_ex(*dev, **kw).cpu().numpy()
+            out[mode + "_bf16"] = wf.wf_sample_ex(*dev, out_dtype="bf16", **kw).float().cpu().numpy()
+        finally:
+            wf.wf_set_large_image_sampler(prev)
+    for c in range(chains):
+        for m in range(3):
+            assert rel(out["cluster"][c, m], out["global"][c, m]) < 1e-5, (c, m)
+            assert rel(out["cluster_bf16"][c, m], out["cluster"][c, m]) < 2.0 ** -8
+    # and the first chain is the oracle's (chain word 5, step words from 11)
+    ref = M.sample(p.d, p.Ndiag, p.mask, p.Pk, 2 + 3 * 2, seed=77, chain=5, start_step=11,
+                   init_s=init[0].cpu().numpy())
+    for m in range(3):
+        assert rel(out["cluster"][0, m], ref[2 + 2 * m + 1]) < SAMPLE_TOL
 
 
 def test_sample_1024_one_sweep():
