@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the plain, single-chain and batch measurements")
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed-size batch measurement")
-    ap.add_argument("--extras", default="batch,plain,precision,grad,bf16,band,spin2",
+    ap.add_argument("--extras", default="batch,plain,precision,grad,bf16,band,spin2,large",
                     help="extra workloads (comma list of batch, plain, precision, grad, bf16, band, spin2)")
     ap.add_argument("--batch-images", type=int, default=4096, help="images of the mixed-size batch")
     ap.add_argument("--batch-large-streams", type=int, default=8,
@@ -466,6 +466,43 @@ def spin2_sampler(dev, n_chains: int = 512):
                          "frac": 2 * FLOPS_PER_SWEEP * n_chains * N_SAMPLES / (kms / 1e3) / 1e12 / FP32_PEAK_TFLOPS}}
 
 
+def large_sampler(dev):
+    """Samplers for 256x256 and 512x512 (one thread-block cluster per chain, field in distributed shared
+    memory) against the global-memory sampler on the same problem: paper-like field model (slope -2,
+    k0 = 1/32, noise variance U[0.05, 0.5], 10% masked); 456 chains x 20 samples (256^2) and 152 chains
+    x 10 samples (512^2), every sweep kept."""
+    import torch
+    from paper_1810_02821_gb300 import synth, wf
+    res = {}
+    for H, chains, ns in ((256, 456, 20), (512, 152, 10)):
+        p = synth.make_problem(H, seed=H, mask_frac=0.1, slope=-2.0, k0=1.0 / 32, sigma2=(0.05, 0.5))
+        args = [torch.from_numpy(x).to(dev) for x in (p.d, p.Ndiag, p.mask, p.Pk)]
+        out = torch.empty((chains, ns, H, H), device=dev)
+        row = {"workload": f"{H}x{H}, {chains} chains x {ns} samples"}
+        for mode in ("cluster", "global"):
+            prev = wf.wf_set_large_image_sampler(mode)
+            try:
+                wf.wf_sample_ex(*args, seed=1, n_samples=ns, n_chains=chains, out=out)
+                ks = []
+                for i in range(3):
+                    wf.wf_sample_ex(*args, seed=2 + i, n_samples=ns, n_chains=chains, out=out)
+                    ks.append(wf.wf_last_kernel_ms())
+            finally:
+                wf.wf_set_large_image_sampler(prev)
+            kms = statistics.mean(ks)
+            n = H * H
+            flops = 5.0 * n * math.log2(n) * chains * ns
+            row[mode] = {"kernel_ms": kms, "samples_per_s": chains * ns / (kms / 1e3),
+                         "pixel_sweeps_per_s": chains * ns * n / (kms / 1e3),
+                         "roofline": {"bound": "alu", "achieved": flops / (kms / 1e3) / 1e12,
+                                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                      "frac": flops / (kms / 1e3) / 1e12 / FP32_PEAK_TFLOPS}}
+        row["cluster_vs_global"] = row["global"]["kernel_ms"] / row["cluster"]["kernel_ms"]
+        res[f"{H}x{H}"] = row
+        del out
+    return res
+
+
 def main():
     global N_CHAINS, N_SAMPLES
     a = parse()
@@ -589,7 +626,8 @@ def main():
             ("grad", "differentiation_256x256", differentiation_256),
             ("bf16", "bf16_sample_storage", reduced_output),
             ("band", "hierarchical_band_sampler", band_sampler),
-            ("spin2", "spin2_shear_sampler", spin2_sampler)) if k in want and not (k == "batch" and a.no_batch)]
+            ("spin2", "spin2_shear_sampler", spin2_sampler),
+            ("large", "large_image_sampler", large_sampler)) if k in want and not (k == "batch" and a.no_batch)]
         for _, name, fn in jobs:
             try:
                 other[name] = fn(dev)

@@ -1143,12 +1143,16 @@ long long batch_slot_any(int H) {
 // Large images (H >= 256) of a batch: the images of a size class are split into chunks, and every chunk
 // is one cooperative launch of k_gbatch with one field per image (see wf_gbatch.cuh). Per-field buffers:
 // pixel tables aq, dn [n], mode table fg [nm], state Z and previous Wiener iterate [H][W/2].
+// With `cluster` (256 and 512, samples requested, a sampler cluster fits the device) k_gbatch runs the
+// solves only and the samples come from one k_csample_batch launch (one cluster per image) that starts
+// from each image's s_W (the caller's out_wf, else a per-field scratch image f_sw).
 struct GBChunk {
   int H = 0, stream = 0;
+  bool cluster = false;
   std::vector<int> items;  // batch item indices
   size_t o_fields = 0, o_idx = 0, o_sc = 0, o_state = 0, o_acc = 0, o_bn = 0, o_active = 0, o_bar = 0, o_tr = 0,
          o_tc = 0, o_tw = 0, o_data = 0, per_field = 0;
-  size_t f_aq = 0, f_dn = 0, f_fg = 0, f_z = 0, f_prev = 0;
+  size_t f_aq = 0, f_dn = 0, f_fg = 0, f_z = 0, f_prev = 0, f_sw = 0;
 };
 
 void layout_chunk(GBChunk& c, Carve& cv) {
@@ -1171,6 +1175,7 @@ void layout_chunk(GBChunk& c, Carve& cv) {
   c.f_fg = f.take<float2>(nm);
   c.f_z = f.take<float2>(nz);
   c.f_prev = f.take<float2>(nz);
+  if (c.cluster) c.f_sw = f.take<float>(n);
   c.per_field = f.off;
   c.o_data = cv.take<char>(c.per_field * size_t(F));
 }
@@ -1188,7 +1193,7 @@ std::vector<wf::GBField> chunk_fields(const GBChunk& c, const std::vector<wf::Ba
     g.Pk = it.Pk;
     g.Z = reinterpret_cast<float2*>(base + c.f_z);
     g.prev = reinterpret_cast<float2*>(base + c.f_prev);
-    g.out_wf = it.out_wf;
+    g.out_wf = it.out_wf ? it.out_wf : (c.cluster ? reinterpret_cast<float*>(base + c.f_sw) : nullptr);
     g.out_samples = it.out_samples;
     g.chain = it.chain;
     g.key0 = uint32_t(it.seed & 0xffffffffu);
@@ -1304,10 +1309,19 @@ wf_status run_chunk(const GBChunk& c, const wf::BatchItem* d_items, wf::BatchRes
   a.max_iter = o.max_iter;
   a.level_max = o.level_max;
   a.check = o.check;
-  a.n_samples = o.n_samples;
+  a.n_samples = c.cluster ? 0 : o.n_samples;
   a.grid_pct = o.large_grid_pct;
-  const cudaError_t e = launch_gbatch_any(H, a, st);
+  cudaError_t e = launch_gbatch_any(H, a, st);
   if (e != cudaSuccess) return cuda_fail(e);
+  if (c.cluster && o.n_samples > 0) {
+    wf::CBArgs cb{};
+    cb.fields = fields;
+    cb.sc = sc;
+    cb.F = F;
+    cb.n_samples = o.n_samples;
+    e = H == 256 ? wf::launch_csample_batch<256>(cb, st) : wf::launch_csample_batch<512>(cb, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
   return WF_OK;
 }
 
@@ -1392,6 +1406,7 @@ wf_status plan_batch(const wf_batch_item* items, int n_items, const wf_batch_opt
       GBChunk ch;
       ch.H = kBatchSizes[c];
       ch.stream = k;
+      ch.cluster = (ch.H == 256 || ch.H == 512) && o.n_samples > 0 && g_large_sampler == 0 && cluster_fits(ch.H);
       for (int i = k * nc / parts; i < (k + 1) * nc / parts; ++i) ch.items.push_back(p->cls[c][i]);
       layout_chunk(ch, cv);
       p->chunks.push_back(std::move(ch));

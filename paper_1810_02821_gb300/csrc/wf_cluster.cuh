@@ -21,7 +21,7 @@
 
 #include <cooperative_groups.h>
 
-#include "wf_gibbs.cuh"
+#include "wf_gbatch.cuh"
 
 namespace wf {
 
@@ -289,22 +289,23 @@ __device__ __forceinline__ void ccol_draw(cooperative_groups::cluster_group& cl,
 }
 
 // ---------------------------------------------------------------------------------------------
-// kernel: grid = n_chains clusters of P CTAs (chain = cluster index)
+// kernels
 // ---------------------------------------------------------------------------------------------
 template <int N>
 constexpr int csample_min_ctas() { return N == 256 ? 3 : 1; }
 
+// the sweeps of one chain by its cluster: s_0 from init (row-major [H][W], nullptr: zero), sample m (the
+// state after sweep burn_in + (m + 1) thin) to out + m H W elements of type out_dtype
 template <int N>
-__global__ void __launch_bounds__(N / 2, csample_min_ctas<N>()) k_csample(SampleArgs a) {
+__device__ __forceinline__ void csample_chain(cooperative_groups::cluster_group& cl, unsigned char* smem_raw,
+                                              const float2* __restrict__ aq, const float2* __restrict__ fg,
+                                              float sqrt_tau, const float* init, void* out_v, int out_dtype,
+                                              int n_sweeps, int burn_in, int thin, uint32_t step0, uint32_t chain,
+                                              uint32_t k0, uint32_t k1) {
   using G = CGeo<N>;
-  namespace cg = cooperative_groups;
-  cg::cluster_group cl = cg::this_cluster();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* rows = reinterpret_cast<float2*>(smem_raw);
   float2* tw = reinterpret_cast<float2*>(smem_raw + G::ROWS_BYTES);
-  if (a.sc->status != 0) return;  // uniform over the grid
   const int tid = threadIdx.x, b = int(cl.block_rank());
-  const long long ci = blockIdx.x / G::P;
   for (int j = tid; j < N; j += G::L) {  // exp(-2 pi i j / N), FP64 then rounded once
     double sn, cs;
     sincospi(-2.0 * double(j) / double(N), &sn, &cs);
@@ -313,46 +314,80 @@ __global__ void __launch_bounds__(N / 2, csample_min_ctas<N>()) k_csample(Sample
   for (int e = tid; e < G::A * G::L; e += G::L) {
     const int ar = e / G::L, i = e % G::L;
     float2 v = make_float2(0.f, 0.f);
-    if (a.init_s != nullptr)
-      v = WF_LDG(reinterpret_cast<const float2*>(a.init_s + ci * a.init_stride +
-                                                 (long long)(G::P * ar + b) * G::W) + i);
+    if (init != nullptr) v = WF_LDG(reinterpret_cast<const float2*>(init + (long long)(G::P * ar + b) * G::W) + i);
     rows[ar * G::SP + i] = v;
   }
   __syncthreads();
   const int ar = tid / G::R, h = tid % G::R, y = G::P * ar + b;
   float2* row = rows + ar * G::SP;
-  const uint32_t chain = a.chain0 + uint32_t(ci);
-  const float sqrt_tau = a.sc->sqrt_tau;
-  const int eb = out_elem_bytes(a.out_dtype);
-  char* out = reinterpret_cast<char*>(a.out) + ci * a.n_samples * (long long)(G::H * G::W) * eb;
+  const int eb = out_elem_bytes(out_dtype);
+  char* out = reinterpret_cast<char*>(out_v);
   for (int done = 0;;) {
-    const uint32_t step = a.step0 + uint32_t(done);
-    ct_draw<N>(row, y, h, a.aq, sqrt_tau, step, chain, a.key0, a.key1);
+    const uint32_t step = step0 + uint32_t(done);
+    ct_draw<N>(row, y, h, aq, sqrt_tau, step, chain, k0, k1);
     __syncwarp();
     crow_fwd<N>(row, h, tw);
     __syncthreads();
     ccol_fwd<N>(rows, tid, b, tw);
     cl.sync();  // every CTA's partial column transforms are in place
-    ccol_draw<N>(cl, rows, b * G::L + tid, a.fg, step, chain, a.key0, a.key1);
+    ccol_draw<N>(cl, rows, b * G::L + tid, fg, step, chain, k0, k1);
     cl.sync();  // every unit's inverse stage has landed
     ccol_inv<N>(rows, tid, b, tw);
     __syncthreads();
     crow_inv<N>(row, h, tw);
     ++done;
-    if (done > a.burn_in && (done - a.burn_in) % a.thin == 0) {
-      const long long m = (done - a.burn_in) / a.thin - 1;
+    if (done > burn_in && (done - burn_in) % thin == 0) {
+      const long long m = (done - burn_in) / thin - 1;
       __syncthreads();
       char* dst = out + m * (long long)(G::H * G::W) * eb;
       for (int e = tid; e < G::A * G::L; e += G::L) {
         const int r2 = e / G::L, i = e % G::L;
-        store_pair(dst, (long long)(G::P * r2 + b) * G::L + i, rows[r2 * G::SP + i], a.out_dtype);
+        store_pair(dst, (long long)(G::P * r2 + b) * G::L + i, rows[r2 * G::SP + i], out_dtype);
       }
       __syncthreads();
     }
-    if (done == a.n_sweeps) break;
+    if (done == n_sweeps) break;
     __syncwarp();
   }
   cl.sync();  // no CTA leaves while another may still address its shared memory
+}
+
+// one problem, grid = n_chains clusters of P CTAs (chain = cluster index)
+template <int N>
+__global__ void __launch_bounds__(N / 2, csample_min_ctas<N>()) k_csample(SampleArgs a) {
+  using G = CGeo<N>;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (a.sc->status != 0) return;  // uniform over the grid
+  const long long ci = blockIdx.x / G::P;
+  const int eb = out_elem_bytes(a.out_dtype);
+  csample_chain<N>(cl, smem_raw, a.aq, a.fg, a.sc->sqrt_tau, a.init_s ? a.init_s + ci * a.init_stride : nullptr,
+                   reinterpret_cast<char*>(a.out) + ci * a.n_samples * (long long)(G::H * G::W) * eb, a.out_dtype,
+                   a.n_sweeps, a.burn_in, a.thin, a.step0, a.chain0 + uint32_t(ci), a.key0, a.key1);
+}
+
+// the sampling phase of a batch of large images (one cluster per image, after the Wiener solve): image f
+// samples n_samples sweeps from its s_W (fields[f].out_wf) with step words 0, 1, ... and its own chain and
+// key, into fields[f].out_samples; images whose set-up failed are skipped
+struct CBArgs {
+  const GBField* fields;
+  const Scalars* sc;
+  int F;
+  int n_samples;
+};
+template <int N>
+__global__ void __launch_bounds__(N / 2, csample_min_ctas<N>()) k_csample_batch(CBArgs a) {
+  using G = CGeo<N>;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int f = blockIdx.x / G::P;
+  const GBField fd = a.fields[f];
+  const Scalars sc = a.sc[f];
+  if (sc.status != 0 || fd.out_samples == nullptr || fd.out_wf == nullptr) return;  // uniform over the cluster
+  csample_chain<N>(cl, smem_raw, fd.aq, fd.fg, sc.sqrt_tau, fd.out_wf, fd.out_samples, kOutF32, a.n_samples, 0, 1,
+                   0u, fd.chain, fd.key0, fd.key1);
 }
 
 }  // namespace wf

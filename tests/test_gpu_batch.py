@@ -128,8 +128,17 @@ def test_batch_launch_shapes_and_autotune_keep_the_results():
         assert rel(gw, rw) < WF_TOL and rel(gs, rs) < SAMPLE_TOL
 
 
-def test_batch_large_images_in_shared_launches():
+@pytest.fixture(params=["cluster", "global"])
+def large_sampler(request):
+    prev = wf.wf_set_large_image_sampler(request.param)
+    yield request.param
+    wf.wf_set_large_image_sampler(prev)
+
+
+def test_batch_large_images_in_shared_launches(large_sampler):
     # many images above 128 x 128: every size class runs as chunks of fields of one cooperative launch
+    # (solves, and the samples with the global-memory sampler) or the samples come from one cluster per
+    # image; the single-image references use the same sampler
     sizes = [256] * 10 + [512] * 3
     probs = _mixed(sizes, seed0=200)
     bad = synth.make_problem(256, seed=7, mask_frac=0.1)
@@ -152,6 +161,29 @@ def test_batch_large_images_in_shared_launches():
         g, w = imgs[i].out_samples.cpu().numpy(), ref[0].cpu().numpy()
         for m in range(n_samples):
             assert rel(g[m], w[m]) < SAMPLE_TOL, (i, m)
+
+
+def test_batch_large_samples_without_wf_output():
+    """Through the C call with out_wf = NULL on the large images: the cluster sampling phase starts from
+    the library's own copy of s_W and gives the samples of a run that keeps s_W."""
+    sizes = [256, 512, 256]
+    probs = _mixed(sizes, seed0=400)
+    n_samples = 4
+    ref = [wf.BatchImage(*to_dev(p), seed=40 + i, chain=3 + i) for i, p in enumerate(probs)]
+    wf.wf_batch_run(ref, n_samples=n_samples, tol=1e-6)
+    imgs = [wf.BatchImage(*to_dev(p), seed=40 + i, chain=3 + i) for i, p in enumerate(probs)]
+    L = wf.load_library()
+    import ctypes
+    arr = wf._batch_items(imgs, n_samples)
+    for i in range(len(imgs)):
+        arr[i].out_wf = None
+    o = wf._batch_opts(n_samples=n_samples, tol=1e-6)
+    assert L.wf_batch_run(arr, len(imgs), ctypes.byref(o), None) == 0
+    torch.cuda.synchronize()
+    for i in range(len(imgs)):
+        assert arr[i].status == 0
+        for m in range(n_samples):
+            assert rel(imgs[i].out_samples[m].cpu().numpy(), ref[i].out_samples[m].cpu().numpy()) < 1e-5, (i, m)
 
 
 def test_full_size_mixed_batch_4096_sampled():
