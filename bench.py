@@ -63,8 +63,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the plain, single-chain and batch measurements")
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed-size batch measurement")
+    ap.add_argument("--large-chains", type=int, default=456,
+                    help="chains of the 256x256 large-image sampler measurement (512x512: a third)")
+    ap.add_argument("--large-samples", type=int, default=20,
+                    help="samples per chain of the 256x256 measurement (512x512: half)")
     ap.add_argument("--extras", default="batch,plain,precision,grad,bf16,band,spin2,large",
-                    help="extra workloads (comma list of batch, plain, precision, grad, bf16, band, spin2)")
+                    help="extra workloads (comma list of batch, plain, precision, grad, bf16, band, spin2, large)")
     ap.add_argument("--batch-images", type=int, default=4096, help="images of the mixed-size batch")
     ap.add_argument("--batch-large-streams", type=int, default=8,
                     help="large-image chunks per size class of the untuned batch replay")
@@ -466,15 +470,15 @@ def spin2_sampler(dev, n_chains: int = 512):
                          "frac": 2 * FLOPS_PER_SWEEP * n_chains * N_SAMPLES / (kms / 1e3) / 1e12 / FP32_PEAK_TFLOPS}}
 
 
-def large_sampler(dev):
+def large_sampler(dev, chains256: int = 456, samples256: int = 20):
     """Samplers for 256x256 and 512x512 (one thread-block cluster per chain, field in distributed shared
     memory) against the global-memory sampler on the same problem: paper-like field model (slope -2,
-    k0 = 1/32, noise variance U[0.05, 0.5], 10% masked); 456 chains x 20 samples (256^2) and 152 chains
-    x 10 samples (512^2), every sweep kept."""
+    k0 = 1/32, noise variance U[0.05, 0.5], 10% masked); by default 456 chains x 20 samples (256^2) and
+    152 chains x 10 samples (512^2), every sweep kept."""
     import torch
     from paper_1810_02821_gb300 import synth, wf
     res = {}
-    for H, chains, ns in ((256, 456, 20), (512, 152, 10)):
+    for H, chains, ns in ((256, chains256, samples256), (512, max(1, chains256 // 3), max(1, samples256 // 2))):
         p = synth.make_problem(H, seed=H, mask_frac=0.1, slope=-2.0, k0=1.0 / 32, sigma2=(0.05, 0.5))
         args = [torch.from_numpy(x).to(dev) for x in (p.d, p.Ndiag, p.mask, p.Pk)]
         out = torch.empty((chains, ns, H, H), device=dev)
@@ -627,7 +631,8 @@ def main():
             ("bf16", "bf16_sample_storage", reduced_output),
             ("band", "hierarchical_band_sampler", band_sampler),
             ("spin2", "spin2_shear_sampler", spin2_sampler),
-            ("large", "large_image_sampler", large_sampler)) if k in want and not (k == "batch" and a.no_batch)]
+            ("large", "large_image_sampler",
+             lambda dv: large_sampler(dv, a.large_chains, a.large_samples))) if k in want and not (k == "batch" and a.no_batch)]
         for _, name, fn in jobs:
             try:
                 other[name] = fn(dev)

@@ -21,8 +21,8 @@
  *     the minimum observed Ndiag (max_k P_k if every pixel is missing). A tau above the minimum observed
  *     Ndiag is rejected with WF_ERR_TAU.
  *   - Supported sizes: H == W in {16, 32, 64, 128, 256, 512, 1024} (wf_supported_size). Up to 128 x 128
- *     a chain's field stays in one SM's shared memory for the whole call. The 256 x 256 and 512 x 512
- *     samplers keep a chain's field in the shared memory of one thread-block cluster
+ *     a chain's field stays in one SM's shared memory for the whole call. At 256 x 256 and 512 x 512 the
+ *     samplers and Wiener filters keep the field in the shared memory of one thread-block cluster
  *     (wf_set_large_image_sampler). Otherwise larger images keep the field in global memory and run as
  *     one cooperative launch (all CTAs co-resident) whose phases are separated by a bounded grid barrier
  *     (WF_ERR_TIMEOUT if a barrier wait gives up). For those sizes wf_solve_ex starts from zero
@@ -392,11 +392,13 @@ void wf_set_kernel_timing(int32_t enable);
 double wf_last_kernel_ms(void);
 
 /*
- * Sampler used by wf_sample / wf_sample_ex for 256 x 256 and 512 x 512 images, per host thread:
- * mode 0 (default) keeps each chain's field in the distributed shared memory of one thread-block
- * cluster (N / 64 CTAs) for all sweeps, where the device can host such a cluster, else falls back to
- * mode 1; mode 1 keeps the fields in global memory and runs the sweeps as one cooperative launch. Both
- * give the same chain (the same draws; FP32 results agree to rounding). Returns the previous mode.
+ * Path for 256 x 256 and 512 x 512 images (wf_sample, wf_sample_ex, the first pass of wf_solve /
+ * wf_solve_ex, and the large images of wf_batch_run and the batch graphs), per host thread: mode 0
+ * (default) keeps each chain's or image's field in the distributed shared memory of one thread-block
+ * cluster (N / 64 CTAs) for all its sweeps (a batch image runs its level norms, cooled solve and samples
+ * in one cluster), where the device can host such a cluster, else falls back to mode 1; mode 1 keeps the
+ * fields in global memory and runs the sweeps as cooperative launches. Both compute the same chain and
+ * the same filter (the same draws and schedule; FP32 results agree to rounding). Returns the previous mode.
  */
 int32_t wf_set_large_image_sampler(int32_t mode);
 

@@ -498,6 +498,55 @@ const char* wf_status_string(wf_status s) {
 
 namespace {
 
+// Wiener filter for 256 and 512 on one thread-block cluster (k_cpipe with one image and no samples): level
+// norms, then the cooled iteration from zero, the field in distributed shared memory.
+wf_status solve_cluster(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int H, int W,
+                        const wf_solve_opts& o, float* out_s, int32_t* iters_out, double* resid_out, cudaStream_t st,
+                        wf::LaunchTimer* timer) {
+  const size_t n = size_t(H) * W, nz = size_t(H) * (W / 2);
+  Carve cv;
+  const size_t o_sc = cv.take<wf::Scalars>(1), o_res = cv.take<wf::BatchResult>(1), o_f = cv.take<wf::GBField>(1),
+               o_dn = cv.take<float2>(n), o_prev = cv.take<float2>(nz);
+  Scratch scr;
+  scr.st = st;
+  WF_CUDA(cudaMallocAsync(&scr.base, cv.off, st));
+  char* b = static_cast<char*>(scr.base);
+  auto* sc = reinterpret_cast<wf::Scalars*>(b + o_sc);
+  auto* res = reinterpret_cast<wf::BatchResult*>(b + o_res);
+  k_prep<<<1, 1024, 0, st>>>(d, Ndiag, mask, Pk, H, W, o.tau, o.eta, sc);
+  WF_CUDA(cudaGetLastError());
+  k_tables<<<int((n + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc, nullptr,
+                                                 reinterpret_cast<float2*>(b + o_dn), nullptr);
+  WF_CUDA(cudaGetLastError());
+  wf::GBField fd{};
+  fd.dn = reinterpret_cast<const float2*>(b + o_dn);
+  fd.Pk = Pk;
+  fd.prev = reinterpret_cast<float2*>(b + o_prev);
+  fd.out_wf = out_s;
+  fd.item = 0;
+  WF_CUDA(cudaMemcpyAsync(b + o_f, &fd, sizeof(fd), cudaMemcpyHostToDevice, st));
+  wf::CBArgs cb{};
+  cb.fields = reinterpret_cast<const wf::GBField*>(b + o_f);
+  cb.sc = sc;
+  cb.res = res;
+  cb.F = 1;
+  cb.tol = o.tol;
+  cb.eta = o.eta;
+  cb.level_tol = o.level_tol;
+  cb.max_iter = o.max_iter;
+  cb.level_max = o.level_max;
+  cb.check = o.check;
+  cb.n_samples = 0;
+  const cudaError_t e = H == 256 ? wf::launch_cpipe<256>(cb, st, timer) : wf::launch_cpipe<512>(cb, st, timer);
+  if (e != cudaSuccess) return cuda_fail(e);
+  wf::BatchResult hr;
+  WF_CUDA(cudaMemcpyAsync(&hr, res, sizeof(hr), cudaMemcpyDeviceToHost, st));
+  WF_CUDA(cudaStreamSynchronize(st));
+  if (iters_out) *iters_out = hr.iters;
+  if (resid_out) *resid_out = hr.resid;
+  return wf_status(hr.status);
+}
+
 // One cooled messenger solve (data mode, or rhs mode when rhs_tab is given: solves (S^-1 + N^-1) s = r
 // with the table's r and the supplied per-level norms).
 wf_status solve_pass(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int32_t H, int32_t W,
@@ -505,6 +554,8 @@ wf_status solve_pass(const float* d, const float* Ndiag, const uint8_t* mask, co
                      wf::LaunchTimer* timer, const float2* rhs_tab = nullptr, const double* rhs_norms = nullptr) {
   if (!size_on_chip(H)) {
     if (o.init_s) return WF_ERR_ARG;  // the large-image solve starts from zero
+    if (!rhs_tab && (H == 256 || H == 512) && g_large_sampler == 0 && cluster_fits(H))
+      return solve_cluster(d, Ndiag, mask, Pk, H, W, o, out_s, iters_out, resid_out, st, timer);
     return solve_global(d, Ndiag, mask, Pk, H, W, o, out_s, iters_out, resid_out, st, timer, rhs_tab, rhs_norms);
   }
   const size_t n = size_t(H) * W, nm = size_t(H) * (W / 2 + 1);
@@ -1143,16 +1194,16 @@ long long batch_slot_any(int H) {
 // Large images (H >= 256) of a batch: the images of a size class are split into chunks, and every chunk
 // is one cooperative launch of k_gbatch with one field per image (see wf_gbatch.cuh). Per-field buffers:
 // pixel tables aq, dn [n], mode table fg [nm], state Z and previous Wiener iterate [H][W/2].
-// With `cluster` (256 and 512, samples requested, a sampler cluster fits the device) k_gbatch runs the
-// solves only and the samples come from one k_csample_batch launch (one cluster per image) that starts
-// from each image's s_W (the caller's out_wf, else a per-field scratch image f_sw).
+// With `cluster` (256 and 512 where a cluster fits the device) the chunk is one k_cpipe launch instead:
+// one thread-block cluster per image runs its level norms, cooled solve and samples with the field in
+// distributed shared memory (Z unused).
 struct GBChunk {
   int H = 0, stream = 0;
   bool cluster = false;
   std::vector<int> items;  // batch item indices
   size_t o_fields = 0, o_idx = 0, o_sc = 0, o_state = 0, o_acc = 0, o_bn = 0, o_active = 0, o_bar = 0, o_tr = 0,
          o_tc = 0, o_tw = 0, o_data = 0, per_field = 0;
-  size_t f_aq = 0, f_dn = 0, f_fg = 0, f_z = 0, f_prev = 0, f_sw = 0;
+  size_t f_aq = 0, f_dn = 0, f_fg = 0, f_z = 0, f_prev = 0;
 };
 
 void layout_chunk(GBChunk& c, Carve& cv) {
@@ -1173,9 +1224,8 @@ void layout_chunk(GBChunk& c, Carve& cv) {
   c.f_aq = f.take<float2>(n);
   c.f_dn = f.take<float2>(n);
   c.f_fg = f.take<float2>(nm);
-  c.f_z = f.take<float2>(nz);
+  if (!c.cluster) c.f_z = f.take<float2>(nz);
   c.f_prev = f.take<float2>(nz);
-  if (c.cluster) c.f_sw = f.take<float>(n);
   c.per_field = f.off;
   c.o_data = cv.take<char>(c.per_field * size_t(F));
 }
@@ -1191,9 +1241,9 @@ std::vector<wf::GBField> chunk_fields(const GBChunk& c, const std::vector<wf::Ba
     g.dn = reinterpret_cast<const float2*>(base + c.f_dn);
     g.fg = reinterpret_cast<const float2*>(base + c.f_fg);
     g.Pk = it.Pk;
-    g.Z = reinterpret_cast<float2*>(base + c.f_z);
+    g.Z = c.cluster ? nullptr : reinterpret_cast<float2*>(base + c.f_z);
     g.prev = reinterpret_cast<float2*>(base + c.f_prev);
-    g.out_wf = it.out_wf ? it.out_wf : (c.cluster ? reinterpret_cast<float*>(base + c.f_sw) : nullptr);
+    g.out_wf = it.out_wf;
     g.out_samples = it.out_samples;
     g.chain = it.chain;
     g.key0 = uint32_t(it.seed & 0xffffffffu);
@@ -1277,15 +1327,32 @@ wf_status run_chunk(const GBChunk& c, const wf::BatchItem* d_items, wf::BatchRes
   auto* bn = reinterpret_cast<double*>(b + c.o_bn);
   auto* active = reinterpret_cast<int*>(b + c.o_active);
   auto* bar = reinterpret_cast<wf::GridBar*>(b + c.o_bar);
-  const long long init_words = 2LL * F * 16;
-  k_gb_init<<<int((init_words + 255) / 256 < 1024 ? (init_words + 255) / 256 : 1024), 256, 0, st>>>(state, acc, bn,
-                                                                                                   active, bar, F);
-  WF_CUDA(cudaGetLastError());
   k_prep_fields<<<F, 1024, 0, st>>>(d_items, idx, H, o.tau, o.eta, sc);
   WF_CUDA(cudaGetLastError());
   const long long tab = (long long)F * (size_t(H) * H + size_t(H) * (H / 2 + 1));
   k_tables_fields<<<int((tab + 255) / 256 < 4096 ? (tab + 255) / 256 : 4096), 256, 0, st>>>(d_items, idx, fields, sc,
                                                                                            F, H);
+  WF_CUDA(cudaGetLastError());
+  if (c.cluster) {
+    wf::CBArgs cb{};
+    cb.fields = fields;
+    cb.sc = sc;
+    cb.res = d_res;
+    cb.F = F;
+    cb.tol = o.tol;
+    cb.eta = o.eta;
+    cb.level_tol = o.level_tol;
+    cb.max_iter = o.max_iter;
+    cb.level_max = o.level_max;
+    cb.check = o.check;
+    cb.n_samples = o.n_samples;
+    const cudaError_t e = H == 256 ? wf::launch_cpipe<256>(cb, st, nullptr) : wf::launch_cpipe<512>(cb, st, nullptr);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return WF_OK;
+  }
+  const long long init_words = 2LL * F * 16;
+  k_gb_init<<<int((init_words + 255) / 256 < 1024 ? (init_words + 255) / 256 : 1024), 256, 0, st>>>(state, acc, bn,
+                                                                                                   active, bar, F);
   WF_CUDA(cudaGetLastError());
   k_twiddles<<<8, 256, 0, st>>>(H, H, reinterpret_cast<float2*>(b + c.o_tr), reinterpret_cast<float2*>(b + c.o_tc),
                                 reinterpret_cast<float2*>(b + c.o_tw));
@@ -1309,19 +1376,10 @@ wf_status run_chunk(const GBChunk& c, const wf::BatchItem* d_items, wf::BatchRes
   a.max_iter = o.max_iter;
   a.level_max = o.level_max;
   a.check = o.check;
-  a.n_samples = c.cluster ? 0 : o.n_samples;
+  a.n_samples = o.n_samples;
   a.grid_pct = o.large_grid_pct;
-  cudaError_t e = launch_gbatch_any(H, a, st);
+  const cudaError_t e = launch_gbatch_any(H, a, st);
   if (e != cudaSuccess) return cuda_fail(e);
-  if (c.cluster && o.n_samples > 0) {
-    wf::CBArgs cb{};
-    cb.fields = fields;
-    cb.sc = sc;
-    cb.F = F;
-    cb.n_samples = o.n_samples;
-    e = H == 256 ? wf::launch_csample_batch<256>(cb, st) : wf::launch_csample_batch<512>(cb, st);
-    if (e != cudaSuccess) return cuda_fail(e);
-  }
   return WF_OK;
 }
 
@@ -1406,7 +1464,7 @@ wf_status plan_batch(const wf_batch_item* items, int n_items, const wf_batch_opt
       GBChunk ch;
       ch.H = kBatchSizes[c];
       ch.stream = k;
-      ch.cluster = (ch.H == 256 || ch.H == 512) && o.n_samples > 0 && g_large_sampler == 0 && cluster_fits(ch.H);
+      ch.cluster = (ch.H == 256 || ch.H == 512) && g_large_sampler == 0 && cluster_fits(ch.H);
       for (int i = k * nc / parts; i < (k + 1) * nc / parts; ++i) ch.items.push_back(p->cls[c][i]);
       layout_chunk(ch, cv);
       p->chunks.push_back(std::move(ch));

@@ -32,15 +32,27 @@ struct CGeo {
   static constexpr int A = 64;       // rows per CTA
   static constexpr int L = N / 2;    // complex length of a row transform = threads per CTA
   static constexpr int R = L / 64;   // threads per row in the row passes
-  static constexpr int SP = L + R;   // float2 stride of a row: a half-warp's R-strided loads hit distinct banks
+  // float2 stride of a row: with the row-major lane map below (the R threads of a row are lanes
+  // a, a + 32/R, ...), a half-warp's accesses in the row passes hit distinct banks (R = 2) or at most two
+  // per bank (R = 4)
+  static constexpr int SP = L + R / 2;
   static constexpr int ROWS_BYTES = A * SP * 8;
-  static constexpr int SMEM = ROWS_BYTES + N * 8;  // rows, then the twiddles exp(-2 pi i j / N)
+  static constexpr int SMEM = ROWS_BYTES + N * 8 + (33 + 16 + kMaxLevels) * 8;  // rows, twiddles, FP64 sums, level norms
   static constexpr int WH = W / 2 + 1;
 };
 
 // ---------------------------------------------------------------------------------------------
 // row passes (R threads per row, h = the thread's index within its row)
 // ---------------------------------------------------------------------------------------------
+// local row a and index h of thread tid: a warp holds 32/R rows, thread h of each in lanes 32h/R ..
+template <int N>
+WF_HD void crow_of(int tid, int& a, int& h) {
+  constexpr int per = 32 / CGeo<N>::R;
+  const int lane = tid % 32;
+  a = (tid / 32) * per + lane % per;
+  h = lane / per;
+}
+
 // real-transform post pass of the mode pair (K, L - K) (forward): c[K] and c[L - K] of the packed-complex
 // FFT -> R[K] and R[L - K], with W = exp(-2 pi i K / N)
 WF_HD void c_r2c_pair(float2& a, float2& b, float2 w) {
@@ -242,13 +254,13 @@ __device__ __forceinline__ void cdraw_pair(float2& y1, float2& y2, int K, int ky
   }
 }
 
-// cross-cluster radix-P stage with the s-draw. Work unit (slot t, k' = u with its mirror v = 64 - u):
-// gathers Y_j[u] (and Y_j[v]) from every CTA j, forms the column spectrum t_hat[u + 64 m], draws, and
-// scatters the inverse stage back. g = the thread's index in the cluster.
-template <int N>
-__device__ __forceinline__ void ccol_draw(cooperative_groups::cluster_group& cl, float2* rows, int g,
-                                          const float2* __restrict__ fg, uint32_t step, uint32_t chain,
-                                          uint32_t k0, uint32_t k1) {
+// Cross-cluster radix-P stage. Work unit (slot t, k' = u with its mirror v = 64 - u): gathers Y_j[u]
+// (and Y_j[v]) from every CTA j, forms the column spectrum t_hat[u + 64 m], hands every mode pair
+// (ky1 < N/2, ky2 = N - ky1, or N/2 when ky1 = 0) of column K to fn(K, y1, y2, ky1, ky2), and with WRITE
+// scatters the inverse stage back. g = the thread's index in the cluster. Every mode of the half spectrum
+// is in exactly one pair of one unit.
+template <int N, bool WRITE, class F>
+__device__ __forceinline__ void ccol_units(cooperative_groups::cluster_group& cl, float2* rows, int g, F&& fn) {
   using G = CGeo<N>;
   constexpr int P = G::P, L = G::L, R = G::R;
   for (int w = g; w < L * 33; w += P * L) {
@@ -264,28 +276,175 @@ __device__ __forceinline__ void ccol_draw(cooperative_groups::cluster_group& cl,
     }
     fft<P, false>(p);  // p[m] = t_hat[u + 64 m]
     if (u == 0) {
-      cdraw_pair<N>(p[0], p[P / 2], K, 0, N / 2, fg, step, chain, k0, k1);
+      fn(K, p[0], p[P / 2], 0, N / 2);
 #pragma unroll
-      for (int m = 1; m < P / 2; ++m) cdraw_pair<N>(p[m], p[P - m], K, 64 * m, N - 64 * m, fg, step, chain, k0, k1);
+      for (int m = 1; m < P / 2; ++m) fn(K, p[m], p[P - m], 64 * m, N - 64 * m);
     } else if (u == 32) {
 #pragma unroll
-      for (int m = 0; m < P / 2; ++m)
-        cdraw_pair<N>(p[m], p[P - 1 - m], K, 32 + 64 * m, N - 32 - 64 * m, fg, step, chain, k0, k1);
+      for (int m = 0; m < P / 2; ++m) fn(K, p[m], p[P - 1 - m], 32 + 64 * m, N - 32 - 64 * m);
     } else {
       fft<P, false>(q);  // q[m] = t_hat[v + 64 m]
 #pragma unroll
       for (int m = 0; m < P / 2; ++m) {
-        cdraw_pair<N>(p[m], q[P - 1 - m], K, u + 64 * m, N - u - 64 * m, fg, step, chain, k0, k1);
-        cdraw_pair<N>(q[m], p[P - 1 - m], K, v + 64 * m, N - v - 64 * m, fg, step, chain, k0, k1);
+        fn(K, p[m], q[P - 1 - m], u + 64 * m, N - u - 64 * m);
+        fn(K, q[m], p[P - 1 - m], v + 64 * m, N - v - 64 * m);
       }
-      fft<P, true>(q);
+      if (WRITE) {
+        fft<P, true>(q);
 #pragma unroll
-      for (int j = 0; j < P; ++j) cl.map_shared_rank(rows, j)[v * G::SP + t] = q[j];
+        for (int j = 0; j < P; ++j) cl.map_shared_rank(rows, j)[v * G::SP + t] = q[j];
+      }
     }
-    fft<P, true>(p);
+    if (WRITE) {
+      fft<P, true>(p);
 #pragma unroll
-    for (int j = 0; j < P; ++j) cl.map_shared_rank(rows, j)[u * G::SP + t] = p[j];
+      for (int j = 0; j < P; ++j) cl.map_shared_rank(rows, j)[u * G::SP + t] = p[j];
+    }
   }
+}
+
+// the s-draw of Alg. 1 on every mode
+template <int N>
+__device__ __forceinline__ void ccol_draw(cooperative_groups::cluster_group& cl, float2* rows, int g,
+                                          const float2* __restrict__ fg, uint32_t step, uint32_t chain,
+                                          uint32_t k0, uint32_t k1) {
+  ccol_units<N, true>(cl, rows, g, [&](int K, float2& y1, float2& y2, int ky1, int ky2) {
+    cdraw_pair<N>(y1, y2, K, ky1, ky2, fg, step, chain, k0, k1);
+  });
+}
+
+// Wiener-filter update at level lambda (G -> 0): s_hat = f t_hat with f = P / (P + lambda tau) (scaled by
+// 1/n). With CMP the residual of the previous iterate, |s_hat_new - s_hat_old|^2 (1 + P / (lambda tau))^2,
+// is summed over the full spectrum (the mirror modes counted; returned as this thread's share); with STORE
+// the new modes go to prev[ky * W/2 + K] (packed edge column as stored).
+template <int N>
+__device__ __forceinline__ double ccol_wf(cooperative_groups::cluster_group& cl, float2* rows, int g,
+                                          const float* __restrict__ Pk, float lt_, float2* __restrict__ prev,
+                                          bool cmp, bool store) {
+  using G = CGeo<N>;
+  constexpr int WH = G::WH, LR = G::L;
+  constexpr float INV_N = 1.0f / float(G::H * G::W);
+  const float inv_lt = 1.0f / lt_;
+  auto wres = [&](float P, float dre, float dim) -> double {
+    const float q = fmaf(P, inv_lt, 1.0f);
+    return double(fmaf(dre, dre, dim * dim) * (q * q));
+  };
+  auto fcoef = [&](float P) { return wf_fdiv(P, P + lt_) * INV_N; };
+  double acc = 0.0;
+  ccol_units<N, true>(cl, rows, g, [&](int K, float2& y1, float2& y2, int ky1, int ky2) {
+    if (K != 0) {
+      const float P1 = WF_LDG(Pk + ky1 * WH + K), P2 = WF_LDG(Pk + ky2 * WH + K);
+      const float2 n1 = cscale(y1, fcoef(P1)), n2 = cscale(y2, fcoef(P2));
+      if (cmp) {
+        const float2 o1 = prev[ky1 * LR + K], o2 = prev[ky2 * LR + K];
+        acc += 2.0 * (wres(P1, n1.x - o1.x, n1.y - o1.y) + wres(P2, n2.x - o2.x, n2.y - o2.y));
+      }
+      y1 = n1;
+      y2 = n2;
+    } else {
+      const float Pa1 = WF_LDG(Pk + ky1 * WH), Pb1 = WF_LDG(Pk + ky1 * WH + G::W / 2);
+      const float fa1 = fcoef(Pa1), fb1 = fcoef(Pb1);
+      if (ky1 == 0) {
+        const float Pa2 = WF_LDG(Pk + ky2 * WH), Pb2 = WF_LDG(Pk + ky2 * WH + G::W / 2);
+        const float2 n1 = make_float2(fa1 * y1.x, fb1 * y1.y);
+        const float2 n2 = make_float2(fcoef(Pa2) * y2.x, fcoef(Pb2) * y2.y);
+        if (cmp) {
+          const float2 o1 = prev[ky1 * LR], o2 = prev[ky2 * LR];
+          acc += wres(Pa1, n1.x - o1.x, 0.f) + wres(Pb1, n1.y - o1.y, 0.f) + wres(Pa2, n2.x - o2.x, 0.f) +
+                 wres(Pb2, n2.y - o2.y, 0.f);
+        }
+        y1 = n1;
+        y2 = n2;
+      } else {
+        const float2 y2c = cconj(y2);
+        const float2 A = cscale(cscale(cadd(y1, y2c), 0.5f), fa1);
+        const float2 B = cscale(cmul_mi(cscale(csub(y1, y2c), 0.5f)), fb1);
+        if (cmp) {
+          const float2 o1 = prev[ky1 * LR], o2c = cconj(prev[ky2 * LR]);
+          const float2 oA = cscale(cadd(o1, o2c), 0.5f);
+          const float2 oB = cmul_mi(cscale(csub(o1, o2c), 0.5f));
+          acc += 2.0 * (wres(Pa1, A.x - oA.x, A.y - oA.y) + wres(Pb1, B.x - oB.x, B.y - oB.y));
+        }
+        y1 = cadd(A, cmul_i(B));
+        y2 = cadd(cconj(A), cmul_i(cconj(B)));
+      }
+    }
+    if (store) {
+      prev[ky1 * LR + K] = y1;
+      prev[ky2 * LR + K] = y2;
+    }
+  });
+  return acc;
+}
+
+// sum over the full spectrum of P^2 |V|^2 for the forward transform V (level norms); this thread's share
+template <int N>
+__device__ __forceinline__ double ccol_p2(cooperative_groups::cluster_group& cl, float2* rows, int g,
+                                          const float* __restrict__ Pk) {
+  using G = CGeo<N>;
+  constexpr int WH = G::WH;
+  auto p2 = [](float P, float re, float im) -> double { return double(P * P * fmaf(re, re, im * im)); };
+  double acc = 0.0;
+  ccol_units<N, false>(cl, rows, g, [&](int K, float2& y1, float2& y2, int ky1, int ky2) {
+    if (K != 0) {
+      acc += 2.0 * (p2(WF_LDG(Pk + ky1 * WH + K), y1.x, y1.y) + p2(WF_LDG(Pk + ky2 * WH + K), y2.x, y2.y));
+    } else if (ky1 == 0) {
+      acc += p2(WF_LDG(Pk + ky1 * WH), y1.x, 0.f) + p2(WF_LDG(Pk + ky1 * WH + G::W / 2), y1.y, 0.f) +
+             p2(WF_LDG(Pk + ky2 * WH), y2.x, 0.f) + p2(WF_LDG(Pk + ky2 * WH + G::W / 2), y2.y, 0.f);
+    } else {
+      const float2 y2c = cconj(y2);
+      const float2 A = cscale(cadd(y1, y2c), 0.5f);
+      const float2 B = cmul_mi(cscale(csub(y1, y2c), 0.5f));
+      acc += 2.0 * (p2(WF_LDG(Pk + ky1 * WH), A.x, A.y) + p2(WF_LDG(Pk + ky1 * WH + G::W / 2), B.x, B.y));
+    }
+  });
+  return acc;
+}
+
+// Wiener-filter pixel update of global row y at level lambda: t = d + w (s - d), w = 1 / (1 + lambda tau /
+// N_bar), table dn[x*H + y] = (d, 1/N_bar) ((0, 0) on missing pixels: t = s)
+template <int N>
+__device__ __forceinline__ void ct_update_wf(float2* row, int y, int h, const float2* __restrict__ dn, float lt_) {
+  using G = CGeo<N>;
+  for (int x2 = h; x2 < G::W / 2; x2 += G::R) {
+    float2 v = row[x2];
+    const float2 c0 = WF_LDG(dn + (2 * x2) * G::H + y), c1 = WF_LDG(dn + (2 * x2 + 1) * G::H + y);
+    const float w0 = wf_rcp(fmaf(lt_, c0.y, 1.0f)), w1 = wf_rcp(fmaf(lt_, c1.y, 1.0f));
+    v.x = fmaf(w0, v.x - c0.x, c0.x);
+    v.y = fmaf(w1, v.y - c1.x, c1.x);
+    row[x2] = v;
+  }
+}
+
+// right-hand side N_lambda^-1 d = d / (N_bar + lambda tau) of this CTA's rows (0 on missing pixels)
+template <int N>
+__device__ __forceinline__ void crhs_rows(float2* rows, int b, const float2* __restrict__ dn, float lt_) {
+  using G = CGeo<N>;
+  for (int e = threadIdx.x; e < G::A * G::L; e += G::L) {
+    const int ar = e / G::L, i = e % G::L, y = G::P * ar + b;
+    float2 r;
+    const float2 c0 = WF_LDG(dn + (2 * i) * G::H + y), c1 = WF_LDG(dn + (2 * i + 1) * G::H + y);
+    const float nb0 = c0.y > 0.0f ? wf_rcp(c0.y) : wf_inf(), nb1 = c1.y > 0.0f ? wf_rcp(c1.y) : wf_inf();
+    r.x = c0.x / (nb0 + lt_);
+    r.y = c1.x / (nb1 + lt_);
+    rows[ar * G::SP + i] = r;
+  }
+}
+
+// Cluster-wide sum of one double per thread, the same in every thread: block sums, then the P CTA sums
+// collected in CTA 0's shared slots part[0..P) and added in rank order. red: >= 33 doubles.
+template <int N>
+__device__ __forceinline__ double cluster_sum(cooperative_groups::cluster_group& cl, double v, double* red,
+                                              double* part) {
+  using G = CGeo<N>;
+  const double s = block_sum(v, red);
+  if (threadIdx.x == 0) cl.map_shared_rank(part, 0)[cl.block_rank()] = s;
+  cl.sync();
+  const double* p0 = cl.map_shared_rank(part, 0);
+  double tot = 0.0;
+#pragma unroll
+  for (int j = 0; j < G::P; ++j) tot += p0[j];
+  return tot;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -294,31 +453,50 @@ __device__ __forceinline__ void ccol_draw(cooperative_groups::cluster_group& cl,
 template <int N>
 constexpr int csample_min_ctas() { return N == 256 ? 3 : 1; }
 
-// the sweeps of one chain by its cluster: s_0 from init (row-major [H][W], nullptr: zero), sample m (the
-// state after sweep burn_in + (m + 1) thin) to out + m H W elements of type out_dtype
+// twiddles exp(-2 pi i j / N) (FP64, rounded once) into shared memory
 template <int N>
-__device__ __forceinline__ void csample_chain(cooperative_groups::cluster_group& cl, unsigned char* smem_raw,
-                                              const float2* __restrict__ aq, const float2* __restrict__ fg,
-                                              float sqrt_tau, const float* init, void* out_v, int out_dtype,
-                                              int n_sweeps, int burn_in, int thin, uint32_t step0, uint32_t chain,
-                                              uint32_t k0, uint32_t k1) {
-  using G = CGeo<N>;
-  float2* rows = reinterpret_cast<float2*>(smem_raw);
-  float2* tw = reinterpret_cast<float2*>(smem_raw + G::ROWS_BYTES);
-  const int tid = threadIdx.x, b = int(cl.block_rank());
-  for (int j = tid; j < N; j += G::L) {  // exp(-2 pi i j / N), FP64 then rounded once
+__device__ __forceinline__ void ctw_init(float2* tw) {
+  for (int j = threadIdx.x; j < N; j += CGeo<N>::L) {
     double sn, cs;
     sincospi(-2.0 * double(j) / double(N), &sn, &cs);
     tw[j] = make_float2(float(cs), float(sn));
   }
-  for (int e = tid; e < G::A * G::L; e += G::L) {
+}
+
+// this CTA's rows of a row-major [H][W] image into the staged rows (nullptr: zero)
+template <int N>
+__device__ __forceinline__ void crows_load(float2* rows, int b, const float* src) {
+  using G = CGeo<N>;
+  for (int e = threadIdx.x; e < G::A * G::L; e += G::L) {
     const int ar = e / G::L, i = e % G::L;
     float2 v = make_float2(0.f, 0.f);
-    if (init != nullptr) v = WF_LDG(reinterpret_cast<const float2*>(init + (long long)(G::P * ar + b) * G::W) + i);
+    if (src != nullptr) v = WF_LDG(reinterpret_cast<const float2*>(src + (long long)(G::P * ar + b) * G::W) + i);
     rows[ar * G::SP + i] = v;
   }
-  __syncthreads();
-  const int ar = tid / G::R, h = tid % G::R, y = G::P * ar + b;
+}
+
+// the staged rows to this CTA's rows of an image of element type t
+template <int N>
+__device__ __forceinline__ void crows_store(const float2* rows, int b, void* dst, int t) {
+  using G = CGeo<N>;
+  for (int e = threadIdx.x; e < G::A * G::L; e += G::L) {
+    const int r2 = e / G::L, i = e % G::L;
+    store_pair(dst, (long long)(G::P * r2 + b) * G::L + i, rows[r2 * G::SP + i], t);
+  }
+}
+
+// Sampler sweeps (Alg. 1) of one chain by its cluster from the staged rows (the current s): sample m (the
+// state after sweep burn_in + (m + 1) thin) to out + m H W elements of type out_dtype
+template <int N>
+__device__ __forceinline__ void csample_loop(cooperative_groups::cluster_group& cl, float2* rows, const float2* tw,
+                                             const float2* __restrict__ aq, const float2* __restrict__ fg,
+                                             float sqrt_tau, void* out_v, int out_dtype, int n_sweeps, int burn_in,
+                                             int thin, uint32_t step0, uint32_t chain, uint32_t k0, uint32_t k1) {
+  using G = CGeo<N>;
+  const int tid = threadIdx.x, b = int(cl.block_rank());
+  int ar, h;
+  crow_of<N>(tid, ar, h);
+  const int y = G::P * ar + b;
   float2* row = rows + ar * G::SP;
   const int eb = out_elem_bytes(out_dtype);
   char* out = reinterpret_cast<char*>(out_v);
@@ -339,17 +517,91 @@ __device__ __forceinline__ void csample_chain(cooperative_groups::cluster_group&
     if (done > burn_in && (done - burn_in) % thin == 0) {
       const long long m = (done - burn_in) / thin - 1;
       __syncthreads();
-      char* dst = out + m * (long long)(G::H * G::W) * eb;
-      for (int e = tid; e < G::A * G::L; e += G::L) {
-        const int r2 = e / G::L, i = e % G::L;
-        store_pair(dst, (long long)(G::P * r2 + b) * G::L + i, rows[r2 * G::SP + i], out_dtype);
-      }
+      crows_store<N>(rows, b, out + m * (long long)(G::H * G::W) * eb, out_dtype);
       __syncthreads();
     }
     if (done == n_sweeps) break;
     __syncwarp();
   }
-  cl.sync();  // no CTA leaves while another may still address its shared memory
+}
+
+// The cooled G -> 0 iteration (Alg. 1 without draws, lambda-cooling) of one image by its cluster from
+// s = 0, with the per-level norms ||S N_lambda^-1 d||^2 computed first. Leaves s_W in the staged rows and
+// returns the wf_status (0 converged, 5 not converged, 6 non-finite); it and rho receive the sweeps and
+// the last measured residual. red: 33 doubles, part: P doubles, bn: kMaxLevels doubles (shared).
+template <int N>
+__device__ __forceinline__ int csolve_loop(cooperative_groups::cluster_group& cl, float2* rows, const float2* tw,
+                                           double* red, double* part, double* bn, const float2* __restrict__ dn,
+                                           const float* __restrict__ Pk, const Scalars& sc, float2* prev, double tol,
+                                           double eta, double level_tol, int max_iter, int level_max, int check,
+                                           int& it, double& rho) {
+  using G = CGeo<N>;
+  const int tid = threadIdx.x, b = int(cl.block_rank()), g = b * G::L + tid;
+  int ar, h;
+  crow_of<N>(tid, ar, h);
+  const int y = G::P * ar + b;
+  float2* row = rows + ar * G::SP;
+  constexpr double NPIX = double(G::H) * double(G::W);
+  for (int lev = 0; lev < sc.n_levels; ++lev) {  // level norms
+    crhs_rows<N>(rows, b, dn, float(level_lambda(sc, lev, eta) * sc.tau));
+    __syncthreads();
+    crow_fwd<N>(row, h, tw);
+    __syncthreads();
+    ccol_fwd<N>(rows, tid, b, tw);
+    cl.sync();
+    const double tot = cluster_sum<N>(cl, ccol_p2<N>(cl, rows, g, Pk), red, part);
+    if (tid == 0) bn[lev] = tot / NPIX;
+    cl.sync();  // every CTA has read the partial sums and finished its remote reads of the rows
+  }
+  crows_load<N>(rows, b, nullptr);
+  __syncthreads();
+  const double tau = sc.tau;
+  int lev = 0, k = 0, status = 1;
+  double lam = sc.lam0;
+  float ltau = float(lam * tau);
+  const int last_level = sc.n_levels - 1;
+  it = 0;
+  rho = -1.0;
+  while (true) {
+    ++k;
+    ++it;
+    const bool cmp = (k % check == 0) && k >= 2;
+    const bool store = ((k + 1) % check == 0);
+    ct_update_wf<N>(row, y, h, dn, ltau);
+    __syncwarp();
+    crow_fwd<N>(row, h, tw);
+    __syncthreads();
+    ccol_fwd<N>(rows, tid, b, tw);
+    cl.sync();
+    const double acc = ccol_wf<N>(cl, rows, g, Pk, ltau, prev, cmp, store);
+    cl.sync();
+    if (cmp) {
+      const double tot = cluster_sum<N>(cl, acc, red, part) * NPIX;
+      const double bnl = bn[lev];
+      const double r2 = bnl > 0.0 ? tot / bnl : tot;
+      rho = sqrt(r2);
+      if (!(r2 == r2) || r2 > 1e300) {
+        status = 6;  // non-finite residual
+      } else if (lev < last_level) {
+        if (rho < level_tol || k >= level_max) {
+          ++lev;
+          lam = level_lambda(sc, lev, eta);
+          ltau = float(lam * tau);
+          k = 0;
+        }
+      } else if (rho < tol) {
+        status = 0;
+      }
+    }
+    if (status == 1 && it >= max_iter) status = 5;  // not converged
+    ccol_inv<N>(rows, tid, b, tw);
+    __syncthreads();
+    crow_inv<N>(row, h, tw);
+    if (status != 1) break;
+    __syncwarp();
+  }
+  __syncthreads();
+  return status;
 }
 
 // one problem, grid = n_chains clusters of P CTAs (chain = cluster index)
@@ -359,35 +611,64 @@ __global__ void __launch_bounds__(N / 2, csample_min_ctas<N>()) k_csample(Sample
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* rows = reinterpret_cast<float2*>(smem_raw);
+  float2* tw = reinterpret_cast<float2*>(smem_raw + G::ROWS_BYTES);
   if (a.sc->status != 0) return;  // uniform over the grid
   const long long ci = blockIdx.x / G::P;
   const int eb = out_elem_bytes(a.out_dtype);
-  csample_chain<N>(cl, smem_raw, a.aq, a.fg, a.sc->sqrt_tau, a.init_s ? a.init_s + ci * a.init_stride : nullptr,
-                   reinterpret_cast<char*>(a.out) + ci * a.n_samples * (long long)(G::H * G::W) * eb, a.out_dtype,
-                   a.n_sweeps, a.burn_in, a.thin, a.step0, a.chain0 + uint32_t(ci), a.key0, a.key1);
+  ctw_init<N>(tw);
+  crows_load<N>(rows, int(cl.block_rank()), a.init_s ? a.init_s + ci * a.init_stride : nullptr);
+  __syncthreads();
+  csample_loop<N>(cl, rows, tw, a.aq, a.fg, a.sc->sqrt_tau,
+                  reinterpret_cast<char*>(a.out) + ci * a.n_samples * (long long)(G::H * G::W) * eb, a.out_dtype,
+                  a.n_sweeps, a.burn_in, a.thin, a.step0, a.chain0 + uint32_t(ci), a.key0, a.key1);
+  cl.sync();  // no CTA leaves while another may still address its shared memory
 }
 
-// the sampling phase of a batch of large images (one cluster per image, after the Wiener solve): image f
-// samples n_samples sweeps from its s_W (fields[f].out_wf) with step words 0, 1, ... and its own chain and
-// key, into fields[f].out_samples; images whose set-up failed are skipped
+// Whole pipeline of a batch of large images, one cluster per image: level norms, the cooled Wiener solve
+// from s = 0 (result to fields[f].out_wf when given, status to res[fields[f].item]), then n_samples
+// sampler sweeps from s_W with step words 0, 1, ... and the image's chain and key into
+// fields[f].out_samples. Images whose set-up failed only report their status.
 struct CBArgs {
   const GBField* fields;
   const Scalars* sc;
+  BatchResult* res;
   int F;
-  int n_samples;
+  double tol, eta, level_tol;
+  int max_iter, level_max, check, n_samples;
 };
 template <int N>
-__global__ void __launch_bounds__(N / 2, csample_min_ctas<N>()) k_csample_batch(CBArgs a) {
+__global__ void __launch_bounds__(N / 2, csample_min_ctas<N>()) k_cpipe(CBArgs a) {
   using G = CGeo<N>;
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* rows = reinterpret_cast<float2*>(smem_raw);
+  float2* tw = reinterpret_cast<float2*>(smem_raw + G::ROWS_BYTES);
+  double* red = reinterpret_cast<double*>(smem_raw + G::ROWS_BYTES + N * 8);
+  double* part = red + 33;
+  double* bn = part + 16;
   const int f = blockIdx.x / G::P;
   const GBField fd = a.fields[f];
   const Scalars sc = a.sc[f];
-  if (sc.status != 0 || fd.out_samples == nullptr || fd.out_wf == nullptr) return;  // uniform over the cluster
-  csample_chain<N>(cl, smem_raw, fd.aq, fd.fg, sc.sqrt_tau, fd.out_wf, fd.out_samples, kOutF32, a.n_samples, 0, 1,
-                   0u, fd.chain, fd.key0, fd.key1);
+  const bool lead = cl.block_rank() == 0 && threadIdx.x == 0;
+  if (sc.status != 0) {  // uniform over the cluster
+    if (lead) a.res[fd.item] = BatchResult{-1.0, 0, sc.status};
+    return;
+  }
+  ctw_init<N>(tw);
+  __syncthreads();
+  int it = 0;
+  double rho = -1.0;
+  const int status = csolve_loop<N>(cl, rows, tw, red, part, bn, fd.dn, fd.Pk, sc, fd.prev, a.tol, a.eta,
+                                    a.level_tol, a.max_iter, a.level_max, a.check, it, rho);
+  if (fd.out_wf) crows_store<N>(rows, int(cl.block_rank()), fd.out_wf, kOutF32);
+  if (lead) a.res[fd.item] = BatchResult{rho, it, status};
+  __syncthreads();
+  if (a.n_samples > 0 && fd.out_samples)
+    csample_loop<N>(cl, rows, tw, fd.aq, fd.fg, sc.sqrt_tau, fd.out_samples, kOutF32, a.n_samples, 0, 1, 0u,
+                    fd.chain, fd.key0, fd.key1);
+  cl.sync();  // no CTA leaves while another may still address its shared memory
 }
 
 }  // namespace wf

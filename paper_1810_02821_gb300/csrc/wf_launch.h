@@ -58,9 +58,9 @@ cudaError_t launch_csample(const SampleArgs& a, cudaStream_t st, LaunchTimer* t)
 // clusters of k_csample<N> that can be resident at once on the current device (0: none)
 template <int N>
 cudaError_t csample_clusters(int* clusters);
-// sampling phase of a batch of large images: one cluster per image (k_csample_batch)
+// whole pipeline (level norms, cooled solve, samples) of a batch of large images: one cluster per image
 template <int N>
-cudaError_t launch_csample_batch(const CBArgs& a, cudaStream_t st);
+cudaError_t launch_cpipe(const CBArgs& a, cudaStream_t st, LaunchTimer* t);
 
 // definitions, included by the per-size translation units only
 #if defined(WF_LAUNCH_DEFINE)
@@ -224,7 +224,7 @@ cudaError_t csample_config(cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr, i
   using G = CGeo<N>;
   cudaError_t e = cudaFuncSetAttribute(k_csample<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_csample_batch<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+  e = cudaFuncSetAttribute(k_cpipe<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
   if (e != cudaSuccess) return e;
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = G::P;
@@ -259,18 +259,20 @@ cudaError_t launch_csample(const SampleArgs& a, cudaStream_t st, LaunchTimer* t)
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 template <int N>
-cudaError_t launch_csample_batch(const CBArgs& a, cudaStream_t st) {
+cudaError_t launch_cpipe(const CBArgs& a, cudaStream_t st, LaunchTimer* t) {
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
   cudaError_t e = csample_config<N>(&cfg, attr, a.F, st);
   if (e != cudaSuccess) return e;
-  e = cudaLaunchKernelEx(&cfg, k_csample_batch<N>, a);
+  if (t) t->start();
+  e = cudaLaunchKernelEx(&cfg, k_cpipe<N>, a);
+  if (t) t->stop();
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 #define WF_INSTANTIATE_CLUSTER(N)                                                            \
   template cudaError_t launch_csample<N>(const SampleArgs&, cudaStream_t, LaunchTimer*);     \
   template cudaError_t csample_clusters<N>(int*);                                            \
-  template cudaError_t launch_csample_batch<N>(const CBArgs&, cudaStream_t);
+  template cudaError_t launch_cpipe<N>(const CBArgs&, cudaStream_t, LaunchTimer*);
 #endif
 
 }  // namespace wf

@@ -627,9 +627,10 @@ def wf_set_kernel_timing(enable: bool) -> None:
 
 
 def wf_set_large_image_sampler(mode: str) -> str:
-    """Sampler for 256 x 256 and 512 x 512 images on this thread: "cluster" (the field in the shared memory
-    of one thread-block cluster per chain, where the device can host it) or "global" (fields in global
-    memory, one cooperative launch). Returns the previous mode."""
+    """Path for 256 x 256 and 512 x 512 images on this thread (samplers, Wiener filters, batches):
+    "cluster" (the field in the shared memory of one thread-block cluster per chain or image, where the
+    device can host it) or "global" (fields in global memory, cooperative launches). Returns the previous
+    mode."""
     modes = {"cluster": 0, "global": 1}
     if mode not in modes:
         raise ValueError(f"mode must be one of {sorted(modes)}")

@@ -83,13 +83,34 @@ def _easy(H):
 
 
 @pytest.mark.parametrize("H", [256, 512])
-def test_wiener_filter_large(H):
+def test_wiener_filter_large(H, sampler):
     p = _easy(H)
     r = wf.wf_solve(*to_dev(p), tol=1e-7)
     assert r.status == 0
     ref, it, rho = M.wf_solve(p.d, p.Ndiag, p.mask, p.Pk, tol=1e-10)
     assert rho < 1e-10
     assert rel(r.s.cpu().numpy(), ref) < WF_TOL
+
+
+@pytest.mark.parametrize("H", [256, 512])
+def test_wiener_filter_cluster_and_global_agree(H):
+    """A harder problem (slope -2, k0 = 1/32, 15% masked, noise U[0.02, 0.8]: many cooling levels): the
+    cluster and global-memory solves take the same schedule and reach the same filter."""
+    p = synth.make_problem(H, seed=H + 9, mask_frac=0.15, slope=-2.0, k0=1.0 / 32, sigma2=(0.02, 0.8))
+    dev = to_dev(p)
+    res = {}
+    for mode in ("cluster", "global"):
+        prev = wf.wf_set_large_image_sampler(mode)
+        try:
+            res[mode] = wf.wf_solve_ex(*dev, tol=1e-6, max_iter=20000)
+        finally:
+            wf.wf_set_large_image_sampler(prev)
+    c, g = res["cluster"], res["global"]
+    assert c.status == 0 and g.status == 0
+    assert abs(c.iters - g.iters) <= 8, (c.iters, g.iters)
+    assert rel(c.s.cpu().numpy(), g.s.cpu().numpy()) < 1e-5
+    s = c.s.double().cpu().numpy()
+    assert _residual_fft(s, p) < 2e-6
 
 
 def _residual_fft(s, p):
