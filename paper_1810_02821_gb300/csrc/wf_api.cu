@@ -112,20 +112,25 @@ __global__ void k_prep(const float* __restrict__ d, const float* __restrict__ Nd
 
 // Per-pixel tables ([W][H], x-major so that row threads read consecutive addresses) and the
 // per-mode sample table, in FP64 then rounded once.
+// Pixel tables are x-major, aq[x*H + ty] and dn[x*H + ty], with ty = y, or with perm = P > 0 (the
+// cluster kernels, CTA b holding the rows y = P a + b) ty = (y mod P) H/P + y / P, so that the rows of one
+// CTA are contiguous and its row threads read consecutive addresses.
+__host__ __device__ inline int table_row(int y, int H, int perm) { return perm ? (y % perm) * (H / perm) + y / perm : y; }
+
 __global__ void k_tables(const float* __restrict__ d, const float* __restrict__ Ndiag, const uint8_t* __restrict__ mask,
                          const float* __restrict__ Pk, int H, int W, const wf::Scalars* __restrict__ sc,
-                         float2* __restrict__ aq, float2* __restrict__ dn, float2* __restrict__ fg) {
+                         float2* __restrict__ aq, float2* __restrict__ dn, float2* __restrict__ fg, int perm = 0) {
   if (sc->status != 0) return;
   const double tau = sc->tau;
   const int n = H * W, nm = H * (W / 2 + 1);
   const double inv_n = 1.0 / double(n);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + nm; i += gridDim.x * blockDim.x) {
     if (i < n) {
-      const int y = i / W, x = i % W;
+      const int y = i / W, x = i % W, ty = table_row(y, H, perm);
       float2 a2, d2;
       wf::table_pixel(d[i], Ndiag[i], mask[i] == 0, tau, &a2, &d2);
-      if (aq) aq[x * H + y] = a2;
-      if (dn) dn[x * H + y] = d2;
+      if (aq) aq[x * H + ty] = a2;
+      if (dn) dn[x * H + ty] = d2;
     } else if (fg) {
       const int j = i - n;
       fg[j] = wf::table_mode(Pk[j], tau, inv_n);
@@ -516,7 +521,7 @@ wf_status solve_cluster(const float* d, const float* Ndiag, const uint8_t* mask,
   k_prep<<<1, 1024, 0, st>>>(d, Ndiag, mask, Pk, H, W, o.tau, o.eta, sc);
   WF_CUDA(cudaGetLastError());
   k_tables<<<int((n + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc, nullptr,
-                                                 reinterpret_cast<float2*>(b + o_dn), nullptr);
+                                                 reinterpret_cast<float2*>(b + o_dn), nullptr, H / 64);
   WF_CUDA(cudaGetLastError());
   wf::GBField fd{};
   fd.dn = reinterpret_cast<const float2*>(b + o_dn);
@@ -772,7 +777,8 @@ wf_status wf_sample_ex(const float* d, const float* Ndiag, const uint8_t* mask, 
   auto* fg = reinterpret_cast<float2*>(b + off_fg);
   k_prep<<<1, 1024, 0, st>>>(d, Ndiag, mask, Pk, H, W, o.tau, 0.5, sc);
   WF_CUDA(cudaGetLastError());
-  k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc, aq, nullptr, fg);
+  k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc, aq, nullptr, fg,
+                                                       cluster ? H / 64 : 0);
   WF_CUDA(cudaGetLastError());
   wf::SampleArgs a{};
   a.aq = aq; a.fg = fg; a.sc = sc; a.init_s = o.init_s;
@@ -1263,7 +1269,7 @@ __global__ void k_prep_fields(const wf::BatchItem* __restrict__ items, const int
 // per-field tables (as k_tables), grid-stride over fields x (n + nm)
 __global__ void k_tables_fields(const wf::BatchItem* __restrict__ items, const int* __restrict__ idx,
                                 const wf::GBField* __restrict__ fields, const wf::Scalars* __restrict__ sc, int F,
-                                int H) {
+                                int H, int perm) {
   const long long n = (long long)H * H, nm = (long long)H * (H / 2 + 1), per = n + nm;
   const double inv_n = 1.0 / double(n);
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < per * F;
@@ -1275,11 +1281,11 @@ __global__ void k_tables_fields(const wf::BatchItem* __restrict__ items, const i
     const wf::BatchItem it = items[idx[f]];
     const wf::GBField fd = fields[f];
     if (i < n) {
-      const int y = int(i / H), x = int(i % H);
+      const int y = int(i / H), x = int(i % H), ty = table_row(y, H, perm);
       float2 a2, d2;
       wf::table_pixel(it.d[i], it.Ndiag[i], it.mask[i] == 0, s.tau, &a2, &d2);
-      const_cast<float2*>(fd.aq)[x * H + y] = a2;
-      const_cast<float2*>(fd.dn)[x * H + y] = d2;
+      const_cast<float2*>(fd.aq)[x * H + ty] = a2;
+      const_cast<float2*>(fd.dn)[x * H + ty] = d2;
     } else {
       const long long j = i - n;
       const_cast<float2*>(fd.fg)[j] = wf::table_mode(it.Pk[j], s.tau, inv_n);
@@ -1330,8 +1336,8 @@ wf_status run_chunk(const GBChunk& c, const wf::BatchItem* d_items, wf::BatchRes
   k_prep_fields<<<F, 1024, 0, st>>>(d_items, idx, H, o.tau, o.eta, sc);
   WF_CUDA(cudaGetLastError());
   const long long tab = (long long)F * (size_t(H) * H + size_t(H) * (H / 2 + 1));
-  k_tables_fields<<<int((tab + 255) / 256 < 4096 ? (tab + 255) / 256 : 4096), 256, 0, st>>>(d_items, idx, fields, sc,
-                                                                                           F, H);
+  k_tables_fields<<<int((tab + 255) / 256 < 4096 ? (tab + 255) / 256 : 4096), 256, 0, st>>>(
+      d_items, idx, fields, sc, F, H, c.cluster ? H / 64 : 0);
   WF_CUDA(cudaGetLastError());
   if (c.cluster) {
     wf::CBArgs cb{};

@@ -168,19 +168,20 @@ __device__ __forceinline__ void crow_inv(float2* row, int h, const float2* tw) {
   for (int i = 0; i < 64; ++i) row[R * i + h] = x[i];
 }
 
-// t-draw of global row y on its staged row: t = a + q (q s + sqrt(tau) xi), table aq[x*H + y] =
-// ((1 - w) d, sqrt(w)); Philox stream 0, group y*W/4 + q feeds pixels 4q .. 4q+3 (q = h, h + R, ...)
+// t-draw of global row y on its staged row: t = a + q (q s + sqrt(tau) xi), table aq[x*H + ty] =
+// ((1 - w) d, sqrt(w)) with the CTA-contiguous row index ty = b*64 + a; Philox stream 0, group y*W/4 + q
+// feeds pixels 4q .. 4q+3 (q = h, h + R, ...)
 template <int N>
-__device__ __forceinline__ void ct_draw(float2* row, int y, int h, const float2* __restrict__ aq, float sqrt_tau,
-                                        uint32_t step, uint32_t chain, uint32_t k0, uint32_t k1) {
+__device__ __forceinline__ void ct_draw(float2* row, int y, int ty, int h, const float2* __restrict__ aq,
+                                        float sqrt_tau, uint32_t step, uint32_t chain, uint32_t k0, uint32_t k1) {
   using G = CGeo<N>;
 #pragma unroll 2
   for (int q = h; q < G::W / 4; q += G::R) {
     float z[4];
     normals4(uint32_t(y * (G::W / 4) + q), step, chain, 0u, k0, k1, z);
     float2 p0 = row[2 * q], p1 = row[2 * q + 1];
-    const float2 c0 = WF_LDG(aq + (4 * q) * G::H + y), c1 = WF_LDG(aq + (4 * q + 1) * G::H + y);
-    const float2 c2 = WF_LDG(aq + (4 * q + 2) * G::H + y), c3 = WF_LDG(aq + (4 * q + 3) * G::H + y);
+    const float2 c0 = WF_LDG(aq + (4 * q) * G::H + ty), c1 = WF_LDG(aq + (4 * q + 1) * G::H + ty);
+    const float2 c2 = WF_LDG(aq + (4 * q + 2) * G::H + ty), c3 = WF_LDG(aq + (4 * q + 3) * G::H + ty);
     p0.x = fmaf(c0.y, fmaf(c0.y, p0.x, sqrt_tau * z[0]), c0.x);
     p0.y = fmaf(c1.y, fmaf(c1.y, p0.y, sqrt_tau * z[1]), c1.x);
     p1.x = fmaf(c2.y, fmaf(c2.y, p1.x, sqrt_tau * z[2]), c2.x);
@@ -401,8 +402,8 @@ __device__ __forceinline__ double ccol_p2(cooperative_groups::cluster_group& cl,
   return acc;
 }
 
-// Wiener-filter pixel update of global row y at level lambda: t = d + w (s - d), w = 1 / (1 + lambda tau /
-// N_bar), table dn[x*H + y] = (d, 1/N_bar) ((0, 0) on missing pixels: t = s)
+// Wiener-filter pixel update of a row at level lambda: t = d + w (s - d), w = 1 / (1 + lambda tau / N_bar),
+// table dn[x*H + y] = (d, 1/N_bar) ((0, 0) on missing pixels: t = s), y the CTA-contiguous table row b*64 + a
 template <int N>
 __device__ __forceinline__ void ct_update_wf(float2* row, int y, int h, const float2* __restrict__ dn, float lt_) {
   using G = CGeo<N>;
@@ -421,7 +422,7 @@ template <int N>
 __device__ __forceinline__ void crhs_rows(float2* rows, int b, const float2* __restrict__ dn, float lt_) {
   using G = CGeo<N>;
   for (int e = threadIdx.x; e < G::A * G::L; e += G::L) {
-    const int ar = e / G::L, i = e % G::L, y = G::P * ar + b;
+    const int ar = e / G::L, i = e % G::L, y = b * 64 + ar;  // CTA-contiguous table row
     float2 r;
     const float2 c0 = WF_LDG(dn + (2 * i) * G::H + y), c1 = WF_LDG(dn + (2 * i + 1) * G::H + y);
     const float nb0 = c0.y > 0.0f ? wf_rcp(c0.y) : wf_inf(), nb1 = c1.y > 0.0f ? wf_rcp(c1.y) : wf_inf();
@@ -502,7 +503,7 @@ __device__ __forceinline__ void csample_loop(cooperative_groups::cluster_group& 
   char* out = reinterpret_cast<char*>(out_v);
   for (int done = 0;;) {
     const uint32_t step = step0 + uint32_t(done);
-    ct_draw<N>(row, y, h, aq, sqrt_tau, step, chain, k0, k1);
+    ct_draw<N>(row, y, b * 64 + ar, h, aq, sqrt_tau, step, chain, k0, k1);
     __syncwarp();
     crow_fwd<N>(row, h, tw);
     __syncthreads();
@@ -567,7 +568,7 @@ __device__ __forceinline__ int csolve_loop(cooperative_groups::cluster_group& cl
     ++it;
     const bool cmp = (k % check == 0) && k >= 2;
     const bool store = ((k + 1) % check == 0);
-    ct_update_wf<N>(row, y, h, dn, ltau);
+    ct_update_wf<N>(row, b * 64 + ar, h, dn, ltau);
     __syncwarp();
     crow_fwd<N>(row, h, tw);
     __syncthreads();
