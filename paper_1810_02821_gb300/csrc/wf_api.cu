@@ -521,7 +521,7 @@ wf_status solve_cluster(const float* d, const float* Ndiag, const uint8_t* mask,
   k_prep<<<1, 1024, 0, st>>>(d, Ndiag, mask, Pk, H, W, o.tau, o.eta, sc);
   WF_CUDA(cudaGetLastError());
   k_tables<<<int((n + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc, nullptr,
-                                                 reinterpret_cast<float2*>(b + o_dn), nullptr, H / 64);
+                                                 reinterpret_cast<float2*>(b + o_dn), nullptr, H / wf::cluster_rows(H));
   WF_CUDA(cudaGetLastError());
   wf::GBField fd{};
   fd.dn = reinterpret_cast<const float2*>(b + o_dn);
@@ -778,7 +778,7 @@ wf_status wf_sample_ex(const float* d, const float* Ndiag, const uint8_t* mask, 
   k_prep<<<1, 1024, 0, st>>>(d, Ndiag, mask, Pk, H, W, o.tau, 0.5, sc);
   WF_CUDA(cudaGetLastError());
   k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc, aq, nullptr, fg,
-                                                       cluster ? H / 64 : 0);
+                                                       cluster ? H / wf::cluster_rows(H) : 0);
   WF_CUDA(cudaGetLastError());
   wf::SampleArgs a{};
   a.aq = aq; a.fg = fg; a.sc = sc; a.init_s = o.init_s;
@@ -1337,7 +1337,7 @@ wf_status run_chunk(const GBChunk& c, const wf::BatchItem* d_items, wf::BatchRes
   WF_CUDA(cudaGetLastError());
   const long long tab = (long long)F * (size_t(H) * H + size_t(H) * (H / 2 + 1));
   k_tables_fields<<<int((tab + 255) / 256 < 4096 ? (tab + 255) / 256 : 4096), 256, 0, st>>>(
-      d_items, idx, fields, sc, F, H, c.cluster ? H / 64 : 0);
+      d_items, idx, fields, sc, F, H, c.cluster ? H / wf::cluster_rows(H) : 0);
   WF_CUDA(cudaGetLastError());
   if (c.cluster) {
     wf::CBArgs cb{};

@@ -1,17 +1,18 @@
 // Cluster-resident sampler for 256 x 256 and 512 x 512 images (Alg. 1 of the paper with A = I).
 //
 // A 256^2 field's packed half spectrum (256 KB) does not fit one SM, but it fits the distributed shared
-// memory of a thread-block cluster. One field (one chain) is a cluster of P = N / 64 CTAs of N / 2 threads;
-// CTA b keeps the global rows y = P a + b (a < 64), each row as N / 2 float2 slots, for all sweeps.
+// memory of a thread-block cluster. One field (one chain) is a cluster of P = N / M CTAs of N / 2 threads
+// (M = 64 rows per CTA at 256^2, 32 at 512^2); CTA b keeps the global rows y = P a + b (a < M), each row
+// as N / 2 float2 slots, for all sweeps.
 //
-// Row transforms (length L = N / 2 complex, real-to-complex packing) stay inside a CTA: the R = L / 64
-// threads of a row (neighbouring lanes of one warp) each run a 64-point register FFT over every R-th slot,
-// then radix-R butterflies across them, with the real-transform pre/post pass of the mode pairs
-// (K, L - K) fused into the butterflies. The half spectrum of a row is kept in digit-reversed slot
-// order, X[K] at slot R (K mod 64) + K / 64, which the column pass simply follows.
+// Row transforms (length L = N / 2 complex, real-to-complex packing) stay inside a CTA: the R = L / M
+// threads of a row (lanes of one warp) each run an M-point register FFT over every R-th slot, then
+// radix-R butterflies across them, with the real-transform pre/post pass of the mode pairs (K, L - K)
+// fused into the butterflies. The half spectrum of a row is kept in digit-reversed slot order, X[K] at
+// slot R (K mod M) + K / M, which the column pass simply follows.
 //
 // Column transforms (length N) are split over the cluster by decimation in time over the CTA rank:
-// each CTA runs a 64-point register FFT down every column of its rows (twiddled by W_N^(b k')), then one
+// each CTA runs an M-point register FFT down every column of its rows (twiddled by W_N^(b k')), then one
 // radix-P stage combines the P partial transforms through distributed shared memory; the s-draw happens
 // right there, on the complete column spectrum, followed by the inverse radix-P stage, the inverse twiddle
 // and the local inverse FFTs. Two cluster barriers per sweep (hardware barriers, no spin waits).
@@ -25,17 +26,25 @@
 
 namespace wf {
 
+// rows per CTA (the local transform length): 64 at 256^2 (clusters of 4 CTAs, 3 per SM); 32 at 512^2
+// (clusters of 16 CTAs of 66 KB, 2 per SM, instead of 8 CTAs of 130 KB, 1 per SM)
+#ifndef WF_CLUSTER_ROWS_512
+#define WF_CLUSTER_ROWS_512 32
+#endif
+__host__ __device__ constexpr int cluster_rows(int N) { return N == 512 ? WF_CLUSTER_ROWS_512 : 64; }
+
 template <int N_>
 struct CGeo {
   static constexpr int N = N_, H = N_, W = N_;
-  static constexpr int P = N / 64;   // CTAs per cluster
-  static constexpr int A = 64;       // rows per CTA
-  static constexpr int L = N / 2;    // complex length of a row transform = threads per CTA
-  static constexpr int R = L / 64;   // threads per row in the row passes
+  static constexpr int M = cluster_rows(N_);  // rows per CTA = local transform length
+  static constexpr int A = M;
+  static constexpr int P = N / M;             // CTAs per cluster
+  static constexpr int L = N / 2;             // complex length of a row transform = threads per CTA
+  static constexpr int R = L / M;             // threads per row in the row passes
   // float2 stride of a row: with the row-major lane map below (the R threads of a row are lanes
   // a, a + 32/R, ...), a half-warp's accesses in the row passes hit distinct banks (R = 2) or at most two
-  // per bank (R = 4)
-  static constexpr int SP = L + R / 2;
+  // per bank (R = 4, 8)
+  static constexpr int SP = L + ilog2(R);
   static constexpr int ROWS_BYTES = A * SP * 8;
   static constexpr int SMEM = ROWS_BYTES + N * 8 + (33 + 16 + kMaxLevels) * 8;  // rows, twiddles, FP64 sums, level norms
   static constexpr int WH = W / 2 + 1;
@@ -78,39 +87,39 @@ __device__ __forceinline__ void crow_fwd(float2* row, int h, const float2* tw) {
   using G = CGeo<N>;
   constexpr int R = G::R;
   {
-    float2 x[64];
+    float2 x[G::M];
 #pragma unroll
-    for (int i = 0; i < 64; ++i) x[i] = row[R * i + h];
-    fft<64, false>(x);
+    for (int i = 0; i < G::M; ++i) x[i] = row[R * i + h];
+    fft<G::M, false>(x);
 #pragma unroll
-    for (int k = 0; k < 64; ++k) row[R * k + h] = k == 0 ? x[0] : cmul(x[k], tw[2 * h * k]);  // W_L^(h k)
+    for (int k = 0; k < G::M; ++k) row[R * k + h] = k == 0 ? x[0] : cmul(x[k], tw[2 * h * k]);  // W_L^(h k)
   }
   __syncwarp();
-  for (int u = h; u <= 32; u += R) {  // butterfly unit k' = u with its mirror v = 64 - u
-    const int v = 64 - u;
-    const bool two = u != 0 && u != 32;
+  for (int u = h; u <= G::M / 2; u += R) {  // butterfly unit k' = u with its mirror v = M - u
+    const int v = G::M - u;
+    const bool two = u != 0 && u != G::M / 2;
     float2 p[R], q[R];
 #pragma unroll
     for (int j = 0; j < R; ++j) p[j] = row[R * u + j];
-    fft<R, false>(p);  // p[m] = C[u + 64 m]
+    fft<R, false>(p);  // p[m] = C[u + M m]
     if (two) {
 #pragma unroll
       for (int j = 0; j < R; ++j) q[j] = row[R * v + j];
-      fft<R, false>(q);  // q[m] = C[v + 64 m]
+      fft<R, false>(q);  // q[m] = C[v + M m]
     }
     if (u == 0) {
       p[0] = make_float2(p[0].x + p[0].y, p[0].x - p[0].y);  // (R[0], R[L])
 #pragma unroll
       for (int m = 1; m < R; ++m) {
         if (2 * m == R) p[m] = cconj(p[m]);
-        else if (m < R - m) c_r2c_pair(p[m], p[R - m], tw[64 * m]);
+        else if (m < R - m) c_r2c_pair(p[m], p[R - m], tw[G::M * m]);
       }
-    } else if (u == 32) {
+    } else if (u == G::M / 2) {
 #pragma unroll
-      for (int m = 0; m < R / 2; ++m) c_r2c_pair(p[m], p[R - 1 - m], tw[32 + 64 * m]);
+      for (int m = 0; m < R / 2; ++m) c_r2c_pair(p[m], p[R - 1 - m], tw[G::M / 2 + G::M * m]);
     } else {
 #pragma unroll
-      for (int m = 0; m < R; ++m) c_r2c_pair(p[m], q[R - 1 - m], tw[u + 64 * m]);
+      for (int m = 0; m < R; ++m) c_r2c_pair(p[m], q[R - 1 - m], tw[u + G::M * m]);
     }
 #pragma unroll
     for (int m = 0; m < R; ++m) row[R * u + m] = p[m];
@@ -126,9 +135,9 @@ template <int N>
 __device__ __forceinline__ void crow_inv(float2* row, int h, const float2* tw) {
   using G = CGeo<N>;
   constexpr int R = G::R;
-  for (int u = h; u <= 32; u += R) {
-    const int v = 64 - u;
-    const bool two = u != 0 && u != 32;
+  for (int u = h; u <= G::M / 2; u += R) {
+    const int v = G::M - u;
+    const bool two = u != 0 && u != G::M / 2;
     float2 p[R], q[R];
 #pragma unroll
     for (int m = 0; m < R; ++m) p[m] = row[R * u + m];
@@ -141,16 +150,16 @@ __device__ __forceinline__ void crow_inv(float2* row, int h, const float2* tw) {
 #pragma unroll
       for (int m = 1; m < R; ++m) {
         if (2 * m == R) p[m] = cscale(cconj(p[m]), 2.0f);
-        else if (m < R - m) c_c2r_pair(p[m], p[R - m], tw[64 * m]);
+        else if (m < R - m) c_c2r_pair(p[m], p[R - m], tw[G::M * m]);
       }
-    } else if (u == 32) {
+    } else if (u == G::M / 2) {
 #pragma unroll
-      for (int m = 0; m < R / 2; ++m) c_c2r_pair(p[m], p[R - 1 - m], tw[32 + 64 * m]);
+      for (int m = 0; m < R / 2; ++m) c_c2r_pair(p[m], p[R - 1 - m], tw[G::M / 2 + G::M * m]);
     } else {
 #pragma unroll
-      for (int m = 0; m < R; ++m) c_c2r_pair(p[m], q[R - 1 - m], tw[u + 64 * m]);
+      for (int m = 0; m < R; ++m) c_c2r_pair(p[m], q[R - 1 - m], tw[u + G::M * m]);
     }
-    fft<R, true>(p);  // p[j] = sum_m exp(+2 pi i j m / R) C'[u + 64 m]
+    fft<R, true>(p);  // p[j] = sum_m exp(+2 pi i j m / R) C'[u + M m]
 #pragma unroll
     for (int j = 0; j < R; ++j) row[R * u + j] = j == 0 ? p[0] : cmul(p[j], cconj(tw[2 * j * u]));
     if (two) {
@@ -160,16 +169,16 @@ __device__ __forceinline__ void crow_inv(float2* row, int h, const float2* tw) {
     }
   }
   __syncwarp();
-  float2 x[64];
+  float2 x[G::M];
 #pragma unroll
-  for (int k = 0; k < 64; ++k) x[k] = row[R * k + h];
-  fft<64, true>(x);
+  for (int k = 0; k < G::M; ++k) x[k] = row[R * k + h];
+  fft<G::M, true>(x);
 #pragma unroll
-  for (int i = 0; i < 64; ++i) row[R * i + h] = x[i];
+  for (int i = 0; i < G::M; ++i) row[R * i + h] = x[i];
 }
 
 // t-draw of global row y on its staged row: t = a + q (q s + sqrt(tau) xi), table aq[x*H + ty] =
-// ((1 - w) d, sqrt(w)) with the CTA-contiguous row index ty = b*64 + a; Philox stream 0, group y*W/4 + q
+// ((1 - w) d, sqrt(w)) with the CTA-contiguous row index ty = b*M + a; Philox stream 0, group y*W/4 + q
 // feeds pixels 4q .. 4q+3 (q = h, h + R, ...)
 template <int N>
 __device__ __forceinline__ void ct_draw(float2* row, int y, int ty, int h, const float2* __restrict__ aq,
@@ -194,30 +203,30 @@ __device__ __forceinline__ void ct_draw(float2* row, int y, int ty, int h, const
 // ---------------------------------------------------------------------------------------------
 // column passes
 // ---------------------------------------------------------------------------------------------
-// local forward: 64-point FFT down slot t of this CTA's rows, output k' twiddled by W_N^(b k')
+// local forward: M-point FFT down slot t of this CTA's rows, output k' twiddled by W_N^(b k')
 template <int N>
 __device__ __forceinline__ void ccol_fwd(float2* rows, int t, int b, const float2* tw) {
   using G = CGeo<N>;
-  float2 x[64];
+  float2 x[G::M];
 #pragma unroll
-  for (int a = 0; a < 64; ++a) x[a] = rows[a * G::SP + t];
-  fft<64, false>(x);
+  for (int a = 0; a < G::M; ++a) x[a] = rows[a * G::SP + t];
+  fft<G::M, false>(x);
 #pragma unroll
-  for (int k = 0; k < 64; ++k) rows[k * G::SP + t] = k == 0 ? x[0] : cmul(x[k], tw[b * k]);
+  for (int k = 0; k < G::M; ++k) rows[k * G::SP + t] = k == 0 ? x[0] : cmul(x[k], tw[b * k]);
 }
-// local inverse: untwiddle by W_N^(-b k'), inverse 64-point FFT back to the rows
+// local inverse: untwiddle by W_N^(-b k'), inverse M-point FFT back to the rows
 template <int N>
 __device__ __forceinline__ void ccol_inv(float2* rows, int t, int b, const float2* tw) {
   using G = CGeo<N>;
-  float2 x[64];
+  float2 x[G::M];
 #pragma unroll
-  for (int k = 0; k < 64; ++k) {
+  for (int k = 0; k < G::M; ++k) {
     const float2 v = rows[k * G::SP + t];
     x[k] = k == 0 ? v : cmul(v, cconj(tw[b * k]));
   }
-  fft<64, true>(x);
+  fft<G::M, true>(x);
 #pragma unroll
-  for (int a = 0; a < 64; ++a) rows[a * G::SP + t] = x[a];
+  for (int a = 0; a < G::M; ++a) rows[a * G::SP + t] = x[a];
 }
 
 // One mode pair (ky1, ky2 = N - ky1, or N/2 when ky1 = 0) of packed column slot t (kx = K) with the
@@ -255,8 +264,8 @@ __device__ __forceinline__ void cdraw_pair(float2& y1, float2& y2, int K, int ky
   }
 }
 
-// Cross-cluster radix-P stage. Work unit (slot t, k' = u with its mirror v = 64 - u): gathers Y_j[u]
-// (and Y_j[v]) from every CTA j, forms the column spectrum t_hat[u + 64 m], hands every mode pair
+// Cross-cluster radix-P stage. Work unit (slot t, k' = u with its mirror v = M - u): gathers Y_j[u]
+// (and Y_j[v]) from every CTA j, forms the column spectrum t_hat[u + M m], hands every mode pair
 // (ky1 < N/2, ky2 = N - ky1, or N/2 when ky1 = 0) of column K to fn(K, y1, y2, ky1, ky2), and with WRITE
 // scatters the inverse stage back. g = the thread's index in the cluster. Every mode of the half spectrum
 // is in exactly one pair of one unit.
@@ -264,10 +273,11 @@ template <int N, bool WRITE, class F>
 __device__ __forceinline__ void ccol_units(cooperative_groups::cluster_group& cl, float2* rows, int g, F&& fn) {
   using G = CGeo<N>;
   constexpr int P = G::P, L = G::L, R = G::R;
-  for (int w = g; w < L * 33; w += P * L) {
-    const int t = w % L, u = w / L, v = 64 - u;
-    const int K = (t % R) * 64 + t / R;  // kx held by slot t
-    const bool two = u != 0 && u != 32;
+  constexpr int M = G::M;
+  for (int w = g; w < L * (M / 2 + 1); w += P * L) {
+    const int t = w % L, u = w / L, v = M - u;
+    const int K = (t % R) * M + t / R;  // kx held by slot t
+    const bool two = u != 0 && u != M / 2;
     float2 p[P], q[P];
 #pragma unroll
     for (int j = 0; j < P; ++j) p[j] = cl.map_shared_rank(rows, j)[u * G::SP + t];
@@ -275,20 +285,20 @@ __device__ __forceinline__ void ccol_units(cooperative_groups::cluster_group& cl
 #pragma unroll
       for (int j = 0; j < P; ++j) q[j] = cl.map_shared_rank(rows, j)[v * G::SP + t];
     }
-    fft<P, false>(p);  // p[m] = t_hat[u + 64 m]
+    fft<P, false>(p);  // p[m] = t_hat[u + M m]
     if (u == 0) {
       fn(K, p[0], p[P / 2], 0, N / 2);
 #pragma unroll
-      for (int m = 1; m < P / 2; ++m) fn(K, p[m], p[P - m], 64 * m, N - 64 * m);
-    } else if (u == 32) {
+      for (int m = 1; m < P / 2; ++m) fn(K, p[m], p[P - m], M * m, N - M * m);
+    } else if (u == M / 2) {
 #pragma unroll
-      for (int m = 0; m < P / 2; ++m) fn(K, p[m], p[P - 1 - m], 32 + 64 * m, N - 32 - 64 * m);
+      for (int m = 0; m < P / 2; ++m) fn(K, p[m], p[P - 1 - m], M / 2 + M * m, N - M / 2 - M * m);
     } else {
-      fft<P, false>(q);  // q[m] = t_hat[v + 64 m]
+      fft<P, false>(q);  // q[m] = t_hat[v + M m]
 #pragma unroll
       for (int m = 0; m < P / 2; ++m) {
-        fn(K, p[m], q[P - 1 - m], u + 64 * m, N - u - 64 * m);
-        fn(K, q[m], p[P - 1 - m], v + 64 * m, N - v - 64 * m);
+        fn(K, p[m], q[P - 1 - m], u + M * m, N - u - M * m);
+        fn(K, q[m], p[P - 1 - m], v + M * m, N - v - M * m);
       }
       if (WRITE) {
         fft<P, true>(q);
@@ -403,7 +413,7 @@ __device__ __forceinline__ double ccol_p2(cooperative_groups::cluster_group& cl,
 }
 
 // Wiener-filter pixel update of a row at level lambda: t = d + w (s - d), w = 1 / (1 + lambda tau / N_bar),
-// table dn[x*H + y] = (d, 1/N_bar) ((0, 0) on missing pixels: t = s), y the CTA-contiguous table row b*64 + a
+// table dn[x*H + y] = (d, 1/N_bar) ((0, 0) on missing pixels: t = s), y the CTA-contiguous table row b*M + a
 template <int N>
 __device__ __forceinline__ void ct_update_wf(float2* row, int y, int h, const float2* __restrict__ dn, float lt_) {
   using G = CGeo<N>;
@@ -422,7 +432,7 @@ template <int N>
 __device__ __forceinline__ void crhs_rows(float2* rows, int b, const float2* __restrict__ dn, float lt_) {
   using G = CGeo<N>;
   for (int e = threadIdx.x; e < G::A * G::L; e += G::L) {
-    const int ar = e / G::L, i = e % G::L, y = b * 64 + ar;  // CTA-contiguous table row
+    const int ar = e / G::L, i = e % G::L, y = b * G::M + ar;  // CTA-contiguous table row
     float2 r;
     const float2 c0 = WF_LDG(dn + (2 * i) * G::H + y), c1 = WF_LDG(dn + (2 * i + 1) * G::H + y);
     const float nb0 = c0.y > 0.0f ? wf_rcp(c0.y) : wf_inf(), nb1 = c1.y > 0.0f ? wf_rcp(c1.y) : wf_inf();
@@ -452,7 +462,7 @@ __device__ __forceinline__ double cluster_sum(cooperative_groups::cluster_group&
 // kernels
 // ---------------------------------------------------------------------------------------------
 template <int N>
-constexpr int csample_min_ctas() { return N == 256 ? 3 : 1; }
+constexpr int csample_min_ctas() { return CGeo<N>::L <= 128 ? 3 : (CGeo<N>::M <= 32 ? 2 : 1); }
 
 // twiddles exp(-2 pi i j / N) (FP64, rounded once) into shared memory
 template <int N>
@@ -503,7 +513,7 @@ __device__ __forceinline__ void csample_loop(cooperative_groups::cluster_group& 
   char* out = reinterpret_cast<char*>(out_v);
   for (int done = 0;;) {
     const uint32_t step = step0 + uint32_t(done);
-    ct_draw<N>(row, y, b * 64 + ar, h, aq, sqrt_tau, step, chain, k0, k1);
+    ct_draw<N>(row, y, b * G::M + ar, h, aq, sqrt_tau, step, chain, k0, k1);
     __syncwarp();
     crow_fwd<N>(row, h, tw);
     __syncthreads();
@@ -568,7 +578,7 @@ __device__ __forceinline__ int csolve_loop(cooperative_groups::cluster_group& cl
     ++it;
     const bool cmp = (k % check == 0) && k >= 2;
     const bool store = ((k + 1) % check == 0);
-    ct_update_wf<N>(row, b * 64 + ar, h, dn, ltau);
+    ct_update_wf<N>(row, b * G::M + ar, h, dn, ltau);
     __syncwarp();
     crow_fwd<N>(row, h, tw);
     __syncthreads();

@@ -226,6 +226,12 @@ cudaError_t csample_config(cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr, i
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_cpipe<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
   if (e != cudaSuccess) return e;
+  if (G::P > 8) {  // clusters above the portable size of 8
+    e = cudaFuncSetAttribute(k_csample<N>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_cpipe<N>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = G::P;
   attr[0].val.clusterDim.y = 1;
