@@ -596,6 +596,29 @@ WF_HD void t_draw_staged(float* stg, int y, const float2* __restrict__ aq, float
   }
 }
 
+// Wiener-filter t-update (as t_update_wf) of the staged row y, rolled over groups of four pixels: the
+// row's registers are dead meanwhile, so more table loads can be in flight
+template <int N>
+WF_HD void t_update_wf_staged(float* stg, int y, const float2* __restrict__ dn, float lt_, bool rhs) {
+  using G = Geo<N>;
+  float2* row = reinterpret_cast<float2*>(stg) + y * G::SP;
+  const float g = rhs ? 0.0f : 1.0f, h = rhs ? lt_ : 1.0f;
+#pragma unroll (kRngUnroll)
+  for (int q = 0; q < G::W / 4; ++q) {
+    float2 p0 = row[2 * q], p1 = row[2 * q + 1];
+    const float2 c0 = WF_LDG(dn + (4 * q) * G::H + y), c1 = WF_LDG(dn + (4 * q + 1) * G::H + y);
+    const float2 c2 = WF_LDG(dn + (4 * q + 2) * G::H + y), c3 = WF_LDG(dn + (4 * q + 3) * G::H + y);
+    const float w0 = wf_rcp(fmaf(lt_, c0.y, 1.0f)), w1 = wf_rcp(fmaf(lt_, c1.y, 1.0f));
+    const float w2 = wf_rcp(fmaf(lt_, c2.y, 1.0f)), w3 = wf_rcp(fmaf(lt_, c3.y, 1.0f));
+    p0.x = fmaf(w0, fmaf(-g, c0.x, p0.x), h * c0.x);
+    p0.y = fmaf(w1, fmaf(-g, c1.x, p0.y), h * c1.x);
+    p1.x = fmaf(w2, fmaf(-g, c2.x, p1.x), h * c2.x);
+    p1.y = fmaf(w3, fmaf(-g, c3.x, p1.y), h * c3.x);
+    row[2 * q] = p0;
+    row[2 * q + 1] = p1;
+  }
+}
+
 template <int N>
 WF_HD void load_staged_row(const float* stg, int y, float2 (&c)[N / 2]) {
   using G = Geo<N>;
@@ -1141,7 +1164,14 @@ __device__ __forceinline__ int solve_sweeps(float2* S, double* red, int lt, floa
   double lam = sc.lam0;
   float ltau = float(lam * tau);
   const int last_level = sc.n_levels - 1;
-  t_update_wf<N>(c, lt, dn, ltau, rhs);
+  // t-update on the thread's own staged row (the spectrum row it stores to next)
+  float* stg = reinterpret_cast<float*>(S);
+  auto t_update = [&](float lt_) {
+    stage_row<N>(stg, lt, c);
+    t_update_wf_staged<N>(stg, lt, dn, lt_, rhs);
+    load_staged_row<N>(stg, lt, c);
+  };
+  t_update(ltau);
   row_forward<N>(c);
   row_store_spec<N>(S, lt, c);
   __syncthreads();
@@ -1188,7 +1218,7 @@ __device__ __forceinline__ int solve_sweeps(float2* S, double* red, int lt, floa
     __syncthreads();
     row_inverse<N>(c);
     if (status != 1) break;
-    t_update_wf<N>(c, lt, dn, ltau, rhs);
+    t_update(ltau);
     row_forward<N>(c);
     row_store_spec<N>(S, lt, c);
     __syncthreads();
