@@ -369,78 +369,6 @@ WF_HD void rhs_row(float2 (&c)[N / 2], int y, const float2* __restrict__ dn, flo
 // ---------------------------------------------------------------------------------------------
 // Fourier-space updates (Alg. 1 s-update) on the modes held by a column thread
 // ---------------------------------------------------------------------------------------------
-// Wiener-filter mode at level lambda: s_hat = f t_hat with f = P/(P + lambda tau) (scaled by 1/n).
-// With STORE the result is written to prev[ky*LR + col]; with CMP the residual of the previous iterate,
-// |r_k| = |s_hat_new - s_hat_old| / (1 - f), is accumulated over the full spectrum (returned, scaled 1/n).
-template <int N, bool CMP, bool STORE>
-WF_HD double s_update_wf(float2 (&x)[N / 2], int lt, const float* __restrict__ Pk, float lt_,
-                                              float2* __restrict__ prev) {
-  using G = Geo<N>;
-  constexpr int WH = G::WH;
-  constexpr float INV_N = 1.0f / float(G::H * G::W);
-  const int col = lt % G::LC, r = lt / G::LC;
-  double acc = 0.0;
-  // |d|^2 / (1 - f_true)^2 with 1/(1 - f_true) = (P + lambda tau) / (lambda tau) = 1 + P / (lambda tau):
-  // per-mode terms in FP32 (a residual estimate needs a few digits), summed in FP64
-  const float inv_lt = 1.0f / lt_;
-  auto wres = [&](float P, float dre, float dim) -> double {
-    const float g = fmaf(P, inv_lt, 1.0f);
-    return double(fmaf(dre, dre, dim * dim) * (g * g));
-  };
-  auto fcoef = [&](float P) { return wf_fdiv(P, P + lt_) * INV_N; };
-  for_mode_pairs<N>(r, [&](auto KP, auto KQ, int ky1, int ky2, auto ZG) {
-    constexpr int kp = decltype(KP)::value, kq = decltype(KQ)::value;
-    constexpr bool zero_group = decltype(ZG)::value != 0;
-    if (col != 0) {
-      const float P1 = WF_LDG(Pk + ky1 * WH + col), P2 = WF_LDG(Pk + ky2 * WH + col);
-      const float f1 = fcoef(P1), f2 = fcoef(P2);
-      const float2 n1 = cscale(x[kp], f1), n2 = cscale(x[kq], f2);
-      if constexpr (CMP) {
-        const float2 o1 = prev[ky1 * G::LR + col], o2 = prev[ky2 * G::LR + col];
-        acc += 2.0 * (wres(P1, n1.x - o1.x, n1.y - o1.y) + wres(P2, n2.x - o2.x, n2.y - o2.y));
-      }
-      x[kp] = n1;
-      x[kq] = n2;
-    } else {
-      const float Pa1 = WF_LDG(Pk + ky1 * WH), Pb1 = WF_LDG(Pk + ky1 * WH + G::W / 2);
-      const float Pa2 = WF_LDG(Pk + ky2 * WH), Pb2 = WF_LDG(Pk + ky2 * WH + G::W / 2);
-      const float fa1 = fcoef(Pa1), fb1 = fcoef(Pb1);
-      const float fa2 = fcoef(Pa2), fb2 = fcoef(Pb2);
-      if constexpr (zero_group) {
-        const float2 n1 = make_float2(fa1 * x[kp].x, fb1 * x[kp].y);
-        const float2 n2 = make_float2(fa2 * x[kq].x, fb2 * x[kq].y);
-        if constexpr (CMP) {
-          const float2 o1 = prev[ky1 * G::LR], o2 = prev[ky2 * G::LR];
-          acc += wres(Pa1, n1.x - o1.x, 0.f) + wres(Pb1, n1.y - o1.y, 0.f) + wres(Pa2, n2.x - o2.x, 0.f) +
-                 wres(Pb2, n2.y - o2.y, 0.f);
-        }
-        x[kp] = n1;
-        x[kq] = n2;
-      } else {
-        const float2 y1 = x[kp], y2c = cconj(x[kq]);
-        const float2 A = cscale(cscale(cadd(y1, y2c), 0.5f), fa1);
-        const float2 B = cscale(cmul_mi(cscale(csub(y1, y2c), 0.5f)), fb1);
-        const float2 n1 = cadd(A, cmul_i(B));
-        const float2 n2 = cadd(cconj(A), cmul_i(cconj(B)));
-        if constexpr (CMP) {
-          const float2 o1 = prev[ky1 * G::LR], o2c = cconj(prev[ky2 * G::LR]);
-          const float2 oA = cscale(cadd(o1, o2c), 0.5f);
-          const float2 oB = cmul_mi(cscale(csub(o1, o2c), 0.5f));
-          // modes ky1 and H - ky1 of each edge column have equal magnitude: weight 2
-          acc += 2.0 * (wres(Pa1, A.x - oA.x, A.y - oA.y) + wres(Pb1, B.x - oB.x, B.y - oB.y));
-        }
-        x[kp] = n1;
-        x[kq] = n2;
-      }
-    }
-    if constexpr (STORE) {
-      prev[ky1 * G::LR + col] = x[kp];
-      prev[ky2 * G::LR + col] = x[kq];
-    }
-  });
-  return acc;
-}
-
 // sum over the full spectrum of P^2 |V|^2 for the forward transform V held by this thread
 // (edge columns separated into kx = 0 and kx = W/2)
 template <int N>
@@ -654,6 +582,79 @@ WF_HD void mode_pair(int r, int kp, int& kq, int& ky1, int& ky2) {
   kq = r == 0 ? (kp == 0 ? G::LC / 2 : G::LC - kp) : G::LC - 1 - kp;
   ky1 = 2 * kp + r;
   ky2 = r == 0 ? (kp == 0 ? G::H / 2 : G::H - 2 * kp) : G::H - 2 * kp - 1;
+}
+
+// Wiener-filter s-update at level lambda on the thread's parked modes (park_modes): s_hat = f t_hat with
+// f = P/(P + lambda tau) (scaled by 1/n), rolled over the thread's mode pairs (the column registers are dead
+// meanwhile, so more Pk / prev loads are in flight; each thread touches only its own parked slots, the
+// packed edge column included). With CMP the residual of the previous iterate, |r_k| = |s_hat_new -
+// s_hat_old| / (1 - f), is accumulated over the full spectrum (returned, scaled 1/n): per-mode terms in
+// FP32 (a residual estimate needs a few digits), summed in FP64. With STORE the new modes go to
+// prev[ky*LR + col].
+template <int N>
+WF_HD double s_update_wf_parked(float2* cs, int lt, const float* __restrict__ Pk, float lt_,
+                                float2* __restrict__ prev, bool CMP, bool STORE) {
+  using G = Geo<N>;
+  constexpr int WH = G::WH, LC = G::LC;
+  constexpr float INV_N = 1.0f / float(G::H * G::W);
+  const int col = lt % LC, r = lt / LC;
+  double acc = 0.0;
+  const float inv_lt = 1.0f / lt_;
+  auto wres = [&](float P, float dre, float dim) -> double {
+    const float g = fmaf(P, inv_lt, 1.0f);
+    return double(fmaf(dre, dre, dim * dim) * (g * g));
+  };
+  auto fcoef = [&](float P) { return wf_fdiv(P, P + lt_) * INV_N; };
+#pragma unroll 4
+  for (int kp = 0; kp < LC / 2; ++kp) {
+    int kq, ky1, ky2;
+    mode_pair<N>(r, kp, kq, ky1, ky2);
+    const int i1 = park_index<N>(lt, kp), i2 = park_index<N>(lt, kq);
+    const float2 x1 = cs[i1], x2 = cs[i2];
+    float2 n1, n2;
+    if (col != 0) {
+      const float P1 = WF_LDG(Pk + ky1 * WH + col), P2 = WF_LDG(Pk + ky2 * WH + col);
+      n1 = cscale(x1, fcoef(P1));
+      n2 = cscale(x2, fcoef(P2));
+      if (CMP) {
+        const float2 o1 = prev[ky1 * G::LR + col], o2 = prev[ky2 * G::LR + col];
+        acc += 2.0 * (wres(P1, n1.x - o1.x, n1.y - o1.y) + wres(P2, n2.x - o2.x, n2.y - o2.y));
+      }
+    } else {
+      const float Pa1 = WF_LDG(Pk + ky1 * WH), Pb1 = WF_LDG(Pk + ky1 * WH + G::W / 2);
+      const float fa1 = fcoef(Pa1), fb1 = fcoef(Pb1);
+      if (r == 0 && kp == 0) {  // the four self-conjugate modes
+        const float Pa2 = WF_LDG(Pk + ky2 * WH), Pb2 = WF_LDG(Pk + ky2 * WH + G::W / 2);
+        n1 = make_float2(fa1 * x1.x, fb1 * x1.y);
+        n2 = make_float2(fcoef(Pa2) * x2.x, fcoef(Pb2) * x2.y);
+        if (CMP) {
+          const float2 o1 = prev[ky1 * G::LR], o2 = prev[ky2 * G::LR];
+          acc += wres(Pa1, n1.x - o1.x, 0.f) + wres(Pb1, n1.y - o1.y, 0.f) + wres(Pa2, n2.x - o2.x, 0.f) +
+                 wres(Pb2, n2.y - o2.y, 0.f);
+        }
+      } else {
+        const float2 y2c = cconj(x2);
+        const float2 A = cscale(cscale(cadd(x1, y2c), 0.5f), fa1);
+        const float2 B = cscale(cmul_mi(cscale(csub(x1, y2c), 0.5f)), fb1);
+        n1 = cadd(A, cmul_i(B));
+        n2 = cadd(cconj(A), cmul_i(cconj(B)));
+        if (CMP) {
+          const float2 o1 = prev[ky1 * G::LR], o2c = cconj(prev[ky2 * G::LR]);
+          const float2 oA = cscale(cadd(o1, o2c), 0.5f);
+          const float2 oB = cmul_mi(cscale(csub(o1, o2c), 0.5f));
+          // modes ky1 and H - ky1 of each edge column have equal magnitude: weight 2
+          acc += 2.0 * (wres(Pa1, A.x - oA.x, A.y - oA.y) + wres(Pb1, B.x - oB.x, B.y - oB.y));
+        }
+      }
+    }
+    cs[i1] = n1;
+    cs[i2] = n2;
+    if (STORE) {
+      prev[ky1 * G::LR + col] = n1;
+      prev[ky2 * G::LR + col] = n2;
+    }
+  }
+  return acc;
 }
 
 // Mode coefficients (f/n, g/sqrt(2n)) of the s-draw. TableCoef reads the per-call table; BandCoef (the
@@ -1188,11 +1189,10 @@ __device__ __forceinline__ int solve_sweeps(float2* S, double* red, int lt, floa
     col_load<N>(S, lt, c);
     __syncthreads();
     fft<G::LC, false>(c);
-    double acc;
-    if (cmp && store) acc = s_update_wf<N, true, true>(c, lt, Pk, ltau, prev);
-    else if (cmp) acc = s_update_wf<N, true, false>(c, lt, Pk, ltau, prev);
-    else if (store) acc = s_update_wf<N, false, true>(c, lt, Pk, ltau, prev);
-    else acc = s_update_wf<N, false, false>(c, lt, Pk, ltau, prev);
+    // s-update on the parked modes (the slots this thread stores to after the inverse transform)
+    park_modes<N>(S, lt, c);
+    const double acc = s_update_wf_parked<N>(S, lt, Pk, ltau, prev, cmp, store);
+    unpark_modes<N>(S, lt, c);
     if (cmp) {
       const double tot = block_sum(acc, red) * double(G::H * G::W);
       const double bn = bnorm2[lev];

@@ -368,7 +368,7 @@ __device__ __forceinline__ double col_update(int mode, float2* buf, int c0, cons
         }
       }
     } else if (mode == 1) {
-      // per-mode residual terms in FP32, summed in FP64 (see s_update_wf)
+      // per-mode residual terms in FP32, summed in FP64 (as s_update_wf_parked)
       const float inv_lt = 1.0f / ltau;
       auto wres = [&](float P, float dre, float dim) -> double {
         const float g = fmaf(P, inv_lt, 1.0f);
