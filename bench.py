@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the plain, single-chain and batch measurements")
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed-size batch measurement")
+    ap.add_argument("--large-path", choices=("cluster", "global"), default="cluster",
+                    help="256x256 / 512x512 kernels outside the large-image comparison: thread-block clusters "
+                         "(default) or the global-memory kernels")
     ap.add_argument("--large-chains", type=int, default=456,
                     help="chains of the 256x256 large-image sampler measurement (512x512: a third)")
     ap.add_argument("--large-samples", type=int, default=20,
@@ -523,6 +526,7 @@ def main():
     build.build()
     wf.load_library()
     wf.wf_set_kernel_timing(True)
+    wf.wf_set_large_image_sampler(a.large_path)
     dev = torch.device("cuda", local)
     p = synth.config_paper128(0)
     host = [torch.from_numpy(x) for x in (p.d, p.Ndiag, p.mask, p.Pk)]
