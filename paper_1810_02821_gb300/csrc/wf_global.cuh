@@ -5,9 +5,9 @@
 // sweep as two phases separated by a bounded grid barrier:
 //   row phase    (CTA = RB rows of one field): Z rows -> C2R -> s -> [sample write] -> t-draw -> R2C -> Z
 //   column phase (CTA = CB columns of one field): Z columns -> FFT -> s-draw -> inverse FFT -> Z
-// (Alg. 1 of the paper with A = I). Each 1D transform of length L = R * 64 runs in shared memory as
-// R-point register DFTs on the 64 strided subsequences with twiddles W_L^(q n), then 64-point register
-// FFTs (decimation in frequency), with 1 float2 of padding per 64 to keep the strided accesses
+// (Alg. 1 of the paper with A = I). Each 1D transform of length L = R * S (S = 64, or 32 at 1024^2) runs
+// in shared memory as R-point register DFTs on the S strided subsequences with twiddles W_L^(q n), then
+// S-point register FFTs (decimation in frequency), with 1 float2 of padding per 64 to keep the strided accesses
 // conflict-free. Every CTA uses 128 threads and 66,560 bytes of shared memory.
 #pragma once
 
@@ -15,23 +15,29 @@
 
 namespace wf {
 
+// Length of the register sub-transforms: 64, or 32 at 1024 x 1024, which halves the rows and columns per
+// CTA and doubles the work items of a phase (a single 1024^2 field then keeps 128 CTAs busy, not 64).
+#ifndef WF_GLOBAL_SUB_1024
+#define WF_GLOBAL_SUB_1024 32
+#endif
 template <int N_>
 struct GGeo {
   static constexpr int N = N_, H = N_, W = N_;
+  static constexpr int S = N_ >= 1024 ? WF_GLOBAL_SUB_1024 : 64;  // register sub-transform length
   static constexpr int LR = W / 2;          // complex length of a row transform
-  static constexpr int RR = LR / 64;        // row radix (2, 4, 8)
-  static constexpr int RC = H / 64;         // column radix (4, 8, 16)
+  static constexpr int RR = LR / S;         // row radix
+  static constexpr int RC = H / S;          // column radix
   static constexpr int RB = 128 / RR;       // rows per CTA
   static constexpr int CB = 128 / RC;       // columns per CTA
   // float2 stride between vectors in shared memory: each vector carries 1 float2 of padding per 64,
   // and the stride is odd (2 x odd when only 8 vectors share a half-warp) so that a half-warp reading
   // the same element of consecutive vectors hits distinct banks
-  static constexpr int vstride(int len, int r, int nv) {
-    const int v = len + r;
+  static constexpr int vstride(int len, int nv) {
+    const int v = len + len / 64;
     return nv >= 16 ? (v % 2 == 1 ? v : v + 1) : (v % 16 == 2 ? v : v + ((18 - v % 16) % 16));
   }
-  static constexpr int VROW = vstride(LR, RR, 128 / RR);
-  static constexpr int VCOL = vstride(H, RC, 128 / RC);
+  static constexpr int VROW = vstride(LR, 128 / RR);
+  static constexpr int VCOL = vstride(H, 128 / RC);
   static constexpr int SMEM = (RB * VROW > CB * VCOL ? RB * VROW : CB * VCOL) * 8;
   static constexpr int ROW_ITEMS = H / RB;  // row-phase work items per field
   static constexpr int COL_ITEMS = LR / CB; // column-phase work items per field
@@ -40,44 +46,41 @@ struct GGeo {
 
 WF_HD int padi(int i) { return i + (i >> 6); }
 
-// Forward DFT of length L = R*64 of the padded vectors v_j = buf + j*V (j < NV), natural order in and out.
-// tw[j] = exp(-2 pi i j / L). INV: inverse via conjugation on the way in and out. 128 threads.
-template <int R, int NV, int V, bool INV>
+// Forward DFT of length L = R*S of the padded vectors v_j = buf + j*V (j < NV), natural order in and out.
+// tw[j] = exp(-2 pi i j / L). INV: inverse via conjugation on the way in and out. 128 threads = NV * R.
+template <int R, int NV, int V, bool INV, int S = 64>
 __device__ __forceinline__ void fft_smem(float2* buf, const float2* __restrict__ tw) {
+  static_assert(NV * R == 128, "one sub-transform per thread in step C");
   const int tid = threadIdx.x;
-  // step A: R-point DFT across the 64 strided subsequences, twiddled by W_L^(q n)
-  for (int task = tid; task < NV * 64; task += 128) {
-    const int j = task >> 6, n = task & 63;
+  // step A: R-point DFT across the S strided subsequences, twiddled by W_L^(q n)
+  for (int task = tid; task < NV * S; task += 128) {
+    const int j = task / S, n = task % S;
     float2* v = buf + j * V;
     float2 a[R];
 #pragma unroll
     for (int m = 0; m < R; ++m) {
-      a[m] = v[padi(n + 64 * m)];
+      a[m] = v[padi(n + S * m)];
       if (INV) a[m].y = -a[m].y;
     }
     fft<R, false>(a);
 #pragma unroll
-    for (int q = 0; q < R; ++q) v[padi(n + 64 * q)] = q == 0 ? a[0] : cmul(a[q], __ldg(tw + q * n));
+    for (int q = 0; q < R; ++q) v[padi(n + S * q)] = q == 0 ? a[0] : cmul(a[q], __ldg(tw + q * n));
   }
   __syncthreads();
-  // step C: 64-point FFT of each twiddled subsequence q; output k goes to position q + R k
+  // step C: S-point FFT of each twiddled subsequence q; output k goes to position q + R k
   // (consecutive threads take consecutive vectors)
   const int j = tid % NV, q = tid / NV;
   float2* v = buf + j * V;
-  float2 u[64];
-  if (j < NV) {
+  float2 u[S];
 #pragma unroll
-    for (int n = 0; n < 64; ++n) u[n] = v[padi(64 * q + n)];
-  }
+  for (int n = 0; n < S; ++n) u[n] = v[padi(S * q + n)];
   __syncthreads();
-  if (j < NV) {
-    fft<64, false>(u);
+  fft<S, false>(u);
 #pragma unroll
-    for (int k = 0; k < 64; ++k) {
-      float2 o = u[k];
-      if (INV) o.y = -o.y;
-      v[padi(q + R * k)] = o;
-    }
+  for (int k = 0; k < S; ++k) {
+    float2 o = u[k];
+    if (INV) o.y = -o.y;
+    v[padi(q + R * k)] = o;
   }
   __syncthreads();
 }
@@ -277,7 +280,7 @@ __device__ void row_item(const GlobalArgs& a, float2* buf, int f, int y0, int do
     }
     __syncthreads();
     real_pass<N, false>(buf, G::RB, a.tw_real);
-    fft_smem<G::RR, G::RB, G::VROW, true>(buf, a.tw_row);
+    fft_smem<G::RR, G::RB, G::VROW, true, G::S>(buf, a.tw_row);
   }
   // buf rows hold (s[2m], s[2m+1]) (scaled as the fused kernels: unnormalised transforms, the 1/n and
   // 1/sqrt(2n) factors are in the Fourier-space tables)
@@ -310,7 +313,7 @@ __device__ void row_item(const GlobalArgs& a, float2* buf, int f, int y0, int do
                     sc.sqrt_tau, ltau, a.rhs_mode, a.mode == 2 ? float(level_lambda(sc, f, a.eta) * sc.tau) : 0.f);
   else
     __syncthreads();
-  fft_smem<G::RR, G::RB, G::VROW, false>(buf, a.tw_row);
+  fft_smem<G::RR, G::RB, G::VROW, false, G::S>(buf, a.tw_row);
   real_pass<N, true>(buf, G::RB, a.tw_real);
   for (int e = threadIdx.x; e < G::RB * L; e += nthr) {
     const int j = e / L, m = e % L;
@@ -450,11 +453,11 @@ __device__ double col_item(const GlobalArgs& a, float2* buf, int f, int c0, int 
     buf[j * G::VCOL + padi(y)] = __ldcg(Zf + (long long)y * L + c0 + j);
   }
   __syncthreads();
-  fft_smem<G::RC, G::CB, G::VCOL, false>(buf, a.tw_col);
+  fft_smem<G::RC, G::CB, G::VCOL, false, G::S>(buf, a.tw_col);
   const double acc = col_update<N>(a.mode, buf, c0, a.fg, a.Pk, a.prev, a.step0 + uint32_t(done),
                                    a.chain0 + uint32_t(f), a.key0, a.key1, ltau, cmp, store);
   if (a.mode == 2) return acc;
-  fft_smem<G::RC, G::CB, G::VCOL, true>(buf, a.tw_col);
+  fft_smem<G::RC, G::CB, G::VCOL, true, G::S>(buf, a.tw_col);
   for (int e = threadIdx.x; e < G::CB * H; e += 128) {
     const int j = e % G::CB, y = e / G::CB;
     __stcg(Zf + (long long)y * L + c0 + j, buf[j * G::VCOL + padi(y)]);
@@ -474,7 +477,7 @@ __device__ void col_wpower(const GlobalArgs& a, float2* buf, int f, int c0, doub
     buf[j * G::VCOL + padi(y)] = __ldcg(Zf + (long long)y * L + c0 + j);
   }
   __syncthreads();
-  fft_smem<G::RC, G::CB, G::VCOL, false>(buf, a.tw_col);
+  fft_smem<G::RC, G::CB, G::VCOL, false, G::S>(buf, a.tw_col);
   auto sq = [](float p, float q) -> double { return double(p) * p + double(q) * q; };
   for (int task = threadIdx.x; task < G::CB * (H / 2); task += 128) {
     const int jc = task / (H / 2), j = task % (H / 2);
