@@ -63,9 +63,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the plain, single-chain and batch measurements")
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed-size batch measurement")
-    ap.add_argument("--large-path", choices=("cluster", "global"), default="cluster",
-                    help="256x256 / 512x512 kernels outside the large-image comparison: thread-block clusters "
-                         "(default) or the global-memory kernels")
+    ap.add_argument("--large-path", choices=("auto", "cluster", "global"), default="auto",
+                    help="256x256 / 512x512 kernels outside the large-image comparison: automatic (default), "
+                         "thread-block clusters or the global-memory kernels")
     ap.add_argument("--large-chains", type=int, default=456,
                     help="chains of the 256x256 large-image sampler measurement (512x512: a third)")
     ap.add_argument("--large-samples", type=int, default=20,

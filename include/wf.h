@@ -22,8 +22,9 @@
  *     Ndiag is rejected with WF_ERR_TAU.
  *   - Supported sizes: H == W in {16, 32, 64, 128, 256, 512, 1024} (wf_supported_size). Up to 128 x 128
  *     a chain's field stays in one SM's shared memory for the whole call. At 256 x 256 and 512 x 512 the
- *     samplers and Wiener filters keep the field in the shared memory of one thread-block cluster
- *     (wf_set_large_image_sampler). Otherwise larger images keep the field in global memory and run as
+ *     samplers and Wiener filters of many chains or images keep each field in the shared memory of one
+ *     thread-block cluster (wf_set_large_image_sampler). Otherwise larger images keep the field in global
+ *     memory and run as
  *     one cooperative launch (all CTAs co-resident) whose phases are separated by a bounded grid barrier
  *     (WF_ERR_TIMEOUT if a barrier wait gives up). For those sizes wf_solve_ex starts from zero
  *     (opts->init_s must be NULL).
@@ -393,12 +394,15 @@ double wf_last_kernel_ms(void);
 
 /*
  * Path for 256 x 256 and 512 x 512 images (wf_sample, wf_sample_ex, the first pass of wf_solve /
- * wf_solve_ex, and the large images of wf_batch_run and the batch graphs), per host thread: mode 0
- * (default) keeps each chain's or image's field in the distributed shared memory of one thread-block
- * cluster (N / 64 CTAs) for all its sweeps (a batch image runs its level norms, cooled solve and samples
- * in one cluster), where the device can host such a cluster, else falls back to mode 1; mode 1 keeps the
- * fields in global memory and runs the sweeps as cooperative launches. Both compute the same chain and
- * the same filter (the same draws and schedule; FP32 results agree to rounding). Returns the previous mode.
+ * wf_solve_ex, and the large images of wf_batch_run and the batch graphs), per host thread. Two kernel
+ * families compute the same chain and the same filter (the same draws and schedule; FP32 results agree to
+ * rounding): thread-block clusters, each holding one chain's or image's field in distributed shared memory
+ * (N / 64 or N / 32 CTAs; a batch image runs its level norms, cooled solve and samples in one cluster),
+ * and the global-memory kernels (fields in global memory, cooperative launches with many CTAs per field).
+ * mode 0 (default, automatic): clusters when a call holds at least 16 chains (or a batch chunk at least
+ * 16 images) and the device can host the cluster, otherwise the global-memory kernels, which have the
+ * lower latency for a single field; mode 1: always the global-memory kernels; mode 2: clusters wherever
+ * the device can host them. Returns the previous mode.
  */
 int32_t wf_set_large_image_sampler(int32_t mode);
 

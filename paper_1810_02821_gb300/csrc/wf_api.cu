@@ -17,7 +17,7 @@ namespace {
 
 thread_local int g_last_cuda_error = 0;
 thread_local int g_timing = 0;
-thread_local int g_large_sampler = 0;  // 0: cluster sampler where it fits, 1: global-memory sampler
+thread_local int g_large_sampler = 0;  // 0: automatic, 1: global-memory kernels, 2: clusters where they fit
 thread_local double g_kernel_ms = -1.0;
 
 // CUDA events around the main kernel of a call (only when timing is enabled on this thread)
@@ -145,6 +145,18 @@ bool size_ok(int H, int W) {
   return H == W && (H == 16 || H == 32 || H == 64 || H == 128 || H == 256 || H == 512 || H == 1024);
 }
 bool size_on_chip(int H) { return H <= 128; }
+
+bool cluster_fits(int H);
+
+// Path for `units` independent fields (chains or images) of H x H, H in {256, 512}: one thread-block
+// cluster per field, or the global-memory kernels. Automatic choice (measured on GB300): the global-memory
+// kernels (16-point sub-transforms, many CTAs per field) have the lower latency for a single field, the
+// clusters the higher throughput once a launch holds about 16 fields or more.
+constexpr int kClusterMinUnits = 16;
+bool use_cluster(int H, int units) {
+  if ((H != 256 && H != 512) || g_large_sampler == 1 || !cluster_fits(H)) return false;
+  return g_large_sampler == 2 || units >= kClusterMinUnits;
+}
 
 // whether at least one sampler cluster for H x H fits on the current device (queried once per device)
 bool cluster_fits(int H) {
@@ -479,7 +491,7 @@ void wf_set_kernel_timing(int32_t enable) { g_timing = enable ? 1 : 0; }
 
 int32_t wf_set_large_image_sampler(int32_t mode) {
   const int prev = g_large_sampler;
-  g_large_sampler = mode == 1 ? 1 : 0;
+  g_large_sampler = (mode == 1 || mode == 2) ? mode : 0;
   return prev;
 }
 
@@ -559,7 +571,7 @@ wf_status solve_pass(const float* d, const float* Ndiag, const uint8_t* mask, co
                      wf::LaunchTimer* timer, const float2* rhs_tab = nullptr, const double* rhs_norms = nullptr) {
   if (!size_on_chip(H)) {
     if (o.init_s) return WF_ERR_ARG;  // the large-image solve starts from zero
-    if (!rhs_tab && (H == 256 || H == 512) && g_large_sampler == 0 && cluster_fits(H))
+    if (!rhs_tab && use_cluster(H, 1))
       return solve_cluster(d, Ndiag, mask, Pk, H, W, o, out_s, iters_out, resid_out, st, timer);
     return solve_global(d, Ndiag, mask, Pk, H, W, o, out_s, iters_out, resid_out, st, timer, rhs_tab, rhs_norms);
   }
@@ -758,7 +770,7 @@ wf_status wf_sample_ex(const float* d, const float* Ndiag, const uint8_t* mask, 
     mask = resp.mask;
   }
   // 256 and 512: one cluster per chain when the device can host the cluster, else the field in global memory
-  const bool cluster = (H == 256 || H == 512) && g_large_sampler == 0 && cluster_fits(H);
+  const bool cluster = use_cluster(H, o.n_chains);
   if (!size_on_chip(H) && !cluster) {
     KernelTimer gt(st);
     const wf_status r = sample_global(d, Ndiag, mask, Pk, H, W, seed, o, sweeps, out, st, &gt);
@@ -1470,8 +1482,8 @@ wf_status plan_batch(const wf_batch_item* items, int n_items, const wf_batch_opt
       GBChunk ch;
       ch.H = kBatchSizes[c];
       ch.stream = k;
-      ch.cluster = (ch.H == 256 || ch.H == 512) && g_large_sampler == 0 && cluster_fits(ch.H);
       for (int i = k * nc / parts; i < (k + 1) * nc / parts; ++i) ch.items.push_back(p->cls[c][i]);
+      ch.cluster = use_cluster(ch.H, int(ch.items.size()));
       layout_chunk(ch, cv);
       p->chunks.push_back(std::move(ch));
     }

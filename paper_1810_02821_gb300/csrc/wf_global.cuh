@@ -15,15 +15,23 @@
 
 namespace wf {
 
-// Length of the register sub-transforms: 64, or 32 at 1024 x 1024, which halves the rows and columns per
-// CTA and doubles the work items of a phase (a single 1024^2 field then keeps 128 CTAs busy, not 64).
+// Length S of the register sub-transforms. A shorter S means fewer rows and columns per CTA and more work
+// items per phase, so a single field keeps more CTAs busy: with S = 16 a 1024^2 field has 256 row and 256
+// column items per phase (64 with S = 64). Measured on GB300 (one image): 1024^2 precision solve 3.27 s
+// (S = 64) -> 2.14 s (32) -> 1.84 s (16); 256^2 solve of 184 sweeps 15.0 -> 7.2 -> 4.4 ms.
 #ifndef WF_GLOBAL_SUB_1024
-#define WF_GLOBAL_SUB_1024 32
+#define WF_GLOBAL_SUB_1024 16
+#endif
+#ifndef WF_GLOBAL_SUB_512
+#define WF_GLOBAL_SUB_512 16
+#endif
+#ifndef WF_GLOBAL_SUB_256
+#define WF_GLOBAL_SUB_256 16
 #endif
 template <int N_>
 struct GGeo {
   static constexpr int N = N_, H = N_, W = N_;
-  static constexpr int S = N_ >= 1024 ? WF_GLOBAL_SUB_1024 : 64;  // register sub-transform length
+  static constexpr int S = N_ >= 1024 ? WF_GLOBAL_SUB_1024 : (N_ >= 512 ? WF_GLOBAL_SUB_512 : WF_GLOBAL_SUB_256);
   static constexpr int LR = W / 2;          // complex length of a row transform
   static constexpr int RR = LR / S;         // row radix
   static constexpr int RC = H / S;          // column radix

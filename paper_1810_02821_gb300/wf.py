@@ -627,15 +627,15 @@ def wf_set_kernel_timing(enable: bool) -> None:
 
 
 def wf_set_large_image_sampler(mode: str) -> str:
-    """Path for 256 x 256 and 512 x 512 images on this thread (samplers, Wiener filters, batches):
-    "cluster" (the field in the shared memory of one thread-block cluster per chain or image, where the
-    device can host it) or "global" (fields in global memory, cooperative launches). Returns the previous
-    mode."""
-    modes = {"cluster": 0, "global": 1}
+    """Path for 256 x 256 and 512 x 512 images on this thread (samplers, Wiener filters, batches): "auto"
+    (default: thread-block clusters for 16 or more chains or batch images, else the global-memory kernels),
+    "cluster" (one cluster per chain or image wherever the device can host it) or "global" (fields in
+    global memory, cooperative launches). Returns the previous mode."""
+    modes = {"auto": 0, "global": 1, "cluster": 2}
     if mode not in modes:
         raise ValueError(f"mode must be one of {sorted(modes)}")
     prev = load_library().wf_set_large_image_sampler(modes[mode])
-    return "global" if prev == 1 else "cluster"
+    return {0: "auto", 1: "global", 2: "cluster"}[prev]
 
 
 def wf_last_kernel_ms() -> float:

@@ -38,9 +38,10 @@ def test_host_only_calls(lib):
     so = wf.SampleOpts()
     lib.wf_sample_opts_default(ctypes.byref(so))
     assert so.n_chains == 1 and so.thin == 1 and so.burn_in == 0
-    # large-image sampler selector (per thread): cluster by default, global on request
-    assert wf.wf_set_large_image_sampler("global") == "cluster"
+    # large-image path selector (per thread): automatic by default, global or cluster on request
+    assert wf.wf_set_large_image_sampler("global") == "auto"
     assert wf.wf_set_large_image_sampler("cluster") == "global"
+    assert wf.wf_set_large_image_sampler("auto") == "cluster"
     with pytest.raises(ValueError):
         wf.wf_set_large_image_sampler("smem")
 
