@@ -1173,55 +1173,68 @@ __device__ __forceinline__ int solve_sweeps(float2* S, double* red, int lt, floa
     load_staged_row<N>(stg, lt, c);
   };
   t_update(ltau);
-  row_forward<N>(c);
-  row_store_spec<N>(S, lt, c);
-  __syncthreads();
-
+  // One sweep = four transforms, all run by the single forward FFT at the top of the loop (an inverse
+  // transform is conj(FFT(conj(x)))), as in the sampler: one copy of the transform code.
+  enum { ROW_FWD, COL_FWD, COL_INV, ROW_INV };
+  int phase = ROW_FWD;
   it = 0;
   int k = 0;       // sweeps at the current level
   int status = 1;  // 1 = running
   rho = -1.0;
   while (true) {
-    ++k;
-    ++it;
-    const bool cmp = (k % check == 0) && k >= 2;
-    const bool store = ((k + 1) % check == 0);
-    col_load<N>(S, lt, c);
-    __syncthreads();
-    fft<G::LC, false>(c);
-    // s-update on the parked modes (the slots this thread stores to after the inverse transform)
-    park_modes<N>(S, lt, c);
-    const double acc = s_update_wf_parked<N>(S, lt, Pk, ltau, prev, cmp, store);
-    unpark_modes<N>(S, lt, c);
-    if (cmp) {
-      const double tot = block_sum(acc, red) * double(G::H * G::W);
-      const double bn = bnorm2[lev];
-      const double r2 = bn > 0.0 ? tot / bn : tot;
-      rho = sqrt(r2);
-      if (!(r2 == r2) || r2 > 1e300) {
-        status = 6;  // non-finite residual
-      } else if (lev < last_level) {
-        if (rho < level_tol || k >= level_max) {
-          ++lev;
-          lam = level_lambda(sc, lev, eta);
-          ltau = float(lam * tau);
-          k = 0;
+    fft<G::LR, false>(c);
+    if (phase == ROW_FWD) {
+      r2c_post_all<G::LR>(c, std::make_integer_sequence<int, G::LR>{});
+      row_store_spec<N>(S, lt, c);
+      __syncthreads();
+      col_load<N>(S, lt, c);
+      __syncthreads();
+      phase = COL_FWD;
+    } else if (phase == COL_FWD) {
+      ++k;
+      ++it;
+      const bool cmp = (k % check == 0) && k >= 2;
+      const bool store = ((k + 1) % check == 0);
+      // s-update on the parked modes (the slots this thread stores to after the inverse transform)
+      park_modes<N>(S, lt, c);
+      const double acc = s_update_wf_parked<N>(S, lt, Pk, ltau, prev, cmp, store);
+      unpark_modes<N>(S, lt, c);
+      if (cmp) {
+        const double tot = block_sum(acc, red) * double(G::H * G::W);
+        const double bn = bnorm2[lev];
+        const double r2 = bn > 0.0 ? tot / bn : tot;
+        rho = sqrt(r2);
+        if (!(r2 == r2) || r2 > 1e300) {
+          status = 6;  // non-finite residual
+        } else if (lev < last_level) {
+          if (rho < level_tol || k >= level_max) {
+            ++lev;
+            lam = level_lambda(sc, lev, eta);
+            ltau = float(lam * tau);
+            k = 0;
+          }
+        } else if (rho < tol) {
+          status = 0;
         }
-      } else if (rho < tol) {
-        status = 0;
       }
+      if (status == 1 && it >= max_iter) status = 5;  // not converged
+      conj_all<G::LC>(c);
+      phase = COL_INV;
+    } else if (phase == COL_INV) {
+      conj_all<G::LC>(c);
+      col_store_inv<N>(S, lt, c);
+      __syncthreads();
+      row_load_spec<N>(S, lt, c);
+      __syncthreads();
+      c2r_pre_all<G::LR>(c, std::make_integer_sequence<int, G::LR>{});
+      conj_all<G::LR>(c);
+      phase = ROW_INV;
+    } else {
+      conj_all<G::LR>(c);  // c[m] = (s[2m], s[2m+1])
+      if (status != 1) break;
+      t_update(ltau);
+      phase = ROW_FWD;
     }
-    if (status == 1 && it >= max_iter) status = 5;  // not converged
-    col_inverse_store<N>(S, lt, c);
-    __syncthreads();
-    row_load_spec<N>(S, lt, c);
-    __syncthreads();
-    row_inverse<N>(c);
-    if (status != 1) break;
-    t_update(ltau);
-    row_forward<N>(c);
-    row_store_spec<N>(S, lt, c);
-    __syncthreads();
   }
   return status;
 }
