@@ -70,6 +70,22 @@ def test_cluster_and_global_samplers_agree(H):
         assert rel(out["cluster"][0, m], ref[2 + 2 * m + 1]) < SAMPLE_TOL
 
 
+def test_automatic_path_switch_keeps_the_chain():
+    """In the default (automatic) mode 15 chains of 256^2 run on the global-memory kernels and 16 on
+    clusters; the chains they share (same chain words) agree to FP32 rounding."""
+    p = synth.make_problem(256, seed=31, mask_frac=0.1, slope=-2.0, k0=1.0 / 32, sigma2=(0.05, 0.5))
+    dev = to_dev(p)
+    prev = wf.wf_set_large_image_sampler("auto")
+    try:
+        few = wf.wf_sample_ex(*dev, seed=5, n_samples=2, n_chains=15, chain_offset=3).cpu().numpy()
+        many = wf.wf_sample_ex(*dev, seed=5, n_samples=2, n_chains=16, chain_offset=3).cpu().numpy()
+    finally:
+        wf.wf_set_large_image_sampler(prev)
+    for c in (0, 7, 14):
+        for m in range(2):
+            assert rel(few[c, m], many[c, m]) < 1e-5, (c, m)
+
+
 def test_sample_1024_one_sweep():
     p = synth.make_problem(1024, seed=4, mask_frac=0.05, slope=-1.5, sigma2=(0.001, 0.1))
     got = wf.wf_sample_ex(*to_dev(p), seed=3, n_samples=1, n_chains=1).cpu().numpy()
