@@ -193,12 +193,6 @@ WF_HD void row_store_spec(float2* S, int y, const float2 (&c)[N / 2]) {
   for (int k = 0; k < G::LR; ++k) S[y * G::SP + k] = c[k];
 }
 
-// packed half-spectrum row (after the inverse column transform) -> c[m] = (s[2m], s[2m+1])
-template <int N>
-WF_HD void row_inverse(float2 (&c)[N / 2]) {
-  c2r_pre_all<N / 2>(c, std::make_integer_sequence<int, N / 2>{});
-  fft<N / 2, true>(c);
-}
 // c[m] = (t[2m], t[2m+1]) -> packed half-spectrum row
 template <int N>
 WF_HD void row_forward(float2 (&c)[N / 2]) {
@@ -252,24 +246,6 @@ template <int L>
 WF_HD void conj_all(float2 (&x)[L]) {
 #pragma unroll
   for (int k = 0; k < L; ++k) x[k].y = -x[k].y;
-}
-
-// inverse column transform of the modes held by this thread, then store e[n] (r = 0, rows [0, LC))
-// or o[n] = exp(+2 pi i n / H) * IFFT(odd)[n] (r = 1, rows [LC, H)).
-template <int N>
-WF_HD void col_inverse_store(float2* S, int lt, float2 (&x)[N / 2]) {
-  using G = Geo<N>;
-  const int col = lt % G::LC, r = lt / G::LC;
-  fft<G::LC, true>(x);
-  if (r == 0) {
-#pragma unroll
-    for (int n = 0; n < G::LC; ++n) S[n * G::SP + col] = x[n];
-  } else {
-    sfor<G::LC>([&](auto I) {
-      constexpr int n = decltype(I)::value;
-      S[(n + G::LC) * G::SP + col] = twiddle<n, G::H, true>(x[n]);
-    });
-  }
 }
 
 // mode pairs held by a column thread: register kp and its mirror register, with their ky values.
@@ -336,23 +312,6 @@ __device__ __forceinline__ void copy_out_t(const float* stg, int lt, void* __res
 // ---------------------------------------------------------------------------------------------
 // pixel-space updates (Alg. 1 t-update), row y, c[m] = (s[2m], s[2m+1]) -> (t[2m], t[2m+1])
 // ---------------------------------------------------------------------------------------------
-// Wiener-filter mode at level lambda: table dn[x*H + y] = (d, 1/N_bar) (0 on missing pixels),
-// w = N_bar / (lambda tau + N_bar) = 1 / (1 + lambda tau / N_bar), t = d + w (s - d).
-// rhs mode (refinement corrections): dn holds (r, 1/N_bar) and t = lambda tau r + w s, whose fixed point
-// solves (S^-1 + N_lambda^-1) s = r for any pixel-space r (r need not vanish on missing pixels).
-template <int N>
-WF_HD void t_update_wf(float2 (&c)[N / 2], int y, const float2* __restrict__ dn, float lt_, bool rhs = false) {
-  using G = Geo<N>;
-  const float g = rhs ? 0.0f : 1.0f, h = rhs ? lt_ : 1.0f;
-#pragma unroll
-  for (int x = 0; x < G::W; ++x) {
-    const float2 co = WF_LDG(dn + x * G::H + y);
-    const float w = wf_rcp(fmaf(lt_, co.y, 1.0f));
-    float& v = (x & 1) ? c[x / 2].y : c[x / 2].x;
-    v = fmaf(w, fmaf(-g, co.x, v), h * co.x);
-  }
-}
-
 // right-hand side of the level-lambda Wiener equation, N_lambda^-1 d = d / (N_bar + lambda tau)
 template <int N>
 WF_HD void rhs_row(float2 (&c)[N / 2], int y, const float2* __restrict__ dn, float lt_) {
@@ -524,8 +483,12 @@ WF_HD void t_draw_staged(float* stg, int y, const float2* __restrict__ aq, float
   }
 }
 
-// Wiener-filter t-update (as t_update_wf) of the staged row y, rolled over groups of four pixels: the
-// row's registers are dead meanwhile, so more table loads can be in flight
+// Wiener-filter t-update at level lambda of the staged row y: table dn[x*H + y] = (d, 1/N_bar) ((0, 0) on
+// missing pixels), w = N_bar / (lambda tau + N_bar) = 1 / (1 + lambda tau / N_bar), t = d + w (s - d).
+// rhs mode (refinement corrections): dn holds (r, 1/N_bar) and t = lambda tau r + w s, whose fixed point
+// solves (S^-1 + N_lambda^-1) s = r for any pixel-space r (r need not vanish on missing pixels).
+// Rolled over groups of four pixels: the row's registers are dead meanwhile, so more table loads are in
+// flight.
 template <int N>
 WF_HD void t_update_wf_staged(float* stg, int y, const float2* __restrict__ dn, float lt_, bool rhs) {
   using G = Geo<N>;
