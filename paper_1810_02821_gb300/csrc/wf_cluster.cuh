@@ -427,18 +427,16 @@ __device__ __forceinline__ void ct_update_wf(float2* row, int y, int h, const fl
   }
 }
 
-// right-hand side N_lambda^-1 d = d / (N_bar + lambda tau) of this CTA's rows (0 on missing pixels)
+// right-hand side N_lambda^-1 d = d / (N_bar + lambda tau) of one staged row (0 on missing pixels), by the
+// row's R threads over the same slots as the pixel updates (x2 = h, h + R, ...), table row ty (CTA-
+// contiguous, so the row threads' loads coalesce); each thread writes only slots it reads next
 template <int N>
-__device__ __forceinline__ void crhs_rows(float2* rows, int b, const float2* __restrict__ dn, float lt_) {
+__device__ __forceinline__ void crhs_row(float2* row, int ty, int h, const float2* __restrict__ dn, float lt_) {
   using G = CGeo<N>;
-  for (int e = threadIdx.x; e < G::A * G::L; e += G::L) {
-    const int ar = e / G::L, i = e % G::L, y = b * G::M + ar;  // CTA-contiguous table row
-    float2 r;
-    const float2 c0 = WF_LDG(dn + (2 * i) * G::H + y), c1 = WF_LDG(dn + (2 * i + 1) * G::H + y);
+  for (int x2 = h; x2 < G::W / 2; x2 += G::R) {
+    const float2 c0 = WF_LDG(dn + (2 * x2) * G::H + ty), c1 = WF_LDG(dn + (2 * x2 + 1) * G::H + ty);
     const float nb0 = c0.y > 0.0f ? wf_rcp(c0.y) : wf_inf(), nb1 = c1.y > 0.0f ? wf_rcp(c1.y) : wf_inf();
-    r.x = c0.x / (nb0 + lt_);
-    r.y = c1.x / (nb1 + lt_);
-    rows[ar * G::SP + i] = r;
+    row[x2] = make_float2(c0.x / (nb0 + lt_), c1.x / (nb1 + lt_));
   }
 }
 
@@ -554,8 +552,8 @@ __device__ __forceinline__ int csolve_loop(cooperative_groups::cluster_group& cl
   float2* row = rows + ar * G::SP;
   constexpr double NPIX = double(G::H) * double(G::W);
   for (int lev = 0; lev < sc.n_levels; ++lev) {  // level norms
-    crhs_rows<N>(rows, b, dn, float(level_lambda(sc, lev, eta) * sc.tau));
-    __syncthreads();
+    crhs_row<N>(row, b * G::M + ar, h, dn, float(level_lambda(sc, lev, eta) * sc.tau));
+    __syncwarp();
     crow_fwd<N>(row, h, tw);
     __syncthreads();
     ccol_fwd<N>(rows, tid, b, tw);
