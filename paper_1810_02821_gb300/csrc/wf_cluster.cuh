@@ -1,4 +1,5 @@
-// Cluster-resident sampler for 256 x 256 and 512 x 512 images (Alg. 1 of the paper with A = I).
+// Cluster-resident sampler and Wiener filter for 256 x 256 and 512 x 512 images (Alg. 1 of the paper with
+// A = I, and its G -> 0 form with lambda-cooling, §2.2).
 //
 // A 256^2 field's packed half spectrum (256 KB) does not fit one SM, but it fits the distributed shared
 // memory of a thread-block cluster. One field (one chain) is a cluster of P = N / M CTAs of N / 2 threads
@@ -17,7 +18,9 @@
 // right there, on the complete column spectrum, followed by the inverse radix-P stage, the inverse twiddle
 // and the local inverse FFTs. Two cluster barriers per sweep (hardware barriers, no spin waits).
 // Draws follow the Philox counter layout of the on-chip sampler, so the chain is the same Markov chain
-// draw for draw.
+// draw for draw. The Wiener-filter form (k_cpipe: level norms, cooled solve, then samples from s_W, one
+// image per cluster) replaces the draw by the level-lambda update and sums its FP64 residual per CTA and
+// then across the cluster in rank order, so every thread takes the same schedule decisions.
 #pragma once
 
 #include <cooperative_groups.h>
