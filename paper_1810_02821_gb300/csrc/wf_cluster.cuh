@@ -51,6 +51,10 @@ struct CGeo {
   static constexpr int ROWS_BYTES = A * SP * 8;
   static constexpr int SMEM = ROWS_BYTES + N * 8 + (33 + 16 + kMaxLevels) * 8;  // rows, twiddles, FP64 sums, level norms
   static constexpr int WH = W / 2 + 1;
+  static_assert(M * P == N && R * M == L && R >= 2 && 32 % R == 0, "cluster geometry");
+  static_assert(P <= 16, "at most 16 CTAs per cluster (the non-portable maximum)");
+  static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
+  static_assert(ROWS_BYTES % 8 == 0, "FP64 sums after the rows stay 8-byte aligned");
 };
 
 // ---------------------------------------------------------------------------------------------
