@@ -86,6 +86,24 @@ def test_automatic_path_switch_keeps_the_chain():
             assert rel(few[c, m], many[c, m]) < 1e-5, (c, m)
 
 
+@pytest.mark.parametrize("H", [256, 512])
+def test_large_degenerate_cases(H, sampler):
+    """Zero power: every sample and the filter are exactly 0. Every pixel missing: the filter is 0 and the
+    samples are draws from the prior, the oracle's draw for draw (16 chains, so the automatic mode too
+    would take the clusters)."""
+    p = synth.make_problem(H, seed=H + 17, mask_frac=0.1, slope=-2.0, k0=1.0 / 32, sigma2=(0.05, 0.5))
+    dev = list(to_dev(p))
+    dev[3] = torch.zeros_like(dev[3])
+    assert float(wf.wf_sample_ex(*dev, seed=1, n_samples=2, n_chains=16).abs().max()) == 0.0
+    assert float(wf.wf_solve(*dev).s.abs().max()) == 0.0
+    q = synth.flat_problem(H, seed=2, all_masked=True)
+    assert float(wf.wf_solve(*to_dev(q)).s.abs().max()) == 0.0
+    got = wf.wf_sample_ex(*to_dev(q), seed=4, n_samples=2, n_chains=16, chain_offset=1).cpu().numpy()
+    ref = M.sample(q.d, q.Ndiag, q.mask, q.Pk, 2, seed=4, chain=1)
+    for m in range(2):
+        assert rel(got[0, m], ref[m]) < SAMPLE_TOL, m
+
+
 def test_sample_1024_one_sweep():
     p = synth.make_problem(1024, seed=4, mask_frac=0.05, slope=-1.5, sigma2=(0.001, 0.1))
     got = wf.wf_sample_ex(*to_dev(p), seed=3, n_samples=1, n_chains=1).cpu().numpy()
