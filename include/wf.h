@@ -399,10 +399,10 @@ double wf_last_kernel_ms(void);
  * rounding): thread-block clusters, each holding one chain's or image's field in distributed shared memory
  * (N / 64 or N / 32 CTAs; a batch image runs its level norms, cooled solve and samples in one cluster),
  * and the global-memory kernels (fields in global memory, cooperative launches with many CTAs per field).
- * mode 0 (default, automatic): clusters when a call holds at least 16 chains (or a batch chunk at least
- * 16 images) and the device can host the cluster, otherwise the global-memory kernels, which have the
- * lower latency for a single field; mode 1: always the global-memory kernels; mode 2: clusters wherever
- * the device can host them. Returns the previous mode.
+ * mode 0 (default, automatic): clusters when a call holds at least 32 chains at 256 x 256 or 8 at
+ * 512 x 512 (a batch chunk as many images) and the device can host the cluster, otherwise the
+ * global-memory kernels, which are faster for few fields; mode 1: always the global-memory kernels;
+ * mode 2: clusters wherever the device can host them. Returns the previous mode.
  */
 int32_t wf_set_large_image_sampler(int32_t mode);
 

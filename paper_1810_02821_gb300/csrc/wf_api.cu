@@ -149,13 +149,14 @@ bool size_on_chip(int H) { return H <= 128; }
 bool cluster_fits(int H);
 
 // Path for `units` independent fields (chains or images) of H x H, H in {256, 512}: one thread-block
-// cluster per field, or the global-memory kernels. Automatic choice (measured on GB300): the global-memory
-// kernels (16-point sub-transforms, many CTAs per field) have the lower latency for a single field, the
-// clusters the higher throughput once a launch holds about 16 fields or more.
-constexpr int kClusterMinUnits = 16;
+// cluster per field, or the global-memory kernels. Automatic choice (measured on GB300, 50 sweeps): the
+// global-memory kernels (16-point sub-transforms, many CTAs per field) are faster for few fields, the
+// clusters from about 32 fields at 256^2 (24 chains: 1.40 vs 1.84 ms; 32 chains: 2.46 vs 1.88 ms) and
+// from about 8 at 512^2 (4 chains: 1.39 vs 1.58 ms; 8 chains: 2.88 vs 2.07 ms).
+int cluster_min_units(int H) { return H == 256 ? 32 : 8; }
 bool use_cluster(int H, int units) {
   if ((H != 256 && H != 512) || g_large_sampler == 1 || !cluster_fits(H)) return false;
-  return g_large_sampler == 2 || units >= kClusterMinUnits;
+  return g_large_sampler == 2 || units >= cluster_min_units(H);
 }
 
 // whether at least one sampler cluster for H x H fits on the current device (queried once per device)

@@ -628,7 +628,8 @@ def wf_set_kernel_timing(enable: bool) -> None:
 
 def wf_set_large_image_sampler(mode: str) -> str:
     """Path for 256 x 256 and 512 x 512 images on this thread (samplers, Wiener filters, batches): "auto"
-    (default: thread-block clusters for 16 or more chains or batch images, else the global-memory kernels),
+    (default: thread-block clusters from 32 chains or batch images at 256^2 and from 8 at 512^2, else the
+    global-memory kernels),
     "cluster" (one cluster per chain or image wherever the device can host it) or "global" (fields in
     global memory, cooperative launches). Returns the previous mode."""
     modes = {"auto": 0, "global": 1, "cluster": 2}

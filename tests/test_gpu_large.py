@@ -70,18 +70,19 @@ def test_cluster_and_global_samplers_agree(H):
         assert rel(out["cluster"][0, m], ref[2 + 2 * m + 1]) < SAMPLE_TOL
 
 
-def test_automatic_path_switch_keeps_the_chain():
-    """In the default (automatic) mode 15 chains of 256^2 run on the global-memory kernels and 16 on
-    clusters; the chains they share (same chain words) agree to FP32 rounding."""
-    p = synth.make_problem(256, seed=31, mask_frac=0.1, slope=-2.0, k0=1.0 / 32, sigma2=(0.05, 0.5))
+@pytest.mark.parametrize("H,below", [(256, 31), (512, 7)])
+def test_automatic_path_switch_keeps_the_chain(H, below):
+    """In the default (automatic) mode 31 chains of 256^2 (7 of 512^2) run on the global-memory kernels and
+    one more on clusters; the chains they share (same chain words) agree to FP32 rounding."""
+    p = synth.make_problem(H, seed=31, mask_frac=0.1, slope=-2.0, k0=1.0 / 32, sigma2=(0.05, 0.5))
     dev = to_dev(p)
     prev = wf.wf_set_large_image_sampler("auto")
     try:
-        few = wf.wf_sample_ex(*dev, seed=5, n_samples=2, n_chains=15, chain_offset=3).cpu().numpy()
-        many = wf.wf_sample_ex(*dev, seed=5, n_samples=2, n_chains=16, chain_offset=3).cpu().numpy()
+        few = wf.wf_sample_ex(*dev, seed=5, n_samples=2, n_chains=below, chain_offset=3).cpu().numpy()
+        many = wf.wf_sample_ex(*dev, seed=5, n_samples=2, n_chains=below + 1, chain_offset=3).cpu().numpy()
     finally:
         wf.wf_set_large_image_sampler(prev)
-    for c in (0, 7, 14):
+    for c in (0, below // 2, below - 1):
         for m in range(2):
             assert rel(few[c, m], many[c, m]) < 1e-5, (c, m)
 
@@ -89,8 +90,7 @@ def test_automatic_path_switch_keeps_the_chain():
 @pytest.mark.parametrize("H", [256, 512])
 def test_large_degenerate_cases(H, sampler):
     """Zero power: every sample and the filter are exactly 0. Every pixel missing: the filter is 0 and the
-    samples are draws from the prior, the oracle's draw for draw (16 chains, so the automatic mode too
-    would take the clusters)."""
+    samples are draws from the prior, the oracle's draw for draw."""
     p = synth.make_problem(H, seed=H + 17, mask_frac=0.1, slope=-2.0, k0=1.0 / 32, sigma2=(0.05, 0.5))
     dev = list(to_dev(p))
     dev[3] = torch.zeros_like(dev[3])
