@@ -39,6 +39,23 @@ def test_host_output_equals_device_output(H, dt):
             assert rel(host[1, m].numpy(), ref[2 + 2 * m + 1]) < 1e-4
 
 
+@pytest.mark.parametrize("mode", ["cluster", "global"])
+def test_host_output_large_paths(mode):
+    """256^2 with the sample stores of the cluster kernel and of the global-memory kernel going to host
+    memory."""
+    p = synth.make_problem(256, seed=5, mask_frac=0.1, slope=-2.0, k0=1.0 / 32, sigma2=(0.05, 0.5))
+    dev = to_dev(p)
+    prev = wf.wf_set_large_image_sampler(mode)
+    try:
+        kw = dict(seed=3, n_samples=2, n_chains=4, out_dtype="bf16")
+        on_dev = wf.wf_sample_ex(*dev, **kw)
+        host = torch.zeros((4, 2, 256, 256), dtype=torch.bfloat16).pin_memory()
+        wf.wf_sample_ex(*dev, out=host, **kw)
+    finally:
+        wf.wf_set_large_image_sampler(prev)
+    assert torch.equal(host, on_dev.cpu())
+
+
 def test_host_output_single_chain_call():
     p = synth.make_problem(64, seed=3, mask_frac=0.2, slope=-2.0, k0=1.0 / 16, sigma2=(0.05, 0.5))
     dev = to_dev(p)
