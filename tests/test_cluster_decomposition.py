@@ -1,0 +1,125 @@
+"""CPU checks of the index algebra behind the cluster kernels (256^2 and 512^2 fields split over the CTAs
+of a thread-block cluster), restated in FP64 NumPy from the decomposition the kernels use:
+
+* rows: the packed-complex row transform of length L = R M as R interleaved M-point transforms, twiddles
+  W_L^(h k'), then radix-R butterflies; X[K] kept at slot R (K mod M) + K / M (digit-reversed order);
+* columns: CTA b holds rows y = P a + b; an M-point transform per CTA, twiddles W_N^(b k'), then one radix-P
+  stage across the CTAs; the inverse runs the same steps backwards;
+* the work units of the radix-P stage (k' = u with its mirror M - u) hold every mode pair (ky, N - ky) of a
+  column exactly once, so the pairwise s-draw and the Hermitian edge column can be done inside a unit.
+
+No GPU: these are the identities the kernels rely on, checked against numpy.fft.
+"""
+import numpy as np
+import pytest
+
+GEOMETRIES = [(256, 64), (512, 32), (512, 64)]  # (N, M): M rows per CTA, P = N / M CTAs
+
+
+def _units(N, M):
+    """Mode pairs (ky1, ky2) of one column as the radix-P stage enumerates them, unit by unit."""
+    P = N // M
+    out = []
+    for u in range(M // 2 + 1):
+        v = M - u
+        if u == 0:
+            pairs = [(0, N // 2)] + [(M * m, N - M * m) for m in range(1, P // 2)]
+        elif u == M // 2:
+            pairs = [(M // 2 + M * m, N - M // 2 - M * m) for m in range(P // 2)]
+        else:
+            pairs = [(u + M * m, N - u - M * m) for m in range(P // 2)] + \
+                    [(v + M * m, N - v - M * m) for m in range(P // 2)]
+        # every mode of a pair belongs to the unit's butterflies u or v
+        for a, b in pairs:
+            assert a % M in (u, v % M) and b % M in (u, v % M)
+        out.extend(pairs)
+    return out
+
+
+@pytest.mark.parametrize("N,M", GEOMETRIES)
+def test_units_cover_every_mode_pair_once(N, M):
+    pairs = _units(N, M)
+    modes = sorted(k for p in pairs for k in p)
+    assert modes == list(range(N))                         # every ky exactly once
+    for a, b in pairs:
+        assert a < N // 2 and (b == (N - a) % N or (a == 0 and b == N // 2))   # Hermitian partner
+    # the s-draw's Philox group of a pair is its ky1 (< N/2): groups are distinct
+    assert len({a for a, _ in pairs}) == len(pairs) == N // 2
+
+
+def _row_forward(z, M):
+    """Packed-complex row transform of length L = R M by the row threads' decomposition; returns the
+    digit-reversed slots."""
+    L = z.size
+    R = L // M
+    slots = np.empty(L, complex)
+    for h in range(R):                                     # thread h: every R-th slot
+        Z = np.fft.fft(z[h::R])                            # M-point transform
+        slots[R * np.arange(M) + h] = Z * np.exp(-2j * np.pi * h * np.arange(M) / L)
+    out = np.empty(L, complex)
+    for k in range(M):                                     # radix-R butterflies over the R threads
+        t = slots[R * k + np.arange(R)]
+        for m in range(R):
+            K = k + M * m
+            out[R * (K % M) + K // M] = np.sum(t * np.exp(-2j * np.pi * np.arange(R) * m / R))
+    return out
+
+
+@pytest.mark.parametrize("N,M", GEOMETRIES)
+def test_row_transform_in_digit_reversed_slots(N, M):
+    rng = np.random.default_rng(N + M)
+    L = N // 2
+    z = rng.standard_normal(L) + 1j * rng.standard_normal(L)
+    slots = _row_forward(z, M)
+    ref = np.fft.fft(z)
+    R = L // M
+    for K in range(L):
+        assert abs(slots[R * (K % M) + K // M] - ref[K]) < 1e-9 * np.sqrt(L)
+
+
+def _column_forward(x, M):
+    """Column transform of length N = P M: CTA b holds x[P a + b]; M-point transforms, twiddles
+    W_N^(b k'), then the radix-P stage across CTAs."""
+    N = x.size
+    P = N // M
+    Y = np.array([np.fft.fft(x[b::P]) * np.exp(-2j * np.pi * b * np.arange(M) / N) for b in range(P)])
+    X = np.empty(N, complex)
+    for k in range(M):
+        for m in range(P):
+            X[k + M * m] = np.sum(Y[:, k] * np.exp(-2j * np.pi * np.arange(P) * m / P))
+    return X, Y
+
+
+def _column_inverse(X, M):
+    """The inverse steps: radix-P stage back to CTA b, untwiddle W_N^(-b k'), inverse M-point transforms
+    (unnormalised, as the kernels)."""
+    N = X.size
+    P = N // M
+    x = np.empty(N, complex)
+    for b in range(P):
+        y = np.array([np.sum(X[k + M * np.arange(P)] * np.exp(2j * np.pi * b * np.arange(P) / P))
+                      for k in range(M)])
+        y = y * np.exp(2j * np.pi * b * np.arange(M) / N)
+        x[b::P] = np.fft.ifft(y) * M
+    return x
+
+
+@pytest.mark.parametrize("N,M", GEOMETRIES)
+def test_column_split_over_cluster(N, M):
+    rng = np.random.default_rng(3 * N + M)
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    X, _ = _column_forward(x, M)
+    assert np.max(np.abs(X - np.fft.fft(x))) < 1e-9 * N
+    back = _column_inverse(X, M)
+    assert np.max(np.abs(back - N * x)) < 1e-8 * N   # unnormalised round trip = N
+
+
+def test_table_rows_of_a_cta_are_contiguous():
+    """The pixel tables' row order for the clusters: row y = P a + b at index b M + a, so CTA b's rows
+    occupy [b M, b M + M) and the permutation is a bijection."""
+    for N, M in GEOMETRIES:
+        P = N // M
+        idx = [(y % P) * (N // P) + y // P for y in range(N)]
+        assert sorted(idx) == list(range(N))
+        for b in range(P):
+            assert sorted(idx[y] for y in range(b, N, P)) == list(range(b * M, b * M + M))
