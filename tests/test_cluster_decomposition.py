@@ -6,7 +6,9 @@ of a thread-block cluster), restated in FP64 NumPy from the decomposition the ke
 * columns: CTA b holds rows y = P a + b; an M-point transform per CTA, twiddles W_N^(b k'), then one radix-P
   stage across the CTAs; the inverse runs the same steps backwards;
 * the work units of the radix-P stage (k' = u with its mirror M - u) hold every mode pair (ky, N - ky) of a
-  column exactly once, so the pairwise s-draw and the Hermitian edge column can be done inside a unit.
+  column exactly once, so the pairwise s-draw and the Hermitian edge column can be done inside a unit;
+* and the shared-memory transform of the global-memory kernels (R-point DFTs across S strided
+  subsequences, then S-point transforms).
 
 No GPU: these are the identities the kernels rely on, checked against numpy.fft.
 """
@@ -123,3 +125,22 @@ def test_table_rows_of_a_cta_are_contiguous():
         assert sorted(idx) == list(range(N))
         for b in range(P):
             assert sorted(idx[y] for y in range(b, N, P)) == list(range(b * M, b * M + M))
+
+
+@pytest.mark.parametrize("L,S", [(128, 16), (256, 16), (512, 16), (1024, 16), (512, 64), (1024, 32)])
+def test_global_memory_transform_decomposition(L, S):
+    """The shared-memory transform of the global-memory kernels: an R-point DFT across the S strided
+    subsequences with twiddles W_L^(q n), then an S-point FFT of each subsequence q, output k at position
+    q + R k (L = R S; decimation in frequency)."""
+    rng = np.random.default_rng(L + S)
+    v = rng.standard_normal(L) + 1j * rng.standard_normal(L)
+    R = L // S
+    w = v.copy()
+    for n in range(S):                       # step A: tasks (vector, n)
+        a = w[n + S * np.arange(R)]
+        A = np.array([np.sum(a * np.exp(-2j * np.pi * np.arange(R) * q / R)) for q in range(R)])
+        w[n + S * np.arange(R)] = A * np.exp(-2j * np.pi * np.arange(R) * n / L)
+    out = np.empty(L, complex)
+    for q in range(R):                       # step C: one S-point transform per thread
+        out[q + R * np.arange(S)] = np.fft.fft(w[S * q + np.arange(S)])
+    assert np.max(np.abs(out - np.fft.fft(v))) < 1e-9 * L
