@@ -20,6 +20,10 @@ Printed JSON line (rank 0):
   plain_32x32, precision_1024x1024, differentiation_256x256
              the other workloads: the 32x32 plain case, the 1024x1024 solve to FP64 residual 1e-7, and
              likelihood gradients / Wiener-map VJPs of 64 images of 256x256
+  bf16_sample_storage, hierarchical_band_sampler, spin2_shear_sampler, large_image_sampler
+             the headline workload with BF16 sample storage (kernel and end-to-end rates), the sampler with
+             band-power draws, the shear pair, and the 256x256 / 512x512 samplers on thread-block clusters
+             against the global-memory kernels
 
 ``--impl reference`` times the oracle itself (the reference arm for this build) and prints the same line.
 Multi-GPU (torchrun): every rank runs the same workload on different chains (replicas, weak scaling).
