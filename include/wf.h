@@ -73,10 +73,14 @@ typedef struct {
   int32_t level_max; /* ... or after level_max sweeps at that level */
   int32_t check;     /* residual measured every `check` sweeps (>= 1) */
   int32_t max_iter;  /* sweep budget of each messenger solve; WF_ERR_NOT_CONVERGED when exhausted */
-  int32_t refine;    /* 0: plain FP32 iteration (its residual estimate floors near 1e-6); k > 0: up to k
-                        mixed-precision refinement steps: the residual r = N^-1 (d - s) - S^-1 s and the
-                        stopping test are evaluated in FP64 on the GPU and each step adds the FP32 messenger
-                        solution e of (S^-1 + N^-1) e = r; resid_out is then the FP64 residual */
+  int32_t refine;    /* k > 0 (default 3): up to k mixed-precision refinement steps. The FP32 messenger
+                        solve stops at max(tol, 1e-5); then the residual r = N^-1 (d - s) - S^-1 s of the
+                        map and the stopping test are evaluated in FP64 on the GPU, and each step adds the
+                        FP32 messenger solution e of (S^-1 + N^-1) e = r. resid_out is then the FP64
+                        relative residual of the returned map, and WF_ERR_NOT_CONVERGED means it is still
+                        >= tol after k steps. 0: the plain FP32 iteration to tol; resid_out is then its
+                        own estimate from two consecutive FP32 iterates, which keeps falling below the
+                        FP32 floor (the true residual of the map plateaus near 2e-6) */
   const float* init_s; /* device [H][W] starting iterate, or NULL for zero (sizes <= 128 only) */
   double refine_tol; /* relative residual target of each correction solve */
   const float* A;    /* device [H][W] diagonal pixel response of d = A s + n (Eq. 1), or NULL for A = I.
@@ -112,9 +116,11 @@ void wf_sample_opts_default(wf_sample_opts* o);
 
 /*
  * Wiener filter (Eq. 2-3) by the G -> 0 messenger iteration with lambda-cooling (§2.2).
- * out_s: device float32 [H][W]. iters_out (host, may be NULL): sweeps performed. resid_out (host, may
- * be NULL): last measured lambda = 1 relative residual (-1 if never measured).
- * Uses the defaults of wf_solve_opts_default with the given tau and tol.
+ * out_s: device float32 [H][W]. iters_out (host, may be NULL): sweeps performed (all solves).
+ * resid_out (host, may be NULL): the relative residual ||s + S N^-1 (s - d)|| / ||S N^-1 d|| of the
+ * returned map, summed in FP64 on the GPU (-1 if never measured). WF_OK means it is below tol.
+ * Uses the defaults of wf_solve_opts_default (FP64-residual refinement, refine = 3) with the given tau
+ * and tol.
  */
 wf_status wf_solve(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int32_t H,
                    int32_t W, double tau, double tol, float* out_s, int32_t* iters_out, double* resid_out,
@@ -408,20 +414,24 @@ int32_t wf_set_large_image_sampler(int32_t mode);
 
 /*
  * wf_sample_ex without any device allocation. The paper has no counterpart: this entry point exists for
- * callers that cannot allocate GPU memory at call time, for instance code running while a CUDA graph is
- * being captured, real-time loops that forbid the allocator's latency and synchronisation, or hosts
- * whose memory budget is fixed in advance. Arguments, results and statuses are those of wf_sample_ex;
- * the caller passes every input and the output buffer as before.
+ * callers that cannot allocate GPU memory at call time, for instance real-time loops that cannot wait on
+ * the allocator's latency and synchronisation, or host applications whose device memory is all owned by
+ * their own pool or fixed in advance. Arguments, results and statuses are those of wf_sample_ex (the
+ * output pointer is checked the same way, and a pixel response A is refused with WF_ERR_ARG because it
+ * needs transformed copies of the inputs); the caller passes every input and the output buffer as before.
  *   - Scratch (the per-call coefficient tables) lives in one statically sized device array compiled into
  *     the library, 262,144 bytes, which every GPU that loads the library keeps until the process exits.
- *     Images needing more (H * W > 128 * 128; all sizes wf_supported_size accepts fit) are rejected with
- *     WF_ERR_SHAPE before anything is launched.
+ *     Only H = W in {16, 32, 64, 128} fit; the larger sizes that wf_supported_size accepts (256, 512,
+ *     1024) are rejected with WF_ERR_SHAPE before anything is launched.
  *   - The first call on each device looks up that array's device address (cudaGetSymbolAddress) with the
- *     device current; make that first call before any stream capture. Later calls reuse the address.
+ *     device current; make that first call before any stream capture. Later calls reuse the address. The
+ *     address belongs to the device's primary context: after cudaDeviceReset on a device, do not call
+ *     this entry point on that device again in the same process.
  *   - No cudaMalloc, cudaFree or allocating library routine is called.
  *   - All calls on a device share the one array and leave the last call's tables in it; every call
  *     rewrites what it reads before reading it, so nothing needs clearing, but calls that overlap on the
  *     GPU (other streams or host threads on the same device) race on it: serialise them.
+ *   - The call waits for its own stream to finish before it returns, to read the status word.
  */
 wf_status wf_sample_noalloc(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, int32_t H,
                             int32_t W, uint64_t seed, const wf_sample_opts* opts, float* out, wf_stream_t stream);

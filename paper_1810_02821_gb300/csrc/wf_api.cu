@@ -463,7 +463,7 @@ void wf_solve_opts_default(wf_solve_opts* o) {
   o->level_max = 64;
   o->check = 4;
   o->max_iter = 20000;
-  o->refine = 0;
+  o->refine = 3;  // the returned residual is the FP64 residual of the returned map
   o->init_s = nullptr;
   o->refine_tol = 1e-3;
 }
@@ -1994,6 +1994,7 @@ wf_status wf_loglike_grad(const float* d, const float* sigma2, const uint8_t* ma
   // the probe solves only need an error far below the Monte-Carlo error of the trace estimate
   wf_solve_opts sp = so;
   sp.tol = tol > 1e-5 ? tol : 1e-5;
+  sp.refine = 0;  // plain FP32 iteration: its error is far below the trace estimate's
   double tsum[3] = {0, 0, 0}, tsq[3] = {0, 0, 0};
   for (int j = 0; j < n_probes; ++j) {
     k_rademacher<<<int((n / 4 + 255) / 256), 256, 0, st>>>(int(n), uint32_t(j), uint32_t(seed & 0xffffffffu),
@@ -2242,8 +2243,8 @@ wf_status wf_wiener_vjp(const float* d, const float* sigma2, const uint8_t* mask
 
 // ---------------------------------------------------------------------------------------------
 // wf_sample_noalloc: the sampler with its scratch in a static device array instead of cudaMallocAsync,
-// for callers that cannot allocate device memory when they call (graph capture, real-time loops, fixed
-// memory budgets).
+// for callers that cannot allocate device memory when they call (real-time loops that cannot wait on the
+// allocator, hosts whose device memory is all owned by their own pool or fixed in advance).
 // ---------------------------------------------------------------------------------------------
 namespace {
 
@@ -2255,7 +2256,10 @@ std::mutex g_noalloc_mu;
 void* g_noalloc_addr[kNoAllocMaxDevices] = {};
 
 // Device address of g_noalloc_scratch on the current device, looked up once per device. In host code
-// the array's name is only a host-side stand-in, so the kernels must be given this address.
+// the array's name is only a host-side stand-in, so the kernels must be given this address. The cached
+// address belongs to the device's primary context: it does not survive cudaDeviceReset, after which the
+// module is loaded again and the array may move (a process that resets a device must not call this
+// entry point on it afterwards).
 cudaError_t noalloc_scratch(void** ptr) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -2290,7 +2294,7 @@ wf_status wf_sample_noalloc(const float* d, const float* Ndiag, const uint8_t* m
   if (o.A) return WF_ERR_ARG;  // the response needs transformed copies of the inputs (device memory)
   if (o.out_dtype < WF_OUT_F32 || o.out_dtype > WF_OUT_F16) return WF_ERR_ARG;
   if (o.n_samples == 0) return WF_OK;
-  if (!out) return WF_ERR_ARG;
+  if (!out || !out_ptr_ok(out)) return WF_ERR_ARG;
   const long long sweeps = (long long)o.burn_in + o.n_samples * (long long)o.thin;
   if (sweeps > 0x7fffffffLL || o.n_samples > 0x7fffffffLL) return WF_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

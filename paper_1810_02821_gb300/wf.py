@@ -212,14 +212,16 @@ def wf_solve(d, Ndiag, mask, Pk, tau: float = 0.0, tol: float = 1e-6, out=None, 
 
 def wf_solve_ex(d, Ndiag, mask, Pk, *, tau: float = 0.0, tol: float = 1e-6, eta: float = 0.5,
                 level_tol: float = 1e-2, level_max: int = 64, check: int = 4, max_iter: int = 20000,
-                refine: int = 0, refine_tol: float = 1e-3, init_s=None, A=None, out=None, stream=None,
+                refine: int = 3, refine_tol: float = 1e-3, init_s=None, A=None, out=None, stream=None,
                 allow_not_converged: bool = False) -> SolveResult:
     """All options of the cooled Wiener-filter solve (C call ``wf_solve_ex``).
 
-    ``refine`` > 0 turns on mixed-precision iterative refinement: after the FP32 messenger solve, up to
-    ``refine`` corrections, each an FP32 messenger solve of (S^-1 + N^-1) e = r (to relative residual
-    ``refine_tol``) for the residual r = N^-1 (d - s) - S^-1 s evaluated in FP64. The returned residual is
-    then the FP64 relative residual ||S r|| / ||S N^-1 d||, and ``iters`` counts the sweeps of all solves.
+    ``refine`` > 0 (default 3) is mixed-precision iterative refinement: after the FP32 messenger solve (to
+    max(tol, 1e-5)), up to ``refine`` corrections, each an FP32 messenger solve of (S^-1 + N^-1) e = r (to
+    relative residual ``refine_tol``) for the residual r = N^-1 (d - s) - S^-1 s evaluated in FP64. The
+    returned residual is then the FP64 relative residual ||S r|| / ||S N^-1 d|| of the returned map, and
+    ``iters`` counts the sweeps of all solves. ``refine=0``: the plain FP32 iteration to ``tol``, whose
+    reported residual is its own estimate from consecutive FP32 iterates.
     ``A``: optional CUDA float32 [H][W] diagonal pixel response of d = A s + n.
     """
     import torch

@@ -1,5 +1,5 @@
 """GPU checks of the differentiation form: spectral powers vs numpy.fft, gradients vs the dense oracle
-(exact trace, 16x16) and vs central finite differences of the data term (256x256, h = 1e-3)."""
+(exact trace, 16x16) and vs central finite differences of the data term (256x256, h = 1e-3, to 1e-4)."""
 import numpy as np
 import pytest
 
@@ -69,7 +69,9 @@ def test_gradient_quad_term_matches_finite_differences_256():
         qp = wf.wf_loglike_grad(dev[0], dev[1], dev[2], tp[0], tp[1], k0, tp[2], tol=1e-7, with_trace=False).quad
         qm = wf.wf_loglike_grad(dev[0], dev[1], dev[2], tm[0], tm[1], k0, tm[2], tol=1e-7, with_trace=False).quad
         fd = (qp - qm) / (2 * h)
-        assert abs(r.grad_quad[i] - fd) < 1e-2 * abs(fd) + 1e-6, (i, r.grad_quad[i], fd)
+        # the solves' FP64 residual is below 1e-7, so the data term is accurate to far below what h = 1e-3
+        # differences need for 1e-4; the central difference's own truncation error is O(h^2)
+        assert abs(r.grad_quad[i] - fd) < 1e-4 * abs(fd) + 1e-6, (i, r.grad_quad[i], fd)
 
 
 def test_autograd_function_returns_the_gradient():

@@ -24,13 +24,33 @@ def _lib():
 
 
 def test_plain32_wiener_filter_matches_dense():
+    """The plain 32x32 case: a solve to relative residual 1e-6 delivers it. The residual the call reports is
+    the FP64 residual of the map it returns, so the oracle's own FP64 residual of that map agrees with it."""
     p = synth.config_plain32(0)
     r = wf.wf_solve(*to_dev(p), tol=1e-6)
     ref = dense.wiener_dense(p.d, p.Ndiag, p.mask, p.Pk)
     s = r.s.cpu().numpy()
     assert r.status == 0 and 0 < r.resid < 1e-6
     assert rel(s, ref) < WF_TOL
-    assert M.residual(s, p.d, p.Ndiag, p.mask, p.Pk) < 5e-6
+    rho = M.residual(s.astype(np.float64), p.d, p.Ndiag, p.mask, p.Pk)
+    assert rho < 1e-6
+    assert abs(rho - r.resid) <= 1e-3 * rho + 1e-14, (rho, r.resid)
+
+
+@pytest.mark.parametrize("H", [16, 32, 64, 128, 256, 512, 1024])
+def test_reported_residual_is_the_true_residual(H):
+    """At every size the default solve's reported residual is the FP64 residual of the returned map (the
+    oracle's, to 1e-3 of itself) and is below the requested tolerance."""
+    if H == 128:
+        p = synth.config_paper128(0)
+    elif H <= 64:
+        p = synth.make_problem(H, seed=H + 5, mask_frac=0.1, block=(1, H // 4, 2, H // 3))
+    else:
+        p = synth.make_problem(H, seed=H + 5, mask_frac=0.1, slope=-2.0, k0=1.0 / 32, sigma2=(0.05, 0.5))
+    r = wf.wf_solve(*to_dev(p), tol=1e-6)
+    assert r.status == 0 and 0 <= r.resid < 1e-6, (r.status, r.resid)
+    rho = M.residual(r.s.double().cpu().numpy(), p.d, p.Ndiag, p.mask, p.Pk)
+    assert rho < 1e-6 and abs(rho - r.resid) <= 1e-3 * rho + 1e-14, (H, rho, r.resid)
 
 
 def test_plain32_1000_samples_draw_for_draw():
@@ -153,7 +173,7 @@ def test_error_statuses():
     with pytest.raises(wf.WFError) as e:
         wf.wf_sample(d_nan, *dev[1:], 2, seed=1)
     assert e.value.status == 6
-    r = wf.wf_solve_ex(*dev, tol=1e-12, max_iter=3, allow_not_converged=True)
+    r = wf.wf_solve_ex(*dev, tol=1e-12, max_iter=3, refine=0, allow_not_converged=True)
     assert r.status == 5 and r.iters == 3
     out = torch.full((0, 32, 32), 0.0, device="cuda")
     assert wf.wf_sample(*dev, 0, seed=1, out=out).shape == (0, 32, 32)

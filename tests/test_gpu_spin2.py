@@ -10,6 +10,7 @@ from paper_1810_02821_gb300 import build, synth, wf
 pytestmark = pytest.mark.gpu
 
 SAMPLE_TOL = 1e-4
+WF_TOL = 1e-5
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -62,5 +63,6 @@ def test_spin2_wiener_filter_matches_dense(H):
     r = wf.wf_solve_spin2(*_dev(p.d, d2, p.Ndiag, N2, p.mask, p.Pk, PB), tol=5e-6)
     got = r.s.cpu().numpy()
     print(f"spin-2 WF {H}: resid {r.resid:.2e} sweeps {r.iters} err {rel(got[0], ref[0]):.2e} {rel(got[1], ref[1]):.2e}")
+    # the reported residual is the FP64 residual of the returned pair (summed on the GPU in FP64)
     assert r.status == 0 and r.resid < 5e-6
-    assert rel(got[0], ref[0]) < 2e-5 and rel(got[1], ref[1]) < 2e-5
+    assert rel(got[0], ref[0]) < WF_TOL and rel(got[1], ref[1]) < WF_TOL

@@ -1,10 +1,11 @@
 """wf_sample_noalloc: the sampler for callers that cannot allocate device memory at call time.
 
-Such callers (code inside CUDA-graph capture, real-time loops that cannot afford the allocator, programs
-with a fixed memory budget) get the same samples as wf_sample_ex, with the scratch tables kept in a
-static device array inside the library. The test calls the entry point through the C ABI twice in a row
-(different image sizes, so the second call runs on the first call's leftover scratch contents) and
-compares each result with wf_sample_ex within the sampler tolerance of the other GPU tests.
+Such callers (real-time loops that cannot wait on the allocator, host applications whose device memory
+is all owned by their own pool or fixed in advance) get the same samples as wf_sample_ex, with the
+scratch tables kept in a static device array inside the library. The test calls the entry point through
+the C ABI twice in a row (different image sizes, so the second call runs on the first call's leftover
+scratch contents) and compares each result with wf_sample_ex within the sampler tolerance of the other
+GPU tests.
 """
 import ctypes
 
@@ -58,12 +59,32 @@ def test_noalloc_matches_allocating_sampler_twice():
 
 
 def test_noalloc_rejects_oversized_and_bad_arguments():
+    """Every rejected call is refused before a launch; real device buffers are passed anyway, so a
+    reordering of the checks could not send a kernel to a bogus address."""
     need_gpu()
     build.build()
     L, fn = _entry()
-    p = ctypes.c_void_p(16)
     o = wf.SampleOpts()
     L.wf_sample_opts_default(ctypes.byref(o))
     o.n_samples = 1
-    assert fn(p, p, p, p, 256, 256, 0, ctypes.byref(o), p, None) == 3      # beyond the static scratch
-    assert fn(None, p, p, p, 32, 32, 0, ctypes.byref(o), p, None) == 1
+    big = torch.zeros(256 * 256, device="cuda")
+    bm = torch.zeros(256 * 256, dtype=torch.uint8, device="cuda")
+    ptr = big.data_ptr()
+    # beyond the static scratch
+    assert fn(ptr, ptr, bm.data_ptr(), ptr, 256, 256, 0, ctypes.byref(o), ptr, None) == 3
+    # a null input
+    assert fn(None, ptr, bm.data_ptr(), ptr, 32, 32, 0, ctypes.byref(o), ptr, None) == 1
+
+
+def test_noalloc_output_in_mapped_host_memory():
+    """The output pointer passes the same check as wf_sample_ex's: page-locked host memory that the
+    device can address is accepted, and the kernel's stores there equal a device-buffer call."""
+    need_gpu()
+    build.build()
+    p = synth.config_plain32(0)
+    host = torch.full((2, 3, 32, 32), float("nan")).pin_memory()
+    st, dev = _noalloc(p, 5, 3, 2, host)
+    torch.cuda.synchronize()
+    assert st == 0, wf.load_library().wf_status_string(st)
+    ref = wf.wf_sample_ex(*dev, seed=5, n_samples=3, n_chains=2)
+    assert torch.equal(host, ref.cpu())
