@@ -11,7 +11,8 @@ Printed JSON line (rank 0):
   e2e        same metric through the same C call with host buffers: pinned H2D of the inputs, and every
              sample stored by the kernel into page-locked host memory, inside the timed region
   roofline   the fused sampler kernel k_sample<128,1>: FFT flops (5 n log2 n per sweep) per launch over
-             its event-timed duration, against the FP32 peak derived from the SM count and max clock
+             its event-timed duration, against the FP32 FMA throughput measured on the device
+             (wf_measure_fp32_peak: every SM filled with independent FMA chains, CUDA events, best launch)
   cpu_baseline  the FP64 oracle on the host cores, on a bounded sample of the same workload
   batched_vs_plain  the 1024-chain launch against one chain per launch
   batch_mixed_sizes 4096 images of mixed sizes (40% 64^2, 40% 128^2, 15% 256^2, 5% 512^2), each a Wiener
@@ -51,8 +52,10 @@ N_SAMPLES = 100
 METRIC = "128x128 Wiener-posterior samples/s (1 GB300)"
 UNIT = "samples/s"
 FLOPS_PER_SWEEP = 5.0 * H * W * math.log2(H * W)   # two real 2D FFTs at 2.5 n log2 n each
-SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # FMA = 2 flops
+FP32_LANES = 128   # FP32 FMA lanes per SM (for the derived figure shown beside the measured peak)
+# FP32 roofline denominator: measured on the device by wf_measure_fp32_peak before the extra workloads
+# (set in main); the derived SMs x lanes x 2 x max clock figure is reported only as a note
+FP32_PEAK_TFLOPS = None
 WORKLOAD = "paper-shaped 128x128 image, 1024 independent chains x 100 posterior samples per step"
 PROFILE = os.path.join(ROOT, "profiles", "k_sample_128_paper128.txt")
 
@@ -191,6 +194,36 @@ class ClockSampler:
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def measure_fp32_peak(dev, local: int, target_ms: float = 7.0, reps: int = 5):
+    """FP32 FMA throughput of this GPU: launches of the library's FMA-rate kernel (scalar FFMA and the
+    paired FFMA2 form) sized to about the headline kernel's launch length, best of ``reps`` each, with the
+    SM clock sampled meanwhile. Changes no device setting."""
+    import torch
+    from paper_1810_02821_gb300 import wf
+    props = torch.cuda.get_device_properties(dev)
+    out = {}
+    with ClockSampler(local) as clk:
+        for paired in (False, True):
+            _, ms = wf.wf_measure_fp32_peak(paired, 4096)                 # warm-up and calibration
+            iters = max(1024, int(4096 * target_ms / max(ms, 1e-3)))
+            best = 0.0
+            for _ in range(reps):
+                tf, ms = wf.wf_measure_fp32_peak(paired, iters)
+                best = max(best, tf)
+            out["paired_tflops" if paired else "scalar_tflops"] = best
+            out["paired_ms" if paired else "scalar_ms"] = ms
+    c = clk.summary()
+    sms = props.multi_processor_count
+    mx = c.get("sm_max_mhz") or 2070.0
+    out.update({"tflops": max(out["scalar_tflops"], out["paired_tflops"]), "sms": sms,
+                "sm_mhz_median": c.get("sm_mhz"), "sm_max_mhz": c.get("sm_max_mhz"), "reasons": c.get("reasons"),
+                "derived_tflops": sms * FP32_LANES * 2 * mx * 1e6 / 1e12,
+                "how": f"wf_measure_fp32_peak: {sms} SMs x full occupancy x 256 threads x 16 independent FMA "
+                       f"chains, scalar and paired forms, best of {reps} launches of ~{target_ms:.0f} ms each "
+                       "(CUDA events)"})
+    return out
 
 
 def cpu_baseline(target_s: float = 12.0):
@@ -515,7 +548,7 @@ def large_sampler(dev, chains256: int = 456, samples256: int = 20):
 
 
 def main():
-    global N_CHAINS, N_SAMPLES
+    global N_CHAINS, N_SAMPLES, FP32_PEAK_TFLOPS
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
@@ -567,6 +600,8 @@ def main():
         barrier()
     total_ms = max_over_ranks(sum(step_ms), world, dev)
     value = aggregate_throughput(N_CHAINS * N_SAMPLES * a.steps, world, total_ms)
+    fp32_peak = measure_fp32_peak(dev, local)
+    FP32_PEAK_TFLOPS = fp32_peak["tflops"]
 
     # end to end through the same call with host buffers: each step copies its inputs from pinned host
     # memory to the device and the kernel stores its samples straight into a page-locked host buffer over
@@ -663,7 +698,10 @@ def main():
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
                      "kernel": "wf::k_sample<128,1>", "kernel_ms": kms,
                      "flops_per_launch": flops,
-                     "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x 2070 MHz (derived, not measured)"},
+                     "peak_note": "of measured: FP32 FMA throughput of this GPU (fp32_peak); derived "
+                                  f"{fp32_peak['sms']} SMs x {FP32_LANES} lanes x 2 x max clock = "
+                                  f"{fp32_peak['derived_tflops']:.1f} TFLOP/s shown only as a note"},
+        "fp32_peak": fp32_peak,
         "batched_vs_plain": ({"batched": value, "plain_one_chain_per_launch": plain, "speedup": value / plain,
                               "plain_chains_timed": n_plain} if plain else None),
         "single_chain_sweeps_per_s": single,

@@ -380,6 +380,19 @@ wf_status wf_wiener_vjp(const float* d, const float* sigma2, const uint8_t* mask
  */
 wf_status wf_selftest_wait_timeout(int32_t n_blocks, double* elapsed_ms);
 
+/*
+ * FP32 fused multiply-add throughput of the current device, measured: the denominator of the FP32
+ * roofline the transforms' 5 n log2 n flops per sweep are reported against (the paper's method has no
+ * dense contraction, so its bound is the FP32 pipe, not the tensor cores). One launch fills every SM to
+ * its occupancy limit with CTAs of 256 threads, each thread running 16 independent chains of `iters`
+ * FMAs (paired = 0: scalar FFMA; paired = 1: the paired form, two FMAs per instruction), timed with CUDA
+ * events on `stream`; the call waits for it. tflops_out (HOST, may be NULL): 2 x FMAs / time in TFLOP/s;
+ * ms_out (HOST, may be NULL): the launch's duration. iters in 1 .. 2^40, else WF_ERR_ARG. Changes no
+ * device setting. The paper has no counterpart: this is measurement infrastructure.
+ */
+wf_status wf_measure_fp32_peak(int32_t paired, int64_t iters, double* tflops_out, double* ms_out,
+                               wf_stream_t stream);
+
 /* 1 if (H, W) is supported by wf_solve / wf_sample, else 0. */
 int32_t wf_supported_size(int32_t H, int32_t W);
 

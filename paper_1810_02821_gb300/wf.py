@@ -130,6 +130,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.wf_loglike_grad_batch.restype = ctypes.c_int
     L.wf_selftest_wait_timeout.argtypes = [I32, ctypes.POINTER(D)]
     L.wf_selftest_wait_timeout.restype = ctypes.c_int
+    L.wf_measure_fp32_peak.argtypes = [I32, ctypes.c_int64, ctypes.POINTER(D), ctypes.POINTER(D), P]
+    L.wf_measure_fp32_peak.restype = ctypes.c_int
     L.wf_wiener_vjp.argtypes = [P, P, P, I32, I32, ctypes.POINTER(D), P, P, D, ctypes.POINTER(D), P, P]
     L.wf_wiener_vjp.restype = ctypes.c_int
     L.wf_set_large_image_sampler.argtypes = [I32]
@@ -718,3 +720,14 @@ def wf_selftest_wait_timeout(n_blocks: int = 64):
     ms = ctypes.c_double(0.0)
     st = L.wf_selftest_wait_timeout(int(n_blocks), ctypes.byref(ms))
     return st, ms.value
+
+
+def wf_measure_fp32_peak(paired: bool = False, iters: int = 65536, stream=None):
+    """Measured FP32 FMA throughput of the current device (C call ``wf_measure_fp32_peak``) ->
+    (TFLOP/s, ms) of one launch that fills every SM with independent FMA chains."""
+    L = load_library()
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    st = L.wf_measure_fp32_peak(1 if paired else 0, int(iters), ctypes.byref(tf), ctypes.byref(ms),
+                                _stream_ptr(stream))
+    _check(st, "wf_measure_fp32_peak")
+    return tf.value, ms.value

@@ -72,7 +72,7 @@ def test_product_path_has_no_oracle_import():
 def test_refine_options_validated_without_gpu(lib):
     o = wf.SolveOpts()
     lib.wf_solve_opts_default(ctypes.byref(o))
-    assert o.refine == 0 and o.refine_tol == 1e-3 and not o.init_s
+    assert o.refine == 3 and o.refine_tol == 1e-3 and not o.init_s
     p = ctypes.c_void_p(16)
     it, rs = ctypes.c_int32(0), ctypes.c_double(0.0)
     for field, value in (("refine", -1), ("refine_tol", 0.0)):
