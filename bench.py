@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--extras", default="batch,plain,precision,grad,bf16,band,spin2,large",
                     help="extra workloads (comma list of batch, plain, precision, grad, bf16, band, spin2, large)")
     ap.add_argument("--batch-images", type=int, default=4096, help="images of the mixed-size batch")
+    ap.add_argument("--batch-samples", type=int, default=64,
+                    help="profiling only: samples per image of the mixed-size batch (0: Wiener solves only)")
     ap.add_argument("--batch-large-streams", type=int, default=8,
                     help="large-image chunks per size class of the untuned batch replay")
     ap.add_argument("--chains", type=int, default=N_CHAINS, help="profiling only: chains per step")
@@ -318,9 +320,11 @@ def batch_mixed(dev, n_images: int = 4096, n_samples: int = 64, n_plain: int = 6
     t0 = time.perf_counter()
     for i in range(n_plain):
         im = imgs[i]
-        r = wf.wf_solve_ex(im.d, im.Ndiag, im.mask, im.Pk, tol=1e-5, allow_not_converged=True)
-        wf.wf_sample_ex(im.d, im.Ndiag, im.mask, im.Pk, seed=i, n_samples=n_samples, chain_offset=i, init_s=r.s,
-                        out=im.out_samples.unsqueeze(0))
+        # the batch's own solve: the plain FP32 iteration to 1e-5 (no FP64 refinement)
+        r = wf.wf_solve_ex(im.d, im.Ndiag, im.mask, im.Pk, tol=1e-5, refine=0, allow_not_converged=True)
+        if n_samples > 0:
+            wf.wf_sample_ex(im.d, im.Ndiag, im.mask, im.Pk, seed=i, n_samples=n_samples, chain_offset=i,
+                            init_s=r.s, out=im.out_samples.unsqueeze(0))
     torch.cuda.synchronize()
     plain_ms_per_image = (time.perf_counter() - t0) * 1e3 / n_plain
     plain_pix = sum(sizes[:n_plain])
@@ -668,7 +672,8 @@ def main():
         want = set(a.extras.split(","))
         jobs = [(k, name, fn) for k, name, fn in (
             ("batch", "batch_mixed_sizes",
-             lambda dv: batch_mixed(dv, n_images=a.batch_images, large_streams=a.batch_large_streams)),
+             lambda dv: batch_mixed(dv, n_images=a.batch_images, n_samples=a.batch_samples,
+                                    large_streams=a.batch_large_streams)),
             ("plain", "plain_32x32", plain_32), ("precision", "precision_1024x1024", precision_1024),
             ("grad", "differentiation_256x256", differentiation_256),
             ("bf16", "bf16_sample_storage", reduced_output),

@@ -252,7 +252,11 @@ typedef struct {
                              the occupancy limit (1..100; 0 = 100) */
   int32_t large_grid_pct; /* launch shape: CTAs of each cooperative launch for larger images, in percent of
                              the co-resident limit (1..100; 0 = 100); smaller grids let pipelines overlap */
-  int32_t reserved;
+  int32_t small_path;  /* images up to 128 x 128: 0 (default) = phased: per-image set-up and tables, then one
+                          launch of every image's solve (a CTA each) and one of every image's samples (as
+                          many images per CTA as the single-image sampler puts chains); 1 = fused: one
+                          persistent kernel per size whose CTAs take images from a work counter and run the
+                          whole pipeline each (small_grid_pct applies) */
 } wf_batch_opts;
 
 void wf_batch_opts_default(wf_batch_opts* o);
@@ -262,8 +266,8 @@ wf_status wf_batch_run(wf_batch_item* items, int32_t n_items, const wf_batch_opt
  * The batched form recorded once as a CUDA graph and replayed. wf_batch_graph_create validates the items
  * and options exactly as wf_batch_run, allocates the batch's scratch for the graph's lifetime (device
  * memory, freed by wf_batch_graph_destroy), uploads the item table and captures the whole batch -- the
- * resets of the work counters and statuses, one persistent launch per size class up to 128 x 128 and the
- * cooperative pipelines of the larger images, forked over streams and joined -- into one graph.
+ * resets of the work counters and statuses, the launches of every size class up to 128 x 128 (phased or
+ * fused, small_path) and the pipelines of the larger images, forked over streams and joined -- into one graph.
  *   - wf_batch_graph_launch enqueues one replay on `stream` and returns without waiting. Every replay
  *     recomputes every item from its inputs as they are in device memory when it runs (the pointers are
  *     fixed at creation). Replays share the graph's scratch: launch them on one stream (or order them).
@@ -284,7 +288,8 @@ void wf_batch_graph_destroy(wf_batch_graph g);
  * Launch-shape autotuner of the batched form. Starting from *opts, it times graph replays of this batch
  * (one warm-up and `reps` timed replays per candidate, CUDA events on `stream`) and keeps, one knob at a
  * time, the fastest large_grid_pct in {100, 50, 25, 12}, large_streams in {1, 2, 4, 8, 16} (when the batch has
- * images above 128 x 128) and small_grid_pct in {100, 50, 25}; the chosen values are written back to *opts and the
+ * images above 128 x 128), small_path in {0, 1} and, for the fused path, small_grid_pct in {100, 50, 25} (when
+ * it has images up to 128 x 128); the chosen values are written back to *opts and the
  * best replay time to *best_ms (HOST, may be NULL). The items' outputs are overwritten by the trial runs.
  * A representative subset of a large batch tunes faster than the whole batch.
  */

@@ -1272,6 +1272,54 @@ std::vector<wf::GBField> chunk_fields(const GBChunk& c, const std::vector<wf::Ba
   return v;
 }
 
+// A size class up to 128 x 128 in the phased form (small_path 0): per-image set-up, tables, then one
+// k_bsolve launch and one k_bsample launch over all its images. Per-image buffers: pixel tables aq, dn [n],
+// mode table fg [nm], previous Wiener iterate [H][W/2], and s_W [n] for images without an out_wf.
+struct SmallClass {
+  int H = 0;
+  std::vector<int> items;
+  size_t o_fields = 0, o_idx = 0, o_sc = 0, o_data = 0, per_field = 0;
+  size_t f_aq = 0, f_dn = 0, f_fg = 0, f_prev = 0, f_sw = 0;
+};
+
+void layout_small(SmallClass& c, Carve& cv) {
+  const int H = c.H, F = int(c.items.size());
+  const size_t n = size_t(H) * H, nm = size_t(H) * (H / 2 + 1), nz = size_t(H) * (H / 2);
+  c.o_fields = cv.take<wf::GBField>(F);
+  c.o_idx = cv.take<int>(F);
+  c.o_sc = cv.take<wf::Scalars>(F);
+  Carve f;
+  c.f_aq = f.take<float2>(n);
+  c.f_dn = f.take<float2>(n);
+  c.f_fg = f.take<float2>(nm);
+  c.f_prev = f.take<float2>(nz);
+  c.f_sw = f.take<float>(n);
+  c.per_field = f.off;
+  c.o_data = cv.take<char>(c.per_field * size_t(F));
+}
+
+std::vector<wf::GBField> small_fields(const SmallClass& c, const std::vector<wf::BatchItem>& items, char* b) {
+  std::vector<wf::GBField> v(c.items.size());
+  for (size_t f = 0; f < c.items.size(); ++f) {
+    const wf::BatchItem& it = items[c.items[f]];
+    char* base = b + c.o_data + f * c.per_field;
+    wf::GBField& g = v[f];
+    g.aq = reinterpret_cast<const float2*>(base + c.f_aq);
+    g.dn = reinterpret_cast<const float2*>(base + c.f_dn);
+    g.fg = reinterpret_cast<const float2*>(base + c.f_fg);
+    g.Pk = it.Pk;
+    g.Z = nullptr;
+    g.prev = reinterpret_cast<float2*>(base + c.f_prev);
+    g.out_wf = it.out_wf ? it.out_wf : reinterpret_cast<float*>(base + c.f_sw);  // s_W always kept
+    g.out_samples = it.out_samples;
+    g.chain = it.chain;
+    g.key0 = uint32_t(it.seed & 0xffffffffu);
+    g.key1 = uint32_t(it.seed >> 32);
+    g.item = c.items[f];
+  }
+  return v;
+}
+
 // per-field set-up: one block per field (as k_prep)
 __global__ void k_prep_fields(const wf::BatchItem* __restrict__ items, const int* __restrict__ idx, int H,
                               double tau_user, double eta, wf::Scalars* sc) {
@@ -1332,6 +1380,60 @@ cudaError_t launch_gbatch_any(int H, const wf::GBArgs& a, cudaStream_t st) {
     case 1024: return wf::launch_gbatch<1024>(a, st);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_bsolve_any(int H, const wf::BSolveArgs& a, cudaStream_t st) {
+  switch (H) {
+    case 16: return wf::launch_bsolve<16>(a, st);
+    case 32: return wf::launch_bsolve<32>(a, st);
+    case 64: return wf::launch_bsolve<64>(a, st);
+    case 128: return wf::launch_bsolve<128>(a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t launch_bsample_any(int H, const wf::BSampleArgs& a, cudaStream_t st) {
+  switch (H) {
+    case 16: return wf::launch_bsample<16>(a, st);
+    case 32: return wf::launch_bsample<32>(a, st);
+    case 64: return wf::launch_bsample<64>(a, st);
+    case 128: return wf::launch_bsample<128>(a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// the phased pipeline of one small size class on stream st (item table uploaded, descriptors in place)
+wf_status run_small(const SmallClass& c, const wf::BatchItem* d_items, wf::BatchResult* d_res,
+                    const wf_batch_opts& o, char* b, cudaStream_t st) {
+  const int F = int(c.items.size()), H = c.H;
+  auto* fields = reinterpret_cast<wf::GBField*>(b + c.o_fields);
+  auto* idx = reinterpret_cast<int*>(b + c.o_idx);
+  auto* sc = reinterpret_cast<wf::Scalars*>(b + c.o_sc);
+  k_prep_fields<<<F, 1024, 0, st>>>(d_items, idx, H, o.tau, o.eta, sc);
+  WF_CUDA(cudaGetLastError());
+  const long long tab = (long long)F * (size_t(H) * H + size_t(H) * (H / 2 + 1));
+  k_tables_fields<<<int((tab + 255) / 256 < 4096 ? (tab + 255) / 256 : 4096), 256, 0, st>>>(d_items, idx, fields,
+                                                                                           sc, F, H, 0);
+  WF_CUDA(cudaGetLastError());
+  wf::BSolveArgs sa{};
+  sa.fields = fields;
+  sa.sc = sc;
+  sa.res = d_res;
+  sa.F = F;
+  sa.tol = o.tol;
+  sa.eta = o.eta;
+  sa.level_tol = o.level_tol;
+  sa.max_iter = o.max_iter;
+  sa.level_max = o.level_max;
+  sa.check = o.check;
+  cudaError_t e = launch_bsolve_any(H, sa, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  wf::BSampleArgs pa{};
+  pa.fields = fields;
+  pa.sc = sc;
+  pa.F = F;
+  pa.n_samples = o.n_samples;
+  if ((e = launch_bsample_any(H, pa, st)) != cudaSuccess) return cuda_fail(e);
+  return WF_OK;
 }
 
 // set-up and launch of one chunk on stream st (item table uploaded, descriptors in place)
@@ -1436,12 +1538,13 @@ struct BatchPlan {
   size_t o_items = 0, o_order = 0, o_res = 0, o_q = 0, o_slot[4] = {0, 0, 0, 0}, bytes = 0;
   int nls = 0;                  // streams of the large-image chunks
   std::vector<GBChunk> chunks;  // large images: one cooperative launch each
+  std::vector<SmallClass> small;  // phased small classes (small_path 0)
 };
 
 bool batch_opts_ok(const wf_batch_opts& o) {
   return o.tol >= 0.0 && o.eta > 0.0 && o.eta < 1.0 && o.level_max >= 1 && o.check >= 1 && o.max_iter >= 1 &&
          o.n_samples >= 0 && o.large_streams >= 1 && o.small_grid_pct >= 0 && o.small_grid_pct <= 100 &&
-         o.large_grid_pct >= 0 && o.large_grid_pct <= 100;
+         o.large_grid_pct >= 0 && o.large_grid_pct <= 100 && (o.small_path == 0 || o.small_path == 1);
 }
 
 wf_status plan_batch(const wf_batch_item* items, int n_items, const wf_batch_opts& o, BatchPlan* p) {
@@ -1465,8 +1568,17 @@ wf_status plan_batch(const wf_batch_item* items, int n_items, const wf_batch_opt
   p->o_order = cv.take<int>(n_items);
   p->o_res = cv.take<wf::BatchResult>(n_items);
   p->o_q = cv.take<int>(8);
+  p->small.clear();
   for (int c = 0; c < 4; ++c) {
     if (p->cls[c].empty()) continue;
+    if (o.small_path == 0) {
+      SmallClass sc;
+      sc.H = kBatchSizes[c];
+      sc.items = p->cls[c];
+      layout_small(sc, cv);
+      p->small.push_back(std::move(sc));
+      continue;
+    }
     int grid = 0;
     cudaError_t e = batch_grid_any(kBatchSizes[c], int(p->cls[c].size()), o.small_grid_pct, &grid);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -1528,8 +1640,14 @@ wf_status record_batch(const BatchPlan& p, char* b, cudaStream_t st, ForkJoin& f
     return cudaStreamWaitEvent(*out, ready, 0);
   };
   wf_status fail = WF_OK;
+  for (size_t k = 0; k < p.small.size() && fail == WF_OK; ++k) {
+    cudaStream_t s2;
+    cudaError_t e = new_stream(&s2);
+    if (e != cudaSuccess) { fail = cuda_fail(e); break; }
+    fail = run_small(p.small[k], d_items, d_res, o, b, s2);
+  }
   int offset = 0;
-  for (int c = 0; c < 4 && fail == WF_OK; ++c) {
+  for (int c = 0; c < 4 && fail == WF_OK && o.small_path == 1; ++c) {
     if (p.cls[c].empty()) continue;
     cudaStream_t s2;
     cudaError_t e = new_stream(&s2);
@@ -1582,6 +1700,15 @@ wf_status upload_batch(const BatchPlan& p, char* b, cudaStream_t st, std::vector
   WF_CUDA(cudaMemcpyAsync(b + p.o_items, p.dev_items.data(), p.n_items * sizeof(wf::BatchItem), cudaMemcpyHostToDevice,
                           st));
   WF_CUDA(cudaMemcpyAsync(b + p.o_order, p.order.data(), p.n_items * sizeof(int), cudaMemcpyHostToDevice, st));
+  for (const SmallClass& c : p.small) {
+    const std::vector<wf::GBField> fv = small_fields(c, p.dev_items, b);
+    keep.emplace_back(reinterpret_cast<const char*>(fv.data()),
+                      reinterpret_cast<const char*>(fv.data()) + fv.size() * sizeof(wf::GBField));
+    WF_CUDA(cudaMemcpyAsync(b + c.o_fields, keep.back().data(), keep.back().size(), cudaMemcpyHostToDevice, st));
+    keep.emplace_back(reinterpret_cast<const char*>(c.items.data()),
+                      reinterpret_cast<const char*>(c.items.data()) + c.items.size() * sizeof(int));
+    WF_CUDA(cudaMemcpyAsync(b + c.o_idx, keep.back().data(), keep.back().size(), cudaMemcpyHostToDevice, st));
+  }
   for (const GBChunk& c : p.chunks) {
     const std::vector<wf::GBField> fv = chunk_fields(c, p.dev_items, b);
     keep.emplace_back(reinterpret_cast<const char*>(fv.data()),
@@ -1760,7 +1887,12 @@ wf_status wf_batch_autotune(const wf_batch_item* items, int32_t n_items, wf_batc
     try_knob(&wf_batch_opts::large_grid_pct, {100, 50, 25, 12});
     try_knob(&wf_batch_opts::large_streams, {1, 2, 4, 8, 16});
   }
-  try_knob(&wf_batch_opts::small_grid_pct, {100, 50, 25});
+  bool has_small = false;
+  for (int i = 0; i < n_items; ++i) has_small |= items[i].H <= 128;
+  if (has_small) {
+    try_knob(&wf_batch_opts::small_path, {0, 1});
+    if (best.small_path == 1) try_knob(&wf_batch_opts::small_grid_pct, {100, 50, 25});
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (r != WF_OK) return r;

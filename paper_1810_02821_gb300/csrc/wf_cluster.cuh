@@ -271,49 +271,45 @@ __device__ __forceinline__ void cdraw_pair(float2& y1, float2& y2, int K, int ky
   }
 }
 
-// Cross-cluster radix-P stage. Work unit (slot t, k' = u with its mirror v = M - u): gathers Y_j[u]
-// (and Y_j[v]) from every CTA j, forms the column spectrum t_hat[u + M m], hands every mode pair
-// (ky1 < N/2, ky2 = N - ky1, or N/2 when ky1 = 0) of column K to fn(K, y1, y2, ky1, ky2), and with WRITE
-// scatters the inverse stage back. g = the thread's index in the cluster. Every mode of the half spectrum
-// is in exactly one pair of one unit.
+// Cross-cluster radix-P stage. Work unit (slot t, k' = u with its mirror v = M - u; u = 0 is paired with
+// u = M/2, the two half-size units): gathers Y_j[u] (and Y_j[v]) from every CTA j, forms the column spectrum
+// t_hat[u + M m], hands every mode pair (ky1 < N/2, ky2 = N - ky1, or N/2 when ky1 = 0) of column K to
+// fn(K, y1, y2, ky1, ky2), and with WRITE scatters the inverse stage back. g = the thread's index in the
+// cluster. Every mode of the half spectrum is in exactly one pair of one unit, and there are L M / 2 units
+// of equal size, a whole number per thread of the cluster (one each at 512^2, eight at 256^2).
 template <int N, bool WRITE, class F>
 __device__ __forceinline__ void ccol_units(cooperative_groups::cluster_group& cl, float2* rows, int g, F&& fn) {
   using G = CGeo<N>;
   constexpr int P = G::P, L = G::L, R = G::R;
   constexpr int M = G::M;
-  for (int w = g; w < L * (M / 2 + 1); w += P * L) {
-    const int t = w % L, u = w / L, v = M - u;
+  static_assert((L * (M / 2)) % (P * L) == 0, "equal work units per thread");
+  for (int w = g; w < L * (M / 2); w += P * L) {
+    const int t = w % L, u = w / L, v = u == 0 ? M / 2 : M - u;
     const int K = (t % R) * M + t / R;  // kx held by slot t
-    const bool two = u != 0 && u != M / 2;
     float2 p[P], q[P];
 #pragma unroll
     for (int j = 0; j < P; ++j) p[j] = cl.map_shared_rank(rows, j)[u * G::SP + t];
-    if (two) {
 #pragma unroll
-      for (int j = 0; j < P; ++j) q[j] = cl.map_shared_rank(rows, j)[v * G::SP + t];
-    }
+    for (int j = 0; j < P; ++j) q[j] = cl.map_shared_rank(rows, j)[v * G::SP + t];
     fft<P, false>(p);  // p[m] = t_hat[u + M m]
+    fft<P, false>(q);  // q[m] = t_hat[v + M m]
     if (u == 0) {
       fn(K, p[0], p[P / 2], 0, N / 2);
 #pragma unroll
       for (int m = 1; m < P / 2; ++m) fn(K, p[m], p[P - m], M * m, N - M * m);
-    } else if (u == M / 2) {
 #pragma unroll
-      for (int m = 0; m < P / 2; ++m) fn(K, p[m], p[P - 1 - m], M / 2 + M * m, N - M / 2 - M * m);
+      for (int m = 0; m < P / 2; ++m) fn(K, q[m], q[P - 1 - m], M / 2 + M * m, N - M / 2 - M * m);
     } else {
-      fft<P, false>(q);  // q[m] = t_hat[v + M m]
 #pragma unroll
       for (int m = 0; m < P / 2; ++m) {
         fn(K, p[m], q[P - 1 - m], u + M * m, N - u - M * m);
         fn(K, q[m], p[P - 1 - m], v + M * m, N - v - M * m);
       }
-      if (WRITE) {
-        fft<P, true>(q);
-#pragma unroll
-        for (int j = 0; j < P; ++j) cl.map_shared_rank(rows, j)[v * G::SP + t] = q[j];
-      }
     }
     if (WRITE) {
+      fft<P, true>(q);
+#pragma unroll
+      for (int j = 0; j < P; ++j) cl.map_shared_rank(rows, j)[v * G::SP + t] = q[j];
       fft<P, true>(p);
 #pragma unroll
       for (int j = 0; j < P; ++j) cl.map_shared_rank(rows, j)[u * G::SP + t] = p[j];
@@ -333,7 +329,8 @@ __device__ __forceinline__ void ccol_draw(cooperative_groups::cluster_group& cl,
 
 // Wiener-filter update at level lambda (G -> 0): s_hat = f t_hat with f = P / (P + lambda tau) (scaled by
 // 1/n). With CMP the residual of the previous iterate, |s_hat_new - s_hat_old|^2 (1 + P / (lambda tau))^2,
-// is summed over the full spectrum (the mirror modes counted; returned as this thread's share); with STORE
+// is summed over the full spectrum (the mirror modes counted; returned as this thread's share, summed in
+// FP32 over its units); with STORE
 // the new modes go to prev[ky * W/2 + K] (packed edge column as stored).
 template <int N>
 __device__ __forceinline__ double ccol_wf(cooperative_groups::cluster_group& cl, float2* rows, int g,
@@ -343,19 +340,19 @@ __device__ __forceinline__ double ccol_wf(cooperative_groups::cluster_group& cl,
   constexpr int WH = G::WH, LR = G::L;
   constexpr float INV_N = 1.0f / float(G::H * G::W);
   const float inv_lt = 1.0f / lt_;
-  auto wres = [&](float P, float dre, float dim) -> double {
+  auto wres = [&](float P, float dre, float dim) -> float {
     const float q = fmaf(P, inv_lt, 1.0f);
-    return double(fmaf(dre, dre, dim * dim) * (q * q));
+    return fmaf(dre, dre, dim * dim) * (q * q);
   };
   auto fcoef = [&](float P) { return wf_fdiv(P, P + lt_) * INV_N; };
-  double acc = 0.0;
+  float acc = 0.0f;  // this thread's units in FP32; the cluster sum is FP64
   ccol_units<N, true>(cl, rows, g, [&](int K, float2& y1, float2& y2, int ky1, int ky2) {
     if (K != 0) {
       const float P1 = WF_LDG(Pk + ky1 * WH + K), P2 = WF_LDG(Pk + ky2 * WH + K);
       const float2 n1 = cscale(y1, fcoef(P1)), n2 = cscale(y2, fcoef(P2));
       if (cmp) {
         const float2 o1 = prev[ky1 * LR + K], o2 = prev[ky2 * LR + K];
-        acc += 2.0 * (wres(P1, n1.x - o1.x, n1.y - o1.y) + wres(P2, n2.x - o2.x, n2.y - o2.y));
+        acc += 2.0f * (wres(P1, n1.x - o1.x, n1.y - o1.y) + wres(P2, n2.x - o2.x, n2.y - o2.y));
       }
       y1 = n1;
       y2 = n2;
@@ -381,7 +378,7 @@ __device__ __forceinline__ double ccol_wf(cooperative_groups::cluster_group& cl,
           const float2 o1 = prev[ky1 * LR], o2c = cconj(prev[ky2 * LR]);
           const float2 oA = cscale(cadd(o1, o2c), 0.5f);
           const float2 oB = cmul_mi(cscale(csub(o1, o2c), 0.5f));
-          acc += 2.0 * (wres(Pa1, A.x - oA.x, A.y - oA.y) + wres(Pb1, B.x - oB.x, B.y - oB.y));
+          acc += 2.0f * (wres(Pa1, A.x - oA.x, A.y - oA.y) + wres(Pb1, B.x - oB.x, B.y - oB.y));
         }
         y1 = cadd(A, cmul_i(B));
         y2 = cadd(cconj(A), cmul_i(cconj(B)));
@@ -392,7 +389,7 @@ __device__ __forceinline__ double ccol_wf(cooperative_groups::cluster_group& cl,
       prev[ky2 * LR + K] = y2;
     }
   });
-  return acc;
+  return double(acc);
 }
 
 // sum over the full spectrum of P^2 |V|^2 for the forward transform V (level norms); this thread's share
@@ -401,11 +398,11 @@ __device__ __forceinline__ double ccol_p2(cooperative_groups::cluster_group& cl,
                                           const float* __restrict__ Pk) {
   using G = CGeo<N>;
   constexpr int WH = G::WH;
-  auto p2 = [](float P, float re, float im) -> double { return double(P * P * fmaf(re, re, im * im)); };
-  double acc = 0.0;
+  auto p2 = [](float P, float re, float im) -> float { return P * P * fmaf(re, re, im * im); };
+  float acc = 0.0f;
   ccol_units<N, false>(cl, rows, g, [&](int K, float2& y1, float2& y2, int ky1, int ky2) {
     if (K != 0) {
-      acc += 2.0 * (p2(WF_LDG(Pk + ky1 * WH + K), y1.x, y1.y) + p2(WF_LDG(Pk + ky2 * WH + K), y2.x, y2.y));
+      acc += 2.0f * (p2(WF_LDG(Pk + ky1 * WH + K), y1.x, y1.y) + p2(WF_LDG(Pk + ky2 * WH + K), y2.x, y2.y));
     } else if (ky1 == 0) {
       acc += p2(WF_LDG(Pk + ky1 * WH), y1.x, 0.f) + p2(WF_LDG(Pk + ky1 * WH + G::W / 2), y1.y, 0.f) +
              p2(WF_LDG(Pk + ky2 * WH), y2.x, 0.f) + p2(WF_LDG(Pk + ky2 * WH + G::W / 2), y2.y, 0.f);
@@ -413,10 +410,10 @@ __device__ __forceinline__ double ccol_p2(cooperative_groups::cluster_group& cl,
       const float2 y2c = cconj(y2);
       const float2 A = cscale(cadd(y1, y2c), 0.5f);
       const float2 B = cmul_mi(cscale(csub(y1, y2c), 0.5f));
-      acc += 2.0 * (p2(WF_LDG(Pk + ky1 * WH), A.x, A.y) + p2(WF_LDG(Pk + ky1 * WH + G::W / 2), B.x, B.y));
+      acc += 2.0f * (p2(WF_LDG(Pk + ky1 * WH), A.x, A.y) + p2(WF_LDG(Pk + ky1 * WH + G::W / 2), B.x, B.y));
     }
   });
-  return acc;
+  return double(acc);
 }
 
 // Wiener-filter pixel update of a row at level lambda: t = d + w (s - d), w = 1 / (1 + lambda tau / N_bar),

@@ -335,13 +335,13 @@ WF_HD double p2_power(const float2 (&x)[N / 2], int lt, const float* __restrict_
   using G = Geo<N>;
   constexpr int WH = G::WH;
   const int col = lt % G::LC, r = lt / G::LC;
-  double acc = 0.0;
-  auto p2 = [](float P, float re, float im) -> double { return double(P * P * fmaf(re, re, im * im)); };
+  float acc = 0.0f;  // the thread's LC modes in FP32; the caller sums the threads in FP64
+  auto p2 = [](float P, float re, float im) -> float { return P * P * fmaf(re, re, im * im); };
   for_mode_pairs<N>(r, [&](auto KP, auto KQ, int ky1, int ky2, auto ZG) {
     constexpr int kp = decltype(KP)::value, kq = decltype(KQ)::value;
     constexpr bool zero_group = decltype(ZG)::value != 0;
     if (col != 0) {
-      acc += 2.0 * (p2(WF_LDG(Pk + ky1 * WH + col), x[kp].x, x[kp].y) + p2(WF_LDG(Pk + ky2 * WH + col), x[kq].x, x[kq].y));
+      acc += 2.0f * (p2(WF_LDG(Pk + ky1 * WH + col), x[kp].x, x[kp].y) + p2(WF_LDG(Pk + ky2 * WH + col), x[kq].x, x[kq].y));
     } else if constexpr (zero_group) {
       acc += p2(WF_LDG(Pk + ky1 * WH), x[kp].x, 0.f) + p2(WF_LDG(Pk + ky1 * WH + G::W / 2), x[kp].y, 0.f) +
              p2(WF_LDG(Pk + ky2 * WH), x[kq].x, 0.f) + p2(WF_LDG(Pk + ky2 * WH + G::W / 2), x[kq].y, 0.f);
@@ -349,10 +349,10 @@ WF_HD double p2_power(const float2 (&x)[N / 2], int lt, const float* __restrict_
       const float2 y1 = x[kp], y2c = cconj(x[kq]);
       const float2 A = cscale(cadd(y1, y2c), 0.5f);
       const float2 B = cmul_mi(cscale(csub(y1, y2c), 0.5f));
-      acc += 2.0 * (p2(WF_LDG(Pk + ky1 * WH), A.x, A.y) + p2(WF_LDG(Pk + ky1 * WH + G::W / 2), B.x, B.y));
+      acc += 2.0f * (p2(WF_LDG(Pk + ky1 * WH), A.x, A.y) + p2(WF_LDG(Pk + ky1 * WH + G::W / 2), B.x, B.y));
     }
   });
-  return acc;
+  return double(acc);
 }
 
 // sum over the full spectrum of w_j(k) |V_k|^2, j < nw <= 4, for the forward transform V held by this
@@ -551,9 +551,10 @@ WF_HD void mode_pair(int r, int kp, int& kq, int& ky1, int& ky2) {
 // f = P/(P + lambda tau) (scaled by 1/n), rolled over the thread's mode pairs (the column registers are dead
 // meanwhile, so more Pk / prev loads are in flight; each thread touches only its own parked slots, the
 // packed edge column included). With CMP the residual of the previous iterate, |r_k| = |s_hat_new -
-// s_hat_old| / (1 - f), is accumulated over the full spectrum (returned, scaled 1/n): per-mode terms in
-// FP32 (a residual estimate needs a few digits), summed in FP64. With STORE the new modes go to
-// prev[ky*LR + col].
+// s_hat_old| / (1 - f), is accumulated over the full spectrum (returned, scaled 1/n): per-mode terms and
+// the thread's partial sum (its 2 x LC/2 modes) in FP32 (a residual estimate needs a few digits, and FP64
+// arithmetic runs at a small fraction of the FP32 rate), the threads' partial sums in FP64 by the caller.
+// With STORE the new modes go to prev[ky*LR + col].
 template <int N>
 WF_HD double s_update_wf_parked(float2* cs, int lt, const float* __restrict__ Pk, float lt_,
                                 float2* __restrict__ prev, bool CMP, bool STORE) {
@@ -561,11 +562,11 @@ WF_HD double s_update_wf_parked(float2* cs, int lt, const float* __restrict__ Pk
   constexpr int WH = G::WH, LC = G::LC;
   constexpr float INV_N = 1.0f / float(G::H * G::W);
   const int col = lt % LC, r = lt / LC;
-  double acc = 0.0;
+  float acc = 0.0f;
   const float inv_lt = 1.0f / lt_;
-  auto wres = [&](float P, float dre, float dim) -> double {
+  auto wres = [&](float P, float dre, float dim) -> float {
     const float g = fmaf(P, inv_lt, 1.0f);
-    return double(fmaf(dre, dre, dim * dim) * (g * g));
+    return fmaf(dre, dre, dim * dim) * (g * g);
   };
   auto fcoef = [&](float P) { return wf_fdiv(P, P + lt_) * INV_N; };
 #pragma unroll 4
@@ -581,7 +582,7 @@ WF_HD double s_update_wf_parked(float2* cs, int lt, const float* __restrict__ Pk
       n2 = cscale(x2, fcoef(P2));
       if (CMP) {
         const float2 o1 = prev[ky1 * G::LR + col], o2 = prev[ky2 * G::LR + col];
-        acc += 2.0 * (wres(P1, n1.x - o1.x, n1.y - o1.y) + wres(P2, n2.x - o2.x, n2.y - o2.y));
+        acc += 2.0f * (wres(P1, n1.x - o1.x, n1.y - o1.y) + wres(P2, n2.x - o2.x, n2.y - o2.y));
       }
     } else {
       const float Pa1 = WF_LDG(Pk + ky1 * WH), Pb1 = WF_LDG(Pk + ky1 * WH + G::W / 2);
@@ -606,7 +607,7 @@ WF_HD double s_update_wf_parked(float2* cs, int lt, const float* __restrict__ Pk
           const float2 oA = cscale(cadd(o1, o2c), 0.5f);
           const float2 oB = cmul_mi(cscale(csub(o1, o2c), 0.5f));
           // modes ky1 and H - ky1 of each edge column have equal magnitude: weight 2
-          acc += 2.0 * (wres(Pa1, A.x - oA.x, A.y - oA.y) + wres(Pb1, B.x - oB.x, B.y - oB.y));
+          acc += 2.0f * (wres(Pa1, A.x - oA.x, A.y - oA.y) + wres(Pb1, B.x - oB.x, B.y - oB.y));
         }
       }
     }
@@ -617,7 +618,7 @@ WF_HD double s_update_wf_parked(float2* cs, int lt, const float* __restrict__ Pk
       prev[ky2 * G::LR + col] = n2;
     }
   }
-  return acc;
+  return double(acc);
 }
 
 // Mode coefficients (f/n, g/sqrt(2n)) of the s-draw. TableCoef reads the per-call table; BandCoef (the

@@ -346,7 +346,7 @@ __device__ __forceinline__ double col_update(int mode, float2* buf, int c0, cons
   using G = GGeo<N>;
   constexpr int L = G::LR, H = G::H, WH = G::WH;
   constexpr float INV_N = 1.0f / float(G::H * G::W);
-  double acc = 0.0;
+  float acc = 0.0f;  // this thread's tasks in FP32; the CTA and grid sums are FP64
   // mode pairs (j, H - j) of each column, j in [0, H/2); j = 0 pairs ky = 0 with ky = H/2
   for (int task = threadIdx.x; task < G::CB * (H / 2); task += 128) {
     const int jc = task / (H / 2), j = task % (H / 2);
@@ -379,18 +379,19 @@ __device__ __forceinline__ double col_update(int mode, float2* buf, int c0, cons
         }
       }
     } else if (mode == 1) {
-      // per-mode residual terms in FP32, summed in FP64 (as s_update_wf_parked)
+      // per-mode residual terms and the thread's partial sum in FP32, CTA and grid sums in FP64 (as
+      // s_update_wf_parked)
       const float inv_lt = 1.0f / ltau;
-      auto wres = [&](float P, float dre, float dim) -> double {
+      auto wres = [&](float P, float dre, float dim) -> float {
         const float g = fmaf(P, inv_lt, 1.0f);
-        return double(fmaf(dre, dre, dim * dim) * (g * g));
+        return fmaf(dre, dre, dim * dim) * (g * g);
       };
       if (col != 0) {
         const float P1 = __ldg(Pk + ky1 * WH + col), P2 = __ldg(Pk + ky2 * WH + col);
         const float2 n1 = cscale(y1, wf_fdiv(P1, P1 + ltau) * INV_N), n2 = cscale(y2, wf_fdiv(P2, P2 + ltau) * INV_N);
         if (cmp) {
           const float2 o1 = prev[ky1 * L + col], o2 = prev[ky2 * L + col];
-          acc += 2.0 * (wres(P1, n1.x - o1.x, n1.y - o1.y) + wres(P2, n2.x - o2.x, n2.y - o2.y));
+          acc += 2.0f * (wres(P1, n1.x - o1.x, n1.y - o1.y) + wres(P2, n2.x - o2.x, n2.y - o2.y));
         }
         y1 = n1;
         y2 = n2;
@@ -416,7 +417,7 @@ __device__ __forceinline__ double col_update(int mode, float2* buf, int c0, cons
             const float2 o1 = prev[ky1 * L], o2c = cconj(prev[ky2 * L]);
             const float2 oA = cscale(cadd(o1, o2c), 0.5f);
             const float2 oB = cmul_mi(cscale(csub(o1, o2c), 0.5f));
-            acc += 2.0 * (wres(Pa1, A.x - oA.x, A.y - oA.y) + wres(Pb1, B.x - oB.x, B.y - oB.y));
+            acc += 2.0f * (wres(Pa1, A.x - oA.x, A.y - oA.y) + wres(Pb1, B.x - oB.x, B.y - oB.y));
           }
           y1 = cadd(A, cmul_i(B));
           y2 = cadd(cconj(A), cmul_i(cconj(B)));
@@ -427,9 +428,9 @@ __device__ __forceinline__ double col_update(int mode, float2* buf, int c0, cons
         prev[ky2 * L + col] = y2;
       }
     } else {
-      auto p2 = [](float P, float re, float im) -> double { return double(P * P * fmaf(re, re, im * im)); };
+      auto p2 = [](float P, float re, float im) -> float { return P * P * fmaf(re, re, im * im); };
       if (col != 0) {
-        acc += 2.0 * (p2(__ldg(Pk + ky1 * WH + col), y1.x, y1.y) + p2(__ldg(Pk + ky2 * WH + col), y2.x, y2.y));
+        acc += 2.0f * (p2(__ldg(Pk + ky1 * WH + col), y1.x, y1.y) + p2(__ldg(Pk + ky2 * WH + col), y2.x, y2.y));
       } else if (j == 0) {
         acc += p2(__ldg(Pk + ky1 * WH), y1.x, 0.f) + p2(__ldg(Pk + ky1 * WH + G::W / 2), y1.y, 0.f) +
                p2(__ldg(Pk + ky2 * WH), y2.x, 0.f) + p2(__ldg(Pk + ky2 * WH + G::W / 2), y2.y, 0.f);
@@ -437,14 +438,14 @@ __device__ __forceinline__ double col_update(int mode, float2* buf, int c0, cons
         const float2 y2c = cconj(y2);
         const float2 A = cscale(cadd(y1, y2c), 0.5f);
         const float2 B = cmul_mi(cscale(csub(y1, y2c), 0.5f));
-        acc += 2.0 * (p2(__ldg(Pk + ky1 * WH), A.x, A.y) + p2(__ldg(Pk + ky1 * WH + G::W / 2), B.x, B.y));
+        acc += 2.0f * (p2(__ldg(Pk + ky1 * WH), A.x, A.y) + p2(__ldg(Pk + ky1 * WH + G::W / 2), B.x, B.y));
       }
     }
     v[padi(ky1)] = y1;
     v[padi(ky2)] = y2;
   }
   __syncthreads();
-  return acc;
+  return double(acc);
 }
 
 // Column phase on one work item: columns c0 .. c0+CB-1 of field f.

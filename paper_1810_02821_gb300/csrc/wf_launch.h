@@ -8,6 +8,7 @@
 #include "wf_batch.cuh"
 #include "wf_gbatch.cuh"
 #include "wf_cluster.cuh"
+#include "wf_bphase.cuh"
 
 namespace wf {
 
@@ -36,6 +37,13 @@ cudaError_t launch_solve(const SolveArgs& a, const BnormArgs& b, cudaStream_t st
 // batched persistent form for N <= 128: grid = min(items, resident CTAs), per-CTA scratch slots
 template <int N>
 cudaError_t launch_batch(const BatchArgs& b, int* grid_out, cudaStream_t st);
+
+// batched form for N <= 128 in phases (after the per-image set-up kernels): one CTA per image for the
+// cooled solves, then the samplers with fields_per_cta<N>() images per CTA
+template <int N>
+cudaError_t launch_bsolve(const BSolveArgs& a, cudaStream_t st);
+template <int N>
+cudaError_t launch_bsample(const BSampleArgs& a, cudaStream_t st);
 
 // weighted spectral power of real fields (N <= 128, one CTA per field)
 template <int N>
@@ -152,6 +160,26 @@ cudaError_t launch_batch(const BatchArgs& b, int* grid_out, cudaStream_t st) {
 }
 
 template <int N>
+cudaError_t launch_bsolve(const BSolveArgs& a, cudaStream_t st) {
+  const int smem = bsolve_smem_bytes<N>();
+  cudaError_t e = cudaFuncSetAttribute(k_bsolve<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  if (a.F > 0) k_bsolve<N><<<a.F, N, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_bsample(const BSampleArgs& a, cudaStream_t st) {
+  constexpr int FPC = fields_per_cta<N>();
+  const int smem = FPC * Geo<N>::FIELD_BYTES;
+  auto kern = k_bsample<N, FPC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  if (a.F > 0 && a.n_samples > 0) kern<<<(a.F + FPC - 1) / FPC, N * FPC, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int N>
 cudaError_t launch_wpower(const WpowerArgs& p, cudaStream_t st) {
   const int smem = Geo<N>::FIELD_BYTES + 33 * 8;
   cudaError_t e = cudaFuncSetAttribute(k_wpower<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -167,6 +195,8 @@ cudaError_t launch_wpower(const WpowerArgs& p, cudaStream_t st) {
   template cudaError_t launch_solve<N>(const SolveArgs&, const BnormArgs&, cudaStream_t, LaunchTimer*); \
   template cudaError_t launch_batch<N>(const BatchArgs&, int*, cudaStream_t);                     \
   template cudaError_t batch_grid<N>(int, int, int*);                                                   \
+  template cudaError_t launch_bsolve<N>(const BSolveArgs&, cudaStream_t);                                \
+  template cudaError_t launch_bsample<N>(const BSampleArgs&, cudaStream_t);                              \
   template cudaError_t launch_wpower<N>(const WpowerArgs&, cudaStream_t);
 #endif
 

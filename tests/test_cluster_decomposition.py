@@ -5,8 +5,9 @@ of a thread-block cluster), restated in FP64 NumPy from the decomposition the ke
   W_L^(h k'), then radix-R butterflies; X[K] kept at slot R (K mod M) + K / M (digit-reversed order);
 * columns: CTA b holds rows y = P a + b; an M-point transform per CTA, twiddles W_N^(b k'), then one radix-P
   stage across the CTAs; the inverse runs the same steps backwards;
-* the work units of the radix-P stage (k' = u with its mirror M - u) hold every mode pair (ky, N - ky) of a
-  column exactly once, so the pairwise s-draw and the Hermitian edge column can be done inside a unit;
+* the work units of the radix-P stage (k' = u with its mirror M - u, and u = 0 with M/2) hold every mode
+  pair (ky, N - ky) of a column exactly once, in units of equal size, so the pairwise s-draw and the
+  Hermitian edge column can be done inside a unit and every thread of the cluster gets the same share;
 * and the shared-memory transform of the global-memory kernels (R-point DFTs across S strided
   subsequences, then S-point transforms).
 
@@ -19,15 +20,15 @@ GEOMETRIES = [(256, 64), (512, 32), (512, 64)]  # (N, M): M rows per CTA, P = N 
 
 
 def _units(N, M):
-    """Mode pairs (ky1, ky2) of one column as the radix-P stage enumerates them, unit by unit."""
+    """Mode pairs (ky1, ky2) of one column as the radix-P stage enumerates them, unit by unit: unit u in
+    [0, M/2) holds the butterflies u and v = M - u (u = 0 with v = M/2, the two half-size ones)."""
     P = N // M
-    out = []
-    for u in range(M // 2 + 1):
-        v = M - u
+    out, sizes = [], []
+    for u in range(M // 2):
+        v = M // 2 if u == 0 else M - u
         if u == 0:
-            pairs = [(0, N // 2)] + [(M * m, N - M * m) for m in range(1, P // 2)]
-        elif u == M // 2:
-            pairs = [(M // 2 + M * m, N - M // 2 - M * m) for m in range(P // 2)]
+            pairs = [(0, N // 2)] + [(M * m, N - M * m) for m in range(1, P // 2)] + \
+                    [(M // 2 + M * m, N - M // 2 - M * m) for m in range(P // 2)]
         else:
             pairs = [(u + M * m, N - u - M * m) for m in range(P // 2)] + \
                     [(v + M * m, N - v - M * m) for m in range(P // 2)]
@@ -35,6 +36,8 @@ def _units(N, M):
         for a, b in pairs:
             assert a % M in (u, v % M) and b % M in (u, v % M)
         out.extend(pairs)
+        sizes.append(len(pairs))
+    assert sizes == [P] * (M // 2)             # equal units: the cluster's threads get equal shares
     return out
 
 
