@@ -111,7 +111,7 @@ __global__ void k_prep(const float* __restrict__ d, const float* __restrict__ Nd
 }
 
 // Per-pixel tables ([W][H], x-major so that row threads read consecutive addresses) and the
-// per-mode sample table, in FP64 then rounded once.
+// per-mode sample table (table_pixel, table_mode: within 2 ulp of the exact coefficients).
 // Pixel tables are x-major, aq[x*H + ty] and dn[x*H + ty], with ty = y, or with perm = P > 0 (the
 // cluster kernels, CTA b holding the rows y = P a + b) ty = (y mod P) H/P + y / P, so that the rows of one
 // CTA are contiguous and its row threads read consecutive addresses.
@@ -1278,7 +1278,7 @@ std::vector<wf::GBField> chunk_fields(const GBChunk& c, const std::vector<wf::Ba
 struct SmallClass {
   int H = 0;
   std::vector<int> items;
-  size_t o_fields = 0, o_idx = 0, o_sc = 0, o_data = 0, per_field = 0;
+  size_t o_fields = 0, o_idx = 0, o_sc = 0, o_bn = 0, o_data = 0, per_field = 0;
   size_t f_aq = 0, f_dn = 0, f_fg = 0, f_prev = 0, f_sw = 0;
 };
 
@@ -1288,6 +1288,7 @@ void layout_small(SmallClass& c, Carve& cv) {
   c.o_fields = cv.take<wf::GBField>(F);
   c.o_idx = cv.take<int>(F);
   c.o_sc = cv.take<wf::Scalars>(F);
+  c.o_bn = cv.take<double>(size_t(F) * wf::kMaxLevels);
   Carve f;
   c.f_aq = f.take<float2>(n);
   c.f_dn = f.take<float2>(n);
@@ -1418,6 +1419,7 @@ wf_status run_small(const SmallClass& c, const wf::BatchItem* d_items, wf::Batch
   sa.fields = fields;
   sa.sc = sc;
   sa.res = d_res;
+  sa.bnorm = reinterpret_cast<double*>(b + c.o_bn);
   sa.F = F;
   sa.tol = o.tol;
   sa.eta = o.eta;

@@ -1,8 +1,9 @@
-// Batched form for images up to 128 x 128, in phases: the images of a size class go through three
+// Batched form for images up to 128 x 128, in phases: the images of a size class go through a few
 // launches instead of one persistent kernel that runs the whole pipeline per image:
 //   set-up    per-image tau, lambda_0 and checks, then every image's coefficient tables (wf_api.cu);
-//   k_bsolve  one CTA per image: its level norms and the lambda-cooled G -> 0 iteration (§2.2), s_W to
-//             the image's output (or scratch), status / sweeps / residual to the batch results;
+//   k_blevels one CTA per (image, cooling level): the level norms ||S N_lambda^-1 d||^2;
+//   k_bsolve  one CTA per image: the lambda-cooled G -> 0 iteration (§2.2), s_W to the image's output
+//             (or scratch), status / sweeps / residual to the batch results;
 //   k_bsample fields of several images per CTA (as the single-image sampler): n_samples sweeps of
 //             Alg. 1 from s_W, each image with its own tables, chain and key.
 // Each kernel holds one stage's code only (the fused kernel's instruction footprint stalled its warps on
@@ -18,6 +19,7 @@ struct BSolveArgs {
   const GBField* fields;  // [F]: dn, Pk, prev, out_wf (never null here), item
   const Scalars* sc;      // [F]
   BatchResult* res;       // indexed by GBField::item
+  double* bnorm;          // [F][kMaxLevels] level norms (written by k_blevels, read by k_bsolve)
   int F;
   double tol, eta, level_tol;
   int max_iter, level_max, check;
@@ -33,16 +35,30 @@ struct BSampleArgs {
 template <int N>
 constexpr int bsolve_min_ctas() { return N >= 128 ? 3 : (N == 64 ? 8 : 16); }
 template <int N>
-constexpr int bsolve_smem_bytes() { return Geo<N>::FIELD_BYTES + (33 + kMaxLevels) * 8; }
+constexpr int bsolve_smem_bytes() { return Geo<N>::FIELD_BYTES + 33 * 8; }
 
-// one image per CTA: level norms, cooled solve from s = 0, s_W out
+// one CTA per (image blockIdx.x, level blockIdx.y): ||S N_lambda^-1 d||^2 of that cooling level
+template <int N>
+__global__ void __launch_bounds__(N) k_blevels(BSolveArgs a) {
+  using G = Geo<N>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* S = reinterpret_cast<float2*>(smem_raw);
+  double* red = reinterpret_cast<double*>(smem_raw + G::FIELD_BYTES);
+  const int f = blockIdx.x, lev = blockIdx.y;
+  const Scalars sc = a.sc[f];
+  if (sc.status != 0 || lev >= sc.n_levels) return;  // uniform over the CTA
+  const GBField fd = a.fields[f];
+  const double v = level_norm<N>(S, red, threadIdx.x, fd.dn, fd.Pk, float(level_lambda(sc, lev, a.eta) * sc.tau));
+  if (threadIdx.x == 0) a.bnorm[f * kMaxLevels + lev] = v;
+}
+
+// one image per CTA: cooled solve from s = 0 with the level norms of k_blevels, s_W out
 template <int N>
 __global__ void __launch_bounds__(N, bsolve_min_ctas<N>()) k_bsolve(BSolveArgs a) {
   using G = Geo<N>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* S = reinterpret_cast<float2*>(smem_raw);
   double* red = reinterpret_cast<double*>(smem_raw + G::FIELD_BYTES);
-  double* bn = red + 33;
   const int lt = threadIdx.x;
   const GBField fd = a.fields[blockIdx.x];
   const Scalars sc = a.sc[blockIdx.x];
@@ -50,18 +66,13 @@ __global__ void __launch_bounds__(N, bsolve_min_ctas<N>()) k_bsolve(BSolveArgs a
     if (lt == 0) a.res[fd.item] = BatchResult{-1.0, 0, sc.status};
     return;
   }
-  for (int lev = 0; lev < sc.n_levels; ++lev) {
-    const double v = level_norm<N>(S, red, lt, fd.dn, fd.Pk, float(level_lambda(sc, lev, a.eta) * sc.tau));
-    if (lt == 0) bn[lev] = v;
-    __syncthreads();
-  }
   float2 c[G::LR];
 #pragma unroll
   for (int m = 0; m < G::LR; ++m) c[m] = make_float2(0.f, 0.f);
   int iters = 0;
   double rho = -1.0;
-  const int status = solve_sweeps<N>(S, red, lt, c, fd.dn, fd.Pk, sc, bn, fd.prev, a.tol, a.eta, a.level_tol,
-                                     a.max_iter, a.level_max, a.check, iters, rho);
+  const int status = solve_sweeps<N>(S, red, lt, c, fd.dn, fd.Pk, sc, a.bnorm + blockIdx.x * kMaxLevels, fd.prev,
+                                     a.tol, a.eta, a.level_tol, a.max_iter, a.level_max, a.check, iters, rho);
   float* stg = reinterpret_cast<float*>(S);
   stage_row<N>(stg, lt, c);
   __syncthreads();

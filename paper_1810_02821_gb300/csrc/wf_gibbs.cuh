@@ -139,33 +139,62 @@ WF_HD Scalars make_scalars(float min_obs, int n_obs, float pmax, int bad, int ne
   return r;
 }
 
-// lambda of cooling level lev
+// lambda of cooling level lev. eta^lev by binary powers (at most a dozen FP64 products): every thread of a
+// CTA evaluates this at each level change, and the library pow() is a long FP64 instruction sequence on a
+// GPU whose FP64 rate is a small fraction of its FP32 rate.
 WF_HD double level_lambda(const Scalars& sc, int lev, double eta) {
-  return lev >= sc.n_levels - 1 ? 1.0 : fmax(1.0, sc.lam0 * pow(eta, double(lev)));
+  if (lev >= sc.n_levels - 1) return 1.0;
+  double p = 1.0, b = eta;
+  for (int e = lev; e > 0; e >>= 1) {
+    if (e & 1) p *= b;
+    b *= b;
+  }
+  return fmax(1.0, sc.lam0 * p);
+}
+
+// correctly rounded FP32 division, reciprocal and square root (IEEE round to nearest even)
+WF_HD float fdiv_rn(float a, float b) {
+#if defined(__CUDA_ARCH__)
+  return __fdiv_rn(a, b);
+#else
+  return a / b;
+#endif
+}
+WF_HD float fsqrt_rn(float a) {
+#if defined(__CUDA_ARCH__)
+  return __fsqrt_rn(a);
+#else
+  return std::sqrt(a);
+#endif
 }
 
 // per-pixel tables of pixel i = y*W + x, stored at x*H + y:
 //   aq = ((1 - w) d, sqrt(w)) with w = N_bar/(tau + N_bar)  (sampler, lambda = 1; w = 1, a = 0 if missing)
 //   dn = (d, 1/N_bar)                                        (Wiener filter; (0, 0) if missing)
+// N_bar = N - tau is formed by one FP64 subtraction (exact for a tau taken from the data) and rounded once;
+// since tau + N_bar = N, w = N_bar / N and 1 - w = tau / N, each from one correctly rounded FP32 division,
+// so every entry is within 2 ulp of its exact value (FP64 division and square root, run per pixel, would
+// cost tens of FP64 instructions each on a GPU whose FP64 rate is a small fraction of its FP32 rate).
 WF_HD void table_pixel(float dv_in, float nv, bool obs, double tau, float2* aq, float2* dn) {
-  double a = 0.0, wgt = 1.0, dv = 0.0, inb = 0.0;
+  float a = 0.0f, wgt = 1.0f, dv = 0.0f, inb = 0.0f;
   if (obs) {
-    dv = double(dv_in);
-    const double nbar = double(nv) - tau;  // >= 0 since tau <= min observed Ndiag
-    wgt = nbar / (tau + nbar);
-    a = tau / (tau + nbar) * dv;
-    inb = nbar > 0.0 ? 1.0 / nbar : double(wf_inf());
+    dv = dv_in;
+    const float nbar = float(double(nv) - tau);  // >= 0 since tau <= min observed Ndiag
+    wgt = fdiv_rn(nbar, nv);
+    a = fdiv_rn(float(tau), nv) * dv;
+    inb = nbar > 0.0f ? fdiv_rn(1.0f, nbar) : wf_inf();
   }
-  *aq = make_float2(float(a), float(sqrt(wgt)));
-  *dn = make_float2(float(dv), float(inb));
+  *aq = make_float2(a, fsqrt_rn(wgt));
+  *dn = make_float2(dv, inb);
 }
 
-// per-mode sampler table: (f / n, g / sqrt(2 n)), f = P/(P + tau), g^2 = P tau/(P + tau) (Alg. 1)
+// per-mode sampler table: (f / n, g / sqrt(2 n)), f = P/(P + tau), g^2 = P tau/(P + tau) = f tau (Alg. 1);
+// correctly rounded FP32 operations (1/n and 1/(2n) are powers of two), within 2 ulp of the exact values
 WF_HD float2 table_mode(float Pv, double tau, double inv_n) {
-  const double P = double(Pv);
-  const double f = P > 0.0 ? P / (P + tau) : 0.0;
-  const double g2 = P > 0.0 ? P * tau / (P + tau) : 0.0;
-  return make_float2(float(f * inv_n), float(sqrt(g2 * 0.5 * inv_n)));
+  if (!(Pv > 0.0f)) return make_float2(0.0f, 0.0f);
+  const float t = float(tau), in = float(inv_n);
+  const float f = fdiv_rn(Pv, Pv + t);
+  return make_float2(f * in, fsqrt_rn(f * t * (0.5f * in)));
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -38,8 +38,9 @@ cudaError_t launch_solve(const SolveArgs& a, const BnormArgs& b, cudaStream_t st
 template <int N>
 cudaError_t launch_batch(const BatchArgs& b, int* grid_out, cudaStream_t st);
 
-// batched form for N <= 128 in phases (after the per-image set-up kernels): one CTA per image for the
-// cooled solves, then the samplers with fields_per_cta<N>() images per CTA
+// batched form for N <= 128 in phases (after the per-image set-up kernels): one CTA per image and level
+// for the level norms, one CTA per image for the cooled solves, then the samplers with
+// fields_per_cta<N>() images per CTA
 template <int N>
 cudaError_t launch_bsolve(const BSolveArgs& a, cudaStream_t st);
 template <int N>
@@ -162,9 +163,14 @@ cudaError_t launch_batch(const BatchArgs& b, int* grid_out, cudaStream_t st) {
 template <int N>
 cudaError_t launch_bsolve(const BSolveArgs& a, cudaStream_t st) {
   const int smem = bsolve_smem_bytes<N>();
-  cudaError_t e = cudaFuncSetAttribute(k_bsolve<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(k_blevels<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  if (a.F > 0) k_bsolve<N><<<a.F, N, smem, st>>>(a);
+  e = cudaFuncSetAttribute(k_bsolve<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  if (a.F > 0) {
+    k_blevels<N><<<dim3(a.F, kMaxLevels), N, smem, st>>>(a);
+    k_bsolve<N><<<a.F, N, smem, st>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -373,14 +373,17 @@ WF_HD u4 philox4x32_10(u4 c, uint32_t k0, uint32_t k1) {
 WF_HD float to_uniform(uint32_t x) { return float(2u * (x >> 9) + 1u) * 5.9604644775390625e-08f; }
 
 // (z0, z1) = sqrt(-2 ln u0) (cos 2 pi u1, sin 2 pi u1), u = (2 floor(x / 2^9) + 1) 2^-24.
-// Device: -2 ln u0 = -2 ln(2) log2(u0) from the hardware log2, clamped at the smallest normal float
-// (log2 of the largest u, 1 - 2^-24, may round to zero), its square root as x * rsqrt(x); the angle
-// 2 pi (u1 - 1/2) in (-pi, pi), for which cos(2 pi u) = -cos(2 pi (u - 1/2)) and likewise for sin.
+// Device: the 23 bits k = floor(x / 2^9) become v = 1 + k 2^-23 by placing them under the exponent of 1
+// (exact, no integer-to-float conversion), and u = v - (1 - 2^-24) = (2k + 1) 2^-24 exactly (the operands
+// are within a factor of two, so the difference is exact); -2 ln u0 = -2 ln(2) log2(u0) from the hardware
+// log2, clamped at the smallest normal float (log2 of the largest u, 1 - 2^-24, may round to zero), its
+// square root as x * rsqrt(x); the angle 2 pi (u1 - 1/2) = 2 pi v1 - 2 pi (3/2 - 2^-24) in (-pi, pi) as one
+// FMA (absolute error below 3.5e-7), for which cos(2 pi u) = -cos(2 pi (u - 1/2)) and likewise for sin.
 WF_HD void box_muller(uint32_t a, uint32_t b, float& z0, float& z1) {
 #if defined(__CUDA_ARCH__)
-  const float ka = float(a >> 9), kb = float(b >> 9);
-  const float u0 = fmaf(ka, 1.1920928955078125e-07f, 5.9604644775390625e-08f);        // (2k + 1) 2^-24
-  const float ang = fmaf(kb, 7.490140565847157e-07f, -3.1415922790827646f);            // 2 pi (u1 - 1/2)
+  const float u0 = __int_as_float(0x3f800000u | (a >> 9)) - 0.999999940395355224609375f;   // (2k + 1) 2^-24
+  const float ang = fmaf(__int_as_float(0x3f800000u | (b >> 9)), 6.2831854820251465f,
+                         -9.424777848530681f);                                              // 2 pi (u1 - 1/2)
   const float e = fmaxf(-1.3862943611198906f * __log2f(u0), 1.17549435e-38f);          // -2 ln u0
   const float r = e * rsqrtf(e);
   float sn, cs;
