@@ -1278,7 +1278,7 @@ std::vector<wf::GBField> chunk_fields(const GBChunk& c, const std::vector<wf::Ba
 struct SmallClass {
   int H = 0;
   std::vector<int> items;
-  size_t o_fields = 0, o_idx = 0, o_sc = 0, o_bn = 0, o_data = 0, per_field = 0;
+  size_t o_fields = 0, o_idx = 0, o_sc = 0, o_bn = 0, o_order = 0, o_data = 0, per_field = 0;
   size_t f_aq = 0, f_dn = 0, f_fg = 0, f_prev = 0, f_sw = 0;
 };
 
@@ -1289,6 +1289,7 @@ void layout_small(SmallClass& c, Carve& cv) {
   c.o_idx = cv.take<int>(F);
   c.o_sc = cv.take<wf::Scalars>(F);
   c.o_bn = cv.take<double>(size_t(F) * wf::kMaxLevels);
+  c.o_order = cv.take<int>(F);
   Carve f;
   c.f_aq = f.take<float2>(n);
   c.f_dn = f.take<float2>(n);
@@ -1402,6 +1403,31 @@ cudaError_t launch_bsample_any(int H, const wf::BSampleArgs& a, cudaStream_t st)
   return cudaErrorInvalidValue;
 }
 
+// Solve order of a small size class: images by decreasing number of cooling levels (a cheap predictor
+// of the solve's length), failed set-ups last. One CTA: counting sort over the level counts; the order
+// within a count is arbitrary (every image's result is independent of it).
+__global__ void k_order_by_levels(const wf::Scalars* __restrict__ sc, int F, int* order) {
+  __shared__ int start[wf::kMaxLevels + 1];
+  for (int b = threadIdx.x; b <= wf::kMaxLevels; b += blockDim.x) start[b] = 0;
+  __syncthreads();
+  auto bin = [&](int f) {
+    const wf::Scalars s = sc[f];
+    return s.status == 0 ? wf::kMaxLevels - s.n_levels : wf::kMaxLevels;  // more levels -> smaller bin
+  };
+  for (int f = threadIdx.x; f < F; f += blockDim.x) atomicAdd(&start[bin(f)], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int b = 0; b <= wf::kMaxLevels; ++b) {
+      const int c = start[b];
+      start[b] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (int f = threadIdx.x; f < F; f += blockDim.x) order[atomicAdd(&start[bin(f)], 1)] = f;
+}
+
 // the phased pipeline of one small size class on stream st (item table uploaded, descriptors in place)
 wf_status run_small(const SmallClass& c, const wf::BatchItem* d_items, wf::BatchResult* d_res,
                     const wf_batch_opts& o, char* b, cudaStream_t st) {
@@ -1420,7 +1446,10 @@ wf_status run_small(const SmallClass& c, const wf::BatchItem* d_items, wf::Batch
   sa.sc = sc;
   sa.res = d_res;
   sa.bnorm = reinterpret_cast<double*>(b + c.o_bn);
+  sa.order = reinterpret_cast<const int*>(b + c.o_order);
   sa.F = F;
+  k_order_by_levels<<<1, 1024, 0, st>>>(sc, F, reinterpret_cast<int*>(b + c.o_order));
+  WF_CUDA(cudaGetLastError());
   sa.tol = o.tol;
   sa.eta = o.eta;
   sa.level_tol = o.level_tol;

@@ -168,7 +168,7 @@ cudaError_t launch_bsolve(const BSolveArgs& a, cudaStream_t st) {
   e = cudaFuncSetAttribute(k_bsolve<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   if (a.F > 0) {
-    k_blevels<N><<<dim3(a.F, kMaxLevels), N, smem, st>>>(a);
+    k_blevels<N><<<dim3(a.F, kLevelCtas), N, smem, st>>>(a);
     k_bsolve<N><<<a.F, N, smem, st>>>(a);
   }
   return cudaGetLastError();
