@@ -257,6 +257,12 @@ typedef struct {
                           many images per CTA as the single-image sampler puts chains); 1 = fused: one
                           persistent kernel per size whose CTAs take images from a work counter and run the
                           whole pipeline each (small_grid_pct applies) */
+  int32_t large_cluster_rows; /* 512 x 512 images on thread-block clusters: rows of the field per CTA, 32
+                                 (clusters of 16 CTAs, 2 per SM) or 64 (clusters of 8 CTAs, 1 per SM);
+                                 0 = 32 */
+  int32_t small_fields_per_cta; /* phased path: images per CTA of the sampler launch of each size class up
+                                   to 128 x 128, 1, 2, 4 or 8, capped at 128 / H (128 threads per CTA);
+                                   0 = the cap */
 } wf_batch_opts;
 
 void wf_batch_opts_default(wf_batch_opts* o);
@@ -288,8 +294,10 @@ void wf_batch_graph_destroy(wf_batch_graph g);
  * Launch-shape autotuner of the batched form. Starting from *opts, it times graph replays of this batch
  * (one warm-up and `reps` timed replays per candidate, CUDA events on `stream`) and keeps, one knob at a
  * time, the fastest large_grid_pct in {100, 50, 25, 12}, large_streams in {1, 2, 4, 8, 16} (when the batch has
- * images above 128 x 128), small_path in {0, 1} and, for the fused path, small_grid_pct in {100, 50, 25} (when
- * it has images up to 128 x 128); the chosen values are written back to *opts and the
+ * images above 128 x 128), large_cluster_rows in {32, 64} (when it has 512 x 512 images), small_path in {0, 1}
+ * and then, for the fused path, small_grid_pct in {100, 50, 25} or, for the phased path,
+ * small_fields_per_cta in {1, 2, 4, 8} (when it has images up to 128 x 128); the chosen values are written
+ * back to *opts and the
  * best replay time to *best_ms (HOST, may be NULL). The items' outputs are overwritten by the trial runs.
  * A representative subset of a large batch tunes faster than the whole batch.
  */

@@ -146,7 +146,7 @@ bool size_ok(int H, int W) {
 }
 bool size_on_chip(int H) { return H <= 128; }
 
-bool cluster_fits(int H);
+bool cluster_fits(int H, int rows = 0);
 
 // Path for `units` independent fields (chains or images) of H x H, H in {256, 512}: one thread-block
 // cluster per field, or the global-memory kernels. Automatic choice (measured on GB300, 50 sweeps): the
@@ -154,25 +154,42 @@ bool cluster_fits(int H);
 // clusters from about 32 fields at 256^2 (24 chains: 1.40 vs 1.84 ms; 32 chains: 2.46 vs 1.88 ms) and
 // from about 8 at 512^2 (4 chains: 1.39 vs 1.58 ms; 8 chains: 2.88 vs 2.07 ms).
 int cluster_min_units(int H) { return H == 256 ? 32 : 8; }
-bool use_cluster(int H, int units) {
-  if ((H != 256 && H != 512) || g_large_sampler == 1 || !cluster_fits(H)) return false;
+
+// rows per CTA of the cluster kernels: 64 at 256; at 512 the caller's choice of 32 or 64 (0: the default)
+int cluster_rows_of(int H, int rows) { return H == 512 && (rows == 32 || rows == 64) ? rows : wf::cluster_rows(H); }
+
+cudaError_t csample_clusters_any(int H, int rows, int* n) {
+  if (H == 256) return wf::csample_clusters<256, 64>(n);
+  return rows == 64 ? wf::csample_clusters<512, 64>(n) : wf::csample_clusters<512, 32>(n);
+}
+cudaError_t launch_csample_any(int H, int rows, const wf::SampleArgs& a, cudaStream_t st, wf::LaunchTimer* t) {
+  if (H == 256) return wf::launch_csample<256, 64>(a, st, t);
+  return rows == 64 ? wf::launch_csample<512, 64>(a, st, t) : wf::launch_csample<512, 32>(a, st, t);
+}
+cudaError_t launch_cpipe_any(int H, int rows, const wf::CBArgs& a, cudaStream_t st, wf::LaunchTimer* t) {
+  if (H == 256) return wf::launch_cpipe<256, 64>(a, st, t);
+  return rows == 64 ? wf::launch_cpipe<512, 64>(a, st, t) : wf::launch_cpipe<512, 32>(a, st, t);
+}
+
+bool use_cluster(int H, int units, int rows = 0) {
+  if ((H != 256 && H != 512) || g_large_sampler == 1 || !cluster_fits(H, rows)) return false;
   return g_large_sampler == 2 || units >= cluster_min_units(H);
 }
 
-// whether at least one sampler cluster for H x H fits on the current device (queried once per device)
-bool cluster_fits(int H) {
+// whether at least one sampler cluster of that geometry fits on the current device (queried once per device)
+bool cluster_fits(int H, int rows) {
   static std::mutex mu;
-  static int known[2][64] = {};  // 0 unknown, 1 fits, 2 does not
+  static int known[3][64] = {};  // 0 unknown, 1 fits, 2 does not
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
     cudaGetLastError();
     return false;
   }
-  const int k = H == 256 ? 0 : 1;
+  const int k = H == 256 ? 0 : (cluster_rows_of(H, rows) == 64 ? 2 : 1);
   std::lock_guard<std::mutex> lock(mu);
   if (known[k][dev] == 0) {
     int clusters = 0;
-    const cudaError_t e = H == 256 ? wf::csample_clusters<256>(&clusters) : wf::csample_clusters<512>(&clusters);
+    const cudaError_t e = csample_clusters_any(H, cluster_rows_of(H, rows), &clusters);
     if (e != cudaSuccess) cudaGetLastError();
     known[k][dev] = (e == cudaSuccess && clusters > 0) ? 1 : 2;
   }
@@ -534,7 +551,7 @@ wf_status solve_cluster(const float* d, const float* Ndiag, const uint8_t* mask,
   k_prep<<<1, 1024, 0, st>>>(d, Ndiag, mask, Pk, H, W, o.tau, o.eta, sc);
   WF_CUDA(cudaGetLastError());
   k_tables<<<int((n + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc, nullptr,
-                                                 reinterpret_cast<float2*>(b + o_dn), nullptr, H / wf::cluster_rows(H));
+                                                 reinterpret_cast<float2*>(b + o_dn), nullptr, H / cluster_rows_of(H, 0));
   WF_CUDA(cudaGetLastError());
   wf::GBField fd{};
   fd.dn = reinterpret_cast<const float2*>(b + o_dn);
@@ -555,7 +572,7 @@ wf_status solve_cluster(const float* d, const float* Ndiag, const uint8_t* mask,
   cb.level_max = o.level_max;
   cb.check = o.check;
   cb.n_samples = 0;
-  const cudaError_t e = H == 256 ? wf::launch_cpipe<256>(cb, st, timer) : wf::launch_cpipe<512>(cb, st, timer);
+  const cudaError_t e = launch_cpipe_any(H, cluster_rows_of(H, 0), cb, st, timer);
   if (e != cudaSuccess) return cuda_fail(e);
   wf::BatchResult hr;
   WF_CUDA(cudaMemcpyAsync(&hr, res, sizeof(hr), cudaMemcpyDeviceToHost, st));
@@ -791,7 +808,7 @@ wf_status wf_sample_ex(const float* d, const float* Ndiag, const uint8_t* mask, 
   k_prep<<<1, 1024, 0, st>>>(d, Ndiag, mask, Pk, H, W, o.tau, 0.5, sc);
   WF_CUDA(cudaGetLastError());
   k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc, aq, nullptr, fg,
-                                                       cluster ? H / wf::cluster_rows(H) : 0);
+                                                       cluster ? H / cluster_rows_of(H, 0) : 0);
   WF_CUDA(cudaGetLastError());
   wf::SampleArgs a{};
   a.aq = aq; a.fg = fg; a.sc = sc; a.init_s = o.init_s;
@@ -807,8 +824,8 @@ wf_status wf_sample_ex(const float* d, const float* Ndiag, const uint8_t* mask, 
     case 32: e = wf::launch_sample<32>(a, st, &timer); break;
     case 64: e = wf::launch_sample<64>(a, st, &timer); break;
     case 128: e = wf::launch_sample<128>(a, st, &timer); break;
-    case 256: e = wf::launch_csample<256>(a, st, &timer); break;
-    case 512: e = wf::launch_csample<512>(a, st, &timer); break;
+    case 256:
+    case 512: e = launch_csample_any(H, cluster_rows_of(H, 0), a, st, &timer); break;
   }
   if (e != cudaSuccess) return cuda_fail(e);
   wf::Scalars hsc;
@@ -1219,6 +1236,7 @@ long long batch_slot_any(int H) {
 struct GBChunk {
   int H = 0, stream = 0;
   bool cluster = false;
+  int rows = 0;  // rows per CTA of the cluster kernels
   std::vector<int> items;  // batch item indices
   size_t o_fields = 0, o_idx = 0, o_sc = 0, o_state = 0, o_acc = 0, o_bn = 0, o_active = 0, o_bar = 0, o_tr = 0,
          o_tc = 0, o_tw = 0, o_data = 0, per_field = 0;
@@ -1393,12 +1411,14 @@ cudaError_t launch_bsolve_any(int H, const wf::BSolveArgs& a, cudaStream_t st) {
   }
   return cudaErrorInvalidValue;
 }
-cudaError_t launch_bsample_any(int H, const wf::BSampleArgs& a, cudaStream_t st) {
+// fpc: images per sampler CTA, clamped to 1 .. 128 / H (0: 128 / H)
+cudaError_t launch_bsample_any(int H, const wf::BSampleArgs& a, int fpc, cudaStream_t st) {
+  if (fpc > 128 / H) fpc = 128 / H;
   switch (H) {
-    case 16: return wf::launch_bsample<16>(a, st);
-    case 32: return wf::launch_bsample<32>(a, st);
-    case 64: return wf::launch_bsample<64>(a, st);
-    case 128: return wf::launch_bsample<128>(a, st);
+    case 16: return wf::launch_bsample<16>(a, fpc, st);
+    case 32: return wf::launch_bsample<32>(a, fpc, st);
+    case 64: return wf::launch_bsample<64>(a, fpc, st);
+    case 128: return wf::launch_bsample<128>(a, fpc, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -1463,7 +1483,7 @@ wf_status run_small(const SmallClass& c, const wf::BatchItem* d_items, wf::Batch
   pa.sc = sc;
   pa.F = F;
   pa.n_samples = o.n_samples;
-  if ((e = launch_bsample_any(H, pa, st)) != cudaSuccess) return cuda_fail(e);
+  if ((e = launch_bsample_any(H, pa, o.small_fields_per_cta, st)) != cudaSuccess) return cuda_fail(e);
   return WF_OK;
 }
 
@@ -1483,7 +1503,7 @@ wf_status run_chunk(const GBChunk& c, const wf::BatchItem* d_items, wf::BatchRes
   WF_CUDA(cudaGetLastError());
   const long long tab = (long long)F * (size_t(H) * H + size_t(H) * (H / 2 + 1));
   k_tables_fields<<<int((tab + 255) / 256 < 4096 ? (tab + 255) / 256 : 4096), 256, 0, st>>>(
-      d_items, idx, fields, sc, F, H, c.cluster ? H / wf::cluster_rows(H) : 0);
+      d_items, idx, fields, sc, F, H, c.cluster ? H / c.rows : 0);
   WF_CUDA(cudaGetLastError());
   if (c.cluster) {
     wf::CBArgs cb{};
@@ -1498,7 +1518,7 @@ wf_status run_chunk(const GBChunk& c, const wf::BatchItem* d_items, wf::BatchRes
     cb.level_max = o.level_max;
     cb.check = o.check;
     cb.n_samples = o.n_samples;
-    const cudaError_t e = H == 256 ? wf::launch_cpipe<256>(cb, st, nullptr) : wf::launch_cpipe<512>(cb, st, nullptr);
+    const cudaError_t e = launch_cpipe_any(H, c.rows, cb, st, nullptr);
     if (e != cudaSuccess) return cuda_fail(e);
     return WF_OK;
   }
@@ -1575,7 +1595,10 @@ struct BatchPlan {
 bool batch_opts_ok(const wf_batch_opts& o) {
   return o.tol >= 0.0 && o.eta > 0.0 && o.eta < 1.0 && o.level_max >= 1 && o.check >= 1 && o.max_iter >= 1 &&
          o.n_samples >= 0 && o.large_streams >= 1 && o.small_grid_pct >= 0 && o.small_grid_pct <= 100 &&
-         o.large_grid_pct >= 0 && o.large_grid_pct <= 100 && (o.small_path == 0 || o.small_path == 1);
+         o.large_grid_pct >= 0 && o.large_grid_pct <= 100 && (o.small_path == 0 || o.small_path == 1) &&
+         (o.large_cluster_rows == 0 || o.large_cluster_rows == 32 || o.large_cluster_rows == 64) &&
+         (o.small_fields_per_cta == 0 || o.small_fields_per_cta == 1 || o.small_fields_per_cta == 2 ||
+          o.small_fields_per_cta == 4 || o.small_fields_per_cta == 8);
 }
 
 wf_status plan_batch(const wf_batch_item* items, int n_items, const wf_batch_opts& o, BatchPlan* p) {
@@ -1627,7 +1650,8 @@ wf_status plan_batch(const wf_batch_item* items, int n_items, const wf_batch_opt
       ch.H = kBatchSizes[c];
       ch.stream = k;
       for (int i = k * nc / parts; i < (k + 1) * nc / parts; ++i) ch.items.push_back(p->cls[c][i]);
-      ch.cluster = use_cluster(ch.H, int(ch.items.size()));
+      ch.cluster = use_cluster(ch.H, int(ch.items.size()), o.large_cluster_rows);
+      ch.rows = cluster_rows_of(ch.H, o.large_cluster_rows);
       layout_chunk(ch, cv);
       p->chunks.push_back(std::move(ch));
     }
@@ -1914,15 +1938,22 @@ wf_status wf_batch_autotune(const wf_batch_item* items, int32_t n_items, wf_batc
       }
     }
   };
+  bool has_512 = false;
+  for (int i = 0; i < n_items; ++i) has_512 |= items[i].H == 512;
   if (has_large) {
     try_knob(&wf_batch_opts::large_grid_pct, {100, 50, 25, 12});
     try_knob(&wf_batch_opts::large_streams, {1, 2, 4, 8, 16});
   }
+  if (has_512) try_knob(&wf_batch_opts::large_cluster_rows, {32, 64});
   bool has_small = false;
   for (int i = 0; i < n_items; ++i) has_small |= items[i].H <= 128;
+  int min_small = 1024;
+  for (int i = 0; i < n_items; ++i)
+    if (items[i].H < min_small) min_small = items[i].H;
   if (has_small) {
     try_knob(&wf_batch_opts::small_path, {0, 1});
     if (best.small_path == 1) try_knob(&wf_batch_opts::small_grid_pct, {100, 50, 25});
+    if (best.small_path == 0 && min_small < 128) try_knob(&wf_batch_opts::small_fields_per_cta, {1, 2, 4, 8});
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

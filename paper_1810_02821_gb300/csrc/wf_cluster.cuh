@@ -29,17 +29,15 @@
 
 namespace wf {
 
-// rows per CTA (the local transform length): 64 at 256^2 (clusters of 4 CTAs, 3 per SM); 32 at 512^2
-// (clusters of 16 CTAs of 66 KB, 2 per SM, instead of 8 CTAs of 130 KB, 1 per SM)
-#ifndef WF_CLUSTER_ROWS_512
-#define WF_CLUSTER_ROWS_512 32
-#endif
-__host__ __device__ constexpr int cluster_rows(int N) { return N == 512 ? WF_CLUSTER_ROWS_512 : 64; }
+// rows per CTA (the local transform length), by default: 64 at 256^2 (clusters of 4 CTAs, 3 per SM); 32 at
+// 512^2 (clusters of 16 CTAs of 66 KB, 2 per SM). 512^2 is also built with 64 rows (clusters of 8 CTAs of
+// 130 KB, 1 per SM), which the batch autotuner can choose.
+__host__ __device__ constexpr int cluster_rows(int N) { return N == 512 ? 32 : 64; }
 
-template <int N_>
+template <int N_, int M_>
 struct CGeo {
   static constexpr int N = N_, H = N_, W = N_;
-  static constexpr int M = cluster_rows(N_);  // rows per CTA = local transform length
+  static constexpr int M = M_;  // rows per CTA = local transform length
   static constexpr int A = M;
   static constexpr int P = N / M;             // CTAs per cluster
   static constexpr int L = N / 2;             // complex length of a row transform = threads per CTA
@@ -62,9 +60,9 @@ struct CGeo {
 // row passes (R threads per row, h = the thread's index within its row)
 // ---------------------------------------------------------------------------------------------
 // local row a and index h of thread tid: a warp holds 32/R rows, thread h of each in lanes 32h/R ..
-template <int N>
+template <int N, int MR>
 WF_HD void crow_of(int tid, int& a, int& h) {
-  constexpr int per = 32 / CGeo<N>::R;
+  constexpr int per = 32 / CGeo<N, MR>::R;
   const int lane = tid % 32;
   a = (tid / 32) * per + lane % per;
   h = lane / per;
@@ -90,9 +88,9 @@ WF_HD void c_c2r_pair(float2& a, float2& b, float2 w) {
 }
 
 // forward: staged real row (slot i = (s[2i], s[2i+1])) -> packed half spectrum in digit-reversed slots
-template <int N>
+template <int N, int MR>
 __device__ __forceinline__ void crow_fwd(float2* row, int h, const float2* tw) {
-  using G = CGeo<N>;
+  using G = CGeo<N, MR>;
   constexpr int R = G::R;
   {
     float2 x[G::M];
@@ -139,9 +137,9 @@ __device__ __forceinline__ void crow_fwd(float2* row, int h, const float2* tw) {
 }
 
 // inverse: packed half spectrum (digit-reversed slots) -> real row in natural slots (unnormalised)
-template <int N>
+template <int N, int MR>
 __device__ __forceinline__ void crow_inv(float2* row, int h, const float2* tw) {
-  using G = CGeo<N>;
+  using G = CGeo<N, MR>;
   constexpr int R = G::R;
   for (int u = h; u <= G::M / 2; u += R) {
     const int v = G::M - u;
@@ -188,10 +186,10 @@ __device__ __forceinline__ void crow_inv(float2* row, int h, const float2* tw) {
 // t-draw of global row y on its staged row: t = a + q (q s + sqrt(tau) xi), table aq[x*H + ty] =
 // ((1 - w) d, sqrt(w)) with the CTA-contiguous row index ty = b*M + a; Philox stream 0, group y*W/4 + q
 // feeds pixels 4q .. 4q+3 (q = h, h + R, ...)
-template <int N>
+template <int N, int MR>
 __device__ __forceinline__ void ct_draw(float2* row, int y, int ty, int h, const float2* __restrict__ aq,
                                         float sqrt_tau, uint32_t step, uint32_t chain, uint32_t k0, uint32_t k1) {
-  using G = CGeo<N>;
+  using G = CGeo<N, MR>;
 #pragma unroll 2
   for (int q = h; q < G::W / 4; q += G::R) {
     float z[4];
@@ -212,9 +210,9 @@ __device__ __forceinline__ void ct_draw(float2* row, int y, int ty, int h, const
 // column passes
 // ---------------------------------------------------------------------------------------------
 // local forward: M-point FFT down slot t of this CTA's rows, output k' twiddled by W_N^(b k')
-template <int N>
+template <int N, int MR>
 __device__ __forceinline__ void ccol_fwd(float2* rows, int t, int b, const float2* tw) {
-  using G = CGeo<N>;
+  using G = CGeo<N, MR>;
   float2 x[G::M];
 #pragma unroll
   for (int a = 0; a < G::M; ++a) x[a] = rows[a * G::SP + t];
@@ -223,9 +221,9 @@ __device__ __forceinline__ void ccol_fwd(float2* rows, int t, int b, const float
   for (int k = 0; k < G::M; ++k) rows[k * G::SP + t] = k == 0 ? x[0] : cmul(x[k], tw[b * k]);
 }
 // local inverse: untwiddle by W_N^(-b k'), inverse M-point FFT back to the rows
-template <int N>
+template <int N, int MR>
 __device__ __forceinline__ void ccol_inv(float2* rows, int t, int b, const float2* tw) {
-  using G = CGeo<N>;
+  using G = CGeo<N, MR>;
   float2 x[G::M];
 #pragma unroll
   for (int k = 0; k < G::M; ++k) {
@@ -242,11 +240,11 @@ __device__ __forceinline__ void ccol_inv(float2* rows, int t, int b, const float
 // stream 1 group K*H/2 + ky1, variates 0, 1 for ky1 and 2, 3 for ky2. Packed edge column (K = 0: kx = 0 as
 // A and kx = W/2 as B in Y = A + i B): group ky1 draws (ky1, 0) from variates 0, 1 and (ky1, W/2) from
 // 2, 3, the conjugates filling ky2; group 0 holds the four real modes (0,0), (H/2,0), (0,W/2), (H/2,W/2).
-template <int N>
+template <int N, int MR>
 __device__ __forceinline__ void cdraw_pair(float2& y1, float2& y2, int K, int ky1, int ky2,
                                            const float2* __restrict__ fg, uint32_t step, uint32_t chain,
                                            uint32_t k0, uint32_t k1) {
-  using G = CGeo<N>;
+  using G = CGeo<N, MR>;
   float z[4];
   normals4(uint32_t(K * (G::H / 2) + ky1), step, chain, 1u, k0, k1, z);
   if (K != 0) {
@@ -278,9 +276,9 @@ __device__ __forceinline__ void cdraw_pair(float2& y1, float2& y2, int K, int ky
 // fn(K, y1, y2, ky1, ky2), and with WRITE scatters the inverse stage back. g = the thread's index in the
 // cluster. Every mode of the half spectrum is in exactly one pair of one unit, and there are L M / 2 units
 // of equal size, a whole number per thread of the cluster (one each at 512^2, eight at 256^2).
-template <int N, bool WRITE, class F>
+template <int N, int MR, bool WRITE, class F>
 __device__ __forceinline__ void ccol_units(cooperative_groups::cluster_group& cl, float2* rows, int g, F&& fn) {
-  using G = CGeo<N>;
+  using G = CGeo<N, MR>;
   constexpr int P = G::P, L = G::L, R = G::R;
   constexpr int M = G::M;
   static_assert((L * (M / 2)) % (P * L) == 0, "equal work units per thread");
@@ -319,12 +317,12 @@ __device__ __forceinline__ void ccol_units(cooperative_groups::cluster_group& cl
 }
 
 // the s-draw of Alg. 1 on every mode
-template <int N>
+template <int N, int MR>
 __device__ __forceinline__ void ccol_draw(cooperative_groups::cluster_group& cl, float2* rows, int g,
                                           const float2* __restrict__ fg, uint32_t step, uint32_t chain,
                                           uint32_t k0, uint32_t k1) {
-  ccol_units<N, true>(cl, rows, g, [&](int K, float2& y1, float2& y2, int ky1, int ky2) {
-    cdraw_pair<N>(y1, y2, K, ky1, ky2, fg, step, chain, k0, k1);
+  ccol_units<N, MR, true>(cl, rows, g, [&](int K, float2& y1, float2& y2, int ky1, int ky2) {
+    cdraw_pair<N, MR>(y1, y2, K, ky1, ky2, fg, step, chain, k0, k1);
   });
 }
 
@@ -333,11 +331,11 @@ __device__ __forceinline__ void ccol_draw(cooperative_groups::cluster_group& cl,
 // is summed over the full spectrum (the mirror modes counted; returned as this thread's share, summed in
 // FP32 over its units); with STORE
 // the new modes go to prev[ky * W/2 + K] (packed edge column as stored).
-template <int N>
+template <int N, int MR>
 __device__ __forceinline__ double ccol_wf(cooperative_groups::cluster_group& cl, float2* rows, int g,
                                           const float* __restrict__ Pk, float lt_, float2* __restrict__ prev,
                                           bool cmp, bool store) {
-  using G = CGeo<N>;
+  using G = CGeo<N, MR>;
   constexpr int WH = G::WH, LR = G::L;
   constexpr float INV_N = 1.0f / float(G::H * G::W);
   const float inv_lt = 1.0f / lt_;
@@ -347,7 +345,7 @@ __device__ __forceinline__ double ccol_wf(cooperative_groups::cluster_group& cl,
   };
   auto fcoef = [&](float P) { return wf_fdiv(P, P + lt_) * INV_N; };
   float acc = 0.0f;  // this thread's units in FP32; the cluster sum is FP64
-  ccol_units<N, true>(cl, rows, g, [&](int K, float2& y1, float2& y2, int ky1, int ky2) {
+  ccol_units<N, MR, true>(cl, rows, g, [&](int K, float2& y1, float2& y2, int ky1, int ky2) {
     if (K != 0) {
       const float P1 = WF_LDG(Pk + ky1 * WH + K), P2 = WF_LDG(Pk + ky2 * WH + K);
       const float2 n1 = cscale(y1, fcoef(P1)), n2 = cscale(y2, fcoef(P2));
@@ -394,14 +392,14 @@ __device__ __forceinline__ double ccol_wf(cooperative_groups::cluster_group& cl,
 }
 
 // sum over the full spectrum of P^2 |V|^2 for the forward transform V (level norms); this thread's share
-template <int N>
+template <int N, int MR>
 __device__ __forceinline__ double ccol_p2(cooperative_groups::cluster_group& cl, float2* rows, int g,
                                           const float* __restrict__ Pk) {
-  using G = CGeo<N>;
+  using G = CGeo<N, MR>;
   constexpr int WH = G::WH;
   auto p2 = [](float P, float re, float im) -> float { return P * P * fmaf(re, re, im * im); };
   float acc = 0.0f;
-  ccol_units<N, false>(cl, rows, g, [&](int K, float2& y1, float2& y2, int ky1, int ky2) {
+  ccol_units<N, MR, false>(cl, rows, g, [&](int K, float2& y1, float2& y2, int ky1, int ky2) {
     if (K != 0) {
       acc += 2.0f * (p2(WF_LDG(Pk + ky1 * WH + K), y1.x, y1.y) + p2(WF_LDG(Pk + ky2 * WH + K), y2.x, y2.y));
     } else if (ky1 == 0) {
@@ -419,9 +417,9 @@ __device__ __forceinline__ double ccol_p2(cooperative_groups::cluster_group& cl,
 
 // Wiener-filter pixel update of a row at level lambda: t = d + w (s - d), w = 1 / (1 + lambda tau / N_bar),
 // table dn[x*H + y] = (d, 1/N_bar) ((0, 0) on missing pixels: t = s), y the CTA-contiguous table row b*M + a
-template <int N>
+template <int N, int MR>
 __device__ __forceinline__ void ct_update_wf(float2* row, int y, int h, const float2* __restrict__ dn, float lt_) {
-  using G = CGeo<N>;
+  using G = CGeo<N, MR>;
   for (int x2 = h; x2 < G::W / 2; x2 += G::R) {
     float2 v = row[x2];
     const float2 c0 = WF_LDG(dn + (2 * x2) * G::H + y), c1 = WF_LDG(dn + (2 * x2 + 1) * G::H + y);
@@ -435,9 +433,9 @@ __device__ __forceinline__ void ct_update_wf(float2* row, int y, int h, const fl
 // right-hand side N_lambda^-1 d = d / (N_bar + lambda tau) of one staged row (0 on missing pixels), by the
 // row's R threads over the same slots as the pixel updates (x2 = h, h + R, ...), table row ty (CTA-
 // contiguous, so the row threads' loads coalesce); each thread writes only slots it reads next
-template <int N>
+template <int N, int MR>
 __device__ __forceinline__ void crhs_row(float2* row, int ty, int h, const float2* __restrict__ dn, float lt_) {
-  using G = CGeo<N>;
+  using G = CGeo<N, MR>;
   for (int x2 = h; x2 < G::W / 2; x2 += G::R) {
     const float2 c0 = WF_LDG(dn + (2 * x2) * G::H + ty), c1 = WF_LDG(dn + (2 * x2 + 1) * G::H + ty);
     const float nb0 = c0.y > 0.0f ? wf_rcp(c0.y) : wf_inf(), nb1 = c1.y > 0.0f ? wf_rcp(c1.y) : wf_inf();
@@ -447,10 +445,10 @@ __device__ __forceinline__ void crhs_row(float2* row, int ty, int h, const float
 
 // Cluster-wide sum of one double per thread, the same in every thread: block sums, then the P CTA sums
 // collected in CTA 0's shared slots part[0..P) and added in rank order. red: >= 33 doubles.
-template <int N>
+template <int N, int MR>
 __device__ __forceinline__ double cluster_sum(cooperative_groups::cluster_group& cl, double v, double* red,
                                               double* part) {
-  using G = CGeo<N>;
+  using G = CGeo<N, MR>;
   const double s = block_sum(v, red);
   if (threadIdx.x == 0) cl.map_shared_rank(part, 0)[cl.block_rank()] = s;
   cl.sync();
@@ -464,13 +462,13 @@ __device__ __forceinline__ double cluster_sum(cooperative_groups::cluster_group&
 // ---------------------------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------------------------
-template <int N>
-constexpr int csample_min_ctas() { return CGeo<N>::L <= 128 ? 3 : (CGeo<N>::M <= 32 ? 2 : 1); }
+template <int N, int MR>
+constexpr int csample_min_ctas() { return CGeo<N, MR>::L <= 128 ? 3 : (CGeo<N, MR>::M <= 32 ? 2 : 1); }
 
 // twiddles exp(-2 pi i j / N) (FP64, rounded once) into shared memory
-template <int N>
+template <int N, int MR>
 __device__ __forceinline__ void ctw_init(float2* tw) {
-  for (int j = threadIdx.x; j < N; j += CGeo<N>::L) {
+  for (int j = threadIdx.x; j < N; j += CGeo<N, MR>::L) {
     double sn, cs;
     sincospi(-2.0 * double(j) / double(N), &sn, &cs);
     tw[j] = make_float2(float(cs), float(sn));
@@ -478,9 +476,9 @@ __device__ __forceinline__ void ctw_init(float2* tw) {
 }
 
 // this CTA's rows of a row-major [H][W] image into the staged rows (nullptr: zero)
-template <int N>
+template <int N, int MR>
 __device__ __forceinline__ void crows_load(float2* rows, int b, const float* src) {
-  using G = CGeo<N>;
+  using G = CGeo<N, MR>;
   for (int e = threadIdx.x; e < G::A * G::L; e += G::L) {
     const int ar = e / G::L, i = e % G::L;
     float2 v = make_float2(0.f, 0.f);
@@ -490,9 +488,9 @@ __device__ __forceinline__ void crows_load(float2* rows, int b, const float* src
 }
 
 // the staged rows to this CTA's rows of an image of element type t
-template <int N>
+template <int N, int MR>
 __device__ __forceinline__ void crows_store(const float2* rows, int b, void* dst, int t) {
-  using G = CGeo<N>;
+  using G = CGeo<N, MR>;
   for (int e = threadIdx.x; e < G::A * G::L; e += G::L) {
     const int r2 = e / G::L, i = e % G::L;
     store_pair(dst, (long long)(G::P * r2 + b) * G::L + i, rows[r2 * G::SP + i], t);
@@ -501,37 +499,37 @@ __device__ __forceinline__ void crows_store(const float2* rows, int b, void* dst
 
 // Sampler sweeps (Alg. 1) of one chain by its cluster from the staged rows (the current s): sample m (the
 // state after sweep burn_in + (m + 1) thin) to out + m H W elements of type out_dtype
-template <int N>
+template <int N, int MR>
 __device__ __forceinline__ void csample_loop(cooperative_groups::cluster_group& cl, float2* rows, const float2* tw,
                                              const float2* __restrict__ aq, const float2* __restrict__ fg,
                                              float sqrt_tau, void* out_v, int out_dtype, int n_sweeps, int burn_in,
                                              int thin, uint32_t step0, uint32_t chain, uint32_t k0, uint32_t k1) {
-  using G = CGeo<N>;
+  using G = CGeo<N, MR>;
   const int tid = threadIdx.x, b = int(cl.block_rank());
   int ar, h;
-  crow_of<N>(tid, ar, h);
+  crow_of<N, MR>(tid, ar, h);
   const int y = G::P * ar + b;
   float2* row = rows + ar * G::SP;
   const int eb = out_elem_bytes(out_dtype);
   char* out = reinterpret_cast<char*>(out_v);
   for (int done = 0;;) {
     const uint32_t step = step0 + uint32_t(done);
-    ct_draw<N>(row, y, b * G::M + ar, h, aq, sqrt_tau, step, chain, k0, k1);
+    ct_draw<N, MR>(row, y, b * G::M + ar, h, aq, sqrt_tau, step, chain, k0, k1);
     __syncwarp();
-    crow_fwd<N>(row, h, tw);
+    crow_fwd<N, MR>(row, h, tw);
     __syncthreads();
-    ccol_fwd<N>(rows, tid, b, tw);
+    ccol_fwd<N, MR>(rows, tid, b, tw);
     cl.sync();  // every CTA's partial column transforms are in place
-    ccol_draw<N>(cl, rows, b * G::L + tid, fg, step, chain, k0, k1);
+    ccol_draw<N, MR>(cl, rows, b * G::L + tid, fg, step, chain, k0, k1);
     cl.sync();  // every unit's inverse stage has landed
-    ccol_inv<N>(rows, tid, b, tw);
+    ccol_inv<N, MR>(rows, tid, b, tw);
     __syncthreads();
-    crow_inv<N>(row, h, tw);
+    crow_inv<N, MR>(row, h, tw);
     ++done;
     if (done > burn_in && (done - burn_in) % thin == 0) {
       const long long m = (done - burn_in) / thin - 1;
       __syncthreads();
-      crows_store<N>(rows, b, out + m * (long long)(G::H * G::W) * eb, out_dtype);
+      crows_store<N, MR>(rows, b, out + m * (long long)(G::H * G::W) * eb, out_dtype);
       __syncthreads();
     }
     if (done == n_sweeps) break;
@@ -543,31 +541,31 @@ __device__ __forceinline__ void csample_loop(cooperative_groups::cluster_group& 
 // s = 0, with the per-level norms ||S N_lambda^-1 d||^2 computed first. Leaves s_W in the staged rows and
 // returns the wf_status (0 converged, 5 not converged, 6 non-finite); it and rho receive the sweeps and
 // the last measured residual. red: 33 doubles, part: P doubles, bn: kMaxLevels doubles (shared).
-template <int N>
+template <int N, int MR>
 __device__ __forceinline__ int csolve_loop(cooperative_groups::cluster_group& cl, float2* rows, const float2* tw,
                                            double* red, double* part, double* bn, const float2* __restrict__ dn,
                                            const float* __restrict__ Pk, const Scalars& sc, float2* prev, double tol,
                                            double eta, double level_tol, int max_iter, int level_max, int check,
                                            int& it, double& rho) {
-  using G = CGeo<N>;
+  using G = CGeo<N, MR>;
   const int tid = threadIdx.x, b = int(cl.block_rank()), g = b * G::L + tid;
   int ar, h;
-  crow_of<N>(tid, ar, h);
+  crow_of<N, MR>(tid, ar, h);
   const int y = G::P * ar + b;
   float2* row = rows + ar * G::SP;
   constexpr double NPIX = double(G::H) * double(G::W);
   for (int lev = 0; lev < sc.n_levels; ++lev) {  // level norms
-    crhs_row<N>(row, b * G::M + ar, h, dn, float(level_lambda(sc, lev, eta) * sc.tau));
+    crhs_row<N, MR>(row, b * G::M + ar, h, dn, float(level_lambda(sc, lev, eta) * sc.tau));
     __syncwarp();
-    crow_fwd<N>(row, h, tw);
+    crow_fwd<N, MR>(row, h, tw);
     __syncthreads();
-    ccol_fwd<N>(rows, tid, b, tw);
+    ccol_fwd<N, MR>(rows, tid, b, tw);
     cl.sync();
-    const double tot = cluster_sum<N>(cl, ccol_p2<N>(cl, rows, g, Pk), red, part);
+    const double tot = cluster_sum<N, MR>(cl, ccol_p2<N, MR>(cl, rows, g, Pk), red, part);
     if (tid == 0) bn[lev] = tot / NPIX;
     cl.sync();  // every CTA has read the partial sums and finished its remote reads of the rows
   }
-  crows_load<N>(rows, b, nullptr);
+  crows_load<N, MR>(rows, b, nullptr);
   __syncthreads();
   const double tau = sc.tau;
   int lev = 0, k = 0, status = 1;
@@ -581,16 +579,16 @@ __device__ __forceinline__ int csolve_loop(cooperative_groups::cluster_group& cl
     ++it;
     const bool cmp = (k % check == 0) && k >= 2;
     const bool store = ((k + 1) % check == 0);
-    ct_update_wf<N>(row, b * G::M + ar, h, dn, ltau);
+    ct_update_wf<N, MR>(row, b * G::M + ar, h, dn, ltau);
     __syncwarp();
-    crow_fwd<N>(row, h, tw);
+    crow_fwd<N, MR>(row, h, tw);
     __syncthreads();
-    ccol_fwd<N>(rows, tid, b, tw);
+    ccol_fwd<N, MR>(rows, tid, b, tw);
     cl.sync();
-    const double acc = ccol_wf<N>(cl, rows, g, Pk, ltau, prev, cmp, store);
+    const double acc = ccol_wf<N, MR>(cl, rows, g, Pk, ltau, prev, cmp, store);
     cl.sync();
     if (cmp) {
-      const double tot = cluster_sum<N>(cl, acc, red, part) * NPIX;
+      const double tot = cluster_sum<N, MR>(cl, acc, red, part) * NPIX;
       const double bnl = bn[lev];
       const double r2 = bnl > 0.0 ? tot / bnl : tot;
       rho = sqrt(r2);
@@ -608,9 +606,9 @@ __device__ __forceinline__ int csolve_loop(cooperative_groups::cluster_group& cl
       }
     }
     if (status == 1 && it >= max_iter) status = 5;  // not converged
-    ccol_inv<N>(rows, tid, b, tw);
+    ccol_inv<N, MR>(rows, tid, b, tw);
     __syncthreads();
-    crow_inv<N>(row, h, tw);
+    crow_inv<N, MR>(row, h, tw);
     if (status != 1) break;
     __syncwarp();
   }
@@ -619,9 +617,9 @@ __device__ __forceinline__ int csolve_loop(cooperative_groups::cluster_group& cl
 }
 
 // one problem, grid = n_chains clusters of P CTAs (chain = cluster index)
-template <int N>
-__global__ void __launch_bounds__(N / 2, csample_min_ctas<N>()) k_csample(SampleArgs a) {
-  using G = CGeo<N>;
+template <int N, int MR>
+__global__ void __launch_bounds__(N / 2, csample_min_ctas<N, MR>()) k_csample(SampleArgs a) {
+  using G = CGeo<N, MR>;
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -630,10 +628,10 @@ __global__ void __launch_bounds__(N / 2, csample_min_ctas<N>()) k_csample(Sample
   if (a.sc->status != 0) return;  // uniform over the grid
   const long long ci = blockIdx.x / G::P;
   const int eb = out_elem_bytes(a.out_dtype);
-  ctw_init<N>(tw);
-  crows_load<N>(rows, int(cl.block_rank()), a.init_s ? a.init_s + ci * a.init_stride : nullptr);
+  ctw_init<N, MR>(tw);
+  crows_load<N, MR>(rows, int(cl.block_rank()), a.init_s ? a.init_s + ci * a.init_stride : nullptr);
   __syncthreads();
-  csample_loop<N>(cl, rows, tw, a.aq, a.fg, a.sc->sqrt_tau,
+  csample_loop<N, MR>(cl, rows, tw, a.aq, a.fg, a.sc->sqrt_tau,
                   reinterpret_cast<char*>(a.out) + ci * a.n_samples * (long long)(G::H * G::W) * eb, a.out_dtype,
                   a.n_sweeps, a.burn_in, a.thin, a.step0, a.chain0 + uint32_t(ci), a.key0, a.key1);
   cl.sync();  // no CTA leaves while another may still address its shared memory
@@ -651,9 +649,9 @@ struct CBArgs {
   double tol, eta, level_tol;
   int max_iter, level_max, check, n_samples;
 };
-template <int N>
-__global__ void __launch_bounds__(N / 2, csample_min_ctas<N>()) k_cpipe(CBArgs a) {
-  using G = CGeo<N>;
+template <int N, int MR>
+__global__ void __launch_bounds__(N / 2, csample_min_ctas<N, MR>()) k_cpipe(CBArgs a) {
+  using G = CGeo<N, MR>;
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -670,17 +668,17 @@ __global__ void __launch_bounds__(N / 2, csample_min_ctas<N>()) k_cpipe(CBArgs a
     if (lead) a.res[fd.item] = BatchResult{-1.0, 0, sc.status};
     return;
   }
-  ctw_init<N>(tw);
+  ctw_init<N, MR>(tw);
   __syncthreads();
   int it = 0;
   double rho = -1.0;
-  const int status = csolve_loop<N>(cl, rows, tw, red, part, bn, fd.dn, fd.Pk, sc, fd.prev, a.tol, a.eta,
+  const int status = csolve_loop<N, MR>(cl, rows, tw, red, part, bn, fd.dn, fd.Pk, sc, fd.prev, a.tol, a.eta,
                                     a.level_tol, a.max_iter, a.level_max, a.check, it, rho);
-  if (fd.out_wf) crows_store<N>(rows, int(cl.block_rank()), fd.out_wf, kOutF32);
+  if (fd.out_wf) crows_store<N, MR>(rows, int(cl.block_rank()), fd.out_wf, kOutF32);
   if (lead) a.res[fd.item] = BatchResult{rho, it, status};
   __syncthreads();
   if (a.n_samples > 0 && fd.out_samples)
-    csample_loop<N>(cl, rows, tw, fd.aq, fd.fg, sc.sqrt_tau, fd.out_samples, kOutF32, a.n_samples, 0, 1, 0u,
+    csample_loop<N, MR>(cl, rows, tw, fd.aq, fd.fg, sc.sqrt_tau, fd.out_samples, kOutF32, a.n_samples, 0, 1, 0u,
                     fd.chain, fd.key0, fd.key1);
   cl.sync();  // no CTA leaves while another may still address its shared memory
 }

@@ -1,7 +1,7 @@
-// Cluster-resident sampler for 512x512 images (field in the distributed shared memory of one cluster).
+// Cluster-resident sampler and batch pipeline for 512x512 images (clusters of 16 CTAs of 32 rows).
 #define WF_LAUNCH_DEFINE_CLUSTER
 #include "wf_launch.h"
 
 namespace wf {
-WF_INSTANTIATE_CLUSTER(512)
+WF_INSTANTIATE_CLUSTER(512, 32)
 }  // namespace wf

@@ -1,0 +1,7 @@
+// Cluster-resident sampler and batch pipeline for 512x512 images (clusters of 8 CTAs of 64 rows).
+#define WF_LAUNCH_DEFINE_CLUSTER
+#include "wf_launch.h"
+
+namespace wf {
+WF_INSTANTIATE_CLUSTER(512, 64)
+}  // namespace wf

@@ -38,13 +38,12 @@ cudaError_t launch_solve(const SolveArgs& a, const BnormArgs& b, cudaStream_t st
 template <int N>
 cudaError_t launch_batch(const BatchArgs& b, int* grid_out, cudaStream_t st);
 
-// batched form for N <= 128 in phases (after the per-image set-up kernels): one CTA per image and level
-// for the level norms, one CTA per image for the cooled solves, then the samplers with
-// fields_per_cta<N>() images per CTA
+// batched form for N <= 128 in phases (after the per-image set-up kernels): a few CTAs per image for the
+// level norms, one CTA per image for the cooled solves, then the samplers with fpc images per CTA
 template <int N>
 cudaError_t launch_bsolve(const BSolveArgs& a, cudaStream_t st);
 template <int N>
-cudaError_t launch_bsample(const BSampleArgs& a, cudaStream_t st);
+cudaError_t launch_bsample(const BSampleArgs& a, int fpc, cudaStream_t st);
 
 // weighted spectral power of real fields (N <= 128, one CTA per field)
 template <int N>
@@ -60,15 +59,15 @@ cudaError_t launch_global(const GlobalArgs& a, cudaStream_t st, LaunchTimer* t);
 template <int N>
 cudaError_t launch_gbatch(const GBArgs& a, cudaStream_t st);
 
-// cluster-resident sampler (N in {256, 512}): one cluster of N / 64 CTAs per chain.
-// cudaErrorNotSupported when no cluster of that shape can be resident on the device.
-template <int N>
+// cluster-resident sampler (N in {256, 512}): one cluster of N / MR CTAs of MR rows each per chain
+// (MR = 64 at 256; 32 or 64 at 512). cudaErrorNotSupported when no cluster of that shape can be resident.
+template <int N, int MR>
 cudaError_t launch_csample(const SampleArgs& a, cudaStream_t st, LaunchTimer* t);
-// clusters of k_csample<N> that can be resident at once on the current device (0: none)
-template <int N>
+// clusters of k_csample<N, MR> that can be resident at once on the current device (0: none)
+template <int N, int MR>
 cudaError_t csample_clusters(int* clusters);
 // whole pipeline (level norms, cooled solve, samples) of a batch of large images: one cluster per image
-template <int N>
+template <int N, int MR>
 cudaError_t launch_cpipe(const CBArgs& a, cudaStream_t st, LaunchTimer* t);
 
 // definitions, included by the per-size translation units only
@@ -174,15 +173,28 @@ cudaError_t launch_bsolve(const BSolveArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int N>
-cudaError_t launch_bsample(const BSampleArgs& a, cudaStream_t st) {
-  constexpr int FPC = fields_per_cta<N>();
+template <int N, int FPC>
+cudaError_t launch_bsample_fpc(const BSampleArgs& a, cudaStream_t st) {
   const int smem = FPC * Geo<N>::FIELD_BYTES;
   auto kern = k_bsample<N, FPC>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   if (a.F > 0 && a.n_samples > 0) kern<<<(a.F + FPC - 1) / FPC, N * FPC, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+// fields (images) per CTA fpc in 1 .. 128 / N (0: fields_per_cta<N>())
+template <int N>
+cudaError_t launch_bsample(const BSampleArgs& a, int fpc, cudaStream_t st) {
+  if (fpc == 0) fpc = fields_per_cta<N>();
+  if (fpc < 1 || fpc > fields_per_cta<N>()) return cudaErrorInvalidValue;
+  switch (fpc) {
+    case 1: return launch_bsample_fpc<N, 1>(a, st);
+    case 2: if constexpr (fields_per_cta<N>() >= 2) return launch_bsample_fpc<N, 2>(a, st); break;
+    case 4: if constexpr (fields_per_cta<N>() >= 4) return launch_bsample_fpc<N, 4>(a, st); break;
+    case 8: if constexpr (fields_per_cta<N>() >= 8) return launch_bsample_fpc<N, 8>(a, st); break;
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <int N>
@@ -202,7 +214,7 @@ cudaError_t launch_wpower(const WpowerArgs& p, cudaStream_t st) {
   template cudaError_t launch_batch<N>(const BatchArgs&, int*, cudaStream_t);                     \
   template cudaError_t batch_grid<N>(int, int, int*);                                                   \
   template cudaError_t launch_bsolve<N>(const BSolveArgs&, cudaStream_t);                                \
-  template cudaError_t launch_bsample<N>(const BSampleArgs&, cudaStream_t);                              \
+  template cudaError_t launch_bsample<N>(const BSampleArgs&, int, cudaStream_t);                         \
   template cudaError_t launch_wpower<N>(const WpowerArgs&, cudaStream_t);
 #endif
 
@@ -255,17 +267,17 @@ cudaError_t launch_gbatch(const GBArgs& a, cudaStream_t st) {
 #endif
 
 #if defined(WF_LAUNCH_DEFINE_CLUSTER)
-template <int N>
+template <int N, int MR>
 cudaError_t csample_config(cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr, int n_chains, cudaStream_t st) {
-  using G = CGeo<N>;
-  cudaError_t e = cudaFuncSetAttribute(k_csample<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+  using G = CGeo<N, MR>;
+  cudaError_t e = cudaFuncSetAttribute(k_csample<N, MR>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_cpipe<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+  e = cudaFuncSetAttribute(k_cpipe<N, MR>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
   if (e != cudaSuccess) return e;
   if (G::P > 8) {  // clusters above the portable size of 8
-    e = cudaFuncSetAttribute(k_csample<N>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(k_csample<N, MR>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_cpipe<N>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(k_cpipe<N, MR>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
   }
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -281,40 +293,40 @@ cudaError_t csample_config(cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr, i
   cfg->numAttrs = 1;
   return cudaSuccess;
 }
-template <int N>
+template <int N, int MR>
 cudaError_t csample_clusters(int* clusters) {
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
-  cudaError_t e = csample_config<N>(&cfg, attr, 1, nullptr);
+  cudaError_t e = csample_config<N, MR>(&cfg, attr, 1, nullptr);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveClusters(clusters, k_csample<N>, &cfg);
+  return cudaOccupancyMaxActiveClusters(clusters, k_csample<N, MR>, &cfg);
 }
-template <int N>
+template <int N, int MR>
 cudaError_t launch_csample(const SampleArgs& a, cudaStream_t st, LaunchTimer* t) {
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
-  cudaError_t e = csample_config<N>(&cfg, attr, a.n_chains, st);
+  cudaError_t e = csample_config<N, MR>(&cfg, attr, a.n_chains, st);
   if (e != cudaSuccess) return e;
   if (t) t->start();
-  e = cudaLaunchKernelEx(&cfg, k_csample<N>, a);
+  e = cudaLaunchKernelEx(&cfg, k_csample<N, MR>, a);
   if (t) t->stop();
   return e != cudaSuccess ? e : cudaGetLastError();
 }
-template <int N>
+template <int N, int MR>
 cudaError_t launch_cpipe(const CBArgs& a, cudaStream_t st, LaunchTimer* t) {
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
-  cudaError_t e = csample_config<N>(&cfg, attr, a.F, st);
+  cudaError_t e = csample_config<N, MR>(&cfg, attr, a.F, st);
   if (e != cudaSuccess) return e;
   if (t) t->start();
-  e = cudaLaunchKernelEx(&cfg, k_cpipe<N>, a);
+  e = cudaLaunchKernelEx(&cfg, k_cpipe<N, MR>, a);
   if (t) t->stop();
   return e != cudaSuccess ? e : cudaGetLastError();
 }
-#define WF_INSTANTIATE_CLUSTER(N)                                                            \
-  template cudaError_t launch_csample<N>(const SampleArgs&, cudaStream_t, LaunchTimer*);     \
-  template cudaError_t csample_clusters<N>(int*);                                            \
-  template cudaError_t launch_cpipe<N>(const CBArgs&, cudaStream_t, LaunchTimer*);
+#define WF_INSTANTIATE_CLUSTER(N, MR)                                                          \
+  template cudaError_t launch_csample<N, MR>(const SampleArgs&, cudaStream_t, LaunchTimer*);   \
+  template cudaError_t csample_clusters<N, MR>(int*);                                          \
+  template cudaError_t launch_cpipe<N, MR>(const CBArgs&, cudaStream_t, LaunchTimer*);
 #endif
 
 }  // namespace wf

@@ -60,7 +60,8 @@ class BatchOpts(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("tol", ctypes.c_double), ("eta", ctypes.c_double),
                 ("level_tol", ctypes.c_double), ("level_max", ctypes.c_int32), ("check", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("n_samples", ctypes.c_int32), ("large_streams", ctypes.c_int32),
-                ("small_grid_pct", ctypes.c_int32), ("large_grid_pct", ctypes.c_int32), ("small_path", ctypes.c_int32)]
+                ("small_grid_pct", ctypes.c_int32), ("large_grid_pct", ctypes.c_int32), ("small_path", ctypes.c_int32),
+                ("large_cluster_rows", ctypes.c_int32), ("small_fields_per_cta", ctypes.c_int32)]
 
 
 _lib = None
@@ -427,14 +428,16 @@ def _batch_items(images, n_samples: int):
 
 
 def _batch_opts(n_samples=0, tau=0.0, tol=1e-5, eta=0.5, level_tol=1e-2, level_max=64, check=4, max_iter=20000,
-                large_streams=8, small_grid_pct=0, large_grid_pct=0, small_path=0) -> BatchOpts:
+                large_streams=8, small_grid_pct=0, large_grid_pct=0, small_path=0, large_cluster_rows=0,
+                small_fields_per_cta=0) -> BatchOpts:
     L = load_library()
     o = BatchOpts()
     L.wf_batch_opts_default(ctypes.byref(o))
     o.tau, o.tol, o.eta, o.level_tol = float(tau), float(tol), float(eta), float(level_tol)
     o.level_max, o.check, o.max_iter, o.n_samples = int(level_max), int(check), int(max_iter), int(n_samples)
     o.large_streams, o.small_grid_pct, o.large_grid_pct = int(large_streams), int(small_grid_pct), int(large_grid_pct)
-    o.small_path = int(small_path)
+    o.small_path, o.large_cluster_rows = int(small_path), int(large_cluster_rows)
+    o.small_fields_per_cta = int(small_fields_per_cta)
     return o
 
 
@@ -447,7 +450,7 @@ def wf_batch_run(images, *, n_samples: int = 0, stream=None, allow_not_converged
     """Wiener filter + ``n_samples`` posterior samples for every image (C call ``wf_batch_run``).
 
     ``opts``: tau, tol, eta, level_tol, level_max, check, max_iter, large_streams, small_grid_pct,
-    large_grid_pct, small_path (as ``wf_batch_opts``). Fills ``out_wf``, ``out_samples``, ``status``, ``iters`` and
+    large_grid_pct, small_path, large_cluster_rows, small_fields_per_cta (as ``wf_batch_opts``). Fills ``out_wf``, ``out_samples``, ``status``, ``iters`` and
     ``resid`` of each ``BatchImage``.
     """
     L = load_library()
@@ -510,7 +513,8 @@ def wf_batch_autotune(images, *, n_samples: int = 0, reps: int = 1, stream=None,
     _check(L.wf_batch_autotune(arr, len(images), ctypes.byref(o), int(reps), ctypes.byref(best), _stream_ptr(stream)),
            "wf_batch_autotune")
     return dict(large_streams=o.large_streams, small_grid_pct=o.small_grid_pct,
-                large_grid_pct=o.large_grid_pct, small_path=o.small_path), best.value
+                large_grid_pct=o.large_grid_pct, small_path=o.small_path,
+                large_cluster_rows=o.large_cluster_rows, small_fields_per_cta=o.small_fields_per_cta), best.value
 
 
 def wf_spectral_power(a, w, b=None, sgn: float = 1.0, stream=None):

@@ -114,18 +114,29 @@ def test_batch_graph_replays_match_the_direct_run_and_follow_input_changes():
 
 
 def test_batch_launch_shapes_and_autotune_keep_the_results():
-    sizes = [64, 128, 256, 256, 32]
+    """Every launch shape the autotuner can choose gives the same outputs: the fused and the phased
+    small-image paths, persistent grid sizes, images per sampler CTA, pipeline streams, and 512^2 clusters
+    of 16 CTAs of 32 rows or 8 CTAs of 64 rows (clusters forced for the single 512^2 image)."""
+    sizes = [64, 128, 256, 256, 32, 512]
     probs = _mixed(sizes, seed0=90)
-    ref_imgs = [wf.BatchImage(*to_dev(p), seed=i, chain=i) for i, p in enumerate(probs)]
-    wf.wf_batch_run(ref_imgs, n_samples=2, tol=1e-5)
-    ref = _outputs(ref_imgs)
-    imgs = [wf.BatchImage(*to_dev(p), seed=i, chain=i) for i, p in enumerate(probs)]
-    wf.wf_batch_run(imgs, n_samples=2, tol=1e-5, small_grid_pct=25, large_grid_pct=25, large_streams=2)
-    for (rw, rs), (gw, gs) in zip(ref, _outputs(imgs)):
-        assert rel(gw, rw) < WF_TOL and rel(gs, rs) < SAMPLE_TOL
-    chosen, ms = wf.wf_batch_autotune(imgs, n_samples=2, reps=1, tol=1e-5)
+    prev = wf.wf_set_large_image_sampler("cluster")
+    try:
+        ref_imgs = [wf.BatchImage(*to_dev(p), seed=i, chain=i) for i, p in enumerate(probs)]
+        wf.wf_batch_run(ref_imgs, n_samples=2, tol=1e-5)
+        ref = _outputs(ref_imgs)
+        imgs = [wf.BatchImage(*to_dev(p), seed=i, chain=i) for i, p in enumerate(probs)]
+        for shape in (dict(small_grid_pct=25, large_grid_pct=25, large_streams=2, small_path=1),
+                      dict(small_path=1), dict(large_cluster_rows=64), dict(large_cluster_rows=32, large_streams=1),
+                      dict(small_fields_per_cta=1), dict(small_fields_per_cta=2), dict(small_fields_per_cta=4)):
+            wf.wf_batch_run(imgs, n_samples=2, tol=1e-5, **shape)
+            for i, ((rw, rs), (gw, gs)) in enumerate(zip(ref, _outputs(imgs))):
+                assert rel(gw, rw) < WF_TOL and rel(gs, rs) < SAMPLE_TOL, (shape, sizes[i])
+        chosen, ms = wf.wf_batch_autotune(imgs, n_samples=2, reps=1, tol=1e-5)
+    finally:
+        wf.wf_set_large_image_sampler(prev)
     assert chosen["large_grid_pct"] in (0, 100, 50, 25, 12) and chosen["large_streams"] in (1, 2, 4, 8, 16)
-    assert chosen["small_grid_pct"] in (0, 100, 50, 25) and ms > 0
+    assert chosen["small_grid_pct"] in (0, 100, 50, 25) and chosen["small_path"] in (0, 1) and ms > 0
+    assert chosen["large_cluster_rows"] in (0, 32, 64) and chosen["small_fields_per_cta"] in (0, 1, 2, 4, 8)
     wf.wf_batch_run(imgs, n_samples=2, tol=1e-5, **chosen)
     for (rw, rs), (gw, gs) in zip(ref, _outputs(imgs)):
         assert rel(gw, rw) < WF_TOL and rel(gs, rs) < SAMPLE_TOL
