@@ -147,3 +147,32 @@ def test_global_memory_transform_decomposition(L, S):
     for q in range(R):                       # step C: one S-point transform per thread
         out[q + R * np.arange(S)] = np.fft.fft(w[S * q + np.arange(S)])
     assert np.max(np.abs(out - np.fft.fft(v))) < 1e-9 * L
+
+
+@pytest.mark.parametrize("L,S", [(1024, 16), (512, 16)])
+def test_global_memory_transform_split_step_a(L, S):
+    """The same transform when the R-point DFTs of step A are split in two shared-memory passes
+    (R = R1 R2, m = m2 + R2 m1, q = q1 + R1 q2): R1-point DFTs over m1 twiddled by w_R^(m2 q1), then
+    R2-point DFTs over m2 twiddled by W_L^(q n), as the kernels do when one or two warps would carry
+    step A alone."""
+    rng = np.random.default_rng(L + 7)
+    v = rng.standard_normal(L) + 1j * rng.standard_normal(L)
+    R = L // S
+    R1, R2 = 8, R // 8
+    w = v.copy()
+    for n in range(S):                       # A1: tasks (n, m2)
+        for m2 in range(R2):
+            idx = n + S * (m2 + R2 * np.arange(R1))
+            B = np.array([np.sum(w[idx] * np.exp(-2j * np.pi * np.arange(R1) * q1 / R1)) for q1 in range(R1)])
+            w[idx] = B * np.exp(-2j * np.pi * m2 * np.arange(R1) / R)
+    w2 = w.copy()
+    for n in range(S):                       # A2: tasks (n, q1)
+        for q1 in range(R1):
+            b = w[n + S * (np.arange(R2) + R2 * q1)]
+            C = np.array([np.sum(b * np.exp(-2j * np.pi * np.arange(R2) * q2 / R2)) for q2 in range(R2)])
+            q = q1 + R1 * np.arange(R2)
+            w2[n + S * q] = C * np.exp(-2j * np.pi * q * n / L)
+    out = np.empty(L, complex)
+    for q in range(R):                       # step C
+        out[q + R * np.arange(S)] = np.fft.fft(w2[S * q + np.arange(S)])
+    assert np.max(np.abs(out - np.fft.fft(v))) < 1e-9 * L
