@@ -104,7 +104,7 @@ __device__ __forceinline__ void gb_rows_in(const GBArgs& a, float2* buf, const f
   }
   __syncthreads();
   real_pass<N, false>(buf, G::RB, a.tw_real);
-  fft_smem<G::RR, G::RB, G::VROW, true, G::S>(buf, a.tw_row);
+  fft_smem<G::RR, G::RB, G::VROW, true, G::SR>(buf, a.tw_row);
 }
 
 // the real rows in buf to out[y0 .. y0+RB-1][W]
@@ -123,7 +123,7 @@ template <int N>
 __device__ __forceinline__ void gb_rows_out(const GBArgs& a, float2* buf, float2* Z, int y0) {
   using G = GGeo<N>;
   constexpr int L = G::LR;
-  fft_smem<G::RR, G::RB, G::VROW, false, G::S>(buf, a.tw_row);
+  fft_smem<G::RR, G::RB, G::VROW, false, G::SR>(buf, a.tw_row);
   real_pass<N, true>(buf, G::RB, a.tw_real);
   for (int e = threadIdx.x; e < G::RB * L; e += 128) {
     const int j = e / L, m = e % L;
@@ -143,11 +143,11 @@ __device__ __forceinline__ double gb_cols(const GBArgs& a, float2* buf, const GB
     buf[j * G::VCOL + padi(y)] = __ldcg(fd.Z + (long long)y * L + c0 + j);
   }
   __syncthreads();
-  fft_smem<G::RC, G::CB, G::VCOL, false, G::S>(buf, a.tw_col);
+  fft_smem<G::RC, G::CB, G::VCOL, false, G::SC>(buf, a.tw_col);
   const double acc =
       col_update<N>(mode, buf, c0, fd.fg, fd.Pk, fd.prev, step, fd.chain, fd.key0, fd.key1, ltau, cmp, store);
   if (mode == 2) return acc;
-  fft_smem<G::RC, G::CB, G::VCOL, true, G::S>(buf, a.tw_col);
+  fft_smem<G::RC, G::CB, G::VCOL, true, G::SC>(buf, a.tw_col);
   for (int e = threadIdx.x; e < G::CB * H; e += 128) {
     const int j = e % G::CB, y = e / G::CB;
     __stcg(fd.Z + (long long)y * L + c0 + j, buf[j * G::VCOL + padi(y)]);

@@ -19,22 +19,19 @@ namespace wf {
 // items per phase, so a single field keeps more CTAs busy: with S = 16 a 1024^2 field has 256 row and 256
 // column items per phase (64 with S = 64). Measured on GB300 (one image): 1024^2 precision solve 3.27 s
 // (S = 64) -> 2.14 s (32) -> 1.84 s (16); 256^2 solve of 184 sweeps 15.0 -> 7.2 -> 4.4 ms.
-#ifndef WF_GLOBAL_SUB_1024
-#define WF_GLOBAL_SUB_1024 16
-#endif
-#ifndef WF_GLOBAL_SUB_512
-#define WF_GLOBAL_SUB_512 16
-#endif
-#ifndef WF_GLOBAL_SUB_256
-#define WF_GLOBAL_SUB_256 16
-#endif
+// Row and column sub-transform lengths measured on GB300 (one image, after the split of large step-A
+// DFTs), microseconds per Wiener-filter sweep at 256^2 / 512^2 / 1024^2 (and ms for 4 chains x 50 samples
+// at 256^2 / 512^2): rows 16, columns 16: 23.0 / 25.1 / 42.6 (0.97 / 1.56); rows 16, columns 32: 27.7 /
+// 28.3 / 42.5; rows 32, columns 16: 34.1 / 48.7 / 65.3; rows 8, columns 16: 18.0 / 20.9 / 52.7 (0.80 /
+// 2.14). So rows of 8-point sub-transforms at 256^2 and 16 elsewhere, columns 16.
 template <int N_>
 struct GGeo {
   static constexpr int N = N_, H = N_, W = N_;
-  static constexpr int S = N_ >= 1024 ? WF_GLOBAL_SUB_1024 : (N_ >= 512 ? WF_GLOBAL_SUB_512 : WF_GLOBAL_SUB_256);
+  static constexpr int SR = N_ == 256 ? 8 : 16;  // sub-transform length of the row transforms
+  static constexpr int SC = 16;                  // ... and of the column transforms
   static constexpr int LR = W / 2;          // complex length of a row transform
-  static constexpr int RR = LR / S;         // row radix
-  static constexpr int RC = H / S;          // column radix
+  static constexpr int RR = LR / SR;        // row radix
+  static constexpr int RC = H / SC;         // column radix
   static constexpr int RB = 128 / RR;       // rows per CTA
   static constexpr int CB = 128 / RC;       // columns per CTA
   // float2 stride between vectors in shared memory: each vector carries 1 float2 of padding per 64,
@@ -349,7 +346,7 @@ __device__ void row_item(const GlobalArgs& a, float2* buf, int f, int y0, int do
     }
     __syncthreads();
     real_pass<N, false>(buf, G::RB, a.tw_real);
-    fft_smem<G::RR, G::RB, G::VROW, true, G::S>(buf, a.tw_row);
+    fft_smem<G::RR, G::RB, G::VROW, true, G::SR>(buf, a.tw_row);
   }
   // buf rows hold (s[2m], s[2m+1]) (scaled as the fused kernels: unnormalised transforms, the 1/n and
   // 1/sqrt(2n) factors are in the Fourier-space tables)
@@ -382,7 +379,7 @@ __device__ void row_item(const GlobalArgs& a, float2* buf, int f, int y0, int do
                     sc.sqrt_tau, ltau, a.rhs_mode, a.mode == 2 ? float(level_lambda(sc, f, a.eta) * sc.tau) : 0.f);
   else
     __syncthreads();
-  fft_smem<G::RR, G::RB, G::VROW, false, G::S>(buf, a.tw_row);
+  fft_smem<G::RR, G::RB, G::VROW, false, G::SR>(buf, a.tw_row);
   real_pass<N, true>(buf, G::RB, a.tw_real);
   for (int e = threadIdx.x; e < G::RB * L; e += nthr) {
     const int j = e / L, m = e % L;
@@ -523,11 +520,11 @@ __device__ double col_item(const GlobalArgs& a, float2* buf, int f, int c0, int 
     buf[j * G::VCOL + padi(y)] = __ldcg(Zf + (long long)y * L + c0 + j);
   }
   __syncthreads();
-  fft_smem<G::RC, G::CB, G::VCOL, false, G::S>(buf, a.tw_col);
+  fft_smem<G::RC, G::CB, G::VCOL, false, G::SC>(buf, a.tw_col);
   const double acc = col_update<N>(a.mode, buf, c0, a.fg, a.Pk, a.prev, a.step0 + uint32_t(done),
                                    a.chain0 + uint32_t(f), a.key0, a.key1, ltau, cmp, store);
   if (a.mode == 2) return acc;
-  fft_smem<G::RC, G::CB, G::VCOL, true, G::S>(buf, a.tw_col);
+  fft_smem<G::RC, G::CB, G::VCOL, true, G::SC>(buf, a.tw_col);
   for (int e = threadIdx.x; e < G::CB * H; e += 128) {
     const int j = e % G::CB, y = e / G::CB;
     __stcg(Zf + (long long)y * L + c0 + j, buf[j * G::VCOL + padi(y)]);
@@ -547,7 +544,7 @@ __device__ void col_wpower(const GlobalArgs& a, float2* buf, int f, int c0, doub
     buf[j * G::VCOL + padi(y)] = __ldcg(Zf + (long long)y * L + c0 + j);
   }
   __syncthreads();
-  fft_smem<G::RC, G::CB, G::VCOL, false, G::S>(buf, a.tw_col);
+  fft_smem<G::RC, G::CB, G::VCOL, false, G::SC>(buf, a.tw_col);
   auto sq = [](float p, float q) -> double { return double(p) * p + double(q) * q; };
   for (int task = threadIdx.x; task < G::CB * (H / 2); task += 128) {
     const int jc = task / (H / 2), j = task % (H / 2);
