@@ -34,15 +34,16 @@ struct GGeo {
   static constexpr int RC = H / SC;         // column radix
   static constexpr int RB = 128 / RR;       // rows per CTA
   static constexpr int CB = 128 / RC;       // columns per CTA
-  // float2 stride between vectors in shared memory: each vector carries 1 float2 of padding per 64,
-  // and the stride is odd (2 x odd when only 8 vectors share a half-warp) so that a half-warp reading
-  // the same element of consecutive vectors hits distinct banks
-  static constexpr int vstride(int len, int nv) {
-    const int v = len + len / 64;
+  // float2 stride between vectors in shared memory: each vector carries 1 float2 of padding per 64 and
+  // room for the skewed blocks between the two steps of fft_smem (R blocks of S + 1), and the stride is odd
+  // (2 x odd when only 8 vectors share a half-warp) so that a half-warp reading the same element of
+  // consecutive vectors hits distinct banks
+  static constexpr int vstride(int len, int nv, int r) {
+    const int v0 = len + len / 64, v = v0 > len + r ? v0 : len + r;
     return nv >= 16 ? (v % 2 == 1 ? v : v + 1) : (v % 16 == 2 ? v : v + ((18 - v % 16) % 16));
   }
-  static constexpr int VROW = vstride(LR, 128 / RR);
-  static constexpr int VCOL = vstride(H, 128 / RC);
+  static constexpr int VROW = vstride(LR, 128 / RR, RR);
+  static constexpr int VCOL = vstride(H, 128 / RC, RC);
   static constexpr int SMEM = (RB * VROW > CB * VCOL ? RB * VROW : CB * VCOL) * 8;
   static constexpr int ROW_ITEMS = H / RB;  // row-phase work items per field
   static constexpr int COL_ITEMS = LR / CB; // column-phase work items per field
@@ -54,17 +55,19 @@ WF_HD int padi(int i) { return i + (i >> 6); }
 // Forward DFT of length L = R*S of the padded vectors v_j = buf + j*V (j < NV), natural order in and out.
 // tw[j] = exp(-2 pi i j / L). INV: inverse via conjugation on the way in and out. 128 threads = NV * R.
 //   step A: for each n < S, the R-point DFT A[q] = sum_m x[n + S m] w_R^(q m), twiddled by W_L^(q n),
-//           stored at n + S q;
-//   step C: for each q < R, the S-point FFT of the contiguous block S q .. S q + S - 1; output k goes to
-//           q + R k (decimation in frequency: X[q + R k] = sum_n W_L^(q n) w_S^(n k) A_n[q]).
+//           stored at n + S q (block q);
+//   step C: for each q < R, the S-point FFT of block q; output k goes to q + R k (decimation in
+//           frequency: X[q + R k] = sum_n W_L^(q n) w_S^(n k) A_n[q]).
 // When NV * S < 128 (one or two warps would carry step A alone) the R-point DFTs are themselves split,
 // R = R1 R2 with m = m2 + R2 m1 and q = q1 + R1 q2:
 //   A1: for each (n, m2), B[q1] = sum_m1 x[n + S (m2 + R2 m1)] w_R1^(q1 m1), twiddled by w_R^(m2 q1),
 //       stored back at n + S (m2 + R2 q1);
 //   A2: for each (n, q1), A[q1 + R1 q2] = sum_m2 B'[m2][q1] w_R2^(q2 m2), twiddled by W_L^(q n) and
-//       stored at n + S q,
-// so every pass has NV S R2 or NV S R1 small DFTs spread over all 128 threads (A2 reads and writes
-// different positions, so each thread holds its inputs in registers across a CTA barrier).
+//       stored in block q,
+// so every pass has NV S R2 or NV S R1 small DFTs spread over all 128 threads, consecutive threads on
+// consecutive n (contiguous addresses). A2 holds its inputs in registers across a CTA barrier anyway, so
+// it writes the blocks skewed by one float2 each (block q at q (S + 1), not padded): the threads of a warp,
+// each reading its own block in step C, then hit distinct banks.
 template <int R>
 __host__ __device__ constexpr int fft_smem_r1() { return R > 16 ? 8 : R; }
 
@@ -72,9 +75,11 @@ template <int R, int NV, int V, bool INV, int S = 64>
 __device__ __forceinline__ void fft_smem(float2* buf, const float2* __restrict__ tw) {
   static_assert(NV * R == 128, "one sub-transform per thread in step C");
   constexpr int L = R * S;
+  constexpr bool SPLIT = !(NV * S >= 128 || R <= 16);
+  static_assert(!SPLIT || R * (S + 1) <= V, "room for the skewed blocks");
   const int tid = threadIdx.x;
-  if constexpr (NV * S >= 128 || R <= 16) {
-    // step A: R-point DFT across the S strided subsequences, twiddled by W_L^(q n)
+  if constexpr (!SPLIT) {
+    // step A: R-point DFT across the S strided subsequences, twiddled by W_L^(q n), in place
     for (int task = tid; task < NV * S; task += 128) {
       const int j = task / S, n = task % S;
       float2* v = buf + j * V;
@@ -93,7 +98,7 @@ __device__ __forceinline__ void fft_smem(float2* buf, const float2* __restrict__
     static_assert(R1 * R2 == R && (NV * S * R2) % 128 == 0 && (NV * S * R1) % 128 == 0, "split step A");
     // A1: R1-point DFTs over m1, twiddle w_R^(m2 q1) = W_L^((L/R) m2 q1), in place
     for (int task = tid; task < NV * S * R2; task += 128) {
-      const int j = task / (S * R2), n = (task / R2) % S, m2 = task % R2;
+      const int n = task % S, m2 = (task / S) % R2, j = task / (S * R2);
       float2* v = buf + j * V;
       float2 a[R1];
 #pragma unroll
@@ -107,39 +112,39 @@ __device__ __forceinline__ void fft_smem(float2* buf, const float2* __restrict__
         v[padi(n + S * (m2 + R2 * q1))] = q1 == 0 ? a[0] : cmul(a[q1], __ldg(tw + (L / R) * m2 * q1));
     }
     __syncthreads();
-    // A2: R2-point DFTs over m2, twiddle W_L^(q n), q = q1 + R1 q2, to n + S q
+    // A2: R2-point DFTs over m2, twiddle W_L^(q n), q = q1 + R1 q2, to block q
     constexpr int T2 = NV * S * R1 / 128;  // tasks per thread
     float2 b[T2][R2];
 #pragma unroll
     for (int t = 0; t < T2; ++t) {
       const int task = tid + 128 * t;
-      const int j = task / (S * R1), n = (task / R1) % S, q1 = task % R1;
+      const int n = task % S, q1 = (task / S) % R1, j = task / (S * R1);
       const float2* v = buf + j * V;
 #pragma unroll
       for (int m2 = 0; m2 < R2; ++m2) b[t][m2] = v[padi(n + S * (m2 + R2 * q1))];
+      fft<R2, false>(b[t]);
     }
     __syncthreads();
 #pragma unroll
     for (int t = 0; t < T2; ++t) {
       const int task = tid + 128 * t;
-      const int j = task / (S * R1), n = (task / R1) % S, q1 = task % R1;
+      const int n = task % S, q1 = (task / S) % R1, j = task / (S * R1);
       float2* v = buf + j * V;
-      fft<R2, false>(b[t]);
 #pragma unroll
       for (int q2 = 0; q2 < R2; ++q2) {
         const int q = q1 + R1 * q2;
-        v[padi(n + S * q)] = q == 0 ? b[t][q2] : cmul(b[t][q2], __ldg(tw + q * n));
+        v[q * (S + 1) + n] = q == 0 ? b[t][q2] : cmul(b[t][q2], __ldg(tw + q * n));
       }
     }
   }
   __syncthreads();
-  // step C: S-point FFT of each twiddled subsequence q; output k goes to position q + R k
+  // step C: S-point FFT of each twiddled subsequence q (block q); output k goes to position q + R k
   // (consecutive threads take consecutive vectors)
   const int j = tid % NV, q = tid / NV;
   float2* v = buf + j * V;
   float2 u[S];
 #pragma unroll
-  for (int n = 0; n < S; ++n) u[n] = v[padi(S * q + n)];
+  for (int n = 0; n < S; ++n) u[n] = SPLIT ? v[q * (S + 1) + n] : v[padi(S * q + n)];
   __syncthreads();
   fft<S, false>(u);
 #pragma unroll
