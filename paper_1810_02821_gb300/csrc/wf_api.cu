@@ -117,9 +117,21 @@ __global__ void k_prep(const float* __restrict__ d, const float* __restrict__ Nd
 // CTA are contiguous and its row threads read consecutive addresses.
 __host__ __device__ inline int table_row(int y, int H, int perm) { return perm ? (y % perm) * (H / perm) + y / perm : y; }
 
+// Position of half-spectrum entry j = ky (W/2 + 1) + kx in a mode table: natural (cm = 0), or the column slot
+// order of the cluster kernels with cm rows per CTA (kx < W/2 at ky W/2 + t, t = (kx mod cm) R + kx / cm,
+// R = (W/2) / cm, the slot holding kx; kx = W/2 at H W/2 + ky), so that a column unit's threads read
+// consecutive addresses.
+__host__ __device__ inline int mode_pos(int j, int H, int W, int cm) {
+  if (!cm) return j;
+  const int L = W / 2, ky = j / (L + 1), kx = j % (L + 1);
+  return kx < L ? ky * L + (kx % cm) * (L / cm) + kx / cm : H * L + ky;
+}
+
+// pks (optional): P in the same order as the mode table (the cluster solve reads it there)
 __global__ void k_tables(const float* __restrict__ d, const float* __restrict__ Ndiag, const uint8_t* __restrict__ mask,
                          const float* __restrict__ Pk, int H, int W, const wf::Scalars* __restrict__ sc,
-                         float2* __restrict__ aq, float2* __restrict__ dn, float2* __restrict__ fg, int perm = 0) {
+                         float2* __restrict__ aq, float2* __restrict__ dn, float2* __restrict__ fg, int perm = 0,
+                         int cm = 0, float* __restrict__ pks = nullptr) {
   if (sc->status != 0) return;
   const double tau = sc->tau;
   const int n = H * W, nm = H * (W / 2 + 1);
@@ -131,9 +143,10 @@ __global__ void k_tables(const float* __restrict__ d, const float* __restrict__ 
       wf::table_pixel(d[i], Ndiag[i], mask[i] == 0, tau, &a2, &d2);
       if (aq) aq[x * H + ty] = a2;
       if (dn) dn[x * H + ty] = d2;
-    } else if (fg) {
-      const int j = i - n;
-      fg[j] = wf::table_mode(Pk[j], tau, inv_n);
+    } else {
+      const int j = i - n, q = mode_pos(j, H, W, cm);
+      if (fg) fg[q] = wf::table_mode(Pk[j], tau, inv_n);
+      if (pks) pks[q] = Pk[j];
     }
   }
 }
@@ -540,8 +553,9 @@ wf_status solve_cluster(const float* d, const float* Ndiag, const uint8_t* mask,
                         wf::LaunchTimer* timer) {
   const size_t n = size_t(H) * W, nz = size_t(H) * (W / 2);
   Carve cv;
+  const size_t nm = size_t(H) * (W / 2 + 1);
   const size_t o_sc = cv.take<wf::Scalars>(1), o_res = cv.take<wf::BatchResult>(1), o_f = cv.take<wf::GBField>(1),
-               o_dn = cv.take<float2>(n), o_prev = cv.take<float2>(nz);
+               o_dn = cv.take<float2>(n), o_prev = cv.take<float2>(nz), o_pk = cv.take<float>(nm);
   Scratch scr;
   scr.st = st;
   WF_CUDA(cudaMallocAsync(&scr.base, cv.off, st));
@@ -550,12 +564,14 @@ wf_status solve_cluster(const float* d, const float* Ndiag, const uint8_t* mask,
   auto* res = reinterpret_cast<wf::BatchResult*>(b + o_res);
   k_prep<<<1, 1024, 0, st>>>(d, Ndiag, mask, Pk, H, W, o.tau, o.eta, sc);
   WF_CUDA(cudaGetLastError());
-  k_tables<<<int((n + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc, nullptr,
-                                                 reinterpret_cast<float2*>(b + o_dn), nullptr, H / cluster_rows_of(H, 0));
+  const int rows = cluster_rows_of(H, 0);
+  k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc, nullptr,
+                                                      reinterpret_cast<float2*>(b + o_dn), nullptr, H / rows, rows,
+                                                      reinterpret_cast<float*>(b + o_pk));
   WF_CUDA(cudaGetLastError());
   wf::GBField fd{};
   fd.dn = reinterpret_cast<const float2*>(b + o_dn);
-  fd.Pk = Pk;
+  fd.Pk = reinterpret_cast<const float*>(b + o_pk);  // slot order of the cluster kernels
   fd.prev = reinterpret_cast<float2*>(b + o_prev);
   fd.out_wf = out_s;
   fd.item = 0;
@@ -808,7 +824,8 @@ wf_status wf_sample_ex(const float* d, const float* Ndiag, const uint8_t* mask, 
   k_prep<<<1, 1024, 0, st>>>(d, Ndiag, mask, Pk, H, W, o.tau, 0.5, sc);
   WF_CUDA(cudaGetLastError());
   k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc, aq, nullptr, fg,
-                                                       cluster ? H / cluster_rows_of(H, 0) : 0);
+                                                       cluster ? H / cluster_rows_of(H, 0) : 0,
+                                                       cluster ? cluster_rows_of(H, 0) : 0);
   WF_CUDA(cudaGetLastError());
   wf::SampleArgs a{};
   a.aq = aq; a.fg = fg; a.sc = sc; a.init_s = o.init_s;
@@ -1240,7 +1257,7 @@ struct GBChunk {
   std::vector<int> items;  // batch item indices
   size_t o_fields = 0, o_idx = 0, o_sc = 0, o_state = 0, o_acc = 0, o_bn = 0, o_active = 0, o_bar = 0, o_tr = 0,
          o_tc = 0, o_tw = 0, o_data = 0, per_field = 0;
-  size_t f_aq = 0, f_dn = 0, f_fg = 0, f_z = 0, f_prev = 0;
+  size_t f_aq = 0, f_dn = 0, f_fg = 0, f_z = 0, f_prev = 0, f_pk = 0;
 };
 
 void layout_chunk(GBChunk& c, Carve& cv) {
@@ -1262,6 +1279,7 @@ void layout_chunk(GBChunk& c, Carve& cv) {
   c.f_dn = f.take<float2>(n);
   c.f_fg = f.take<float2>(nm);
   if (!c.cluster) c.f_z = f.take<float2>(nz);
+  if (c.cluster) c.f_pk = f.take<float>(nm);  // P in the clusters' slot order
   c.f_prev = f.take<float2>(nz);
   c.per_field = f.off;
   c.o_data = cv.take<char>(c.per_field * size_t(F));
@@ -1277,7 +1295,7 @@ std::vector<wf::GBField> chunk_fields(const GBChunk& c, const std::vector<wf::Ba
     g.aq = reinterpret_cast<const float2*>(base + c.f_aq);
     g.dn = reinterpret_cast<const float2*>(base + c.f_dn);
     g.fg = reinterpret_cast<const float2*>(base + c.f_fg);
-    g.Pk = it.Pk;
+    g.Pk = c.cluster ? reinterpret_cast<const float*>(base + c.f_pk) : it.Pk;
     g.Z = c.cluster ? nullptr : reinterpret_cast<float2*>(base + c.f_z);
     g.prev = reinterpret_cast<float2*>(base + c.f_prev);
     g.out_wf = it.out_wf;
@@ -1348,9 +1366,11 @@ __global__ void k_prep_fields(const wf::BatchItem* __restrict__ items, const int
 }
 
 // per-field tables (as k_tables), grid-stride over fields x (n + nm)
+// cm > 0 (cluster chunks, cm rows per CTA): the mode table in the clusters' slot order, and a copy of P in
+// that order at the field's Pk (chunk scratch)
 __global__ void k_tables_fields(const wf::BatchItem* __restrict__ items, const int* __restrict__ idx,
                                 const wf::GBField* __restrict__ fields, const wf::Scalars* __restrict__ sc, int F,
-                                int H, int perm) {
+                                int H, int perm, int cm = 0) {
   const long long n = (long long)H * H, nm = (long long)H * (H / 2 + 1), per = n + nm;
   const double inv_n = 1.0 / double(n);
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < per * F;
@@ -1368,8 +1388,9 @@ __global__ void k_tables_fields(const wf::BatchItem* __restrict__ items, const i
       const_cast<float2*>(fd.aq)[x * H + ty] = a2;
       const_cast<float2*>(fd.dn)[x * H + ty] = d2;
     } else {
-      const long long j = i - n;
-      const_cast<float2*>(fd.fg)[j] = wf::table_mode(it.Pk[j], s.tau, inv_n);
+      const int j = int(i - n), q = mode_pos(j, H, H, cm);
+      const_cast<float2*>(fd.fg)[q] = wf::table_mode(it.Pk[j], s.tau, inv_n);
+      if (cm) const_cast<float*>(fd.Pk)[q] = it.Pk[j];
     }
   }
 }
@@ -1503,7 +1524,7 @@ wf_status run_chunk(const GBChunk& c, const wf::BatchItem* d_items, wf::BatchRes
   WF_CUDA(cudaGetLastError());
   const long long tab = (long long)F * (size_t(H) * H + size_t(H) * (H / 2 + 1));
   k_tables_fields<<<int((tab + 255) / 256 < 4096 ? (tab + 255) / 256 : 4096), 256, 0, st>>>(
-      d_items, idx, fields, sc, F, H, c.cluster ? H / c.rows : 0);
+      d_items, idx, fields, sc, F, H, c.cluster ? H / c.rows : 0, c.cluster ? c.rows : 0);
   WF_CUDA(cudaGetLastError());
   if (c.cluster) {
     wf::CBArgs cb{};

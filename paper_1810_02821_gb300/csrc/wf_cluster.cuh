@@ -56,6 +56,21 @@ struct CGeo {
   static_assert(ROWS_BYTES % 8 == 0, "FP64 sums after the rows stay 8-byte aligned");
 };
 
+// Mode tables of the cluster kernels (the s-draw coefficients fg and the spectrum P) are stored in the
+// column slot order of the packed half spectrum, so that the threads of a column unit (consecutive slots
+// t) read consecutive addresses: entry (ky, kx) with kx < W/2 at ky L + t, t = (kx mod M) R + kx / M (the
+// slot holding kx), and the Nyquist column kx = W/2 (packed with kx = 0 in slot 0) at H L + ky.
+template <int N, int MR>
+__host__ __device__ inline int cslot_of(int kx) {
+  using G = CGeo<N, MR>;
+  return (kx % G::M) * G::R + kx / G::M;
+}
+template <int N, int MR>
+__host__ __device__ inline int ctab_index(int ky, int kx) {
+  using G = CGeo<N, MR>;
+  return kx < G::W / 2 ? ky * G::L + cslot_of<N, MR>(kx) : G::H * G::L + ky;
+}
+
 // ---------------------------------------------------------------------------------------------
 // row passes (R threads per row, h = the thread's index within its row)
 // ---------------------------------------------------------------------------------------------
@@ -236,26 +251,26 @@ __device__ __forceinline__ void ccol_inv(float2* rows, int t, int b, const float
 }
 
 // One mode pair (ky1, ky2 = N - ky1, or N/2 when ky1 = 0) of packed column slot t (kx = K) with the
-// s-draw s_hat = f t_hat + g zeta, table fg[ky*WH + kx] = (f / n, g / sqrt(2 n)). Interior columns: Philox
+// s-draw s_hat = f t_hat + g zeta, table fg = (f / n, g / sqrt(2 n)) in slot order (ctab_index). Interior columns: Philox
 // stream 1 group K*H/2 + ky1, variates 0, 1 for ky1 and 2, 3 for ky2. Packed edge column (K = 0: kx = 0 as
 // A and kx = W/2 as B in Y = A + i B): group ky1 draws (ky1, 0) from variates 0, 1 and (ky1, W/2) from
 // 2, 3, the conjugates filling ky2; group 0 holds the four real modes (0,0), (H/2,0), (0,W/2), (H/2,W/2).
 template <int N, int MR>
-__device__ __forceinline__ void cdraw_pair(float2& y1, float2& y2, int K, int ky1, int ky2,
+__device__ __forceinline__ void cdraw_pair(float2& y1, float2& y2, int K, int t, int ky1, int ky2,
                                            const float2* __restrict__ fg, uint32_t step, uint32_t chain,
                                            uint32_t k0, uint32_t k1) {
   using G = CGeo<N, MR>;
   float z[4];
   normals4(uint32_t(K * (G::H / 2) + ky1), step, chain, 1u, k0, k1, z);
   if (K != 0) {
-    const float2 m1 = WF_LDG(fg + ky1 * G::WH + K), m2 = WF_LDG(fg + ky2 * G::WH + K);
+    const float2 m1 = WF_LDG(fg + ky1 * G::L + t), m2 = WF_LDG(fg + ky2 * G::L + t);
     y1 = make_float2(fmaf(m1.x, y1.x, m1.y * z[0]), fmaf(m1.x, y1.y, m1.y * z[1]));
     y2 = make_float2(fmaf(m2.x, y2.x, m2.y * z[2]), fmaf(m2.x, y2.y, m2.y * z[3]));
     return;
   }
-  const float2 a1 = WF_LDG(fg + ky1 * G::WH), b1 = WF_LDG(fg + ky1 * G::WH + G::W / 2);
+  const float2 a1 = WF_LDG(fg + ky1 * G::L), b1 = WF_LDG(fg + G::H * G::L + ky1);
   if (ky1 == 0) {
-    const float2 a2 = WF_LDG(fg + ky2 * G::WH), b2 = WF_LDG(fg + ky2 * G::WH + G::W / 2);
+    const float2 a2 = WF_LDG(fg + ky2 * G::L), b2 = WF_LDG(fg + G::H * G::L + ky2);
     constexpr float R2 = 1.41421356237309505f;
     y1 = make_float2(fmaf(a1.x, y1.x, R2 * a1.y * z[0]), fmaf(b1.x, y1.y, R2 * b1.y * z[2]));
     y2 = make_float2(fmaf(a2.x, y2.x, R2 * a2.y * z[1]), fmaf(b2.x, y2.y, R2 * b2.y * z[3]));
@@ -273,7 +288,7 @@ __device__ __forceinline__ void cdraw_pair(float2& y1, float2& y2, int K, int ky
 // Cross-cluster radix-P stage. Work unit (slot t, k' = u with its mirror v = M - u; u = 0 is paired with
 // u = M/2, the two half-size units): gathers Y_j[u] (and Y_j[v]) from every CTA j, forms the column spectrum
 // t_hat[u + M m], hands every mode pair (ky1 < N/2, ky2 = N - ky1, or N/2 when ky1 = 0) of column K to
-// fn(K, y1, y2, ky1, ky2), and with WRITE scatters the inverse stage back. g = the thread's index in the
+// fn(K, t, y1, y2, ky1, ky2), and with WRITE scatters the inverse stage back. g = the thread's index in the
 // cluster. Every mode of the half spectrum is in exactly one pair of one unit, and there are L M / 2 units
 // of equal size, a whole number per thread of the cluster (one each at 512^2, eight at 256^2).
 template <int N, int MR, bool WRITE, class F>
@@ -293,16 +308,16 @@ __device__ __forceinline__ void ccol_units(cooperative_groups::cluster_group& cl
     fft<P, false>(p);  // p[m] = t_hat[u + M m]
     fft<P, false>(q);  // q[m] = t_hat[v + M m]
     if (u == 0) {
-      fn(K, p[0], p[P / 2], 0, N / 2);
+      fn(K, t, p[0], p[P / 2], 0, N / 2);
 #pragma unroll
-      for (int m = 1; m < P / 2; ++m) fn(K, p[m], p[P - m], M * m, N - M * m);
+      for (int m = 1; m < P / 2; ++m) fn(K, t, p[m], p[P - m], M * m, N - M * m);
 #pragma unroll
-      for (int m = 0; m < P / 2; ++m) fn(K, q[m], q[P - 1 - m], M / 2 + M * m, N - M / 2 - M * m);
+      for (int m = 0; m < P / 2; ++m) fn(K, t, q[m], q[P - 1 - m], M / 2 + M * m, N - M / 2 - M * m);
     } else {
 #pragma unroll
       for (int m = 0; m < P / 2; ++m) {
-        fn(K, p[m], q[P - 1 - m], u + M * m, N - u - M * m);
-        fn(K, q[m], p[P - 1 - m], v + M * m, N - v - M * m);
+        fn(K, t, p[m], q[P - 1 - m], u + M * m, N - u - M * m);
+        fn(K, t, q[m], p[P - 1 - m], v + M * m, N - v - M * m);
       }
     }
     if (WRITE) {
@@ -321,8 +336,8 @@ template <int N, int MR>
 __device__ __forceinline__ void ccol_draw(cooperative_groups::cluster_group& cl, float2* rows, int g,
                                           const float2* __restrict__ fg, uint32_t step, uint32_t chain,
                                           uint32_t k0, uint32_t k1) {
-  ccol_units<N, MR, true>(cl, rows, g, [&](int K, float2& y1, float2& y2, int ky1, int ky2) {
-    cdraw_pair<N, MR>(y1, y2, K, ky1, ky2, fg, step, chain, k0, k1);
+  ccol_units<N, MR, true>(cl, rows, g, [&](int K, int t, float2& y1, float2& y2, int ky1, int ky2) {
+    cdraw_pair<N, MR>(y1, y2, K, t, ky1, ky2, fg, step, chain, k0, k1);
   });
 }
 
@@ -330,13 +345,14 @@ __device__ __forceinline__ void ccol_draw(cooperative_groups::cluster_group& cl,
 // 1/n). With CMP the residual of the previous iterate, |s_hat_new - s_hat_old|^2 (1 + P / (lambda tau))^2,
 // is summed over the full spectrum (the mirror modes counted; returned as this thread's share, summed in
 // FP32 over its units); with STORE
-// the new modes go to prev[ky * W/2 + K] (packed edge column as stored).
+// the new modes go to prev[ky * W/2 + t] (slot order; packed edge column as stored). Pk in slot order
+// (ctab_index).
 template <int N, int MR>
 __device__ __forceinline__ double ccol_wf(cooperative_groups::cluster_group& cl, float2* rows, int g,
                                           const float* __restrict__ Pk, float lt_, float2* __restrict__ prev,
                                           bool cmp, bool store) {
   using G = CGeo<N, MR>;
-  constexpr int WH = G::WH, LR = G::L;
+  constexpr int LR = G::L;
   constexpr float INV_N = 1.0f / float(G::H * G::W);
   const float inv_lt = 1.0f / lt_;
   auto wres = [&](float P, float dre, float dim) -> float {
@@ -345,21 +361,21 @@ __device__ __forceinline__ double ccol_wf(cooperative_groups::cluster_group& cl,
   };
   auto fcoef = [&](float P) { return wf_fdiv(P, P + lt_) * INV_N; };
   float acc = 0.0f;  // this thread's units in FP32; the cluster sum is FP64
-  ccol_units<N, MR, true>(cl, rows, g, [&](int K, float2& y1, float2& y2, int ky1, int ky2) {
+  ccol_units<N, MR, true>(cl, rows, g, [&](int K, int t, float2& y1, float2& y2, int ky1, int ky2) {
     if (K != 0) {
-      const float P1 = WF_LDG(Pk + ky1 * WH + K), P2 = WF_LDG(Pk + ky2 * WH + K);
+      const float P1 = WF_LDG(Pk + ky1 * LR + t), P2 = WF_LDG(Pk + ky2 * LR + t);
       const float2 n1 = cscale(y1, fcoef(P1)), n2 = cscale(y2, fcoef(P2));
       if (cmp) {
-        const float2 o1 = prev[ky1 * LR + K], o2 = prev[ky2 * LR + K];
+        const float2 o1 = prev[ky1 * LR + t], o2 = prev[ky2 * LR + t];
         acc += 2.0f * (wres(P1, n1.x - o1.x, n1.y - o1.y) + wres(P2, n2.x - o2.x, n2.y - o2.y));
       }
       y1 = n1;
       y2 = n2;
     } else {
-      const float Pa1 = WF_LDG(Pk + ky1 * WH), Pb1 = WF_LDG(Pk + ky1 * WH + G::W / 2);
+      const float Pa1 = WF_LDG(Pk + ky1 * LR), Pb1 = WF_LDG(Pk + G::H * LR + ky1);
       const float fa1 = fcoef(Pa1), fb1 = fcoef(Pb1);
       if (ky1 == 0) {
-        const float Pa2 = WF_LDG(Pk + ky2 * WH), Pb2 = WF_LDG(Pk + ky2 * WH + G::W / 2);
+        const float Pa2 = WF_LDG(Pk + ky2 * LR), Pb2 = WF_LDG(Pk + G::H * LR + ky2);
         const float2 n1 = make_float2(fa1 * y1.x, fb1 * y1.y);
         const float2 n2 = make_float2(fcoef(Pa2) * y2.x, fcoef(Pb2) * y2.y);
         if (cmp) {
@@ -384,8 +400,8 @@ __device__ __forceinline__ double ccol_wf(cooperative_groups::cluster_group& cl,
       }
     }
     if (store) {
-      prev[ky1 * LR + K] = y1;
-      prev[ky2 * LR + K] = y2;
+      prev[ky1 * LR + t] = y1;
+      prev[ky2 * LR + t] = y2;
     }
   });
   return double(acc);
@@ -399,17 +415,17 @@ __device__ __forceinline__ double ccol_p2(cooperative_groups::cluster_group& cl,
   constexpr int WH = G::WH;
   auto p2 = [](float P, float re, float im) -> float { return P * P * fmaf(re, re, im * im); };
   float acc = 0.0f;
-  ccol_units<N, MR, false>(cl, rows, g, [&](int K, float2& y1, float2& y2, int ky1, int ky2) {
+  ccol_units<N, MR, false>(cl, rows, g, [&](int K, int t, float2& y1, float2& y2, int ky1, int ky2) {
     if (K != 0) {
-      acc += 2.0f * (p2(WF_LDG(Pk + ky1 * WH + K), y1.x, y1.y) + p2(WF_LDG(Pk + ky2 * WH + K), y2.x, y2.y));
+      acc += 2.0f * (p2(WF_LDG(Pk + ky1 * G::L + t), y1.x, y1.y) + p2(WF_LDG(Pk + ky2 * G::L + t), y2.x, y2.y));
     } else if (ky1 == 0) {
-      acc += p2(WF_LDG(Pk + ky1 * WH), y1.x, 0.f) + p2(WF_LDG(Pk + ky1 * WH + G::W / 2), y1.y, 0.f) +
-             p2(WF_LDG(Pk + ky2 * WH), y2.x, 0.f) + p2(WF_LDG(Pk + ky2 * WH + G::W / 2), y2.y, 0.f);
+      acc += p2(WF_LDG(Pk + ky1 * G::L), y1.x, 0.f) + p2(WF_LDG(Pk + G::H * G::L + ky1), y1.y, 0.f) +
+             p2(WF_LDG(Pk + ky2 * G::L), y2.x, 0.f) + p2(WF_LDG(Pk + G::H * G::L + ky2), y2.y, 0.f);
     } else {
       const float2 y2c = cconj(y2);
       const float2 A = cscale(cadd(y1, y2c), 0.5f);
       const float2 B = cmul_mi(cscale(csub(y1, y2c), 0.5f));
-      acc += 2.0f * (p2(WF_LDG(Pk + ky1 * WH), A.x, A.y) + p2(WF_LDG(Pk + ky1 * WH + G::W / 2), B.x, B.y));
+      acc += 2.0f * (p2(WF_LDG(Pk + ky1 * G::L), A.x, A.y) + p2(WF_LDG(Pk + G::H * G::L + ky1), B.x, B.y));
     }
   });
   return double(acc);

@@ -176,3 +176,23 @@ def test_global_memory_transform_split_step_a(L, S):
     for q in range(R):                       # step C
         out[q + R * np.arange(S)] = np.fft.fft(w2[S * q + np.arange(S)])
     assert np.max(np.abs(out - np.fft.fft(v))) < 1e-9 * L
+
+
+@pytest.mark.parametrize("N,M", GEOMETRIES)
+def test_mode_tables_in_slot_order(N, M):
+    """The cluster kernels' mode tables (s-draw coefficients, P): half-spectrum entry (ky, kx) at
+    ky L + t with t = (kx mod M) R + kx / M, the slot whose digit-reversed index K(t) = (t mod R) M + t / R
+    is kx, and the Nyquist column kx = W/2 at H L + ky; a bijection onto [0, H (W/2 + 1))."""
+    H = W = N
+    L = W // 2
+    R = L // M
+    pos = []
+    for ky in range(H):
+        for kx in range(L + 1):
+            if kx < L:
+                t = (kx % M) * R + kx // M
+                assert (t % R) * M + t // R == kx
+                pos.append(ky * L + t)
+            else:
+                pos.append(H * L + ky)
+    assert sorted(pos) == list(range(H * (L + 1)))
