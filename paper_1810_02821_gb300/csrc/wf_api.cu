@@ -869,6 +869,16 @@ __global__ void k_check_band(const int32_t* __restrict__ bins, int nm, int n_bin
   }
   if (bad && sc->status == 0) sc->status = WF_ERR_ARG;
 }
+
+// the bin map [H][W/2+1] in the column slot order of the cluster kernels with cm rows per CTA (mode_pos)
+__global__ void k_bins_slots(const int32_t* __restrict__ bins, int H, int W, int cm, int32_t* __restrict__ out) {
+  const int nm = H * (W / 2 + 1);
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nm; j += gridDim.x * blockDim.x)
+    out[mode_pos(j, H, W, cm)] = bins[j];
+}
+
+// largest number of bins of the hierarchical sampler at size H
+int band_max_bins(int H) { return H <= 256 ? 256 : 512; }
 }  // namespace
 
 extern "C" {
@@ -879,9 +889,8 @@ wf_status wf_sample_band(const float* d, const float* Ndiag, const uint8_t* mask
   if (!opts) return WF_ERR_ARG;
   const wf_sample_opts o = *opts;
   if (!d || !Ndiag || !mask || !Pk || !bins || (n_bins > 0 && !P0)) return WF_ERR_ARG;
-  if (!size_ok(H, W)) return WF_ERR_SHAPE;
-  if (!size_on_chip(H)) return WF_ERR_SHAPE;
-  if (n_bins < 0 || n_bins > 256 || o.A) return WF_ERR_ARG;
+  if (!size_ok(H, W) || H > 512) return WF_ERR_SHAPE;
+  if (n_bins < 0 || n_bins > band_max_bins(H) || o.A) return WF_ERR_ARG;
   if (o.n_samples < 0 || o.n_chains < 1 || o.burn_in < 0 || o.thin < 1) return WF_ERR_ARG;
   if (o.out_dtype < WF_OUT_F32 || o.out_dtype > WF_OUT_F16) return WF_ERR_ARG;
   if (o.n_samples == 0) return WF_OK;
@@ -890,8 +899,12 @@ wf_status wf_sample_band(const float* d, const float* Ndiag, const uint8_t* mask
   if (sweeps > 0x7fffffffLL || o.n_samples > 0x7fffffffLL) return WF_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const size_t n = size_t(H) * W, nm = size_t(H) * (W / 2 + 1);
+  // 256 and 512: one thread-block cluster per chain, tables in the cluster kernels' orders
+  const bool cluster = !size_on_chip(H);
+  const int cm = cluster ? wf::cluster_rows(H) : 0, perm = cluster ? H / cm : 0;
   Carve cv;
-  const size_t off_sc = cv.take<wf::Scalars>(1), off_aq = cv.take<float2>(n), off_fg = cv.take<float2>(nm);
+  const size_t off_sc = cv.take<wf::Scalars>(1), off_aq = cv.take<float2>(n), off_fg = cv.take<float2>(nm),
+               off_bins = cv.take<int32_t>(cluster ? nm : 0);
   Scratch scr;
   scr.st = st;
   WF_CUDA(cudaMallocAsync(&scr.base, cv.off, st));
@@ -903,8 +916,14 @@ wf_status wf_sample_band(const float* d, const float* Ndiag, const uint8_t* mask
   WF_CUDA(cudaGetLastError());
   k_check_band<<<int((nm + n_bins + 255) / 256), 256, 0, st>>>(bins, int(nm), n_bins, P0, sc);
   WF_CUDA(cudaGetLastError());
-  k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc, aq, nullptr, fg);
+  k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc, aq, nullptr, fg, perm, cm);
   WF_CUDA(cudaGetLastError());
+  if (cluster) {
+    auto* bs = reinterpret_cast<int32_t*>(b + off_bins);
+    k_bins_slots<<<int((nm + 255) / 256), 256, 0, st>>>(bins, H, W, cm, bs);
+    WF_CUDA(cudaGetLastError());
+    bins = bs;
+  }
   wf::SampleArgs a{};
   a.aq = aq; a.fg = fg; a.sc = sc; a.init_s = o.init_s;
   a.init_stride = (o.init_s && o.init_per_chain) ? (long long)n : 0;
@@ -920,6 +939,8 @@ wf_status wf_sample_band(const float* d, const float* Ndiag, const uint8_t* mask
     case 32: e = wf::launch_sample_band<32>(a, st, &timer); break;
     case 64: e = wf::launch_sample_band<64>(a, st, &timer); break;
     case 128: e = wf::launch_sample_band<128>(a, st, &timer); break;
+    case 256: e = wf::launch_csample_band<256, 64>(a, st, &timer); break;
+    case 512: e = wf::launch_csample_band<512, 32>(a, st, &timer); break;
   }
   if (e != cudaSuccess) return cuda_fail(e);
   wf::Scalars hsc;
@@ -951,8 +972,7 @@ wf_status wf_sample_spin2(const float* d1, const float* d2, const float* N1, con
   if (!opts) return WF_ERR_ARG;
   const wf_sample_opts o = *opts;
   if (!d1 || !d2 || !N1 || !N2 || !mask || !PE || !PB) return WF_ERR_ARG;
-  if (!size_ok(H, W)) return WF_ERR_SHAPE;
-  if (!size_on_chip(H)) return WF_ERR_SHAPE;
+  if (!size_ok(H, W) || H > 512) return WF_ERR_SHAPE;
   if (o.A || o.n_samples < 0 || o.n_chains < 1 || o.burn_in < 0 || o.thin < 1) return WF_ERR_ARG;
   if (o.out_dtype < WF_OUT_F32 || o.out_dtype > WF_OUT_F16) return WF_ERR_ARG;
   if (o.n_samples == 0) return WF_OK;
@@ -978,8 +998,11 @@ wf_status wf_sample_spin2(const float* d1, const float* d2, const float* N1, con
   k_prep<<<1, 1024, 0, st>>>(d2, N2, mask, PB, H, W, o.tau, 0.5, sc + 1);
   k_min_tau<<<1, 32, 0, st>>>(sc, sc + 1, o.tau);
   WF_CUDA(cudaGetLastError());
-  k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d1, N1, mask, PE, H, W, sc, aq, nullptr, fgE);
-  k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d2, N2, mask, PB, H, W, sc, aq + n, nullptr, fgB);
+  // 256 and 512: both components of a chain in one thread-block cluster of 32-row CTAs, tables in the
+  // cluster kernels' orders
+  const int cm = size_on_chip(H) ? 0 : 32, perm = cm ? H / cm : 0;
+  k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d1, N1, mask, PE, H, W, sc, aq, nullptr, fgE, perm, cm);
+  k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d2, N2, mask, PB, H, W, sc, aq + n, nullptr, fgB, perm, cm);
   WF_CUDA(cudaGetLastError());
   wf::Spin2Args a{};
   a.aq2 = aq; a.fgE = fgE; a.fgB = fgB; a.sc = sc; a.init_s = o.init_s;
@@ -995,6 +1018,8 @@ wf_status wf_sample_spin2(const float* d1, const float* d2, const float* N1, con
     case 32: e = wf::launch_sample_spin2<32>(a, st, &timer); break;
     case 64: e = wf::launch_sample_spin2<64>(a, st, &timer); break;
     case 128: e = wf::launch_sample_spin2<128>(a, st, &timer); break;
+    case 256: e = wf::launch_csample_spin2<256, 32>(a, st, &timer); break;
+    case 512: e = wf::launch_csample_spin2<512, 32>(a, st, &timer); break;
   }
   if (e != cudaSuccess) return cuda_fail(e);
   wf::Scalars hsc;

@@ -199,16 +199,17 @@ __device__ __forceinline__ void crow_inv(float2* row, int h, const float2* tw) {
 }
 
 // t-draw of global row y on its staged row: t = a + q (q s + sqrt(tau) xi), table aq[x*H + ty] =
-// ((1 - w) d, sqrt(w)) with the CTA-contiguous row index ty = b*M + a; Philox stream 0, group y*W/4 + q
-// feeds pixels 4q .. 4q+3 (q = h, h + R, ...)
+// ((1 - w) d, sqrt(w)) with the CTA-contiguous row index ty = b*M + a; Philox stream ts (0; 8 for the
+// second shear component), group y*W/4 + q feeds pixels 4q .. 4q+3 (q = h, h + R, ...)
 template <int N, int MR>
 __device__ __forceinline__ void ct_draw(float2* row, int y, int ty, int h, const float2* __restrict__ aq,
-                                        float sqrt_tau, uint32_t step, uint32_t chain, uint32_t k0, uint32_t k1) {
+                                        float sqrt_tau, uint32_t step, uint32_t chain, uint32_t k0, uint32_t k1,
+                                        uint32_t ts = 0u) {
   using G = CGeo<N, MR>;
 #pragma unroll 2
   for (int q = h; q < G::W / 4; q += G::R) {
     float z[4];
-    normals4(uint32_t(y * (G::W / 4) + q), step, chain, 0u, k0, k1, z);
+    normals4(uint32_t(y * (G::W / 4) + q), step, chain, ts, k0, k1, z);
     float2 p0 = row[2 * q], p1 = row[2 * q + 1];
     const float2 c0 = WF_LDG(aq + (4 * q) * G::H + ty), c1 = WF_LDG(aq + (4 * q + 1) * G::H + ty);
     const float2 c2 = WF_LDG(aq + (4 * q + 2) * G::H + ty), c3 = WF_LDG(aq + (4 * q + 3) * G::H + ty);
@@ -250,30 +251,78 @@ __device__ __forceinline__ void ccol_inv(float2* rows, int t, int b, const float
   for (int a = 0; a < G::M; ++a) rows[a * G::SP + t] = x[a];
 }
 
+// Mode coefficients of the cluster s-draw, looked up by the slot-order index i = ctab_index(ky, kx).
+// CTabCoef reads the per-call table fg = (f / n, g / sqrt(2 n)). CBandCoef (the hierarchical sampler)
+// derives them from the band power P_b of the mode's bin (bins >= 0; -1: the table's coefficients) with
+// band_coef, and sums the band statistics of the new modes into this CTA's shared accumulators:
+// S_b += n |s_hat|^2 (unitary scale, the mirror modes counted) and X_b += the squares of the stream-6
+// normals, FP32 atomics (their order of addition varies, so band powers repeat to FP32 rounding).
+struct CTabCoef {
+  static constexpr bool kBand = false;
+  const float2* __restrict__ fg;
+  __device__ __forceinline__ float2 m(int i) const { return WF_LDG(fg + i); }
+  __device__ __forceinline__ void add(int, float, float) const {}
+};
+struct CBandCoef {
+  static constexpr bool kBand = true;
+  const float2* __restrict__ fg;
+  const int* __restrict__ bins;  // slot order, as fg
+  const float* Pb;               // shared [n_bins]
+  float* acc;                    // shared [2][n_bins] of the current sweep: S_b, then X_b
+  int n_bins;
+  float tau, inv_n, n;
+  __device__ __forceinline__ float2 m(int i) const {
+    const int b = WF_LDG(bins + i);
+    return b < 0 ? WF_LDG(fg + i) : band_coef(Pb[b], tau, inv_n);
+  }
+  __device__ __forceinline__ void add(int i, float s2, float x2) const {
+    const int b = WF_LDG(bins + i);
+    if (b < 0) return;
+    atomicAdd(acc + b, s2 * n);
+    atomicAdd(acc + n_bins + b, x2);
+  }
+};
+
 // One mode pair (ky1, ky2 = N - ky1, or N/2 when ky1 = 0) of packed column slot t (kx = K) with the
-// s-draw s_hat = f t_hat + g zeta, table fg = (f / n, g / sqrt(2 n)) in slot order (ctab_index). Interior columns: Philox
-// stream 1 group K*H/2 + ky1, variates 0, 1 for ky1 and 2, 3 for ky2. Packed edge column (K = 0: kx = 0 as
-// A and kx = W/2 as B in Y = A + i B): group ky1 draws (ky1, 0) from variates 0, 1 and (ky1, W/2) from
-// 2, 3, the conjugates filling ky2; group 0 holds the four real modes (0,0), (H/2,0), (0,W/2), (H/2,W/2).
-template <int N, int MR>
-__device__ __forceinline__ void cdraw_pair(float2& y1, float2& y2, int K, int t, int ky1, int ky2,
-                                           const float2* __restrict__ fg, uint32_t step, uint32_t chain,
-                                           uint32_t k0, uint32_t k1) {
+// s-draw s_hat = f t_hat + g zeta, coefficients from cf. Interior columns: Philox stream 1 group
+// K*H/2 + ky1, variates 0, 1 for ky1 and 2, 3 for ky2. Packed edge column (K = 0: kx = 0 as A and
+// kx = W/2 as B in Y = A + i B): group ky1 draws (ky1, 0) from variates 0, 1 and (ky1, W/2) from 2, 3,
+// the conjugates filling ky2; group 0 holds the four real modes (0,0), (H/2,0), (0,W/2), (H/2,W/2).
+// With band statistics the stream-6 normals of the same group enter X_b in the same pattern.
+template <int N, int MR, class C>
+__device__ __forceinline__ void cdraw_pair(float2& y1, float2& y2, int K, int t, int ky1, int ky2, const C& cf,
+                                           uint32_t step, uint32_t chain, uint32_t k0, uint32_t k1) {
   using G = CGeo<N, MR>;
-  float z[4];
-  normals4(uint32_t(K * (G::H / 2) + ky1), step, chain, 1u, k0, k1, z);
+  const uint32_t grp = uint32_t(K * (G::H / 2) + ky1);
+  float z[4], zb[4];
+  normals4(grp, step, chain, 1u, k0, k1, z);
+  if constexpr (C::kBand) normals4(grp, step, chain, 6u, k0, k1, zb);
+  auto sq = [](float2 v) { return fmaf(v.x, v.x, v.y * v.y); };
   if (K != 0) {
-    const float2 m1 = WF_LDG(fg + ky1 * G::L + t), m2 = WF_LDG(fg + ky2 * G::L + t);
+    const int i1 = ky1 * G::L + t, i2 = ky2 * G::L + t;
+    const float2 m1 = cf.m(i1), m2 = cf.m(i2);
     y1 = make_float2(fmaf(m1.x, y1.x, m1.y * z[0]), fmaf(m1.x, y1.y, m1.y * z[1]));
     y2 = make_float2(fmaf(m2.x, y2.x, m2.y * z[2]), fmaf(m2.x, y2.y, m2.y * z[3]));
+    if constexpr (C::kBand) {  // both modes have their mirror in the other half plane: weight 2
+      cf.add(i1, 2.0f * sq(y1), fmaf(zb[0], zb[0], zb[1] * zb[1]));
+      cf.add(i2, 2.0f * sq(y2), fmaf(zb[2], zb[2], zb[3] * zb[3]));
+    }
     return;
   }
-  const float2 a1 = WF_LDG(fg + ky1 * G::L), b1 = WF_LDG(fg + G::H * G::L + ky1);
+  const int ia1 = ky1 * G::L, ib1 = G::H * G::L + ky1;
+  const float2 a1 = cf.m(ia1), b1 = cf.m(ib1);
   if (ky1 == 0) {
-    const float2 a2 = WF_LDG(fg + ky2 * G::L), b2 = WF_LDG(fg + G::H * G::L + ky2);
+    const int ia2 = ky2 * G::L, ib2 = G::H * G::L + ky2;
+    const float2 a2 = cf.m(ia2), b2 = cf.m(ib2);
     constexpr float R2 = 1.41421356237309505f;
     y1 = make_float2(fmaf(a1.x, y1.x, R2 * a1.y * z[0]), fmaf(b1.x, y1.y, R2 * b1.y * z[2]));
     y2 = make_float2(fmaf(a2.x, y2.x, R2 * a2.y * z[1]), fmaf(b2.x, y2.y, R2 * b2.y * z[3]));
+    if constexpr (C::kBand) {  // one real degree of freedom each
+      cf.add(ia1, y1.x * y1.x, zb[0] * zb[0]);
+      cf.add(ib1, y1.y * y1.y, zb[2] * zb[2]);
+      cf.add(ia2, y2.x * y2.x, zb[1] * zb[1]);
+      cf.add(ib2, y2.y * y2.y, zb[3] * zb[3]);
+    }
   } else {
     const float2 y2c = cconj(y2);
     const float2 Am = cscale(cadd(y1, y2c), 0.5f);
@@ -282,6 +331,10 @@ __device__ __forceinline__ void cdraw_pair(float2& y1, float2& y2, int K, int t,
     const float2 Bp = make_float2(fmaf(b1.x, Bm.x, b1.y * z[2]), fmaf(b1.x, Bm.y, b1.y * z[3]));
     y1 = cadd(Ap, cmul_i(Bp));
     y2 = cadd(cconj(Ap), cmul_i(cconj(Bp)));
+    if constexpr (C::kBand) {  // (ky1, 0) and (ky1, W/2) with their mirrors at H - ky1: weight 2
+      cf.add(ia1, 2.0f * sq(Ap), fmaf(zb[0], zb[0], zb[1] * zb[1]));
+      cf.add(ib1, 2.0f * sq(Bp), fmaf(zb[2], zb[2], zb[3] * zb[3]));
+    }
   }
 }
 
@@ -332,12 +385,11 @@ __device__ __forceinline__ void ccol_units(cooperative_groups::cluster_group& cl
 }
 
 // the s-draw of Alg. 1 on every mode
-template <int N, int MR>
-__device__ __forceinline__ void ccol_draw(cooperative_groups::cluster_group& cl, float2* rows, int g,
-                                          const float2* __restrict__ fg, uint32_t step, uint32_t chain,
-                                          uint32_t k0, uint32_t k1) {
+template <int N, int MR, class C>
+__device__ __forceinline__ void ccol_draw(cooperative_groups::cluster_group& cl, float2* rows, int g, const C& cf,
+                                          uint32_t step, uint32_t chain, uint32_t k0, uint32_t k1) {
   ccol_units<N, MR, true>(cl, rows, g, [&](int K, int t, float2& y1, float2& y2, int ky1, int ky2) {
-    cdraw_pair<N, MR>(y1, y2, K, t, ky1, ky2, fg, step, chain, k0, k1);
+    cdraw_pair<N, MR>(y1, y2, K, t, ky1, ky2, cf, step, chain, k0, k1);
   });
 }
 
@@ -513,44 +565,74 @@ __device__ __forceinline__ void crows_store(const float2* rows, int b, void* dst
   }
 }
 
-// Sampler sweeps (Alg. 1) of one chain by its cluster from the staged rows (the current s): sample m (the
-// state after sweep burn_in + (m + 1) thin) to out + m H W elements of type out_dtype
+// Sampler sweeps (Alg. 1) of one chain by its cluster from the staged rows (the current s) of NC fields
+// (NC = 2: the two shear components, field c's rows at rows + c A SP, its pixel table at aq + c H W, its
+// t-draw from Philox stream 8 c). Per sweep: t-draws and forward transforms, then col(step) between the
+// two cluster barriers (the column spectra complete: the s-draw), post(step) right after the second
+// (every CTA's column work done), the inverse transforms. Sample m (the state after sweep
+// burn_in + (m + 1) thin) goes to out + (m NC + c) H W elements of type out_dtype, then on_sample(m).
+template <int N, int MR, int NC, class Col, class Post, class OnSample>
+__device__ __forceinline__ void csweeps(cooperative_groups::cluster_group& cl, float2* rows, const float2* tw,
+                                        const float2* __restrict__ aq, float sqrt_tau, void* out_v, int out_dtype,
+                                        int n_sweeps, int burn_in, int thin, uint32_t step0, uint32_t chain,
+                                        uint32_t k0, uint32_t k1, Col&& col, Post&& post, OnSample&& on_sample) {
+  using G = CGeo<N, MR>;
+  constexpr int CS = G::A * G::SP;
+  constexpr long long NPIX = (long long)G::H * G::W;
+  const int tid = threadIdx.x, b = int(cl.block_rank());
+  int ar, h;
+  crow_of<N, MR>(tid, ar, h);
+  const int y = G::P * ar + b;
+  const int eb = out_elem_bytes(out_dtype);
+  char* out = reinterpret_cast<char*>(out_v);
+  for (int done = 0;;) {
+    const uint32_t step = step0 + uint32_t(done);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      float2* row = rows + c * CS + ar * G::SP;
+      ct_draw<N, MR>(row, y, b * G::M + ar, h, aq + c * NPIX, sqrt_tau, step, chain, k0, k1, 8u * uint32_t(c));
+      __syncwarp();
+      crow_fwd<N, MR>(row, h, tw);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < NC; ++c) ccol_fwd<N, MR>(rows + c * CS, tid, b, tw);
+    cl.sync();  // every CTA's partial column transforms are in place
+    col(step);
+    cl.sync();  // every unit's inverse stage has landed
+    post(step);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) ccol_inv<N, MR>(rows + c * CS, tid, b, tw);
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < NC; ++c) crow_inv<N, MR>(rows + c * CS + ar * G::SP, h, tw);
+    ++done;
+    if (done > burn_in && (done - burn_in) % thin == 0) {
+      const long long m = (done - burn_in) / thin - 1;
+      __syncthreads();
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+        crows_store<N, MR>(rows + c * CS, b, out + (m * NC + c) * NPIX * eb, out_dtype);
+      on_sample(m);
+      __syncthreads();
+    }
+    if (done == n_sweeps) break;
+    __syncwarp();
+  }
+}
+
+// the scalar sampler's sweeps (table coefficients fg in slot order)
 template <int N, int MR>
 __device__ __forceinline__ void csample_loop(cooperative_groups::cluster_group& cl, float2* rows, const float2* tw,
                                              const float2* __restrict__ aq, const float2* __restrict__ fg,
                                              float sqrt_tau, void* out_v, int out_dtype, int n_sweeps, int burn_in,
                                              int thin, uint32_t step0, uint32_t chain, uint32_t k0, uint32_t k1) {
   using G = CGeo<N, MR>;
-  const int tid = threadIdx.x, b = int(cl.block_rank());
-  int ar, h;
-  crow_of<N, MR>(tid, ar, h);
-  const int y = G::P * ar + b;
-  float2* row = rows + ar * G::SP;
-  const int eb = out_elem_bytes(out_dtype);
-  char* out = reinterpret_cast<char*>(out_v);
-  for (int done = 0;;) {
-    const uint32_t step = step0 + uint32_t(done);
-    ct_draw<N, MR>(row, y, b * G::M + ar, h, aq, sqrt_tau, step, chain, k0, k1);
-    __syncwarp();
-    crow_fwd<N, MR>(row, h, tw);
-    __syncthreads();
-    ccol_fwd<N, MR>(rows, tid, b, tw);
-    cl.sync();  // every CTA's partial column transforms are in place
-    ccol_draw<N, MR>(cl, rows, b * G::L + tid, fg, step, chain, k0, k1);
-    cl.sync();  // every unit's inverse stage has landed
-    ccol_inv<N, MR>(rows, tid, b, tw);
-    __syncthreads();
-    crow_inv<N, MR>(row, h, tw);
-    ++done;
-    if (done > burn_in && (done - burn_in) % thin == 0) {
-      const long long m = (done - burn_in) / thin - 1;
-      __syncthreads();
-      crows_store<N, MR>(rows, b, out + m * (long long)(G::H * G::W) * eb, out_dtype);
-      __syncthreads();
-    }
-    if (done == n_sweeps) break;
-    __syncwarp();
-  }
+  const int g = int(cl.block_rank()) * G::L + int(threadIdx.x);
+  csweeps<N, MR, 1>(
+      cl, rows, tw, aq, sqrt_tau, out_v, out_dtype, n_sweeps, burn_in, thin, step0, chain, k0, k1,
+      [&](uint32_t step) { ccol_draw<N, MR>(cl, rows, g, CTabCoef{fg}, step, chain, k0, k1); },
+      [](uint32_t) {}, [](long long) {});
 }
 
 // The cooled G -> 0 iteration (Alg. 1 without draws, lambda-cooling) of one image by its cluster from

@@ -655,6 +655,14 @@ WF_HD double s_update_wf_parked(float2* cs, int lt, const float* __restrict__ Pk
 // memory) with the formulas of table_mode in FP32, and accumulates the band-power statistics of the new
 // modes: S_b += |s_hat|^2 (unitary scale, full spectrum) and X_b += the squares of the stream-6 normals,
 // in FP32 shared-memory sums (their order of addition varies, so band powers repeat to FP32 rounding).
+// s-draw coefficients (f/n, g/sqrt(2n)) of band power P (table_mode's formulas in FP32; (0, 0) for P <= 0)
+WF_HD float2 band_coef(float P, float tau, float inv_n) {
+  if (!(P > 0.0f)) return make_float2(0.0f, 0.0f);
+  const float q = P * wf_rcp(P + tau);
+  const float g2 = q * tau * 0.5f * inv_n;
+  return make_float2(q * inv_n, g2 * wf_rsqrt(g2));
+}
+
 struct TableCoef {
   static constexpr bool kBand = false;
   const float2* __restrict__ fg;
@@ -673,12 +681,7 @@ struct BandCoef {
   float tau, inv_n, n;
   WF_HD float2 coef(int ky, int kx) const {
     const int b = WF_LDG(bins + ky * wh + kx);
-    if (b < 0) return WF_LDG(fg + ky * wh + kx);
-    const float P = Pb[b];
-    if (!(P > 0.0f)) return make_float2(0.0f, 0.0f);
-    const float q = P * wf_rcp(P + tau);
-    const float g2 = q * tau * 0.5f * inv_n;
-    return make_float2(q * inv_n, g2 * wf_rsqrt(g2));
+    return b < 0 ? WF_LDG(fg + ky * wh + kx) : band_coef(Pb[b], tau, inv_n);
   }
   WF_HD int bin(int ky, int kx) const { return WF_LDG(bins + ky * wh + kx); }
   WF_HD void flush(int b, float s2, float x2) const {

@@ -8,6 +8,7 @@
 #include "wf_batch.cuh"
 #include "wf_gbatch.cuh"
 #include "wf_cluster.cuh"
+#include "wf_cluster_ext.cuh"
 #include "wf_bphase.cuh"
 
 namespace wf {
@@ -69,6 +70,14 @@ cudaError_t csample_clusters(int* clusters);
 // whole pipeline (level norms, cooled solve, samples) of a batch of large images: one cluster per image
 template <int N, int MR>
 cudaError_t launch_cpipe(const CBArgs& a, cudaStream_t st, LaunchTimer* t);
+
+// cluster-resident hierarchical sampler (a.bins and a.fg in slot order; N / MR CTAs per chain) and
+// spin-2 sampler (both components per cluster). cudaErrorNotSupported when no cluster of that shape
+// can be resident.
+template <int N, int MR>
+cudaError_t launch_csample_band(const SampleArgs& a, cudaStream_t st, LaunchTimer* t);
+template <int N, int MR>
+cudaError_t launch_csample_spin2(const Spin2Args& a, cudaStream_t st, LaunchTimer* t);
 
 // definitions, included by the per-size translation units only
 #if defined(WF_LAUNCH_DEFINE)
@@ -327,6 +336,66 @@ cudaError_t launch_cpipe(const CBArgs& a, cudaStream_t st, LaunchTimer* t) {
   template cudaError_t launch_csample<N, MR>(const SampleArgs&, cudaStream_t, LaunchTimer*);   \
   template cudaError_t csample_clusters<N, MR>(int*);                                          \
   template cudaError_t launch_cpipe<N, MR>(const CBArgs&, cudaStream_t, LaunchTimer*);
+#endif
+
+#if defined(WF_LAUNCH_DEFINE_CLUSTER_EXT)
+// launch configuration of `clusters` clusters of P CTAs of `threads` threads with `smem` dynamic shared
+// bytes each; cudaErrorNotSupported when not one such cluster can be resident
+template <class Kern>
+cudaError_t cluster_launch_config(Kern kern, int P, int threads, int smem, int clusters, cudaStream_t st,
+                                  cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  if (P > 8) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = unsigned(P);
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  *cfg = cudaLaunchConfig_t{};
+  cfg->gridDim = dim3(unsigned(clusters) * unsigned(P), 1, 1);
+  cfg->blockDim = dim3(unsigned(threads), 1, 1);
+  cfg->dynamicSmemBytes = size_t(smem);
+  cfg->stream = st;
+  cfg->attrs = attr;
+  cfg->numAttrs = 1;
+  int resident = 0;
+  e = cudaOccupancyMaxActiveClusters(&resident, kern, cfg);
+  if (e != cudaSuccess) return e;
+  return resident > 0 ? cudaSuccess : cudaErrorNotSupported;
+}
+template <int N, int MR>
+cudaError_t launch_csample_band(const SampleArgs& a, cudaStream_t st, LaunchTimer* t) {
+  using G = CGeo<N, MR>;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  cudaError_t e = cluster_launch_config(k_csample_band<N, MR>, G::P, G::L, cband_smem<N, MR>(a.n_bins), a.n_chains,
+                                        st, &cfg, attr);
+  if (e != cudaSuccess) return e;
+  if (t) t->start();
+  e = cudaLaunchKernelEx(&cfg, k_csample_band<N, MR>, a);
+  if (t) t->stop();
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+template <int N, int MR>
+cudaError_t launch_csample_spin2(const Spin2Args& a, cudaStream_t st, LaunchTimer* t) {
+  using G = CGeo<N, MR>;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  cudaError_t e =
+      cluster_launch_config(k_csample_spin2<N, MR>, G::P, G::L, cspin2_smem<N, MR>(), a.n_chains, st, &cfg, attr);
+  if (e != cudaSuccess) return e;
+  if (t) t->start();
+  e = cudaLaunchKernelEx(&cfg, k_csample_spin2<N, MR>, a);
+  if (t) t->stop();
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+#define WF_INSTANTIATE_CLUSTER_BAND(N, MR) \
+  template cudaError_t launch_csample_band<N, MR>(const SampleArgs&, cudaStream_t, LaunchTimer*);
+#define WF_INSTANTIATE_CLUSTER_SPIN2(N, MR) \
+  template cudaError_t launch_csample_spin2<N, MR>(const Spin2Args&, cudaStream_t, LaunchTimer*);
 #endif
 
 }  // namespace wf

@@ -52,3 +52,53 @@ def test_band_sampler_checks_and_fixed_bins():
     xs, Ps = wf.wf_sample_band(*dev, none, torch.zeros(0, device="cuda"), seed=5, n_samples=3, chain_offset=2)
     ref = wf.wf_sample_ex(*dev, seed=5, n_samples=3, chain_offset=2)
     assert torch.equal(xs, ref) and Ps.shape == (1, 3, 0)
+
+
+@pytest.mark.parametrize("H", [256, 512])
+def test_band_sampler_large_draw_for_draw(H):
+    """256^2 and 512^2: one thread-block cluster per chain, band statistics summed across the cluster."""
+    p = synth.make_problem(H, seed=H + 9, mask_frac=0.1, block=(10, 60, 20, 90), slope=-2.0, k0=1.0 / 32,
+                           sigma2=(0.05, 0.5))
+    bins, nb = HG.radial_bins(H, H)
+    P0 = np.full(nb, 0.5, np.float32)
+    n = 4 if H == 256 else 3
+    xs, Ps = wf.wf_sample_band(*to_dev(p), torch.from_numpy(bins).cuda(), torch.from_numpy(P0).cuda(), seed=8,
+                               n_samples=n, n_chains=2, chain_offset=3, burn_in=1)
+    xs, Ps = xs.cpu().numpy(), Ps.cpu().numpy()
+    for c in range(2):
+        rs, rP = HG.sample(p.d, p.Ndiag, p.mask, p.Pk, bins, P0, n, seed=8, chain=3 + c, burn_in=1)
+        for m in range(n):
+            assert rel(xs[c, m], rs[m]) < SAMPLE_TOL, (H, c, m, rel(xs[c, m], rs[m]))
+            assert rel(Ps[c, m], rP[m]) < SAMPLE_TOL, (H, c, m, rel(Ps[c, m], rP[m]))
+
+
+def test_band_sampler_large_thin_resume_and_fixed_bins():
+    """256^2: thinning and a resumed chain (start_step, init_s, the band powers carried over) repeat the
+    uninterrupted chain; with every mode fixed (bins = -1) the band sampler is the plain cluster sampler."""
+    H = 256
+    p = synth.make_problem(H, seed=5, mask_frac=0.1, slope=-2.0, k0=1.0 / 32, sigma2=(0.05, 0.5))
+    dev = to_dev(p)
+    bins, nb = HG.radial_bins(H, H)
+    bd = torch.from_numpy(bins).cuda()
+    P0 = torch.full((nb,), 0.5, device="cuda")
+    full, fP = wf.wf_sample_band(*dev, bd, P0, seed=4, n_samples=2, thin=2)
+    rs, rP = HG.sample(p.d, p.Ndiag, p.mask, p.Pk, bins, P0.cpu().numpy(), 2, seed=4, thin=2)
+    for m in range(2):
+        assert rel(full[0, m].cpu().numpy(), rs[m]) < SAMPLE_TOL
+        assert rel(fP[0, m].cpu().numpy(), rP[m]) < SAMPLE_TOL
+    # resume after sweep 2 from (s, P) of the first kept sample
+    tail, tP = wf.wf_sample_band(*dev, bd, fP[0, 0].contiguous(), seed=4, n_samples=1, thin=2, start_step=2,
+                                 init_s=full[0, 0].contiguous())
+    assert rel(tail[0, 0].cpu().numpy(), full[0, 1].cpu().numpy()) < SAMPLE_TOL
+    assert rel(tP[0, 0].cpu().numpy(), fP[0, 1].cpu().numpy()) < SAMPLE_TOL
+    none = torch.full((H, H // 2 + 1), -1, dtype=torch.int32, device="cuda")
+    xs, Ps = wf.wf_sample_band(*dev, none, torch.zeros(0, device="cuda"), seed=5, n_samples=2, n_chains=2)
+    prev = wf.wf_set_large_image_sampler("cluster")
+    try:
+        ref = wf.wf_sample_ex(*dev, seed=5, n_samples=2, n_chains=2)
+    finally:
+        wf.wf_set_large_image_sampler(prev)
+    assert torch.equal(xs, ref) and Ps.shape == (2, 2, 0)
+    with pytest.raises(wf.WFError) as e:  # more bins than the 256^2 kernel holds
+        wf.wf_sample_band(*dev, bd, torch.full((257,), 0.5, device="cuda"), seed=1, n_samples=1)
+    assert e.value.status == 1

@@ -46,6 +46,37 @@ def test_spin2_sampler_draw_for_draw(H):
                 assert rel(got[c, m, comp], ref[m, comp]) < SAMPLE_TOL, (H, c, m, comp)
 
 
+@pytest.mark.parametrize("H", [256, 512])
+def test_spin2_sampler_large_draw_for_draw(H):
+    """256^2 and 512^2: both shear components of a chain in one thread-block cluster."""
+    p, d2, N2, PB = _pair(H, H + 2)
+    n = 3 if H == 256 else 2
+    got = wf.wf_sample_spin2(*_dev(p.d, d2, p.Ndiag, N2, p.mask, p.Pk, PB), seed=6, n_samples=n, n_chains=2,
+                             chain_offset=1).cpu().numpy()
+    for c in range(2):
+        ref = S2.sample(p.d, d2, p.Ndiag, N2, p.mask, p.Pk, PB, n, seed=6, chain=1 + c)
+        for m in range(n):
+            for comp in range(2):
+                assert rel(got[c, m, comp], ref[m, comp]) < SAMPLE_TOL, (H, c, m, comp,
+                                                                         rel(got[c, m, comp], ref[m, comp]))
+
+
+def test_spin2_sampler_large_resume_and_zero_b_power():
+    """256^2: a chain resumed from its first sample (init, start_step) repeats the second; with P_B = 0 the
+    B modes of every sample vanish (kappa_B = 0 up to rounding) while E carries the signal."""
+    H = 256
+    p, d2, N2, PB = _pair(H, 11)
+    dev = _dev(p.d, d2, p.Ndiag, N2, p.mask, p.Pk, PB)
+    full = wf.wf_sample_spin2(*dev, seed=3, n_samples=2)
+    tail = wf.wf_sample_spin2(*dev, seed=3, n_samples=1, start_step=1, init=full[0, 0].contiguous())
+    assert rel(tail[0, 0].cpu().numpy(), full[0, 1].cpu().numpy()) < SAMPLE_TOL
+    dev[6] = torch.zeros_like(dev[6])
+    g = wf.wf_sample_spin2(*dev, seed=3, n_samples=2, n_chains=2)
+    k = wf.wf_shear_to_convergence(g.reshape(4, 2, H, H)).cpu().numpy()
+    for i in range(4):
+        assert np.linalg.norm(k[i, 1]) < 1e-5 * np.linalg.norm(k[i, 0])
+
+
 def test_shear_to_convergence_matches_oracle():
     rng = np.random.default_rng(3)
     for H in (16, 128, 256):
