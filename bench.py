@@ -165,6 +165,11 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # the timed region starts after the first sample: nvidia-smi's start-up (driver queries) can
+            # otherwise delay the first timed launches by milliseconds
+            t0 = time.time()
+            while not self.lines and self.proc.poll() is None and time.time() - t0 < 5.0:
+                time.sleep(0.01)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
@@ -489,9 +494,39 @@ def band_sampler(dev):
         wf.wf_sample_band(d, Nd, mk, Pk, bt, P0, seed=2 + i, n_samples=N_SAMPLES, n_chains=N_CHAINS)
         ks.append(wf.wf_last_kernel_ms())
     kms = statistics.mean(ks)
-    return {"workload": f"paper-shaped 128x128, 1024 chains x 100 sweeps, {nb} radial band powers drawn each sweep",
-            "samples_per_s": N_CHAINS * N_SAMPLES / (kms / 1e3), "kernel_ms": kms,
-            "n_bins": nb}
+    res = {"workload": f"paper-shaped 128x128, 1024 chains x 100 sweeps, {nb} radial band powers drawn each sweep",
+           "samples_per_s": N_CHAINS * N_SAMPLES / (kms / 1e3), "kernel_ms": kms,
+           "n_bins": nb}
+    # 256^2 and 512^2: one thread-block cluster per chain
+    for Hl, chains, ns in ((256, 456, 20), (512, 76, 10)):
+        q = synth.make_problem(Hl, seed=Hl, mask_frac=0.1, slope=-2.0, k0=1.0 / 32, sigma2=(0.05, 0.5))
+        args = [torch.from_numpy(x).to(dev) for x in (q.d, q.Ndiag, q.mask, q.Pk)]
+        kyl = np.fft.fftfreq(Hl) * Hl
+        rl = np.sqrt(kyl[:, None] ** 2 + np.arange(Hl // 2 + 1)[None, :] ** 2)
+        bl = np.floor(rl).astype(np.int32) - 1
+        bl[0, 0] = -1
+        nbl = int(bl.max()) + 1
+        btl, P0l = torch.from_numpy(bl).to(dev), torch.ones(nbl, device=dev)
+        wf.wf_sample_band(*args, btl, P0l, seed=1, n_samples=ns, n_chains=chains)
+        ks = []
+        for i in range(3):
+            wf.wf_sample_band(*args, btl, P0l, seed=2 + i, n_samples=ns, n_chains=chains)
+            ks.append(wf.wf_last_kernel_ms())
+        kl = statistics.mean(ks)
+        res[f"{Hl}x{Hl}"] = {"workload": f"{Hl}x{Hl}, {chains} chains x {ns} sweeps (all kept), {nbl} radial band "
+                                         "powers drawn each sweep, one thread-block cluster per chain",
+                             "samples_per_s": chains * ns / (kl / 1e3), "kernel_ms": kl, "n_bins": nbl,
+                             "roofline": _fft_roofline(Hl, chains * ns, kl)}
+    return res
+
+
+def _fft_roofline(H: int, sweeps: int, kernel_ms: float, fields: int = 1) -> dict:
+    """ALU roofline of `sweeps` field sweeps of H x H (5 n log2 n flops each: the sweep's two real 2D
+    transforms) against the measured FP32 FMA peak."""
+    n = H * H
+    achieved = 5.0 * n * math.log2(n) * fields * sweeps / (kernel_ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS}
 
 
 def spin2_sampler(dev, n_chains: int = 512):
@@ -512,11 +547,29 @@ def spin2_sampler(dev, n_chains: int = 512):
         wf.wf_sample_spin2(*args, seed=2 + i, n_samples=N_SAMPLES, n_chains=n_chains)
         ks.append(wf.wf_last_kernel_ms())
     kms = statistics.mean(ks)
-    return {"workload": f"128x128 shear pair, {n_chains} chains x 100 sweeps (4 real 2D FFTs per sweep)",
-            "samples_per_s": n_chains * N_SAMPLES / (kms / 1e3), "kernel_ms": kms,
-            "roofline": {"bound": "alu", "achieved": 2 * FLOPS_PER_SWEEP * n_chains * N_SAMPLES / (kms / 1e3) / 1e12,
-                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": 2 * FLOPS_PER_SWEEP * n_chains * N_SAMPLES / (kms / 1e3) / 1e12 / FP32_PEAK_TFLOPS}}
+    res = {"workload": f"128x128 shear pair, {n_chains} chains x 100 sweeps (4 real 2D FFTs per sweep)",
+           "samples_per_s": n_chains * N_SAMPLES / (kms / 1e3), "kernel_ms": kms,
+           "roofline": {"bound": "alu", "achieved": 2 * FLOPS_PER_SWEEP * n_chains * N_SAMPLES / (kms / 1e3) / 1e12,
+                        "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": 2 * FLOPS_PER_SWEEP * n_chains * N_SAMPLES / (kms / 1e3) / 1e12 / FP32_PEAK_TFLOPS}}
+    # 256^2 and 512^2: both components of a chain in one thread-block cluster
+    for Hl, chains, ns in ((256, 228, 20), (512, 36, 10)):
+        q = synth.make_problem(Hl, seed=Hl, mask_frac=0.1, slope=-2.0, k0=1.0 / 32, sigma2=(0.05, 0.5))
+        d2l = np.where(q.mask == 1, 0.0, rng.standard_normal(q.d.shape)).astype(np.float32)
+        N2l = rng.uniform(0.05, 0.5, q.d.shape).astype(np.float32)
+        argl = [torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+                for x in (q.d, d2l, q.Ndiag, N2l, q.mask, q.Pk, (0.2 * q.Pk).astype(np.float32))]
+        wf.wf_sample_spin2(*argl, seed=1, n_samples=ns, n_chains=chains)
+        ks = []
+        for i in range(3):
+            wf.wf_sample_spin2(*argl, seed=2 + i, n_samples=ns, n_chains=chains)
+            ks.append(wf.wf_last_kernel_ms())
+        kl = statistics.mean(ks)
+        res[f"{Hl}x{Hl}"] = {"workload": f"{Hl}x{Hl} shear pair, {chains} chains x {ns} sweeps (all kept), "
+                                         "both components of a chain in one thread-block cluster",
+                             "samples_per_s": chains * ns / (kl / 1e3), "kernel_ms": kl,
+                             "roofline": _fft_roofline(Hl, chains * ns, kl, fields=2)}
+    return res
 
 
 def large_sampler(dev, chains256: int = 456, samples256: int = 20):

@@ -870,11 +870,64 @@ __global__ void k_check_band(const int32_t* __restrict__ bins, int nm, int n_bin
   if (bad && sc->status == 0) sc->status = WF_ERR_ARG;
 }
 
-// the bin map [H][W/2+1] in the column slot order of the cluster kernels with cm rows per CTA (mode_pos)
-__global__ void k_bins_slots(const int32_t* __restrict__ bins, int H, int W, int cm, int32_t* __restrict__ out) {
-  const int nm = H * (W / 2 + 1);
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nm; j += gridDim.x * blockDim.x)
-    out[mode_pos(j, H, W, cm)] = bins[j];
+// Plan of the cluster hierarchical sampler's band sums. bmap (column slot order of the cluster kernels with
+// cm rows per CTA, mode_pos) = (bin, position): the modes the s-draw visits (cband_visited) with a bin get
+// consecutive positions per bin, bins in order and modes in slot order within a bin (so the sums run in
+// the same order every call); off[b] = first position of bin b; lo[j] = first bin summed by CTA j of a
+// cluster of P (contiguous ranges of about equal mode counts).
+__global__ void k_band_map(const int32_t* __restrict__ bins, int H, int W, int cm, int n_bins, int2* __restrict__ bmap,
+                           int* __restrict__ cnt) {
+  const int nm = H * (W / 2 + 1), L = W / 2;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nm; j += gridDim.x * blockDim.x) {
+    const int q = mode_pos(j, H, W, cm), b = bins[j];
+    bmap[q] = make_int2(b, -1);
+    if (b >= 0 && b < n_bins && wf::cband_visited(q, H, L)) atomicAdd(cnt + b, 1);
+  }
+}
+__global__ void k_band_offsets(const int* __restrict__ cnt, int n_bins, int P, int* __restrict__ off,
+                               int* __restrict__ lo) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int acc = 0;
+  for (int b = 0; b < n_bins; ++b) {
+    off[b] = acc;
+    acc += cnt[b];
+  }
+  off[n_bins] = acc;
+  int b = 0;
+  for (int j = 0; j < P; ++j) {  // CTA j starts at the first bin whose modes begin at or after j/P of all
+    const long long target = (long long)acc * j / P;
+    while (b < n_bins && off[b] < target) ++b;
+    lo[j] = b;
+  }
+  lo[P] = n_bins;
+}
+// one block per bin: the bin's visited modes in slot order get positions off[b], off[b] + 1, ...
+__global__ void k_band_positions(int H, int W, const int* __restrict__ off, int2* __restrict__ bmap) {
+  __shared__ int wsum[8];
+  const int b = blockIdx.x, nm = H * (W / 2 + 1), L = W / 2;
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  int base = off[b];
+  for (int c = 0; c < nm; c += 256) {
+    const int i = c + int(threadIdx.x);
+    const bool f = i < nm && bmap[i].x == b && wf::cband_visited(i, H, L);
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    if (l == 0) wsum[w] = __popc(bal);
+    __syncthreads();
+    int pre = 0, tot = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      pre += k < w ? wsum[k] : 0;
+      tot += wsum[k];
+    }
+    if (f) bmap[i].y = base + pre + __popc(bal & ((1u << l) - 1u));
+    base += tot;
+    __syncthreads();  // wsum is rewritten in the next chunk
+  }
+}
+
+// clusters of the hierarchical sampler at size H that can be resident at once
+cudaError_t band_clusters_any(int H, int n_bins, int* n) {
+  return H == 256 ? wf::csample_band_clusters<256, 64>(n_bins, n) : wf::csample_band_clusters<512, 32>(n_bins, n);
 }
 
 // largest number of bins of the hierarchical sampler at size H
@@ -899,12 +952,21 @@ wf_status wf_sample_band(const float* d, const float* Ndiag, const uint8_t* mask
   if (sweeps > 0x7fffffffLL || o.n_samples > 0x7fffffffLL) return WF_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const size_t n = size_t(H) * W, nm = size_t(H) * (W / 2 + 1);
-  // 256 and 512: one thread-block cluster per chain, tables in the cluster kernels' orders
+  // 256 and 512: thread-block clusters (as many as can be resident, each looping over chains), tables in
+  // the cluster kernels' orders, the band-sum plan and one statistics buffer per cluster
   const bool cluster = !size_on_chip(H);
   const int cm = cluster ? wf::cluster_rows(H) : 0, perm = cluster ? H / cm : 0;
+  int n_cl = 0;
+  if (cluster) {
+    WF_CUDA(band_clusters_any(H, n_bins, &n_cl));
+    if (n_cl < 1) return cuda_fail(cudaErrorNotSupported);
+    if (n_cl > o.n_chains) n_cl = o.n_chains;
+  }
   Carve cv;
   const size_t off_sc = cv.take<wf::Scalars>(1), off_aq = cv.take<float2>(n), off_fg = cv.take<float2>(nm),
-               off_bins = cv.take<int32_t>(cluster ? nm : 0);
+               off_map = cv.take<int2>(cluster ? nm : 0), off_cnt = cv.take<int>(cluster ? n_bins + 1 : 0),
+               off_off = cv.take<int>(cluster ? n_bins + 1 : 0), off_lo = cv.take<int>(cluster ? perm + 1 : 0),
+               off_buf = cv.take<float2>(cluster ? size_t(n_cl) * nm : 0);
   Scratch scr;
   scr.st = st;
   WF_CUDA(cudaMallocAsync(&scr.base, cv.off, st));
@@ -918,11 +980,16 @@ wf_status wf_sample_band(const float* d, const float* Ndiag, const uint8_t* mask
   WF_CUDA(cudaGetLastError());
   k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc, aq, nullptr, fg, perm, cm);
   WF_CUDA(cudaGetLastError());
-  if (cluster) {
-    auto* bs = reinterpret_cast<int32_t*>(b + off_bins);
-    k_bins_slots<<<int((nm + 255) / 256), 256, 0, st>>>(bins, H, W, cm, bs);
+  int2* bmap = reinterpret_cast<int2*>(b + off_map);
+  int* band_off = reinterpret_cast<int*>(b + off_off);
+  int* band_lo = reinterpret_cast<int*>(b + off_lo);
+  if (cluster) {  // the bins were checked by k_check_band, but the plan is built before its status is read
+    int* cnt = reinterpret_cast<int*>(b + off_cnt);
+    WF_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (n_bins + 1), st));
+    k_band_map<<<int((nm + 255) / 256), 256, 0, st>>>(bins, H, W, cm, n_bins, bmap, cnt);
+    k_band_offsets<<<1, 32, 0, st>>>(cnt, n_bins, perm, band_off, band_lo);
+    if (n_bins > 0) k_band_positions<<<n_bins, 256, 0, st>>>(H, W, band_off, bmap);
     WF_CUDA(cudaGetLastError());
-    bins = bs;
   }
   wf::SampleArgs a{};
   a.aq = aq; a.fg = fg; a.sc = sc; a.init_s = o.init_s;
@@ -932,6 +999,8 @@ wf_status wf_sample_band(const float* d, const float* Ndiag, const uint8_t* mask
   a.key0 = uint32_t(seed & 0xffffffffu); a.key1 = uint32_t(seed >> 32);
   a.out_dtype = o.out_dtype;
   a.bins = bins; a.n_bins = n_bins; a.P0 = P0; a.out_P = out_P;
+  a.band_map = bmap; a.band_off = band_off; a.band_lo = band_lo;
+  a.band_buf = reinterpret_cast<float2*>(b + off_buf); a.band_clusters = n_cl;
   KernelTimer timer(st);
   cudaError_t e = cudaSuccess;
   switch (H) {

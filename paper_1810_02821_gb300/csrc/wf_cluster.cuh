@@ -253,33 +253,35 @@ __device__ __forceinline__ void ccol_inv(float2* rows, int t, int b, const float
 
 // Mode coefficients of the cluster s-draw, looked up by the slot-order index i = ctab_index(ky, kx).
 // CTabCoef reads the per-call table fg = (f / n, g / sqrt(2 n)). CBandCoef (the hierarchical sampler)
-// derives them from the band power P_b of the mode's bin (bins >= 0; -1: the table's coefficients) with
-// band_coef, and sums the band statistics of the new modes into this CTA's shared accumulators:
-// S_b += n |s_hat|^2 (unitary scale, the mirror modes counted) and X_b += the squares of the stream-6
-// normals, FP32 atomics (their order of addition varies, so band powers repeat to FP32 rounding).
+// takes them from the per-band table cb = band_coef(P_b) of the mode's bin (bmap[i].x >= 0; -1: the
+// table's coefficients) and stores the band statistics of each new mode, (n |s_hat|^2 weighted by the
+// mirror modes it stands for, the squares of its stream-6 normals), to its own position bmap[i].y of the
+// chain's bin-ordered buffer (-1: not summed), so that the band sums need no atomics.
 struct CTabCoef {
   static constexpr bool kBand = false;
   const float2* __restrict__ fg;
   __device__ __forceinline__ float2 m(int i) const { return WF_LDG(fg + i); }
-  __device__ __forceinline__ void add(int, float, float) const {}
+  __device__ __forceinline__ void add2(int, float, float, int, float, float) const {}
 };
 struct CBandCoef {
   static constexpr bool kBand = true;
   const float2* __restrict__ fg;
-  const int* __restrict__ bins;  // slot order, as fg
-  const float* Pb;               // shared [n_bins]
-  float* acc;                    // shared [2][n_bins] of the current sweep: S_b, then X_b
-  int n_bins;
-  float tau, inv_n, n;
+  const int2* __restrict__ bmap;  // slot order: (bin, position in the bin-ordered buffer)
+  const float2* cb;               // shared [n_bins]: band_coef of each band power
+  float2* buf;                    // this chain's statistics, bin-ordered (global, L2)
+  float n;
   __device__ __forceinline__ float2 m(int i) const {
-    const int b = WF_LDG(bins + i);
-    return b < 0 ? WF_LDG(fg + i) : band_coef(Pb[b], tau, inv_n);
+    const int b = WF_LDG(bmap + i).x;
+    return b < 0 ? WF_LDG(fg + i) : cb[b];
   }
-  __device__ __forceinline__ void add(int i, float s2, float x2) const {
-    const int b = WF_LDG(bins + i);
-    if (b < 0) return;
-    atomicAdd(acc + b, s2 * n);
-    atomicAdd(acc + n_bins + b, x2);
+  __device__ __forceinline__ void put(int i, float s2, float x2) const {
+    if (i < 0) return;
+    const int pos = WF_LDG(bmap + i).y;
+    if (pos >= 0) __stcg(buf + pos, make_float2(s2 * n, x2));
+  }
+  __device__ __forceinline__ void add2(int i0, float s0, float x0, int i1, float s1, float x1) const {
+    put(i0, s0, x0);
+    put(i1, s1, x1);
   }
 };
 
@@ -298,43 +300,49 @@ __device__ __forceinline__ void cdraw_pair(float2& y1, float2& y2, int K, int t,
   normals4(grp, step, chain, 1u, k0, k1, z);
   if constexpr (C::kBand) normals4(grp, step, chain, 6u, k0, k1, zb);
   auto sq = [](float2 v) { return fmaf(v.x, v.x, v.y * v.y); };
+  // band statistics of the new modes: (index, weighted |s_hat|^2, sum of squared stream-6 normals), two
+  // entries per pair; the edge lane's real modes (H/2, 0), (H/2, W/2) of group 0 come after
+  int ia = -1, ib = -1;
+  float sa = 0.f, xa = 0.f, sb = 0.f, xb = 0.f;
   if (K != 0) {
     const int i1 = ky1 * G::L + t, i2 = ky2 * G::L + t;
     const float2 m1 = cf.m(i1), m2 = cf.m(i2);
     y1 = make_float2(fmaf(m1.x, y1.x, m1.y * z[0]), fmaf(m1.x, y1.y, m1.y * z[1]));
     y2 = make_float2(fmaf(m2.x, y2.x, m2.y * z[2]), fmaf(m2.x, y2.y, m2.y * z[3]));
     if constexpr (C::kBand) {  // both modes have their mirror in the other half plane: weight 2
-      cf.add(i1, 2.0f * sq(y1), fmaf(zb[0], zb[0], zb[1] * zb[1]));
-      cf.add(i2, 2.0f * sq(y2), fmaf(zb[2], zb[2], zb[3] * zb[3]));
-    }
-    return;
-  }
-  const int ia1 = ky1 * G::L, ib1 = G::H * G::L + ky1;
-  const float2 a1 = cf.m(ia1), b1 = cf.m(ib1);
-  if (ky1 == 0) {
-    const int ia2 = ky2 * G::L, ib2 = G::H * G::L + ky2;
-    const float2 a2 = cf.m(ia2), b2 = cf.m(ib2);
-    constexpr float R2 = 1.41421356237309505f;
-    y1 = make_float2(fmaf(a1.x, y1.x, R2 * a1.y * z[0]), fmaf(b1.x, y1.y, R2 * b1.y * z[2]));
-    y2 = make_float2(fmaf(a2.x, y2.x, R2 * a2.y * z[1]), fmaf(b2.x, y2.y, R2 * b2.y * z[3]));
-    if constexpr (C::kBand) {  // one real degree of freedom each
-      cf.add(ia1, y1.x * y1.x, zb[0] * zb[0]);
-      cf.add(ib1, y1.y * y1.y, zb[2] * zb[2]);
-      cf.add(ia2, y2.x * y2.x, zb[1] * zb[1]);
-      cf.add(ib2, y2.y * y2.y, zb[3] * zb[3]);
+      ia = i1, sa = 2.0f * sq(y1), xa = fmaf(zb[0], zb[0], zb[1] * zb[1]);
+      ib = i2, sb = 2.0f * sq(y2), xb = fmaf(zb[2], zb[2], zb[3] * zb[3]);
     }
   } else {
-    const float2 y2c = cconj(y2);
-    const float2 Am = cscale(cadd(y1, y2c), 0.5f);
-    const float2 Bm = cmul_mi(cscale(csub(y1, y2c), 0.5f));
-    const float2 Ap = make_float2(fmaf(a1.x, Am.x, a1.y * z[0]), fmaf(a1.x, Am.y, a1.y * z[1]));
-    const float2 Bp = make_float2(fmaf(b1.x, Bm.x, b1.y * z[2]), fmaf(b1.x, Bm.y, b1.y * z[3]));
-    y1 = cadd(Ap, cmul_i(Bp));
-    y2 = cadd(cconj(Ap), cmul_i(cconj(Bp)));
-    if constexpr (C::kBand) {  // (ky1, 0) and (ky1, W/2) with their mirrors at H - ky1: weight 2
-      cf.add(ia1, 2.0f * sq(Ap), fmaf(zb[0], zb[0], zb[1] * zb[1]));
-      cf.add(ib1, 2.0f * sq(Bp), fmaf(zb[2], zb[2], zb[3] * zb[3]));
+    const int ia1 = ky1 * G::L, ib1 = G::H * G::L + ky1;
+    const float2 a1 = cf.m(ia1), b1 = cf.m(ib1);
+    if (ky1 == 0) {
+      const float2 a2 = cf.m(ky2 * G::L), b2 = cf.m(G::H * G::L + ky2);
+      constexpr float R2 = 1.41421356237309505f;
+      y1 = make_float2(fmaf(a1.x, y1.x, R2 * a1.y * z[0]), fmaf(b1.x, y1.y, R2 * b1.y * z[2]));
+      y2 = make_float2(fmaf(a2.x, y2.x, R2 * a2.y * z[1]), fmaf(b2.x, y2.y, R2 * b2.y * z[3]));
+      if constexpr (C::kBand) {  // one real degree of freedom each
+        ia = ia1, sa = y1.x * y1.x, xa = zb[0] * zb[0];
+        ib = ib1, sb = y1.y * y1.y, xb = zb[2] * zb[2];
+      }
+    } else {
+      const float2 y2c = cconj(y2);
+      const float2 Am = cscale(cadd(y1, y2c), 0.5f);
+      const float2 Bm = cmul_mi(cscale(csub(y1, y2c), 0.5f));
+      const float2 Ap = make_float2(fmaf(a1.x, Am.x, a1.y * z[0]), fmaf(a1.x, Am.y, a1.y * z[1]));
+      const float2 Bp = make_float2(fmaf(b1.x, Bm.x, b1.y * z[2]), fmaf(b1.x, Bm.y, b1.y * z[3]));
+      y1 = cadd(Ap, cmul_i(Bp));
+      y2 = cadd(cconj(Ap), cmul_i(cconj(Bp)));
+      if constexpr (C::kBand) {  // (ky1, 0) and (ky1, W/2) with their mirrors at H - ky1: weight 2
+        ia = ia1, sa = 2.0f * sq(Ap), xa = fmaf(zb[0], zb[0], zb[1] * zb[1]);
+        ib = ib1, sb = 2.0f * sq(Bp), xb = fmaf(zb[2], zb[2], zb[3] * zb[3]);
+      }
     }
+  }
+  if constexpr (C::kBand) {
+    cf.add2(ia, sa, xa, ib, sb, xb);
+    if (K == 0 && ky1 == 0)  // the edge lane's real modes (H/2, 0) and (H/2, W/2)
+      cf.add2(ky2 * G::L, y2.x * y2.x, zb[1] * zb[1], G::H * G::L + ky2, y2.y * y2.y, zb[3] * zb[3]);
   }
 }
 
@@ -567,15 +575,16 @@ __device__ __forceinline__ void crows_store(const float2* rows, int b, void* dst
 
 // Sampler sweeps (Alg. 1) of one chain by its cluster from the staged rows (the current s) of NC fields
 // (NC = 2: the two shear components, field c's rows at rows + c A SP, its pixel table at aq + c H W, its
-// t-draw from Philox stream 8 c). Per sweep: t-draws and forward transforms, then col(step) between the
-// two cluster barriers (the column spectra complete: the s-draw), post(step) right after the second
-// (every CTA's column work done), the inverse transforms. Sample m (the state after sweep
-// burn_in + (m + 1) thin) goes to out + (m NC + c) H W elements of type out_dtype, then on_sample(m).
-template <int N, int MR, int NC, class Col, class Post, class OnSample>
+// t-draw from Philox stream 8 c). Per sweep (done = the sweeps before it in this call, step = step0 +
+// done): t-draws and forward transforms, then col(step, done) between the two cluster barriers (the column
+// spectra complete: the s-draw), post(step, done) right after the second (every CTA's column work done),
+// the inverse transforms. Sample m (the state after sweep burn_in + (m + 1) thin) goes to
+// out + (m NC + c) H W elements of type out_dtype.
+template <int N, int MR, int NC, class Col, class Post>
 __device__ __forceinline__ void csweeps(cooperative_groups::cluster_group& cl, float2* rows, const float2* tw,
                                         const float2* __restrict__ aq, float sqrt_tau, void* out_v, int out_dtype,
                                         int n_sweeps, int burn_in, int thin, uint32_t step0, uint32_t chain,
-                                        uint32_t k0, uint32_t k1, Col&& col, Post&& post, OnSample&& on_sample) {
+                                        uint32_t k0, uint32_t k1, Col&& col, Post&& post) {
   using G = CGeo<N, MR>;
   constexpr int CS = G::A * G::SP;
   constexpr long long NPIX = (long long)G::H * G::W;
@@ -598,9 +607,9 @@ __device__ __forceinline__ void csweeps(cooperative_groups::cluster_group& cl, f
 #pragma unroll
     for (int c = 0; c < NC; ++c) ccol_fwd<N, MR>(rows + c * CS, tid, b, tw);
     cl.sync();  // every CTA's partial column transforms are in place
-    col(step);
+    col(step, done);
     cl.sync();  // every unit's inverse stage has landed
-    post(step);
+    post(step, done);
 #pragma unroll
     for (int c = 0; c < NC; ++c) ccol_inv<N, MR>(rows + c * CS, tid, b, tw);
     __syncthreads();
@@ -613,7 +622,6 @@ __device__ __forceinline__ void csweeps(cooperative_groups::cluster_group& cl, f
 #pragma unroll
       for (int c = 0; c < NC; ++c)
         crows_store<N, MR>(rows + c * CS, b, out + (m * NC + c) * NPIX * eb, out_dtype);
-      on_sample(m);
       __syncthreads();
     }
     if (done == n_sweeps) break;
@@ -631,8 +639,8 @@ __device__ __forceinline__ void csample_loop(cooperative_groups::cluster_group& 
   const int g = int(cl.block_rank()) * G::L + int(threadIdx.x);
   csweeps<N, MR, 1>(
       cl, rows, tw, aq, sqrt_tau, out_v, out_dtype, n_sweeps, burn_in, thin, step0, chain, k0, k1,
-      [&](uint32_t step) { ccol_draw<N, MR>(cl, rows, g, CTabCoef{fg}, step, chain, k0, k1); },
-      [](uint32_t) {}, [](long long) {});
+      [&](uint32_t step, int) { ccol_draw<N, MR>(cl, rows, g, CTabCoef{fg}, step, chain, k0, k1); },
+      [](uint32_t, int) {});
 }
 
 // The cooled G -> 0 iteration (Alg. 1 without draws, lambda-cooling) of one image by its cluster from

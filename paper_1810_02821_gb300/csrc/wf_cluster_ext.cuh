@@ -2,13 +2,16 @@
 // extensions of §5 on the cluster geometry of wf_cluster.cuh: one chain per thread-block cluster, CTA b
 // keeping the global rows y = P a + b for all sweeps).
 //
-// Hierarchical (power spectrum inference): the s-draw takes its coefficients from band powers held in
-// every CTA's shared memory and sums the band statistics S_b, X_b of its column units into its own
-// shared accumulators. After the sweep's second cluster barrier every CTA adds the P CTAs' accumulators
-// in rank order and draws P_b = S_b / X_b, so all CTAs hold the same band powers. The accumulators
-// alternate between two sets by the parity of the sweep: the set summed in sweep k is reset only in sweep
-// k + 1, after that sweep's second barrier, when every other CTA has finished reading it (their reads
-// end before they arrive at the first barrier of sweep k + 1).
+// Hierarchical (power spectrum inference): the s-draw takes its coefficients from the band powers held
+// in every CTA's shared memory (as the per-band table band_coef(P_b)) and stores each new mode's
+// statistics (n |s_hat|^2 with its mirror weight, the squares of its stream-6 normals) at the mode's own
+// position of a bin-ordered buffer in global memory (one per cluster, L2-resident). After the sweep's
+// second cluster barrier CTA j sums its range of bins from that buffer (a warp per bin, lane-strided
+// partial sums then a fixed shuffle tree: the same order every run), draws P_b = S_b / X_b and writes
+// P_b and band_coef(P_b) into the shared memory of every CTA of the cluster (and P_b to out_P when the
+// sweep is kept). Those writes land before the next sweep's first barrier, and nobody reads the tables
+// between the second barrier and the next first one, so no further barrier is needed; the buffer is
+// rewritten only after the next first barrier, when every CTA has finished reading it.
 //
 // Spin-2 (shear): both shear components of a chain in one cluster, each CTA holding its rows of both,
 // and a column unit gathering the column spectra of both components so that the Kaiser-Squires rotation
@@ -22,13 +25,23 @@ namespace wf {
 // ---------------------------------------------------------------------------------------------
 // hierarchical sampler
 // ---------------------------------------------------------------------------------------------
-// shared bytes: rows, twiddles, band powers [n_bins], accumulators [2 sets][2][n_bins] (floats)
+// shared bytes: rows, twiddles, per-band s-draw coefficients [n_bins] (float2), band powers [n_bins]
 template <int N, int MR>
 __host__ __device__ constexpr int cband_smem(int n_bins) {
-  return CGeo<N, MR>::ROWS_BYTES + N * 8 + ((5 * n_bins * 4 + 15) / 16) * 16;
+  return CGeo<N, MR>::ROWS_BYTES + N * 8 + ((12 * n_bins + 15) / 16) * 16;
 }
 
-// one chain per cluster; a.fg and a.bins in slot order (ctab_index), a.aq with the CTA-contiguous rows
+// whether slot-order mode i is one the s-draw visits as itself (its statistics stored): every interior
+// mode, and on the packed edge column (kx = 0 in slot 0, kx = W/2 after the H L interior slots) the rows
+// ky <= H/2 (the rows above are the conjugates of those, counted through their mirror weight)
+// (H rows, L = W / 2 interior slots per row)
+__host__ __device__ inline bool cband_visited(int i, int H, int L) {
+  if (i >= H * L) return i - H * L <= H / 2;
+  return i % L != 0 || i / L <= H / 2;
+}
+
+// a.band_clusters clusters; cluster c runs chains c, c + band_clusters, ... (one statistics buffer each);
+// a.fg and a.band_map in slot order (ctab_index), a.aq with the CTA-contiguous rows
 template <int N, int MR>
 __global__ void __launch_bounds__(N / 2, csample_min_ctas<N, MR>()) k_csample_band(SampleArgs a) {
   using G = CGeo<N, MR>;
@@ -37,52 +50,65 @@ __global__ void __launch_bounds__(N / 2, csample_min_ctas<N, MR>()) k_csample_ba
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* rows = reinterpret_cast<float2*>(smem_raw);
   float2* tw = reinterpret_cast<float2*>(smem_raw + G::ROWS_BYTES);
-  float* Pb = reinterpret_cast<float*>(smem_raw + G::ROWS_BYTES + N * 8);
-  float* accs = Pb + a.n_bins;
+  float2* cb = reinterpret_cast<float2*>(smem_raw + G::ROWS_BYTES + N * 8);
+  float* Pb = reinterpret_cast<float*>(cb + a.n_bins);
   if (a.sc->status != 0) return;  // uniform over the grid
-  const long long ci = blockIdx.x / G::P;
   const int nb = a.n_bins, tid = threadIdx.x, b = int(cl.block_rank()), g = b * G::L + tid;
-  for (int i = tid; i < nb; i += G::L) {
-    Pb[i] = a.P0[i];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) accs[j * nb + i] = 0.0f;
-  }
-  ctw_init<N, MR>(tw);
-  crows_load<N, MR>(rows, b, a.init_s ? a.init_s + ci * a.init_stride : nullptr);
-  __syncthreads();
-  const uint32_t chain = a.chain0 + uint32_t(ci);
+  const int cid = blockIdx.x / G::P;
   const float tau = float(a.sc->tau);
   constexpr float NPIX = float(G::H * G::W);
-  float* out_P = a.out_P ? a.out_P + ci * a.n_samples * nb : nullptr;
-  const long long out_off = ci * a.n_samples * (long long)(G::H * G::W) * out_elem_bytes(a.out_dtype);
-  csweeps<N, MR, 1>(
-      cl, rows, tw, a.aq, a.sc->sqrt_tau, reinterpret_cast<char*>(a.out) + out_off,
-      a.out_dtype, a.n_sweeps, a.burn_in, a.thin, a.step0, chain, a.key0, a.key1,
-      [&](uint32_t step) {  // s-draw with P_k = P_b(k); statistics into this sweep's set
-        const CBandCoef cf{a.fg, a.bins, Pb, accs + (step & 1u) * 2 * nb, nb, tau, 1.0f / NPIX, NPIX};
-        ccol_draw<N, MR>(cl, rows, g, cf, step, chain, a.key0, a.key1);
-      },
-      [&](uint32_t step) {  // P_b | s from the cluster's sums; the other set reset for the next sweep
-        const float* cur = accs + (step & 1u) * 2 * nb;
-        float* nxt = accs + ((step + 1u) & 1u) * 2 * nb;
-        for (int i = tid; i < nb; i += G::L) {
-          float S = 0.0f, X = 0.0f;
+  float2* buf = a.band_buf + (long long)cid * (nb > 0 ? a.band_off[nb] : 0);
+  const int lo = a.band_lo[b], hi = a.band_lo[b + 1];
+  const int warp = tid / 32, lane = tid % 32;
+  ctw_init<N, MR>(tw);
+  for (long long ci = cid; ci < a.n_chains; ci += a.band_clusters) {
+    for (int i = tid; i < nb; i += G::L) {
+      Pb[i] = a.P0[i];
+      cb[i] = band_coef(a.P0[i], tau, 1.0f / NPIX);
+    }
+    crows_load<N, MR>(rows, b, a.init_s ? a.init_s + ci * a.init_stride : nullptr);
+    __syncthreads();
+    const uint32_t chain = a.chain0 + uint32_t(ci);
+    float* out_P = a.out_P ? a.out_P + ci * a.n_samples * nb : nullptr;
+    const long long out_off = ci * a.n_samples * (long long)(G::H * G::W) * out_elem_bytes(a.out_dtype);
+    csweeps<N, MR, 1>(
+        cl, rows, tw, a.aq, a.sc->sqrt_tau, reinterpret_cast<char*>(a.out) + out_off, a.out_dtype, a.n_sweeps,
+        a.burn_in, a.thin, a.step0, chain, a.key0, a.key1,
+        [&](uint32_t step, int) {  // s-draw with P_k = P_b(k); each mode's statistics to the buffer
+          ccol_draw<N, MR>(cl, rows, g, CBandCoef{a.fg, a.band_map, cb, buf, NPIX}, step, chain, a.key0, a.key1);
+        },
+        [&](uint32_t, int done) {  // P_b | s for this CTA's bins, to every CTA of the cluster
+          const int kept = done + 1 - a.burn_in;
+          const long long m = (kept > 0 && kept % a.thin == 0) ? kept / a.thin - 1 : -1;
+          for (int bb = lo + warp; bb < hi; bb += G::L / 32) {
+            const int o1 = a.band_off[bb + 1];
+            float S = 0.0f, X = 0.0f;
+            for (int j = a.band_off[bb] + lane; j < o1; j += 8 * 32) {  // eight loads in flight per lane
+              float2 v[8];
 #pragma unroll
-          for (int j = 0; j < G::P; ++j) {
-            const float* r = cl.map_shared_rank(cur, j);
-            S += r[i];
-            X += r[nb + i];
+              for (int u = 0; u < 8; ++u)
+                v[u] = j + 32 * u < o1 ? __ldcg(buf + j + 32 * u) : make_float2(0.0f, 0.0f);
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                S += v[u].x;
+                X += v[u].y;
+              }
+            }
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) {
+              S += __shfl_xor_sync(0xffffffffu, S, d);
+              X += __shfl_xor_sync(0xffffffffu, X, d);
+            }
+            const float P = X > 0.0f ? S / X : 0.0f;
+            if (lane < G::P) {
+              cl.map_shared_rank(Pb, lane)[bb] = P;
+              cl.map_shared_rank(cb, lane)[bb] = band_coef(P, tau, 1.0f / NPIX);
+            }
+            if (lane == 0 && out_P && m >= 0) out_P[m * nb + bb] = P;
           }
-          Pb[i] = X > 0.0f ? S / X : 0.0f;
-          nxt[i] = 0.0f;
-          nxt[nb + i] = 0.0f;
-        }
-      },
-      [&](long long m) {  // the band powers drawn in the kept sweep (every CTA holds them; CTA 0 writes)
-        if (out_P && b == 0)
-          for (int i = tid; i < nb; i += G::L) out_P[m * nb + i] = Pb[i];
-      });
-  cl.sync();  // no CTA leaves while another may still address its shared memory
+        });
+    cl.sync();  // the chain's last remote writes and reads are done before the next chain starts
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -217,14 +243,14 @@ __global__ void __launch_bounds__(N / 2, cspin2_min_ctas<N, MR>()) k_csample_spi
   csweeps<N, MR, 2>(
       cl, rows, tw, a.aq2, a.sc->sqrt_tau, reinterpret_cast<char*>(a.out) + ci * a.n_samples * 2 * NPIX * eb,
       a.out_dtype, a.n_sweeps, a.burn_in, a.thin, a.step0, chain, a.key0, a.key1,
-      [&](uint32_t step) {
+      [&](uint32_t step, int) {
         ccol_units2<N, MR>(cl, rows, g,
                            [&](int K, int t, float2& y1a, float2& y2a, float2& y1b, float2& y2b, int ky1, int ky2) {
                              cspin2_pair<N, MR>(y1a, y2a, y1b, y2b, K, t, ky1, ky2, a.fgE, a.fgB, step, chain,
                                                 a.key0, a.key1);
                            });
       },
-      [](uint32_t) {}, [](long long) {});
+      [](uint32_t, int) {});
   cl.sync();  // no CTA leaves while another may still address its shared memory
 }
 

@@ -465,10 +465,17 @@ struct SampleArgs {
   int n_bins;
   const float* P0;       // [n_bins] initial band powers
   float* out_P;          // [n_chains][n_samples][n_bins] or nullptr
+  // cluster form of the hierarchical sampler (k_csample_band) only
+  const int2* band_map;  // slot order: (bin, position in the bin-ordered statistics buffer or -1)
+  const int* band_off;   // [n_bins + 1] start of each bin in the statistics buffer
+  const int* band_lo;    // [CTAs per cluster + 1] bins summed by each CTA of a cluster
+  float2* band_buf;      // [band_clusters][band_off[n_bins]] statistics buffers, one per cluster
+  int band_clusters;     // clusters launched; each runs chains c, c + band_clusters, ...
 };
 
-// shared bytes per field of the hierarchical sampler: the two accumulators and the band powers
-WF_HD int band_bytes(int n_bins) { return ((n_bins * 12 + 15) / 16) * 16; }
+// shared bytes per field of the hierarchical sampler: the per-band s-draw coefficients (float2), the two
+// accumulators and the band powers (floats)
+WF_HD int band_bytes(int n_bins) { return ((n_bins * 20 + 15) / 16) * 16; }
 
 // CTAs per SM the sample kernel is compiled for (register budget 65536 / (threads * CTAs)):
 // 128^2 fields are limited to three per SM by shared memory (66.5 KB each).
@@ -675,13 +682,14 @@ struct BandCoef {
   const float2* __restrict__ fg;
   int wh;
   const int* __restrict__ bins;  // [H][W/2+1], -1: the table's coefficients
+  float2* cb;                    // shared [n_bins]: band_coef of each band power
   float* Pb;                     // shared [n_bins]
   float* acc;                    // shared [2][n_bins]: S_b then X_b
   int n_bins;
   float tau, inv_n, n;
   WF_HD float2 coef(int ky, int kx) const {
     const int b = WF_LDG(bins + ky * wh + kx);
-    return b < 0 ? WF_LDG(fg + ky * wh + kx) : band_coef(Pb[b], tau, inv_n);
+    return b < 0 ? WF_LDG(fg + ky * wh + kx) : cb[b];
   }
   WF_HD int bin(int ky, int kx) const { return WF_LDG(bins + ky * wh + kx); }
   WF_HD void flush(int b, float s2, float x2) const {
@@ -920,7 +928,9 @@ template <int N>
 WF_HD void band_update(const BandCoef& bc, int lt) {
   for (int b = lt; b < bc.n_bins; b += N) {
     const float S = bc.acc[b], X = bc.acc[bc.n_bins + b];
-    bc.Pb[b] = X > 0.0f ? S / X : 0.0f;
+    const float P = X > 0.0f ? S / X : 0.0f;
+    bc.Pb[b] = P;
+    bc.cb[b] = band_coef(P, bc.tau, bc.inv_n);
     bc.acc[b] = 0.0f;
     bc.acc[bc.n_bins + b] = 0.0f;
   }
@@ -1049,13 +1059,17 @@ __global__ void __launch_bounds__(N * FPC, sample_min_ctas<N>()) k_sample_band(S
   const bool active = ci < a.n_chains;
   float2* S = reinterpret_cast<float2*>(smem_raw + fld * G::FIELD_BYTES);
   unsigned char* band = smem_raw + FPC * G::FIELD_BYTES + fld * band_bytes(a.n_bins);
-  float* acc = reinterpret_cast<float*>(band);
+  float2* cb = reinterpret_cast<float2*>(band);
+  float* acc = reinterpret_cast<float*>(cb + a.n_bins);
   float* Pb = acc + 2 * a.n_bins;
   if (a.sc->status != 0) return;  // uniform over the grid
+  const float tau = float(a.sc->tau);
+  constexpr float NPIX = float(G::H * G::W);
   for (int b = lt; b < a.n_bins; b += N) {
     acc[b] = 0.0f;
     acc[a.n_bins + b] = 0.0f;
     Pb[b] = a.P0[b];
+    cb[b] = band_coef(a.P0[b], tau, 1.0f / NPIX);
   }
   __syncthreads();
   float2 c[G::LR];
@@ -1067,8 +1081,7 @@ __global__ void __launch_bounds__(N * FPC, sample_min_ctas<N>()) k_sample_band(S
 #pragma unroll
     for (int m = 0; m < G::LR; ++m) c[m] = make_float2(0.f, 0.f);
   }
-  const float tau = float(a.sc->tau);
-  const BandCoef cf{a.fg, G::WH, a.bins, Pb, acc, a.n_bins, tau, 1.0f / float(G::H * G::W), float(G::H * G::W)};
+  const BandCoef cf{a.fg, G::WH, a.bins, cb, Pb, acc, a.n_bins, tau, 1.0f / NPIX, NPIX};
   sample_sweeps<N>(S, lt, c, a.aq, cf, a.sc->sqrt_tau, a.step0, a.chain0 + uint32_t(ci), a.key0, a.key1,
                    a.n_sweeps, a.burn_in, a.thin,
                    reinterpret_cast<char*>(a.out) +

@@ -71,11 +71,15 @@ cudaError_t csample_clusters(int* clusters);
 template <int N, int MR>
 cudaError_t launch_cpipe(const CBArgs& a, cudaStream_t st, LaunchTimer* t);
 
-// cluster-resident hierarchical sampler (a.bins and a.fg in slot order; N / MR CTAs per chain) and
+// cluster-resident hierarchical sampler (a.band_clusters clusters of N / MR CTAs looping over the chains;
+// a.fg and a.band_map in slot order) and
 // spin-2 sampler (both components per cluster). cudaErrorNotSupported when no cluster of that shape
 // can be resident.
 template <int N, int MR>
 cudaError_t launch_csample_band(const SampleArgs& a, cudaStream_t st, LaunchTimer* t);
+// clusters of k_csample_band<N, MR> with n_bins bands that can be resident at once (0: none)
+template <int N, int MR>
+cudaError_t csample_band_clusters(int n_bins, int* clusters);
 template <int N, int MR>
 cudaError_t launch_csample_spin2(const Spin2Args& a, cudaStream_t st, LaunchTimer* t);
 
@@ -367,12 +371,24 @@ cudaError_t cluster_launch_config(Kern kern, int P, int threads, int smem, int c
   return resident > 0 ? cudaSuccess : cudaErrorNotSupported;
 }
 template <int N, int MR>
+cudaError_t csample_band_clusters(int n_bins, int* clusters) {
+  using G = CGeo<N, MR>;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  *clusters = 0;
+  cudaError_t e = cluster_launch_config(k_csample_band<N, MR>, G::P, G::L, cband_smem<N, MR>(n_bins), 1, nullptr,
+                                        &cfg, attr);
+  if (e == cudaErrorNotSupported) return cudaSuccess;
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveClusters(clusters, k_csample_band<N, MR>, &cfg);
+}
+template <int N, int MR>
 cudaError_t launch_csample_band(const SampleArgs& a, cudaStream_t st, LaunchTimer* t) {
   using G = CGeo<N, MR>;
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
-  cudaError_t e = cluster_launch_config(k_csample_band<N, MR>, G::P, G::L, cband_smem<N, MR>(a.n_bins), a.n_chains,
-                                        st, &cfg, attr);
+  cudaError_t e = cluster_launch_config(k_csample_band<N, MR>, G::P, G::L, cband_smem<N, MR>(a.n_bins),
+                                        a.band_clusters, st, &cfg, attr);
   if (e != cudaSuccess) return e;
   if (t) t->start();
   e = cudaLaunchKernelEx(&cfg, k_csample_band<N, MR>, a);
@@ -392,8 +408,9 @@ cudaError_t launch_csample_spin2(const Spin2Args& a, cudaStream_t st, LaunchTime
   if (t) t->stop();
   return e != cudaSuccess ? e : cudaGetLastError();
 }
-#define WF_INSTANTIATE_CLUSTER_BAND(N, MR) \
-  template cudaError_t launch_csample_band<N, MR>(const SampleArgs&, cudaStream_t, LaunchTimer*);
+#define WF_INSTANTIATE_CLUSTER_BAND(N, MR)                                                      \
+  template cudaError_t launch_csample_band<N, MR>(const SampleArgs&, cudaStream_t, LaunchTimer*); \
+  template cudaError_t csample_band_clusters<N, MR>(int, int*);
 #define WF_INSTANTIATE_CLUSTER_SPIN2(N, MR) \
   template cudaError_t launch_csample_spin2<N, MR>(const Spin2Args&, cudaStream_t, LaunchTimer*);
 #endif

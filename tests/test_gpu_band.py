@@ -102,3 +102,21 @@ def test_band_sampler_large_thin_resume_and_fixed_bins():
     with pytest.raises(wf.WFError) as e:  # more bins than the 256^2 kernel holds
         wf.wf_sample_band(*dev, bd, torch.full((257,), 0.5, device="cuda"), seed=1, n_samples=1)
     assert e.value.status == 1
+
+
+def test_band_sampler_large_chains_loop_and_repeat_exactly():
+    """256^2 with more chains than clusters can be resident (each cluster runs several chains in turn):
+    chains early and late in the loop follow the oracle, and the band sums, taken in a fixed order, make a
+    repeated call bit-identical."""
+    H, chains = 256, 300
+    p = synth.make_problem(H, seed=21, mask_frac=0.1, slope=-2.0, k0=1.0 / 32, sigma2=(0.05, 0.5))
+    dev = to_dev(p)
+    bins, nb = HG.radial_bins(H, H)
+    bd, P0 = torch.from_numpy(bins).cuda(), torch.full((nb,), 0.5, device="cuda")
+    xs, Ps = wf.wf_sample_band(*dev, bd, P0, seed=12, n_samples=1, n_chains=chains, burn_in=1)
+    xs2, Ps2 = wf.wf_sample_band(*dev, bd, P0, seed=12, n_samples=1, n_chains=chains, burn_in=1)
+    assert torch.equal(xs, xs2) and torch.equal(Ps, Ps2)
+    for c in (0, 151, chains - 1):
+        rs, rP = HG.sample(p.d, p.Ndiag, p.mask, p.Pk, bins, P0.cpu().numpy(), 1, seed=12, chain=c, burn_in=1)
+        assert rel(xs[c, 0].cpu().numpy(), rs[0]) < SAMPLE_TOL, (c, rel(xs[c, 0].cpu().numpy(), rs[0]))
+        assert rel(Ps[c, 0].cpu().numpy(), rP[0]) < SAMPLE_TOL, c
