@@ -544,18 +544,19 @@ constexpr int csample_min_ctas() { return CGeo<N, MR>::L <= 128 ? 3 : (CGeo<N, M
 // twiddles exp(-2 pi i j / N) (FP64, rounded once) into shared memory
 template <int N, int MR>
 __device__ __forceinline__ void ctw_init(float2* tw) {
-  for (int j = threadIdx.x; j < N; j += CGeo<N, MR>::L) {
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
     double sn, cs;
     sincospi(-2.0 * double(j) / double(N), &sn, &cs);
     tw[j] = make_float2(float(cs), float(sn));
   }
 }
 
-// this CTA's rows of a row-major [H][W] image into the staged rows (nullptr: zero)
+// this CTA's rows of a row-major [H][W] image into the staged rows (nullptr: zero), by the L threads
+// lt = 0 .. L-1
 template <int N, int MR>
-__device__ __forceinline__ void crows_load(float2* rows, int b, const float* src) {
+__device__ __forceinline__ void crows_load(float2* rows, int b, const float* src, int lt = threadIdx.x) {
   using G = CGeo<N, MR>;
-  for (int e = threadIdx.x; e < G::A * G::L; e += G::L) {
+  for (int e = lt; e < G::A * G::L; e += G::L) {
     const int ar = e / G::L, i = e % G::L;
     float2 v = make_float2(0.f, 0.f);
     if (src != nullptr) v = WF_LDG(reinterpret_cast<const float2*>(src + (long long)(G::P * ar + b) * G::W) + i);
@@ -563,11 +564,11 @@ __device__ __forceinline__ void crows_load(float2* rows, int b, const float* src
   }
 }
 
-// the staged rows to this CTA's rows of an image of element type t
+// the staged rows to this CTA's rows of an image of element type t, by the L threads lt = 0 .. L-1
 template <int N, int MR>
-__device__ __forceinline__ void crows_store(const float2* rows, int b, void* dst, int t) {
+__device__ __forceinline__ void crows_store(const float2* rows, int b, void* dst, int t, int lt = threadIdx.x) {
   using G = CGeo<N, MR>;
-  for (int e = threadIdx.x; e < G::A * G::L; e += G::L) {
+  for (int e = lt; e < G::A * G::L; e += G::L) {
     const int r2 = e / G::L, i = e % G::L;
     store_pair(dst, (long long)(G::P * r2 + b) * G::L + i, rows[r2 * G::SP + i], t);
   }
@@ -575,29 +576,34 @@ __device__ __forceinline__ void crows_store(const float2* rows, int b, void* dst
 
 // Sampler sweeps (Alg. 1) of one chain by its cluster from the staged rows (the current s) of NC fields
 // (NC = 2: the two shear components, field c's rows at rows + c A SP, its pixel table at aq + c H W, its
-// t-draw from Philox stream 8 c). Per sweep (done = the sweeps before it in this call, step = step0 +
-// done): t-draws and forward transforms, then col(step, done) between the two cluster barriers (the column
-// spectra complete: the s-draw), post(step, done) right after the second (every CTA's column work done),
-// the inverse transforms. Sample m (the state after sweep burn_in + (m + 1) thin) goes to
-// out + (m NC + c) H W elements of type out_dtype.
-template <int N, int MR, int NC, class Col, class Post>
+// t-draw from Philox stream 8 c). With SPLIT (NC = 2, 2 L threads) threads c L .. c L + L - 1 run field
+// c's row and column passes; otherwise each of the L threads runs them for every field in turn. Per sweep
+// (done = the sweeps before it in this call, step = step0 + done): t-draws and forward transforms, then
+// col(step, done) between the two cluster barriers (the column spectra complete: the s-draw),
+// post(step, done) right after the second (every CTA's column work done), the inverse transforms. Sample
+// m (the state after sweep burn_in + (m + 1) thin) goes to out + (m NC + c) H W elements of type out_dtype.
+template <int N, int MR, int NC, bool SPLIT, class Col, class Post>
 __device__ __forceinline__ void csweeps(cooperative_groups::cluster_group& cl, float2* rows, const float2* tw,
                                         const float2* __restrict__ aq, float sqrt_tau, void* out_v, int out_dtype,
                                         int n_sweeps, int burn_in, int thin, uint32_t step0, uint32_t chain,
                                         uint32_t k0, uint32_t k1, Col&& col, Post&& post) {
   using G = CGeo<N, MR>;
+  static_assert(!SPLIT || NC == 2, "split threads: one field per half of the CTA");
   constexpr int CS = G::A * G::SP;
+  constexpr int C0N = SPLIT ? 1 : NC;  // fields per thread
   constexpr long long NPIX = (long long)G::H * G::W;
-  const int tid = threadIdx.x, b = int(cl.block_rank());
+  const int lt = SPLIT ? int(threadIdx.x) % G::L : int(threadIdx.x), b = int(cl.block_rank());
+  const int cf = SPLIT ? int(threadIdx.x) / G::L : 0;  // the thread's first field
   int ar, h;
-  crow_of<N, MR>(tid, ar, h);
+  crow_of<N, MR>(lt, ar, h);
   const int y = G::P * ar + b;
   const int eb = out_elem_bytes(out_dtype);
   char* out = reinterpret_cast<char*>(out_v);
   for (int done = 0;;) {
     const uint32_t step = step0 + uint32_t(done);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
+    for (int k = 0; k < C0N; ++k) {
+      const int c = cf + k;
       float2* row = rows + c * CS + ar * G::SP;
       ct_draw<N, MR>(row, y, b * G::M + ar, h, aq + c * NPIX, sqrt_tau, step, chain, k0, k1, 8u * uint32_t(c));
       __syncwarp();
@@ -605,23 +611,23 @@ __device__ __forceinline__ void csweeps(cooperative_groups::cluster_group& cl, f
     }
     __syncthreads();
 #pragma unroll
-    for (int c = 0; c < NC; ++c) ccol_fwd<N, MR>(rows + c * CS, tid, b, tw);
+    for (int k = 0; k < C0N; ++k) ccol_fwd<N, MR>(rows + (cf + k) * CS, lt, b, tw);
     cl.sync();  // every CTA's partial column transforms are in place
     col(step, done);
     cl.sync();  // every unit's inverse stage has landed
     post(step, done);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) ccol_inv<N, MR>(rows + c * CS, tid, b, tw);
+    for (int k = 0; k < C0N; ++k) ccol_inv<N, MR>(rows + (cf + k) * CS, lt, b, tw);
     __syncthreads();
 #pragma unroll
-    for (int c = 0; c < NC; ++c) crow_inv<N, MR>(rows + c * CS + ar * G::SP, h, tw);
+    for (int k = 0; k < C0N; ++k) crow_inv<N, MR>(rows + (cf + k) * CS + ar * G::SP, h, tw);
     ++done;
     if (done > burn_in && (done - burn_in) % thin == 0) {
       const long long m = (done - burn_in) / thin - 1;
       __syncthreads();
 #pragma unroll
-      for (int c = 0; c < NC; ++c)
-        crows_store<N, MR>(rows + c * CS, b, out + (m * NC + c) * NPIX * eb, out_dtype);
+      for (int k = 0; k < C0N; ++k)
+        crows_store<N, MR>(rows + (cf + k) * CS, b, out + (m * NC + cf + k) * NPIX * eb, out_dtype, lt);
       __syncthreads();
     }
     if (done == n_sweeps) break;
@@ -637,7 +643,7 @@ __device__ __forceinline__ void csample_loop(cooperative_groups::cluster_group& 
                                              int thin, uint32_t step0, uint32_t chain, uint32_t k0, uint32_t k1) {
   using G = CGeo<N, MR>;
   const int g = int(cl.block_rank()) * G::L + int(threadIdx.x);
-  csweeps<N, MR, 1>(
+  csweeps<N, MR, 1, false>(
       cl, rows, tw, aq, sqrt_tau, out_v, out_dtype, n_sweeps, burn_in, thin, step0, chain, k0, k1,
       [&](uint32_t step, int) { ccol_draw<N, MR>(cl, rows, g, CTabCoef{fg}, step, chain, k0, k1); },
       [](uint32_t, int) {});

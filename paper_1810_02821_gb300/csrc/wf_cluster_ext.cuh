@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(N / 2, csample_min_ctas<N, MR>()) k_csample_ba
     const uint32_t chain = a.chain0 + uint32_t(ci);
     float* out_P = a.out_P ? a.out_P + ci * a.n_samples * nb : nullptr;
     const long long out_off = ci * a.n_samples * (long long)(G::H * G::W) * out_elem_bytes(a.out_dtype);
-    csweeps<N, MR, 1>(
+    csweeps<N, MR, 1, false>(
         cl, rows, tw, a.aq, a.sc->sqrt_tau, reinterpret_cast<char*>(a.out) + out_off, a.out_dtype, a.n_sweeps,
         a.burn_in, a.thin, a.step0, chain, a.key0, a.key1,
         [&](uint32_t step, int) {  // s-draw with P_k = P_b(k); each mode's statistics to the buffer
@@ -117,8 +117,18 @@ __global__ void __launch_bounds__(N / 2, csample_min_ctas<N, MR>()) k_csample_ba
 // shared bytes: the rows of both components, twiddles
 template <int N, int MR>
 __host__ __device__ constexpr int cspin2_smem() { return 2 * CGeo<N, MR>::ROWS_BYTES + N * 8; }
+// threads per CTA: 2 L (one component's row and column passes per half) where the column units then
+// still come out whole per thread (256^2: 8-CTA clusters of 256 threads, 2 per SM), else L (each thread
+// both components; 512^2: 16-CTA clusters of 256 threads, 1 per SM)
 template <int N, int MR>
-constexpr int cspin2_min_ctas() { return cspin2_smem<N, MR>() <= 72 * 1024 ? 3 : 1; }
+__host__ __device__ constexpr bool cspin2_split() {
+  using G = CGeo<N, MR>;
+  return (G::L * (G::M / 2)) % (G::P * 2 * G::L) == 0 && 2 * G::ROWS_BYTES + N * 8 <= 110 * 1024;
+}
+template <int N, int MR>
+__host__ __device__ constexpr int cspin2_threads() { return cspin2_split<N, MR>() ? 2 * CGeo<N, MR>::L : CGeo<N, MR>::L; }
+template <int N, int MR>
+__host__ __device__ constexpr int cspin2_min_ctas() { return cspin2_split<N, MR>() ? 2 : 1; }
 
 // The spin-2 s-draw of one mode pair (ky1, ky2) of packed column slot t (kx = K) on both components
 // (y1a, y2a: component 1; y1b, y2b: component 2): per mode, rotation by (c, s) = (cos 2 phi, sin 2 phi)
@@ -173,14 +183,15 @@ __device__ __forceinline__ void cspin2_pair(float2& y1a, float2& y2a, float2& y1
 }
 
 // The cross-cluster radix-P stage of ccol_units on both components at once (component c's rows at
-// rows + c A SP): the same work units and mode pairs, fn(K, t, y1a, y2a, y1b, y2b, ky1, ky2) receiving
+// rows + c A SP), shared out to the T threads of each CTA (g = the thread's index in the cluster): the
+// same work units and mode pairs, fn(K, t, y1a, y2a, y1b, y2b, ky1, ky2) receiving
 // the pair's values of both components, then the inverse stage scattered back for both.
-template <int N, int MR, class F>
+template <int N, int MR, int T, class F>
 __device__ __forceinline__ void ccol_units2(cooperative_groups::cluster_group& cl, float2* rows, int g, F&& fn) {
   using G = CGeo<N, MR>;
   constexpr int P = G::P, L = G::L, R = G::R, M = G::M, CS = G::A * G::SP;
-  static_assert((L * (M / 2)) % (P * L) == 0, "equal work units per thread");
-  for (int w = g; w < L * (M / 2); w += P * L) {
+  static_assert((L * (M / 2)) % (P * T) == 0, "equal work units per thread");
+  for (int w = g; w < L * (M / 2); w += P * T) {
     const int t = w % L, u = w / L, v = u == 0 ? M / 2 : M - u;
     const int K = (t % R) * M + t / R;  // kx held by slot t
     float2 p[2][P], q[2][P];
@@ -222,8 +233,10 @@ __device__ __forceinline__ void ccol_units2(cooperative_groups::cluster_group& c
 // one chain (both components) per cluster; a.aq2 [2] pixel tables with the CTA-contiguous rows, a.fgE and
 // a.fgB in slot order; out [n_chains][n_samples][2][H][W]
 template <int N, int MR>
-__global__ void __launch_bounds__(N / 2, cspin2_min_ctas<N, MR>()) k_csample_spin2(Spin2Args a) {
+__global__ void __launch_bounds__(cspin2_threads<N, MR>(), cspin2_min_ctas<N, MR>()) k_csample_spin2(Spin2Args a) {
   using G = CGeo<N, MR>;
+  constexpr bool SPLIT = cspin2_split<N, MR>();
+  constexpr int T = cspin2_threads<N, MR>();
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -232,19 +245,22 @@ __global__ void __launch_bounds__(N / 2, cspin2_min_ctas<N, MR>()) k_csample_spi
   if (a.sc->status != 0) return;  // uniform over the grid
   const long long ci = blockIdx.x / G::P;
   constexpr long long NPIX = (long long)G::H * G::W;
-  const int b = int(cl.block_rank()), g = b * G::L + int(threadIdx.x);
+  const int b = int(cl.block_rank()), g = b * T + int(threadIdx.x);
   ctw_init<N, MR>(tw);
 #pragma unroll
-  for (int c = 0; c < 2; ++c)
-    crows_load<N, MR>(rows + c * G::A * G::SP, b, a.init_s ? a.init_s + ci * a.init_stride + c * NPIX : nullptr);
+  for (int c = 0; c < 2; ++c) {
+    if (SPLIT && int(threadIdx.x) / G::L != c) continue;
+    crows_load<N, MR>(rows + c * G::A * G::SP, b, a.init_s ? a.init_s + ci * a.init_stride + c * NPIX : nullptr,
+                      int(threadIdx.x) % G::L);
+  }
   __syncthreads();
   const uint32_t chain = a.chain0 + uint32_t(ci);
   const int eb = out_elem_bytes(a.out_dtype);
-  csweeps<N, MR, 2>(
+  csweeps<N, MR, 2, SPLIT>(
       cl, rows, tw, a.aq2, a.sc->sqrt_tau, reinterpret_cast<char*>(a.out) + ci * a.n_samples * 2 * NPIX * eb,
       a.out_dtype, a.n_sweeps, a.burn_in, a.thin, a.step0, chain, a.key0, a.key1,
       [&](uint32_t step, int) {
-        ccol_units2<N, MR>(cl, rows, g,
+        ccol_units2<N, MR, T>(cl, rows, g,
                            [&](int K, int t, float2& y1a, float2& y2a, float2& y1b, float2& y2b, int ky1, int ky2) {
                              cspin2_pair<N, MR>(y1a, y2a, y1b, y2b, K, t, ky1, ky2, a.fgE, a.fgB, step, chain,
                                                 a.key0, a.key1);

@@ -401,7 +401,8 @@ cudaError_t launch_csample_spin2(const Spin2Args& a, cudaStream_t st, LaunchTime
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
   cudaError_t e =
-      cluster_launch_config(k_csample_spin2<N, MR>, G::P, G::L, cspin2_smem<N, MR>(), a.n_chains, st, &cfg, attr);
+      cluster_launch_config(k_csample_spin2<N, MR>, G::P, cspin2_threads<N, MR>(), cspin2_smem<N, MR>(), a.n_chains,
+                            st, &cfg, attr);
   if (e != cudaSuccess) return e;
   if (t) t->start();
   e = cudaLaunchKernelEx(&cfg, k_csample_spin2<N, MR>, a);
