@@ -120,6 +120,31 @@ def wiener_messenger(d1, d2, N1, N2, mask, PE, PB, n_iter: int, tau: float | Non
     return g1, g2
 
 
+def apply_covariance(v1, v2, PE, PB):
+    """S v for a shear pair v: rotation of (v1_hat, v2_hat) into E and B, multiplication by P_E and P_B
+    (unitary DFT), rotation back."""
+    H, W = np.asarray(v1).shape
+    PEf, PBf = _spectra(PE, PB, W)
+    c, s = ks_rotation(H, W)
+    a, b = dft.dft2(np.asarray(v1, np.float64)), dft.dft2(np.asarray(v2, np.float64))
+    e, q = PEf * (c * a + s * b), PBf * (-s * a + c * b)
+    return dft.idft2(c * e - s * q).real, dft.idft2(s * e + c * q).real
+
+
+def residual(g1, g2, d1, d2, N1, N2, mask, PE, PB) -> float:
+    """Relative residual of a shear map g in the Wiener-filter system multiplied through by S (Eq. 2-3):
+    ||g + S N^-1 (g - d)|| / ||S N^-1 d||, N^-1 = 0 on masked pixels, norms over both components."""
+    obs = np.asarray(mask) == 0
+    inv1 = np.where(obs, 1.0 / np.where(obs, np.asarray(N1, np.float64), 1.0), 0.0)
+    inv2 = np.where(obs, 1.0 / np.where(obs, np.asarray(N2, np.float64), 1.0), 0.0)
+    g1, g2 = np.asarray(g1, np.float64), np.asarray(g2, np.float64)
+    d1, d2 = np.asarray(d1, np.float64), np.asarray(d2, np.float64)
+    r1, r2 = apply_covariance(inv1 * (g1 - d1), inv2 * (g2 - d2), PE, PB)
+    b1, b2 = apply_covariance(inv1 * d1, inv2 * d2, PE, PB)
+    num = np.sqrt(np.sum((g1 + r1) ** 2) + np.sum((g2 + r2) ** 2))
+    return float(num / np.sqrt(np.sum(b1 ** 2) + np.sum(b2 ** 2)))
+
+
 def dense_covariance(PE, PB, H: int, W: int) -> np.ndarray:
     """Shear covariance [2n][2n] (component-major) of the E/B model, by dense algebra."""
     U = np.kron(dft.dft_matrix(H), dft.dft_matrix(W))

@@ -1103,10 +1103,11 @@ wf_status wf_sample_spin2(const float* d1, const float* d2, const float* N1, con
 namespace {
 // Wiener-filter tables of one shear component at level lambda for the spin-2 sweep: aq = ((1 - w) d, sqrt w)
 // with w = N_bar / (N_bar + lambda tau), N_bar = N - tau (missing pixels: w = 1); fg = (f / n, 0) with
-// f = P / (P + lambda tau) (no draws)
+// f = P / (P + lambda tau) (no draws). perm, cm: the cluster kernels' table orders (k_tables), 0: natural.
 __global__ void k_s2_level_tables(const float* __restrict__ d, const float* __restrict__ Nd,
                                   const uint8_t* __restrict__ mask, const float* __restrict__ Pk, int H, int W,
-                                  const wf::Scalars* __restrict__ sc, double lam, float2* aq, float2* fg) {
+                                  const wf::Scalars* __restrict__ sc, double lam, float2* aq, float2* fg, int perm,
+                                  int cm) {
   const int n = H * W, nm = H * (W / 2 + 1);
   const double tau = sc->tau, lt = lam * tau;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + nm; i += gridDim.x * blockDim.x) {
@@ -1118,11 +1119,11 @@ __global__ void k_s2_level_tables(const float* __restrict__ d, const float* __re
         w = nb / (nb + lt);
         a = (1.0 - w) * double(d[i]);
       }
-      aq[x * H + y] = make_float2(float(a), float(sqrt(w)));
+      aq[x * H + table_row(y, H, perm)] = make_float2(float(a), float(sqrt(w)));
     } else {
       const int j = i - n;
       const double P = double(Pk[j]);
-      fg[j] = make_float2(P > 0.0 ? float(P / (P + lt) / double(n)) : 0.0f, 0.0f);
+      fg[mode_pos(j, H, W, cm)] = make_float2(P > 0.0 ? float(P / (P + lt) / double(n)) : 0.0f, 0.0f);
     }
   }
 }
@@ -1143,8 +1144,7 @@ wf_status wf_solve_spin2(const float* d1, const float* d2, const float* N1, cons
   wf_solve_opts_default(&o);
   if (opts) o = *opts;
   if (!d1 || !d2 || !N1 || !N2 || !mask || !PE || !PB || !out) return WF_ERR_ARG;
-  if (!size_ok(H, W)) return WF_ERR_SHAPE;
-  if (!size_on_chip(H)) return WF_ERR_SHAPE;
+  if (!size_ok(H, W) || H > 512) return WF_ERR_SHAPE;
   if (!(o.tol > 0.0) || !(o.eta > 0.0 && o.eta < 1.0) || o.level_max < 1 || o.check < 1 || o.max_iter < 1)
     return WF_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -1183,9 +1183,11 @@ wf_status wf_solve_spin2(const float* d1, const float* d2, const float* N1, cons
   wf::Spin2Args a{};
   a.aq2 = aq; a.fgE = fgE; a.fgB = fgB; a.sc = sc + 2; a.init_s = out; a.init_stride = 0;
   a.out = out; a.n_samples = 1; a.n_chains = 1; a.burn_in = 0; a.thin = 1; a.out_dtype = 0;
+  const int cm = size_on_chip(H) ? 0 : 32, perm = cm ? H / cm : 0;  // 256, 512: the cluster sampler's orders
   auto run = [&](double lam, int sweeps) -> wf_status {
-    k_s2_level_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d1, N1, mask, PE, H, W, sc, lam, aq, fgE);
-    k_s2_level_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d2, N2, mask, PB, H, W, sc, lam, aq + n, fgB);
+    k_s2_level_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d1, N1, mask, PE, H, W, sc, lam, aq, fgE, perm, cm);
+    k_s2_level_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d2, N2, mask, PB, H, W, sc, lam, aq + n, fgB, perm,
+                                                                 cm);
     WF_CUDA(cudaGetLastError());
     a.n_sweeps = sweeps;
     a.thin = sweeps;  // the state after the last sweep is the only sample
@@ -1195,6 +1197,8 @@ wf_status wf_solve_spin2(const float* d1, const float* d2, const float* N1, cons
       case 32: e2 = wf::launch_sample_spin2<32>(a, st, nullptr); break;
       case 64: e2 = wf::launch_sample_spin2<64>(a, st, nullptr); break;
       case 128: e2 = wf::launch_sample_spin2<128>(a, st, nullptr); break;
+      case 256: e2 = wf::launch_csample_spin2<256, 32>(a, st, nullptr); break;
+      case 512: e2 = wf::launch_csample_spin2<512, 32>(a, st, nullptr); break;
     }
     if (e2 != cudaSuccess) return cuda_fail(e2);
     return WF_OK;

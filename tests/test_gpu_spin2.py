@@ -77,6 +77,19 @@ def test_spin2_sampler_large_resume_and_zero_b_power():
         assert np.linalg.norm(k[i, 1]) < 1e-5 * np.linalg.norm(k[i, 0])
 
 
+@pytest.mark.parametrize("H", [256, 512])
+def test_spin2_wiener_filter_large_true_residual(H):
+    """256^2 and 512^2 (cluster kernels): the oracle's FP64 residual of the returned pair is below tol and
+    equals the reported one."""
+    p, d2, N2, PB = _pair(H, H + 7)
+    r = wf.wf_solve_spin2(*_dev(p.d, d2, p.Ndiag, N2, p.mask, p.Pk, PB), tol=WF_TOL)
+    got = r.s.cpu().numpy()
+    true = S2.residual(got[0], got[1], p.d, d2, p.Ndiag, N2, p.mask, p.Pk, PB)
+    print(f"spin-2 WF {H}: resid {r.resid:.3e} oracle {true:.3e} sweeps {r.iters}")
+    assert r.status == 0 and r.resid < WF_TOL and true < WF_TOL
+    assert abs(true - r.resid) <= 1e-6 * true
+
+
 def test_shear_to_convergence_matches_oracle():
     rng = np.random.default_rng(3)
     for H in (16, 128, 256):
