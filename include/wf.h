@@ -169,9 +169,9 @@ wf_status wf_sample_ex(const float* d, const float* Ndiag, const uint8_t* mask, 
  * 512: one thread-block cluster per chain, the cluster sampler of wf_sample_ex with the band draw added;
  * WF_ERR_CUDA with cudaErrorNotSupported where the device cannot host such a cluster);
  * 0 <= n_bins <= 256 (512 at 512 x 512). A bin outside [-1, n_bins) or a negative or non-finite P0:
- * WF_ERR_ARG. The band sums S_b and X_b are FP32 sums: up to 128 x 128 in a varying order (band powers,
- * and the chain after them, repeat from run to run to FP32 rounding), at 256 and 512 in a fixed order
- * (a repeated call is bit-identical).
+ * WF_ERR_ARG. The band sums S_b and X_b are FP32 sums in a fixed order, so a repeated call is
+ * bit-identical. Scratch: one statistics buffer of 8 bytes per half-spectrum mode for every chain (up to
+ * 128 x 128) or for every resident cluster (256 and 512), allocated per call on `stream`.
  */
 wf_status wf_sample_band(const float* d, const float* Ndiag, const uint8_t* mask, const float* Pk, const int32_t* bins,
                          int32_t n_bins, const float* P0, int32_t H, int32_t W, uint64_t seed,

@@ -870,18 +870,21 @@ __global__ void k_check_band(const int32_t* __restrict__ bins, int nm, int n_bin
   if (bad && sc->status == 0) sc->status = WF_ERR_ARG;
 }
 
-// Plan of the cluster hierarchical sampler's band sums. bmap (column slot order of the cluster kernels with
-// cm rows per CTA, mode_pos) = (bin, position): the modes the s-draw visits (cband_visited) with a bin get
-// consecutive positions per bin, bins in order and modes in slot order within a bin (so the sums run in
-// the same order every call); off[b] = first position of bin b; lo[j] = first bin summed by CTA j of a
-// cluster of P (contiguous ranges of about equal mode counts).
+// Plan of the hierarchical sampler's band sums. bmap, in the order of the mode tables (natural for cm = 0,
+// else the column slot order of the cluster kernels with cm rows per CTA, mode_pos) = (bin, position):
+// the modes the s-draw visits as themselves (every interior mode, and on the columns kx = 0 and W/2 the
+// rows ky <= H/2, whose conjugates count through their mirror weight) with a bin get consecutive
+// positions per bin, bins in order and modes in table order within a bin (so the sums run in the same
+// order every call); the others get position -2. off[b] = first position of bin b; lo[j] = first bin
+// summed by CTA j of a cluster of P (contiguous ranges of about equal mode counts).
 __global__ void k_band_map(const int32_t* __restrict__ bins, int H, int W, int cm, int n_bins, int2* __restrict__ bmap,
                            int* __restrict__ cnt) {
-  const int nm = H * (W / 2 + 1), L = W / 2;
+  const int WH = W / 2 + 1, nm = H * WH;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nm; j += gridDim.x * blockDim.x) {
-    const int q = mode_pos(j, H, W, cm), b = bins[j];
-    bmap[q] = make_int2(b, -1);
-    if (b >= 0 && b < n_bins && wf::cband_visited(q, H, L)) atomicAdd(cnt + b, 1);
+    const int ky = j / WH, kx = j % WH, b = bins[j];
+    const bool counted = b >= 0 && b < n_bins && ((kx != 0 && kx != W / 2) || ky <= H / 2);
+    bmap[mode_pos(j, H, W, cm)] = make_int2(b, counted ? -1 : -2);
+    if (counted) atomicAdd(cnt + b, 1);
   }
 }
 __global__ void k_band_offsets(const int* __restrict__ cnt, int n_bins, int P, int* __restrict__ off,
@@ -901,15 +904,19 @@ __global__ void k_band_offsets(const int* __restrict__ cnt, int n_bins, int P, i
   }
   lo[P] = n_bins;
 }
-// one block per bin: the bin's visited modes in slot order get positions off[b], off[b] + 1, ...
-__global__ void k_band_positions(int H, int W, const int* __restrict__ off, int2* __restrict__ bmap) {
+// one block per bin: the bin's counted modes in table order get positions off[b], off[b] + 1, ...
+__global__ void k_band_positions(int nm, const int* __restrict__ off, int2* __restrict__ bmap) {
   __shared__ int wsum[8];
-  const int b = blockIdx.x, nm = H * (W / 2 + 1), L = W / 2;
+  const int b = blockIdx.x;
   const int w = threadIdx.x / 32, l = threadIdx.x % 32;
   int base = off[b];
   for (int c = 0; c < nm; c += 256) {
     const int i = c + int(threadIdx.x);
-    const bool f = i < nm && bmap[i].x == b && wf::cband_visited(i, H, L);
+    bool f = false;
+    if (i < nm) {
+      const int2 e = bmap[i];
+      f = e.x == b && e.y == -1;
+    }
     const unsigned bal = __ballot_sync(0xffffffffu, f);
     if (l == 0) wsum[w] = __popc(bal);
     __syncthreads();
@@ -952,21 +959,26 @@ wf_status wf_sample_band(const float* d, const float* Ndiag, const uint8_t* mask
   if (sweeps > 0x7fffffffLL || o.n_samples > 0x7fffffffLL) return WF_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const size_t n = size_t(H) * W, nm = size_t(H) * (W / 2 + 1);
-  // 256 and 512: thread-block clusters (as many as can be resident, each looping over chains), tables in
-  // the cluster kernels' orders, the band-sum plan and one statistics buffer per cluster
+  // the band-sum plan, and one statistics buffer per field of the grid (up to 128^2) or per cluster (256
+  // and 512: thread-block clusters, as many as can be resident, each looping over chains, with tables in
+  // the cluster kernels' orders)
   const bool cluster = !size_on_chip(H);
-  const int cm = cluster ? wf::cluster_rows(H) : 0, perm = cluster ? H / cm : 0;
+  const int cm = cluster ? wf::cluster_rows(H) : 0, perm = cluster ? H / cm : 1;
+  long long n_buf = 0;
   int n_cl = 0;
   if (cluster) {
     WF_CUDA(band_clusters_any(H, n_bins, &n_cl));
     if (n_cl < 1) return cuda_fail(cudaErrorNotSupported);
     if (n_cl > o.n_chains) n_cl = o.n_chains;
+    n_buf = n_cl;
+  } else {
+    const int fpc = H >= 128 ? 1 : 128 / H;  // fields per CTA of k_sample_band
+    n_buf = (o.n_chains + fpc - 1) / fpc * (long long)fpc;
   }
   Carve cv;
   const size_t off_sc = cv.take<wf::Scalars>(1), off_aq = cv.take<float2>(n), off_fg = cv.take<float2>(nm),
-               off_map = cv.take<int2>(cluster ? nm : 0), off_cnt = cv.take<int>(cluster ? n_bins + 1 : 0),
-               off_off = cv.take<int>(cluster ? n_bins + 1 : 0), off_lo = cv.take<int>(cluster ? perm + 1 : 0),
-               off_buf = cv.take<float2>(cluster ? size_t(n_cl) * nm : 0);
+               off_map = cv.take<int2>(nm), off_cnt = cv.take<int>(n_bins + 1), off_off = cv.take<int>(n_bins + 1),
+               off_lo = cv.take<int>(perm + 1), off_buf = cv.take<float2>(size_t(n_buf) * nm);
   Scratch scr;
   scr.st = st;
   WF_CUDA(cudaMallocAsync(&scr.base, cv.off, st));
@@ -980,17 +992,17 @@ wf_status wf_sample_band(const float* d, const float* Ndiag, const uint8_t* mask
   WF_CUDA(cudaGetLastError());
   k_tables<<<int((n + nm + 255) / 256), 256, 0, st>>>(d, Ndiag, mask, Pk, H, W, sc, aq, nullptr, fg, perm, cm);
   WF_CUDA(cudaGetLastError());
+  // the plan (built before k_check_band's status is read: invalid bins are never counted, and the
+  // sampler does not run when that status is set)
   int2* bmap = reinterpret_cast<int2*>(b + off_map);
   int* band_off = reinterpret_cast<int*>(b + off_off);
   int* band_lo = reinterpret_cast<int*>(b + off_lo);
-  if (cluster) {  // the bins were checked by k_check_band, but the plan is built before its status is read
-    int* cnt = reinterpret_cast<int*>(b + off_cnt);
-    WF_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (n_bins + 1), st));
-    k_band_map<<<int((nm + 255) / 256), 256, 0, st>>>(bins, H, W, cm, n_bins, bmap, cnt);
-    k_band_offsets<<<1, 32, 0, st>>>(cnt, n_bins, perm, band_off, band_lo);
-    if (n_bins > 0) k_band_positions<<<n_bins, 256, 0, st>>>(H, W, band_off, bmap);
-    WF_CUDA(cudaGetLastError());
-  }
+  int* cnt = reinterpret_cast<int*>(b + off_cnt);
+  WF_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (n_bins + 1), st));
+  k_band_map<<<int((nm + 255) / 256), 256, 0, st>>>(bins, H, W, cm, n_bins, bmap, cnt);
+  k_band_offsets<<<1, 32, 0, st>>>(cnt, n_bins, perm, band_off, band_lo);
+  if (n_bins > 0) k_band_positions<<<n_bins, 256, 0, st>>>(int(nm), band_off, bmap);
+  WF_CUDA(cudaGetLastError());
   wf::SampleArgs a{};
   a.aq = aq; a.fg = fg; a.sc = sc; a.init_s = o.init_s;
   a.init_stride = (o.init_s && o.init_per_chain) ? (long long)n : 0;
@@ -998,7 +1010,7 @@ wf_status wf_sample_band(const float* d, const float* Ndiag, const uint8_t* mask
   a.burn_in = o.burn_in; a.thin = o.thin; a.chain0 = o.chain_offset; a.step0 = o.start_step;
   a.key0 = uint32_t(seed & 0xffffffffu); a.key1 = uint32_t(seed >> 32);
   a.out_dtype = o.out_dtype;
-  a.bins = bins; a.n_bins = n_bins; a.P0 = P0; a.out_P = out_P;
+  a.n_bins = n_bins; a.P0 = P0; a.out_P = out_P;
   a.band_map = bmap; a.band_off = band_off; a.band_lo = band_lo;
   a.band_buf = reinterpret_cast<float2*>(b + off_buf); a.band_clusters = n_cl;
   KernelTimer timer(st);

@@ -31,15 +31,6 @@ __host__ __device__ constexpr int cband_smem(int n_bins) {
   return CGeo<N, MR>::ROWS_BYTES + N * 8 + ((12 * n_bins + 15) / 16) * 16;
 }
 
-// whether slot-order mode i is one the s-draw visits as itself (its statistics stored): every interior
-// mode, and on the packed edge column (kx = 0 in slot 0, kx = W/2 after the H L interior slots) the rows
-// ky <= H/2 (the rows above are the conjugates of those, counted through their mirror weight)
-// (H rows, L = W / 2 interior slots per row)
-__host__ __device__ inline bool cband_visited(int i, int H, int L) {
-  if (i >= H * L) return i - H * L <= H / 2;
-  return i % L != 0 || i / L <= H / 2;
-}
-
 // a.band_clusters clusters; cluster c runs chains c, c + band_clusters, ... (one statistics buffer each);
 // a.fg and a.band_map in slot order (ctab_index), a.aq with the CTA-contiguous rows
 template <int N, int MR>

@@ -461,21 +461,20 @@ struct SampleArgs {
   uint32_t key0, key1;
   int out_dtype;         // OutType of out
   // hierarchical sampler (k_sample_band) only
-  const int* bins;       // [H][W/2+1] bin of each mode, -1: power from the table
   int n_bins;
   const float* P0;       // [n_bins] initial band powers
   float* out_P;          // [n_chains][n_samples][n_bins] or nullptr
-  // cluster form of the hierarchical sampler (k_csample_band) only
-  const int2* band_map;  // slot order: (bin, position in the bin-ordered statistics buffer or -1)
+  const int2* band_map;  // mode table order: (bin or -1, position in the bin-ordered statistics buffer or < 0)
   const int* band_off;   // [n_bins + 1] start of each bin in the statistics buffer
+  float2* band_buf;      // statistics buffers: one per chain (on-chip form), one per cluster (k_csample_band)
+  // cluster form of the hierarchical sampler (k_csample_band) only
   const int* band_lo;    // [CTAs per cluster + 1] bins summed by each CTA of a cluster
-  float2* band_buf;      // [band_clusters][band_off[n_bins]] statistics buffers, one per cluster
   int band_clusters;     // clusters launched; each runs chains c, c + band_clusters, ...
 };
 
-// shared bytes per field of the hierarchical sampler: the per-band s-draw coefficients (float2), the two
-// accumulators and the band powers (floats)
-WF_HD int band_bytes(int n_bins) { return ((n_bins * 20 + 15) / 16) * 16; }
+// shared bytes per field of the hierarchical sampler: the per-band s-draw coefficients (float2) and the
+// band powers (floats)
+WF_HD int band_bytes(int n_bins) { return ((n_bins * 12 + 15) / 16) * 16; }
 
 // CTAs per SM the sample kernel is compiled for (register budget 65536 / (threads * CTAs)):
 // 128^2 fields are limited to three per SM by shared memory (66.5 KB each).
@@ -658,10 +657,11 @@ WF_HD double s_update_wf_parked(float2* cs, int lt, const float* __restrict__ Pk
 }
 
 // Mode coefficients (f/n, g/sqrt(2n)) of the s-draw. TableCoef reads the per-call table; BandCoef (the
-// hierarchical sampler) derives them from the band power P_b of the mode's bin (bins >= 0, in shared
-// memory) with the formulas of table_mode in FP32, and accumulates the band-power statistics of the new
-// modes: S_b += |s_hat|^2 (unitary scale, full spectrum) and X_b += the squares of the stream-6 normals,
-// in FP32 shared-memory sums (their order of addition varies, so band powers repeat to FP32 rounding).
+// hierarchical sampler) takes them from the per-band table cb = band_coef(P_b) in shared memory for modes
+// with a bin (bmap[j].x >= 0, j = ky (W/2+1) + kx; -1: the table's coefficients) and stores the band
+// statistics of each new mode, (n |s_hat|^2 with its mirror weight, the squares of its stream-6 normals),
+// to its own position bmap[j].y of the chain's bin-ordered buffer in global memory (< 0: not summed), so
+// that the band sums need no atomics and run in a fixed order.
 // s-draw coefficients (f/n, g/sqrt(2n)) of band power P (table_mode's formulas in FP32; (0, 0) for P <= 0)
 WF_HD float2 band_coef(float P, float tau, float inv_n) {
   if (!(P > 0.0f)) return make_float2(0.0f, 0.0f);
@@ -681,25 +681,23 @@ struct BandCoef {
   static constexpr bool kBand = true;
   const float2* __restrict__ fg;
   int wh;
-  const int* __restrict__ bins;  // [H][W/2+1], -1: the table's coefficients
-  float2* cb;                    // shared [n_bins]: band_coef of each band power
-  float* Pb;                     // shared [n_bins]
-  float* acc;                    // shared [2][n_bins]: S_b then X_b
+  const int2* __restrict__ bmap;  // [H][W/2+1]: (bin, position in the statistics buffer)
+  float2* cb;                     // shared [n_bins]: band_coef of each band power
+  float* Pb;                      // shared [n_bins]
+  float2* buf;                    // this chain's statistics, bin-ordered (global, L2)
+  const int* off;                 // [n_bins + 1] start of each bin in buf
   int n_bins;
   float tau, inv_n, n;
   WF_HD float2 coef(int ky, int kx) const {
-    const int b = WF_LDG(bins + ky * wh + kx);
+    const int b = WF_LDG(bmap + ky * wh + kx).x;
     return b < 0 ? WF_LDG(fg + ky * wh + kx) : cb[b];
   }
-  WF_HD int bin(int ky, int kx) const { return WF_LDG(bins + ky * wh + kx); }
-  WF_HD void flush(int b, float s2, float x2) const {
+  WF_HD void add(int ky, int kx, float s2, float x2) const {
 #if defined(__CUDA_ARCH__)
-    if (b < 0) return;
-    atomicAdd(acc + b, s2 * n);
-    atomicAdd(acc + n_bins + b, x2);
+    const int pos = WF_LDG(bmap + ky * wh + kx).y;
+    if (pos >= 0) __stcg(buf + pos, make_float2(s2 * n, x2));
 #endif
   }
-  WF_HD void add(int ky, int kx, float s2, float x2) const { flush(bin(ky, kx), s2, x2); }
 };
 
 // interior columns (col > 0): every thread but the edge thread updates its own parked modes
@@ -710,23 +708,6 @@ WF_HD void s_draw_interior(float2* cs, int lt, const Coef& cf, uint32_t step, ui
   constexpr int LC = G::LC, H = G::H;
   const int col = lt % LC, r = lt / LC;
   if (col == 0) return;
-  // band statistics: consecutive modes of a column thread mostly share a bin, so they are summed in
-  // registers and added to the shared FP64 sums once per run of equal bins
-  int run_b = -1;
-  float run_s = 0.0f, run_x = 0.0f;
-  auto band_add = [&](int ky, float s2, float x2) {
-    if constexpr (Coef::kBand) {
-      const int b = cf.bin(ky, col);
-      if (b != run_b) {
-        cf.flush(run_b, run_s, run_x);
-        run_b = b;
-        run_s = 0.0f;
-        run_x = 0.0f;
-      }
-      run_s += s2;
-      run_x += x2;
-    }
-  };
 #pragma unroll (kRngUnroll)
   for (int kp = 0; kp < LC / 2; ++kp) {
     int kq, ky1, ky2;
@@ -743,11 +724,10 @@ WF_HD void s_draw_interior(float2* cs, int lt, const Coef& cf, uint32_t step, ui
     if constexpr (Coef::kBand) {  // both modes have their mirror in the other half plane: weight 2
       float zb[4];
       normals4(uint32_t(col * (H / 2) + ky1), step, chain, 6u, k0, k1, zb);
-      band_add(ky1, 2.0f * (y1.x * y1.x + y1.y * y1.y), zb[0] * zb[0] + zb[1] * zb[1]);
-      band_add(ky2, 2.0f * (y2.x * y2.x + y2.y * y2.y), zb[2] * zb[2] + zb[3] * zb[3]);
+      cf.add(ky1, col, 2.0f * (y1.x * y1.x + y1.y * y1.y), zb[0] * zb[0] + zb[1] * zb[1]);
+      cf.add(ky2, col, 2.0f * (y2.x * y2.x + y2.y * y2.y), zb[2] * zb[2] + zb[3] * zb[3]);
     }
   }
-  if constexpr (Coef::kBand) cf.flush(run_b, run_s, run_x);
 }
 
 // the packed edge column (col 0: kx = 0 as A and kx = W/2 as B in Y = A + i B, both Hermitian in ky):
@@ -923,16 +903,55 @@ WF_HD void spin2_edge(const Spin2Coef& cf, int lt, uint32_t step, uint32_t chain
   cf.cs1[i2] = y2b;
 }
 
-// band-power draw after the s-draw (all accumulations done): P_b = S_b / X_b, accumulators reset
+// band-power draw after the s-draw (every mode's statistics stored and visible to the field's threads):
+// the field's threads in groups of G = min(N, 32) lanes take four bins at a time, each lane summing its
+// lane-strided entries of the four bins (16 loads in flight), then a fixed shuffle tree per bin: the same
+// order every run; P_b = S_b / X_b and band_coef(P_b) to shared memory. Called by all lanes of every
+// warp (the loop bounds are the same for every field of a warp).
 template <int N>
-WF_HD void band_update(const BandCoef& bc, int lt) {
-  for (int b = lt; b < bc.n_bins; b += N) {
-    const float S = bc.acc[b], X = bc.acc[bc.n_bins + b];
-    const float P = X > 0.0f ? S / X : 0.0f;
-    bc.Pb[b] = P;
-    bc.cb[b] = band_coef(P, bc.tau, bc.inv_n);
-    bc.acc[b] = 0.0f;
-    bc.acc[bc.n_bins + b] = 0.0f;
+__device__ __forceinline__ void band_update(const BandCoef& bc, int lt) {
+  constexpr int G = N < 32 ? N : 32, NG = N / G, KB = 4, U = 4;
+  const int gl = lt % G;
+  for (int b0 = lt / G; b0 < bc.n_bins; b0 += NG * KB) {
+    int o0[KB], len[KB], most = 0;
+    float S[KB], X[KB];
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      const int b = b0 + k * NG;
+      o0[k] = b < bc.n_bins ? bc.off[b] : 0;
+      len[k] = b < bc.n_bins ? bc.off[b + 1] - o0[k] : 0;
+      most = len[k] > most ? len[k] : most;
+      S[k] = X[k] = 0.0f;
+    }
+    for (int j = gl; j < most; j += U * G) {
+      float2 v[KB][U];
+#pragma unroll
+      for (int k = 0; k < KB; ++k)
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          v[k][u] = j + G * u < len[k] ? __ldcg(bc.buf + o0[k] + j + G * u) : make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int k = 0; k < KB; ++k)
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          S[k] += v[k][u].x;
+          X[k] += v[k][u].y;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+#pragma unroll
+      for (int d = G / 2; d > 0; d >>= 1) {
+        S[k] += __shfl_xor_sync(0xffffffffu, S[k], d);
+        X[k] += __shfl_xor_sync(0xffffffffu, X[k], d);
+      }
+      const int b = b0 + k * NG;
+      if (gl == 0 && b < bc.n_bins) {
+        const float P = X[k] > 0.0f ? S[k] / X[k] : 0.0f;
+        bc.Pb[b] = P;
+        bc.cb[b] = band_coef(P, bc.tau, bc.inv_n);
+      }
+    }
   }
 }
 
@@ -1060,17 +1079,17 @@ __global__ void __launch_bounds__(N * FPC, sample_min_ctas<N>()) k_sample_band(S
   float2* S = reinterpret_cast<float2*>(smem_raw + fld * G::FIELD_BYTES);
   unsigned char* band = smem_raw + FPC * G::FIELD_BYTES + fld * band_bytes(a.n_bins);
   float2* cb = reinterpret_cast<float2*>(band);
-  float* acc = reinterpret_cast<float*>(cb + a.n_bins);
-  float* Pb = acc + 2 * a.n_bins;
+  float* Pb = reinterpret_cast<float*>(cb + a.n_bins);
   if (a.sc->status != 0) return;  // uniform over the grid
   const float tau = float(a.sc->tau);
   constexpr float NPIX = float(G::H * G::W);
   for (int b = lt; b < a.n_bins; b += N) {
-    acc[b] = 0.0f;
-    acc[a.n_bins + b] = 0.0f;
     Pb[b] = a.P0[b];
     cb[b] = band_coef(a.P0[b], tau, 1.0f / NPIX);
   }
+  // one statistics buffer per field of the grid (inactive fields past the last chain run the sweeps with
+  // the CTA, its barriers and warp shuffles, into their own buffer, and write no output)
+  float2* buf = a.band_buf + (long long)ci * (a.n_bins > 0 ? a.band_off[a.n_bins] : 0);
   __syncthreads();
   float2 c[G::LR];
   if (a.init_s != nullptr && active) {
@@ -1081,7 +1100,7 @@ __global__ void __launch_bounds__(N * FPC, sample_min_ctas<N>()) k_sample_band(S
 #pragma unroll
     for (int m = 0; m < G::LR; ++m) c[m] = make_float2(0.f, 0.f);
   }
-  const BandCoef cf{a.fg, G::WH, a.bins, cb, Pb, acc, a.n_bins, tau, 1.0f / NPIX, NPIX};
+  const BandCoef cf{a.fg, G::WH, a.band_map, cb, Pb, buf, a.band_off, a.n_bins, tau, 1.0f / NPIX, NPIX};
   sample_sweeps<N>(S, lt, c, a.aq, cf, a.sc->sqrt_tau, a.step0, a.chain0 + uint32_t(ci), a.key0, a.key1,
                    a.n_sweeps, a.burn_in, a.thin,
                    reinterpret_cast<char*>(a.out) +

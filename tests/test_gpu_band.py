@@ -120,3 +120,39 @@ def test_band_sampler_large_chains_loop_and_repeat_exactly():
         rs, rP = HG.sample(p.d, p.Ndiag, p.mask, p.Pk, bins, P0.cpu().numpy(), 1, seed=12, chain=c, burn_in=1)
         assert rel(xs[c, 0].cpu().numpy(), rs[0]) < SAMPLE_TOL, (c, rel(xs[c, 0].cpu().numpy(), rs[0]))
         assert rel(Ps[c, 0].cpu().numpy(), rP[0]) < SAMPLE_TOL, c
+
+
+def test_band_sampler_large_storage_options():
+    """512^2: BF16 sample storage is the FP32 chain rounded once (torch's round-to-nearest-even), band powers
+    not kept, per-chain initial states; a bin outside [-1, n_bins) is refused before any sweep."""
+    H = 512
+    p = synth.make_problem(H, seed=31, mask_frac=0.1, slope=-2.0, k0=1.0 / 32, sigma2=(0.05, 0.5))
+    dev = to_dev(p)
+    bins, nb = HG.radial_bins(H, H)
+    bd, P0 = torch.from_numpy(bins).cuda(), torch.full((nb,), 0.5, device="cuda")
+    init = torch.randn((2, H, H), device="cuda")
+    f32, Pf = wf.wf_sample_band(*dev, bd, P0, seed=2, n_samples=2, n_chains=2, init_s=init)
+    b16, Pn = wf.wf_sample_band(*dev, bd, P0, seed=2, n_samples=2, n_chains=2, init_s=init, out_dtype="bf16",
+                                keep_P=False)
+    assert Pn is None and torch.equal(b16, f32.to(torch.bfloat16))
+    rs, rP = HG.sample(p.d, p.Ndiag, p.mask, p.Pk, bins, P0.cpu().numpy(), 2, seed=2, chain=1,
+                       init_s=init[1].cpu().numpy())
+    assert rel(f32[1, 1].cpu().numpy(), rs[1]) < SAMPLE_TOL and rel(Pf[1, 1].cpu().numpy(), rP[1]) < SAMPLE_TOL
+    bad = bd.clone()
+    bad[5, 7] = nb
+    with pytest.raises(wf.WFError) as e:
+        wf.wf_sample_band(*dev, bad, P0, seed=1, n_samples=1)
+    assert e.value.status == 1
+
+
+@pytest.mark.parametrize("H", [32, 128])
+def test_band_sampler_repeats_exactly(H):
+    """The band sums run in a fixed order at every size: a repeated call is bit-identical (3 chains at 32^2
+    leave one field of the last CTA inactive)."""
+    p = synth.make_problem(H, seed=H + 3, mask_frac=0.1, slope=-2.0, k0=1.0 / 32, sigma2=(0.05, 0.5))
+    dev = to_dev(p)
+    bins, nb = HG.radial_bins(H, H)
+    bd, P0 = torch.from_numpy(bins).cuda(), torch.full((nb,), 0.5, device="cuda")
+    a = wf.wf_sample_band(*dev, bd, P0, seed=5, n_samples=3, n_chains=3)
+    b = wf.wf_sample_band(*dev, bd, P0, seed=5, n_samples=3, n_chains=3)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])

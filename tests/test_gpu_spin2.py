@@ -90,6 +90,21 @@ def test_spin2_wiener_filter_large_true_residual(H):
     assert abs(true - r.resid) <= 1e-6 * true
 
 
+def test_spin2_sampler_large_per_chain_init_and_bf16():
+    """512^2: per-chain initial pairs follow the oracle from those states; BF16 storage is the FP32 chain
+    rounded once."""
+    H = 512
+    p, d2, N2, PB = _pair(H, 41)
+    dev = _dev(p.d, d2, p.Ndiag, N2, p.mask, p.Pk, PB)
+    init = torch.randn((2, 2, H, H), device="cuda")
+    f32 = wf.wf_sample_spin2(*dev, seed=9, n_samples=1, n_chains=2, init=init)
+    b16 = wf.wf_sample_spin2(*dev, seed=9, n_samples=1, n_chains=2, init=init, out_dtype="bf16")
+    assert torch.equal(b16, f32.to(torch.bfloat16))
+    ref = S2.sample(p.d, d2, p.Ndiag, N2, p.mask, p.Pk, PB, 1, seed=9, chain=1, init=init[1].cpu().numpy())
+    for comp in range(2):
+        assert rel(f32[1, 0, comp].cpu().numpy(), ref[0, comp]) < SAMPLE_TOL
+
+
 def test_shear_to_convergence_matches_oracle():
     rng = np.random.default_rng(3)
     for H in (16, 128, 256):
