@@ -256,7 +256,7 @@ __device__ __forceinline__ void ccol_inv(float2* rows, int t, int b, const float
 // takes them from the per-band table cb = band_coef(P_b) of the mode's bin (bmap[i].x >= 0; -1: the
 // table's coefficients) and stores the band statistics of each new mode, (n |s_hat|^2 weighted by the
 // mirror modes it stands for, the squares of its stream-6 normals), to its own position bmap[i].y of the
-// chain's bin-ordered buffer (-1: not summed), so that the band sums need no atomics.
+// chain's bin-ordered buffer (< 0: not summed), so that the band sums need no atomics.
 struct CTabCoef {
   static constexpr bool kBand = false;
   const float2* __restrict__ fg;

@@ -460,7 +460,7 @@ struct SampleArgs {
   uint32_t step0;
   uint32_t key0, key1;
   int out_dtype;         // OutType of out
-  // hierarchical sampler (k_sample_band) only
+  // hierarchical samplers (k_sample_band, k_csample_band) only
   int n_bins;
   const float* P0;       // [n_bins] initial band powers
   float* out_P;          // [n_chains][n_samples][n_bins] or nullptr
@@ -1068,7 +1068,9 @@ __global__ void __launch_bounds__(N * FPC, sample_min_ctas<N>()) k_sample(Sample
 
 // The hierarchical sampler: k_sample's sweeps with the s-draw coefficients taken from band powers held in
 // shared memory and a band-power draw (P | s) after every s-draw. Field fld's band region follows the FPC
-// field buffers: accumulators [2][n_bins] doubles, then the band powers [n_bins] floats.
+// field buffers: the per-band draw coefficients [n_bins] float2, then the band powers [n_bins] floats; its
+// mode statistics go to its own bin-ordered buffer in global memory (a.band_buf, a.band_off[n_bins]
+// entries per field of the grid).
 template <int N, int FPC>
 __global__ void __launch_bounds__(N * FPC, sample_min_ctas<N>()) k_sample_band(SampleArgs a) {
   using G = Geo<N>;
