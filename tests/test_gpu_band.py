@@ -156,3 +156,19 @@ def test_band_sampler_repeats_exactly(H):
     a = wf.wf_sample_band(*dev, bd, P0, seed=5, n_samples=3, n_chains=3)
     b = wf.wf_sample_band(*dev, bd, P0, seed=5, n_samples=3, n_chains=3)
     assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("H", [64, 256])
+def test_band_sampler_empty_band(H):
+    """A band with no modes (an extra bin id the map never uses) keeps P_b = 0, and the other bands and the
+    samples still follow the oracle."""
+    p = synth.make_problem(H, seed=H + 17, mask_frac=0.1, slope=-2.0, k0=1.0 / 32, sigma2=(0.05, 0.5))
+    bins, nb = HG.radial_bins(H, H)
+    P0 = np.full(nb + 1, 0.5, np.float32)
+    xs, Ps = wf.wf_sample_band(*to_dev(p), torch.from_numpy(bins).cuda(), torch.from_numpy(P0).cuda(), seed=3,
+                               n_samples=2)
+    rs, rP = HG.sample(p.d, p.Ndiag, p.mask, p.Pk, bins, P0, 2, seed=3)
+    Ps = Ps.cpu().numpy()
+    assert np.all(Ps[0, :, nb] == 0.0) and np.all(rP[:, nb] == 0.0)
+    for m in range(2):
+        assert rel(xs[0, m].cpu().numpy(), rs[m]) < SAMPLE_TOL and rel(Ps[0, m], rP[m]) < SAMPLE_TOL
