@@ -224,9 +224,14 @@ wf_status wf_shear_to_convergence(const float* gamma, int64_t n, int32_t H, int3
  * with the options below, from zero) and then n_samples posterior samples of one chain started at the
  * Wiener filter (Alg. 1 from s_0 = s_W, no burn-in, thin 1, Philox key `seed`, chain word `chain`, step
  * words 0 .. n_samples-1). Chains are independent (§4.2 of the paper runs independent chains in parallel).
- *   - Images up to 128 x 128 run through one persistent launch per size: every CTA keeps one image's field
- *     in shared memory and takes images from an atomic work counter until none is left. Larger images run
- *     their cooperative pipelines on a pool of `large_streams` streams. All of it is ordered after the
+ *   - Images up to 128 x 128, per size (opts->small_path): by default in phases (per-image set-up and
+ *     tables, the level norms, one CTA per image for the cooled solve, then the samplers with several
+ *     images per CTA), or as one persistent launch in which every CTA keeps one image's field in shared
+ *     memory and takes images from an atomic work counter. 256 x 256 and 512 x 512 images: one
+ *     thread-block cluster per image runs its whole pipeline with the field in distributed shared memory;
+ *     1024 x 1024 images, small chunks and devices without room for a cluster: one cooperative launch per
+ *     chunk with the fields in global memory. The size classes and the chunks of the large classes run
+ *     on their own streams (`large_streams` per large class) and overlap. All of it is ordered after the
  *     work already on `stream` and the call returns when everything has finished.
  *   - items: HOST array; the pointers inside are DEVICE pointers owned by the caller; out_wf may be NULL
  *     (then the filter is not written), out_samples may be NULL when n_samples == 0.
