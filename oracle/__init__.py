@@ -18,7 +18,8 @@ It is deliberately plain and slow:
 * ``hierarchical``— Alg. 1 sweeps alternated with inverse-gamma draws of binned band powers (the power
   spectrum inference of §5);
 * ``spin2``    — shear data of a convergence field (the Kaiser-Squires operator of §5's mass mapping) in
-  the messenger sampler, its Wiener filter and posterior by dense algebra.
+  the messenger sampler, its Wiener filter and posterior by dense algebra, and the FP64 residual of a
+  shear map in the Wiener-filter system (the shear covariance applied by FFTs).
 
 Every function is pinned by ``tests/test_oracle_*.py`` against something other than itself
 (explicit DFT sums, numpy.fft, dense linear algebra, closed forms, curand's Philox, Monte-Carlo
