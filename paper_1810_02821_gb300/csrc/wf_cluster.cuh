@@ -357,7 +357,54 @@ __device__ __forceinline__ void ccol_units(cooperative_groups::cluster_group& cl
   using G = CGeo<N, MR>;
   constexpr int P = G::P, L = G::L, R = G::R;
   constexpr int M = G::M;
-  static_assert((L * (M / 2)) % (P * L) == 0, "equal work units per thread");
+  constexpr int PAIRS = L * (M / 2);
+  static_assert(PAIRS % (P * L) == 0, "equal work units per thread");
+  if constexpr (PAIRS == P * L) {
+    // One unit pair per thread (512^2, 16 CTAs of 32 rows): each thread takes one unit of a pair in turn
+    // (two units), its partner lane (lane ^ 16, same slot t) the other, so a thread holds P values instead of
+    // 2 P. For u != 0 each lane leads, at step m, the pair whose first mode is its own y[m] (ky1 = uu + M m):
+    // it fetches the second mode from its partner's y[P-1-m] by a shuffle, runs fn on both, and hands the new
+    // second value back (the led and the handed indices are disjoint). The units u = 0 and M/2 hold their
+    // pairs themselves. Same pairs, roles and draws as the two-unit form below.
+    static_assert(L % 16 == 0, "a half-warp of consecutive slots shares one unit");
+    const int lane = int(threadIdx.x) % 32, half = lane / 16;
+    const int w0 = (g / 32) * 16 + lane % 16;
+#pragma unroll 1
+    for (int rep = 0; rep < 2; ++rep) {
+      const int w = w0 + rep * (PAIRS / 2);
+      const int t = w % L, u = w / L;
+      const int uu = half == 0 ? u : (u == 0 ? M / 2 : M - u);  // this lane's unit
+      const int K = (t % R) * M + t / R;                         // kx held by slot t
+      float2 y[P];
+#pragma unroll
+      for (int j = 0; j < P; ++j) y[j] = cl.map_shared_rank(rows, j)[uu * G::SP + t];
+      fft<P, false>(y);  // y[m] = t_hat[uu + M m]
+      if (u == 0) {      // the same in every lane of the warp
+        if (half == 0) {
+          fn(K, t, y[0], y[P / 2], 0, N / 2);
+#pragma unroll
+          for (int m = 1; m < P / 2; ++m) fn(K, t, y[m], y[P - m], M * m, N - M * m);
+        } else {
+#pragma unroll
+          for (int m = 0; m < P / 2; ++m) fn(K, t, y[m], y[P - 1 - m], M / 2 + M * m, N - M / 2 - M * m);
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < P / 2; ++m) {
+          float2 y2 = make_float2(__shfl_xor_sync(0xffffffffu, y[P - 1 - m].x, 16),
+                                  __shfl_xor_sync(0xffffffffu, y[P - 1 - m].y, 16));
+          fn(K, t, y[m], y2, uu + M * m, N - uu - M * m);
+          y[P - 1 - m] = make_float2(__shfl_xor_sync(0xffffffffu, y2.x, 16), __shfl_xor_sync(0xffffffffu, y2.y, 16));
+        }
+      }
+      if (WRITE) {
+        fft<P, true>(y);
+#pragma unroll
+        for (int j = 0; j < P; ++j) cl.map_shared_rank(rows, j)[uu * G::SP + t] = y[j];
+      }
+    }
+    return;
+  }
   for (int w = g; w < L * (M / 2); w += P * L) {
     const int t = w % L, u = w / L, v = u == 0 ? M / 2 : M - u;
     const int K = (t % R) * M + t / R;  // kx held by slot t
