@@ -181,7 +181,59 @@ template <int N, int MR, int T, class F>
 __device__ __forceinline__ void ccol_units2(cooperative_groups::cluster_group& cl, float2* rows, int g, F&& fn) {
   using G = CGeo<N, MR>;
   constexpr int P = G::P, L = G::L, R = G::R, M = G::M, CS = G::A * G::SP;
-  static_assert((L * (M / 2)) % (P * T) == 0, "equal work units per thread");
+  constexpr int PAIRS = L * (M / 2);
+  static_assert(PAIRS % (P * T) == 0, "equal work units per thread");
+  if constexpr (PAIRS == P * T) {
+    // one unit pair per thread: the two units of a pair go to partner lanes (lane ^ 16, same slot), each
+    // holding its unit's values of both components, as in ccol_units; the lane leading a mode pair fetches
+    // the second mode of both components from its partner and hands the new values back
+    static_assert(L % 16 == 0, "a half-warp of consecutive slots shares one unit");
+    const int lane = int(threadIdx.x) % 32, half = lane / 16;
+    const int w0 = (g / 32) * 16 + lane % 16;
+#pragma unroll 1
+    for (int rep = 0; rep < 2; ++rep) {
+      const int w = w0 + rep * (PAIRS / 2);
+      const int t = w % L, u = w / L;
+      const int uu = half == 0 ? u : (u == 0 ? M / 2 : M - u);
+      const int K = (t % R) * M + t / R;
+      float2 y[2][P];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+#pragma unroll
+        for (int j = 0; j < P; ++j) y[c][j] = cl.map_shared_rank(rows + c * CS, j)[uu * G::SP + t];
+        fft<P, false>(y[c]);
+      }
+      if (u == 0) {  // the same in every lane of the warp
+        if (half == 0) {
+          fn(K, t, y[0][0], y[0][P / 2], y[1][0], y[1][P / 2], 0, N / 2);
+#pragma unroll
+          for (int m = 1; m < P / 2; ++m) fn(K, t, y[0][m], y[0][P - m], y[1][m], y[1][P - m], M * m, N - M * m);
+        } else {
+#pragma unroll
+          for (int m = 0; m < P / 2; ++m)
+            fn(K, t, y[0][m], y[0][P - 1 - m], y[1][m], y[1][P - 1 - m], M / 2 + M * m, N - M / 2 - M * m);
+        }
+      } else {
+        auto swap16 = [](float2 v) {
+          return make_float2(__shfl_xor_sync(0xffffffffu, v.x, 16), __shfl_xor_sync(0xffffffffu, v.y, 16));
+        };
+#pragma unroll
+        for (int m = 0; m < P / 2; ++m) {
+          float2 a2 = swap16(y[0][P - 1 - m]), b2 = swap16(y[1][P - 1 - m]);
+          fn(K, t, y[0][m], a2, y[1][m], b2, uu + M * m, N - uu - M * m);
+          y[0][P - 1 - m] = swap16(a2);
+          y[1][P - 1 - m] = swap16(b2);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        fft<P, true>(y[c]);
+#pragma unroll
+        for (int j = 0; j < P; ++j) cl.map_shared_rank(rows + c * CS, j)[uu * G::SP + t] = y[c][j];
+      }
+    }
+    return;
+  }
   for (int w = g; w < L * (M / 2); w += P * T) {
     const int t = w % L, u = w / L, v = u == 0 ? M / 2 : M - u;
     const int K = (t % R) * M + t / R;  // kx held by slot t
