@@ -108,18 +108,15 @@ __global__ void __launch_bounds__(N / 2, csample_min_ctas<N, MR>()) k_csample_ba
 // shared bytes: the rows of both components, twiddles
 template <int N, int MR>
 __host__ __device__ constexpr int cspin2_smem() { return 2 * CGeo<N, MR>::ROWS_BYTES + N * 8; }
-// threads per CTA: 2 L (one component's row and column passes per half) where the column units then
-// still come out whole per thread (256^2: 8-CTA clusters of 256 threads, 2 per SM), else L (each thread
-// both components; 512^2: 16-CTA clusters of 256 threads, 1 per SM)
+// threads per CTA: 2 L, one component's row and column passes per half (256^2: 8-CTA clusters of 256
+// threads, 2 CTAs per SM; 512^2: 16-CTA clusters of 512 threads, 1 per SM), the column stage then taking
+// one or two units of a pair per thread (ccol_units2)
 template <int N, int MR>
-__host__ __device__ constexpr bool cspin2_split() {
-  using G = CGeo<N, MR>;
-  return (G::L * (G::M / 2)) % (G::P * 2 * G::L) == 0 && 2 * G::ROWS_BYTES + N * 8 <= 110 * 1024;
-}
+__host__ __device__ constexpr bool cspin2_split() { return true; }
 template <int N, int MR>
 __host__ __device__ constexpr int cspin2_threads() { return cspin2_split<N, MR>() ? 2 * CGeo<N, MR>::L : CGeo<N, MR>::L; }
 template <int N, int MR>
-__host__ __device__ constexpr int cspin2_min_ctas() { return cspin2_split<N, MR>() ? 2 : 1; }
+__host__ __device__ constexpr int cspin2_min_ctas() { return 2 * (cspin2_smem<N, MR>() + 1024) <= 228 * 1024 ? 2 : 1; }
 
 // The spin-2 s-draw of one mode pair (ky1, ky2) of packed column slot t (kx = K) on both components
 // (y1a, y2a: component 1; y1b, y2b: component 2): per mode, rotation by (c, s) = (cos 2 phi, sin 2 phi)
@@ -182,17 +179,19 @@ __device__ __forceinline__ void ccol_units2(cooperative_groups::cluster_group& c
   using G = CGeo<N, MR>;
   constexpr int P = G::P, L = G::L, R = G::R, M = G::M, CS = G::A * G::SP;
   constexpr int PAIRS = L * (M / 2);
-  static_assert(PAIRS % (P * T) == 0, "equal work units per thread");
-  if constexpr (PAIRS == P * T) {
-    // one unit pair per thread: the two units of a pair go to partner lanes (lane ^ 16, same slot), each
-    // holding its unit's values of both components, as in ccol_units; the lane leading a mode pair fetches
-    // the second mode of both components from its partner and hands the new values back
+  if constexpr (PAIRS <= P * T) {
+    // at most one unit pair per thread: the two units of a pair go to partner lanes (lane ^ 16, same slot),
+    // each holding its unit's values of both components, as in ccol_units (REPS units per lane); the lane
+    // leading a mode pair fetches the second mode of both components from its partner and hands the new
+    // values back
+    constexpr int REPS = 2 * PAIRS / (P * T);
+    static_assert(REPS >= 1 && 2 * PAIRS == REPS * P * T, "equal work units per thread");
     static_assert(L % 16 == 0, "a half-warp of consecutive slots shares one unit");
     const int lane = int(threadIdx.x) % 32, half = lane / 16;
     const int w0 = (g / 32) * 16 + lane % 16;
 #pragma unroll 1
-    for (int rep = 0; rep < 2; ++rep) {
-      const int w = w0 + rep * (PAIRS / 2);
+    for (int rep = 0; rep < REPS; ++rep) {
+      const int w = w0 + rep * (PAIRS / REPS);
       const int t = w % L, u = w / L;
       const int uu = half == 0 ? u : (u == 0 ? M / 2 : M - u);
       const int K = (t % R) * M + t / R;
@@ -234,6 +233,7 @@ __device__ __forceinline__ void ccol_units2(cooperative_groups::cluster_group& c
     }
     return;
   }
+  static_assert(PAIRS <= P * T || PAIRS % (P * T) == 0, "equal work units per thread");
   for (int w = g; w < L * (M / 2); w += P * T) {
     const int t = w % L, u = w / L, v = u == 0 ? M / 2 : M - u;
     const int K = (t % R) * M + t / R;  // kx held by slot t
