@@ -71,6 +71,24 @@ __host__ __device__ inline int ctab_index(int ky, int kx) {
   return kx < G::W / 2 ? ky * G::L + cslot_of<N, MR>(kx) : G::H * G::L + ky;
 }
 
+// Loads of the per-call tables marked evict-last in L2: the tables are re-read every sweep (in a batch
+// each image has its own), while the samples stream out with evict-first stores (crows_store)
+__device__ __forceinline__ uint64_t l2_keep() {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ float2 ldk(const float2* a, uint64_t pol) {
+  float2 v;
+  asm("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ float ldk(const float* a, uint64_t pol) {
+  float v;
+  asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
+  return v;
+}
+
 // ---------------------------------------------------------------------------------------------
 // row passes (R threads per row, h = the thread's index within its row)
 // ---------------------------------------------------------------------------------------------
@@ -206,13 +224,14 @@ __device__ __forceinline__ void ct_draw(float2* row, int y, int ty, int h, const
                                         float sqrt_tau, uint32_t step, uint32_t chain, uint32_t k0, uint32_t k1,
                                         uint32_t ts = 0u) {
   using G = CGeo<N, MR>;
+  const uint64_t pol = l2_keep();
 #pragma unroll 2
   for (int q = h; q < G::W / 4; q += G::R) {
     float z[4];
     normals4(uint32_t(y * (G::W / 4) + q), step, chain, ts, k0, k1, z);
     float2 p0 = row[2 * q], p1 = row[2 * q + 1];
-    const float2 c0 = WF_LDG(aq + (4 * q) * G::H + ty), c1 = WF_LDG(aq + (4 * q + 1) * G::H + ty);
-    const float2 c2 = WF_LDG(aq + (4 * q + 2) * G::H + ty), c3 = WF_LDG(aq + (4 * q + 3) * G::H + ty);
+    const float2 c0 = ldk(aq + (4 * q) * G::H + ty, pol), c1 = ldk(aq + (4 * q + 1) * G::H + ty, pol);
+    const float2 c2 = ldk(aq + (4 * q + 2) * G::H + ty, pol), c3 = ldk(aq + (4 * q + 3) * G::H + ty, pol);
     p0.x = fmaf(c0.y, fmaf(c0.y, p0.x, sqrt_tau * z[0]), c0.x);
     p0.y = fmaf(c1.y, fmaf(c1.y, p0.y, sqrt_tau * z[1]), c1.x);
     p1.x = fmaf(c2.y, fmaf(c2.y, p1.x, sqrt_tau * z[2]), c2.x);
@@ -260,7 +279,7 @@ __device__ __forceinline__ void ccol_inv(float2* rows, int t, int b, const float
 struct CTabCoef {
   static constexpr bool kBand = false;
   const float2* __restrict__ fg;
-  __device__ __forceinline__ float2 m(int i) const { return WF_LDG(fg + i); }
+  __device__ __forceinline__ float2 m(int i) const { return ldk(fg + i, l2_keep()); }
   __device__ __forceinline__ void add2(int, float, float, int, float, float) const {}
 };
 struct CBandCoef {
@@ -468,9 +487,10 @@ __device__ __forceinline__ double ccol_wf(cooperative_groups::cluster_group& cl,
   };
   auto fcoef = [&](float P) { return wf_fdiv(P, P + lt_) * INV_N; };
   float acc = 0.0f;  // this thread's units in FP32; the cluster sum is FP64
+  const uint64_t pol = l2_keep();
   ccol_units<N, MR, true>(cl, rows, g, [&](int K, int t, float2& y1, float2& y2, int ky1, int ky2) {
     if (K != 0) {
-      const float P1 = WF_LDG(Pk + ky1 * LR + t), P2 = WF_LDG(Pk + ky2 * LR + t);
+      const float P1 = ldk(Pk + ky1 * LR + t, pol), P2 = ldk(Pk + ky2 * LR + t, pol);
       const float2 n1 = cscale(y1, fcoef(P1)), n2 = cscale(y2, fcoef(P2));
       if (cmp) {
         const float2 o1 = prev[ky1 * LR + t], o2 = prev[ky2 * LR + t];
@@ -543,9 +563,10 @@ __device__ __forceinline__ double ccol_p2(cooperative_groups::cluster_group& cl,
 template <int N, int MR>
 __device__ __forceinline__ void ct_update_wf(float2* row, int y, int h, const float2* __restrict__ dn, float lt_) {
   using G = CGeo<N, MR>;
+  const uint64_t pol = l2_keep();
   for (int x2 = h; x2 < G::W / 2; x2 += G::R) {
     float2 v = row[x2];
-    const float2 c0 = WF_LDG(dn + (2 * x2) * G::H + y), c1 = WF_LDG(dn + (2 * x2 + 1) * G::H + y);
+    const float2 c0 = ldk(dn + (2 * x2) * G::H + y, pol), c1 = ldk(dn + (2 * x2 + 1) * G::H + y, pol);
     const float w0 = wf_rcp(fmaf(lt_, c0.y, 1.0f)), w1 = wf_rcp(fmaf(lt_, c1.y, 1.0f));
     v.x = fmaf(w0, v.x - c0.x, c0.x);
     v.y = fmaf(w1, v.y - c1.x, c1.x);
@@ -617,7 +638,13 @@ __device__ __forceinline__ void crows_store(const float2* rows, int b, void* dst
   using G = CGeo<N, MR>;
   for (int e = lt; e < G::A * G::L; e += G::L) {
     const int r2 = e / G::L, i = e % G::L;
-    store_pair(dst, (long long)(G::P * r2 + b) * G::L + i, rows[r2 * G::SP + i], t);
+    const long long at = (long long)(G::P * r2 + b) * G::L + i;
+    const float2 v = rows[r2 * G::SP + i];
+    if (t == kOutF32) {
+      __stcs(reinterpret_cast<float2*>(dst) + at, v);  // evict-first: the samples are not read again
+    } else {
+      store_pair(dst, at, v, t);
+    }
   }
 }
 
