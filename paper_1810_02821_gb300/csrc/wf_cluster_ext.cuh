@@ -13,9 +13,10 @@
 // between the second barrier and the next first one, so no further barrier is needed; the buffer is
 // rewritten only after the next first barrier, when every CTA has finished reading it.
 //
-// Spin-2 (shear): both shear components of a chain in one cluster, each CTA holding its rows of both,
-// and a column unit gathering the column spectra of both components so that the Kaiser-Squires rotation
-// into E and B, the two scalar s-draws and the rotation back happen on complete mode pairs.
+// Spin-2 (shear): both shear components of a chain in one cluster, each CTA holding its rows of both
+// (2 x N/2 threads, one component's row and column passes per half), and a column unit gathering the
+// column spectra of both components so that the Kaiser-Squires rotation into E and B, the two scalar
+// s-draws and the rotation back happen on complete mode pairs (the two units of a pair on partner lanes).
 #pragma once
 
 #include "wf_cluster.cuh"
