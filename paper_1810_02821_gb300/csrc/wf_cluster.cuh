@@ -89,6 +89,18 @@ __device__ __forceinline__ float ldk(const float* a, uint64_t pol) {
   return v;
 }
 
+// Physical position of slot s of a staged row. With R = 8 threads per row (512^2, 32 rows per CTA) the R
+// slots of each butterfly unit u (slots R u .. R u + R - 1) are stored XOR-swizzled by u mod 4, so that a
+// half-warp's reads of one slot of four units of four rows fall in 16 distinct bank pairs both in the
+// radix-R butterflies and in the strided M-point pass (without it the butterflies were 4-way conflicted);
+// every access to the row buffers goes through this map.
+template <int N, int MR>
+__host__ __device__ inline int cphys(int s) {
+  constexpr int R = CGeo<N, MR>::R;
+  if constexpr (R == 8) return s ^ ((s >> 3) & 3);
+  return s;
+}
+
 // ---------------------------------------------------------------------------------------------
 // row passes (R threads per row, h = the thread's index within its row)
 // ---------------------------------------------------------------------------------------------
@@ -128,10 +140,10 @@ __device__ __forceinline__ void crow_fwd(float2* row, int h, const float2* tw) {
   {
     float2 x[G::M];
 #pragma unroll
-    for (int i = 0; i < G::M; ++i) x[i] = row[R * i + h];
+    for (int i = 0; i < G::M; ++i) x[i] = row[cphys<N, MR>(R * i + h)];
     fft<G::M, false>(x);
 #pragma unroll
-    for (int k = 0; k < G::M; ++k) row[R * k + h] = k == 0 ? x[0] : cmul(x[k], tw[2 * h * k]);  // W_L^(h k)
+    for (int k = 0; k < G::M; ++k) row[cphys<N, MR>(R * k + h)] = k == 0 ? x[0] : cmul(x[k], tw[2 * h * k]);  // W_L^(h k)
   }
   __syncwarp();
   for (int u = h; u <= G::M / 2; u += R) {  // butterfly unit k' = u with its mirror v = M - u
@@ -139,11 +151,11 @@ __device__ __forceinline__ void crow_fwd(float2* row, int h, const float2* tw) {
     const bool two = u != 0 && u != G::M / 2;
     float2 p[R], q[R];
 #pragma unroll
-    for (int j = 0; j < R; ++j) p[j] = row[R * u + j];
+    for (int j = 0; j < R; ++j) p[j] = row[cphys<N, MR>(R * u + j)];
     fft<R, false>(p);  // p[m] = C[u + M m]
     if (two) {
 #pragma unroll
-      for (int j = 0; j < R; ++j) q[j] = row[R * v + j];
+      for (int j = 0; j < R; ++j) q[j] = row[cphys<N, MR>(R * v + j)];
       fft<R, false>(q);  // q[m] = C[v + M m]
     }
     if (u == 0) {
@@ -161,10 +173,10 @@ __device__ __forceinline__ void crow_fwd(float2* row, int h, const float2* tw) {
       for (int m = 0; m < R; ++m) c_r2c_pair(p[m], q[R - 1 - m], tw[u + G::M * m]);
     }
 #pragma unroll
-    for (int m = 0; m < R; ++m) row[R * u + m] = p[m];
+    for (int m = 0; m < R; ++m) row[cphys<N, MR>(R * u + m)] = p[m];
     if (two) {
 #pragma unroll
-      for (int m = 0; m < R; ++m) row[R * v + m] = q[m];
+      for (int m = 0; m < R; ++m) row[cphys<N, MR>(R * v + m)] = q[m];
     }
   }
 }
@@ -179,10 +191,10 @@ __device__ __forceinline__ void crow_inv(float2* row, int h, const float2* tw) {
     const bool two = u != 0 && u != G::M / 2;
     float2 p[R], q[R];
 #pragma unroll
-    for (int m = 0; m < R; ++m) p[m] = row[R * u + m];
+    for (int m = 0; m < R; ++m) p[m] = row[cphys<N, MR>(R * u + m)];
     if (two) {
 #pragma unroll
-      for (int m = 0; m < R; ++m) q[m] = row[R * v + m];
+      for (int m = 0; m < R; ++m) q[m] = row[cphys<N, MR>(R * v + m)];
     }
     if (u == 0) {
       p[0] = make_float2(p[0].x + p[0].y, p[0].x - p[0].y);
@@ -200,20 +212,20 @@ __device__ __forceinline__ void crow_inv(float2* row, int h, const float2* tw) {
     }
     fft<R, true>(p);  // p[j] = sum_m exp(+2 pi i j m / R) C'[u + M m]
 #pragma unroll
-    for (int j = 0; j < R; ++j) row[R * u + j] = j == 0 ? p[0] : cmul(p[j], cconj(tw[2 * j * u]));
+    for (int j = 0; j < R; ++j) row[cphys<N, MR>(R * u + j)] = j == 0 ? p[0] : cmul(p[j], cconj(tw[2 * j * u]));
     if (two) {
       fft<R, true>(q);
 #pragma unroll
-      for (int j = 0; j < R; ++j) row[R * v + j] = j == 0 ? q[0] : cmul(q[j], cconj(tw[2 * j * v]));
+      for (int j = 0; j < R; ++j) row[cphys<N, MR>(R * v + j)] = j == 0 ? q[0] : cmul(q[j], cconj(tw[2 * j * v]));
     }
   }
   __syncwarp();
   float2 x[G::M];
 #pragma unroll
-  for (int k = 0; k < G::M; ++k) x[k] = row[R * k + h];
+  for (int k = 0; k < G::M; ++k) x[k] = row[cphys<N, MR>(R * k + h)];
   fft<G::M, true>(x);
 #pragma unroll
-  for (int i = 0; i < G::M; ++i) row[R * i + h] = x[i];
+  for (int i = 0; i < G::M; ++i) row[cphys<N, MR>(R * i + h)] = x[i];
 }
 
 // t-draw of global row y on its staged row: t = a + q (q s + sqrt(tau) xi), table aq[x*H + ty] =
@@ -229,15 +241,15 @@ __device__ __forceinline__ void ct_draw(float2* row, int y, int ty, int h, const
   for (int q = h; q < G::W / 4; q += G::R) {
     float z[4];
     normals4(uint32_t(y * (G::W / 4) + q), step, chain, ts, k0, k1, z);
-    float2 p0 = row[2 * q], p1 = row[2 * q + 1];
+    float2 p0 = row[cphys<N, MR>(2 * q)], p1 = row[cphys<N, MR>(2 * q + 1)];
     const float2 c0 = ldk(aq + (4 * q) * G::H + ty, pol), c1 = ldk(aq + (4 * q + 1) * G::H + ty, pol);
     const float2 c2 = ldk(aq + (4 * q + 2) * G::H + ty, pol), c3 = ldk(aq + (4 * q + 3) * G::H + ty, pol);
     p0.x = fmaf(c0.y, fmaf(c0.y, p0.x, sqrt_tau * z[0]), c0.x);
     p0.y = fmaf(c1.y, fmaf(c1.y, p0.y, sqrt_tau * z[1]), c1.x);
     p1.x = fmaf(c2.y, fmaf(c2.y, p1.x, sqrt_tau * z[2]), c2.x);
     p1.y = fmaf(c3.y, fmaf(c3.y, p1.y, sqrt_tau * z[3]), c3.x);
-    row[2 * q] = p0;
-    row[2 * q + 1] = p1;
+    row[cphys<N, MR>(2 * q)] = p0;
+    row[cphys<N, MR>(2 * q + 1)] = p1;
   }
 }
 
@@ -249,25 +261,27 @@ template <int N, int MR>
 __device__ __forceinline__ void ccol_fwd(float2* rows, int t, int b, const float2* tw) {
   using G = CGeo<N, MR>;
   float2 x[G::M];
+  const int pt = cphys<N, MR>(t);
 #pragma unroll
-  for (int a = 0; a < G::M; ++a) x[a] = rows[a * G::SP + t];
+  for (int a = 0; a < G::M; ++a) x[a] = rows[a * G::SP + pt];
   fft<G::M, false>(x);
 #pragma unroll
-  for (int k = 0; k < G::M; ++k) rows[k * G::SP + t] = k == 0 ? x[0] : cmul(x[k], tw[b * k]);
+  for (int k = 0; k < G::M; ++k) rows[k * G::SP + pt] = k == 0 ? x[0] : cmul(x[k], tw[b * k]);
 }
 // local inverse: untwiddle by W_N^(-b k'), inverse M-point FFT back to the rows
 template <int N, int MR>
 __device__ __forceinline__ void ccol_inv(float2* rows, int t, int b, const float2* tw) {
   using G = CGeo<N, MR>;
   float2 x[G::M];
+  const int pt = cphys<N, MR>(t);
 #pragma unroll
   for (int k = 0; k < G::M; ++k) {
-    const float2 v = rows[k * G::SP + t];
+    const float2 v = rows[k * G::SP + pt];
     x[k] = k == 0 ? v : cmul(v, cconj(tw[b * k]));
   }
   fft<G::M, true>(x);
 #pragma unroll
-  for (int a = 0; a < G::M; ++a) rows[a * G::SP + t] = x[a];
+  for (int a = 0; a < G::M; ++a) rows[a * G::SP + pt] = x[a];
 }
 
 // Mode coefficients of the cluster s-draw, looked up by the slot-order index i = ctab_index(ky, kx).
@@ -396,7 +410,7 @@ __device__ __forceinline__ void ccol_units(cooperative_groups::cluster_group& cl
       const int K = (t % R) * M + t / R;                         // kx held by slot t
       float2 y[P];
 #pragma unroll
-      for (int j = 0; j < P; ++j) y[j] = cl.map_shared_rank(rows, j)[uu * G::SP + t];
+      for (int j = 0; j < P; ++j) y[j] = cl.map_shared_rank(rows, j)[uu * G::SP + cphys<N, MR>(t)];
       fft<P, false>(y);  // y[m] = t_hat[uu + M m]
       if (u == 0) {      // the same in every lane of the warp
         if (half == 0) {
@@ -419,7 +433,7 @@ __device__ __forceinline__ void ccol_units(cooperative_groups::cluster_group& cl
       if (WRITE) {
         fft<P, true>(y);
 #pragma unroll
-        for (int j = 0; j < P; ++j) cl.map_shared_rank(rows, j)[uu * G::SP + t] = y[j];
+        for (int j = 0; j < P; ++j) cl.map_shared_rank(rows, j)[uu * G::SP + cphys<N, MR>(t)] = y[j];
       }
     }
     return;
@@ -429,9 +443,9 @@ __device__ __forceinline__ void ccol_units(cooperative_groups::cluster_group& cl
     const int K = (t % R) * M + t / R;  // kx held by slot t
     float2 p[P], q[P];
 #pragma unroll
-    for (int j = 0; j < P; ++j) p[j] = cl.map_shared_rank(rows, j)[u * G::SP + t];
+    for (int j = 0; j < P; ++j) p[j] = cl.map_shared_rank(rows, j)[u * G::SP + cphys<N, MR>(t)];
 #pragma unroll
-    for (int j = 0; j < P; ++j) q[j] = cl.map_shared_rank(rows, j)[v * G::SP + t];
+    for (int j = 0; j < P; ++j) q[j] = cl.map_shared_rank(rows, j)[v * G::SP + cphys<N, MR>(t)];
     fft<P, false>(p);  // p[m] = t_hat[u + M m]
     fft<P, false>(q);  // q[m] = t_hat[v + M m]
     if (u == 0) {
@@ -450,10 +464,10 @@ __device__ __forceinline__ void ccol_units(cooperative_groups::cluster_group& cl
     if (WRITE) {
       fft<P, true>(q);
 #pragma unroll
-      for (int j = 0; j < P; ++j) cl.map_shared_rank(rows, j)[v * G::SP + t] = q[j];
+      for (int j = 0; j < P; ++j) cl.map_shared_rank(rows, j)[v * G::SP + cphys<N, MR>(t)] = q[j];
       fft<P, true>(p);
 #pragma unroll
-      for (int j = 0; j < P; ++j) cl.map_shared_rank(rows, j)[u * G::SP + t] = p[j];
+      for (int j = 0; j < P; ++j) cl.map_shared_rank(rows, j)[u * G::SP + cphys<N, MR>(t)] = p[j];
     }
   }
 }
@@ -565,12 +579,12 @@ __device__ __forceinline__ void ct_update_wf(float2* row, int y, int h, const fl
   using G = CGeo<N, MR>;
   const uint64_t pol = l2_keep();
   for (int x2 = h; x2 < G::W / 2; x2 += G::R) {
-    float2 v = row[x2];
+    float2 v = row[cphys<N, MR>(x2)];
     const float2 c0 = ldk(dn + (2 * x2) * G::H + y, pol), c1 = ldk(dn + (2 * x2 + 1) * G::H + y, pol);
     const float w0 = wf_rcp(fmaf(lt_, c0.y, 1.0f)), w1 = wf_rcp(fmaf(lt_, c1.y, 1.0f));
     v.x = fmaf(w0, v.x - c0.x, c0.x);
     v.y = fmaf(w1, v.y - c1.x, c1.x);
-    row[x2] = v;
+    row[cphys<N, MR>(x2)] = v;
   }
 }
 
@@ -583,7 +597,7 @@ __device__ __forceinline__ void crhs_row(float2* row, int ty, int h, const float
   for (int x2 = h; x2 < G::W / 2; x2 += G::R) {
     const float2 c0 = WF_LDG(dn + (2 * x2) * G::H + ty), c1 = WF_LDG(dn + (2 * x2 + 1) * G::H + ty);
     const float nb0 = c0.y > 0.0f ? wf_rcp(c0.y) : wf_inf(), nb1 = c1.y > 0.0f ? wf_rcp(c1.y) : wf_inf();
-    row[x2] = make_float2(c0.x / (nb0 + lt_), c1.x / (nb1 + lt_));
+    row[cphys<N, MR>(x2)] = make_float2(c0.x / (nb0 + lt_), c1.x / (nb1 + lt_));
   }
 }
 
@@ -628,7 +642,7 @@ __device__ __forceinline__ void crows_load(float2* rows, int b, const float* src
     const int ar = e / G::L, i = e % G::L;
     float2 v = make_float2(0.f, 0.f);
     if (src != nullptr) v = WF_LDG(reinterpret_cast<const float2*>(src + (long long)(G::P * ar + b) * G::W) + i);
-    rows[ar * G::SP + i] = v;
+    rows[ar * G::SP + cphys<N, MR>(i)] = v;
   }
 }
 
@@ -639,7 +653,7 @@ __device__ __forceinline__ void crows_store(const float2* rows, int b, void* dst
   for (int e = lt; e < G::A * G::L; e += G::L) {
     const int r2 = e / G::L, i = e % G::L;
     const long long at = (long long)(G::P * r2 + b) * G::L + i;
-    const float2 v = rows[r2 * G::SP + i];
+    const float2 v = rows[r2 * G::SP + cphys<N, MR>(i)];
     if (t == kOutF32) {
       __stcs(reinterpret_cast<float2*>(dst) + at, v);  // evict-first: the samples are not read again
     } else {

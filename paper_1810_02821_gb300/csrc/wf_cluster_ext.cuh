@@ -200,7 +200,7 @@ __device__ __forceinline__ void ccol_units2(cooperative_groups::cluster_group& c
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
 #pragma unroll
-        for (int j = 0; j < P; ++j) y[c][j] = cl.map_shared_rank(rows + c * CS, j)[uu * G::SP + t];
+        for (int j = 0; j < P; ++j) y[c][j] = cl.map_shared_rank(rows + c * CS, j)[uu * G::SP + cphys<N, MR>(t)];
         fft<P, false>(y[c]);
       }
       if (u == 0) {  // the same in every lane of the warp
@@ -229,7 +229,7 @@ __device__ __forceinline__ void ccol_units2(cooperative_groups::cluster_group& c
       for (int c = 0; c < 2; ++c) {
         fft<P, true>(y[c]);
 #pragma unroll
-        for (int j = 0; j < P; ++j) cl.map_shared_rank(rows + c * CS, j)[uu * G::SP + t] = y[c][j];
+        for (int j = 0; j < P; ++j) cl.map_shared_rank(rows + c * CS, j)[uu * G::SP + cphys<N, MR>(t)] = y[c][j];
       }
     }
     return;
@@ -242,9 +242,9 @@ __device__ __forceinline__ void ccol_units2(cooperative_groups::cluster_group& c
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
 #pragma unroll
-      for (int j = 0; j < P; ++j) p[c][j] = cl.map_shared_rank(rows + c * CS, j)[u * G::SP + t];
+      for (int j = 0; j < P; ++j) p[c][j] = cl.map_shared_rank(rows + c * CS, j)[u * G::SP + cphys<N, MR>(t)];
 #pragma unroll
-      for (int j = 0; j < P; ++j) q[c][j] = cl.map_shared_rank(rows + c * CS, j)[v * G::SP + t];
+      for (int j = 0; j < P; ++j) q[c][j] = cl.map_shared_rank(rows + c * CS, j)[v * G::SP + cphys<N, MR>(t)];
       fft<P, false>(p[c]);
       fft<P, false>(q[c]);
     }
@@ -266,10 +266,10 @@ __device__ __forceinline__ void ccol_units2(cooperative_groups::cluster_group& c
     for (int c = 0; c < 2; ++c) {
       fft<P, true>(q[c]);
 #pragma unroll
-      for (int j = 0; j < P; ++j) cl.map_shared_rank(rows + c * CS, j)[v * G::SP + t] = q[c][j];
+      for (int j = 0; j < P; ++j) cl.map_shared_rank(rows + c * CS, j)[v * G::SP + cphys<N, MR>(t)] = q[c][j];
       fft<P, true>(p[c]);
 #pragma unroll
-      for (int j = 0; j < P; ++j) cl.map_shared_rank(rows + c * CS, j)[u * G::SP + t] = p[c][j];
+      for (int j = 0; j < P; ++j) cl.map_shared_rank(rows + c * CS, j)[u * G::SP + cphys<N, MR>(t)] = p[c][j];
     }
   }
 }

@@ -196,3 +196,23 @@ def test_mode_tables_in_slot_order(N, M):
             else:
                 pos.append(H * L + ky)
     assert sorted(pos) == list(range(H * (L + 1)))
+
+
+def test_row_swizzle_of_the_512_cluster_rows_is_conflict_free():
+    """512^2 with 32 rows per CTA (R = 8 threads per row): the slot map s -> s ^ ((s >> 3) & 3) used for the
+    staged rows is a bijection, and a half-warp's float2 reads (4 rows x 4 threads of a row, row stride
+    L + R/2) fall in 16 distinct bank pairs both in the strided M-point pass (slot R i + h) and in the
+    radix-R butterflies (slot R u + j, u = h + R k)."""
+    def phys(s):
+        return s ^ ((s >> 3) & 3)
+    L, R, M = 256, 8, 32
+    SP = L + R // 2
+    assert sorted(phys(s) for s in range(L)) == list(range(L))
+    rows_per_warp = 32 // R
+    for i in range(M):
+        banks = {(a * SP + phys(R * i + h)) % 16 for a in range(rows_per_warp) for h in range(4)}
+        assert len(banks) == 16
+    for k in range((M // 2 + 1 + R - 1) // R):
+        for j in range(R):
+            banks = {(a * SP + phys(R * (h + R * k) + j)) % 16 for a in range(rows_per_warp) for h in range(4)}
+            assert len(banks) == 16
