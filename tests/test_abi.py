@@ -150,3 +150,19 @@ def test_sample_output_type_validated_without_gpu(lib):
 
 def test_selftest_argument_check_without_gpu(lib):
     assert lib.wf_selftest_wait_timeout(0, None) == 1
+
+
+def test_band_and_spin2_size_and_bin_checks_without_gpu(lib):
+    """The hierarchical and spin-2 calls take sizes up to 512 x 512 and at most 256 bands up to 256 x 256
+    (512 at 512 x 512); larger requests are refused before any CUDA call."""
+    p = ctypes.c_void_p(16)
+    o = wf.SampleOpts()
+    lib.wf_sample_opts_default(ctypes.byref(o))
+    o.n_samples = 1
+    band = lib.wf_sample_band
+    assert band(p, p, p, p, p, 4, p, 1024, 1024, 0, ctypes.byref(o), p, None, None) == 3
+    assert band(p, p, p, p, p, 257, p, 256, 256, 0, ctypes.byref(o), p, None, None) == 1
+    assert band(p, p, p, p, p, 513, p, 512, 512, 0, ctypes.byref(o), p, None, None) == 1
+    assert band(p, p, p, p, p, 257, p, 128, 128, 0, ctypes.byref(o), p, None, None) == 1
+    assert lib.wf_sample_spin2(p, p, p, p, p, p, p, 1024, 1024, 0, ctypes.byref(o), p, None) == 3
+    assert lib.wf_solve_spin2(p, p, p, p, p, p, p, 1024, 1024, None, p, None, None, None) == 3
