@@ -165,9 +165,9 @@ wf_status wf_sample_ex(const float* d, const float* Ndiag, const uint8_t* mask, 
  * P_b = S_b / X_b where X_b sums n_b squared normals from Philox stream 6 in the counter layout of the
  * s-draw (a complex mode pair gives Re^2 + Im^2, a self-conjugate mode one square). out_P (device float32
  * [n_chains][n_samples][n_bins], may be NULL) receives the band powers of each kept sample (drawn in the
- * same sweep). opts and out as for wf_sample_ex (opts->A must be NULL). Sizes up to 512 x 512 (256 and
- * 512: one thread-block cluster per chain, the cluster sampler of wf_sample_ex with the band draw added;
- * WF_ERR_CUDA with cudaErrorNotSupported where the device cannot host such a cluster);
+ * same sweep). opts and out as for wf_sample_ex (a pixel response opts->A included). Sizes up to
+ * 512 x 512 (256 and 512: one thread-block cluster per chain, the cluster sampler of wf_sample_ex with the
+ * band draw added; WF_ERR_CUDA with cudaErrorNotSupported where the device cannot host such a cluster);
  * 0 <= n_bins <= 256 (512 at 512 x 512). A bin outside [-1, n_bins) or a negative or non-finite P0:
  * WF_ERR_ARG. The band sums S_b and X_b are FP32 sums in a fixed order, so a repeated call is
  * bit-identical. Scratch: one statistics buffer of 8 bytes per half-spectrum mode for every chain (up to
@@ -190,7 +190,8 @@ wf_status wf_sample_band(const float* d, const float* Ndiag, const uint8_t* mask
  * [n_chains][n_samples][2][H][W] shear samples (element type opts->out_dtype); opts->init_s, when given,
  * is [2][H][W] (or [n_chains][2][H][W] with init_per_chain). Sizes up to 512 x 512 (256 and 512: both
  * components of a chain in one thread-block cluster of 32-row CTAs; WF_ERR_CUDA with
- * cudaErrorNotSupported where the device cannot host such a cluster); opts->A must be NULL.
+ * cudaErrorNotSupported where the device cannot host such a cluster). opts->A, when given, is one pixel
+ * response for both components (as in wf_sample_ex: d_c = A gamma_c + n_c, A = 0 meaning no data).
  */
 wf_status wf_sample_spin2(const float* d1, const float* d2, const float* N1, const float* N2, const uint8_t* mask,
                           const float* PE, const float* PB, int32_t H, int32_t W, uint64_t seed,

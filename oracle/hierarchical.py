@@ -62,16 +62,17 @@ def band_power_draw(sh_full: np.ndarray, zb_full: np.ndarray, bins_full: np.ndar
 
 
 def sample(d, Ndiag, mask, Pk, bins, P0, n_samples: int, seed: int, *, chain: int = 0, tau: float | None = None,
-           burn_in: int = 0, thin: int = 1, init_s=None):
+           burn_in: int = 0, thin: int = 1, init_s=None, A=None):
     """Hierarchical chain -> (samples [n_samples][H][W], band powers [n_samples][n_bins]).
 
-    Sweep i (counter step i): t-draw; s-draw with P_k = P_b(k) (bins >= 0) or Pk (bins = -1); band-power
-    draw from the new s. Sample m = (s, P) after sweep burn_in + (m+1)*thin.
+    Sweep i (counter step i): t-draw (with the diagonal response A when given, as in ``messenger``);
+    s-draw with P_k = P_b(k) (bins >= 0) or Pk (bins = -1); band-power draw from the new s. Sample m =
+    (s, P) after sweep burn_in + (m+1)*thin.
     """
-    d, N, miss, Pfix = _fields(d, Ndiag, mask, Pk)
+    d, N, miss, Pfix = _fields(d, Ndiag, mask, Pk, A)
     H, W = d.shape
     if tau is None:
-        tau = default_tau(N, miss, Pk)
+        tau = default_tau(N, miss, Pk, A)
     bins = np.asarray(bins)
     bf = full_bins(bins, W)
     n_bins = len(P0)
@@ -82,7 +83,7 @@ def sample(d, Ndiag, mask, Pk, bins, P0, n_samples: int, seed: int, *, chain: in
     m = 0
     for i in range(burn_in + n_samples * thin):
         Pfull = np.where(bf >= 0, Pb[np.clip(bf, 0, None)], Pfix) if n_bins else Pfix
-        t = pixel_update(s, d, N, miss, tau, 1.0, draw_xi(seed, chain, i, H, W))
+        t = pixel_update(s, d, N, miss, tau, 1.0, draw_xi(seed, chain, i, H, W), A=A)
         th = dft.dft2(t)
         sh = Pfull / (Pfull + tau) * th + np.sqrt(Pfull * tau / (Pfull + tau)) * draw_zeta(seed, chain, i, H, W)
         s = dft.idft2(sh).real

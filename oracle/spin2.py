@@ -69,10 +69,11 @@ def _spectra(PE, PB, W):
     return dft.half_to_full(np.asarray(PE, np.float64), W), dft.half_to_full(np.asarray(PB, np.float64), W)
 
 
-def sweep(g1, g2, d1, d2, N1, N2, miss, PEf, PBf, c, s, tau, xi=None, zeta=None):
-    """One Alg. 1 sweep of the pair; xi = (xi1, xi2), zeta = (zeta_E, zeta_B) or None (G -> 0)."""
-    t1 = pixel_update(g1, d1, N1, miss, tau, 1.0, None if xi is None else xi[0])
-    t2 = pixel_update(g2, d2, N2, miss, tau, 1.0, None if xi is None else xi[1])
+def sweep(g1, g2, d1, d2, N1, N2, miss, PEf, PBf, c, s, tau, xi=None, zeta=None, A=None):
+    """One Alg. 1 sweep of the pair; xi = (xi1, xi2), zeta = (zeta_E, zeta_B) or None (G -> 0); A: one
+    diagonal pixel response for both components, or None."""
+    t1 = pixel_update(g1, d1, N1, miss, tau, 1.0, None if xi is None else xi[0], A=A)
+    t2 = pixel_update(g2, d2, N2, miss, tau, 1.0, None if xi is None else xi[1], A=A)
     a, b = dft.dft2(t1), dft.dft2(t2)
     e, bb = c * a + s * b, -s * a + c * b
     e = PEf / (PEf + tau) * e
@@ -83,30 +84,30 @@ def sweep(g1, g2, d1, d2, N1, N2, miss, PEf, PBf, c, s, tau, xi=None, zeta=None)
     return dft.idft2(c * e - s * bb).real, dft.idft2(s * e + c * bb).real
 
 
-def _setup(d1, d2, N1, N2, mask, PE, PB, tau):
-    d1, N1v, miss, _ = _fields(d1, N1, mask, PE)
+def _setup(d1, d2, N1, N2, mask, PE, PB, tau, A=None):
+    d1, N1v, miss, _ = _fields(d1, N1, mask, PE, A)
     d2 = np.asarray(d2, np.float64)
     N2v = np.asarray(N2, np.float64)
     H, W = d1.shape
     if tau is None:
-        tau = min(default_tau(N1v, miss, PE), default_tau(N2v, miss, PE))
+        tau = min(default_tau(N1v, miss, PE, A), default_tau(N2v, miss, PE, A))
     PEf, PBf = _spectra(PE, PB, W)
     c, s = ks_rotation(H, W)
     return d1, d2, N1v, N2v, miss, PEf, PBf, c, s, tau
 
 
 def sample(d1, d2, N1, N2, mask, PE, PB, n_samples: int, seed: int, *, chain: int = 0, tau: float | None = None,
-           init=None):
+           init=None, A=None):
     """Spin-2 chain from gamma = 0 (or init = (g1, g2)) -> [n_samples][2][H][W] shear samples; sweep i uses
-    counter step i."""
-    d1, d2, N1v, N2v, miss, PEf, PBf, c, s, tau = _setup(d1, d2, N1, N2, mask, PE, PB, tau)
+    counter step i; A: one diagonal pixel response for both components (None: A = I)."""
+    d1, d2, N1v, N2v, miss, PEf, PBf, c, s, tau = _setup(d1, d2, N1, N2, mask, PE, PB, tau, A)
     H, W = d1.shape
     g1, g2 = (np.zeros((H, W)), np.zeros((H, W))) if init is None else (np.array(init[0], float), np.array(init[1], float))
     out = np.empty((n_samples, 2, H, W))
     for i in range(n_samples):
         xi = (draw_xi(seed, chain, i, H, W, STREAM_T), draw_xi(seed, chain, i, H, W, STREAM_T2))
         ze = (draw_zeta(seed, chain, i, H, W, STREAM_S), draw_zeta(seed, chain, i, H, W, STREAM_SB))
-        g1, g2 = sweep(g1, g2, d1, d2, N1v, N2v, miss, PEf, PBf, c, s, tau, xi, ze)
+        g1, g2 = sweep(g1, g2, d1, d2, N1v, N2v, miss, PEf, PBf, c, s, tau, xi, ze, A)
         out[i, 0], out[i, 1] = g1, g2
     return out
 

@@ -950,7 +950,7 @@ wf_status wf_sample_band(const float* d, const float* Ndiag, const uint8_t* mask
   const wf_sample_opts o = *opts;
   if (!d || !Ndiag || !mask || !Pk || !bins || (n_bins > 0 && !P0)) return WF_ERR_ARG;
   if (!size_ok(H, W) || H > 512) return WF_ERR_SHAPE;
-  if (n_bins < 0 || n_bins > band_max_bins(H) || o.A) return WF_ERR_ARG;
+  if (n_bins < 0 || n_bins > band_max_bins(H)) return WF_ERR_ARG;
   if (o.n_samples < 0 || o.n_chains < 1 || o.burn_in < 0 || o.thin < 1) return WF_ERR_ARG;
   if (o.out_dtype < WF_OUT_F32 || o.out_dtype > WF_OUT_F16) return WF_ERR_ARG;
   if (o.n_samples == 0) return WF_OK;
@@ -958,6 +958,13 @@ wf_status wf_sample_band(const float* d, const float* Ndiag, const uint8_t* mask
   const long long sweeps = (long long)o.burn_in + o.n_samples * (long long)o.thin;
   if (sweeps > 0x7fffffffLL || o.n_samples > 0x7fffffffLL) return WF_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Response resp;  // a pixel response A: data d / A and noise N / A^2, A = 0 as missing (as wf_sample_ex)
+  if (o.A) {
+    WF_CUDA(apply_response(d, Ndiag, mask, o.A, size_t(H) * W, st, &resp));
+    d = resp.d;
+    Ndiag = resp.Nd;
+    mask = resp.mask;
+  }
   const size_t n = size_t(H) * W, nm = size_t(H) * (W / 2 + 1);
   // the band-sum plan, and one statistics buffer per field of the grid (up to 128^2) or per cluster (256
   // and 512: thread-block clusters, as many as can be resident, each looping over chains, with tables in
@@ -1054,13 +1061,23 @@ wf_status wf_sample_spin2(const float* d1, const float* d2, const float* N1, con
   const wf_sample_opts o = *opts;
   if (!d1 || !d2 || !N1 || !N2 || !mask || !PE || !PB) return WF_ERR_ARG;
   if (!size_ok(H, W) || H > 512) return WF_ERR_SHAPE;
-  if (o.A || o.n_samples < 0 || o.n_chains < 1 || o.burn_in < 0 || o.thin < 1) return WF_ERR_ARG;
+  if (o.n_samples < 0 || o.n_chains < 1 || o.burn_in < 0 || o.thin < 1) return WF_ERR_ARG;
   if (o.out_dtype < WF_OUT_F32 || o.out_dtype > WF_OUT_F16) return WF_ERR_ARG;
   if (o.n_samples == 0) return WF_OK;
   if (!out || !out_ptr_ok(out)) return WF_ERR_ARG;
   const long long sweeps = (long long)o.burn_in + o.n_samples * (long long)o.thin;
   if (sweeps > 0x7fffffffLL || o.n_samples > 0x7fffffffLL) return WF_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Response r1, r2;  // one pixel response A for both components (the same mask results for both)
+  if (o.A) {
+    WF_CUDA(apply_response(d1, N1, mask, o.A, size_t(H) * W, st, &r1));
+    WF_CUDA(apply_response(d2, N2, mask, o.A, size_t(H) * W, st, &r2));
+    d1 = r1.d;
+    N1 = r1.Nd;
+    d2 = r2.d;
+    N2 = r2.Nd;
+    mask = r1.mask;
+  }
   const size_t n = size_t(H) * W, nm = size_t(H) * (W / 2 + 1);
   Carve cv;
   const size_t o_sc = cv.take<wf::Scalars>(2), o_aq = cv.take<float2>(2 * n), o_fe = cv.take<float2>(nm),

@@ -297,10 +297,10 @@ def wf_sample_ex(d, Ndiag, mask, Pk, seed: int, n_samples: int, *, n_chains: int
 
 def wf_sample_band(d, Ndiag, mask, Pk, bins, P0, seed: int, n_samples: int, *, n_chains: int = 1,
                    chain_offset: int = 0, start_step: int = 0, burn_in: int = 0, thin: int = 1, tau: float = 0.0,
-                   init_s=None, out_dtype: str = "f32", keep_P: bool = True, stream=None):
+                   init_s=None, A=None, out_dtype: str = "f32", keep_P: bool = True, stream=None):
     """Hierarchical Gibbs sampler (C call ``wf_sample_band``): samples [chains][n][H][W] and band powers
     [chains][n][n_bins] (None unless ``keep_P``). ``bins``: CUDA int32 [H][W/2+1] (-1: power from Pk);
-    ``P0``: CUDA float32 [n_bins] initial band powers."""
+    ``P0``: CUDA float32 [n_bins] initial band powers; ``A``: optional pixel response [H][W]."""
     import torch
     L = load_library()
     H, W, pd, pn, pm, pp = _inputs(d, Ndiag, mask, Pk)
@@ -320,6 +320,7 @@ def wf_sample_band(d, Ndiag, mask, Pk, bins, P0, seed: int, n_samples: int, *, n
         o.init_s = _dev(init_s, torch.float32, (n_chains, H, W) if per_chain else (H, W), "init_s").value
         o.init_per_chain = 1 if per_chain else 0
     o.out_dtype = code
+    o.A = _dev(A, torch.float32, (H, W), "A").value if A is not None else None
     st = L.wf_sample_band(pd, pn, pm, pp, pb, n_bins, p0, H, W, int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(o),
                           ctypes.c_void_p(out.data_ptr()),
                           ctypes.c_void_p(outP.data_ptr()) if outP is not None else None, _stream_ptr(stream))
@@ -329,8 +330,9 @@ def wf_sample_band(d, Ndiag, mask, Pk, bins, P0, seed: int, n_samples: int, *, n
 
 def wf_sample_spin2(d1, d2, N1, N2, mask, PE, PB, seed: int, n_samples: int, *, n_chains: int = 1,
                     chain_offset: int = 0, start_step: int = 0, burn_in: int = 0, thin: int = 1, tau: float = 0.0,
-                    init=None, out_dtype: str = "f32", stream=None):
-    """Spin-2 (shear) sampler (C call ``wf_sample_spin2``) -> shear samples [chains][n][2][H][W]."""
+                    init=None, A=None, out_dtype: str = "f32", stream=None):
+    """Spin-2 (shear) sampler (C call ``wf_sample_spin2``) -> shear samples [chains][n][2][H][W]; ``A``:
+    optional pixel response [H][W] of both components."""
     import torch
     L = load_library()
     H, W, pd1, pn1, pm, pe = _inputs(d1, N1, mask, PE)
@@ -349,6 +351,7 @@ def wf_sample_spin2(d1, d2, N1, N2, mask, PE, PB, seed: int, n_samples: int, *, 
         o.init_s = _dev(init, torch.float32, (n_chains, 2, H, W) if per_chain else (2, H, W), "init").value
         o.init_per_chain = 1 if per_chain else 0
     o.out_dtype = code
+    o.A = _dev(A, torch.float32, (H, W), "A").value if A is not None else None
     st = L.wf_sample_spin2(pd1, pd2, pn1, pn2, pm, pe, pb, H, W, int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(o),
                            ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream))
     _check(st, "wf_sample_spin2")

@@ -172,3 +172,21 @@ def test_band_sampler_empty_band(H):
     assert np.all(Ps[0, :, nb] == 0.0) and np.all(rP[:, nb] == 0.0)
     for m in range(2):
         assert rel(xs[0, m].cpu().numpy(), rs[m]) < SAMPLE_TOL and rel(Ps[0, m], rP[m]) < SAMPLE_TOL
+
+
+@pytest.mark.parametrize("H", [64, 256])
+def test_band_sampler_with_pixel_response(H):
+    """A diagonal pixel response A (with a few A = 0 pixels): samples and band powers follow the oracle's
+    general t-update draw for draw."""
+    p = synth.make_problem(H, seed=H + 23, mask_frac=0.1, slope=-2.0, k0=1.0 / 32, sigma2=(0.05, 0.5))
+    rng = np.random.default_rng(H)
+    A = rng.uniform(0.5, 1.5, (H, H)).astype(np.float32)
+    A[rng.integers(0, H, 5), rng.integers(0, H, 5)] = 0.0
+    bins, nb = HG.radial_bins(H, H)
+    P0 = np.full(nb, 0.5, np.float32)
+    xs, Ps = wf.wf_sample_band(*to_dev(p), torch.from_numpy(bins).cuda(), torch.from_numpy(P0).cuda(), seed=6,
+                               n_samples=2, A=torch.from_numpy(A).cuda())
+    rs, rP = HG.sample(p.d, p.Ndiag, p.mask, p.Pk, bins, P0, 2, seed=6, A=A)
+    for m in range(2):
+        assert rel(xs[0, m].cpu().numpy(), rs[m]) < SAMPLE_TOL, (H, m, rel(xs[0, m].cpu().numpy(), rs[m]))
+        assert rel(Ps[0, m].cpu().numpy(), rP[m]) < SAMPLE_TOL

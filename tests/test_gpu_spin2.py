@@ -105,6 +105,22 @@ def test_spin2_sampler_large_per_chain_init_and_bf16():
         assert rel(f32[1, 0, comp].cpu().numpy(), ref[0, comp]) < SAMPLE_TOL
 
 
+@pytest.mark.parametrize("H", [64, 256])
+def test_spin2_sampler_with_pixel_response(H):
+    """One pixel response A for both shear components (a few A = 0 pixels): draw for draw against the
+    oracle's general t-update."""
+    p, d2, N2, PB = _pair(H, H + 13)
+    rng = np.random.default_rng(H + 1)
+    A = rng.uniform(0.5, 1.5, (H, H)).astype(np.float32)
+    A[rng.integers(0, H, 5), rng.integers(0, H, 5)] = 0.0
+    got = wf.wf_sample_spin2(*_dev(p.d, d2, p.Ndiag, N2, p.mask, p.Pk, PB), seed=7, n_samples=2,
+                             A=torch.from_numpy(A).cuda()).cpu().numpy()
+    ref = S2.sample(p.d, d2, p.Ndiag, N2, p.mask, p.Pk, PB, 2, seed=7, A=A)
+    for m in range(2):
+        for comp in range(2):
+            assert rel(got[0, m, comp], ref[m, comp]) < SAMPLE_TOL, (H, m, comp, rel(got[0, m, comp], ref[m, comp]))
+
+
 def test_shear_to_convergence_matches_oracle():
     rng = np.random.default_rng(3)
     for H in (16, 128, 256):

@@ -104,3 +104,33 @@ def test_band_draw_noise_is_independent_of_the_signal_draw():
         a.append(np.sum(np.abs(zs[bf >= 0]) ** 2))
         b.append(np.sum(np.abs(zb[bf >= 0]) ** 2))
     assert abs(np.corrcoef(a, b)[0, 1]) < 0.25
+
+
+def test_pixel_response_reductions():
+    """With a pixel response A the hierarchical chain follows the general t-update: A = 1 gives the chain
+    without A, and A = 0 at a pixel gives the chain with that pixel masked; a constant A = c equals the
+    A = 1 chain for data d / c and noise N / c^2 (the response's exact rescaling)."""
+    H = 16
+    p = synth.make_problem(H, seed=8, mask_frac=0.1, slope=-2.0, k0=1.0 / H, sigma2=(0.05, 0.5))
+    bins, nb = HG.radial_bins(H, H)
+    P0 = np.full(nb, 0.5)
+    ref = HG.sample(p.d, p.Ndiag, p.mask, p.Pk, bins, P0, 3, seed=2)
+    one = HG.sample(p.d, p.Ndiag, p.mask, p.Pk, bins, P0, 3, seed=2, A=np.ones((H, H)))
+    for a, b in zip(ref, one):
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-12)
+    A = np.ones((H, H))
+    A[3, 5] = 0.0
+    m2 = p.mask.copy()
+    m2[3, 5] = 1
+    zero = HG.sample(p.d, p.Ndiag, p.mask, p.Pk, bins, P0, 3, seed=2, A=A)
+    masked = HG.sample(p.d, p.Ndiag, m2, p.Pk, bins, P0, 3, seed=2)
+    for a, b in zip(zero, masked):
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-12)
+    c = 1.7
+    scaled = HG.sample(p.d, p.Ndiag, p.mask, p.Pk, bins, P0, 3, seed=2, A=np.full((H, H), c))
+    plain = HG.sample(p.d.astype(np.float64) / c, p.Ndiag.astype(np.float64) / c ** 2, p.mask, p.Pk, bins, P0, 3,
+                      seed=2)
+    # (at the pixel that sets tau, N_bar = N - A^2 tau is a rounding residue instead of an exact 0, and its
+    # square root scales a noise draw: agreement to about 1e-8 of the field, where a wrong scaling is O(1))
+    for a, b in zip(scaled, plain):
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-7 * np.abs(b).max())

@@ -90,3 +90,20 @@ def test_covariance_application_and_residual():
     assert abs(S2.residual(z, z, p.d, d2, p.Ndiag, N2, p.mask, p.Pk, PB) - 1.0) < 1e-14
     gw = S2.wiener_dense(p.d, d2, p.Ndiag, N2, p.mask, p.Pk, 1.5 * PB)
     assert S2.residual(*gw, p.d, d2, p.Ndiag, N2, p.mask, p.Pk, PB) > 1e-3
+
+
+def test_spin2_pixel_response_reductions():
+    """A = 1 gives the spin-2 chain without A; A = 0 at a pixel equals masking it in both components."""
+    H = 8
+    p, d2, N2 = _pair(H, 9)
+    PB = 0.3 * p.Pk
+    ref = S2.sample(p.d, d2, p.Ndiag, N2, p.mask, p.Pk, PB, 2, seed=4)
+    one = S2.sample(p.d, d2, p.Ndiag, N2, p.mask, p.Pk, PB, 2, seed=4, A=np.ones((H, H)))
+    np.testing.assert_allclose(ref, one, rtol=0, atol=1e-12)
+    A = np.ones((H, H))
+    A[2, 6] = 0.0
+    m2 = p.mask.copy()
+    m2[2, 6] = 1
+    zero = S2.sample(p.d, d2, p.Ndiag, N2, p.mask, p.Pk, PB, 2, seed=4, A=A)
+    masked = S2.sample(p.d, d2, p.Ndiag, N2, m2, p.Pk, PB, 2, seed=4)
+    np.testing.assert_allclose(zero, masked, rtol=0, atol=1e-12)
