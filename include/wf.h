@@ -205,7 +205,8 @@ wf_status wf_sample_spin2(const float* d1, const float* d2, const float* N1, con
  * the E/B spectra) is evaluated every opts->check sweeps until it is below opts->tol or opts->max_iter
  * sweeps have run (WF_ERR_NOT_CONVERGED). out: device [2][H][W]; iters_out, resid_out: HOST, may be NULL.
  * Sizes up to 512 x 512 (256 and 512 on wf_sample_spin2's thread-block clusters); opts may be NULL
- * (defaults); opts->refine, init_s and A are not used.
+ * (defaults); opts->A, when given, is one pixel response for both components (the filter and its residual
+ * are those of the response problem); opts->refine and init_s are not used.
  */
 wf_status wf_solve_spin2(const float* d1, const float* d2, const float* N1, const float* N2, const uint8_t* mask,
                          const float* PE, const float* PB, int32_t H, int32_t W, const wf_solve_opts* opts, float* out,

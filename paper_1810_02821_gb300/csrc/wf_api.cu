@@ -1177,6 +1177,19 @@ wf_status wf_solve_spin2(const float* d1, const float* d2, const float* N1, cons
   if (!(o.tol > 0.0) || !(o.eta > 0.0 && o.eta < 1.0) || o.level_max < 1 || o.check < 1 || o.max_iter < 1)
     return WF_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // a pixel response A (one for both components): the Wiener filter of (d / A, N / A^2, A = 0 as missing)
+  // is that of the response problem, and so is its relative residual (both are A-weighted forms of the
+  // same system), so the solve and its FP64 residual run on the transformed data
+  Response r1, r2;
+  if (o.A) {
+    WF_CUDA(apply_response(d1, N1, mask, o.A, size_t(H) * W, st, &r1));
+    WF_CUDA(apply_response(d2, N2, mask, o.A, size_t(H) * W, st, &r2));
+    d1 = r1.d;
+    N1 = r1.Nd;
+    d2 = r2.d;
+    N2 = r2.Nd;
+    mask = r1.mask;
+  }
   const size_t n = size_t(H) * W, nm = size_t(H) * (W / 2 + 1);
   Carve cv;
   const size_t o_sc = cv.take<wf::Scalars>(3), o_aq = cv.take<float2>(2 * n), o_fe = cv.take<float2>(nm),

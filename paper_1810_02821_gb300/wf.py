@@ -360,8 +360,9 @@ def wf_sample_spin2(d1, d2, N1, N2, mask, PE, PB, seed: int, n_samples: int, *, 
 
 def wf_solve_spin2(d1, d2, N1, N2, mask, PE, PB, *, tol: float = 1e-5, tau: float = 0.0, eta: float = 0.5,
                    level_sweeps: int = 64, check: int = 16, max_iter: int = 50000, allow_not_converged: bool = False,
-                   stream=None) -> SolveResult:
-    """Wiener filter of a shear pair (C call ``wf_solve_spin2``) -> SolveResult with s = [2][H][W]."""
+                   A=None, stream=None) -> SolveResult:
+    """Wiener filter of a shear pair (C call ``wf_solve_spin2``) -> SolveResult with s = [2][H][W]; ``A``:
+    optional pixel response [H][W] of both components."""
     import torch
     L = load_library()
     H, W, pd1, pn1, pm, pe = _inputs(d1, N1, mask, PE)
@@ -373,6 +374,7 @@ def wf_solve_spin2(d1, d2, N1, N2, mask, PE, PB, *, tol: float = 1e-5, tau: floa
     L.wf_solve_opts_default(ctypes.byref(o))
     o.tau, o.tol, o.eta = float(tau), float(tol), float(eta)
     o.level_max, o.check, o.max_iter = int(level_sweeps), int(check), int(max_iter)
+    o.A = _dev(A, torch.float32, (H, W), "A").value if A is not None else None
     it = ctypes.c_int32(0)
     rs = ctypes.c_double(0.0)
     st = L.wf_solve_spin2(pd1, pd2, pn1, pn2, pm, pe, pb, H, W, ctypes.byref(o), ctypes.c_void_p(out.data_ptr()),

@@ -121,6 +121,34 @@ def test_spin2_sampler_with_pixel_response(H):
             assert rel(got[0, m, comp], ref[m, comp]) < SAMPLE_TOL, (H, m, comp, rel(got[0, m, comp], ref[m, comp]))
 
 
+def test_spin2_wiener_filter_with_pixel_response():
+    """With a pixel response A the spin-2 Wiener filter solves the response problem: at 32^2 it matches the
+    dense filter of the equivalent data d / A, noise N / A^2 (A = 0 pixels masked); at 256^2 the oracle's
+    FP64 residual of that problem for the returned pair is below tol and equals the reported one."""
+    for H in (32, 256):
+        p, d2, N2, PB = _pair(H, H + 29)
+        rng = np.random.default_rng(H + 5)
+        A = rng.uniform(0.5, 1.5, (H, H)).astype(np.float32)
+        A[rng.integers(0, H, 4), rng.integers(0, H, 4)] = 0.0
+        r = wf.wf_solve_spin2(*_dev(p.d, d2, p.Ndiag, N2, p.mask, p.Pk, PB), tol=WF_TOL,
+                              A=torch.from_numpy(A).cuda())
+        got = r.s.cpu().numpy()
+        A64 = A.astype(np.float64)
+        safe = np.where(A64 != 0, A64, 1.0)
+        m2 = np.where(A64 == 0, 1, p.mask).astype(np.uint8)
+        e1, e2 = p.d / safe, d2 / safe
+        n1, n2 = p.Ndiag / safe ** 2, N2 / safe ** 2
+        assert r.status == 0 and r.resid < WF_TOL
+        if H == 32:
+            ref = S2.wiener_dense(e1, e2, n1, n2, m2, p.Pk, PB)
+            assert rel(got[0], ref[0]) < WF_TOL and rel(got[1], ref[1]) < WF_TOL
+        else:
+            # the GPU forms the transformed data in FP64 and rounds it once to FP32: the residuals agree to
+            # 1e-3 of themselves (as for the response in the plain solve), not to FP64 rounding
+            true = S2.residual(got[0], got[1], e1, e2, n1, n2, m2, p.Pk, PB)
+            assert true < WF_TOL and abs(true - r.resid) <= 1e-3 * true
+
+
 def test_shear_to_convergence_matches_oracle():
     rng = np.random.default_rng(3)
     for H in (16, 128, 256):
